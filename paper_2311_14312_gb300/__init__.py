@@ -1,0 +1,271 @@
+"""Python binding of libdc_fmm (argument marshalling only).
+
+Every computation runs in the native library's CUDA kernels; this module
+only converts arrays to pointers.  It raises ImportError when the native
+library has not been built (``paper_2311_14312_gb300.build.build()``): there
+is no fallback path.
+
+The names mirror the C ABI in ``include/dc_fmm.h`` (``dc_create``,
+``dc_build_tree``, ``dc_solve_density``, ``dc_render_viewport``, ...);
+:class:`Context` wraps them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+try:      # torch owns the CUDA runtime in this process; load it first
+    import torch  # noqa: F401
+except Exception:  # pragma: no cover - torch is a hard dependency of the tests
+    torch = None
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdc_fmm.so")
+
+# enums (dc_fmm.h)
+DC_OK, DC_ERR_ARG, DC_ERR_STATE, DC_ERR_CUDA, DC_ERR_OOM = 0, 1, 2, 3, 4
+DC_ERR_NOCONV, DC_ERR_TIMEOUT, DC_ERR_GEOMETRY, DC_ERR_UNSUPPORTED = 5, 6, 7, 8
+DC_FORM_DENSE64, DC_FORM_FMM64, DC_FORM_FMM32 = 0, 1, 2
+DC_X0_ONES, DC_X0_ZEROS, DC_X0_USER = 0, 1, 2
+DC_MEM_DEVICE, DC_MEM_HOST = 0, 1
+DC_F32, DC_F64 = 0, 1
+
+FORMS = {"dense64": DC_FORM_DENSE64, "fmm64": DC_FORM_FMM64, "fmm32": DC_FORM_FMM32}
+
+
+class dc_options(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int), ("g", ctypes.c_int), ("s_per_panel", ctypes.c_int),
+                ("p", ctypes.c_int), ("leaf_size", ctypes.c_int), ("max_depth", ctypes.c_int),
+                ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
+                ("gmres_max_iter", ctypes.c_int), ("x0_mode", ctypes.c_int),
+                ("stream", ctypes.c_void_p), ("domain", ctypes.c_double * 4)]
+
+
+class dc_sizes(ctypes.Structure):
+    _fields_ = [("n_curves", ctypes.c_int), ("n_panels", ctypes.c_int), ("n_nodes", ctypes.c_int),
+                ("n_segments", ctypes.c_int), ("n_pieces", ctypes.c_int),
+                ("n_cells", ctypes.c_int), ("n_leaves", ctypes.c_int), ("depth", ctypes.c_int),
+                ("root", ctypes.c_double * 3)]
+
+
+class dc_solve_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int * 3), ("rel_resid", ctypes.c_double * 3),
+                ("converged", ctypes.c_int), ("n_matvec", ctypes.c_int),
+                ("ms_rhs", ctypes.c_double), ("ms_solve", ctypes.c_double),
+                ("p2p_pairs", ctypes.c_longlong), ("m2l_pairs", ctypes.c_longlong)]
+
+
+class dc_viewport(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("y0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y1", ctypes.c_double), ("width", ctypes.c_int), ("height", ctypes.c_int)]
+
+
+class dc_render_stats(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("pixels", ctypes.c_longlong),
+                ("p2p_pairs", ctypes.c_longlong), ("m2l_pairs", ctypes.c_longlong)]
+
+
+EXPORTS = ["dc_default_options", "dc_create", "dc_destroy", "dc_build_tree", "dc_solve_density",
+           "dc_render_viewport", "dc_eval_points", "dc_get_density", "dc_set_density",
+           "dc_get_nodes", "dc_get_sizes", "dc_last_error", "dc_status_string",
+           "dc_abi_version", "dc_aux_tree_check"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_2311_14312_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.dc_default_options.argtypes = [ctypes.POINTER(dc_options)]
+    lib.dc_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(dc_options)]
+    lib.dc_destroy.argtypes = [P]
+    lib.dc_destroy.restype = None
+    lib.dc_build_tree.argtypes = [P, I, P, P, P, P]
+    lib.dc_solve_density.argtypes = [P, P, ctypes.POINTER(dc_solve_stats)]
+    lib.dc_render_viewport.argtypes = [P, I, ctypes.POINTER(dc_viewport), P, I, P, I,
+                                       ctypes.POINTER(dc_render_stats)]
+    lib.dc_eval_points.argtypes = [P, I, P, I, P, I, I]
+    lib.dc_get_density.argtypes = [P, P]
+    lib.dc_set_density.argtypes = [P, P]
+    lib.dc_get_nodes.argtypes = [P, P, P, P, P]
+    lib.dc_get_sizes.argtypes = [P, ctypes.POINTER(dc_sizes)]
+    lib.dc_last_error.argtypes = [P]
+    lib.dc_last_error.restype = ctypes.c_char_p
+    lib.dc_status_string.argtypes = [I]
+    lib.dc_status_string.restype = ctypes.c_char_p
+    lib.dc_abi_version.restype = I
+    lib.dc_aux_tree_check.argtypes = [I, P, P, I, I, P]
+    for name in EXPORTS:
+        if name not in ("dc_destroy", "dc_last_error", "dc_status_string", "dc_abi_version"):
+            getattr(lib, name).restype = I
+    _ = D
+    return lib
+
+
+_lib = None
+
+
+def _get_lib():
+    """The native library (loaded on first use; ImportError if not built)."""
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    return _lib
+
+
+def __getattr__(name):
+    if name == "lib":
+        return _get_lib()
+    raise AttributeError(name)
+
+
+class DcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[{status}] {msg}")
+        self.status = status
+
+
+def _ptr(a) -> ctypes.c_void_p:
+    if a is None:
+        return ctypes.c_void_p(0)
+    if isinstance(a, np.ndarray):
+        return ctypes.c_void_p(a.ctypes.data)
+    return ctypes.c_void_p(a.data_ptr())       # torch tensor
+
+
+def _is_device(a) -> bool:
+    return a is not None and not isinstance(a, np.ndarray) and a.is_cuda
+
+
+def default_options(**overrides) -> dc_options:
+    o = dc_options()
+    _get_lib().dc_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if k == "form" and isinstance(v, str):
+            v = FORMS[v]
+        if k == "domain":
+            for i in range(4):
+                o.domain[i] = float(v[i])
+            continue
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """One drawing on the current CUDA device (wraps a dc_ctx)."""
+
+    def __init__(self, stream=None, **opts):
+        if stream is None and torch is not None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream().cuda_stream
+        self.options = default_options(stream=stream, **opts)
+        h = ctypes.c_void_p()
+        st = _get_lib().dc_create(ctypes.byref(h), ctypes.byref(self.options))
+        if st != DC_OK:
+            raise DcError(st, _get_lib().dc_last_error(None).decode())
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _get_lib().dc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, allow=()):
+        if st != DC_OK and st not in allow:
+            raise DcError(st, _get_lib().dc_last_error(self._h).decode())
+        return st
+
+    # ------------------------------------------------------------ build --
+    def build_tree(self, ctrl, panel_ptr, panel_start, colours):
+        ctrl = np.ascontiguousarray(ctrl, dtype=np.float64)
+        ptr = np.ascontiguousarray(panel_ptr, dtype=np.int32)
+        start = np.ascontiguousarray(panel_start, dtype=np.float64)
+        col = np.ascontiguousarray(colours, dtype=np.float64)
+        self._check(_get_lib().dc_build_tree(self._h, int(ctrl.shape[0]), _ptr(ctrl), _ptr(ptr),
+                                      _ptr(start), _ptr(col)))
+        return self
+
+    def build_drawing(self, drawing):
+        return self.build_tree(drawing.ctrl, drawing.panel_ptr, drawing.panel_start,
+                               drawing.colours)
+
+    def sizes(self) -> dc_sizes:
+        s = dc_sizes()
+        self._check(_get_lib().dc_get_sizes(self._h, ctypes.byref(s)))
+        return s
+
+    def nodes(self):
+        n = self.sizes().n_nodes
+        xy, t = np.zeros((n, 2)), np.zeros(n)
+        up, um = np.zeros((n, 3)), np.zeros((n, 3))
+        self._check(_get_lib().dc_get_nodes(self._h, _ptr(xy), _ptr(t), _ptr(up), _ptr(um)))
+        return xy, t, up, um
+
+    # ------------------------------------------------------------ solve --
+    def solve_density(self, x0=None, allow_noconv=False) -> dc_solve_stats:
+        stats = dc_solve_stats()
+        x = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        allow = (DC_ERR_NOCONV,) if allow_noconv else ()
+        self._check(_get_lib().dc_solve_density(self._h, _ptr(x), ctypes.byref(stats)), allow)
+        return stats
+
+    def get_density(self) -> np.ndarray:
+        out = np.zeros((self.sizes().n_nodes, 3))
+        self._check(_get_lib().dc_get_density(self._h, _ptr(out)))
+        return out
+
+    def set_density(self, sigma):
+        s = np.ascontiguousarray(sigma, dtype=np.float64)
+        self._check(_get_lib().dc_set_density(self._h, _ptr(s)))
+
+    # ----------------------------------------------------------- render --
+    def render_viewport(self, viewports, rgb=None, rgb8=None, stats=False):
+        """viewports: list of (x0, y0, x1, y1, width, height).  rgb / rgb8:
+        preallocated [sum h w, 3] arrays (torch CUDA tensors for device
+        output, numpy arrays for host output); rgb float32 or float64."""
+        n = len(viewports)
+        arr = (dc_viewport * max(n, 1))()
+        for i, v in enumerate(viewports):
+            arr[i] = dc_viewport(float(v[0]), float(v[1]), float(v[2]), float(v[3]),
+                                 int(v[4]), int(v[5]))
+        where = DC_MEM_DEVICE if (_is_device(rgb) or _is_device(rgb8)) else DC_MEM_HOST
+        dt = DC_F64
+        if rgb is not None:
+            dt = DC_F64 if str(rgb.dtype) in ("float64", "torch.float64") else DC_F32
+        st = dc_render_stats()
+        self._check(_get_lib().dc_render_viewport(self._h, n, arr, _ptr(rgb), dt, _ptr(rgb8), where,
+                                           ctypes.byref(st) if stats else None))
+        return st if stats else None
+
+    def eval_points(self, xy, out):
+        """xy [n, 2] float64 and out [n, 3] (float32/float64), both numpy
+        (host) or both torch CUDA tensors (device)."""
+        n = int(xy.shape[0])
+        xw = DC_MEM_DEVICE if _is_device(xy) else DC_MEM_HOST
+        ow = DC_MEM_DEVICE if _is_device(out) else DC_MEM_HOST
+        dt = DC_F64 if str(out.dtype) in ("float64", "torch.float64") else DC_F32
+        if isinstance(xy, np.ndarray):
+            xy = np.ascontiguousarray(xy, dtype=np.float64)
+        self._check(_get_lib().dc_eval_points(self._h, n, _ptr(xy), xw, _ptr(out), dt, ow))
+        return out
+
+
+def aux_tree_check(seg_xy, domain=(0.0, 0.0, 1.0, 1.0), leaf_size=64, max_depth=30):
+    """Host-only quadtree check (dc_aux_tree_check): returns a dict."""
+    seg = np.ascontiguousarray(seg_xy, dtype=np.float64).reshape(-1, 4)
+    dom = np.ascontiguousarray(domain, dtype=np.float64)
+    out = np.zeros(6)
+    st = _get_lib().dc_aux_tree_check(int(seg.shape[0]), _ptr(seg), _ptr(dom), int(leaf_size),
+                                      int(max_depth), _ptr(out))
+    if st != DC_OK:
+        raise DcError(st, "dc_aux_tree_check failed")
+    keys = ["cells", "leaves", "depth", "pieces", "bad_pairs", "clip_rel_err"]
+    return dict(zip(keys, out.tolist()))

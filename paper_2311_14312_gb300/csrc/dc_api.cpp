@@ -1,0 +1,621 @@
+// C ABI of libdc_fmm (declarations and contracts in include/dc_fmm.h).
+//
+// The entry points follow the paper's problem statement: build the
+// discretisation and quadtree (Alg. 3 lines 1-2), solve for the density
+// (Alg. 3 lines 3-5), render viewports (Alg. 4 line 3).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "dc_internal.h"
+#include "fmm.h"
+#include "tree.h"
+
+using dc::DevBuf;
+
+struct dc_ctx {
+    dc_options opt{};
+    std::string err;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int state = 0;                 // 0 empty, 1 built, 2 density available
+    dc::Geometry geo;
+    dc::DevGeom dg;
+    DevBuf<double> mu, sigma, b, fmu, sbar, mbar, u64, xy;
+    DevBuf<float> u32;
+    DevBuf<unsigned char> stage8;
+    DevBuf<double> stage64;
+    DevBuf<double> AG, AF;         // dense form
+    bool seg_density_valid = false;
+    dc::GmresWork *gw = nullptr;
+    std::unique_ptr<dc::Fmm> fmm;  // FMM forms
+    ~dc_ctx() {
+        if (gw) dc::gmres_work_destroy(gw);
+    }
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+dc_status fail(dc_ctx *ctx, dc_status st, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+dc_status cuda_fail(dc_ctx *ctx, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, DC_ERR_OOM, m);
+    return fail(ctx, DC_ERR_CUDA, m);
+}
+
+#define DC_CK(ctx, expr, where)                        \
+    do {                                               \
+        cudaError_t e__ = (expr);                      \
+        if (e__ != cudaSuccess) return cuda_fail(ctx, e__, where); \
+    } while (0)
+
+dc_status check_options(const dc_options &o, std::string &msg) {
+    if (o.form < DC_FORM_DENSE64 || o.form > DC_FORM_FMM32) {
+        msg = "options: unknown form";
+        return DC_ERR_ARG;
+    }
+    if (o.g < 1 || o.g > dc::kMaxG) {
+        msg = "options: g must be in [1, 32]";
+        return DC_ERR_ARG;
+    }
+    if (o.s_per_panel < o.g || o.s_per_panel > 4096) {
+        msg = "options: s_per_panel must be in [g, 4096]";
+        return DC_ERR_ARG;
+    }
+    if (o.p < 1 || o.p > dc::kMaxP) {
+        msg = "options: p must be in [1, 40]";
+        return DC_ERR_ARG;
+    }
+    if (o.leaf_size < 1 || o.leaf_size > 4096) {
+        msg = "options: leaf_size must be in [1, 4096]";
+        return DC_ERR_ARG;
+    }
+    if (o.max_depth < 1 || o.max_depth > 40) {
+        msg = "options: max_depth must be in [1, 40]";
+        return DC_ERR_ARG;
+    }
+    if (!(o.gmres_tol > 0.0) || o.gmres_restart < 1 || o.gmres_max_iter < 1 ||
+        o.gmres_restart > 4096) {
+        msg = "options: need gmres_tol > 0, 1 <= gmres_restart <= 4096, gmres_max_iter >= 1";
+        return DC_ERR_ARG;
+    }
+    if (o.x0_mode < DC_X0_ONES || o.x0_mode > DC_X0_USER) {
+        msg = "options: unknown x0_mode";
+        return DC_ERR_ARG;
+    }
+    for (double d : o.domain)
+        if (!std::isfinite(d)) {
+            msg = "options: domain must be finite";
+            return DC_ERR_ARG;
+        }
+    if (!(o.domain[2] >= o.domain[0]) || !(o.domain[3] >= o.domain[1])) {
+        msg = "options: domain must have x1 >= x0 and y1 >= y0";
+        return DC_ERR_ARG;
+    }
+    return DC_OK;
+}
+
+// Dense operator y = A_G x (plain form).
+struct DenseOp : dc::Operator {
+    const double *A;
+    int N;
+    cudaError_t apply(const double *x, double *y, cudaStream_t st) override {
+        return dc::launch_dense_gemv(A, N, x, y, st);
+    }
+};
+
+// FMM operator y = G_H x (Alg. 3 line 5, the matvec of GMRES).
+struct FmmOp : dc::Operator {
+    dc::Fmm *fmm;
+    cudaError_t apply(const double *x, double *y, cudaStream_t st) override {
+        return fmm->apply_single_layer(x, y, st);
+    }
+};
+
+dc_status ensure_segment_density(dc_ctx *ctx) {
+    if (ctx->seg_density_valid) return DC_OK;
+    DC_CK(ctx, dc::launch_interp(ctx->dg, ctx->sigma.ptr, ctx->sbar.ptr, ctx->stream), "interp");
+    DC_CK(ctx, dc::launch_interp(ctx->dg, ctx->mu.ptr, ctx->mbar.ptr, ctx->stream), "interp");
+    ctx->seg_density_valid = true;
+    return DC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dc_abi_version(void) { return DC_ABI_VERSION; }
+
+dc_status dc_aux_tree_check(int n_seg, const double *seg_xy, const double *domain, int leaf_size,
+                            int max_depth, double *out) {
+    if (n_seg < 0 || (n_seg > 0 && !seg_xy) || !domain || !out || leaf_size < 1 ||
+        max_depth < 1 || max_depth > 40)
+        return DC_ERR_ARG;
+    std::vector<double> seg(seg_xy, seg_xy + 4 * size_t(n_seg));
+    for (double v : seg)
+        if (!std::isfinite(v)) return DC_ERR_ARG;
+    for (int i = 0; i < 4; ++i)
+        if (!std::isfinite(domain[i])) return DC_ERR_ARG;
+    dc::Tree t;
+    std::string msg;
+    if (!dc::build_quadtree(seg, domain, leaf_size, max_depth, t, msg)) return DC_ERR_GEOMETRY;
+    out[0] = t.n_cells();
+    out[1] = t.n_leaves();
+    out[2] = t.depth;
+    out[3] = double(t.pc_seg.size());
+    out[4] = double(dc::check_quadtree_routes(t));
+    std::vector<double> sum(n_seg, 0.0);
+    for (size_t i = 0; i < t.pc_seg.size(); ++i) {
+        const double *q = &t.pc_xy[4 * i];
+        sum[t.pc_seg[i]] += std::hypot(q[2] - q[0], q[3] - q[1]);
+    }
+    double worst = 0.0;
+    for (int k = 0; k < n_seg; ++k) {
+        const double *q = &seg[4 * size_t(k)];
+        double L = std::hypot(q[2] - q[0], q[3] - q[1]);
+        if (L > 0) worst = std::max(worst, std::fabs(sum[k] - L) / L);
+    }
+    out[5] = worst;
+    return DC_OK;
+}
+
+const char *dc_status_string(dc_status st) {
+    switch (st) {
+        case DC_OK: return "ok";
+        case DC_ERR_ARG: return "invalid argument";
+        case DC_ERR_STATE: return "call out of order";
+        case DC_ERR_CUDA: return "CUDA error";
+        case DC_ERR_OOM: return "out of memory";
+        case DC_ERR_NOCONV: return "GMRES did not converge";
+        case DC_ERR_TIMEOUT: return "device wait timed out";
+        case DC_ERR_GEOMETRY: return "degenerate geometry";
+        case DC_ERR_UNSUPPORTED: return "unsupported option combination";
+    }
+    return "unknown status";
+}
+
+const char *dc_last_error(dc_ctx *ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return ctx->err.c_str();
+}
+
+dc_status dc_default_options(dc_options *opt) {
+    if (!opt) return DC_ERR_ARG;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->form = DC_FORM_FMM32;
+    opt->g = 16;
+    opt->s_per_panel = 80;
+    opt->p = 24;
+    opt->leaf_size = 64;
+    opt->max_depth = 30;
+    opt->gmres_tol = 1e-10;
+    opt->gmres_restart = 200;
+    opt->gmres_max_iter = 2000;
+    opt->x0_mode = DC_X0_ONES;
+    opt->stream = nullptr;
+    opt->domain[0] = 0.0;
+    opt->domain[1] = 0.0;
+    opt->domain[2] = 1.0;
+    opt->domain[3] = 1.0;
+    return DC_OK;
+}
+
+dc_status dc_create(dc_ctx **out, const dc_options *opt) {
+    if (!out) {
+        g_create_error = "dc_create: out is NULL";
+        return DC_ERR_ARG;
+    }
+    *out = nullptr;
+    dc_options o;
+    if (opt) o = *opt;
+    else dc_default_options(&o);
+    std::string msg;
+    dc_status st = check_options(o, msg);
+    if (st != DC_OK) {
+        g_create_error = msg;
+        return st;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("dc_create: ") + cudaGetErrorString(e);
+        return DC_ERR_CUDA;
+    }
+    dc_ctx *ctx = new (std::nothrow) dc_ctx();
+    if (!ctx) {
+        g_create_error = "dc_create: host allocation failed";
+        return DC_ERR_OOM;
+    }
+    ctx->opt = o;
+    ctx->device = dev;
+    ctx->stream = static_cast<cudaStream_t>(o.stream);
+    ctx->gw = dc::gmres_work_create();
+    *out = ctx;
+    return DC_OK;
+}
+
+void dc_destroy(dc_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    delete ctx;
+}
+
+dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int *panel_ptr,
+                        const double *panel_start, const double *colours) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    ctx->state = 0;
+    ctx->seg_density_valid = false;
+    std::string msg;
+    dc_status st = dc::discretise(n_curves, ctrl, panel_ptr, panel_start, colours, ctx->opt.g,
+                                  ctx->opt.s_per_panel, ctx->geo, msg);
+    if (st != DC_OK) return fail(ctx, st, msg);
+    const dc::Geometry &G = ctx->geo;
+    dc::DevGeom &D = ctx->dg;
+    D.N = G.n_nodes();
+    D.S = G.n_segments();
+    D.g = G.g;
+    D.s = G.s;
+    D.n_panels = G.n_panels;
+    cudaStream_t s = ctx->stream;
+    auto up = [&](auto &buf, const auto &vec, const char *what) -> dc_status {
+        DC_CK(ctx, buf.alloc(vec.size()), what);
+        DC_CK(ctx,
+              cudaMemcpyAsync(buf.ptr, vec.data(), vec.size() * sizeof(vec[0]),
+                              cudaMemcpyHostToDevice, s),
+              what);
+        return DC_OK;
+    };
+    if ((st = up(D.seg, G.seg_xy, "upload segments")) != DC_OK) return st;
+    if ((st = up(D.segw, G.seg_w, "upload weights")) != DC_OK) return st;
+    if ((st = up(D.node_xy, G.node_xy, "upload nodes")) != DC_OK) return st;
+    if ((st = up(D.node_seg, G.node_seg, "upload nodes")) != DC_OK) return st;
+    if ((st = up(D.node_seg2, G.node_seg2, "upload nodes")) != DC_OK) return st;
+    if ((st = up(D.lambda, G.lambda, "upload interpolation")) != DC_OK) return st;
+    if ((st = up(D.u_plus, G.u_plus, "upload colours")) != DC_OK) return st;
+    if ((st = up(D.u_minus, G.u_minus, "upload colours")) != DC_OK) return st;
+    size_t n3 = size_t(3) * D.N, s3 = size_t(3) * D.S;
+    DC_CK(ctx, ctx->mu.alloc(n3), "alloc");
+    DC_CK(ctx, ctx->sigma.alloc(n3), "alloc");
+    DC_CK(ctx, ctx->b.alloc(n3), "alloc");
+    DC_CK(ctx, ctx->fmu.alloc(n3), "alloc");
+    DC_CK(ctx, ctx->sbar.alloc(s3), "alloc");
+    DC_CK(ctx, ctx->mbar.alloc(s3), "alloc");
+    DC_CK(ctx, dc::launch_mu(D, ctx->mu.ptr, s), "mu");
+    ctx->AG.release();
+    ctx->AF.release();
+    ctx->fmm.reset();
+    if (ctx->opt.form == DC_FORM_DENSE64) {
+        size_t nn = size_t(D.N) * D.N;
+        DC_CK(ctx, ctx->AG.alloc(nn), "alloc dense A_G");
+        DC_CK(ctx, ctx->AF.alloc(nn), "alloc dense A_F");
+        DC_CK(ctx, dc::launch_dense_assemble(D, ctx->AG.ptr, ctx->AF.ptr, s), "dense assembly");
+    } else {
+        ctx->fmm.reset(new (std::nothrow) dc::Fmm());
+        if (!ctx->fmm) return fail(ctx, DC_ERR_OOM, "build_tree: host allocation failed");
+        st = ctx->fmm->build(ctx->opt, G, D, s, msg);
+        if (st != DC_OK) {
+            ctx->fmm.reset();
+            return fail(ctx, st, msg);
+        }
+    }
+    DC_CK(ctx, cudaStreamSynchronize(s), "build_tree");
+    ctx->state = 1;
+    return DC_OK;
+}
+
+dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "solve_density: call build_tree first");
+    if (ctx->opt.x0_mode == DC_X0_USER && !x0)
+        return fail(ctx, DC_ERR_ARG, "solve_density: x0_mode is DC_X0_USER but x0 is NULL");
+    const int N = ctx->dg.N;
+    cudaStream_t s = ctx->stream;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    cudaEvent_t e0, e1;
+    DC_CK(ctx, cudaEventCreate(&e0), "event");
+    DC_CK(ctx, cudaEventCreate(&e1), "event");
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } guard{e0, e1};
+    DC_CK(ctx, cudaEventRecord(e0, s), "event");
+    // b = (u+ + u-)/2 - F_H mu  (Alg. 3 line 4)
+    if (ctx->opt.form == DC_FORM_DENSE64) {
+        DC_CK(ctx, dc::launch_dense_gemv(ctx->AF.ptr, N, ctx->mu.ptr, ctx->fmu.ptr, s), "rhs");
+    } else {
+        DC_CK(ctx, ctx->fmm->apply_double_layer(ctx->mu.ptr, ctx->fmu.ptr, s), "rhs");
+    }
+    DC_CK(ctx, dc::launch_rhs(ctx->dg, ctx->fmu.ptr, ctx->b.ptr, s), "rhs");
+    DC_CK(ctx, cudaEventRecord(e1, s), "event");
+    // x0
+    size_t n3b = size_t(3) * N * sizeof(double);
+    if (ctx->opt.x0_mode == DC_X0_USER) {
+        for (size_t i = 0; i < size_t(3) * N; ++i)
+            if (!std::isfinite(x0[i])) return fail(ctx, DC_ERR_ARG, "solve_density: non-finite x0");
+        DC_CK(ctx, cudaMemcpyAsync(ctx->sigma.ptr, x0, n3b, cudaMemcpyHostToDevice, s), "x0");
+    } else if (ctx->opt.x0_mode == DC_X0_ZEROS) {
+        DC_CK(ctx, cudaMemsetAsync(ctx->sigma.ptr, 0, n3b, s), "x0");
+    } else {
+        std::vector<double> ones(size_t(3) * N, 1.0);
+        DC_CK(ctx, cudaMemcpyAsync(ctx->sigma.ptr, ones.data(), n3b, cudaMemcpyHostToDevice, s),
+              "x0");
+        DC_CK(ctx, cudaStreamSynchronize(s), "x0");
+    }
+    ctx->seg_density_valid = false;
+    dc::GmresResult gr;
+    std::string msg;
+    auto t0 = std::chrono::steady_clock::now();
+    cudaError_t ce;
+    if (ctx->opt.form == DC_FORM_DENSE64) {
+        DenseOp op;
+        op.A = ctx->AG.ptr;
+        op.N = N;
+        ce = dc::gmres_solve(ctx->gw, op, N, ctx->b.ptr, ctx->sigma.ptr, ctx->opt.gmres_tol,
+                             ctx->opt.gmres_restart, ctx->opt.gmres_max_iter, s, gr, msg);
+    } else {
+        ce = ctx->fmm->solve(ctx->gw, ctx->b.ptr, ctx->sigma.ptr, ctx->opt, s, gr, msg);
+    }
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, msg.empty() ? "gmres" : msg.c_str());
+    DC_CK(ctx, cudaStreamSynchronize(s), "gmres");
+    auto t1 = std::chrono::steady_clock::now();
+    if (stats) {
+        for (int c = 0; c < 3; ++c) {
+            stats->iters[c] = gr.iters[c];
+            stats->rel_resid[c] = gr.rel_resid[c];
+        }
+        stats->converged = gr.converged;
+        stats->n_matvec = gr.n_matvec + 1;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        stats->ms_rhs = ms;
+        stats->ms_solve = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        if (ctx->fmm) {
+            stats->p2p_pairs = ctx->fmm->p2p_pairs_nodes();
+            stats->m2l_pairs = ctx->fmm->m2l_pairs();
+        }
+    }
+    ctx->state = 2;
+    if (!gr.converged)
+        return fail(ctx, DC_ERR_NOCONV, "solve_density: gmres_max_iter reached before gmres_tol");
+    return DC_OK;
+}
+
+dc_status dc_set_density(dc_ctx *ctx, const double *sigma_in) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "set_density: call build_tree first");
+    if (!sigma_in) return fail(ctx, DC_ERR_ARG, "set_density: NULL input");
+    size_t n3 = size_t(3) * ctx->dg.N;
+    for (size_t i = 0; i < n3; ++i)
+        if (!std::isfinite(sigma_in[i]))
+            return fail(ctx, DC_ERR_ARG, "set_density: non-finite value");
+    DC_CK(ctx,
+          cudaMemcpyAsync(ctx->sigma.ptr, sigma_in, n3 * sizeof(double), cudaMemcpyHostToDevice,
+                          ctx->stream),
+          "set_density");
+    DC_CK(ctx, cudaStreamSynchronize(ctx->stream), "set_density");
+    ctx->seg_density_valid = false;
+    ctx->state = 2;
+    return DC_OK;
+}
+
+dc_status dc_get_density(dc_ctx *ctx, double *sigma_out) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (ctx->state < 2) return fail(ctx, DC_ERR_STATE, "get_density: no density yet");
+    if (!sigma_out) return fail(ctx, DC_ERR_ARG, "get_density: NULL output");
+    size_t n3 = size_t(3) * ctx->dg.N;
+    DC_CK(ctx,
+          cudaMemcpyAsync(sigma_out, ctx->sigma.ptr, n3 * sizeof(double), cudaMemcpyDeviceToHost,
+                          ctx->stream),
+          "get_density");
+    DC_CK(ctx, cudaStreamSynchronize(ctx->stream), "get_density");
+    return DC_OK;
+}
+
+dc_status dc_get_nodes(dc_ctx *ctx, double *xy, double *t, double *u_plus, double *u_minus) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "get_nodes: call build_tree first");
+    const dc::Geometry &G = ctx->geo;
+    if (xy) std::memcpy(xy, G.node_xy.data(), G.node_xy.size() * sizeof(double));
+    if (t) std::memcpy(t, G.node_t.data(), G.node_t.size() * sizeof(double));
+    if (u_plus) std::memcpy(u_plus, G.u_plus.data(), G.u_plus.size() * sizeof(double));
+    if (u_minus) std::memcpy(u_minus, G.u_minus.data(), G.u_minus.size() * sizeof(double));
+    return DC_OK;
+}
+
+dc_status dc_get_sizes(dc_ctx *ctx, dc_sizes *out) {
+    if (!ctx || !out) return DC_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "get_sizes: call build_tree first");
+    out->n_curves = ctx->geo.n_curves;
+    out->n_panels = ctx->geo.n_panels;
+    out->n_nodes = ctx->geo.n_nodes();
+    out->n_segments = ctx->geo.n_segments();
+    if (ctx->fmm) ctx->fmm->fill_sizes(out);
+    else out->n_pieces = out->n_segments;
+    return DC_OK;
+}
+
+dc_status dc_render_viewport(dc_ctx *ctx, int n_vp, const dc_viewport *vps, void *rgb,
+                             int rgb_dtype, unsigned char *rgb8, int out_where,
+                             dc_render_stats *stats) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (ctx->state < 2) return fail(ctx, DC_ERR_STATE, "render_viewport: no density yet");
+    if (n_vp < 0 || (n_vp > 0 && !vps)) return fail(ctx, DC_ERR_ARG, "render_viewport: bad viewports");
+    if (rgb && rgb_dtype != DC_F32 && rgb_dtype != DC_F64)
+        return fail(ctx, DC_ERR_ARG, "render_viewport: rgb_dtype must be DC_F32 or DC_F64");
+    if (out_where != DC_MEM_DEVICE && out_where != DC_MEM_HOST)
+        return fail(ctx, DC_ERR_ARG, "render_viewport: out_where must be DC_MEM_DEVICE or DC_MEM_HOST");
+    long long total = 0;
+    for (int v = 0; v < n_vp; ++v) {
+        const dc_viewport &vp = vps[v];
+        if (vp.width < 0 || vp.height < 0 || vp.width > 65536 || vp.height > 65536)
+            return fail(ctx, DC_ERR_ARG, "render_viewport: width/height must be in [0, 65536]");
+        if (!std::isfinite(vp.x0) || !std::isfinite(vp.x1) || !std::isfinite(vp.y0) ||
+            !std::isfinite(vp.y1))
+            return fail(ctx, DC_ERR_ARG, "render_viewport: non-finite viewport");
+        total += (long long)vp.width * vp.height;
+    }
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (total == 0) return DC_OK;
+    cudaStream_t s = ctx->stream;
+    dc_status st = ensure_segment_density(ctx);
+    if (st != DC_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (stats) {
+        DC_CK(ctx, cudaEventCreate(&e0), "event");
+        DC_CK(ctx, cudaEventCreate(&e1), "event");
+        DC_CK(ctx, cudaEventRecord(e0, s), "event");
+    }
+    // destination buffers (device staging when the caller gave host memory)
+    size_t esz = (rgb_dtype == DC_F64) ? sizeof(double) : sizeof(float);
+    void *drgb = rgb;
+    unsigned char *drgb8 = rgb8;
+    if (out_where == DC_MEM_HOST) {
+        if (rgb) {
+            DC_CK(ctx, ctx->stage64.ensure((size_t(3) * total * esz + 7) / 8), "alloc staging");
+            drgb = ctx->stage64.ptr;
+        }
+        if (rgb8) {
+            DC_CK(ctx, ctx->stage8.ensure(size_t(3) * total), "alloc staging");
+            drgb8 = ctx->stage8.ptr;
+        }
+    }
+    if (ctx->fmm) DC_CK(ctx, ctx->fmm->prepare_eval(ctx->sbar.ptr, ctx->mbar.ptr, s), "fmm passes");
+    long long off = 0;
+    for (int v = 0; v < n_vp; ++v) {
+        const dc_viewport &vp = vps[v];
+        long long np = (long long)vp.width * vp.height;
+        if (np == 0) continue;
+        dc::VpDev d;
+        d.x0 = vp.x0;
+        d.y0 = vp.y0;
+        d.dx = (vp.x1 - vp.x0) / vp.width;
+        d.dy = (vp.y1 - vp.y0) / vp.height;
+        d.width = vp.width;
+        d.height = vp.height;
+        d.offset = off;
+        void *orgb = drgb ? static_cast<char *>(drgb) + size_t(3) * off * esz : nullptr;
+        unsigned char *orgb8 = drgb8 ? drgb8 + size_t(3) * off : nullptr;
+        if (ctx->opt.form == DC_FORM_DENSE64) {
+            DC_CK(ctx, ctx->u64.ensure(size_t(3) * np), "alloc");
+            DC_CK(ctx,
+                  dc::launch_dense_eval_grid(ctx->dg, ctx->sbar.ptr, ctx->mbar.ptr, d,
+                                             ctx->u64.ptr, s),
+                  "dense render");
+            DC_CK(ctx, dc::launch_write_outputs(ctx->u64.ptr, np, orgb, rgb_dtype, orgb8, s),
+                  "outputs");
+        } else {
+            std::string msg;
+            dc_status fs = ctx->fmm->render_grid(d, ctx->sbar.ptr, ctx->mbar.ptr, orgb, rgb_dtype,
+                                                 orgb8, s, msg);
+            if (fs != DC_OK) return fail(ctx, fs, msg);
+        }
+        off += np;
+    }
+    if (out_where == DC_MEM_HOST) {
+        if (rgb)
+            DC_CK(ctx,
+                  cudaMemcpyAsync(rgb, drgb, size_t(3) * total * esz, cudaMemcpyDeviceToHost, s),
+                  "copy out");
+        if (rgb8)
+            DC_CK(ctx, cudaMemcpyAsync(rgb8, drgb8, size_t(3) * total, cudaMemcpyDeviceToHost, s),
+                  "copy out");
+        DC_CK(ctx, cudaStreamSynchronize(s), "render");
+    }
+    if (stats) {
+        DC_CK(ctx, cudaEventRecord(e1, s), "event");
+        DC_CK(ctx, cudaEventSynchronize(e1), "event");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        stats->ms = ms;
+        stats->pixels = total;
+        if (ctx->fmm) {
+            stats->p2p_pairs = ctx->fmm->last_render_p2p_pairs();
+            stats->m2l_pairs = ctx->fmm->m2l_pairs();
+        } else {
+            stats->p2p_pairs = total * (long long)ctx->dg.S;
+        }
+    }
+    DC_CK(ctx, cudaGetLastError(), "render");
+    return DC_OK;
+}
+
+dc_status dc_eval_points(dc_ctx *ctx, int n, const void *xy, int xy_where, void *out,
+                         int out_dtype, int out_where) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (ctx->state < 2) return fail(ctx, DC_ERR_STATE, "eval_points: no density yet");
+    if (n < 0 || (n > 0 && (!xy || !out)))
+        return fail(ctx, DC_ERR_ARG, "eval_points: bad arguments");
+    if (out_dtype != DC_F32 && out_dtype != DC_F64)
+        return fail(ctx, DC_ERR_ARG, "eval_points: out_dtype must be DC_F32 or DC_F64");
+    if ((xy_where != DC_MEM_DEVICE && xy_where != DC_MEM_HOST) ||
+        (out_where != DC_MEM_DEVICE && out_where != DC_MEM_HOST))
+        return fail(ctx, DC_ERR_ARG, "eval_points: bad memory kind");
+    if (n == 0) return DC_OK;
+    cudaStream_t s = ctx->stream;
+    dc_status st = ensure_segment_density(ctx);
+    if (st != DC_OK) return st;
+    const double *dxy = static_cast<const double *>(xy);
+    if (xy_where == DC_MEM_HOST) {
+        const double *h = static_cast<const double *>(xy);
+        for (int i = 0; i < 2 * n; ++i)
+            if (!std::isfinite(h[i])) return fail(ctx, DC_ERR_ARG, "eval_points: non-finite point");
+        DC_CK(ctx, ctx->xy.ensure(size_t(2) * n), "alloc");
+        DC_CK(ctx, cudaMemcpyAsync(ctx->xy.ptr, h, size_t(2) * n * sizeof(double),
+                                   cudaMemcpyHostToDevice, s),
+              "copy points");
+        dxy = ctx->xy.ptr;
+    }
+    size_t esz = (out_dtype == DC_F64) ? sizeof(double) : sizeof(float);
+    void *dout = out;
+    if (out_where == DC_MEM_HOST) {
+        DC_CK(ctx, ctx->stage64.ensure((size_t(3) * n * esz + 7) / 8), "alloc staging");
+        dout = ctx->stage64.ptr;
+    }
+    if (ctx->opt.form == DC_FORM_DENSE64) {
+        DC_CK(ctx, ctx->u64.ensure(size_t(3) * n), "alloc");
+        DC_CK(ctx,
+              dc::launch_dense_eval_points(ctx->dg, ctx->sbar.ptr, ctx->mbar.ptr, dxy, n,
+                                           ctx->u64.ptr, s),
+              "dense eval");
+        DC_CK(ctx, dc::launch_write_outputs(ctx->u64.ptr, n, dout, out_dtype, nullptr, s),
+              "outputs");
+    } else {
+        std::string msg;
+        DC_CK(ctx, ctx->fmm->prepare_eval(ctx->sbar.ptr, ctx->mbar.ptr, s), "fmm passes");
+        dc_status fs =
+            ctx->fmm->eval_points(dxy, n, ctx->sbar.ptr, ctx->mbar.ptr, dout, out_dtype, s, msg);
+        if (fs != DC_OK) return fail(ctx, fs, msg);
+    }
+    if (out_where == DC_MEM_HOST) {
+        DC_CK(ctx, cudaMemcpyAsync(out, dout, size_t(3) * n * esz, cudaMemcpyDeviceToHost, s),
+              "copy out");
+        DC_CK(ctx, cudaStreamSynchronize(s), "eval_points");
+    }
+    DC_CK(ctx, cudaGetLastError(), "eval_points");
+    return DC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+// Internal declarations of libdc_fmm (host side).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dc_fmm.h"
+
+namespace dc {
+
+constexpr int kMaxG = 32;        // nodes per panel supported by the kernels
+constexpr int kMaxP = 40;        // expansion order supported by the kernels
+
+// ------------------------------------------------------------ geometry --
+// Host discretisation of a drawing (Sec. 4.2, App. A, App. B).
+struct Geometry {
+    int n_curves = 0, n_panels = 0, g = 0, s = 0;
+    std::vector<double> node_xy;      // [N][2] collocation points (polyline)
+    std::vector<double> node_t;       // [N] Bezier parameter
+    std::vector<int> node_seg;        // [N] segment holding the node
+    std::vector<int> node_seg2;       // [N] second segment at a vertex or -1
+    std::vector<int> node_curve;      // [N]
+    std::vector<double> seg_xy;       // [S][4] x1 y1 x2 y2
+    std::vector<double> seg_w;        // [S] arc length / chord length
+    std::vector<double> lambda;       // [s][g] node -> segment-midpoint map
+    std::vector<double> u_plus;       // [N][3]
+    std::vector<double> u_minus;      // [N][3]
+    std::vector<double> curve_len;    // [n_curves]
+    double bbox[4] = {0, 0, 0, 0};    // of all segment endpoints
+    int n_nodes() const { return n_panels * g; }
+    int n_segments() const { return n_panels * s; }
+};
+
+// Returns DC_OK or an error with a message in err.
+dc_status discretise(int n_curves, const double *ctrl, const int *panel_ptr,
+                     const double *panel_start, const double *colours, int g,
+                     int s, Geometry &out, std::string &err);
+
+// Gauss-Legendre nodes on [-1, 1] (ascending) and weights.
+void gauss_legendre_rule(int n, double *x, double *w);
+
+// ---------------------------------------------------------- device util --
+template <typename T>
+struct DevBuf {
+    T *ptr = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    cudaError_t alloc(size_t count) {
+        release();
+        if (count == 0) return cudaSuccess;
+        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&ptr), count * sizeof(T));
+        if (e == cudaSuccess) n = count; else ptr = nullptr;
+        return e;
+    }
+    cudaError_t ensure(size_t count) {
+        if (count <= n) return cudaSuccess;
+        return alloc(count);
+    }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        n = 0;
+    }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+// Device copy of the discretisation.
+struct DevGeom {
+    int N = 0, S = 0, g = 0, s = 0, n_panels = 0;
+    DevBuf<double> seg;       // [S][4]
+    DevBuf<double> segw;      // [S]
+    DevBuf<double> node_xy;   // [N][2]
+    DevBuf<int> node_seg;     // [N]
+    DevBuf<int> node_seg2;    // [N]
+    DevBuf<double> lambda;    // [s][g]
+    DevBuf<double> u_plus;    // [N][3]
+    DevBuf<double> u_minus;   // [N][3]
+};
+
+// Pixel grid of one viewport on the device.
+struct VpDev {
+    double x0, y0, dx, dy;
+    int width, height;
+    long long offset;         // first output pixel of this viewport
+};
+
+// ------------------------------------------------------- kernel entry --
+// K1: values at segments from values at nodes (sigma_bar = Lambda sigma).
+cudaError_t launch_interp(const DevGeom &G, const double *node_vals, double *seg_vals,
+                          cudaStream_t st);
+
+// K9 (plain dense form): A_G, A_F [N][N] row-major (Eq. 19 / Eq. 27).
+cudaError_t launch_dense_assemble(const DevGeom &G, double *AG, double *AF, cudaStream_t st);
+// y[N][3] = A[N][N] x[N][3]
+cudaError_t launch_dense_gemv(const double *A, int N, const double *x, double *y,
+                              cudaStream_t st);
+// Direct-sum layer potential at pixel centres of one viewport, FP64.
+cudaError_t launch_dense_eval_grid(const DevGeom &G, const double *sbar, const double *mbar,
+                                   const VpDev &vp, double *u, cudaStream_t st);
+// Direct-sum layer potential at explicit points, FP64.
+cudaError_t launch_dense_eval_points(const DevGeom &G, const double *sbar, const double *mbar,
+                                     const double *xy, int n, double *u, cudaStream_t st);
+
+// Output conversion: u[n][3] FP64 -> rgb (f32 or f64) and rgb8 (K12).
+cudaError_t launch_write_outputs(const double *u, long long n, void *rgb, int rgb_dtype,
+                                 unsigned char *rgb8, cudaStream_t st);
+cudaError_t launch_write_outputs_f32(const float *u, long long n, void *rgb, int rgb_dtype,
+                                     unsigned char *rgb8, cudaStream_t st);
+
+// b = (u+ + u-)/2 - Fmu ; mu = u+ - u-
+cudaError_t launch_mu(const DevGeom &G, double *mu, cudaStream_t st);
+cudaError_t launch_rhs(const DevGeom &G, const double *Fmu, double *b, cudaStream_t st);
+
+// --------------------------------------------------------------- GMRES --
+// Matrix-free operator y = A x on [N][3] FP64 vectors (all 3 channels).
+struct Operator {
+    virtual ~Operator() = default;
+    virtual cudaError_t apply(const double *x, double *y, cudaStream_t st) = 0;
+};
+
+struct GmresResult {
+    int iters[3] = {0, 0, 0};
+    double rel_resid[3] = {0, 0, 0};
+    int converged = 0;
+    int n_matvec = 0;
+};
+
+struct GmresWork;   // device workspace (gmres.cu)
+GmresWork *gmres_work_create();
+void gmres_work_destroy(GmresWork *w);
+
+// Restarted GMRES for the 3 channels at once (Sec. 5.5), FP64 Arnoldi by
+// classical Gram-Schmidt with one re-orthogonalisation pass, Givens
+// rotations and the least-squares update on the device.  x holds x0 on
+// entry and the solution on exit.
+cudaError_t gmres_solve(GmresWork *w, Operator &A, int N, const double *b, double *x,
+                        double tol, int restart, int max_iter, cudaStream_t st,
+                        GmresResult &res, std::string &err);
+
+}  // namespace dc

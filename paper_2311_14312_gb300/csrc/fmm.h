@@ -1,0 +1,45 @@
+// FMM forms of the layer-potential operator (App. E, Alg. 8) on a
+// non-uniform quadtree with clipped segments (Sec. 5.2).
+#pragma once
+
+#include <memory>
+#include <string>
+
+#include "dc_internal.h"
+
+namespace dc {
+
+class Fmm {
+public:
+    Fmm();
+    ~Fmm();
+    // quadtree(S) and pre_FMM(S, q, Q) (Alg. 3 lines 1-2).
+    dc_status build(const dc_options &opt, const Geometry &G, const DevGeom &D,
+                    cudaStream_t st, std::string &err);
+    // y = G_H x at the nodes (single layer of the interpolated density).
+    cudaError_t apply_single_layer(const double *x, double *y, cudaStream_t st);
+    // y = F_H x at the nodes (double layer), for the right-hand side.
+    cudaError_t apply_double_layer(const double *x, double *y, cudaStream_t st);
+    // GMRES with this operator (Alg. 3 line 5); x holds x0 on entry.
+    cudaError_t solve(GmresWork *w, const double *b, double *x, const dc_options &opt,
+                      cudaStream_t st, GmresResult &res, std::string &err);
+    // Forms the expansions of segment densities sbar and mbar (Alg. 8 up and
+    // down passes); render_grid / eval_points then evaluate them.
+    cudaError_t prepare_eval(const double *sbar, const double *mbar, cudaStream_t st);
+    // Single + double layer of segment densities at a viewport's pixels.
+    dc_status render_grid(const VpDev &vp, const double *sbar, const double *mbar, void *rgb,
+                          int rgb_dtype, unsigned char *rgb8, cudaStream_t st, std::string &err);
+    dc_status eval_points(const double *xy, int n, const double *sbar, const double *mbar,
+                          void *out, int out_dtype, cudaStream_t st, std::string &err);
+    void fill_sizes(dc_sizes *out) const;
+    long long p2p_pairs_nodes() const;
+    long long m2l_pairs() const;
+    long long last_render_p2p_pairs() const;
+
+    struct Impl;
+
+private:
+    std::unique_ptr<Impl> impl_;
+};
+
+}  // namespace dc

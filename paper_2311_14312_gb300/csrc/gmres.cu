@@ -1,0 +1,367 @@
+// K8: restarted GMRES on the device for the three colour channels at once
+// (Sec. 5.5: x = GMRES(f, x0, y, eps) with the FMM or dense operator as f).
+//
+// Each channel has its own Krylov space; vectors are [N][3] FP64 with the
+// channel fastest.  Arnoldi uses classical Gram-Schmidt with one
+// re-orthogonalisation pass (two dot-product sweeps instead of k sequential
+// ones, same stability as modified Gram-Schmidt in practice); Givens
+// rotations, the residual estimate and the triangular solve run on the
+// device.  Reductions are two-stage with a fixed order, so results are
+// bit-reproducible.  The host reads back three residual estimates per
+// iteration to decide convergence.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "dc_internal.h"
+
+namespace dc {
+
+namespace {
+
+constexpr int kChunk = 4096;     // rows per partial dot-product block
+constexpr int kDotThreads = 256;
+
+// partial[(j * nchunk + chunk) * 3 + c] = sum over rows of the chunk of
+// V_j[i][c] * w[i][c]
+__global__ void dots_partial_kernel(const double *__restrict__ V, size_t vstride,
+                                    const double *__restrict__ w, int N, int nchunk,
+                                    double *__restrict__ partial) {
+    int chunk = blockIdx.x, j = blockIdx.y;
+    const double *v = V + (size_t)j * vstride;
+    int lo = chunk * kChunk, hi = min(N, lo + kChunk);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int i = lo + threadIdx.x; i < hi; i += kDotThreads) {
+        a0 += v[3 * (size_t)i + 0] * w[3 * (size_t)i + 0];
+        a1 += v[3 * (size_t)i + 1] * w[3 * (size_t)i + 1];
+        a2 += v[3 * (size_t)i + 2] * w[3 * (size_t)i + 2];
+    }
+    __shared__ double red[3][kDotThreads];
+    red[0][threadIdx.x] = a0;
+    red[1][threadIdx.x] = a1;
+    red[2][threadIdx.x] = a2;
+    __syncthreads();
+    for (int s = kDotThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3)
+        partial[((size_t)j * nchunk + chunk) * 3 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// h[j][c] (= or +=) sum_chunk partial
+__global__ void dots_finalize_kernel(const double *__restrict__ partial, int nchunk, int nj,
+                                     double *__restrict__ h, int accumulate) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nj * 3) return;
+    int j = t / 3, c = t - 3 * j;
+    double s = 0.0;
+    for (int ch = 0; ch < nchunk; ++ch) s += partial[((size_t)j * nchunk + ch) * 3 + c];
+    h[t] = accumulate ? h[t] + s : s;
+}
+
+// w[i][c] -= sum_{j < nj} h[j][c] V_j[i][c]
+__global__ void orth_update_kernel(const double *__restrict__ V, size_t vstride,
+                                   const double *__restrict__ h, int nj, double *__restrict__ w,
+                                   int N) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double a0 = w[3 * (size_t)i + 0], a1 = w[3 * (size_t)i + 1], a2 = w[3 * (size_t)i + 2];
+    for (int j = 0; j < nj; ++j) {
+        const double *v = V + (size_t)j * vstride + 3 * (size_t)i;
+        a0 -= h[3 * j + 0] * v[0];
+        a1 -= h[3 * j + 1] * v[1];
+        a2 -= h[3 * j + 2] * v[2];
+    }
+    w[3 * (size_t)i + 0] = a0;
+    w[3 * (size_t)i + 1] = a1;
+    w[3 * (size_t)i + 2] = a2;
+}
+
+// out[i][c] = in[i][c] * (nrm[c] > 0 ? 1 / nrm[c] : 0)
+__global__ void scale_kernel(const double *__restrict__ in, const double *__restrict__ nrm,
+                             double *__restrict__ out, int N) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * N) return;
+    int c = t % 3;
+    double n = nrm[c];
+    out[t] = (n > 0.0) ? in[t] / n : 0.0;
+}
+
+// r = b - Ax
+__global__ void residual_kernel(const double *__restrict__ b, const double *__restrict__ Ax,
+                                double *__restrict__ r, int n3) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n3) r[t] = b[t] - Ax[t];
+}
+
+// sqrt of a finalized sum of squares
+__global__ void sqrt3_kernel(double *v) {
+    int c = threadIdx.x;
+    if (c < 3) v[c] = sqrt(fmax(v[c], 0.0));
+}
+
+struct GivensState {
+    // per channel
+    double *R;      // [3][m][m] column-major upper triangle: R[c][k*m + j]
+    double *cs;     // [3][m]
+    double *sn;     // [3][m]
+    double *e;      // [3][m+1]
+    double *y;      // [3][m]
+    int *active;    // [3]
+    int *kc;        // [3] columns used in this cycle
+    double *resid;  // [3] current |e[k+1]|
+};
+
+// Start of a cycle: e = (beta, 0, ...); active = beta > thr.
+__global__ void cycle_start_kernel(GivensState g, const double *__restrict__ beta,
+                                   const double *__restrict__ thr, int m) {
+    int c = threadIdx.x;
+    if (c >= 3) return;
+    for (int k = 0; k <= m; ++k) g.e[c * (m + 1) + k] = 0.0;
+    g.e[c * (m + 1)] = beta[c];
+    g.active[c] = beta[c] > thr[c] ? 1 : 0;
+    g.kc[c] = 0;
+    g.resid[c] = beta[c];
+}
+
+// Column k of the Hessenberg matrix: hcol[0..k] and hnext; rotate, record.
+__global__ void givens_kernel(GivensState g, const double *__restrict__ hcol,
+                              const double *__restrict__ hnext, const double *__restrict__ thr,
+                              int k, int m) {
+    int c = threadIdx.x;
+    if (c >= 3 || !g.active[c]) return;
+    double *col = g.R + (size_t)c * m * m + (size_t)k * m;
+    for (int j = 0; j <= k; ++j) col[j] = hcol[3 * j + c];
+    double *cs = g.cs + c * m, *sn = g.sn + c * m, *e = g.e + c * (m + 1);
+    for (int j = 0; j < k; ++j) {
+        double a = col[j], b = col[j + 1];
+        col[j] = cs[j] * a + sn[j] * b;
+        col[j + 1] = -sn[j] * a + cs[j] * b;
+    }
+    double hn = hnext[c];
+    double den = hypot(col[k], hn);
+    double cc = (den > 0.0) ? col[k] / den : 1.0;
+    double ss = (den > 0.0) ? hn / den : 0.0;
+    cs[k] = cc;
+    sn[k] = ss;
+    col[k] = den;
+    e[k + 1] = -ss * e[k];
+    e[k] = cc * e[k];
+    double res = fabs(e[k + 1]);
+    g.resid[c] = res;
+    g.kc[c] = k + 1;
+    if (res <= thr[c] || !(hn > 0.0) || !(den > 0.0)) g.active[c] = 0;
+}
+
+// Back substitution R y = e for each channel (kc[c] columns).
+__global__ void backsolve_kernel(GivensState g, int m) {
+    int c = threadIdx.x;
+    if (c >= 3) return;
+    int n = g.kc[c];
+    const double *R = g.R + (size_t)c * m * m;
+    double *y = g.y + c * m;
+    const double *e = g.e + c * (m + 1);
+    for (int i = n - 1; i >= 0; --i) {
+        double s = e[i];
+        for (int j = i + 1; j < n; ++j) s -= R[(size_t)j * m + i] * y[j];
+        double d = R[(size_t)i * m + i];
+        y[i] = (d != 0.0) ? s / d : 0.0;
+    }
+    for (int i = n; i < m; ++i) y[i] = 0.0;
+}
+
+// x[i][c] += sum_{j < kc[c]} y[c][j] V_j[i][c]
+__global__ void solution_update_kernel(GivensState g, const double *__restrict__ V, size_t vstride,
+                                       double *__restrict__ x, int N, int m) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int c = 0; c < 3; ++c) {
+        int n = g.kc[c];
+        const double *y = g.y + c * m;
+        double a = x[3 * (size_t)i + c];
+        for (int j = 0; j < n; ++j) a += y[j] * V[(size_t)j * vstride + 3 * (size_t)i + c];
+        x[3 * (size_t)i + c] = a;
+    }
+}
+
+}  // namespace
+
+struct GmresWork {
+    int N = 0, m = 0, nchunk = 0;
+    DevBuf<double> V, w, r, Ax, partial, hcol, hpass, hnext, small;
+    DevBuf<double> R, cs, sn, e, y;
+    DevBuf<int> flags;
+    double *host = nullptr;   // pinned: resid[3], active-as-double[3], norms[3]
+    ~GmresWork() {
+        if (host) cudaFreeHost(host);
+    }
+    cudaError_t ensure(int N_, int m_) {
+        if (N_ == N && m_ == m) return cudaSuccess;
+        N = N_;
+        m = m_;
+        nchunk = (N + kChunk - 1) / kChunk;
+        cudaError_t e_;
+#define DC_TRY(x)               \
+    if ((e_ = (x)) != cudaSuccess) \
+        return e_;
+        DC_TRY(V.alloc((size_t)(m + 1) * N * 3));
+        DC_TRY(w.alloc((size_t)N * 3));
+        DC_TRY(r.alloc((size_t)N * 3));
+        DC_TRY(Ax.alloc((size_t)N * 3));
+        DC_TRY(partial.alloc((size_t)(m + 1) * nchunk * 3));
+        DC_TRY(hcol.alloc((size_t)(m + 1) * 3));
+        DC_TRY(hpass.alloc((size_t)(m + 1) * 3));
+        DC_TRY(hnext.alloc(3));
+        DC_TRY(small.alloc(16));
+        DC_TRY(R.alloc((size_t)3 * m * m));
+        DC_TRY(cs.alloc((size_t)3 * m));
+        DC_TRY(sn.alloc((size_t)3 * m));
+        DC_TRY(e.alloc((size_t)3 * (m + 1)));
+        DC_TRY(y.alloc((size_t)3 * m));
+        DC_TRY(flags.alloc(8));
+        if (!host) DC_TRY(cudaMallocHost(reinterpret_cast<void **>(&host), 16 * sizeof(double)));
+#undef DC_TRY
+        return cudaSuccess;
+    }
+    GivensState gs() {
+        GivensState g;
+        g.R = R.ptr;
+        g.cs = cs.ptr;
+        g.sn = sn.ptr;
+        g.e = e.ptr;
+        g.y = y.ptr;
+        g.active = flags.ptr;
+        g.kc = flags.ptr + 3;
+        g.resid = small.ptr + 8;
+        return g;
+    }
+};
+
+GmresWork *gmres_work_create() { return new GmresWork(); }
+void gmres_work_destroy(GmresWork *w) { delete w; }
+
+namespace {
+
+// nrm[c] = || v[:, c] ||_2 (device), through the deterministic dot kernels.
+cudaError_t norms(GmresWork &W, const double *v, double *nrm, cudaStream_t st) {
+    dim3 grid(W.nchunk, 1);
+    dots_partial_kernel<<<grid, kDotThreads, 0, st>>>(v, 0, v, W.N, W.nchunk, W.partial.ptr);
+    dots_finalize_kernel<<<1, 32, 0, st>>>(W.partial.ptr, W.nchunk, 1, nrm, 0);
+    sqrt3_kernel<<<1, 32, 0, st>>>(nrm);
+    return cudaGetLastError();
+}
+
+__global__ void add_into_kernel(double *__restrict__ dst, const double *__restrict__ src, int n,
+                                int assign) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) dst[t] = assign ? src[t] : dst[t] + src[t];
+}
+
+}  // namespace
+
+cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, double *x, double tol,
+                        int restart, int max_iter, cudaStream_t st, GmresResult &res,
+                        std::string &err) {
+    GmresWork &W = *Wp;
+    res = GmresResult();
+    int m = restart < 1 ? 1 : restart;
+    if (max_iter < m) m = max_iter < 1 ? 1 : max_iter;
+    cudaError_t ce = W.ensure(N, m);
+    if (ce != cudaSuccess) {
+        err = std::string("gmres workspace: ") + cudaGetErrorString(ce);
+        return ce;
+    }
+    const size_t vs = (size_t)N * 3;
+    const int th = 256;
+    GivensState gs = W.gs();
+    double *bnorm = W.small.ptr;        // [3]
+    double *thr = W.small.ptr + 3;      // [3]
+    double *beta = W.small.ptr + 12;    // [3] (slots 8..10 hold resid)
+    // ||b|| and thresholds tol * ||b||
+    if ((ce = norms(W, b, bnorm, st)) != cudaSuccess) return ce;
+    double hb[3];
+    if ((ce = cudaMemcpyAsync(hb, bnorm, 3 * sizeof(double), cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+        return ce;
+    if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return ce;
+    double hthr[3];
+    for (int c = 0; c < 3; ++c) hthr[c] = tol * hb[c];
+    if ((ce = cudaMemcpyAsync(thr, hthr, 3 * sizeof(double), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return ce;
+    int total = 0;
+    bool done_all = false;
+    while (true) {
+        // r = b - A x ; beta = ||r||
+        if ((ce = A.apply(x, W.Ax.ptr, st)) != cudaSuccess) return ce;
+        res.n_matvec++;
+        residual_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(b, W.Ax.ptr, W.r.ptr, 3 * N);
+        if ((ce = norms(W, W.r.ptr, beta, st)) != cudaSuccess) return ce;
+        double hbeta[3];
+        if ((ce = cudaMemcpyAsync(hbeta, beta, 3 * sizeof(double), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess)
+            return ce;
+        if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return ce;
+        bool any = false;
+        for (int c = 0; c < 3; ++c) {
+            res.rel_resid[c] = hb[c] > 0 ? hbeta[c] / hb[c] : 0.0;
+            if (hbeta[c] > hthr[c]) any = true;
+        }
+        if (!any) {
+            done_all = true;
+            break;
+        }
+        if (total >= max_iter) break;
+        cycle_start_kernel<<<1, 32, 0, st>>>(gs, beta, thr, m);
+        scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.r.ptr, beta, W.V.ptr, N);
+        int k = 0;
+        for (; k < m && total < max_iter; ++k) {
+            double *vk = W.V.ptr + (size_t)k * vs;
+            if ((ce = A.apply(vk, W.w.ptr, st)) != cudaSuccess) return ce;
+            res.n_matvec++;
+            // CGS2: two passes of h = V^T w, w -= V h
+            for (int pass = 0; pass < 2; ++pass) {
+                dim3 grid(W.nchunk, k + 1);
+                dots_partial_kernel<<<grid, kDotThreads, 0, st>>>(W.V.ptr, vs, W.w.ptr, N,
+                                                                  W.nchunk, W.partial.ptr);
+                int t3 = (k + 1) * 3;
+                dots_finalize_kernel<<<(t3 + 127) / 128, 128, 0, st>>>(W.partial.ptr, W.nchunk,
+                                                                      k + 1, W.hpass.ptr, 0);
+                orth_update_kernel<<<(N + th - 1) / th, th, 0, st>>>(W.V.ptr, vs, W.hpass.ptr,
+                                                                      k + 1, W.w.ptr, N);
+                add_into_kernel<<<(t3 + 127) / 128, 128, 0, st>>>(W.hcol.ptr, W.hpass.ptr, t3,
+                                                                  pass == 0);
+            }
+            if ((ce = norms(W, W.w.ptr, W.hnext.ptr, st)) != cudaSuccess) return ce;
+            scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.w.ptr, W.hnext.ptr,
+                                                               W.V.ptr + (size_t)(k + 1) * vs, N);
+            givens_kernel<<<1, 32, 0, st>>>(gs, W.hcol.ptr, W.hnext.ptr, thr, k, m);
+            total++;
+            int hact[3];
+            if ((ce = cudaMemcpyAsync(hact, gs.active, 3 * sizeof(int), cudaMemcpyDeviceToHost,
+                                      st)) != cudaSuccess)
+                return ce;
+            if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return ce;
+            if (!hact[0] && !hact[1] && !hact[2]) {
+                ++k;
+                break;
+            }
+        }
+        backsolve_kernel<<<1, 32, 0, st>>>(gs, m);
+        solution_update_kernel<<<(N + th - 1) / th, th, 0, st>>>(gs, W.V.ptr, vs, x, N, m);
+        int hkc[3];
+        if ((ce = cudaMemcpyAsync(hkc, gs.kc, 3 * sizeof(int), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess)
+            return ce;
+        if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return ce;
+        for (int c = 0; c < 3; ++c) res.iters[c] += hkc[c];
+    }
+    res.converged = done_all ? 1 : 0;
+    return cudaGetLastError();
+}
+
+}  // namespace dc

@@ -1,0 +1,44 @@
+// Closed-form integrals of G and F over one straight segment (App. D), as
+// used by every near-field and dense kernel.
+//
+// For a target q and a segment p1 -> p2 of chord length c, let a = p1 - q,
+// b = p2 - q.  The signed angle the segment subtends at q is
+//     phi = atan2(a x b, a . b),
+// and with n the right-hand unit normal of the segment direction,
+//     int F dS = -phi / 2pi                       (Eq. 4 integrated)
+//     int log|p - q| dS = ( s2 log|b|^2 - s1 log|a|^2 ) / 2 - c + (a x b / c) phi
+// where s1 = a.d/c, s2 = b.d/c are the endpoints' coordinates along the
+// chord (d = p2 - p1), and (a x b)/c is the signed offset of q from the
+// chord's line.  int G dS = -(1/2pi) int log|p - q| dS.  Both are scaled
+// by the segment's arc-length weight w (App. A).  When q lies on the
+// segment (its own collocation segment), phi is replaced by 0: the
+// principal value of Eq. 53, and the log form then equals Eq. 52.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace dc {
+
+constexpr double kInv2Pi = 0.15915494309189533577;
+
+__device__ __forceinline__ void seg_gf_f64(double qx, double qy, double x1, double y1,
+                                           double x2, double y2, double w, bool own,
+                                           double &G, double &F) {
+    double ax = x1 - qx, ay = y1 - qy;
+    double bx = x2 - qx, by = y2 - qy;
+    double dx = x2 - x1, dy = y2 - y1;
+    double ic = rsqrt(dx * dx + dy * dy);
+    double c = (dx * dx + dy * dy) * ic;
+    double cr = ax * by - ay * bx;
+    double dt = ax * bx + ay * by;
+    double phi = own ? 0.0 : atan2(cr, dt);
+    double ra2 = ax * ax + ay * ay, rb2 = bx * bx + by * by;
+    double s1 = (ax * dx + ay * dy) * ic, s2 = (bx * dx + by * dy) * ic;
+    double la = (ra2 > 0.0) ? s1 * log(ra2) : 0.0;
+    double lb = (rb2 > 0.0) ? s2 * log(rb2) : 0.0;
+    double ilog = 0.5 * (lb - la) - c + cr * ic * phi;
+    G = -w * kInv2Pi * ilog;
+    F = -w * kInv2Pi * phi;
+}
+
+}  // namespace dc

@@ -18,3 +18,19 @@ def oracle_mod():
     from oracle import oracle as O
     O.build()
     return O
+
+
+@pytest.fixture(scope="session")
+def dcmod():
+    """The native package, built in-tree first if needed (nvcc required)."""
+    from paper_2311_14312_gb300 import build as B
+    B.build()
+    import paper_2311_14312_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="session")
+def cuda_ok():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return True
