@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the hybrid BIE diffusion-curve hot path on GB300.
+
+One step = solve for the density (GMRES, Alg. 3) + render one viewport
+(Alg. 4) of a seeded synthetic drawing: 200 cubic Bezier curves (120 open,
+80 closed) with adaptive panels (27,888 Gauss-Legendre nodes x 3 colour
+channels, 139,440 segments) rendered at 2048 x 2048 over the unit canvas,
+in the chosen form (FP32 FMM, FP64 GMRES with iterative refinement to a
+relative residual of 1e-10).  The metric is render throughput in
+Mpixels/s of the whole step (solve included), with the solve time and the
+render-only rate reported beside it, and the plain FP64 FMM form timed on
+the same inputs.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU runs are independent replicas (the path does not shard here).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixels/s render + GMRES solve ms at <=1e-5 err vs FP64 (chosen vs plain form)"
+UNIT = "Mpixels/s"
+WORKLOAD = "mixed200"
+WIDTH = HEIGHT = 2048
+VIEWPORT = (0.0, 0.0, 1.0, 1.0)
+FORM_OPTS = dict(p=24, leaf_size=64, gmres_tol=1e-10, gmres_restart=200, gmres_max_iter=3000)
+# FP32 vector-unit peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops
+# per FMA x 2.07 GHz maximum SM clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 FMM comparison")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ helpers --
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_for_eval_kernel():
+    """DRAM bytes per launch of the eval kernel from a committed ncu
+    summary, valid only while the kernel source is unchanged."""
+    src = os.path.join(ROOT, "paper_2311_14312_gb300", "csrc", "fmm32.cu")
+    path = os.path.join(ROOT, "profiles", "eval32_traffic.json")
+    try:
+        ref = json.load(open(path))
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        if ref.get("source_sha1") == sha and ref.get("workload") == WORKLOAD:
+            return ref.get("bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------- oracle leg --
+def oracle_sample(seconds: float, seed: int = 1):
+    """Oracle direct-sum render of sampled pixels of the same viewport with
+    a seeded density: (pixels, seconds, threads).  The oracle cannot solve
+    27,888 unknowns in bounded time (dense LU), so only its render leg is
+    timed; the density values do not change its cost."""
+    import numpy as np
+
+    from dc_synth import drawing_by_name, pixel_sample, random_node_values
+    from oracle import oracle as O
+
+    d = drawing_by_name(WORKLOAD)
+    disc = O.discretise(d)
+    sig = random_node_values(disc.n_nodes, seed=seed, scale=0.1)
+    mu = random_node_values(disc.n_nodes, seed=seed + 1, scale=0.1)
+    probe = pixel_sample(WIDTH, HEIGHT, 64, seed=seed)
+    t0 = time.perf_counter()
+    O.layer_potential(disc, O.pixel_centres(VIEWPORT, WIDTH, HEIGHT, probe), sig, mu)
+    rate = len(probe) / max(time.perf_counter() - t0, 1e-6)
+    count = int(max(64, min(WIDTH * HEIGHT, rate * seconds)))
+    idx = pixel_sample(WIDTH, HEIGHT, count, seed=seed + 2)
+    t0 = time.perf_counter()
+    O.layer_potential(disc, O.pixel_centres(VIEWPORT, WIDTH, HEIGHT, idx), sig, mu)
+    dt = time.perf_counter() - t0
+    return count, dt, O.num_threads(), np
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    vals = []
+    per = max(2.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(args.warmup):
+        oracle_sample(0.5)
+    cores = 1
+    total_px, total_t = 0, 0.0
+    for k in range(args.steps):
+        n, dt, cores, _ = oracle_sample(per, seed=100 + k)
+        vals.append(n / dt / 1e6)
+        total_px += n
+        total_t += dt
+    v = total_px / total_t / 1e6
+    sample = (f"oracle FP64 direct-sum render of {total_px} sampled pixels of the "
+              f"{WIDTH}x{HEIGHT} viewport in {args.steps} steps (render leg only: the oracle "
+              f"cannot solve 27,888 unknowns in bounded time)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "width": WIDTH, "height": HEIGHT},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- GPU leg --
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2311_14312_gb300 as P
+    from dc_synth import drawing_by_name
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    d = drawing_by_name(WORKLOAD)
+    ctx = P.Context(form="fmm32", g=d.g, s_per_panel=d.s_per_panel, **FORM_OPTS)
+    ctx.build_drawing(d)
+    npx = WIDTH * HEIGHT
+    vp = [(*VIEWPORT, WIDTH, HEIGHT)]
+    rgb = torch.empty((npx, 3), dtype=torch.float32, device="cuda")
+    rgb8 = torch.empty((npx, 3), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.solve_density()
+        ctx.render_viewport(vp, rgb, rgb8)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # ---- device-resident timed region (L2 flushed before every step)
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = P.kernel_launches()
+    step_ms, solve_ms, render_ms = [], [], []
+    barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.solve_density()
+        e1.record(stream)
+        ctx.render_viewport(vp, rgb, rgb8)
+        e2.record(stream)
+        e2.synchronize()
+        step_ms.append(e0.elapsed_time(e2))
+        solve_ms.append(e0.elapsed_time(e1))
+        render_ms.append(e1.elapsed_time(e2))
+    torch.cuda.synchronize()
+    barrier()
+    launches = P.kernel_launches() - launches0
+    clk = clocks.stop()
+    t_step = statistics.mean(step_ms)
+    if ws > 1:
+        t = torch.tensor([t_step], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(t.item())
+    value = ws * npx / (t_step * 1e-3) / 1e6
+
+    # ---- roofline of the dominant kernel (pixel evaluation), live events
+    rs = ctx.render_viewport(vp, rgb, rgb8, stats=True)
+    achieved = rs.eval_flops / (rs.ms_eval * 1e-3) / 1e12 if rs.ms_eval > 0 else None
+    st = ctx.solve_density()
+    chosen = rgb.float().cpu().numpy()
+
+    # ---- end to end through the C ABI with host buffers
+    from dc_synth import drawing_by_name as _dbn  # noqa: F401
+    ctrl = np.ascontiguousarray(d.ctrl)
+    pptr = np.ascontiguousarray(d.panel_ptr, dtype=np.int32)
+    pst = np.ascontiguousarray(d.panel_start)
+    col = np.ascontiguousarray(d.colours)
+    h_rgb = torch.empty((npx, 3), dtype=torch.float32, pin_memory=True).numpy()
+    h_rgb8 = torch.empty((npx, 3), dtype=torch.uint8, pin_memory=True).numpy()
+    bi = ctrl.nbytes + pptr.nbytes + pst.nbytes + col.nbytes
+    bo = h_rgb.nbytes + h_rgb8.nbytes
+    e2e_ms = []
+    for k in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.build_tree(ctrl, pptr, pst, col)
+        ctx.solve_density()
+        ctx.render_viewport(vp, h_rgb, h_rgb8)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e = npx / (statistics.mean(e2e_ms) * 1e-3) / 1e6
+
+    # ---- plain FP64 FMM form on the same inputs (accuracy reference too)
+    plain = None
+    if not args.no_plain and rank == 0:
+        pctx = P.Context(form="fmm64", g=d.g, s_per_panel=d.s_per_panel, **FORM_OPTS)
+        pctx.build_drawing(d)
+        prgb = torch.empty((npx, 3), dtype=torch.float64, device="cuda")
+        pctx.solve_density()
+        pctx.render_viewport(vp, prgb)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        pst_ = pctx.solve_density()
+        e1.record(stream)
+        pctx.render_viewport(vp, prgb)
+        e2.record(stream)
+        e2.synchronize()
+        ref = prgb.cpu().numpy()
+        err = float(np.abs(chosen - ref).max())
+        q_c = np.floor(255 * np.clip(chosen, 0, 1) + 0.5)
+        q_r = np.floor(255 * np.clip(ref, 0, 1) + 0.5)
+        v8 = 255.0 * np.clip(ref, 0, 1)
+        band = np.abs(v8 - np.floor(v8) - 0.5) <= 255.0 * 1e-5
+        mism = int(((q_c != q_r) & ~band).sum())
+        plain = {"form": "fmm64", "solve_ms": e0.elapsed_time(e1), "render_ms": e1.elapsed_time(e2),
+                 "mpix_s": npx / (e0.elapsed_time(e2) * 1e-3) / 1e6,
+                 "gmres_iters": list(pst_.iters),
+                 "chosen_max_abs_err_vs_plain": err, "chosen_8bit_mismatch_outside_band": mism,
+                 "band_pixels": int(band.sum())}
+        pctx.close()
+
+    cpu = None
+    if rank == 0 and ws == 1:
+        n, dt, cores, _ = oracle_sample(args.cpu_seconds)
+        cpu = {"value": n / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"oracle FP64 direct-sum render of {n} sampled pixels of the "
+                         f"{WIDTH}x{HEIGHT} viewport ({dt:.1f} s; render leg only, the oracle "
+                         f"cannot solve 27,888 unknowns in bounded time)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD,
+                       "drawing": "200 cubic Bezier curves (120 open, 80 closed), seeded; "
+                                  f"{d.n_nodes} GL nodes x 3 channels, {d.n_segments} segments",
+                       "width": WIDTH, "height": HEIGHT, "form": "fmm32", **FORM_OPTS,
+                       "parallelism": f"replicas x{ws}",
+                       "l2": "flushed before every timed step (256 MiB write)"},
+            "solve_ms": statistics.mean(solve_ms), "render_ms": statistics.mean(render_ms),
+            "render_mpix_s": npx / (statistics.mean(render_ms) * 1e-3) / 1e6,
+            "gmres_iters": list(st.iters), "gmres_rel_resid": max(st.rel_resid),
+            "plain_form": plain,
+            "roofline": {"bound": "alu", "kernel": "eval32_kernel<0> (L2P + M2P + P2P per pixel)",
+                         "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": (achieved / FP32_PEAK_TFLOPS) if achieved else None,
+                         "traffic": traffic_for_eval_kernel(),
+                         "eval_ms": rs.ms_eval, "eval_flops": rs.eval_flops,
+                         "p2p_pairs": rs.p2p_pairs, "m2p_pairs": rs.m2p_pairs},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+                    "includes": "build_tree from host arrays + solve + render to pinned host"},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

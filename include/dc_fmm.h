@@ -118,10 +118,15 @@ typedef struct {
 } dc_viewport;
 
 typedef struct {
-    double ms;             /* device time of the render                      */
+    double ms;             /* device time of the whole call                  */
+    double ms_eval;        /* device time of the pixel-evaluation kernels    */
     long long pixels;
-    long long p2p_pairs;
-    long long m2l_pairs;
+    long long p2p_pairs;   /* (pixel, clipped piece) pairs of list 1         */
+    long long m2p_pairs;   /* (pixel, cell) pairs of list 3                  */
+    long long m2l_pairs;   /* cell pairs of list 2 in the passes             */
+    double eval_flops;     /* algorithmic flops of the evaluation kernels:
+                              45 per near-field pair, 24 (p + 1) per L2P and
+                              per list-3 M2P (3 colour channels)              */
 } dc_render_stats;
 
 /* Fills *opt with defaults: DC_FORM_FMM32, g 16, s 80, p 24, leaf 64,
@@ -215,6 +220,10 @@ dc_status dc_aux_tree_check(int n_seg, const double *seg_xy, const double *domai
                             int leaf_size, int max_depth, double *out);
 
 int dc_abi_version(void);
+
+/* Auxiliary: number of CUDA kernels this library has launched in this
+ * process (all contexts), for launch accounting by benchmarks. */
+long long dc_aux_kernel_launches(void);
 
 #ifdef __cplusplus
 }

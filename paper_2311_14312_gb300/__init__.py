@@ -63,14 +63,16 @@ class dc_viewport(ctypes.Structure):
 
 
 class dc_render_stats(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double), ("pixels", ctypes.c_longlong),
-                ("p2p_pairs", ctypes.c_longlong), ("m2l_pairs", ctypes.c_longlong)]
+    _fields_ = [("ms", ctypes.c_double), ("ms_eval", ctypes.c_double),
+                ("pixels", ctypes.c_longlong), ("p2p_pairs", ctypes.c_longlong),
+                ("m2p_pairs", ctypes.c_longlong), ("m2l_pairs", ctypes.c_longlong),
+                ("eval_flops", ctypes.c_double)]
 
 
 EXPORTS = ["dc_default_options", "dc_create", "dc_destroy", "dc_build_tree", "dc_solve_density",
            "dc_render_viewport", "dc_eval_points", "dc_get_density", "dc_set_density",
            "dc_get_nodes", "dc_get_sizes", "dc_last_error", "dc_status_string",
-           "dc_abi_version", "dc_aux_tree_check"]
+           "dc_abi_version", "dc_aux_tree_check", "dc_aux_kernel_launches"]
 
 
 def _load():
@@ -98,8 +100,11 @@ def _load():
     lib.dc_status_string.restype = ctypes.c_char_p
     lib.dc_abi_version.restype = I
     lib.dc_aux_tree_check.argtypes = [I, P, P, I, I, P]
+    lib.dc_aux_kernel_launches.argtypes = []
+    lib.dc_aux_kernel_launches.restype = ctypes.c_longlong
     for name in EXPORTS:
-        if name not in ("dc_destroy", "dc_last_error", "dc_status_string", "dc_abi_version"):
+        if name not in ("dc_destroy", "dc_last_error", "dc_status_string", "dc_abi_version",
+                        "dc_aux_kernel_launches"):
             getattr(lib, name).restype = I
     _ = D
     return lib
@@ -269,3 +274,8 @@ def aux_tree_check(seg_xy, domain=(0.0, 0.0, 1.0, 1.0), leaf_size=64, max_depth=
         raise DcError(st, "dc_aux_tree_check failed")
     keys = ["cells", "leaves", "depth", "pieces", "bad_pairs", "clip_rel_err"]
     return dict(zip(keys, out.tolist()))
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libdc_fmm in this process so far."""
+    return int(_get_lib().dc_aux_kernel_launches())

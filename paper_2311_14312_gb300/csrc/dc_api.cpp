@@ -3,6 +3,7 @@
 // The entry points follow the paper's problem statement: build the
 // discretisation and quadtree (Alg. 3 lines 1-2), solve for the density
 // (Alg. 3 lines 3-5), render viewports (Alg. 4 line 3).
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -16,6 +17,12 @@
 #include "tree.h"
 
 using dc::DevBuf;
+
+namespace dc {
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long kernel_launches() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace dc
 
 struct dc_ctx {
     dc_options opt{};
@@ -135,6 +142,8 @@ dc_status ensure_segment_density(dc_ctx *ctx) {
 extern "C" {
 
 int dc_abi_version(void) { return DC_ABI_VERSION; }
+
+long long dc_aux_kernel_launches(void) { return dc::kernel_launches(); }
 
 dc_status dc_aux_tree_check(int n_seg, const double *seg_xy, const double *domain, int leaf_size,
                             int max_depth, double *out) {
@@ -499,7 +508,11 @@ dc_status dc_render_viewport(dc_ctx *ctx, int n_vp, const dc_viewport *vps, void
             drgb8 = ctx->stage8.ptr;
         }
     }
-    if (ctx->fmm) DC_CK(ctx, ctx->fmm->prepare_eval(ctx->sbar.ptr, ctx->mbar.ptr, s), "fmm passes");
+    if (ctx->fmm) {
+        ctx->fmm->set_eval_timing(stats != nullptr);
+        DC_CK(ctx, ctx->fmm->prepare_eval(ctx->sbar.ptr, ctx->mbar.ptr, s), "fmm passes");
+    }
+    double dense_eval_ms = 0.0;
     long long off = 0;
     for (int v = 0; v < n_vp; ++v) {
         const dc_viewport &vp = vps[v];
@@ -517,10 +530,21 @@ dc_status dc_render_viewport(dc_ctx *ctx, int n_vp, const dc_viewport *vps, void
         unsigned char *orgb8 = drgb8 ? drgb8 + size_t(3) * off : nullptr;
         if (ctx->opt.form == DC_FORM_DENSE64) {
             DC_CK(ctx, ctx->u64.ensure(size_t(3) * np), "alloc");
+            if (stats) DC_CK(ctx, cudaEventRecord(e1, s), "event");
             DC_CK(ctx,
                   dc::launch_dense_eval_grid(ctx->dg, ctx->sbar.ptr, ctx->mbar.ptr, d,
                                              ctx->u64.ptr, s),
                   "dense render");
+            if (stats) {
+                cudaEvent_t e2;
+                DC_CK(ctx, cudaEventCreate(&e2), "event");
+                DC_CK(ctx, cudaEventRecord(e2, s), "event");
+                DC_CK(ctx, cudaEventSynchronize(e2), "event");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e1, e2);
+                cudaEventDestroy(e2);
+                dense_eval_ms += ms;
+            }
             DC_CK(ctx, dc::launch_write_outputs(ctx->u64.ptr, np, orgb, rgb_dtype, orgb8, s),
                   "outputs");
         } else {
@@ -552,9 +576,15 @@ dc_status dc_render_viewport(dc_ctx *ctx, int n_vp, const dc_viewport *vps, void
         stats->pixels = total;
         if (ctx->fmm) {
             stats->p2p_pairs = ctx->fmm->last_render_p2p_pairs();
+            stats->m2p_pairs = ctx->fmm->last_render_m2p_pairs();
             stats->m2l_pairs = ctx->fmm->m2l_pairs();
+            stats->eval_flops = ctx->fmm->last_render_eval_flops();
+            stats->ms_eval = ctx->fmm->last_render_eval_ms();
+            ctx->fmm->set_eval_timing(false);
         } else {
             stats->p2p_pairs = total * (long long)ctx->dg.S;
+            stats->eval_flops = 45.0 * double(stats->p2p_pairs);
+            stats->ms_eval = dense_eval_ms;
         }
     }
     DC_CK(ctx, cudaGetLastError(), "render");

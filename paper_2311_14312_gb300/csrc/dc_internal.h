@@ -43,6 +43,10 @@ dc_status discretise(int n_curves, const double *ctrl, const int *panel_ptr,
 // Gauss-Legendre nodes on [-1, 1] (ascending) and weights.
 void gauss_legendre_rule(int n, double *x, double *w);
 
+// Process-wide count of kernels launched by this library (dc_api.cpp).
+void note_launch(int n = 1);
+long long kernel_launches();
+
 // ---------------------------------------------------------- device util --
 template <typename T>
 struct DevBuf {
@@ -108,6 +112,13 @@ cudaError_t launch_dense_eval_grid(const DevGeom &G, const double *sbar, const d
 cudaError_t launch_dense_eval_points(const DevGeom &G, const double *sbar, const double *mbar,
                                      const double *xy, int n, double *u, cudaStream_t st);
 
+// Block-Jacobi preconditioner over panels: inv[j] = (G_H)_{jj}^-1, the
+// inverse of panel j's g x g self-interaction block; info[j] = 1 if singular.
+cudaError_t launch_panel_block_inverse(const DevGeom &G, double *inv, int *info, cudaStream_t st);
+// y = blockdiag(inv) x on [N][3] vectors.
+cudaError_t launch_block_apply(const double *inv, int n_panels, int g, const double *x, double *y,
+                               cudaStream_t st);
+
 // Output conversion: u[n][3] FP64 -> rgb (f32 or f64) and rgb8 (K12).
 cudaError_t launch_write_outputs(const double *u, long long n, void *rgb, int rgb_dtype,
                                  unsigned char *rgb8, cudaStream_t st);
@@ -143,5 +154,13 @@ void gmres_work_destroy(GmresWork *w);
 cudaError_t gmres_solve(GmresWork *w, Operator &A, int N, const double *b, double *x,
                         double tol, int restart, int max_iter, cudaStream_t st,
                         GmresResult &res, std::string &err);
+
+// Small FP64 vector helpers on [N][3] vectors (gmres.cu).
+cudaError_t vec_residual(const double *b, const double *Ax, double *r, int n3, cudaStream_t st);
+cudaError_t vec_axpy(double *x, const double *d, int n3, cudaStream_t st);
+// zero the channels c with keep[c] == 0
+cudaError_t vec_mask3(double *v, int N, const int keep[3], cudaStream_t st);
+// host_out[c] = || v[:, c] ||_2 (synchronises the stream)
+cudaError_t vec_norms3(GmresWork *w, const double *v, int N, double host_out[3], cudaStream_t st);
 
 }  // namespace dc

@@ -191,6 +191,104 @@ dense_eval_points_kernel(const double *__restrict__ seg, const double *__restric
     }
 }
 
+// ------------------------------------------ panel block preconditioner --
+// Diagonal blocks of G_H: B_j[m][n] = sum_{k in panel j} w_k int_{S_k} G(p, q_jm) dS
+// Lambda[k][n] (the self-interaction of panel j, Eq. 19), one thread per row.
+template <int MAXG>
+__global__ void panel_blocks_kernel(const double *__restrict__ seg, const double *__restrict__ segw,
+                                    const double *__restrict__ nxy, const int *__restrict__ nseg,
+                                    const int *__restrict__ nseg2, const double *__restrict__ lam,
+                                    double *__restrict__ blocks, int s, int g) {
+    int j = blockIdx.x, m = threadIdx.x;
+    if (m >= g) return;
+    int i = j * g + m;
+    double qx = nxy[2 * i], qy = nxy[2 * i + 1];
+    int own1 = nseg[i], own2 = nseg2[i];
+    double acc[MAXG];
+#pragma unroll
+    for (int n = 0; n < MAXG; ++n) acc[n] = 0.0;
+    for (int kk = 0; kk < s; ++kk) {
+        int k = j * s + kk;
+        const double *q = seg + 4 * (size_t)k;
+        double G, F;
+        seg_gf_f64(qx, qy, q[0], q[1], q[2], q[3], segw[k], k == own1 || k == own2, G, F);
+        const double *lr = lam + (size_t)kk * g;
+#pragma unroll
+        for (int n = 0; n < MAXG; ++n)
+            if (n < g) acc[n] += G * lr[n];
+    }
+    double *row = blocks + ((size_t)j * g + m) * g;
+#pragma unroll
+    for (int n = 0; n < MAXG; ++n)
+        if (n < g) row[n] = acc[n];
+}
+
+// In-place inverse of each g x g block by Gauss-Jordan elimination with
+// partial pivoting in shared memory; info[j] = 1 if a pivot vanished.
+__global__ void invert_blocks_kernel(double *__restrict__ blocks, int g, int *__restrict__ info) {
+    __shared__ double a[kMaxG][2 * kMaxG + 1];
+    __shared__ int piv;
+    int j = blockIdx.x, t = threadIdx.x;   // t = column of the augmented matrix
+    double *B = blocks + (size_t)j * g * g;
+    for (int r = 0; r < g; ++r) {
+        if (t < g) a[r][t] = B[r * g + t];
+        if (t < g) a[r][g + t] = (r == t) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    int bad = 0;
+    for (int c = 0; c < g; ++c) {
+        if (t == 0) {
+            int best = c;
+            for (int r = c + 1; r < g; ++r)
+                if (fabs(a[r][c]) > fabs(a[best][c])) best = r;
+            piv = best;
+        }
+        __syncthreads();
+        int pr = piv;
+        if (t < 2 * g && pr != c) {
+            double tmp = a[c][t];
+            a[c][t] = a[pr][t];
+            a[pr][t] = tmp;
+        }
+        __syncthreads();
+        double d = a[c][c];
+        if (d == 0.0) bad = 1;
+        __syncthreads();
+        if (t < 2 * g && d != 0.0) a[c][t] /= d;
+        __syncthreads();
+        for (int r = 0; r < g; ++r) {
+            if (r == c) continue;
+            double f = a[r][c];
+            __syncthreads();
+            if (t < 2 * g) a[r][t] -= f * a[c][t];
+            __syncthreads();
+        }
+    }
+    for (int r = 0; r < g; ++r)
+        if (t < g) B[r * g + t] = a[r][g + t];
+    if (t == 0) info[j] = bad;
+}
+
+// y[j g + m][c] = sum_n inv_j[m][n] x[j g + n][c]
+__global__ void block_apply_kernel(const double *__restrict__ inv, int n_panels, int g,
+                                   const double *__restrict__ x, double *__restrict__ y) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_panels * g) return;
+    int j = i / g, m = i - j * g;
+    const double *row = inv + ((size_t)j * g + m) * g;
+    const double *xs = x + (size_t)j * g * 3;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int n = 0; n < g; ++n) {
+        double v = row[n];
+        a0 += v * xs[3 * n + 0];
+        a1 += v * xs[3 * n + 1];
+        a2 += v * xs[3 * n + 2];
+    }
+    y[3 * (size_t)i + 0] = a0;
+    y[3 * (size_t)i + 1] = a1;
+    y[3 * (size_t)i + 2] = a2;
+}
+
 // ---------------------------------------------------------------- K12 --
 __device__ __forceinline__ unsigned char quantise8(double v) {
     v = fmin(fmax(v, 0.0), 1.0);
@@ -228,7 +326,7 @@ cudaError_t launch_interp(const DevGeom &G, const double *node_vals, double *seg
                           cudaStream_t st) {
     int th = 256;
     interp_kernel<<<(G.S + th - 1) / th, th, 0, st>>>(G.lambda.ptr, node_vals, seg_vals, G.S, G.s,
-                                                      G.g);
+                                                      G.g); note_launch();
     return cudaGetLastError();
 }
 
@@ -245,13 +343,14 @@ cudaError_t launch_dense_assemble(const DevGeom &G, double *AG, double *AF, cuda
     else if (G.g <= 16) DC_ASM(16);
     else DC_ASM(32);
 #undef DC_ASM
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_dense_gemv(const double *A, int N, const double *x, double *y, cudaStream_t st) {
     int th = 256;
     long long threads = (long long)N * 32;
-    dense_gemv_kernel<<<(unsigned)((threads + th - 1) / th), th, 0, st>>>(A, N, x, y);
+    dense_gemv_kernel<<<(unsigned)((threads + th - 1) / th), th, 0, st>>>(A, N, x, y); note_launch();
     return cudaGetLastError();
 }
 
@@ -261,7 +360,7 @@ cudaError_t launch_dense_eval_grid(const DevGeom &G, const double *sbar, const d
     if (npix == 0) return cudaSuccess;
     unsigned blocks = (unsigned)((npix + kEvalThreads - 1) / kEvalThreads);
     dense_eval_grid_kernel<<<blocks, kEvalThreads, 0, st>>>(G.seg.ptr, G.segw.ptr, sbar, mbar, G.S,
-                                                            vp, u);
+                                                            vp, u); note_launch();
     return cudaGetLastError();
 }
 
@@ -269,7 +368,30 @@ cudaError_t launch_dense_eval_points(const DevGeom &G, const double *sbar, const
                                      const double *xy, int n, double *u, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     dense_eval_points_kernel<<<(n + kEvalThreads - 1) / kEvalThreads, kEvalThreads, 0, st>>>(
-        G.seg.ptr, G.segw.ptr, sbar, mbar, G.S, xy, n, u);
+        G.seg.ptr, G.segw.ptr, sbar, mbar, G.S, xy, n, u); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_panel_block_inverse(const DevGeom &G, double *inv, int *info, cudaStream_t st) {
+    int th = 32;
+#define DC_PB(MG)                                                                                 \
+    panel_blocks_kernel<MG><<<G.n_panels, th, 0, st>>>(G.seg.ptr, G.segw.ptr, G.node_xy.ptr,      \
+                                                       G.node_seg.ptr, G.node_seg2.ptr,           \
+                                                       G.lambda.ptr, inv, G.s, G.g)
+    if (G.g <= 4) DC_PB(4);
+    else if (G.g <= 8) DC_PB(8);
+    else if (G.g <= 16) DC_PB(16);
+    else DC_PB(32);
+#undef DC_PB
+    note_launch();
+    invert_blocks_kernel<<<G.n_panels, 2 * kMaxG, 0, st>>>(inv, G.g, info); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_apply(const double *inv, int n_panels, int g, const double *x, double *y,
+                               cudaStream_t st) {
+    int n = n_panels * g, th = 256;
+    block_apply_kernel<<<(n + th - 1) / th, th, 0, st>>>(inv, n_panels, g, x, y); note_launch();
     return cudaGetLastError();
 }
 
@@ -279,7 +401,7 @@ cudaError_t launch_write_outputs(const double *u, long long n, void *rgb, int rg
     if (n3 == 0) return cudaSuccess;
     int th = 256;
     write_outputs_kernel<double><<<(unsigned)((n3 + th - 1) / th), th, 0, st>>>(u, n3, rgb,
-                                                                                 rgb_dtype, rgb8);
+                                                                                 rgb_dtype, rgb8); note_launch();
     return cudaGetLastError();
 }
 
@@ -289,19 +411,19 @@ cudaError_t launch_write_outputs_f32(const float *u, long long n, void *rgb, int
     if (n3 == 0) return cudaSuccess;
     int th = 256;
     write_outputs_kernel<float><<<(unsigned)((n3 + th - 1) / th), th, 0, st>>>(u, n3, rgb,
-                                                                               rgb_dtype, rgb8);
+                                                                               rgb_dtype, rgb8); note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_mu(const DevGeom &G, double *mu, cudaStream_t st) {
     int n3 = 3 * G.N, th = 256;
-    mu_kernel<<<(n3 + th - 1) / th, th, 0, st>>>(G.u_plus.ptr, G.u_minus.ptr, mu, n3);
+    mu_kernel<<<(n3 + th - 1) / th, th, 0, st>>>(G.u_plus.ptr, G.u_minus.ptr, mu, n3); note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_rhs(const DevGeom &G, const double *Fmu, double *b, cudaStream_t st) {
     int n3 = 3 * G.N, th = 256;
-    rhs_kernel<<<(n3 + th - 1) / th, th, 0, st>>>(G.u_plus.ptr, G.u_minus.ptr, Fmu, b, n3);
+    rhs_kernel<<<(n3 + th - 1) / th, th, 0, st>>>(G.u_plus.ptr, G.u_minus.ptr, Fmu, b, n3); note_launch();
     return cudaGetLastError();
 }
 

@@ -25,9 +25,8 @@
 #include <cstring>
 #include <vector>
 
-#include "fmm.h"
+#include "fmm_impl.h"
 #include "segint.cuh"
-#include "tree.h"
 
 namespace dc {
 
@@ -59,16 +58,7 @@ __device__ __forceinline__ void cfma(double2 &acc, double2 m, double2 v) {
     acc.y += m.x * v.y + m.y * v.x;
 }
 
-struct DevTree {
-    const double *cc;       // [nC][2] centres
-    const double *cw;       // [nC] widths
-    const int *parent, *child0, *quad;
-    const int *pstart, *pcount;
-    const double *pc;       // [np][4]
-    const double *pw;       // [np] arc weight
-    const int *pseg;        // [np]
-    const int *u_ptr, *u_idx, *v_ptr, *v_idx, *v_off, *w_ptr, *w_idx, *x_ptr, *x_idx;
-};
+
 
 // ---------------------------------------------------------------- P2M --
 __global__ void p2m_kernel(DevTree t, const int *__restrict__ leaves, const double *__restrict__ sbar,
@@ -327,10 +317,7 @@ __global__ void eval_targets_kernel(DevTree t, const int *__restrict__ leaves,
     }
 }
 
-// One block per pixel tile inside one leaf.
-struct Tile {
-    int leaf, r0, c0, nr, nc;
-};
+
 
 __device__ __forceinline__ unsigned char q8(double v) {
     v = fmin(fmax(v, 0.0), 1.0);
@@ -421,91 +408,66 @@ cudaError_t upload_cd(DevBuf<double2> &buf, const std::vector<cd> &v, cudaStream
 }  // namespace
 
 // ====================================================================== Impl
-struct Fmm::Impl {
-    dc_options opt{};
-    int p = 0, P1 = 0;
-    Tree tree;
-    const DevGeom *D = nullptr;
-    // device tree
-    DevBuf<double> cc, cw, pc, pw;
-    DevBuf<int> parent, child0, quad, pstart, pcount, pseg;
-    DevBuf<int> u_ptr, u_idx, v_ptr, v_idx, v_off, w_ptr, w_idx, x_ptr, x_idx;
-    DevBuf<int> p2m_leaves;
-    int n_p2m = 0;
-    // node targets
-    DevBuf<int> nt_leaves, nt_start, nt_count, nt_perm, nt_own1, nt_own2;
-    DevBuf<double> nt_xy;
-    int n_nt_leaves = 0;
-    // point targets (eval_points)
-    DevBuf<int> pt_leaves, pt_start, pt_count, pt_perm;
-    DevBuf<double> pt_xy, pt_out;
-    // tables and expansions
-    DevBuf<double2> m2m, l2l, m2l, M, L;
-    // scratch
-    DevBuf<double> sbar, mbar;
-    DevBuf<Tile> tiles;
-    long long p2p_nodes = 0, m2l_cnt = 0, render_pairs = 0;
+DevTree Fmm::Impl::dt() const {
+    DevTree t;
+    t.cc = cc.ptr;
+    t.cw = cw.ptr;
+    t.parent = parent.ptr;
+    t.child0 = child0.ptr;
+    t.quad = quad.ptr;
+    t.pstart = pstart.ptr;
+    t.pcount = pcount.ptr;
+    t.pc = pc.ptr;
+    t.pw = pw.ptr;
+    t.pseg = pseg.ptr;
+    t.u_ptr = u_ptr.ptr;
+    t.u_idx = u_idx.ptr;
+    t.v_ptr = v_ptr.ptr;
+    t.v_idx = v_idx.ptr;
+    t.v_off = v_off.ptr;
+    t.w_ptr = w_ptr.ptr;
+    t.w_idx = w_idx.ptr;
+    t.x_ptr = x_ptr.ptr;
+    t.x_idx = x_idx.ptr;
+    return t;
+}
 
-    DevTree dt() const {
-        DevTree t;
-        t.cc = cc.ptr;
-        t.cw = cw.ptr;
-        t.parent = parent.ptr;
-        t.child0 = child0.ptr;
-        t.quad = quad.ptr;
-        t.pstart = pstart.ptr;
-        t.pcount = pcount.ptr;
-        t.pc = pc.ptr;
-        t.pw = pw.ptr;
-        t.pseg = pseg.ptr;
-        t.u_ptr = u_ptr.ptr;
-        t.u_idx = u_idx.ptr;
-        t.v_ptr = v_ptr.ptr;
-        t.v_idx = v_idx.ptr;
-        t.v_off = v_off.ptr;
-        t.w_ptr = w_ptr.ptr;
-        t.w_idx = w_idx.ptr;
-        t.x_ptr = x_ptr.ptr;
-        t.x_idx = x_idx.ptr;
-        return t;
+// Up and down passes for segment densities (sbar / mbar), FP64.
+cudaError_t Fmm::Impl::passes(const double *sb, const double *mb, int use_s, int use_m,
+                              cudaStream_t st) {
+    const int nC = tree.n_cells();
+    size_t ebytes = (size_t)nC * 3 * P1 * sizeof(double2);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(M.ptr, 0, ebytes, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(L.ptr, 0, ebytes, st)) != cudaSuccess) return e;
+    DevTree t = dt();
+    int th = ((P1 + 31) / 32) * 32;
+    if (n_p2m > 0)
+        p2m_kernel<<<n_p2m, th, 0, st>>>(t, p2m_leaves.ptr, sb, mb, use_s, use_m, P1, M.ptr); note_launch();
+    for (int l = tree.depth - 1; l >= 2; --l) {
+        int lo = tree.level_start[l], hi = tree.level_start[l + 1];
+        if (hi > lo) m2m_kernel<<<hi - lo, th, 0, st>>>(t, lo, P1, m2m.ptr, M.ptr); note_launch();
     }
+    for (int l = 2; l <= tree.depth; ++l) {
+        int lo = tree.level_start[l], hi = tree.level_start[l + 1];
+        if (hi > lo)
+            down_kernel<<<hi - lo, th, 0, st>>>(t, lo, l, P1, l2l.ptr, m2l.ptr, M.ptr, sb, mb,
+                                                 use_s, use_m, L.ptr); note_launch();
+    }
+    return cudaGetLastError();
+}
 
-    // Up and down passes for segment densities (sbar / mbar).
-    cudaError_t passes(const double *sb, const double *mb, int use_s, int use_m, cudaStream_t st) {
-        const int nC = tree.n_cells();
-        size_t ebytes = (size_t)nC * 3 * P1 * sizeof(double2);
-        cudaError_t e;
-        if ((e = cudaMemsetAsync(M.ptr, 0, ebytes, st)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(L.ptr, 0, ebytes, st)) != cudaSuccess) return e;
-        DevTree t = dt();
-        int th = ((P1 + 31) / 32) * 32;
-        if (n_p2m > 0)
-            p2m_kernel<<<n_p2m, th, 0, st>>>(t, p2m_leaves.ptr, sb, mb, use_s, use_m, P1, M.ptr);
-        for (int l = tree.depth - 1; l >= 2; --l) {
-            int lo = tree.level_start[l], hi = tree.level_start[l + 1];
-            if (hi > lo) m2m_kernel<<<hi - lo, th, 0, st>>>(t, lo, P1, m2m.ptr, M.ptr);
-        }
-        for (int l = 2; l <= tree.depth; ++l) {
-            int lo = tree.level_start[l], hi = tree.level_start[l + 1];
-            if (hi > lo)
-                down_kernel<<<hi - lo, th, 0, st>>>(t, lo, l, P1, l2l.ptr, m2l.ptr, M.ptr, sb, mb,
-                                                     use_s, use_m, L.ptr);
-        }
-        return cudaGetLastError();
-    }
-
-    cudaError_t apply_nodes(const double *x, double *y, bool single, cudaStream_t st) {
-        cudaError_t e = launch_interp(*D, x, single ? sbar.ptr : mbar.ptr, st);
-        if (e != cudaSuccess) return e;
-        int us = single ? 1 : 0, um = single ? 0 : 1;
-        if ((e = passes(sbar.ptr, mbar.ptr, us, um, st)) != cudaSuccess) return e;
-        if (n_nt_leaves > 0)
-            eval_targets_kernel<<<n_nt_leaves, 64, 0, st>>>(
-                dt(), nt_leaves.ptr, nt_start.ptr, nt_count.ptr, nt_xy.ptr, nt_own1.ptr,
-                nt_own2.ptr, nt_perm.ptr, P1, M.ptr, L.ptr, sbar.ptr, mbar.ptr, us, um, y);
-        return cudaGetLastError();
-    }
-};
+cudaError_t Fmm::Impl::apply_nodes(const double *x, double *y, bool single, cudaStream_t st) {
+    cudaError_t e = launch_interp(*D, x, single ? sbar.ptr : mbar.ptr, st);
+    if (e != cudaSuccess) return e;
+    int us = single ? 1 : 0, um = single ? 0 : 1;
+    if ((e = passes(sbar.ptr, mbar.ptr, us, um, st)) != cudaSuccess) return e;
+    if (n_nt_leaves > 0)
+        eval_targets_kernel<<<n_nt_leaves, 64, 0, st>>>(
+            dt(), nt_leaves.ptr, nt_start.ptr, nt_count.ptr, nt_xy.ptr, nt_own1.ptr, nt_own2.ptr,
+            nt_perm.ptr, P1, M.ptr, L.ptr, sbar.ptr, mbar.ptr, us, um, y); note_launch();
+    return cudaGetLastError();
+}
 
 Fmm::Fmm() : impl_(new Impl()) {}
 Fmm::~Fmm() = default;
@@ -517,10 +479,11 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     I.p = opt.p;
     I.P1 = opt.p + 1;
     I.D = &D;
-    if (opt.form != DC_FORM_FMM64) {
-        err = "this build provides the FP64 FMM form only";
-        return DC_ERR_UNSUPPORTED;
+    if (opt.form != DC_FORM_FMM64 && opt.form != DC_FORM_FMM32) {
+        err = "FMM build called for a non-FMM form";
+        return DC_ERR_ARG;
     }
+    I.fp32 = (opt.form == DC_FORM_FMM32);
     if (!build_quadtree(G.seg_xy, opt.domain, opt.leaf_size, opt.max_depth, I.tree, err))
         return DC_ERR_GEOMETRY;
     const Tree &T = I.tree;
@@ -633,12 +596,47 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     // the other channel of interp output must be defined (zero) for passes
     cudaMemsetAsync(I.sbar.ptr, 0, I.sbar.bytes(), st);
     cudaMemsetAsync(I.mbar.ptr, 0, I.mbar.bytes(), st);
+    // block-Jacobi preconditioner over panels and refinement buffers
+    if ((e = I.pinv.alloc((size_t)D.n_panels * D.g * D.g)) != cudaSuccess ||
+        (e = I.pinfo.alloc((size_t)D.n_panels)) != cudaSuccess ||
+        (e = I.ir_r.alloc((size_t)3 * D.N)) != cudaSuccess ||
+        (e = I.ir_d.alloc((size_t)3 * D.N)) != cudaSuccess ||
+        (e = I.ir_t.alloc((size_t)3 * D.N)) != cudaSuccess ||
+        (e = launch_panel_block_inverse(D, I.pinv.ptr, I.pinfo.ptr, st)) != cudaSuccess) {
+        err = std::string("fmm preconditioner: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
+    }
+    {
+        std::vector<int> info(D.n_panels);
+        e = cudaMemcpyAsync(info.data(), I.pinfo.ptr, info.size() * sizeof(int),
+                            cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            err = cudaGetErrorString(e);
+            return DC_ERR_CUDA;
+        }
+        for (int j = 0; j < D.n_panels; ++j)
+            if (info[j]) {
+                err = "build_tree: singular self-interaction block on panel " + std::to_string(j);
+                return DC_ERR_GEOMETRY;
+            }
+    }
+    if (I.fp32) return I.build32(G, st, err);
     return DC_OK;
 }
 
 cudaError_t Fmm::prepare_eval(const double *sbar, const double *mbar, cudaStream_t st) {
-    impl_->render_pairs = 0;
-    return impl_->passes(sbar, mbar, 1, 1, st);
+    Impl &I = *impl_;
+    I.render_pairs = 0;
+    I.render_m2p = 0;
+    I.render_flops = 0.0;
+    I.render_eval_ms = 0.0;
+    if (I.fp32) {
+        cudaError_t e = I.to_f32_density(sbar, mbar, st);
+        if (e != cudaSuccess) return e;
+        return I.passes32(I.sbar32.ptr, I.mbar32.ptr, 1, 1, st);
+    }
+    return I.passes(sbar, mbar, 1, 1, st);
 }
 
 cudaError_t Fmm::apply_single_layer(const double *x, double *y, cudaStream_t st) {
@@ -650,20 +648,77 @@ cudaError_t Fmm::apply_double_layer(const double *x, double *y, cudaStream_t st)
 }
 
 namespace {
-struct FmmSingleOp : Operator {
-    Fmm *f;
-    cudaError_t apply(const double *x, double *y, cudaStream_t st) override {
-        return f->apply_single_layer(x, y, st);
+// v -> A M^-1 v with M the panel-block preconditioner (right preconditioning).
+struct PrecOp : Operator {
+    Fmm::Impl *f;
+    bool fp32 = false;
+    cudaError_t apply(const double *v, double *y, cudaStream_t st) override {
+        cudaError_t e = launch_block_apply(f->pinv.ptr, f->D->n_panels, f->D->g, v, f->ir_t.ptr, st);
+        if (e != cudaSuccess) return e;
+        return fp32 ? f->apply_nodes32(f->ir_t.ptr, y, true, st)
+                    : f->apply_nodes(f->ir_t.ptr, y, true, st);
     }
 };
 }  // namespace
 
 cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_options &opt,
                        cudaStream_t st, GmresResult &res, std::string &err) {
-    FmmSingleOp op;
-    op.f = this;
-    return gmres_solve(w, op, impl_->D->N, b, x, opt.gmres_tol, opt.gmres_restart,
-                       opt.gmres_max_iter, st, res, err);
+    // Iterative refinement around right-preconditioned GMRES:
+    //   r = b - A x            (FP64 FMM operator)
+    //   z = GMRES(A' M^-1, 0, r, tol')   A' = FP64 or FP32 FMM operator,
+    //                                    M = block diagonal of G_H (panels)
+    //   x += M^-1 z
+    // until ||r|| <= tol ||b|| per channel.  The preconditioner changes the
+    // iteration, not the discrete solution of Eq. 27.
+    Impl &I = *impl_;
+    const int N = I.D->N;
+    PrecOp op;
+    op.f = &I;
+    res = GmresResult();
+    double bn[3], rn[3];
+    cudaError_t e = vec_norms3(w, b, N, bn, st);
+    if (e != cudaSuccess) return e;
+    const int max_outer = I.fp32 ? 12 : 4;
+    int used = 0;
+    for (int outer = 0; outer <= max_outer; ++outer) {
+        if ((e = I.apply_nodes(x, I.ir_t.ptr, true, st)) != cudaSuccess) return e;
+        res.n_matvec++;
+        if ((e = vec_residual(b, I.ir_t.ptr, I.ir_r.ptr, 3 * N, st)) != cudaSuccess) return e;
+        if ((e = vec_norms3(w, I.ir_r.ptr, N, rn, st)) != cudaSuccess) return e;
+        int mask[3], any = 0;
+        double need = 1.0;
+        for (int c = 0; c < 3; ++c) {
+            res.rel_resid[c] = bn[c] > 0 ? rn[c] / bn[c] : 0.0;
+            mask[c] = rn[c] > opt.gmres_tol * bn[c];
+            any |= mask[c];
+            if (mask[c]) need = std::min(need, opt.gmres_tol * bn[c] / rn[c]);
+        }
+        if (!any) {
+            res.converged = 1;
+            break;
+        }
+        if (outer == max_outer || used >= opt.gmres_max_iter) break;
+        if ((e = vec_mask3(I.ir_r.ptr, N, mask, st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(I.ir_d.ptr, 0, sizeof(double) * 3 * N, st)) != cudaSuccess) return e;
+        double inner_tol = I.fp32 ? std::max(1e-5, need) : std::max(0.5 * need, 1e-15);
+        GmresResult inner;
+        op.fp32 = I.fp32;
+        e = gmres_solve(w, op, N, I.ir_r.ptr, I.ir_d.ptr, inner_tol, opt.gmres_restart,
+                        opt.gmres_max_iter - used, st, inner, err);
+        if (e != cudaSuccess) return e;
+        int mx = 0;
+        for (int c = 0; c < 3; ++c) {
+            res.iters[c] += inner.iters[c];
+            mx = std::max(mx, inner.iters[c]);
+        }
+        used += std::max(mx, 1);
+        res.n_matvec += inner.n_matvec;
+        if ((e = launch_block_apply(I.pinv.ptr, I.D->n_panels, I.D->g, I.ir_d.ptr, I.ir_t.ptr, st)) !=
+            cudaSuccess)
+            return e;
+        if ((e = vec_axpy(x, I.ir_t.ptr, 3 * N, st)) != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
 }
 
 namespace {
@@ -704,7 +759,7 @@ dc_status Fmm::render_grid(const VpDev &vp, const double *sbar, const double *mb
         return DC_ERR_CUDA;
     }
     std::vector<Tile> tiles;
-    const int TS = 16;
+    const int TS = 16;   // 16 x 16 pixels per block
     long long pairs = 0;
     for (int c = 0; c < T.n_cells(); ++c) {
         if (!T.is_leaf(c)) continue;
@@ -714,9 +769,12 @@ dc_status Fmm::render_grid(const VpDev &vp, const double *sbar, const double *mb
         pixel_range(vp.x0, vp.dx, vp.width, bx0, bx0 + w, c0, c1);
         pixel_range(vp.y0, vp.dy, vp.height, by0, by0 + w, r0, r1);
         if (c1 <= c0 || r1 <= r0) continue;
-        long long up = 0;
+        long long up = 0, npx = (long long)(c1 - c0) * (r1 - r0);
         for (int e2 = T.u_ptr[c]; e2 < T.u_ptr[c + 1]; ++e2) up += T.piece_count[T.u_idx[e2]];
-        pairs += up * (long long)(c1 - c0) * (r1 - r0);
+        pairs += up * npx;
+        long long wn = T.w_ptr[c + 1] - T.w_ptr[c];
+        I.render_m2p += wn * npx;
+        I.render_flops += 45.0 * double(up * npx) + 24.0 * I.P1 * double((1 + wn) * npx);
         for (int r = r0; r < r1; r += TS)
             for (int cc = c0; cc < c1; cc += TS)
                 tiles.push_back({c, r, cc, std::min(TS, r1 - r), std::min(TS, c1 - cc)});
@@ -727,8 +785,24 @@ dc_status Fmm::render_grid(const VpDev &vp, const double *sbar, const double *mb
         err = cudaGetErrorString(e);
         return DC_ERR_CUDA;
     }
-    eval_tiles_kernel<<<int(tiles.size()), 128, 0, st>>>(I.dt(), I.tiles.ptr, vp, I.P1, I.M.ptr,
-                                                          I.L.ptr, sbar, mbar, rgb, rgb_dtype, rgb8);
+    if (I.eval_timing) {
+        if (!I.ev0 && (e = cudaEventCreate(&I.ev0)) != cudaSuccess) return DC_ERR_CUDA;
+        if (!I.ev1 && (e = cudaEventCreate(&I.ev1)) != cudaSuccess) return DC_ERR_CUDA;
+        cudaEventRecord(I.ev0, st);
+    }
+    if (I.fp32)
+        e = I.render_tiles32(vp, int(tiles.size()), rgb, rgb_dtype, rgb8, st);
+    else
+        eval_tiles_kernel<<<int(tiles.size()), 128, 0, st>>>(I.dt(), I.tiles.ptr, vp, I.P1, I.M.ptr,
+                                                              I.L.ptr, sbar, mbar, rgb, rgb_dtype,
+                                                              rgb8); note_launch();
+    if (I.eval_timing) {
+        cudaEventRecord(I.ev1, st);
+        cudaEventSynchronize(I.ev1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, I.ev0, I.ev1);
+        I.render_eval_ms += ms;
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = cudaGetErrorString(e);
@@ -779,9 +853,25 @@ dc_status Fmm::eval_points(const double *xy, int n, const double *sbar, const do
         err = cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
     }
-    eval_targets_kernel<<<int(leaves.size()), 64, 0, st>>>(
-        I.dt(), I.pt_leaves.ptr, I.pt_start.ptr, I.pt_count.ptr, I.pt_xy.ptr, nullptr, nullptr,
-        I.pt_perm.ptr, I.P1, I.M.ptr, I.L.ptr, sbar, mbar, 1, 1, I.pt_out.ptr);
+    if (I.fp32) {
+        std::vector<Tile> items;
+        std::vector<float2> q32(n);
+        for (int c : leaves) {
+            double cx = T.cx(c), cy = T.cy(c);
+            for (int j = start[c]; j < start[c] + cnt[c]; ++j)
+                q32[j] = make_float2((float)(sxy[2 * j] - cx), (float)(sxy[2 * j + 1] - cy));
+            for (int j = 0; j < cnt[c]; j += 64) items.push_back({c, start[c] + j, 0, std::min(64, cnt[c] - j), 0});
+        }
+        if ((e = upload(I.pt_items, items, st)) != cudaSuccess || (e = upload(I.pt_q32, q32, st)) != cudaSuccess ||
+            (e = I.eval_points32(int(items.size()), I.pt_out.ptr, st)) != cudaSuccess) {
+            err = cudaGetErrorString(e);
+            return DC_ERR_CUDA;
+        }
+    } else {
+        eval_targets_kernel<<<int(leaves.size()), 64, 0, st>>>(
+            I.dt(), I.pt_leaves.ptr, I.pt_start.ptr, I.pt_count.ptr, I.pt_xy.ptr, nullptr, nullptr,
+            I.pt_perm.ptr, I.P1, I.M.ptr, I.L.ptr, sbar, mbar, 1, 1, I.pt_out.ptr); note_launch();
+    }
     if ((e = launch_write_outputs(I.pt_out.ptr, n, out, out_dtype, nullptr, st)) != cudaSuccess) {
         err = cudaGetErrorString(e);
         return DC_ERR_CUDA;
@@ -803,5 +893,9 @@ void Fmm::fill_sizes(dc_sizes *out) const {
 long long Fmm::p2p_pairs_nodes() const { return impl_->p2p_nodes; }
 long long Fmm::m2l_pairs() const { return impl_->m2l_cnt; }
 long long Fmm::last_render_p2p_pairs() const { return impl_->render_pairs; }
+long long Fmm::last_render_m2p_pairs() const { return impl_->render_m2p; }
+double Fmm::last_render_eval_flops() const { return impl_->render_flops; }
+void Fmm::set_eval_timing(bool on) { impl_->eval_timing = on; }
+double Fmm::last_render_eval_ms() const { return impl_->render_eval_ms; }
 
 }  // namespace dc

@@ -35,6 +35,12 @@ public:
     long long p2p_pairs_nodes() const;
     long long m2l_pairs() const;
     long long last_render_p2p_pairs() const;
+    long long last_render_m2p_pairs() const;
+    double last_render_eval_flops() const;
+    // When on, render_grid times its evaluation kernel with CUDA events on
+    // the launching stream (synchronising after each launch).
+    void set_eval_timing(bool on);
+    double last_render_eval_ms() const;
 
     struct Impl;
 

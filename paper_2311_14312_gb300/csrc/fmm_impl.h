@@ -1,0 +1,113 @@
+// Internal state of the FMM forms, shared by the FP64 (fmm.cu) and FP32
+// (fmm32.cu) translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "dc_internal.h"
+#include "fmm.h"
+#include "tree.h"
+
+namespace dc {
+
+// FP64 view of the tree: absolute coordinates.
+struct DevTree {
+    const double *cc;       // [nC][2] centres
+    const double *cw;       // [nC] widths
+    const int *parent, *child0, *quad;
+    const int *pstart, *pcount;
+    const double *pc;       // [np][4]
+    const double *pw;       // [np] arc weight
+    const int *pseg;        // [np]
+    const int *u_ptr, *u_idx, *v_ptr, *v_idx, *v_off, *w_ptr, *w_idx, *x_ptr, *x_idx;
+};
+
+// FP32 view: every coordinate is relative to a cell centre, so FP32 keeps
+// the relative accuracy of the local geometry at any zoom of the canvas.
+struct DevTree32 {
+    const float *iw;        // [nC] 1 / width
+    const float *logw;      // [nC] log(width)
+    const int *parent, *child0, *quad;
+    const int *pstart, *pcount;
+    const float4 *pc;       // [np] endpoints minus the own leaf's centre
+    const float *pw;        // [np] arc weight
+    const float *plen;      // [np] chord length
+    const int *pseg;
+    const int *u_ptr, *u_idx, *v_ptr, *v_idx, *v_off, *w_ptr, *w_idx, *x_ptr, *x_idx;
+    const float2 *u_off;    // per list-1 entry: centre(source) - centre(target)
+    const float2 *w_off;    // per list-3 entry
+    const float2 *x_off;    // per list-4 entry
+};
+
+// A unit of evaluation work inside one leaf: a pixel rectangle (r0, c0,
+// nr x nc) or, for target lists, targets [r0, r0 + nr) with nc = 0.
+struct Tile {
+    int leaf, r0, c0, nr, nc;
+};
+
+struct Fmm::Impl {
+    dc_options opt{};
+    int p = 0, P1 = 0;
+    bool fp32 = false;
+    Tree tree;
+    const DevGeom *D = nullptr;
+    // FP64 tree
+    DevBuf<double> cc, cw, pc, pw;
+    DevBuf<int> parent, child0, quad, pstart, pcount, pseg;
+    DevBuf<int> u_ptr, u_idx, v_ptr, v_idx, v_off, w_ptr, w_idx, x_ptr, x_idx;
+    DevBuf<int> p2m_leaves;
+    int n_p2m = 0;
+    // node targets sorted by leaf
+    DevBuf<int> nt_leaves, nt_start, nt_count, nt_perm, nt_own1, nt_own2;
+    DevBuf<double> nt_xy;
+    int n_nt_leaves = 0;
+    // point targets (eval_points)
+    DevBuf<int> pt_leaves, pt_start, pt_count, pt_perm;
+    DevBuf<double> pt_xy, pt_out;
+    DevBuf<float2> pt_q32;
+    DevBuf<Tile> pt_items;
+    // FP64 tables and expansions
+    DevBuf<double2> m2m, l2l, m2l, M, L;
+    DevBuf<double> sbar, mbar;
+    DevBuf<Tile> tiles;
+    // FP32 form
+    DevBuf<float> iw32, logw32, pw32, plen32;
+    DevBuf<float4> pc32;
+    DevBuf<float2> uoff32, woff32, xoff32;
+    DevBuf<float2> m2m32, l2l32, m2l32, M32, L32;
+    DevBuf<float> sbar32, mbar32;
+    DevBuf<float2> nt_q32;        // node targets minus their leaf centre
+    DevBuf<Tile> nt_items;        // node work items (<= 64 targets each)
+    int n_nt_items = 0;
+    DevBuf<double> ir_r, ir_d, ir_t;   // refinement residual, correction, scratch
+    DevBuf<double> pinv;          // [panels][g][g] inverse self-interaction blocks
+    DevBuf<int> pinfo;
+    long long p2p_nodes = 0, m2l_cnt = 0, render_pairs = 0, render_m2p = 0;
+    double render_flops = 0.0, render_eval_ms = 0.0;
+    bool eval_timing = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    ~Impl() {
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    }
+
+    DevTree dt() const;
+    DevTree32 dt32() const;
+    // FP64 passes / node operator (fmm.cu)
+    cudaError_t passes(const double *sb, const double *mb, int use_s, int use_m, cudaStream_t st);
+    cudaError_t apply_nodes(const double *x, double *y, bool single, cudaStream_t st);
+    // FP32 (fmm32.cu)
+    dc_status build32(const Geometry &G, cudaStream_t st, std::string &err);
+    cudaError_t passes32(const float *sb, const float *mb, int use_s, int use_m, cudaStream_t st);
+    cudaError_t apply_nodes32(const double *x, double *y, bool single, cudaStream_t st);
+    cudaError_t interp32(const double *node_vals, float *seg_vals, cudaStream_t st);
+    cudaError_t render_tiles32(const VpDev &vp, int n_tiles, void *rgb, int rgb_dtype,
+                               unsigned char *rgb8, cudaStream_t st);
+    cudaError_t eval_points32(int n_items, double *out, cudaStream_t st);
+    cudaError_t to_f32_density(const double *sb, const double *mb, cudaStream_t st);
+};
+
+}  // namespace dc

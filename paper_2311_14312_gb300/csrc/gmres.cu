@@ -216,7 +216,7 @@ struct GmresWork {
         DC_TRY(hcol.alloc((size_t)(m + 1) * 3));
         DC_TRY(hpass.alloc((size_t)(m + 1) * 3));
         DC_TRY(hnext.alloc(3));
-        DC_TRY(small.alloc(16));
+        DC_TRY(small.alloc(32));
         DC_TRY(R.alloc((size_t)3 * m * m));
         DC_TRY(cs.alloc((size_t)3 * m));
         DC_TRY(sn.alloc((size_t)3 * m));
@@ -242,6 +242,36 @@ struct GmresWork {
 };
 
 GmresWork *gmres_work_create() { return new GmresWork(); }
+
+namespace {
+__global__ void axpy_kernel(double *__restrict__ x, const double *__restrict__ d, int n3) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n3) x[t] += d[t];
+}
+__global__ void mask3_kernel(double *__restrict__ v, int n3, int k0, int k1, int k2) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n3) return;
+    int c = t % 3;
+    int keep = c == 0 ? k0 : (c == 1 ? k1 : k2);
+    if (!keep) v[t] = 0.0;
+}
+}  // namespace
+
+cudaError_t vec_residual(const double *b, const double *Ax, double *r, int n3, cudaStream_t st) {
+    residual_kernel<<<(n3 + 255) / 256, 256, 0, st>>>(b, Ax, r, n3); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t vec_axpy(double *x, const double *d, int n3, cudaStream_t st) {
+    axpy_kernel<<<(n3 + 255) / 256, 256, 0, st>>>(x, d, n3); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t vec_mask3(double *v, int N, const int keep[3], cudaStream_t st) {
+    int n3 = 3 * N;
+    mask3_kernel<<<(n3 + 255) / 256, 256, 0, st>>>(v, n3, keep[0], keep[1], keep[2]); note_launch();
+    return cudaGetLastError();
+}
 void gmres_work_destroy(GmresWork *w) { delete w; }
 
 namespace {
@@ -249,9 +279,9 @@ namespace {
 // nrm[c] = || v[:, c] ||_2 (device), through the deterministic dot kernels.
 cudaError_t norms(GmresWork &W, const double *v, double *nrm, cudaStream_t st) {
     dim3 grid(W.nchunk, 1);
-    dots_partial_kernel<<<grid, kDotThreads, 0, st>>>(v, 0, v, W.N, W.nchunk, W.partial.ptr);
-    dots_finalize_kernel<<<1, 32, 0, st>>>(W.partial.ptr, W.nchunk, 1, nrm, 0);
-    sqrt3_kernel<<<1, 32, 0, st>>>(nrm);
+    dots_partial_kernel<<<grid, kDotThreads, 0, st>>>(v, 0, v, W.N, W.nchunk, W.partial.ptr); note_launch();
+    dots_finalize_kernel<<<1, 32, 0, st>>>(W.partial.ptr, W.nchunk, 1, nrm, 0); note_launch();
+    sqrt3_kernel<<<1, 32, 0, st>>>(nrm); note_launch();
     return cudaGetLastError();
 }
 
@@ -262,6 +292,17 @@ __global__ void add_into_kernel(double *__restrict__ dst, const double *__restri
 }
 
 }  // namespace
+
+cudaError_t vec_norms3(GmresWork *Wp, const double *v, int N, double host_out[3], cudaStream_t st) {
+    GmresWork &W = *Wp;
+    cudaError_t e = W.ensure(N, W.m > 0 ? W.m : 1);
+    if (e != cudaSuccess) return e;
+    if ((e = norms(W, v, W.small.ptr + 16, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(host_out, W.small.ptr + 16, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                             st)) != cudaSuccess)
+        return e;
+    return cudaStreamSynchronize(st);
+}
 
 cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, double *x, double tol,
                         int restart, int max_iter, cudaStream_t st, GmresResult &res,
@@ -299,7 +340,7 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
         // r = b - A x ; beta = ||r||
         if ((ce = A.apply(x, W.Ax.ptr, st)) != cudaSuccess) return ce;
         res.n_matvec++;
-        residual_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(b, W.Ax.ptr, W.r.ptr, 3 * N);
+        residual_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(b, W.Ax.ptr, W.r.ptr, 3 * N); note_launch();
         if ((ce = norms(W, W.r.ptr, beta, st)) != cudaSuccess) return ce;
         double hbeta[3];
         if ((ce = cudaMemcpyAsync(hbeta, beta, 3 * sizeof(double), cudaMemcpyDeviceToHost, st)) !=
@@ -316,8 +357,8 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
             break;
         }
         if (total >= max_iter) break;
-        cycle_start_kernel<<<1, 32, 0, st>>>(gs, beta, thr, m);
-        scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.r.ptr, beta, W.V.ptr, N);
+        cycle_start_kernel<<<1, 32, 0, st>>>(gs, beta, thr, m); note_launch();
+        scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.r.ptr, beta, W.V.ptr, N); note_launch();
         int k = 0;
         for (; k < m && total < max_iter; ++k) {
             double *vk = W.V.ptr + (size_t)k * vs;
@@ -327,19 +368,19 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
             for (int pass = 0; pass < 2; ++pass) {
                 dim3 grid(W.nchunk, k + 1);
                 dots_partial_kernel<<<grid, kDotThreads, 0, st>>>(W.V.ptr, vs, W.w.ptr, N,
-                                                                  W.nchunk, W.partial.ptr);
+                                                                  W.nchunk, W.partial.ptr); note_launch();
                 int t3 = (k + 1) * 3;
                 dots_finalize_kernel<<<(t3 + 127) / 128, 128, 0, st>>>(W.partial.ptr, W.nchunk,
-                                                                      k + 1, W.hpass.ptr, 0);
+                                                                      k + 1, W.hpass.ptr, 0); note_launch();
                 orth_update_kernel<<<(N + th - 1) / th, th, 0, st>>>(W.V.ptr, vs, W.hpass.ptr,
-                                                                      k + 1, W.w.ptr, N);
+                                                                      k + 1, W.w.ptr, N); note_launch();
                 add_into_kernel<<<(t3 + 127) / 128, 128, 0, st>>>(W.hcol.ptr, W.hpass.ptr, t3,
-                                                                  pass == 0);
+                                                                  pass == 0); note_launch();
             }
             if ((ce = norms(W, W.w.ptr, W.hnext.ptr, st)) != cudaSuccess) return ce;
             scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.w.ptr, W.hnext.ptr,
-                                                               W.V.ptr + (size_t)(k + 1) * vs, N);
-            givens_kernel<<<1, 32, 0, st>>>(gs, W.hcol.ptr, W.hnext.ptr, thr, k, m);
+                                                               W.V.ptr + (size_t)(k + 1) * vs, N); note_launch();
+            givens_kernel<<<1, 32, 0, st>>>(gs, W.hcol.ptr, W.hnext.ptr, thr, k, m); note_launch();
             total++;
             int hact[3];
             if ((ce = cudaMemcpyAsync(hact, gs.active, 3 * sizeof(int), cudaMemcpyDeviceToHost,
@@ -351,8 +392,8 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
                 break;
             }
         }
-        backsolve_kernel<<<1, 32, 0, st>>>(gs, m);
-        solution_update_kernel<<<(N + th - 1) / th, th, 0, st>>>(gs, W.V.ptr, vs, x, N, m);
+        backsolve_kernel<<<1, 32, 0, st>>>(gs, m); note_launch();
+        solution_update_kernel<<<(N + th - 1) / th, th, 0, st>>>(gs, W.V.ptr, vs, x, N, m); note_launch();
         int hkc[3];
         if ((ce = cudaMemcpyAsync(hkc, gs.kc, 3 * sizeof(int), cudaMemcpyDeviceToHost, st)) !=
             cudaSuccess)

@@ -41,4 +41,24 @@ __device__ __forceinline__ void seg_gf_f64(double qx, double qy, double x1, doub
     F = -w * kInv2Pi * phi;
 }
 
+// Unweighted parts of the same rule: ilog = int log|p - q| dS over the chord
+// and phi = subtended angle (0 on the own segment).
+__device__ __forceinline__ void seg_ilog_phi_f64(double qx, double qy, double x1, double y1,
+                                                 double x2, double y2, bool own, double &ilog,
+                                                 double &phi) {
+    double ax = x1 - qx, ay = y1 - qy;
+    double bx = x2 - qx, by = y2 - qy;
+    double dx = x2 - x1, dy = y2 - y1;
+    double ic = rsqrt(dx * dx + dy * dy);
+    double c = (dx * dx + dy * dy) * ic;
+    double cr = ax * by - ay * bx;
+    double dt = ax * bx + ay * by;
+    phi = own ? 0.0 : atan2(cr, dt);
+    double ra2 = ax * ax + ay * ay, rb2 = bx * bx + by * by;
+    double s1 = (ax * dx + ay * dy) * ic, s2 = (bx * dx + by * dy) * ic;
+    double la = (ra2 > 0.0) ? s1 * log(ra2) : 0.0;
+    double lb = (rb2 > 0.0) ? s2 * log(rb2) : 0.0;
+    ilog = 0.5 * (lb - la) - c + cr * ic * phi;
+}
+
 }  // namespace dc
