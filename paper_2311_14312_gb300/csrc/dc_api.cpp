@@ -513,22 +513,29 @@ dc_status dc_render_viewport(dc_ctx *ctx, int n_vp, const dc_viewport *vps, void
         DC_CK(ctx, ctx->fmm->prepare_eval(ctx->sbar.ptr, ctx->mbar.ptr, s), "fmm passes");
     }
     double dense_eval_ms = 0.0;
+    std::vector<dc::VpDev> vl;
     long long off = 0;
     for (int v = 0; v < n_vp; ++v) {
         const dc_viewport &vp = vps[v];
         long long np = (long long)vp.width * vp.height;
-        if (np == 0) continue;
         dc::VpDev d;
         d.x0 = vp.x0;
         d.y0 = vp.y0;
-        d.dx = (vp.x1 - vp.x0) / vp.width;
-        d.dy = (vp.y1 - vp.y0) / vp.height;
+        d.dx = vp.width > 0 ? (vp.x1 - vp.x0) / vp.width : 0.0;
+        d.dy = vp.height > 0 ? (vp.y1 - vp.y0) / vp.height : 0.0;
         d.width = vp.width;
         d.height = vp.height;
         d.offset = off;
-        void *orgb = drgb ? static_cast<char *>(drgb) + size_t(3) * off * esz : nullptr;
-        unsigned char *orgb8 = drgb8 ? drgb8 + size_t(3) * off : nullptr;
-        if (ctx->opt.form == DC_FORM_DENSE64) {
+        vl.push_back(d);
+        off += np;
+    }
+    if (ctx->opt.form == DC_FORM_DENSE64) {
+        for (int v = 0; v < n_vp; ++v) {
+            const dc::VpDev &d = vl[v];
+            long long np = (long long)d.width * d.height;
+            if (np == 0) continue;
+            void *orgb = drgb ? static_cast<char *>(drgb) + size_t(3) * d.offset * esz : nullptr;
+            unsigned char *orgb8 = drgb8 ? drgb8 + size_t(3) * d.offset : nullptr;
             DC_CK(ctx, ctx->u64.ensure(size_t(3) * np), "alloc");
             if (stats) DC_CK(ctx, cudaEventRecord(e1, s), "event");
             DC_CK(ctx,
@@ -547,13 +554,12 @@ dc_status dc_render_viewport(dc_ctx *ctx, int n_vp, const dc_viewport *vps, void
             }
             DC_CK(ctx, dc::launch_write_outputs(ctx->u64.ptr, np, orgb, rgb_dtype, orgb8, s),
                   "outputs");
-        } else {
-            std::string msg;
-            dc_status fs = ctx->fmm->render_grid(d, ctx->sbar.ptr, ctx->mbar.ptr, orgb, rgb_dtype,
-                                                 orgb8, s, msg);
-            if (fs != DC_OK) return fail(ctx, fs, msg);
         }
-        off += np;
+    } else {
+        std::string msg;
+        dc_status fs = ctx->fmm->render_viewports(vl.data(), n_vp, ctx->sbar.ptr, ctx->mbar.ptr, drgb,
+                                                  rgb_dtype, drgb8, s, msg);
+        if (fs != DC_OK) return fail(ctx, fs, msg);
     }
     if (out_where == DC_MEM_HOST) {
         if (rgb)

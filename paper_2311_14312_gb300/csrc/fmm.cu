@@ -25,7 +25,9 @@
 #include <cstring>
 #include <vector>
 
+#include "evalnodes.cuh"
 #include "fmm_impl.h"
+#include "passes.cuh"
 #include "segint.cuh"
 
 namespace dc {
@@ -59,165 +61,6 @@ __device__ __forceinline__ void cfma(double2 &acc, double2 m, double2 v) {
 }
 
 
-
-// ---------------------------------------------------------------- P2M --
-__global__ void p2m_kernel(DevTree t, const int *__restrict__ leaves, const double *__restrict__ sbar,
-                           const double *__restrict__ mbar, int use_s, int use_m, int P1,
-                           double2 *__restrict__ M) {
-    int cell = leaves[blockIdx.x];
-    int k = threadIdx.x;
-    if (k >= P1) return;
-    double cx = t.cc[2 * cell], cy = t.cc[2 * cell + 1], r = t.cw[cell], ir = 1.0 / r;
-    double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
-    int p0 = t.pstart[cell], pn = t.pcount[cell];
-    for (int i = p0; i < p0 + pn; ++i) {
-        const double *q = t.pc + 4 * (size_t)i;
-        double2 a = make_double2((q[0] - cx) * ir, (q[1] - cy) * ir);
-        double2 b = make_double2((q[2] - cx) * ir, (q[3] - cy) * ir);
-        double dx = q[2] - q[0], dy = q[3] - q[1];
-        double len = sqrt(dx * dx + dy * dy);
-        double om = t.pw[i] * len;
-        // S_k, S_{k-1}
-        double2 S = make_double2(1.0, 0.0), Sp = make_double2(0.0, 0.0), ap = make_double2(1.0, 0.0);
-        for (int m = 1; m <= k; ++m) {
-            ap = cmul(ap, a);
-            Sp = S;
-            S = cadd(cmul(b, S), ap);
-        }
-        double2 cg = cscale(S, om / (k + 1));
-        // -i (w / r) S_{k-1} * om,  w = (dx, dy)/len
-        double2 wr = make_double2(dx / len * ir, dy / len * ir);
-        double2 t1 = cmul(wr, Sp);
-        double2 cf = make_double2(t1.y * om, -t1.x * om);
-        int seg = t.pseg[i];
-        for (int c = 0; c < 3; ++c) {
-            if (use_s) {
-                double s = sbar[3 * (size_t)seg + c];
-                acc[c].x += s * cg.x;
-                acc[c].y += s * cg.y;
-            }
-            if (use_m) {
-                double mu = mbar[3 * (size_t)seg + c];
-                acc[c].x += mu * cf.x;
-                acc[c].y += mu * cf.y;
-            }
-        }
-    }
-    for (int c = 0; c < 3; ++c) M[((size_t)cell * 3 + c) * P1 + k] = acc[c];
-}
-
-// ---------------------------------------------------------------- M2M --
-// Parent (cells [c_lo, c_hi) of one level) from its 4 children.
-__global__ void m2m_kernel(DevTree t, int c_lo, int P1, const double2 *__restrict__ tab,
-                           double2 *__restrict__ M) {
-    int cell = c_lo + blockIdx.x;
-    int k = threadIdx.x;
-    int ch0 = t.child0[cell];
-    if (k >= P1 || ch0 < 0) return;
-    double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
-    for (int q = 0; q < 4; ++q) {
-        const double2 *T = tab + ((size_t)q * P1 + k) * P1;
-        const double2 *src = M + (size_t)(ch0 + q) * 3 * P1;
-        for (int j = 0; j <= k; ++j) {
-            double2 tq = T[j];
-            for (int c = 0; c < 3; ++c) cfma(acc[c], tq, src[c * P1 + j]);
-        }
-    }
-    for (int c = 0; c < 3; ++c) M[((size_t)cell * 3 + c) * P1 + k] = acc[c];
-}
-
-// ------------------------------------------------ L2L + M2L + P2L -------
-__global__ void down_kernel(DevTree t, int c_lo, int level, int P1, const double2 *__restrict__ l2l,
-                            const double2 *__restrict__ m2l, const double2 *__restrict__ M,
-                            const double *__restrict__ sbar, const double *__restrict__ mbar,
-                            int use_s, int use_m, double2 *__restrict__ L) {
-    int cell = c_lo + blockIdx.x;
-    int l = threadIdx.x;
-    if (l >= P1) return;
-    double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
-    double w = t.cw[cell];
-    if (level >= 3) {   // Eq. 73 from the parent
-        int par = t.parent[cell], q = t.quad[cell];
-        const double2 *T = l2l + ((size_t)q * P1 + l) * P1;
-        const double2 *src = L + (size_t)par * 3 * P1;
-        for (int k = l; k < P1; ++k) {
-            double2 tq = T[k];
-            for (int c = 0; c < 3; ++c) cfma(acc[c], tq, src[c * P1 + k]);
-        }
-    }
-    // Eq. 69 over list 2
-    double mlogw = -log(w);
-    for (int e = t.v_ptr[cell]; e < t.v_ptr[cell + 1]; ++e) {
-        int src = t.v_idx[e];
-        const double2 *T = m2l + ((size_t)t.v_off[e] * P1 + l) * P1;
-        const double2 *ms = M + (size_t)src * 3 * P1;
-        for (int k = 0; k < P1; ++k) {
-            double2 tq = T[k];
-            for (int c = 0; c < 3; ++c) cfma(acc[c], tq, ms[c * P1 + k]);
-        }
-        if (l == 0)
-            for (int c = 0; c < 3; ++c) cfma(acc[c], make_double2(mlogw, 0.0), ms[c * P1]);
-    }
-    // Eq. 62 / 78 / 79 over list 4 (segments of bigger separated leaves)
-    double cx = t.cc[2 * cell], cy = t.cc[2 * cell + 1], ir = 1.0 / w;
-    for (int e = t.x_ptr[cell]; e < t.x_ptr[cell + 1]; ++e) {
-        int src = t.x_idx[e];
-        int p0 = t.pstart[src], pn = t.pcount[src];
-        for (int i = p0; i < p0 + pn; ++i) {
-            const double *q = t.pc + 4 * (size_t)i;
-            double2 a = make_double2(q[0] - cx, q[1] - cy);
-            double2 b = make_double2(q[2] - cx, q[3] - cy);
-            double dx = q[2] - q[0], dy = q[3] - q[1];
-            double len = sqrt(dx * dx + dy * dy);
-            double om = t.pw[i];
-            double2 wv = make_double2(dx / len, dy / len);
-            double2 cg, cf;   // coefficient of sigma and of mu
-            double2 lba = clog(cmul(b, cinv(a)));   // log(b / a), |arg| < pi
-            if (l == 0) {
-                double2 la = clog(a);
-                double2 wb = cmul(make_double2(wv.x, -wv.y), b);
-                double2 t2 = cmul(wb, lba);
-                cg = make_double2(om * (len * (1.0 - la.x) - t2.x), om * (-len * la.y - t2.y));
-                cf = make_double2(-om * lba.y, om * lba.x);   // i log(b/a)
-            } else if (l == 1) {
-                double2 t2 = cmul(make_double2(wv.x, -wv.y), lba);
-                cg = cscale(t2, om * w);
-                double2 al = cinv(make_double2(a.x * ir, a.y * ir));
-                double2 be = cinv(make_double2(b.x * ir, b.y * ir));
-                double2 ab = cmul(al, be);                      // T_0 = 1
-                double2 iw = make_double2(-wv.y, wv.x);         // i w
-                cf = cscale(cmul(iw, ab), om * len * ir);
-            } else {
-                double2 al = cinv(make_double2(a.x * ir, a.y * ir));
-                double2 be = cinv(make_double2(b.x * ir, b.y * ir));
-                double2 T = make_double2(1.0, 0.0), Tp = T, bp = make_double2(1.0, 0.0);
-                for (int m = 1; m <= l - 1; ++m) {   // T_{l-1}, Tp = T_{l-2}
-                    bp = cmul(bp, be);
-                    Tp = T;
-                    T = cadd(cmul(al, T), bp);
-                }
-                double2 ab = cmul(al, be);
-                cg = cscale(cmul(ab, Tp), om * len / (double(l) * (l - 1)));
-                double2 iw = make_double2(-wv.y, wv.x);
-                cf = cscale(cmul(cmul(iw, ab), T), om * len * ir / l);
-            }
-            int seg = t.pseg[i];
-            for (int c = 0; c < 3; ++c) {
-                if (use_s) {
-                    double s = sbar[3 * (size_t)seg + c];
-                    acc[c].x += s * cg.x;
-                    acc[c].y += s * cg.y;
-                }
-                if (use_m) {
-                    double mu = mbar[3 * (size_t)seg + c];
-                    acc[c].x += mu * cf.x;
-                    acc[c].y += mu * cf.y;
-                }
-            }
-        }
-    }
-    for (int c = 0; c < 3; ++c) L[((size_t)cell * 3 + c) * P1 + l] = acc[c];
-}
 
 // ------------------------------------------------------------- eval ----
 struct Acc3 {
@@ -324,11 +167,12 @@ __device__ __forceinline__ unsigned char q8(double v) {
     return (unsigned char)floor(255.0 * v + 0.5);
 }
 
-__global__ void eval_tiles_kernel(DevTree t, const Tile *__restrict__ tiles, VpDev vp, int P1,
+__global__ void eval_tiles_kernel(DevTree t, const Tile *__restrict__ tiles, const VpDev *__restrict__ vps, int P1,
                                   const double2 *__restrict__ M, const double2 *__restrict__ L,
                                   const double *__restrict__ sbar, const double *__restrict__ mbar,
                                   void *rgb, int rgb_dtype, unsigned char *rgb8) {
     Tile tl = tiles[blockIdx.x];
+    const VpDev vp = vps[tl.vp];
     int npx = tl.nr * tl.nc;
     for (int j = threadIdx.x; j < npx; j += blockDim.x) {
         int r = tl.r0 + j / tl.nc, c = tl.c0 + j % tl.nc;
@@ -336,7 +180,7 @@ __global__ void eval_tiles_kernel(DevTree t, const Tile *__restrict__ tiles, VpD
         Acc3 u;
         long long pairs = 0;
         eval_point(t, tl.leaf, qx, qy, -1, -1, P1, M, L, sbar, mbar, 1, 1, u, pairs);
-        size_t o = 3 * ((size_t)r * vp.width + c);
+        size_t o = 3 * ((size_t)vp.offset + (size_t)r * vp.width + c);
         for (int ch = 0; ch < 3; ++ch) {
             if (rgb) {
                 if (rgb_dtype == DC_F64) static_cast<double *>(rgb)[o + ch] = u.v[ch];
@@ -391,6 +235,24 @@ void build_tables(int p, std::vector<cd> &m2m, std::vector<cd> &l2l, std::vector
         }
 }
 
+// The 7 base M2L matrices (offsets (2,0) (2,1) (2,2) (3,0) (3,1) (3,2) (3,3)),
+// transposed: base[b][k][l] = T_lk(B_b).
+void build_base_tables(int p, std::vector<cd> &base) {
+    const int P1 = p + 1;
+    const int bases[7][2] = {{2, 0}, {2, 1}, {2, 2}, {3, 0}, {3, 1}, {3, 2}, {3, 3}};
+    base.assign(7 * P1 * P1, cd(0));
+    for (int b = 0; b < 7; ++b) {
+        cd D(bases[b][0], bases[b][1]), iD = 1.0 / D;
+        for (int l = 0; l < P1; ++l)
+            for (int k = 0; k < P1; ++k) {
+                cd v;
+                if (l + k == 0) v = -std::log(D);
+                else v = ((l & 1) ? -1.0 : 1.0) * binom(l + k, k) / double(l + k) * std::pow(iD, l + k);
+                base[(size_t)b * P1 * P1 + k * P1 + l] = v;
+            }
+    }
+}
+
 template <typename T>
 cudaError_t upload(DevBuf<T> &buf, const std::vector<T> &v, cudaStream_t st) {
     cudaError_t e = buf.alloc(std::max<size_t>(v.size(), 1));
@@ -432,28 +294,106 @@ DevTree Fmm::Impl::dt() const {
     return t;
 }
 
+passes::TreeView<double> Fmm::Impl::view64() const {
+    passes::TreeView<double> v;
+    v.iw = iw64.ptr;
+    v.logw = logw64.ptr;
+    v.parent = parent.ptr;
+    v.child0 = child0.ptr;
+    v.quad = quad.ptr;
+    v.pstart = pstart.ptr;
+    v.pcount = pcount.ptr;
+    v.pw = pw.ptr;
+    v.plen = plen64.ptr;
+    v.pseg = pseg.ptr;
+    v.v_ptr = v_ptr.ptr;
+    v.v_idx = v_idx.ptr;
+    v.v_code = v_code.ptr;
+    v.x_ptr = x_ptr.ptr;
+    v.x_idx = x_idx.ptr;
+    v.x_off = nullptr;
+    return v;
+}
+
 // Up and down passes for segment densities (sbar / mbar), FP64.
 cudaError_t Fmm::Impl::passes(const double *sb, const double *mb, int use_s, int use_m,
-                              cudaStream_t st) {
+                              cudaStream_t st, const Schedule &sc) {
     const int nC = tree.n_cells();
     size_t ebytes = (size_t)nC * 3 * P1 * sizeof(double2);
     cudaError_t e;
     if ((e = cudaMemsetAsync(M.ptr, 0, ebytes, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(L.ptr, 0, ebytes, st)) != cudaSuccess) return e;
-    DevTree t = dt();
-    int th = ((P1 + 31) / 32) * 32;
-    if (n_p2m > 0)
-        p2m_kernel<<<n_p2m, th, 0, st>>>(t, p2m_leaves.ptr, sb, mb, use_s, use_m, P1, M.ptr); note_launch();
+    if ((e = cudaMemsetAsync(Lm2l.ptr, 0, ebytes, st)) != cudaSuccess) return e;
+    passes::TreeView<double> tv = view64();
+    passes::PiecesF64 ps{pc.ptr, cc.ptr};
+    int th = P1 <= 32 ? 32 : 64;
+    if (n_p2m > 0) {
+        passes::p2m_kernel<double, passes::PiecesF64><<<n_p2m, passes::kChunk, passes::p2m_smem<double>(P1), st>>>(
+            tv, ps, p2m_leaves.ptr, sb, mb, use_s, use_m, P1, M.ptr);
+        note_launch();
+    }
     for (int l = tree.depth - 1; l >= 2; --l) {
-        int lo = tree.level_start[l], hi = tree.level_start[l + 1];
-        if (hi > lo) m2m_kernel<<<hi - lo, th, 0, st>>>(t, lo, P1, m2m.ptr, M.ptr); note_launch();
+        int lo = m2m_ptr[l], hi = m2m_ptr[l + 1];
+        if (hi > lo) {
+            passes::m2m_kernel<double><<<hi - lo, th, 0, st>>>(tv, m2m_cells.ptr + lo, P1, m2m.ptr, M.ptr);
+            note_launch();
+        }
+    }
+    if (sc.n_m2l > 0) {
+        int grid = std::min((sc.n_m2l + passes::kM2LSlots - 1) / passes::kM2LSlots, 4 * n_sms);
+        passes::m2l_kernel<double><<<grid, 32 * passes::kM2LSlots, passes::m2l_smem<double>(P1), st>>>(
+            tv, sc.m2l.ptr, sc.n_m2l, P1, base64.ptr, M.ptr, Lm2l.ptr);
+        note_launch();
+    }
+    if (sc.n_p2l > 0) {
+        passes::p2l_kernel<double, passes::PiecesF64><<<sc.n_p2l, passes::kChunk, passes::p2l_smem<double>(P1), st>>>(
+            tv, ps, sc.p2l.ptr, sb, mb, use_s, use_m, P1, Lm2l.ptr);
+        note_launch();
     }
     for (int l = 2; l <= tree.depth; ++l) {
-        int lo = tree.level_start[l], hi = tree.level_start[l + 1];
-        if (hi > lo)
-            down_kernel<<<hi - lo, th, 0, st>>>(t, lo, l, P1, l2l.ptr, m2l.ptr, M.ptr, sb, mb,
-                                                 use_s, use_m, L.ptr); note_launch();
+        int lo = sc.l2l_ptr[l], hi = sc.l2l_ptr[l + 1];
+        if (hi > lo) {
+            passes::l2l_kernel<double><<<(hi - lo + 3) / 4, 128, 0, st>>>(
+                tv, sc.l2l.ptr + lo, hi - lo, l, P1, l2l.ptr, Lm2l.ptr, L.ptr);
+            note_launch();
+        }
     }
+    return cudaGetLastError();
+}
+
+cudaError_t Fmm::Impl::eval_list64(const int4 *items, int n_items, const double *q64,
+                                   const int *own1, const int *own2, const int *perm,
+                                   const double *sb, const double *mb, int use_s, int use_m,
+                                   double *out, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    evalnodes::NodeArgs<double> a;
+    a.u_ptr = u_ptr.ptr;
+    a.u_idx = u_idx.ptr;
+    a.w_ptr = w_ptr.ptr;
+    a.w_idx = w_idx.ptr;
+    a.pstart = pstart.ptr;
+    a.pcount = pcount.ptr;
+    a.pseg = pseg.ptr;
+    a.pc64 = pc.ptr;
+    a.cc64 = cc.ptr;
+    a.pw = pw.ptr;
+    a.iw = iw64.ptr;
+    a.logw = logw64.ptr;
+    a.items = items;
+    a.q64 = q64;
+    a.own1 = own1;
+    a.own2 = own2;
+    a.perm = perm;
+    a.P1 = P1;
+    a.M = M.ptr;
+    a.L = L.ptr;
+    a.sb = sb;
+    a.mb = mb;
+    a.use_s = use_s;
+    a.use_m = use_m;
+    a.out = out;
+    evalnodes::eval_nodes_kernel<double><<<n_items, 32 * evalnodes::kWarps, 0, st>>>(a);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -461,12 +401,9 @@ cudaError_t Fmm::Impl::apply_nodes(const double *x, double *y, bool single, cuda
     cudaError_t e = launch_interp(*D, x, single ? sbar.ptr : mbar.ptr, st);
     if (e != cudaSuccess) return e;
     int us = single ? 1 : 0, um = single ? 0 : 1;
-    if ((e = passes(sbar.ptr, mbar.ptr, us, um, st)) != cudaSuccess) return e;
-    if (n_nt_leaves > 0)
-        eval_targets_kernel<<<n_nt_leaves, 64, 0, st>>>(
-            dt(), nt_leaves.ptr, nt_start.ptr, nt_count.ptr, nt_xy.ptr, nt_own1.ptr, nt_own2.ptr,
-            nt_perm.ptr, P1, M.ptr, L.ptr, sbar.ptr, mbar.ptr, us, um, y); note_launch();
-    return cudaGetLastError();
+    if ((e = passes(sbar.ptr, mbar.ptr, us, um, st, sched_nodes)) != cudaSuccess) return e;
+    return eval_list64(nt_items4.ptr, n_nt_items4, nt_xy.ptr, nt_own1.ptr, nt_own2.ptr, nt_perm.ptr,
+                       sbar.ptr, mbar.ptr, us, um, y, st);
 }
 
 Fmm::Fmm() : impl_(new Impl()) {}
@@ -486,29 +423,80 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     I.fp32 = (opt.form == DC_FORM_FMM32);
     if (!build_quadtree(G.seg_xy, opt.domain, opt.leaf_size, opt.max_depth, I.tree, err))
         return DC_ERR_GEOMETRY;
-    const Tree &T = I.tree;
+    if (I.P1 > 32) {
+        err = "FMM forms support expansion orders p <= 31";
+        return DC_ERR_UNSUPPORTED;
+    }
+    Tree &T = I.tree;
     const int nC = T.n_cells();
-    std::vector<double> cc(2 * nC), cw(nC);
+    // pieces below each cell; list entries whose source holds none are
+    // dropped (their expansions vanish)
+    std::vector<int> sub_pieces(nC, 0);
+    for (int c = nC - 1; c >= 0; --c) {
+        if (T.is_leaf(c)) sub_pieces[c] = T.piece_count[c];
+        else
+            for (int q = 0; q < 4; ++q) sub_pieces[c] += sub_pieces[T.child0[c] + q];
+    }
+    auto prune = [&](std::vector<int> &ptr, std::vector<int> &idx) {
+        std::vector<int> np(ptr.size(), 0), ni;
+        ni.reserve(idx.size());
+        for (int c = 0; c + 1 < (int)ptr.size(); ++c) {
+            for (int e = ptr[c]; e < ptr[c + 1]; ++e)
+                if (sub_pieces[idx[e]] > 0) ni.push_back(idx[e]);
+            np[c + 1] = int(ni.size());
+        }
+        ptr.swap(np);
+        idx.swap(ni);
+    };
+    prune(T.u_ptr, T.u_idx);
+    prune(T.v_ptr, T.v_idx);
+    prune(T.w_ptr, T.w_idx);
+    prune(T.x_ptr, T.x_idx);
+    std::vector<double> cc(2 * nC), cw(nC), iw64(nC), logw64(nC);
     std::vector<int> quad(nC, 0);
     for (int c = 0; c < nC; ++c) {
         cc[2 * c] = T.cx(c);
         cc[2 * c + 1] = T.cy(c);
         cw[c] = T.width(c);
+        iw64[c] = 1.0 / cw[c];
+        logw64[c] = std::log(cw[c]);
         if (T.parent[c] >= 0) quad[c] = c - T.child0[T.parent[c]];
     }
-    std::vector<double> pw(T.pc_seg.size());
-    for (size_t i = 0; i < pw.size(); ++i) pw[i] = G.seg_w[T.pc_seg[i]];
-    std::vector<int> voff(T.v_idx.size());
+    std::vector<double> pw(T.pc_seg.size()), plen64(T.pc_seg.size());
+    for (size_t i = 0; i < pw.size(); ++i) {
+        pw[i] = G.seg_w[T.pc_seg[i]];
+        const double *q = &T.pc_xy[4 * i];
+        plen64[i] = std::hypot(q[2] - q[0], q[3] - q[1]);
+    }
+    // list-2 entries: M2L symmetry code (base matrix, rotation, conjugation)
+    const int bases[7][2] = {{2, 0}, {2, 1}, {2, 2}, {3, 0}, {3, 1}, {3, 2}, {3, 3}};
+    auto sym_code = [&](int dx, int dy) {
+        for (int b = 0; b < 7; ++b)
+            for (int cj = 0; cj < 2; ++cj)
+                for (int r = 0; r < 4; ++r) {
+                    int x = bases[b][0], y = cj ? -bases[b][1] : bases[b][1];
+                    for (int k = 0; k < r; ++k) {   // times i
+                        int t = x;
+                        x = -y;
+                        y = t;
+                    }
+                    if (x == dx && y == dy) return b | (r << 3) | (cj << 5);
+                }
+        return -1;
+    };
+    std::vector<int> voff(T.v_idx.size()), vcode(T.v_idx.size());
     long long m2l_cnt = 0;
     for (int c = 0; c < nC; ++c)
         for (int e = T.v_ptr[c]; e < T.v_ptr[c + 1]; ++e) {
             int s = T.v_idx[e];
             int dx = int(T.ix[c] - T.ix[s]), dy = int(T.iy[c] - T.iy[s]);
-            if (std::abs(dx) > 3 || std::abs(dy) > 3 || std::max(std::abs(dx), std::abs(dy)) < 2) {
+            int code = sym_code(dx, dy);
+            if (std::abs(dx) > 3 || std::abs(dy) > 3 || code < 0) {
                 err = "internal error: interaction-list offset out of range";
                 return DC_ERR_GEOMETRY;
             }
             voff[e] = offset_code(dx, dy);
+            vcode[e] = code;
             ++m2l_cnt;
         }
     I.m2l_cnt = m2l_cnt;
@@ -527,6 +515,46 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         }
         leaf_of[i] = lf;
         cnt[lf]++;
+    }
+    std::vector<int> sub_nodes(cnt);
+    for (int c = nC - 1; c >= 0; --c)
+        if (!T.is_leaf(c))
+            for (int q = 0; q < 4; ++q) sub_nodes[c] += sub_nodes[T.child0[c] + q];
+    // pass schedules
+    std::vector<int> m2m_cells;
+    I.m2m_ptr.assign(T.depth + 2, 0);
+    for (int l = 0; l <= T.depth; ++l) {
+        I.m2m_ptr[l] = int(m2m_cells.size());
+        if (l >= 2)
+            for (int c = T.level_start[l]; c < T.level_start[l + 1]; ++c)
+                if (!T.is_leaf(c) && sub_pieces[c] > 0) m2m_cells.push_back(c);
+    }
+    I.m2m_ptr[T.depth + 1] = int(m2m_cells.size());
+    auto make_sched = [&](Schedule &sc, bool nodes_only, std::vector<int> &m2l_c,
+                          std::vector<int> &p2l_c, std::vector<int> &l2l_c) {
+        sc.l2l_ptr.assign(T.depth + 2, 0);
+        for (int l = 0; l <= T.depth; ++l) {
+            sc.l2l_ptr[l] = int(l2l_c.size());
+            if (l < 2) continue;
+            for (int c = T.level_start[l]; c < T.level_start[l + 1]; ++c) {
+                if (nodes_only && sub_nodes[c] == 0) continue;
+                l2l_c.push_back(c);
+                if (T.v_ptr[c + 1] > T.v_ptr[c]) m2l_c.push_back(c);
+                if (T.x_ptr[c + 1] > T.x_ptr[c]) p2l_c.push_back(c);
+            }
+        }
+        sc.l2l_ptr[T.depth + 1] = int(l2l_c.size());
+        sc.n_m2l = int(m2l_c.size());
+        sc.n_p2l = int(p2l_c.size());
+    };
+    std::vector<int> am2l, ap2l, al2l, nm2l, np2l, nl2l;
+    make_sched(I.sched_all, false, am2l, ap2l, al2l);
+    make_sched(I.sched_nodes, true, nm2l, np2l, nl2l);
+    {
+        cudaDeviceProp prop;
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
+            I.n_sms = prop.multiProcessorCount;
     }
     std::vector<int> start(nC, 0), perm(N), own1(N), own2(N), leaves;
     std::vector<double> txy(2 * N);
@@ -549,8 +577,24 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     }
     I.p2p_nodes = p2p;
     I.n_nt_leaves = int(leaves.size());
-    std::vector<cd> m2m, l2l, m2l;
+    std::vector<int4> items4;
+    for (int c : leaves)
+        for (int j = 0; j < cnt[c]; j += evalnodes::kNodeItem)
+            items4.push_back(make_int4(c, start[c] + j, std::min(evalnodes::kNodeItem, cnt[c] - j), 0));
+    I.n_nt_items4 = int(items4.size());
+    std::vector<cd> m2m, l2l, m2l, base;
     build_tables(I.p, m2m, l2l, m2l);
+    build_base_tables(I.p, base);
+    const int p_inner = std::min(I.p, 12);
+    I.P1i = p_inner + 1;
+    std::vector<cd> m2mi, l2li, m2li, basei;
+    build_tables(p_inner, m2mi, l2li, m2li);
+    build_base_tables(p_inner, basei);
+    auto to_f2 = [](const std::vector<cd> &v) {
+        std::vector<float2> f(v.size());
+        for (size_t i = 0; i < v.size(); ++i) f[i] = make_float2((float)v[i].real(), (float)v[i].imag());
+        return f;
+    };
     cudaError_t e;
 #define UP(buf, vec)                                                   \
     if ((e = upload(buf, vec, st)) != cudaSuccess) {                   \
@@ -584,10 +628,30 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     UP(I.nt_own1, own1);
     UP(I.nt_own2, own2);
     UP(I.nt_xy, txy);
+    UP(I.nt_items4, items4);
+    UP(I.iw64, iw64);
+    UP(I.logw64, logw64);
+    UP(I.plen64, plen64);
+    UP(I.v_code, vcode);
+    UP(I.m2m_cells, m2m_cells);
+    UP(I.sched_all.m2l, am2l);
+    UP(I.sched_all.p2l, ap2l);
+    UP(I.sched_all.l2l, al2l);
+    UP(I.sched_nodes.m2l, nm2l);
+    UP(I.sched_nodes.p2l, np2l);
+    UP(I.sched_nodes.l2l, nl2l);
 #undef UP
     if ((e = upload_cd(I.m2m, m2m, st)) != cudaSuccess || (e = upload_cd(I.l2l, l2l, st)) != cudaSuccess ||
         (e = upload_cd(I.m2l, m2l, st)) != cudaSuccess || (e = I.M.alloc((size_t)nC * 3 * I.P1)) != cudaSuccess ||
         (e = I.L.alloc((size_t)nC * 3 * I.P1)) != cudaSuccess ||
+        (e = upload_cd(I.base64, base, st)) != cudaSuccess ||
+        (e = upload(I.m2m32i, to_f2(m2mi), st)) != cudaSuccess ||
+        (e = upload(I.l2l32i, to_f2(l2li), st)) != cudaSuccess ||
+        (e = upload(I.base32i, to_f2(basei), st)) != cudaSuccess ||
+        (e = I.M32i.alloc((size_t)nC * 3 * I.P1i)) != cudaSuccess ||
+        (e = I.L32i.alloc((size_t)nC * 3 * I.P1i)) != cudaSuccess ||
+        (e = I.Lm2l32i.alloc((size_t)nC * 3 * I.P1i)) != cudaSuccess ||
+        (e = I.Lm2l.alloc((size_t)nC * 3 * I.P1)) != cudaSuccess ||
         (e = I.sbar.alloc((size_t)3 * D.S)) != cudaSuccess ||
         (e = I.mbar.alloc((size_t)3 * D.S)) != cudaSuccess) {
         err = std::string("fmm allocation: ") + cudaGetErrorString(e);
@@ -621,6 +685,12 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
                 return DC_ERR_GEOMETRY;
             }
     }
+    cudaFuncSetAttribute(passes::m2l_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)passes::m2l_smem<double>(I.P1));
+    cudaFuncSetAttribute(passes::p2l_kernel<double, passes::PiecesF64>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passes::p2l_smem<double>(I.P1));
+    cudaFuncSetAttribute(passes::p2m_kernel<double, passes::PiecesF64>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passes::p2m_smem<double>(I.P1));
     if (I.fp32) return I.build32(G, st, err);
     return DC_OK;
 }
@@ -631,12 +701,8 @@ cudaError_t Fmm::prepare_eval(const double *sbar, const double *mbar, cudaStream
     I.render_m2p = 0;
     I.render_flops = 0.0;
     I.render_eval_ms = 0.0;
-    if (I.fp32) {
-        cudaError_t e = I.to_f32_density(sbar, mbar, st);
-        if (e != cudaSuccess) return e;
-        return I.passes32(I.sbar32.ptr, I.mbar32.ptr, 1, 1, st);
-    }
-    return I.passes(sbar, mbar, 1, 1, st);
+    if (I.fp32) return I.prepare_render32(sbar, mbar, st);
+    return I.passes(sbar, mbar, 1, 1, st, I.sched_all);
 }
 
 cudaError_t Fmm::apply_single_layer(const double *x, double *y, cudaStream_t st) {
@@ -653,10 +719,10 @@ struct PrecOp : Operator {
     Fmm::Impl *f;
     bool fp32 = false;
     cudaError_t apply(const double *v, double *y, cudaStream_t st) override {
+        if (fp32) return f->graph_matvec32(v, y, st);
         cudaError_t e = launch_block_apply(f->pinv.ptr, f->D->n_panels, f->D->g, v, f->ir_t.ptr, st);
         if (e != cudaSuccess) return e;
-        return fp32 ? f->apply_nodes32(f->ir_t.ptr, y, true, st)
-                    : f->apply_nodes(f->ir_t.ptr, y, true, st);
+        return f->apply_nodes(f->ir_t.ptr, y, true, st);
     }
 };
 }  // namespace
@@ -738,22 +804,27 @@ void pixel_range(double o, double d, int n, double a, double b, int &lo, int &hi
 }
 }  // namespace
 
-dc_status Fmm::render_grid(const VpDev &vp, const double *sbar, const double *mbar, void *rgb,
-                           int rgb_dtype, unsigned char *rgb8, cudaStream_t st, std::string &err) {
+dc_status Fmm::render_viewports(const VpDev *vpl, int n_vp, const double *sbar, const double *mbar,
+                                void *rgb, int rgb_dtype, unsigned char *rgb8, cudaStream_t st,
+                                std::string &err) {
     Impl &I = *impl_;
     const Tree &T = I.tree;
-    // every pixel centre must lie inside the root
-    double xa = vp.x0 + 0.5 * vp.dx, xb = vp.x0 + (vp.width - 0.5) * vp.dx;
-    double ya = vp.y0 + 0.5 * vp.dy, yb = vp.y0 + (vp.height - 0.5) * vp.dy;
-    if (!(vp.dx > 0 && vp.dy > 0)) {
-        err = "render_viewport: need x1 > x0 and y1 > y0";
-        return DC_ERR_ARG;
+    for (int v = 0; v < n_vp; ++v) {
+        const VpDev &vp = vpl[v];
+        if (vp.width == 0 || vp.height == 0) continue;
+        // every pixel centre must lie inside the root
+        double xa = vp.x0 + 0.5 * vp.dx, xb = vp.x0 + (vp.width - 0.5) * vp.dx;
+        double ya = vp.y0 + 0.5 * vp.dy, yb = vp.y0 + (vp.height - 0.5) * vp.dy;
+        if (!(vp.dx > 0 && vp.dy > 0)) {
+            err = "render_viewport: need x1 > x0 and y1 > y0";
+            return DC_ERR_ARG;
+        }
+        if (!(xa >= T.x0 && xb < T.x0 + T.w0 && ya >= T.y0 && yb < T.y0 + T.w0)) {
+            err = "render_viewport: pixel centres outside the quadtree root; widen options.domain";
+            return DC_ERR_ARG;
+        }
     }
-    if (!(xa >= T.x0 && xb < T.x0 + T.w0 && ya >= T.y0 && yb < T.y0 + T.w0)) {
-        err = "render_viewport: pixel centres outside the quadtree root; widen options.domain";
-        return DC_ERR_ARG;
-    }
-    cudaError_t e = cudaStreamSynchronize(st);   // the host tile list is rebuilt per call
+    cudaError_t e = cudaStreamSynchronize(st);   // tile and viewport buffers are reused
     if (e != cudaSuccess) {
         err = cudaGetErrorString(e);
         return DC_ERR_CUDA;
@@ -761,27 +832,33 @@ dc_status Fmm::render_grid(const VpDev &vp, const double *sbar, const double *mb
     std::vector<Tile> tiles;
     const int TS = 16;   // 16 x 16 pixels per block
     long long pairs = 0;
-    for (int c = 0; c < T.n_cells(); ++c) {
-        if (!T.is_leaf(c)) continue;
-        double w = T.width(c);
-        double bx0 = T.x0 + double(T.ix[c]) * w, by0 = T.y0 + double(T.iy[c]) * w;
-        int c0, c1, r0, r1;
-        pixel_range(vp.x0, vp.dx, vp.width, bx0, bx0 + w, c0, c1);
-        pixel_range(vp.y0, vp.dy, vp.height, by0, by0 + w, r0, r1);
-        if (c1 <= c0 || r1 <= r0) continue;
-        long long up = 0, npx = (long long)(c1 - c0) * (r1 - r0);
-        for (int e2 = T.u_ptr[c]; e2 < T.u_ptr[c + 1]; ++e2) up += T.piece_count[T.u_idx[e2]];
-        pairs += up * npx;
-        long long wn = T.w_ptr[c + 1] - T.w_ptr[c];
-        I.render_m2p += wn * npx;
-        I.render_flops += 45.0 * double(up * npx) + 24.0 * I.P1 * double((1 + wn) * npx);
-        for (int r = r0; r < r1; r += TS)
-            for (int cc = c0; cc < c1; cc += TS)
-                tiles.push_back({c, r, cc, std::min(TS, r1 - r), std::min(TS, c1 - cc)});
+    for (int v = 0; v < n_vp; ++v) {
+        const VpDev &vp = vpl[v];
+        if (vp.width == 0 || vp.height == 0) continue;
+        for (int c = 0; c < T.n_cells(); ++c) {
+            if (!T.is_leaf(c)) continue;
+            double w = T.width(c);
+            double bx0 = T.x0 + double(T.ix[c]) * w, by0 = T.y0 + double(T.iy[c]) * w;
+            int c0, c1, r0, r1;
+            pixel_range(vp.x0, vp.dx, vp.width, bx0, bx0 + w, c0, c1);
+            if (c1 <= c0) continue;
+            pixel_range(vp.y0, vp.dy, vp.height, by0, by0 + w, r0, r1);
+            if (r1 <= r0) continue;
+            long long up = 0, npx = (long long)(c1 - c0) * (r1 - r0);
+            for (int e2 = T.u_ptr[c]; e2 < T.u_ptr[c + 1]; ++e2) up += T.piece_count[T.u_idx[e2]];
+            pairs += up * npx;
+            long long wn = T.w_ptr[c + 1] - T.w_ptr[c];
+            I.render_m2p += wn * npx;
+            I.render_flops += 45.0 * double(up * npx) + 24.0 * I.P1 * double((1 + wn) * npx);
+            for (int r = r0; r < r1; r += TS)
+                for (int cc = c0; cc < c1; cc += TS)
+                    tiles.push_back({c, r, cc, std::min(TS, r1 - r), std::min(TS, c1 - cc), v});
+        }
     }
     I.render_pairs += pairs;
     if (tiles.empty()) return DC_OK;
-    if ((e = upload(I.tiles, tiles, st)) != cudaSuccess) {
+    std::vector<VpDev> vv(vpl, vpl + n_vp);
+    if ((e = upload(I.tiles, tiles, st)) != cudaSuccess || (e = upload(I.vps, vv, st)) != cudaSuccess) {
         err = cudaGetErrorString(e);
         return DC_ERR_CUDA;
     }
@@ -791,11 +868,14 @@ dc_status Fmm::render_grid(const VpDev &vp, const double *sbar, const double *mb
         cudaEventRecord(I.ev0, st);
     }
     if (I.fp32)
-        e = I.render_tiles32(vp, int(tiles.size()), rgb, rgb_dtype, rgb8, st);
-    else
-        eval_tiles_kernel<<<int(tiles.size()), 128, 0, st>>>(I.dt(), I.tiles.ptr, vp, I.P1, I.M.ptr,
-                                                              I.L.ptr, sbar, mbar, rgb, rgb_dtype,
-                                                              rgb8); note_launch();
+        e = I.render_tiles32(int(tiles.size()), rgb, rgb_dtype, rgb8, sbar, mbar, st);
+    else {
+        eval_tiles_kernel<<<int(tiles.size()), 128, 0, st>>>(I.dt(), I.tiles.ptr, I.vps.ptr, I.P1,
+                                                              I.M.ptr, I.L.ptr, sbar, mbar, rgb,
+                                                              rgb_dtype, rgb8);
+        note_launch();
+        e = cudaGetLastError();
+    }
     if (I.eval_timing) {
         cudaEventRecord(I.ev1, st);
         cudaEventSynchronize(I.ev1);
@@ -803,7 +883,6 @@ dc_status Fmm::render_grid(const VpDev &vp, const double *sbar, const double *mb
         cudaEventElapsedTime(&ms, I.ev0, I.ev1);
         I.render_eval_ms += ms;
     }
-    e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = cudaGetErrorString(e);
         return DC_ERR_CUDA;
@@ -860,17 +939,24 @@ dc_status Fmm::eval_points(const double *xy, int n, const double *sbar, const do
             double cx = T.cx(c), cy = T.cy(c);
             for (int j = start[c]; j < start[c] + cnt[c]; ++j)
                 q32[j] = make_float2((float)(sxy[2 * j] - cx), (float)(sxy[2 * j + 1] - cy));
-            for (int j = 0; j < cnt[c]; j += 64) items.push_back({c, start[c] + j, 0, std::min(64, cnt[c] - j), 0});
+            for (int j = 0; j < cnt[c]; j += 64) items.push_back({c, start[c] + j, 0, std::min(64, cnt[c] - j), 0, 0});
         }
         if ((e = upload(I.pt_items, items, st)) != cudaSuccess || (e = upload(I.pt_q32, q32, st)) != cudaSuccess ||
-            (e = I.eval_points32(int(items.size()), I.pt_out.ptr, st)) != cudaSuccess) {
+            (e = I.eval_points32(int(items.size()), I.pt_out.ptr, sbar, mbar, st)) != cudaSuccess) {
             err = cudaGetErrorString(e);
             return DC_ERR_CUDA;
         }
     } else {
-        eval_targets_kernel<<<int(leaves.size()), 64, 0, st>>>(
-            I.dt(), I.pt_leaves.ptr, I.pt_start.ptr, I.pt_count.ptr, I.pt_xy.ptr, nullptr, nullptr,
-            I.pt_perm.ptr, I.P1, I.M.ptr, I.L.ptr, sbar, mbar, 1, 1, I.pt_out.ptr); note_launch();
+        std::vector<int4> items4;
+        for (int c : leaves)
+            for (int j = 0; j < cnt[c]; j += evalnodes::kNodeItem)
+                items4.push_back(make_int4(c, start[c] + j, std::min(evalnodes::kNodeItem, cnt[c] - j), 0));
+        if ((e = upload(I.pt_items4, items4, st)) != cudaSuccess ||
+            (e = I.eval_list64(I.pt_items4.ptr, int(items4.size()), I.pt_xy.ptr, nullptr, nullptr,
+                               I.pt_perm.ptr, sbar, mbar, 1, 1, I.pt_out.ptr, st)) != cudaSuccess) {
+            err = cudaGetErrorString(e);
+            return DC_ERR_CUDA;
+        }
     }
     if ((e = launch_write_outputs(I.pt_out.ptr, n, out, out_dtype, nullptr, st)) != cudaSuccess) {
         err = cudaGetErrorString(e);

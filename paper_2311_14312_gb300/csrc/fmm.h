@@ -26,9 +26,12 @@ public:
     // Forms the expansions of segment densities sbar and mbar (Alg. 8 up and
     // down passes); render_grid / eval_points then evaluate them.
     cudaError_t prepare_eval(const double *sbar, const double *mbar, cudaStream_t st);
-    // Single + double layer of segment densities at a viewport's pixels.
-    dc_status render_grid(const VpDev &vp, const double *sbar, const double *mbar, void *rgb,
-                          int rgb_dtype, unsigned char *rgb8, cudaStream_t st, std::string &err);
+    // Single + double layer of segment densities at the pixels of n
+    // viewports in one launch; rgb / rgb8 are the outputs of the whole call
+    // and each viewport writes from its VpDev::offset.
+    dc_status render_viewports(const VpDev *vps, int n, const double *sbar, const double *mbar,
+                               void *rgb, int rgb_dtype, unsigned char *rgb8, cudaStream_t st,
+                               std::string &err);
     dc_status eval_points(const double *xy, int n, const double *sbar, const double *mbar,
                           void *out, int out_dtype, cudaStream_t st, std::string &err);
     void fill_sizes(dc_sizes *out) const;
@@ -37,7 +40,7 @@ public:
     long long last_render_p2p_pairs() const;
     long long last_render_m2p_pairs() const;
     double last_render_eval_flops() const;
-    // When on, render_grid times its evaluation kernel with CUDA events on
+    // When on, render_viewports times its evaluation kernel with CUDA events on
     // the launching stream (synchronising after each launch).
     void set_eval_timing(bool on);
     double last_render_eval_ms() const;

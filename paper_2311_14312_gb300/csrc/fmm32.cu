@@ -17,6 +17,7 @@
 #include <complex>
 #include <vector>
 
+#include "evalnodes.cuh"
 #include "fmm_impl.h"
 #include "segint.cuh"
 
@@ -78,140 +79,52 @@ __global__ void interp32_kernel(const double *__restrict__ lam, const double *__
     sv[3 * (size_t)k + 2] = (float)a2;
 }
 
-// --------------------------------------------------------------- P2M --
-__global__ void p2m32_kernel(DevTree32 t, const int *__restrict__ leaves, const float *__restrict__ sb,
-                             const float *__restrict__ mb, int use_s, int use_m, int P1,
-                             float2 *__restrict__ M) {
-    int cell = leaves[blockIdx.x];
-    int k = threadIdx.x;
-    if (k >= P1) return;
-    float iw = t.iw[cell];
-    float2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
-    int p0 = t.pstart[cell], pn = t.pcount[cell];
-    for (int i = p0; i < p0 + pn; ++i) {
-        float4 P = t.pc[i];
-        float2 a = make_float2(P.x * iw, P.y * iw), b = make_float2(P.z * iw, P.w * iw);
-        float len = t.plen[i], om = t.pw[i] * len;
-        float2 S = make_float2(1.f, 0.f), Sp = make_float2(0.f, 0.f), ap = make_float2(1.f, 0.f);
-        for (int m = 1; m <= k; ++m) {
-            ap = fmul(ap, a);
-            Sp = S;
-            S = fadd(fmul(b, S), ap);
-        }
-        float2 cg = fscale(S, om / (k + 1));
-        float il = iw / len;
-        float2 wr = make_float2((P.z - P.x) * il, (P.w - P.y) * il);
-        float2 t1 = fmul(wr, Sp);
-        float2 cf = make_float2(t1.y * om, -t1.x * om);   // -i (w/r) S_{k-1} om
-        int seg = t.pseg[i];
-        for (int c = 0; c < 3; ++c) {
-            float s = use_s ? sb[3 * (size_t)seg + c] : 0.f;
-            float mu = use_m ? mb[3 * (size_t)seg + c] : 0.f;
-            acc[c].x += s * cg.x + mu * cf.x;
-            acc[c].y += s * cg.y + mu * cf.y;
-        }
-    }
-    for (int c = 0; c < 3; ++c) M[((size_t)cell * 3 + c) * P1 + k] = acc[c];
-}
-
-// --------------------------------------------------------------- M2M --
-__global__ void m2m32_kernel(DevTree32 t, int c_lo, int P1, const float2 *__restrict__ tab,
-                             float2 *__restrict__ M) {
-    int cell = c_lo + blockIdx.x;
-    int k = threadIdx.x;
-    int ch0 = t.child0[cell];
-    if (k >= P1 || ch0 < 0) return;
-    float2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
-    for (int q = 0; q < 4; ++q) {
-        const float2 *T = tab + ((size_t)q * P1 + k) * P1;
-        const float2 *src = M + (size_t)(ch0 + q) * 3 * P1;
-        for (int j = 0; j <= k; ++j) {
-            float2 tq = T[j];
-            for (int c = 0; c < 3; ++c) ffma2(acc[c], tq, src[c * P1 + j]);
-        }
-    }
-    for (int c = 0; c < 3; ++c) M[((size_t)cell * 3 + c) * P1 + k] = acc[c];
-}
-
-// ------------------------------------------------ L2L + M2L + P2L ----
-__global__ void down32_kernel(DevTree32 t, int c_lo, int level, int P1, const float2 *__restrict__ l2l,
-                              const float2 *__restrict__ m2l, const float2 *__restrict__ M,
-                              const float *__restrict__ sb, const float *__restrict__ mb, int use_s,
-                              int use_m, float2 *__restrict__ L) {
-    int cell = c_lo + blockIdx.x;
-    int l = threadIdx.x;
-    if (l >= P1) return;
-    float2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
-    if (level >= 3) {
-        int par = t.parent[cell], q = t.quad[cell];
-        const float2 *T = l2l + ((size_t)q * P1 + l) * P1;
-        const float2 *src = L + (size_t)par * 3 * P1;
-        for (int k = l; k < P1; ++k) {
-            float2 tq = T[k];
-            for (int c = 0; c < 3; ++c) ffma2(acc[c], tq, src[c * P1 + k]);
-        }
-    }
-    float mlogw = -t.logw[cell];
-    for (int e = t.v_ptr[cell]; e < t.v_ptr[cell + 1]; ++e) {
-        int src = t.v_idx[e];
-        const float2 *T = m2l + ((size_t)t.v_off[e] * P1 + l) * P1;
-        const float2 *ms = M + (size_t)src * 3 * P1;
+// ---------------------------------------------- render preparation --
+// Cells whose expansions carry large, cancelling coefficients (next to
+// strongly singular densities) are evaluated in FP64: the FP32 rounding of
+// a coefficient is ~6e-8 of its size.  hL: sum_l |Lt_l| > kBigCoef; hM:
+// 10 |Mt_0| + sum_k |Mt_k| > kBigCoef (max over channels).
+constexpr double kBigCoef = 50.0;
+__global__ void big_coef_kernel(const double2 *__restrict__ L, const double2 *__restrict__ M, int n,
+                                int P1, unsigned char *__restrict__ hL, unsigned char *__restrict__ hM) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    double bl = 0.0, bm = 0.0;
+    for (int ch = 0; ch < 3; ++ch) {
+        const double2 *l = L + ((size_t)c * 3 + ch) * P1, *m = M + ((size_t)c * 3 + ch) * P1;
+        double sl = 0.0, sm = 9.0 * hypot(m[0].x, m[0].y);
         for (int k = 0; k < P1; ++k) {
-            float2 tq = T[k];
-            for (int c = 0; c < 3; ++c) ffma2(acc[c], tq, ms[c * P1 + k]);
+            sl += hypot(l[k].x, l[k].y);
+            sm += hypot(m[k].x, m[k].y);
         }
-        if (l == 0)
-            for (int c = 0; c < 3; ++c) ffma2(acc[c], make_float2(mlogw, 0.f), ms[c * P1]);
+        bl = fmax(bl, sl);
+        bm = fmax(bm, sm);
     }
-    float iw = t.iw[cell], wcell = 1.0f / iw, logw = t.logw[cell];
-    for (int e = t.x_ptr[cell]; e < t.x_ptr[cell + 1]; ++e) {
-        int src = t.x_idx[e];
-        float2 off = t.x_off[e];
-        int p0 = t.pstart[src], pn = t.pcount[src];
-        for (int i = p0; i < p0 + pn; ++i) {
-            float4 P = t.pc[i];
-            float2 a = make_float2((P.x + off.x) * iw, (P.y + off.y) * iw);   // scaled
-            float2 b = make_float2((P.z + off.x) * iw, (P.w + off.y) * iw);
-            float len = t.plen[i], om = t.pw[i];
-            float2 wv = make_float2((P.z - P.x) / len, (P.w - P.y) / len);
-            float2 cg, cf;
-            if (l <= 1) {
-                float2 lba = flog_ratio(a, b);
-                if (l == 0) {
-                    // omega sigma [ l (1 - log a) - conj(w) b log(b/a) ],  a = ah * width
-                    float2 la = make_float2(0.5f * __logf(a.x * a.x + a.y * a.y) + logw, atan2f(a.y, a.x));
-                    float2 wb = fmul(make_float2(wv.x, -wv.y), make_float2(b.x * wcell, b.y * wcell));
-                    float2 t2 = fmul(wb, lba);
-                    cg = make_float2(om * (len * (1.f - la.x) - t2.x), om * (-len * la.y - t2.y));
-                    cf = make_float2(-om * lba.y, om * lba.x);
-                } else {
-                    float2 t2 = fmul(make_float2(wv.x, -wv.y), lba);
-                    cg = fscale(t2, om * wcell);
-                    float2 ab = fmul(finv(a), finv(b));
-                    cf = fscale(fmul(make_float2(-wv.y, wv.x), ab), om * len * iw);
-                }
-            } else {
-                float2 al = finv(a), be = finv(b);
-                float2 T = make_float2(1.f, 0.f), Tp = T, bp = make_float2(1.f, 0.f);
-                for (int m = 1; m <= l - 1; ++m) {
-                    bp = fmul(bp, be);
-                    Tp = T;
-                    T = fadd(fmul(al, T), bp);
-                }
-                float2 ab = fmul(al, be);
-                cg = fscale(fmul(ab, Tp), om * len / (float(l) * (l - 1)));
-                cf = fscale(fmul(fmul(make_float2(-wv.y, wv.x), ab), T), om * len * iw / l);
-            }
-            int seg = t.pseg[i];
-            for (int c = 0; c < 3; ++c) {
-                float s = use_s ? sb[3 * (size_t)seg + c] : 0.f;
-                float mu = use_m ? mb[3 * (size_t)seg + c] : 0.f;
-                acc[c].x += s * cg.x + mu * cf.x;
-                acc[c].y += s * cg.y + mu * cf.y;
-            }
-        }
+    hL[c] = bl > kBigCoef;
+    hM[c] = bm > kBigCoef;
+}
+
+template <typename From, typename To>
+__global__ void narrow_kernel(const From *__restrict__ a, To *__restrict__ b, size_t n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        b[i].x = (float)a[i].x;
+        b[i].y = (float)a[i].y;
     }
-    for (int c = 0; c < 3; ++c) L[((size_t)cell * 3 + c) * P1 + l] = acc[c];
+}
+
+// heavy[i] = 1 when max_c |sigma_bar| w len or |mu_bar| w len of piece i
+// exceeds kHeavy: its near-field terms are then summed in FP64.
+constexpr double kHeavy = 1.0;
+__global__ void heavy_kernel(const double *__restrict__ sb, const double *__restrict__ mb,
+                             const int *__restrict__ pseg, const double *__restrict__ pw,
+                             const double *__restrict__ plen, unsigned char *__restrict__ heavy, int np) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    int s = pseg[i];
+    double m = 0.0;
+    for (int c = 0; c < 3; ++c) m = fmax(m, fmax(fabs(sb[3 * (size_t)s + c]), fabs(mb[3 * (size_t)s + c])));
+    heavy[i] = (m * pw[i] * plen[i] > kHeavy) ? 1 : 0;
 }
 
 // -------------------------------------------------------------- eval --
@@ -227,10 +140,14 @@ struct EvalArgs32 {
     const float *sb, *mb;
     int use_s, use_m;
     // pixel mode
-    VpDev vp;
+    const VpDev *vps;
     void *rgb;
     int rgb_dtype;
     unsigned char *rgb8;
+    // FP64 path for heavy pieces and big-coefficient cells (pixel mode)
+    const double *sb64, *mb64;
+    const unsigned char *heavy, *hL, *hM;
+    const double2 *M64, *L64;
     // list mode
     const float2 *q32;
     const double *q64;
@@ -250,7 +167,7 @@ __device__ __forceinline__ void split2(double v, float &hi, float &lo) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kEvThreads) eval32_kernel(EvalArgs32 a) {
+__global__ void __launch_bounds__(kEvThreads, 2) eval32_kernel(EvalArgs32 a) {
     // staged pieces of one list-1 leaf, in the target leaf's frame, each
     // coordinate as a (hi, lo) float pair so differences keep full accuracy
     __shared__ float sx1h[kStage], sx1l[kStage], sy1h[kStage], sy1l[kStage];
@@ -258,21 +175,25 @@ __global__ void __launch_bounds__(kEvThreads) eval32_kernel(EvalArgs32 a) {
     __shared__ float slen[kStage];
     __shared__ float ssg[3][kStage], smg[3][kStage];
     __shared__ int sseg[kStage], sidx[kStage];
+    __shared__ unsigned char shv[kStage];
     const DevTree32 &t = a.t;
     Tile tl = a.items[blockIdx.x];
     const int leaf = tl.leaf;
+    double h0 = 0.0, h1 = 0.0, h2 = 0.0;   // FP64 sums of heavy pieces
     const double cxB = a.t64.cc[2 * leaf], cyB = a.t64.cc[2 * leaf + 1];
     const int j = threadIdx.x;
     bool act;
     double qx64 = 0.0, qy64 = 0.0;
     int own1 = -1, own2 = -1, r = 0, c = 0, ti = 0;
+    VpDev vp;
     if (MODE == 0) {
+        vp = a.vps[tl.vp];
         act = j < tl.nr * tl.nc;
         if (act) {
             r = tl.r0 + j / tl.nc;
             c = tl.c0 + j % tl.nc;
-            qx64 = a.vp.x0 + (c + 0.5) * a.vp.dx;
-            qy64 = a.vp.y0 + (r + 0.5) * a.vp.dy;
+            qx64 = vp.x0 + (c + 0.5) * vp.dx;
+            qy64 = vp.y0 + (r + 0.5) * vp.dy;
         }
     } else {
         act = j < tl.nr;
@@ -294,19 +215,57 @@ __global__ void __launch_bounds__(kEvThreads) eval32_kernel(EvalArgs32 a) {
     const int P1 = a.P1;
     if (act) {
         // L2P (Eq. 64)
-        float iw = t.iw[leaf];
-        float2 z = make_float2(q.x * iw, q.y * iw);
-        const float2 *Lc = a.L + (size_t)leaf * 3 * P1;
-        float2 s0 = Lc[P1 - 1], s1 = Lc[2 * P1 - 1], s2 = Lc[3 * P1 - 1];
-        for (int k = P1 - 2; k >= 0; --k) {
-            s0 = fadd(fmul(s0, z), Lc[k]);
-            s1 = fadd(fmul(s1, z), Lc[P1 + k]);
-            s2 = fadd(fmul(s2, z), Lc[2 * P1 + k]);
+        float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+        if (a.hL && a.hL[leaf]) {
+            const double iw = 1.0 / a.t64.cw[leaf];
+            const double zx = (qx64 - cxB) * iw, zy = (qy64 - cyB) * iw;
+            const double2 *Lc = a.L64 + (size_t)leaf * 3 * P1;
+            for (int ch = 0; ch < 3; ++ch) {
+                double sx = Lc[ch * P1 + P1 - 1].x, sy = Lc[ch * P1 + P1 - 1].y;
+                for (int k = P1 - 2; k >= 0; --k) {
+                    double nx = sx * zx - sy * zy + Lc[ch * P1 + k].x;
+                    sy = sx * zy + sy * zx + Lc[ch * P1 + k].y;
+                    sx = nx;
+                }
+                (ch == 0 ? h0 : ch == 1 ? h1 : h2) += sx * kInv2Pi;
+            }
+        } else {
+            float iw = t.iw[leaf];
+            float2 z = make_float2(q.x * iw, q.y * iw);
+            const float2 *Lc = a.L + (size_t)leaf * 3 * P1;
+            float2 s0 = Lc[P1 - 1], s1 = Lc[2 * P1 - 1], s2 = Lc[3 * P1 - 1];
+            for (int k = P1 - 2; k >= 0; --k) {
+                s0 = fadd(fmul(s0, z), Lc[k]);
+                s1 = fadd(fmul(s1, z), Lc[P1 + k]);
+                s2 = fadd(fmul(s2, z), Lc[2 * P1 + k]);
+            }
+            e0 = s0.x;
+            e1 = s1.x;
+            e2 = s2.x;
         }
-        float e0 = s0.x, e1 = s1.x, e2 = s2.x;
         // M2P over list 3 (Eq. 61)
         for (int e = t.w_ptr[leaf]; e < t.w_ptr[leaf + 1]; ++e) {
             int src = t.w_idx[e];
+            if (a.hM && a.hM[src]) {
+                const double iws = 1.0 / a.t64.cw[src];
+                const double zx = (qx64 - a.t64.cc[2 * src]) * iws, zy = (qy64 - a.t64.cc[2 * src + 1]) * iws;
+                const double d = 1.0 / (zx * zx + zy * zy);
+                const double izx = zx * d, izy = -zy * d;
+                const double lz = 0.5 * log(zx * zx + zy * zy) + log(a.t64.cw[src]);
+                const double2 *Ms = a.M64 + (size_t)src * 3 * P1;
+                for (int ch = 0; ch < 3; ++ch) {
+                    const double2 *m = Ms + ch * P1;
+                    double sx = m[P1 - 1].x / (P1 - 1), sy = m[P1 - 1].y / (P1 - 1);
+                    for (int k = P1 - 2; k >= 1; --k) {
+                        double nx = sx * izx - sy * izy + m[k].x / k;
+                        sy = sx * izy + sy * izx + m[k].y / k;
+                        sx = nx;
+                    }
+                    double rx = sx * izx - sy * izy;
+                    (ch == 0 ? h0 : ch == 1 ? h1 : h2) += (rx - lz * m[0].x) * kInv2Pi;
+                }
+                continue;
+            }
             float2 off = t.w_off[e];
             float iws = t.iw[src];
             float2 zz = make_float2((q.x - off.x) * iws, (q.y - off.y) * iws);
@@ -355,10 +314,24 @@ __global__ void __launch_bounds__(kEvThreads) eval32_kernel(EvalArgs32 a) {
                 }
                 sseg[s] = seg;
                 sidx[s] = i;
+                shv[s] = a.heavy ? a.heavy[i] : 0;
             }
             __syncthreads();
             if (act) {
                 for (int s = 0; s < cnt; ++s) {
+                    if (shv[s]) {
+                        // large density: the whole term in FP64 (App. D forms)
+                        const double *P = a.t64.pc + 4 * (size_t)sidx[s];
+                        const int seg = sseg[s];
+                        const bool own = (seg == own1) || (seg == own2);
+                        double il64, ph64;
+                        seg_ilog_phi_f64(qx64, qy64, P[0], P[1], P[2], P[3], own, il64, ph64);
+                        const double wg = -(double)a.t64.pw[sidx[s]] * kInv2Pi;
+                        h0 += wg * (il64 * a.sb64[3 * (size_t)seg + 0] + ph64 * a.mb64[3 * (size_t)seg + 0]);
+                        h1 += wg * (il64 * a.sb64[3 * (size_t)seg + 1] + ph64 * a.mb64[3 * (size_t)seg + 1]);
+                        h2 += wg * (il64 * a.sb64[3 * (size_t)seg + 2] + ph64 * a.mb64[3 * (size_t)seg + 2]);
+                        continue;
+                    }
                     float ax = (sx1h[s] - qxh) + (sx1l[s] - qxl), ay = (sy1h[s] - qyh) + (sy1l[s] - qyl);
                     float bx = (sx2h[s] - qxh) + (sx2l[s] - qxl), by = (sy2h[s] - qyh) + (sy2l[s] - qyl);
                     float len = slen[s];
@@ -366,7 +339,30 @@ __global__ void __launch_bounds__(kEvThreads) eval32_kernel(EvalArgs32 a) {
                     float dt = ax * bx + ay * by;
                     bool own = (sseg[s] == own1) || (sseg[s] == own2);
                     float ilog, phi;
-                    if (!own && dt < 0.f && fabsf(cr) < kNearFallback * len * len) {
+                    const float mx = 0.5f * (ax + bx), my = 0.5f * (ay + by);   // midpoint - target
+                    const float r2 = mx * mx + my * my;
+                    if (!own && 16.f * len * len < r2) {
+                        // |eta| = len / (2 |z|) < 1/8: the App. D integrals by their series,
+                        // z = midpoint - q, eta = (p2 - p1) / (2 z), zeta = eta^2:
+                        //   int log|p-q| dS = len (log|z| - Re sum_k zeta^k / (2k (2k+1)))
+                        //   phi = 2 Im atanh(eta)
+                        const float dx = bx - ax, dy = by - ay, ir2 = 1.f / r2;
+                        const float ex = 0.5f * (dx * mx + dy * my) * ir2;
+                        const float ey = 0.5f * (dy * mx - dx * my) * ir2;
+                        const float zx = ex * ex - ey * ey, zy = 2.f * ex * ey;
+                        // s = zeta (1/6 + zeta (1/20 + zeta / 42))
+                        float tx = 1.f / 20.f + zx * (1.f / 42.f), ty = zy * (1.f / 42.f);
+                        float ux = 1.f / 6.f + (zx * tx - zy * ty), uy = zx * ty + zy * tx;
+                        const float sre = zx * ux - zy * uy;
+                        ilog = len * (0.5f * __logf(r2) - sre);
+                        // atanh: eta (1 + zeta (1/3 + zeta (1/5 + zeta / 7)))
+                        tx = 1.f / 5.f + zx * (1.f / 7.f);
+                        ty = zy * (1.f / 7.f);
+                        ux = 1.f / 3.f + (zx * tx - zy * ty);
+                        uy = zx * ty + zy * tx;
+                        const float vx = 1.f + (zx * ux - zy * uy), vy = zx * uy + zy * ux;
+                        phi = 2.f * (ex * vy + ey * vx);
+                    } else if (!own && dt < 0.f && fabsf(cr) < kNearFallback * len * len) {
                         // near-singular: the side of the curve is decided in FP64
                         const double *P = a.t64.pc + 4 * (size_t)sidx[s];
                         double il64, ph64;
@@ -401,8 +397,8 @@ __global__ void __launch_bounds__(kEvThreads) eval32_kernel(EvalArgs32 a) {
     }
     if (!act) return;
     if (MODE == 0) {
-        size_t o = 3 * ((size_t)r * a.vp.width + c);
-        float u[3] = {u0, u1, u2};
+        size_t o = 3 * ((size_t)vp.offset + (size_t)r * vp.width + c);
+        float u[3] = {(float)(u0 + h0), (float)(u1 + h1), (float)(u2 + h2)};
         for (int ch = 0; ch < 3; ++ch) {
             if (a.rgb) {
                 if (a.rgb_dtype == DC_F64) static_cast<double *>(a.rgb)[o + ch] = (double)u[ch];
@@ -412,9 +408,9 @@ __global__ void __launch_bounds__(kEvThreads) eval32_kernel(EvalArgs32 a) {
         }
     } else {
         int o = a.perm[ti];
-        a.out[3 * (size_t)o + 0] = u0;
-        a.out[3 * (size_t)o + 1] = u1;
-        a.out[3 * (size_t)o + 2] = u2;
+        a.out[3 * (size_t)o + 0] = u0 + h0;
+        a.out[3 * (size_t)o + 1] = u1 + h1;
+        a.out[3 * (size_t)o + 2] = u2 + h2;
     }
 }
 
@@ -530,7 +526,10 @@ dc_status Fmm::Impl::build32(const Geometry &G, cudaStream_t st, std::string &er
         (e = up(woff32, wo, st)) != cudaSuccess || (e = up(xoff32, xo, st)) != cudaSuccess ||
         (e = up(nt_q32, q32, st)) != cudaSuccess || (e = up(nt_items, items, st)) != cudaSuccess ||
         (e = to_f32(m2m32, m2m, st)) != cudaSuccess || (e = to_f32(l2l32, l2l, st)) != cudaSuccess ||
-        (e = to_f32(m2l32, m2l, st)) != cudaSuccess ||
+        (e = to_f32(m2l32, m2l, st)) != cudaSuccess || (e = to_f32(base32, base64, st)) != cudaSuccess ||
+        (e = Lm2l32.alloc((size_t)nC * 3 * P1)) != cudaSuccess ||
+        (e = heavy.alloc(std::max<size_t>(np, 1))) != cudaSuccess ||
+        (e = heavyL.alloc((size_t)nC)) != cudaSuccess || (e = heavyM.alloc((size_t)nC)) != cudaSuccess ||
         (e = M32.alloc((size_t)nC * 3 * P1)) != cudaSuccess ||
         (e = L32.alloc((size_t)nC * 3 * P1)) != cudaSuccess ||
         (e = sbar32.alloc((size_t)3 * D->S)) != cudaSuccess ||
@@ -540,6 +539,15 @@ dc_status Fmm::Impl::build32(const Geometry &G, cudaStream_t st, std::string &er
     }
     cudaMemsetAsync(sbar32.ptr, 0, sbar32.bytes(), st);
     cudaMemsetAsync(mbar32.ptr, 0, mbar32.bytes(), st);
+    cudaMemsetAsync(heavy.ptr, 0, heavy.bytes(), st);
+    cudaMemsetAsync(heavyL.ptr, 0, heavyL.bytes(), st);
+    cudaMemsetAsync(heavyM.ptr, 0, heavyM.bytes(), st);
+    cudaFuncSetAttribute(passes::m2l_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)passes::m2l_smem<float>(P1));
+    cudaFuncSetAttribute(passes::p2l_kernel<float, passes::PiecesF32>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passes::p2l_smem<float>(P1));
+    cudaFuncSetAttribute(passes::p2m_kernel<float, passes::PiecesF32>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passes::p2m_smem<float>(P1));
     return DC_OK;
 }
 
@@ -556,27 +564,91 @@ cudaError_t Fmm::Impl::to_f32_density(const double *sb, const double *mb, cudaSt
     return cudaGetLastError();
 }
 
+passes::TreeView<float> Fmm::Impl::view32() const {
+    passes::TreeView<float> v;
+    v.iw = iw32.ptr;
+    v.logw = logw32.ptr;
+    v.parent = parent.ptr;
+    v.child0 = child0.ptr;
+    v.quad = quad.ptr;
+    v.pstart = pstart.ptr;
+    v.pcount = pcount.ptr;
+    v.pw = pw32.ptr;
+    v.plen = plen32.ptr;
+    v.pseg = pseg.ptr;
+    v.v_ptr = v_ptr.ptr;
+    v.v_idx = v_idx.ptr;
+    v.v_code = v_code.ptr;
+    v.x_ptr = x_ptr.ptr;
+    v.x_idx = x_idx.ptr;
+    v.x_off = xoff32.ptr;
+    return v;
+}
+
 cudaError_t Fmm::Impl::passes32(const float *sb, const float *mb, int use_s, int use_m,
-                                cudaStream_t st) {
+                                cudaStream_t st, const Schedule &sc) {
     const int nC = tree.n_cells();
+    const int P1 = P1i;
     size_t ebytes = (size_t)nC * 3 * P1 * sizeof(float2);
     cudaError_t e;
-    if ((e = cudaMemsetAsync(M32.ptr, 0, ebytes, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(L32.ptr, 0, ebytes, st)) != cudaSuccess) return e;
-    DevTree32 t = dt32();
-    int th = ((P1 + 31) / 32) * 32;
-    if (n_p2m > 0)
-        p2m32_kernel<<<n_p2m, th, 0, st>>>(t, p2m_leaves.ptr, sb, mb, use_s, use_m, P1, M32.ptr); note_launch();
+    if ((e = cudaMemsetAsync(M32i.ptr, 0, ebytes, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(L32i.ptr, 0, ebytes, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(Lm2l32i.ptr, 0, ebytes, st)) != cudaSuccess) return e;
+    passes::TreeView<float> tv = view32();
+    passes::PiecesF32 ps{pc32.ptr};
+    int th = P1 <= 32 ? 32 : 64;
+    if (n_p2m > 0) {
+        passes::p2m_kernel<float, passes::PiecesF32><<<n_p2m, passes::kChunk, passes::p2m_smem<float>(P1), st>>>(
+            tv, ps, p2m_leaves.ptr, sb, mb, use_s, use_m, P1, M32i.ptr);
+        note_launch();
+    }
     for (int l = tree.depth - 1; l >= 2; --l) {
-        int lo = tree.level_start[l], hi = tree.level_start[l + 1];
-        if (hi > lo) m2m32_kernel<<<hi - lo, th, 0, st>>>(t, lo, P1, m2m32.ptr, M32.ptr); note_launch();
+        int lo = m2m_ptr[l], hi = m2m_ptr[l + 1];
+        if (hi > lo) {
+            passes::m2m_kernel<float><<<hi - lo, th, 0, st>>>(tv, m2m_cells.ptr + lo, P1, m2m32i.ptr, M32i.ptr);
+            note_launch();
+        }
+    }
+    if (sc.n_m2l > 0) {
+        int grid = std::min((sc.n_m2l + passes::kM2LSlots - 1) / passes::kM2LSlots, 4 * n_sms);
+        passes::m2l_kernel<float><<<grid, 32 * passes::kM2LSlots, passes::m2l_smem<float>(P1), st>>>(
+            tv, sc.m2l.ptr, sc.n_m2l, P1, base32i.ptr, M32i.ptr, Lm2l32i.ptr);
+        note_launch();
+    }
+    if (sc.n_p2l > 0) {
+        passes::p2l_kernel<float, passes::PiecesF32><<<sc.n_p2l, passes::kChunk, passes::p2l_smem<float>(P1), st>>>(
+            tv, ps, sc.p2l.ptr, sb, mb, use_s, use_m, P1, Lm2l32i.ptr);
+        note_launch();
     }
     for (int l = 2; l <= tree.depth; ++l) {
-        int lo = tree.level_start[l], hi = tree.level_start[l + 1];
-        if (hi > lo)
-            down32_kernel<<<hi - lo, th, 0, st>>>(t, lo, l, P1, l2l32.ptr, m2l32.ptr, M32.ptr, sb, mb,
-                                                   use_s, use_m, L32.ptr); note_launch();
+        int lo = sc.l2l_ptr[l], hi = sc.l2l_ptr[l + 1];
+        if (hi > lo) {
+            passes::l2l_kernel<float><<<(hi - lo + 3) / 4, 128, 0, st>>>(
+                tv, sc.l2l.ptr + lo, hi - lo, l, P1, l2l32i.ptr, Lm2l32i.ptr, L32i.ptr);
+            note_launch();
+        }
     }
+    return cudaGetLastError();
+}
+
+cudaError_t Fmm::Impl::prepare_render32(const double *sb, const double *mb, cudaStream_t st) {
+    cudaError_t e = to_f32_density(sb, mb, st);
+    if (e != cudaSuccess) return e;
+    if ((e = passes(sb, mb, 1, 1, st, sched_all)) != cudaSuccess) return e;
+    size_t n = (size_t)tree.n_cells() * 3 * P1;
+    int th = 256;
+    narrow_kernel<double2, float2><<<(unsigned)((n + th - 1) / th), th, 0, st>>>(M.ptr, M32.ptr, n);
+    note_launch();
+    narrow_kernel<double2, float2><<<(unsigned)((n + th - 1) / th), th, 0, st>>>(L.ptr, L32.ptr, n);
+    note_launch();
+    int np = int(tree.pc_seg.size());
+    if (np > 0) {
+        heavy_kernel<<<(np + th - 1) / th, th, 0, st>>>(sb, mb, pseg.ptr, pw.ptr, plen64.ptr, heavy.ptr, np);
+        note_launch();
+    }
+    int nC = tree.n_cells();
+    big_coef_kernel<<<(nC + th - 1) / th, th, 0, st>>>(L.ptr, M.ptr, nC, P1, heavyL.ptr, heavyM.ptr);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -584,12 +656,26 @@ cudaError_t Fmm::Impl::apply_nodes32(const double *x, double *y, bool single, cu
     cudaError_t e = interp32(x, single ? sbar32.ptr : mbar32.ptr, st);
     if (e != cudaSuccess) return e;
     int us = single ? 1 : 0, um = single ? 0 : 1;
-    if ((e = passes32(sbar32.ptr, mbar32.ptr, us, um, st)) != cudaSuccess) return e;
-    if (n_nt_items == 0) return cudaSuccess;
-    EvalArgs32 a{};
-    a.t = dt32();
-    a.t64 = dt();
-    a.items = nt_items.ptr;
+    if ((e = passes32(sbar32.ptr, mbar32.ptr, us, um, st, sched_nodes)) != cudaSuccess) return e;
+    if (n_nt_items4 == 0) return cudaSuccess;
+    evalnodes::NodeArgs<float> a;
+    a.u_ptr = u_ptr.ptr;
+    a.u_idx = u_idx.ptr;
+    a.w_ptr = w_ptr.ptr;
+    a.w_idx = w_idx.ptr;
+    a.pstart = pstart.ptr;
+    a.pcount = pcount.ptr;
+    a.pseg = pseg.ptr;
+    a.pc64 = pc.ptr;
+    a.cc64 = cc.ptr;
+    a.pw = pw32.ptr;
+    a.iw = iw32.ptr;
+    a.logw = logw32.ptr;
+    a.items = nt_items4.ptr;
+    a.q64 = nt_xy.ptr;
+    a.own1 = nt_own1.ptr;
+    a.own2 = nt_own2.ptr;
+    a.perm = nt_perm.ptr;
     a.P1 = P1;
     a.M = M32.ptr;
     a.L = L32.ptr;
@@ -597,19 +683,47 @@ cudaError_t Fmm::Impl::apply_nodes32(const double *x, double *y, bool single, cu
     a.mb = mbar32.ptr;
     a.use_s = us;
     a.use_m = um;
-    a.q32 = nt_q32.ptr;
-    a.q64 = nt_xy.ptr;
-    a.own1 = nt_own1.ptr;
-    a.own2 = nt_own2.ptr;
-    a.perm = nt_perm.ptr;
     a.out = y;
-    eval32_kernel<1><<<n_nt_items, 64, 0, st>>>(a); note_launch();
+    a.P1 = P1i;
+    a.M = M32i.ptr;
+    a.L = L32i.ptr;
+    evalnodes::eval_nodes_kernel<float><<<n_nt_items4, 32 * evalnodes::kWarps, 0, st>>>(a);
+    note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t Fmm::Impl::render_tiles32(const VpDev &vp, int n_tiles, void *rgb, int rgb_dtype,
-                                      unsigned char *rgb8, cudaStream_t st) {
+cudaError_t Fmm::Impl::graph_matvec32(const double *x, double *y, cudaStream_t st) {
+    const size_t bytes = sizeof(double) * 3 * (size_t)D->N;
+    cudaError_t e;
+    if (!g32_exec) {
+        if ((e = g_in.ensure(3 * (size_t)D->N)) != cudaSuccess) return e;
+        if ((e = g_out.ensure(3 * (size_t)D->N)) != cudaSuccess) return e;
+        if (!cap_stream && (e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return e;
+        long long before = kernel_launches();
+        if ((e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+        cudaError_t e1 = launch_block_apply(pinv.ptr, D->n_panels, D->g, g_in.ptr, ir_t.ptr, cap_stream);
+        cudaError_t e2 = (e1 == cudaSuccess) ? apply_nodes32(ir_t.ptr, g_out.ptr, true, cap_stream) : e1;
+        e = cudaStreamEndCapture(cap_stream, &g32);
+        g32_kernels = int(kernel_launches() - before);
+        note_launch(-g32_kernels);   // counted again at every graph launch
+        if (e2 != cudaSuccess) return e2;
+        if (e != cudaSuccess) return e;
+        if ((e = cudaGraphInstantiate(&g32_exec, g32, 0)) != cudaSuccess) return e;
+    }
+    if ((e = cudaMemcpyAsync(g_in.ptr, x, bytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaGraphLaunch(g32_exec, st)) != cudaSuccess) return e;
+    note_launch(g32_kernels);
+    return cudaMemcpyAsync(y, g_out.ptr, bytes, cudaMemcpyDeviceToDevice, st);
+}
+
+cudaError_t Fmm::Impl::render_tiles32(int n_tiles, void *rgb, int rgb_dtype,
+                                      unsigned char *rgb8, const double *sb64, const double *mb64,
+                                      cudaStream_t st) {
     EvalArgs32 a{};
+    a.sb64 = sb64;
+    a.mb64 = mb64;
+    a.heavy = heavy.ptr;
     a.t = dt32();
     a.t64 = dt();
     a.items = tiles.ptr;
@@ -620,7 +734,11 @@ cudaError_t Fmm::Impl::render_tiles32(const VpDev &vp, int n_tiles, void *rgb, i
     a.mb = mbar32.ptr;
     a.use_s = 1;
     a.use_m = 1;
-    a.vp = vp;
+    a.hL = heavyL.ptr;
+    a.hM = heavyM.ptr;
+    a.M64 = M.ptr;
+    a.L64 = L.ptr;
+    a.vps = vps.ptr;
     a.rgb = rgb;
     a.rgb_dtype = rgb_dtype;
     a.rgb8 = rgb8;
@@ -628,8 +746,16 @@ cudaError_t Fmm::Impl::render_tiles32(const VpDev &vp, int n_tiles, void *rgb, i
     return cudaGetLastError();
 }
 
-cudaError_t Fmm::Impl::eval_points32(int n_items, double *out, cudaStream_t st) {
+cudaError_t Fmm::Impl::eval_points32(int n_items, double *out, const double *sb64,
+                                     const double *mb64, cudaStream_t st) {
     EvalArgs32 a{};
+    a.sb64 = sb64;
+    a.mb64 = mb64;
+    a.heavy = heavy.ptr;
+    a.hL = heavyL.ptr;
+    a.hM = heavyM.ptr;
+    a.M64 = M.ptr;
+    a.L64 = L.ptr;
     a.t = dt32();
     a.t64 = dt();
     a.items = pt_items.ptr;

@@ -9,6 +9,7 @@
 
 #include "dc_internal.h"
 #include "fmm.h"
+#include "passes.cuh"
 #include "tree.h"
 
 namespace dc {
@@ -45,7 +46,15 @@ struct DevTree32 {
 // A unit of evaluation work inside one leaf: a pixel rectangle (r0, c0,
 // nr x nc) or, for target lists, targets [r0, r0 + nr) with nc = 0.
 struct Tile {
-    int leaf, r0, c0, nr, nc;
+    int leaf, r0, c0, nr, nc, vp;   // vp: viewport index (pixel tiles)
+};
+
+// Cells that need incoming expansions for one set of targets (all cells for
+// pixels; the cells above the nodes for the matvec), by pass.
+struct Schedule {
+    DevBuf<int> m2l, p2l, l2l;        // cells with list 2 / list 4; cells per level
+    std::vector<int> l2l_ptr;         // [depth + 2] offsets into l2l by level
+    int n_m2l = 0, n_p2l = 0;
 };
 
 struct Fmm::Impl {
@@ -69,10 +78,13 @@ struct Fmm::Impl {
     DevBuf<double> pt_xy, pt_out;
     DevBuf<float2> pt_q32;
     DevBuf<Tile> pt_items;
+    DevBuf<int4> nt_items4, pt_items4;   // (leaf, first target, count, 0) work items
+    int n_nt_items4 = 0;
     // FP64 tables and expansions
     DevBuf<double2> m2m, l2l, m2l, M, L;
     DevBuf<double> sbar, mbar;
     DevBuf<Tile> tiles;
+    DevBuf<VpDev> vps;
     // FP32 form
     DevBuf<float> iw32, logw32, pw32, plen32;
     DevBuf<float4> pc32;
@@ -85,28 +97,66 @@ struct Fmm::Impl {
     DevBuf<double> ir_r, ir_d, ir_t;   // refinement residual, correction, scratch
     DevBuf<double> pinv;          // [panels][g][g] inverse self-interaction blocks
     DevBuf<int> pinfo;
+    // pass schedules and tables of the templated passes
+    Schedule sched_all, sched_nodes;
+    DevBuf<int> m2m_cells, v_code;
+    std::vector<int> m2m_ptr;         // [depth + 2]: non-leaf cells with pieces, by level
+    DevBuf<double2> base64, Lm2l;
+    DevBuf<float2> base32, Lm2l32;
+    // the FP32 operator inside GMRES runs at a lower order p_inner (its
+    // accuracy only has to beat the inner tolerance; the FP64 residual at
+    // order p decides convergence): own tables and expansions
+    int P1i = 0;
+    DevBuf<float2> m2m32i, l2l32i, base32i, M32i, L32i, Lm2l32i;
+    DevBuf<double> iw64, logw64, plen64;
+    DevBuf<unsigned char> heavy;      // per piece: near field evaluated in FP64
+    DevBuf<unsigned char> heavyL, heavyM;   // per cell: L2P / M2P evaluated in FP64
+    int n_sms = 152;
+    passes::TreeView<double> view64() const;
+    passes::TreeView<float> view32() const;
     long long p2p_nodes = 0, m2l_cnt = 0, render_pairs = 0, render_m2p = 0;
     double render_flops = 0.0, render_eval_ms = 0.0;
     bool eval_timing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // the FP32 preconditioned matvec v -> A32 M^-1 v captured as one CUDA
+    // graph that reads g_in and writes g_out
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t g32 = nullptr;
+    cudaGraphExec_t g32_exec = nullptr;
+    int g32_kernels = 0;
+    DevBuf<double> g_in, g_out;
+    cudaError_t graph_matvec32(const double *x, double *y, cudaStream_t st);
     ~Impl() {
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
+        if (g32_exec) cudaGraphExecDestroy(g32_exec);
+        if (g32) cudaGraphDestroy(g32);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
     }
 
     DevTree dt() const;
     DevTree32 dt32() const;
     // FP64 passes / node operator (fmm.cu)
-    cudaError_t passes(const double *sb, const double *mb, int use_s, int use_m, cudaStream_t st);
+    cudaError_t passes(const double *sb, const double *mb, int use_s, int use_m, cudaStream_t st,
+                       const Schedule &sc);
     cudaError_t apply_nodes(const double *x, double *y, bool single, cudaStream_t st);
     // FP32 (fmm32.cu)
     dc_status build32(const Geometry &G, cudaStream_t st, std::string &err);
-    cudaError_t passes32(const float *sb, const float *mb, int use_s, int use_m, cudaStream_t st);
+    cudaError_t passes32(const float *sb, const float *mb, int use_s, int use_m, cudaStream_t st,
+                         const Schedule &sc);
+    // render preparation of the FP32 form: FP64 passes, FP32 copies of the
+    // expansions, heavy-piece flags from the FP64 segment densities
+    cudaError_t prepare_render32(const double *sb, const double *mb, cudaStream_t st);
     cudaError_t apply_nodes32(const double *x, double *y, bool single, cudaStream_t st);
     cudaError_t interp32(const double *node_vals, float *seg_vals, cudaStream_t st);
-    cudaError_t render_tiles32(const VpDev &vp, int n_tiles, void *rgb, int rgb_dtype,
-                               unsigned char *rgb8, cudaStream_t st);
-    cudaError_t eval_points32(int n_items, double *out, cudaStream_t st);
+    cudaError_t render_tiles32(int n_tiles, void *rgb, int rgb_dtype,
+                               unsigned char *rgb8, const double *sb64, const double *mb64,
+                               cudaStream_t st);
+    cudaError_t eval_points32(int n_items, double *out, const double *sb64, const double *mb64,
+                              cudaStream_t st);
+    cudaError_t eval_list64(const int4 *items, int n_items, const double *q64, const int *own1,
+                            const int *own2, const int *perm, const double *sb, const double *mb,
+                            int use_s, int use_m, double *out, cudaStream_t st);
     cudaError_t to_f32_density(const double *sb, const double *mb, cudaStream_t st);
 };
 
