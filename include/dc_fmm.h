@@ -184,6 +184,27 @@ dc_status dc_render_viewport(dc_ctx *ctx, int n_vp, const dc_viewport *vps,
 dc_status dc_eval_points(dc_ctx *ctx, int n, const void *xy, int xy_where,
                          void *out, int out_dtype, int out_where);
 
+/* No counterpart in the paper.  An allocation-free variant of
+ * dc_eval_points for callers that must not allocate device memory during a
+ * call -- for example a frame loop whose memory belongs to another
+ * framework, or code held to a fixed memory budget.  It evaluates the layer
+ * potential (single layer of sigma plus double layer of mu) at n points by
+ * the FP64 direct sum over all of the context's segments, whatever its form.
+ *   xy_dev   [n][2] double in device memory (caller-owned)
+ *   out_dev  [n][3] double in device memory (caller-owned), written in
+ *            stream order on the context's stream
+ * Scratch: the segment densities go to one file-scope device array sized for
+ * at most 262,144 segments (12 MiB, held by every GPU that loads the library
+ * until the process exits); a drawing with more segments gets DC_ERR_ARG.
+ * The call allocates nothing (no cudaMalloc / cudaFree, no allocating
+ * library routine).  Its first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current: make that first
+ * call before any stream capture.  All calls share the one array and it
+ * keeps the last call's contents, so calls that overlap on the GPU (other
+ * streams or contexts without ordering between them) race on it.
+ * Errors: DC_ERR_STATE without a density, DC_ERR_ARG for bad sizes. */
+dc_status dc_eval_points_noalloc(dc_ctx *ctx, int n, const double *xy_dev, double *out_dev);
+
 /* Copies the current density sigma at the nodes to host [n_nodes][3]. */
 dc_status dc_get_density(dc_ctx *ctx, double *sigma_out);
 

@@ -72,7 +72,8 @@ class dc_render_stats(ctypes.Structure):
 EXPORTS = ["dc_default_options", "dc_create", "dc_destroy", "dc_build_tree", "dc_solve_density",
            "dc_render_viewport", "dc_eval_points", "dc_get_density", "dc_set_density",
            "dc_get_nodes", "dc_get_sizes", "dc_last_error", "dc_status_string",
-           "dc_abi_version", "dc_aux_tree_check", "dc_aux_kernel_launches"]
+           "dc_abi_version", "dc_aux_tree_check", "dc_aux_kernel_launches",
+           "dc_eval_points_noalloc"]
 
 
 def _load():
@@ -90,6 +91,7 @@ def _load():
     lib.dc_render_viewport.argtypes = [P, I, ctypes.POINTER(dc_viewport), P, I, P, I,
                                        ctypes.POINTER(dc_render_stats)]
     lib.dc_eval_points.argtypes = [P, I, P, I, P, I, I]
+    lib.dc_eval_points_noalloc.argtypes = [P, I, P, P]
     lib.dc_get_density.argtypes = [P, P]
     lib.dc_set_density.argtypes = [P, P]
     lib.dc_get_nodes.argtypes = [P, P, P, P, P]
@@ -249,6 +251,12 @@ class Context:
         self._check(_get_lib().dc_render_viewport(self._h, n, arr, _ptr(rgb), dt, _ptr(rgb8), where,
                                            ctypes.byref(st) if stats else None))
         return st if stats else None
+
+    def eval_points_noalloc(self, xy, out):
+        """dc_eval_points_noalloc: xy [n, 2] and out [n, 3] float64 torch
+        CUDA tensors; nothing is allocated by the call."""
+        self._check(_get_lib().dc_eval_points_noalloc(self._h, int(xy.shape[0]), _ptr(xy), _ptr(out)))
+        return out
 
     def eval_points(self, xy, out):
         """xy [n, 2] float64 and out [n, 3] (float32/float64), both numpy

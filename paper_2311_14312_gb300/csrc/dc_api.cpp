@@ -423,6 +423,21 @@ dc_status dc_set_density(dc_ctx *ctx, const double *sigma_in) {
     return DC_OK;
 }
 
+dc_status dc_eval_points_noalloc(dc_ctx *ctx, int n, const double *xy_dev, double *out_dev) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (ctx->state < 2) return fail(ctx, DC_ERR_STATE, "eval_points_noalloc: no density yet");
+    if (n < 0 || (n > 0 && (!xy_dev || !out_dev)))
+        return fail(ctx, DC_ERR_ARG, "eval_points_noalloc: bad arguments");
+    if (n == 0) return DC_OK;
+    std::string msg;
+    cudaError_t e = dc::eval_points_noalloc(ctx->dg, ctx->sigma.ptr, ctx->mu.ptr, xy_dev, n, out_dev,
+                                            ctx->stream, msg);
+    if (e == cudaErrorInvalidValue && !msg.empty()) return fail(ctx, DC_ERR_ARG, msg);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "eval_points_noalloc");
+    return DC_OK;
+}
+
 dc_status dc_get_density(dc_ctx *ctx, double *sigma_out) {
     if (!ctx) return DC_ERR_ARG;
     ctx->err.clear();

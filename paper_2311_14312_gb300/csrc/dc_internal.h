@@ -155,6 +155,13 @@ cudaError_t gmres_solve(GmresWork *w, Operator &A, int N, const double *b, doubl
                         double tol, int restart, int max_iter, cudaStream_t st,
                         GmresResult &res, std::string &err);
 
+// Allocation-free FP64 direct sum at points (noalloc.cu): segment densities
+// in a static device array of noalloc_max_segments() segments.
+int noalloc_max_segments();
+cudaError_t eval_points_noalloc(const DevGeom &G, const double *sigma, const double *mu,
+                                const double *xy, int n, double *out, cudaStream_t st,
+                                std::string &err);
+
 // Small FP64 vector helpers on [N][3] vectors (gmres.cu).
 cudaError_t vec_residual(const double *b, const double *Ax, double *r, int n3, cudaStream_t st);
 cudaError_t vec_axpy(double *x, const double *d, int n3, cudaStream_t st);
