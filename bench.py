@@ -232,6 +232,7 @@ def run_ours(args):
     step_ms, solve_ms, render_ms = [], [], []
     barrier()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")     # profilers can filter on this range
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -246,6 +247,7 @@ def run_ours(args):
         step_ms.append(e0.elapsed_time(e2))
         solve_ms.append(e0.elapsed_time(e1))
         render_ms.append(e1.elapsed_time(e2))
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     launches = P.kernel_launches() - launches0

@@ -39,6 +39,8 @@
 #ifndef DC_FMM_H
 #define DC_FMM_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -68,7 +70,18 @@ typedef enum {
                                (Arnoldi, least squares, outer residual)     */
 } dc_form;
 
-typedef enum { DC_X0_ONES = 0, DC_X0_ZEROS = 1, DC_X0_USER = 2 } dc_x0_mode;
+typedef enum {
+    DC_X0_ONES = 0,        /* the paper's choice (Sec. 5.5)                  */
+    DC_X0_ZEROS = 1,
+    DC_X0_USER = 2,        /* x0 passed to dc_solve_density                  */
+    DC_X0_LEARNED = 3      /* predicted by the model set with
+                              dc_aux_set_warm_start_model (no counterpart in
+                              the paper): per channel x0 = a x_pred + c 1
+                              with a, c minimising ||b - G_H x0|| (two extra
+                              operator applications); a = 0 is the cold
+                              fallback, so the start is never worse than
+                              zeros or the paper's ones                      */
+} dc_x0_mode;
 typedef enum { DC_MEM_DEVICE = 0, DC_MEM_HOST = 1 } dc_mem;
 typedef enum { DC_F32 = 0, DC_F64 = 1 } dc_dtype;
 
@@ -89,6 +102,12 @@ typedef struct {
     double domain[4];      /* x0, y0, x1, y1: region the quadtree root must
                               cover besides the curves (render targets must
                               lie inside the root)                           */
+    int p_inner;           /* DC_FORM_FMM32: expansion order of the FP32
+                              operator inside the iterative refinement, 1..p
+                              (0 = min(p, 12))                               */
+    double inner_tol;      /* DC_FORM_FMM32: floor of the inner GMRES
+                              tolerance per refinement step, in (0, 1)
+                              (0 = 1e-5)                                     */
 } dc_options;
 
 typedef struct {
@@ -104,9 +123,16 @@ typedef struct {
     int converged;         /* 1 if every channel met gmres_tol               */
     int n_matvec;          /* operator applications, right-hand side included */
     double ms_rhs;         /* right-hand side (Alg. 3 line 4), device time   */
-    double ms_solve;       /* GMRES (Alg. 3 line 5), host wall time          */
+    double ms_solve;       /* x0 set-up and GMRES (Alg. 3 line 5), host wall
+                              time                                           */
     long long p2p_pairs;   /* near-field (target, piece) pairs per matvec    */
     long long m2l_pairs;   /* cell pairs in M2L per matvec                   */
+    int used_warm;         /* DC_X0_LEARNED: bit c set if channel c's start
+                              uses the prediction (a != 0; 0 in other modes) */
+    double warm_resid[3];  /* DC_X0_LEARNED: ||b - G_H x0|| / ||b|| of the
+                              start per channel (0 otherwise)                */
+    double ms_warm;        /* DC_X0_LEARNED: features, network and residual
+                              check, host wall time (inside ms_solve)        */
 } dc_solve_stats;
 
 typedef struct {
@@ -130,7 +156,8 @@ typedef struct {
 } dc_render_stats;
 
 /* Fills *opt with defaults: DC_FORM_FMM32, g 16, s 80, p 24, leaf 64,
- * depth 30, tol 1e-10, restart 200, max_iter 2000, x0 ones, domain [0,1]^2. */
+ * depth 30, tol 1e-10, restart 200, max_iter 2000, x0 ones, domain [0,1]^2,
+ * p_inner 0 and inner_tol 0 (the built-in choices). */
 dc_status dc_default_options(dc_options *opt);
 
 /* Creates a context bound to the current CUDA device.  *out is set to NULL
@@ -239,6 +266,73 @@ const char *dc_status_string(dc_status st);
  * Errors: DC_ERR_ARG for bad sizes or non-finite input. */
 dc_status dc_aux_tree_check(int n_seg, const double *seg_xy, const double *domain,
                             int leaf_size, int max_depth, double *out);
+
+/* ---------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper: its warm start, Sec. 6.1,
+ * re-uses an earlier solution).  A 4-layer perceptron
+ *     n_in -> hidden -> hidden -> hidden -> n_out,  GELU between layers,
+ * predicts one panel's g node densities times the panel's arc length for one
+ * colour channel from n_in = 22 g + 32 local features: the panel's own nodes
+ * (position and normal in the panel frame, scaled by its arc length), its
+ * boundary colours u+ and u-, the boundary colours of the 8 nearest other
+ * panels by node centroid and those panels' centroid offsets and chord
+ * directions.  Parameters are FP32, packed layer by layer as W_l [out][in]
+ * row-major then b_l [out]; the network reads them rounded to BF16 and
+ * accumulates in FP32.  All device pointers below are caller-owned; work is
+ * issued on `stream` (cudaStream_t, NULL = legacy default stream).
+ * --------------------------------------------------------------------- */
+
+/* Parameter count and workspace size (floats) for a batch of `batch` rows. */
+size_t dc_aux_mlp_param_count(int n_in, int hidden, int n_out);
+size_t dc_aux_mlp_workspace_floats(int n_in, int hidden, int n_out, int batch);
+
+/* y [batch][n_out] = net(x [batch][n_in]); params, x, y, work on the device.
+ * Errors: DC_ERR_ARG for bad sizes or NULL pointers, DC_ERR_CUDA. */
+dc_status dc_aux_mlp_forward(int n_in, int hidden, int n_out, const float *params, int batch,
+                             const float *x, float *y, float *work, void *stream);
+
+/* Mean squared error of net(x) against target [batch][n_out] into *loss
+ * (device float) and its gradient with respect to the parameters into
+ * grad [param_count] (device).  The gradient is that of the network as it
+ * computes (BF16-rounded weights, exact GELU), with the bias and weight
+ * reductions over the batch in a fixed order (deterministic). */
+dc_status dc_aux_mlp_loss_grad(int n_in, int hidden, int n_out, const float *params, int batch,
+                               const float *x, const float *target, float *grad, float *loss,
+                               float *work, void *stream);
+
+/* One Adam step (Kingma and Ba 2015) on n parameters: m, v are the moment
+ * buffers (zero before step 1), step counts from 1. */
+dc_status dc_aux_mlp_adam(size_t n, float *params, const float *grad, float *m, float *v, float lr,
+                          float beta1, float beta2, float eps, int step, void *stream);
+
+/* Sizes of the context's feature rows (one per panel and colour channel):
+ * *rows = 3 n_panels, *n_features = 22 g + 32, *n_out = g.
+ * Errors: DC_ERR_STATE before dc_build_tree. */
+dc_status dc_aux_feature_dims(dc_ctx *ctx, int *rows, int *n_features, int *n_out);
+
+/* Writes the features of every (panel, channel) row to feat_dev
+ * [rows][n_features] (device, float) and, if target_dev is not NULL, the
+ * current density as targets [rows][n_out] (sigma times panel arc length;
+ * needs a density: DC_ERR_STATE otherwise).  Row 3 j + c is panel j,
+ * channel c; nodes are in panel order. */
+dc_status dc_aux_panel_features(dc_ctx *ctx, float *feat_dev, float *target_dev);
+
+/* Sets the network that DC_X0_LEARNED uses: params [dc_aux_mlp_param_count(
+ * 22 g + 32, hidden, g)] floats in `where` memory (DC_MEM_HOST or
+ * DC_MEM_DEVICE), copied into the context.  hidden = 0 removes the model.
+ * Errors: DC_ERR_ARG for bad sizes or non-finite parameters. */
+dc_status dc_aux_set_warm_start_model(dc_ctx *ctx, int hidden, const float *params, int where);
+
+/* Auxiliary: one application of the operator at the nodes, the call
+ * FMM(S, sigma, q) of Sec. 5.5 (the matvec of GMRES):
+ *   op 0: y = G_H x (single layer, Eq. 19), op 1: y = F_H x (double layer)
+ * in the context's form.  With inner = 1 and DC_FORM_FMM32 (op 0 only) it
+ * applies the FP32 operator of the inner GMRES instead, y = G_H M^-1 x with
+ * M the block diagonal of G_H over panels (order-12 expansions).
+ *   x, y  [n_nodes][3] double, device, caller-owned, distinct
+ * Errors: DC_ERR_STATE before dc_build_tree, DC_ERR_ARG for a bad op or
+ * pointer, DC_ERR_UNSUPPORTED for inner = 1 in other forms. */
+dc_status dc_aux_apply_operator(dc_ctx *ctx, int op, int inner, const double *x, double *y);
 
 int dc_abi_version(void);
 

@@ -28,7 +28,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libdc_fmm.so")
 DC_OK, DC_ERR_ARG, DC_ERR_STATE, DC_ERR_CUDA, DC_ERR_OOM = 0, 1, 2, 3, 4
 DC_ERR_NOCONV, DC_ERR_TIMEOUT, DC_ERR_GEOMETRY, DC_ERR_UNSUPPORTED = 5, 6, 7, 8
 DC_FORM_DENSE64, DC_FORM_FMM64, DC_FORM_FMM32 = 0, 1, 2
-DC_X0_ONES, DC_X0_ZEROS, DC_X0_USER = 0, 1, 2
+DC_X0_ONES, DC_X0_ZEROS, DC_X0_USER, DC_X0_LEARNED = 0, 1, 2, 3
 DC_MEM_DEVICE, DC_MEM_HOST = 0, 1
 DC_F32, DC_F64 = 0, 1
 
@@ -40,7 +40,8 @@ class dc_options(ctypes.Structure):
                 ("p", ctypes.c_int), ("leaf_size", ctypes.c_int), ("max_depth", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
                 ("gmres_max_iter", ctypes.c_int), ("x0_mode", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("domain", ctypes.c_double * 4)]
+                ("stream", ctypes.c_void_p), ("domain", ctypes.c_double * 4),
+                ("p_inner", ctypes.c_int), ("inner_tol", ctypes.c_double)]
 
 
 class dc_sizes(ctypes.Structure):
@@ -54,7 +55,9 @@ class dc_solve_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int * 3), ("rel_resid", ctypes.c_double * 3),
                 ("converged", ctypes.c_int), ("n_matvec", ctypes.c_int),
                 ("ms_rhs", ctypes.c_double), ("ms_solve", ctypes.c_double),
-                ("p2p_pairs", ctypes.c_longlong), ("m2l_pairs", ctypes.c_longlong)]
+                ("p2p_pairs", ctypes.c_longlong), ("m2l_pairs", ctypes.c_longlong),
+                ("used_warm", ctypes.c_int), ("warm_resid", ctypes.c_double * 3),
+                ("ms_warm", ctypes.c_double)]
 
 
 class dc_viewport(ctypes.Structure):
@@ -73,7 +76,9 @@ EXPORTS = ["dc_default_options", "dc_create", "dc_destroy", "dc_build_tree", "dc
            "dc_render_viewport", "dc_eval_points", "dc_get_density", "dc_set_density",
            "dc_get_nodes", "dc_get_sizes", "dc_last_error", "dc_status_string",
            "dc_abi_version", "dc_aux_tree_check", "dc_aux_kernel_launches",
-           "dc_eval_points_noalloc"]
+           "dc_eval_points_noalloc", "dc_aux_mlp_param_count", "dc_aux_mlp_workspace_floats",
+           "dc_aux_mlp_forward", "dc_aux_mlp_loss_grad", "dc_aux_mlp_adam", "dc_aux_feature_dims",
+           "dc_aux_panel_features", "dc_aux_set_warm_start_model", "dc_aux_apply_operator"]
 
 
 def _load():
@@ -104,9 +109,22 @@ def _load():
     lib.dc_aux_tree_check.argtypes = [I, P, P, I, I, P]
     lib.dc_aux_kernel_launches.argtypes = []
     lib.dc_aux_kernel_launches.restype = ctypes.c_longlong
+    Z, F = ctypes.c_size_t, ctypes.c_float
+    lib.dc_aux_mlp_param_count.argtypes = [I, I, I]
+    lib.dc_aux_mlp_param_count.restype = Z
+    lib.dc_aux_mlp_workspace_floats.argtypes = [I, I, I, I]
+    lib.dc_aux_mlp_workspace_floats.restype = Z
+    lib.dc_aux_mlp_forward.argtypes = [I, I, I, P, I, P, P, P, P]
+    lib.dc_aux_mlp_loss_grad.argtypes = [I, I, I, P, I, P, P, P, P, P, P]
+    lib.dc_aux_mlp_adam.argtypes = [Z, P, P, P, P, F, F, F, F, I, P]
+    lib.dc_aux_feature_dims.argtypes = [P, P, P, P]
+    lib.dc_aux_panel_features.argtypes = [P, P, P]
+    lib.dc_aux_set_warm_start_model.argtypes = [P, I, P, I]
+    lib.dc_aux_apply_operator.argtypes = [P, I, I, P, P]
     for name in EXPORTS:
         if name not in ("dc_destroy", "dc_last_error", "dc_status_string", "dc_abi_version",
-                        "dc_aux_kernel_launches"):
+                        "dc_aux_kernel_launches", "dc_aux_mlp_param_count",
+                        "dc_aux_mlp_workspace_floats"):
             getattr(lib, name).restype = I
     _ = D
     return lib
@@ -252,6 +270,38 @@ class Context:
                                            ctypes.byref(st) if stats else None))
         return st if stats else None
 
+    def apply_operator(self, x, y, op=0, inner=False):
+        """dc_aux_apply_operator: y = G_H x (op 0) or F_H x (op 1) at the
+        nodes; x, y [n_nodes, 3] float64 torch CUDA tensors."""
+        self._check(_get_lib().dc_aux_apply_operator(self._h, int(op), int(bool(inner)), _ptr(x),
+                                                     _ptr(y)))
+        return y
+
+    # ---------------------------------------------------- warm start --
+    def feature_dims(self):
+        """(rows, n_features, n_out) of dc_aux_panel_features."""
+        r, f, o = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(_get_lib().dc_aux_feature_dims(self._h, ctypes.byref(r), ctypes.byref(f),
+                                                   ctypes.byref(o)))
+        return r.value, f.value, o.value
+
+    def panel_features(self, feat, target=None):
+        """feat [rows, n_features] and target [rows, n_out] float32 torch
+        CUDA tensors (target optional; needs a density)."""
+        self._check(_get_lib().dc_aux_panel_features(self._h, _ptr(feat), _ptr(target)))
+        return feat, target
+
+    def set_warm_start_model(self, hidden, params):
+        """params: float32 numpy array (host) or torch CUDA tensor; hidden 0
+        removes the model."""
+        if hidden == 0:
+            self._check(_get_lib().dc_aux_set_warm_start_model(self._h, 0, None, DC_MEM_HOST))
+            return
+        where = DC_MEM_DEVICE if _is_device(params) else DC_MEM_HOST
+        if where == DC_MEM_HOST:
+            params = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(_get_lib().dc_aux_set_warm_start_model(self._h, int(hidden), _ptr(params), where))
+
     def eval_points_noalloc(self, xy, out):
         """dc_eval_points_noalloc: xy [n, 2] and out [n, 3] float64 torch
         CUDA tensors; nothing is allocated by the call."""
@@ -287,3 +337,45 @@ def aux_tree_check(seg_xy, domain=(0.0, 0.0, 1.0, 1.0), leaf_size=64, max_depth=
 def kernel_launches() -> int:
     """Kernels launched by libdc_fmm in this process so far."""
     return int(_get_lib().dc_aux_kernel_launches())
+
+
+# ------------------------------------------------------------- network --
+def _stream(stream):
+    if stream is None and torch is not None and torch.cuda.is_available():
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(stream or 0)
+
+
+def mlp_param_count(n_in: int, hidden: int, n_out: int) -> int:
+    return int(_get_lib().dc_aux_mlp_param_count(n_in, hidden, n_out))
+
+
+def mlp_workspace_floats(n_in: int, hidden: int, n_out: int, batch: int) -> int:
+    return int(_get_lib().dc_aux_mlp_workspace_floats(n_in, hidden, n_out, batch))
+
+
+def mlp_forward(n_in, hidden, n_out, params, x, y, work, stream=None):
+    """dc_aux_mlp_forward on float32 torch CUDA tensors."""
+    st = _get_lib().dc_aux_mlp_forward(n_in, hidden, n_out, _ptr(params), int(x.shape[0]), _ptr(x),
+                                       _ptr(y), _ptr(work), _stream(stream))
+    if st != DC_OK:
+        raise DcError(st, "dc_aux_mlp_forward failed")
+    return y
+
+
+def mlp_loss_grad(n_in, hidden, n_out, params, x, target, grad, loss, work, stream=None):
+    """dc_aux_mlp_loss_grad on float32 torch CUDA tensors (loss: 1 element)."""
+    st = _get_lib().dc_aux_mlp_loss_grad(n_in, hidden, n_out, _ptr(params), int(x.shape[0]),
+                                         _ptr(x), _ptr(target), _ptr(grad), _ptr(loss), _ptr(work),
+                                         _stream(stream))
+    if st != DC_OK:
+        raise DcError(st, "dc_aux_mlp_loss_grad failed")
+
+
+def mlp_adam(params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """dc_aux_mlp_adam on float32 torch CUDA tensors."""
+    st = _get_lib().dc_aux_mlp_adam(int(params.numel()), _ptr(params), _ptr(grad), _ptr(m), _ptr(v),
+                                    float(lr), float(beta1), float(beta2), float(eps), int(step),
+                                    _stream(stream))
+    if st != DC_OK:
+        raise DcError(st, "dc_aux_mlp_adam failed")

@@ -40,6 +40,12 @@ struct dc_ctx {
     bool seg_density_valid = false;
     dc::GmresWork *gw = nullptr;
     std::unique_ptr<dc::Fmm> fmm;  // FMM forms
+    // learned warm start: network parameters, feature tables, buffers
+    int warm_hidden = 0;
+    DevBuf<float> warm_params, warm_feat, warm_pred, warm_work;
+    DevBuf<double> warm_ax, warm_a1;   // G_H x_pred, G_H 1
+    bool warm_a1_valid = false;
+    dc::PanelFeatures pfeat;
     ~dc_ctx() {
         if (gw) dc::gmres_work_destroy(gw);
     }
@@ -96,8 +102,16 @@ dc_status check_options(const dc_options &o, std::string &msg) {
         msg = "options: need gmres_tol > 0, 1 <= gmres_restart <= 4096, gmres_max_iter >= 1";
         return DC_ERR_ARG;
     }
-    if (o.x0_mode < DC_X0_ONES || o.x0_mode > DC_X0_USER) {
+    if (o.x0_mode < DC_X0_ONES || o.x0_mode > DC_X0_LEARNED) {
         msg = "options: unknown x0_mode";
+        return DC_ERR_ARG;
+    }
+    if (o.p_inner < 0 || o.p_inner > o.p) {
+        msg = "options: p_inner must be 0 (default) or in [1, p]";
+        return DC_ERR_ARG;
+    }
+    if (!(o.inner_tol >= 0.0 && o.inner_tol < 1.0)) {
+        msg = "options: inner_tol must be 0 (default) or in (0, 1)";
         return DC_ERR_ARG;
     }
     for (double d : o.domain)
@@ -318,8 +332,71 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
             return fail(ctx, st, msg);
         }
     }
+    DC_CK(ctx, ctx->pfeat.build(G, s), "panel features");
+    ctx->warm_a1_valid = false;
     DC_CK(ctx, cudaStreamSynchronize(s), "build_tree");
     ctx->state = 1;
+    return DC_OK;
+}
+
+// Learned warm start: features -> network -> sigma_p, then per channel the
+// x0 = alpha sigma_p + beta 1 of least residual ||b - G_H x0|| (two FP64
+// operator applications, G_H 1 cached per drawing).  The span holds 0 and the
+// paper's start 1, so the start is never worse than either (cold fallback:
+// alpha = 0 when the prediction does not help).
+dc_status warm_start(dc_ctx *ctx, dc_solve_stats *stats) {
+    cudaStream_t s = ctx->stream;
+    const int N = ctx->dg.N, g = ctx->dg.g;
+    const int rows = ctx->pfeat.rows(), F = dc::PanelFeatures::n_features(g), H = ctx->warm_hidden;
+    DC_CK(ctx, ctx->warm_feat.ensure(size_t(rows) * F), "alloc features");
+    DC_CK(ctx, ctx->warm_pred.ensure(size_t(rows) * g), "alloc prediction");
+    DC_CK(ctx, ctx->warm_work.ensure(dc_aux_mlp_workspace_floats(F, H, g, rows)), "alloc network");
+    DC_CK(ctx, ctx->warm_ax.ensure(size_t(3) * N), "alloc residual");
+    DC_CK(ctx, ctx->warm_a1.ensure(size_t(3) * N), "alloc residual");
+    DC_CK(ctx, ctx->pfeat.compute(ctx->dg, nullptr, ctx->warm_feat.ptr, nullptr, s), "features");
+    dc_status st = dc_aux_mlp_forward(F, H, g, ctx->warm_params.ptr, rows, ctx->warm_feat.ptr,
+                                      ctx->warm_pred.ptr, ctx->warm_work.ptr, s);
+    if (st != DC_OK) return fail(ctx, st, "solve_density: warm-start network failed");
+    DC_CK(ctx, ctx->pfeat.apply(ctx->warm_pred.ptr, ctx->sigma.ptr, s), "warm start");
+    auto apply = [&](const double *x, double *y) -> cudaError_t {
+        if (ctx->opt.form == DC_FORM_DENSE64) return dc::launch_dense_gemv(ctx->AG.ptr, N, x, y, s);
+        return ctx->fmm->apply_single_layer(x, y, s);
+    };
+    if (!ctx->warm_a1_valid) {          // G_H 1, once per drawing
+        const double zero[3] = {0, 0, 0}, one[3] = {1, 1, 1};
+        DC_CK(ctx, dc::vec_combine3(ctx->b.ptr, nullptr, ctx->warm_ax.ptr, N, zero, one, s), "warm start");
+        DC_CK(ctx, apply(ctx->warm_ax.ptr, ctx->warm_a1.ptr), "warm start");
+        ctx->warm_a1_valid = true;
+    }
+    DC_CK(ctx, apply(ctx->sigma.ptr, ctx->warm_ax.ptr), "warm start");
+    double pp[3], p1[3], q1[3], pb[3], qb[3], bb[3];
+    const double *Ap = ctx->warm_ax.ptr, *A1 = ctx->warm_a1.ptr, *b = ctx->b.ptr;
+    DC_CK(ctx, dc::vec_dots3(ctx->gw, Ap, Ap, N, pp, s), "warm start");
+    DC_CK(ctx, dc::vec_dots3(ctx->gw, Ap, A1, N, p1, s), "warm start");
+    DC_CK(ctx, dc::vec_dots3(ctx->gw, A1, A1, N, q1, s), "warm start");
+    DC_CK(ctx, dc::vec_dots3(ctx->gw, Ap, b, N, pb, s), "warm start");
+    DC_CK(ctx, dc::vec_dots3(ctx->gw, A1, b, N, qb, s), "warm start");
+    DC_CK(ctx, dc::vec_dots3(ctx->gw, b, b, N, bb, s), "warm start");
+    double al[3], be[3];
+    int mask = 0;
+    for (int c = 0; c < 3; ++c) {
+        double a = 0.0, q = 0.0;
+        const double det = pp[c] * q1[c] - p1[c] * p1[c];
+        if (det > 1e-12 * pp[c] * q1[c] && det > 0.0) {
+            a = (pb[c] * q1[c] - qb[c] * p1[c]) / det;
+            q = (pp[c] * qb[c] - p1[c] * pb[c]) / det;
+        } else if (q1[c] > 0.0) {
+            q = qb[c] / q1[c];          // the prediction adds nothing independent
+        }
+        if (!std::isfinite(a) || !std::isfinite(q)) a = q = 0.0;
+        al[c] = a;
+        be[c] = q;
+        if (a != 0.0) mask |= 1 << c;
+        const double r2 = std::max(0.0, bb[c] - a * pb[c] - q * qb[c]);
+        if (stats) stats->warm_resid[c] = bb[c] > 0.0 ? std::sqrt(r2 / bb[c]) : 0.0;
+    }
+    DC_CK(ctx, dc::vec_combine3(ctx->sigma.ptr, nullptr, ctx->sigma.ptr, N, al, be, s), "warm start");
+    if (stats) stats->used_warm = mask;
     return DC_OK;
 }
 
@@ -329,6 +406,8 @@ dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats)
     if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "solve_density: call build_tree first");
     if (ctx->opt.x0_mode == DC_X0_USER && !x0)
         return fail(ctx, DC_ERR_ARG, "solve_density: x0_mode is DC_X0_USER but x0 is NULL");
+    if (ctx->opt.x0_mode == DC_X0_LEARNED && ctx->warm_hidden <= 0)
+        return fail(ctx, DC_ERR_STATE, "solve_density: DC_X0_LEARNED needs a warm-start model");
     const int N = ctx->dg.N;
     cudaStream_t s = ctx->stream;
     if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -351,7 +430,7 @@ dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats)
     }
     DC_CK(ctx, dc::launch_rhs(ctx->dg, ctx->fmu.ptr, ctx->b.ptr, s), "rhs");
     DC_CK(ctx, cudaEventRecord(e1, s), "event");
-    // x0
+    auto t0 = std::chrono::steady_clock::now();   // x0 (warm start included) and GMRES
     size_t n3b = size_t(3) * N * sizeof(double);
     if (ctx->opt.x0_mode == DC_X0_USER) {
         for (size_t i = 0; i < size_t(3) * N; ++i)
@@ -359,6 +438,13 @@ dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats)
         DC_CK(ctx, cudaMemcpyAsync(ctx->sigma.ptr, x0, n3b, cudaMemcpyHostToDevice, s), "x0");
     } else if (ctx->opt.x0_mode == DC_X0_ZEROS) {
         DC_CK(ctx, cudaMemsetAsync(ctx->sigma.ptr, 0, n3b, s), "x0");
+    } else if (ctx->opt.x0_mode == DC_X0_LEARNED) {
+        auto w0 = std::chrono::steady_clock::now();
+        dc_status ws = warm_start(ctx, stats);
+        if (ws != DC_OK) return ws;
+        if (stats)
+            stats->ms_warm =
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
     } else {
         std::vector<double> ones(size_t(3) * N, 1.0);
         DC_CK(ctx, cudaMemcpyAsync(ctx->sigma.ptr, ones.data(), n3b, cudaMemcpyHostToDevice, s),
@@ -368,7 +454,6 @@ dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats)
     ctx->seg_density_valid = false;
     dc::GmresResult gr;
     std::string msg;
-    auto t0 = std::chrono::steady_clock::now();
     cudaError_t ce;
     if (ctx->opt.form == DC_FORM_DENSE64) {
         DenseOp op;
@@ -666,6 +751,81 @@ dc_status dc_eval_points(dc_ctx *ctx, int n, const void *xy, int xy_where, void 
         DC_CK(ctx, cudaStreamSynchronize(s), "eval_points");
     }
     DC_CK(ctx, cudaGetLastError(), "eval_points");
+    return DC_OK;
+}
+
+dc_status dc_aux_feature_dims(dc_ctx *ctx, int *rows, int *n_features, int *n_out) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (ctx->state < 1 || !ctx->pfeat.ready())
+        return fail(ctx, DC_ERR_STATE, "feature_dims: call build_tree first");
+    if (rows) *rows = ctx->pfeat.rows();
+    if (n_features) *n_features = dc::PanelFeatures::n_features(ctx->dg.g);
+    if (n_out) *n_out = ctx->dg.g;
+    return DC_OK;
+}
+
+dc_status dc_aux_panel_features(dc_ctx *ctx, float *feat_dev, float *target_dev) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (ctx->state < 1 || !ctx->pfeat.ready())
+        return fail(ctx, DC_ERR_STATE, "panel_features: call build_tree first");
+    if (target_dev && ctx->state < 2)
+        return fail(ctx, DC_ERR_STATE, "panel_features: targets need a density");
+    if (!feat_dev) return fail(ctx, DC_ERR_ARG, "panel_features: NULL feature buffer");
+    DC_CK(ctx,
+          ctx->pfeat.compute(ctx->dg, target_dev ? ctx->sigma.ptr : nullptr, feat_dev, target_dev,
+                             ctx->stream),
+          "panel_features");
+    return DC_OK;
+}
+
+dc_status dc_aux_set_warm_start_model(dc_ctx *ctx, int hidden, const float *params, int where) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (hidden == 0) {
+        ctx->warm_hidden = 0;
+        ctx->warm_params.release();
+        return DC_OK;
+    }
+    if (hidden < 1 || hidden > 4096 || !params || (where != DC_MEM_HOST && where != DC_MEM_DEVICE))
+        return fail(ctx, DC_ERR_ARG, "set_warm_start_model: bad arguments");
+    const int g = ctx->opt.g;
+    size_t n = dc_aux_mlp_param_count(dc::PanelFeatures::n_features(g), hidden, g);
+    if (where == DC_MEM_HOST)
+        for (size_t i = 0; i < n; ++i)
+            if (!std::isfinite(params[i]))
+                return fail(ctx, DC_ERR_ARG, "set_warm_start_model: non-finite parameter");
+    DC_CK(ctx, ctx->warm_params.alloc(n), "alloc model");
+    DC_CK(ctx,
+          cudaMemcpyAsync(ctx->warm_params.ptr, params, n * sizeof(float),
+                          where == DC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                          ctx->stream),
+          "copy model");
+    DC_CK(ctx, cudaStreamSynchronize(ctx->stream), "copy model");
+    ctx->warm_hidden = hidden;
+    return DC_OK;
+}
+
+dc_status dc_aux_apply_operator(dc_ctx *ctx, int op, int inner, const double *x, double *y) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "apply_operator: call build_tree first");
+    if ((op != 0 && op != 1) || !x || !y || x == y)
+        return fail(ctx, DC_ERR_ARG, "apply_operator: need op 0 or 1 and distinct x, y");
+    if (inner && (ctx->opt.form != DC_FORM_FMM32 || op != 0))
+        return fail(ctx, DC_ERR_UNSUPPORTED, "apply_operator: inner needs DC_FORM_FMM32 and op 0");
+    cudaStream_t s = ctx->stream;
+    const int N = ctx->dg.N;
+    if (ctx->opt.form == DC_FORM_DENSE64) {
+        DC_CK(ctx, dc::launch_dense_gemv(op == 0 ? ctx->AG.ptr : ctx->AF.ptr, N, x, y, s), "apply_operator");
+    } else if (inner) {
+        DC_CK(ctx, ctx->fmm->apply_inner(x, y, s), "apply_operator");
+    } else if (op == 0) {
+        DC_CK(ctx, ctx->fmm->apply_single_layer(x, y, s), "apply_operator");
+    } else {
+        DC_CK(ctx, ctx->fmm->apply_double_layer(x, y, s), "apply_operator");
+    }
     return DC_OK;
 }
 

@@ -129,6 +129,27 @@ cudaError_t launch_write_outputs_f32(const float *u, long long n, void *rgb, int
 cudaError_t launch_mu(const DevGeom &G, double *mu, cudaStream_t st);
 cudaError_t launch_rhs(const DevGeom &G, const double *Fmu, double *b, cudaStream_t st);
 
+// Per-panel features of the learned warm start (features.cu): one row per
+// (panel, colour channel), n_features(g) floats; targets are the panel's g
+// node densities times its arc length.
+class PanelFeatures {
+public:
+    static int n_features(int g) { return 22 * g + 32; }
+    cudaError_t build(const Geometry &G, cudaStream_t st);
+    bool ready() const { return P_ > 0; }
+    int rows() const { return 3 * P_; }
+    // feat [rows][n_features]; target [rows][g] (when sigma and target are given)
+    cudaError_t compute(const DevGeom &D, const double *sigma, float *feat, float *target,
+                        cudaStream_t st) const;
+    // sigma [N][3] from predictions pred [rows][g]
+    cudaError_t apply(const float *pred, double *sigma, cudaStream_t st) const;
+
+private:
+    int P_ = 0, g_ = 0;
+    DevBuf<double> pc_, pt_, plen_, nn_;
+    DevBuf<int> nbr_;
+};
+
 // --------------------------------------------------------------- GMRES --
 // Matrix-free operator y = A x on [N][3] FP64 vectors (all 3 channels).
 struct Operator {
@@ -167,6 +188,12 @@ cudaError_t vec_residual(const double *b, const double *Ax, double *r, int n3, c
 cudaError_t vec_axpy(double *x, const double *d, int n3, cudaStream_t st);
 // zero the channels c with keep[c] == 0
 cudaError_t vec_mask3(double *v, int N, const int keep[3], cudaStream_t st);
+// y[:, c] = a[c] x[:, c] + b[c] z[:, c] (z == nullptr: a vector of ones); y may alias x
+cudaError_t vec_combine3(const double *x, const double *z, double *y, int N, const double a[3],
+                         const double b[3], cudaStream_t st);
+// host_out[c] = u[:, c] . v[:, c] (synchronises the stream)
+cudaError_t vec_dots3(GmresWork *w, const double *u, const double *v, int N, double host_out[3],
+                      cudaStream_t st);
 // host_out[c] = || v[:, c] ||_2 (synchronises the stream)
 cudaError_t vec_norms3(GmresWork *w, const double *v, int N, double host_out[3], cudaStream_t st);
 

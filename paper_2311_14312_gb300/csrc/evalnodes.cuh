@@ -27,7 +27,7 @@ template <typename T> struct NodeArgs {
     const double *cc64;            // [cells][2]
     const T *pw;                   // arc weight
     const T *iw, *logw;
-    const int4 *items;             // (leaf, first target, count, 0)
+    const int4 *items;             // (leaf, first target, count, list-1 pieces)
     const double *q64;             // [n][2] sorted targets
     const int *own1, *own2, *perm; // own segments (may be null), output order
     int P1;
@@ -40,6 +40,89 @@ template <typename T> struct NodeArgs {
 __device__ __forceinline__ float elog(float x) { return __logf(x); }
 __device__ __forceinline__ double elog(double x) { return log(x); }
 
+// Far field into the lane sums: target j's L2P (Eq. 64) on lane 8 j mod 32,
+// its list-3 M2P terms (Eq. 61) split over the lanes.  qx, qy: targets
+// relative to the leaf centre.
+constexpr int kPer = kNodeItem / kWarps;   // targets per warp
+
+template <typename T>
+__device__ __forceinline__ void far_into(const NodeArgs<T> &a, int leaf, int t0, int nt, int warp, int lane,
+                                         const T (&qx)[kPer], const T (&qy)[kPer], T (&acc)[kPer][3]) {
+    using C = typename passes::V2<T>::type;
+    const T k2pi = T(0.15915494309189533577);
+    const int P1 = a.P1;
+    const T iwl = a.iw[leaf];
+    const C *Lc = a.L + (size_t)leaf * 3 * P1;
+    const int w0 = a.w_ptr[leaf], w1 = a.w_ptr[leaf + 1];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        if (warp + kWarps * j >= nt) break;
+        const int ti = t0 + warp + kWarps * j;
+        T e0 = 0, e1 = 0, e2 = 0;
+        if (lane == ((8 * j) & 31)) {
+            C z = passes::mk<T>(qx[j] * iwl, qy[j] * iwl);
+            C s0 = Lc[P1 - 1], s1 = Lc[2 * P1 - 1], s2 = Lc[3 * P1 - 1];
+            for (int k = P1 - 2; k >= 0; --k) {
+                s0 = passes::cadd(passes::cmul(s0, z), Lc[k]);
+                s1 = passes::cadd(passes::cmul(s1, z), Lc[P1 + k]);
+                s2 = passes::cadd(passes::cmul(s2, z), Lc[2 * P1 + k]);
+            }
+            e0 = s0.x;
+            e1 = s1.x;
+            e2 = s2.x;
+        }
+        if (w0 + lane < w1) {
+            const double tx = a.q64[2 * ti], ty = a.q64[2 * ti + 1];
+            for (int e = w0 + lane; e < w1; e += 32) {
+                const int src = a.w_idx[e];
+                const T iws = a.iw[src];
+                const T zx = (T)(tx - a.cc64[2 * src]) * iws;
+                const T zy = (T)(ty - a.cc64[2 * src + 1]) * iws;
+                const C iz = passes::cinv(passes::mk<T>(zx, zy));
+                const T lz = T(0.5) * elog(zx * zx + zy * zy) + a.logw[src];
+                const C *Ms = a.M + (size_t)src * 3 * P1;
+                C m0 = passes::cscl(Ms[P1 - 1], T(1) / (P1 - 1));
+                C m1 = passes::cscl(Ms[2 * P1 - 1], T(1) / (P1 - 1));
+                C m2 = passes::cscl(Ms[3 * P1 - 1], T(1) / (P1 - 1));
+                for (int k = P1 - 2; k >= 1; --k) {
+                    const T ik = T(1) / k;
+                    m0 = passes::cadd(passes::cmul(m0, iz), passes::cscl(Ms[k], ik));
+                    m1 = passes::cadd(passes::cmul(m1, iz), passes::cscl(Ms[P1 + k], ik));
+                    m2 = passes::cadd(passes::cmul(m2, iz), passes::cscl(Ms[2 * P1 + k], ik));
+                }
+                m0 = passes::cmul(m0, iz);
+                m1 = passes::cmul(m1, iz);
+                m2 = passes::cmul(m2, iz);
+                e0 += m0.x - lz * Ms[0].x;
+                e1 += m1.x - lz * Ms[P1].x;
+                e2 += m2.x - lz * Ms[2 * P1].x;
+            }
+        }
+        acc[j][0] += e0 * k2pi;
+        acc[j][1] += e1 * k2pi;
+        acc[j][2] += e2 * k2pi;
+    }
+}
+
+// Fixed butterfly over the lanes, then lane 0 writes its targets.
+template <typename T>
+__device__ __forceinline__ void reduce_write(const NodeArgs<T> &a, int t0, int nt, int warp, int lane,
+                                             T (&acc)[kPer][3]) {
+#pragma unroll
+    for (int j = 0; j < kPer; ++j)
+        for (int c = 0; c < 3; ++c)
+            for (int off = 16; off > 0; off >>= 1) acc[j][c] += __shfl_xor_sync(0xffffffffu, acc[j][c], off);
+    if (lane != 0) return;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        if (warp + kWarps * j >= nt) break;
+        const int o = a.perm[t0 + warp + kWarps * j];
+        a.out[3 * (size_t)o + 0] = (double)acc[j][0];
+        a.out[3 * (size_t)o + 1] = (double)acc[j][1];
+        a.out[3 * (size_t)o + 2] = (double)acc[j][2];
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(32 * kWarps) eval_nodes_kernel(NodeArgs<T> a) {
     using C = typename passes::V2<T>::type;
@@ -50,7 +133,6 @@ __global__ void __launch_bounds__(32 * kWarps) eval_nodes_kernel(NodeArgs<T> a) 
     const int leaf = it.x, t0 = it.y, nt = it.z;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double cx = a.cc64[2 * leaf], cy = a.cc64[2 * leaf + 1];
-    constexpr int kPer = kNodeItem / kWarps;   // targets per warp
     T qx[kPer], qy[kPer], acc[kPer][3];
     int o1[kPer], o2[kPer];
 #pragma unroll
@@ -109,62 +191,228 @@ __global__ void __launch_bounds__(32 * kWarps) eval_nodes_kernel(NodeArgs<T> a) 
             }
         }
     }
-    // butterfly over the lanes (fixed order)
-#pragma unroll
-    for (int j = 0; j < kPer; ++j)
-        for (int c = 0; c < 3; ++c)
-            for (int off = 16; off > 0; off >>= 1) acc[j][c] += __shfl_xor_sync(0xffffffffu, acc[j][c], off);
-    // far field by lane 0 of each warp
-    if (lane != 0) return;
-    const int P1 = a.P1;
+    far_into<T>(a, leaf, t0, nt, warp, lane, qx, qy, acc);
+    reduce_write<T>(a, t0, nt, warp, lane, acc);
+}
+
+// ------------------------------------------------- near-field operator --
+// The list-1 (near-field) part of the node operator is the same linear map at
+// every GMRES iteration, so its coefficients are formed once per drawing, in
+// FP64, and kept resident: for work item it (targets of one leaf), target tl
+// of the item and the pl-th piece of the leaf's list 1 (in list order),
+//   cg[off[it] + tl nU + pl] = -(w_p / 2 pi) int_piece log|p - q| dS
+//   cf[off[it] + tl nU + pl] = -(w_p / 2 pi) phi(q, piece)
+// with nU = items[it].w pieces in the list; a node's own segment has phi = 0
+// (Eq. 53) and the log integral of the same antiderivative (Eq. 52).  One
+// application is then a gather-multiply-add over the coefficients, which
+// stream from HBM once per matvec (no transcendental functions).
+static __global__ void __launch_bounds__(32 * kWarps) near_coef_kernel(NodeArgs<double> a,
+                                                                 const long long *__restrict__ off,
+                                                                 double *__restrict__ cg,
+                                                                 double *__restrict__ cf) {
+    __shared__ double sx1[kStageN], sy1[kStageN], sx2[kStageN], sy2[kStageN], swg[kStageN];
+    __shared__ int sseg[kStageN];
+    const int4 it = a.items[blockIdx.x];
+    const int leaf = it.x, t0 = it.y, nt = it.z, nU = it.w;
+    const long long base = off[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double cx = a.cc64[2 * leaf], cy = a.cc64[2 * leaf + 1];
+    double qx[kPer], qy[kPer];
+    int o1[kPer], o2[kPer];
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
-        if (warp + kWarps * j >= nt) break;
-        const int ti = t0 + warp + kWarps * j;
-        T e0 = 0, e1 = 0, e2 = 0;
-        {
-            const T iw = a.iw[leaf];
-            C z = passes::mk<T>(qx[j] * iw, qy[j] * iw);
-            const C *Lc = a.L + (size_t)leaf * 3 * P1;
-            C s0 = Lc[P1 - 1], s1 = Lc[2 * P1 - 1], s2 = Lc[3 * P1 - 1];
-            for (int k = P1 - 2; k >= 0; --k) {
-                s0 = passes::cadd(passes::cmul(s0, z), Lc[k]);
-                s1 = passes::cadd(passes::cmul(s1, z), Lc[P1 + k]);
-                s2 = passes::cadd(passes::cmul(s2, z), Lc[2 * P1 + k]);
-            }
-            e0 = s0.x;
-            e1 = s1.x;
-            e2 = s2.x;
-        }
-        for (int e = a.w_ptr[leaf]; e < a.w_ptr[leaf + 1]; ++e) {
-            const int src = a.w_idx[e];
-            const T iws = a.iw[src];
-            const T zx = (T)(a.q64[2 * ti] - a.cc64[2 * src]) * iws;
-            const T zy = (T)(a.q64[2 * ti + 1] - a.cc64[2 * src + 1]) * iws;
-            const C iz = passes::cinv(passes::mk<T>(zx, zy));
-            const T lz = T(0.5) * elog(zx * zx + zy * zy) + a.logw[src];
-            const C *Ms = a.M + (size_t)src * 3 * P1;
-            C m0 = passes::cscl(Ms[P1 - 1], T(1) / (P1 - 1));
-            C m1 = passes::cscl(Ms[2 * P1 - 1], T(1) / (P1 - 1));
-            C m2 = passes::cscl(Ms[3 * P1 - 1], T(1) / (P1 - 1));
-            for (int k = P1 - 2; k >= 1; --k) {
-                const T ik = T(1) / k;
-                m0 = passes::cadd(passes::cmul(m0, iz), passes::cscl(Ms[k], ik));
-                m1 = passes::cadd(passes::cmul(m1, iz), passes::cscl(Ms[P1 + k], ik));
-                m2 = passes::cadd(passes::cmul(m2, iz), passes::cscl(Ms[2 * P1 + k], ik));
-            }
-            m0 = passes::cmul(m0, iz);
-            m1 = passes::cmul(m1, iz);
-            m2 = passes::cmul(m2, iz);
-            e0 += m0.x - lz * Ms[0].x;
-            e1 += m1.x - lz * Ms[P1].x;
-            e2 += m2.x - lz * Ms[2 * P1].x;
-        }
-        const int o = a.perm[ti];
-        a.out[3 * (size_t)o + 0] = (double)(acc[j][0] + e0 * k2pi);
-        a.out[3 * (size_t)o + 1] = (double)(acc[j][1] + e1 * k2pi);
-        a.out[3 * (size_t)o + 2] = (double)(acc[j][2] + e2 * k2pi);
+        int ti = t0 + warp + kWarps * j;
+        bool ok = (warp + kWarps * j) < nt;
+        qx[j] = ok ? a.q64[2 * ti] - cx : 0.0;
+        qy[j] = ok ? a.q64[2 * ti + 1] - cy : 0.0;
+        o1[j] = (ok && a.own1) ? a.own1[ti] : -1;
+        o2[j] = (ok && a.own2) ? a.own2[ti] : -1;
     }
+    const double k2pi = 0.15915494309189533577;
+    int pl0 = 0;
+    for (int e = a.u_ptr[leaf]; e < a.u_ptr[leaf + 1]; ++e) {
+        const int src = a.u_idx[e];
+        const int p0 = a.pstart[src], pn = a.pcount[src];
+        for (int b = 0; b < pn; b += kStageN) {
+            const int cnt = min(kStageN, pn - b);
+            __syncthreads();
+            for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
+                const int i = p0 + b + s;
+                const double *P = a.pc64 + 4 * (size_t)i;
+                sx1[s] = P[0] - cx;
+                sy1[s] = P[1] - cy;
+                sx2[s] = P[2] - cx;
+                sy2[s] = P[3] - cy;
+                swg[s] = -a.pw[i] * k2pi;
+                sseg[s] = a.pseg[i];
+            }
+            __syncthreads();
+            for (int s = lane; s < cnt; s += 32) {
+                const double x1 = sx1[s], y1 = sy1[s], x2 = sx2[s], y2 = sy2[s];
+                const double dx = x2 - x1, dy = y2 - y1;
+                const double len = sqrt(dx * dx + dy * dy), ilen = 1.0 / len;
+                const int seg = sseg[s];
+                const double wg = swg[s];
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) {
+                    const int tl = warp + kWarps * j;
+                    if (tl >= nt) break;
+                    const double ax = x1 - qx[j], ay = y1 - qy[j], bx = x2 - qx[j], by = y2 - qy[j];
+                    const double cr = ax * by - ay * bx, dt = ax * bx + ay * by;
+                    const bool own = (seg == o1[j]) || (seg == o2[j]);
+                    const double phi = own ? 0.0 : atan2(cr, dt);
+                    const double ra2 = ax * ax + ay * ay, rb2 = bx * bx + by * by;
+                    const double s1 = (ax * dx + ay * dy) * ilen, s2 = s1 + len;
+                    const double la = ra2 > 0.0 ? s1 * log(ra2) : 0.0;
+                    const double lb = rb2 > 0.0 ? s2 * log(rb2) : 0.0;
+                    const double il = 0.5 * (lb - la) - len + cr * ilen * phi;
+                    const long long idx = base + (long long)tl * nU + pl0 + s;
+                    cg[idx] = il * wg;
+                    cf[idx] = phi * wg;
+                }
+            }
+            pl0 += cnt;
+        }
+    }
+}
+
+// Far-field coefficients of the node targets, formed once per drawing in FP64:
+// the L2P (Eq. 64) and list-3 M2P (Eq. 61) sums are linear in the expansion
+// coefficients, u += Re sum_k a_k X_k with
+//   block 0 (the leaf's L):      a_k = z^k / 2pi,       z = (q - c_leaf) / w_leaf
+//   block b (list-3 source b-1): a_0 = -(log|z| + log w_src) / 2pi (times Re M_0),
+//                                a_k = z^-k / (2pi k),  z = (q - c_src) / w_src
+// stored per target as (1 + nW) blocks of P1 complex values from block
+// off[item] + tl (1 + nW); nW = the leaf's list-3 length.
+static __global__ void __launch_bounds__(32 * kWarps) far_coef_kernel(NodeArgs<double> a,
+                                                                      const long long *__restrict__ off,
+                                                                      double2 *__restrict__ cf) {
+    const int4 it = a.items[blockIdx.x];
+    const int leaf = it.x, t0 = it.y, nt = it.z;
+    const int P1 = a.P1;
+    const int w0 = a.w_ptr[leaf], nW = a.w_ptr[leaf + 1] - w0;
+    const int nb = 1 + nW;
+    const long long base = off[blockIdx.x] * P1;
+    const double k2pi = 0.15915494309189533577;
+    for (int u = threadIdx.x; u < nt * nb; u += blockDim.x) {
+        const int tl = u / nb, b = u - tl * nb;
+        const int ti = t0 + tl;
+        double2 *row = cf + base + ((long long)tl * nb + b) * P1;
+        const double qx = a.q64[2 * ti], qy = a.q64[2 * ti + 1];
+        if (b == 0) {
+            const double iw = a.iw[leaf];
+            const double zx = (qx - a.cc64[2 * leaf]) * iw, zy = (qy - a.cc64[2 * leaf + 1]) * iw;
+            double px = k2pi, py = 0.0;
+            for (int k = 0; k < P1; ++k) {
+                row[k] = make_double2(px, py);
+                const double nx = px * zx - py * zy;
+                py = px * zy + py * zx;
+                px = nx;
+            }
+        } else {
+            const int src = a.w_idx[w0 + b - 1];
+            const double iws = a.iw[src];
+            const double zx = (qx - a.cc64[2 * src]) * iws, zy = (qy - a.cc64[2 * src + 1]) * iws;
+            const double r2 = zx * zx + zy * zy;
+            const double ix = zx / r2, iy = -zy / r2;          // 1 / z
+            row[0] = make_double2(-k2pi * (0.5 * log(r2) + a.logw[src]), 0.0);
+            double px = ix, py = iy;                             // z^-k
+            for (int k = 1; k < P1; ++k) {
+                row[k] = make_double2(k2pi * px / k, k2pi * py / k);
+                const double nx = px * ix - py * iy;
+                py = px * iy + py * ix;
+                px = nx;
+            }
+        }
+    }
+}
+
+// Far field from stored coefficients into the lane sums: lanes split the
+// (block, k) terms of each target.
+template <typename T>
+__device__ __forceinline__ void far_rows_into(const NodeArgs<T> &a, const typename passes::V2<T>::type *__restrict__ cf,
+                                              long long base, int leaf, int nt, int warp, int lane,
+                                              T (&acc)[kPer][3]) {
+    using C = typename passes::V2<T>::type;
+    const int P1 = a.P1;
+    const int w0 = a.w_ptr[leaf], nb = 1 + a.w_ptr[leaf + 1] - w0;
+    const int nterm = nb * P1;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int tl = warp + kWarps * j;
+        if (tl >= nt) break;
+        const C *row = cf + base + (long long)tl * nterm;
+        for (int u = lane; u < nterm; u += 32) {
+            const int b = u / P1, k = u - b * P1;
+            const int src = b == 0 ? leaf : a.w_idx[w0 + b - 1];
+            const C *X = (b == 0 ? a.L : a.M) + (size_t)src * 3 * P1 + k;
+            const C co = row[u];
+            const C x0 = X[0], x1 = X[P1], x2 = X[2 * P1];
+            acc[j][0] += co.x * x0.x - co.y * x0.y;
+            acc[j][1] += co.x * x1.x - co.y * x1.y;
+            acc[j][2] += co.x * x2.x - co.y * x2.y;
+        }
+    }
+}
+
+// Node operator with the near field from stored coefficients (near_coef_kernel
+// layout): y = sum_pl coef * dens[seg(pl)] + far field (L2P, list-3 M2P),
+// the far field from stored coefficients too when far != nullptr.
+template <typename T>
+__global__ void __launch_bounds__(32 * kWarps) near_apply_kernel(NodeArgs<T> a, const long long *__restrict__ off,
+                                                                  const T *__restrict__ coef,
+                                                                  const T *__restrict__ dens,
+                                                                  const long long *__restrict__ far_off = nullptr,
+                                                                  const typename passes::V2<T>::type *__restrict__ far = nullptr) {
+    __shared__ T sd[3][kStageN];
+    const int4 it = a.items[blockIdx.x];
+    const int leaf = it.x, t0 = it.y, nt = it.z, nU = it.w;
+    const long long base = off[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double cx = a.cc64[2 * leaf], cy = a.cc64[2 * leaf + 1];
+    T qx[kPer], qy[kPer], acc[kPer][3];
+    const T *row[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int tl = warp + kWarps * j;
+        const int ti = t0 + tl;
+        bool ok = tl < nt;
+        qx[j] = ok ? (T)(a.q64[2 * ti] - cx) : T(0);
+        qy[j] = ok ? (T)(a.q64[2 * ti + 1] - cy) : T(0);
+        row[j] = coef + base + (long long)(ok ? tl : 0) * nU;
+        acc[j][0] = acc[j][1] = acc[j][2] = T(0);
+    }
+    int pl0 = 0;
+    for (int e = a.u_ptr[leaf]; e < a.u_ptr[leaf + 1]; ++e) {
+        const int src = a.u_idx[e];
+        const int p0 = a.pstart[src], pn = a.pcount[src];
+        for (int b = 0; b < pn; b += kStageN) {
+            const int cnt = min(kStageN, pn - b);
+            __syncthreads();
+            for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
+                const int seg = a.pseg[p0 + b + s];
+                for (int c = 0; c < 3; ++c) sd[c][s] = dens[3 * (size_t)seg + c];
+            }
+            __syncthreads();
+            for (int s = lane; s < cnt; s += 32) {
+                const T d0 = sd[0][s], d1 = sd[1][s], d2 = sd[2][s];
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) {
+                    if (warp + kWarps * j >= nt) break;
+                    const T cfv = row[j][pl0 + s];
+                    acc[j][0] += cfv * d0;
+                    acc[j][1] += cfv * d1;
+                    acc[j][2] += cfv * d2;
+                }
+            }
+            pl0 += cnt;
+        }
+    }
+    if (far)
+        far_rows_into<T>(a, far, far_off[blockIdx.x] * a.P1, leaf, nt, warp, lane, acc);
+    else
+        far_into<T>(a, leaf, t0, nt, warp, lane, qx, qy, acc);
+    reduce_write<T>(a, t0, nt, warp, lane, acc);
 }
 
 }  // namespace evalnodes

@@ -326,46 +326,45 @@ cudaError_t Fmm::Impl::passes(const double *sb, const double *mb, int use_s, int
     if ((e = cudaMemsetAsync(Lm2l.ptr, 0, ebytes, st)) != cudaSuccess) return e;
     passes::TreeView<double> tv = view64();
     passes::PiecesF64 ps{pc.ptr, cc.ptr};
-    int th = P1 <= 32 ? 32 : 64;
     if (n_p2m > 0) {
         passes::p2m_kernel<double, passes::PiecesF64><<<n_p2m, passes::kChunk, passes::p2m_smem<double>(P1), st>>>(
-            tv, ps, p2m_leaves.ptr, sb, mb, use_s, use_m, P1, M.ptr);
+            tv, ps, p2m_leaves.ptr, sb, mb, use_s, use_m, P1, M.ptr,
+            rows_ready ? p2m_g64.ptr : nullptr, rows_ready && use_m ? p2m_f64.ptr : nullptr);
         note_launch();
     }
     for (int l = tree.depth - 1; l >= 2; --l) {
-        int lo = m2m_ptr[l], hi = m2m_ptr[l + 1];
-        if (hi > lo) {
-            passes::m2m_kernel<double><<<hi - lo, th, 0, st>>>(tv, m2m_cells.ptr + lo, P1, m2m.ptr, M.ptr);
-            note_launch();
-        }
+        const int lo = m2m_ptr[l], n = m2m_ptr[l + 1] - lo;
+        if (n <= 0) continue;
+        passes::m2m_kernel<double><<<(n + passes::kLevelWarps - 1) / passes::kLevelWarps, 32 * passes::kLevelWarps, 0, st>>>(
+            child0.ptr, m2m_cells.ptr + lo, n, P1, m2m.ptr, M.ptr);
+        note_launch();
     }
     if (sc.n_m2l > 0) {
-        int grid = std::min((sc.n_m2l + passes::kM2LSlots - 1) / passes::kM2LSlots, 4 * n_sms);
-        passes::m2l_kernel<double><<<grid, 32 * passes::kM2LSlots, passes::m2l_smem<double>(P1), st>>>(
-            tv, sc.m2l.ptr, sc.n_m2l, P1, base64.ptr, M.ptr, Lm2l.ptr);
+        int grid = std::min((sc.n_m2l + passes::kM2LffWarps - 1) / passes::kM2LffWarps, 4 * n_sms);
+        passes::m2l_ff_kernel<<<grid, 32 * passes::kM2LffWarps, passes::m2l_ff_smem(P1), st>>>(
+            tv, sc.m2l.ptr, sc.n_m2l, P1, baseff.ptr, M.ptr, Lm2l.ptr);
         note_launch();
     }
     if (sc.n_p2l > 0) {
         passes::p2l_kernel<double, passes::PiecesF64><<<sc.n_p2l, passes::kChunk, passes::p2l_smem<double>(P1), st>>>(
-            tv, ps, sc.p2l.ptr, sb, mb, use_s, use_m, P1, Lm2l.ptr);
+            tv, ps, sc.p2l.ptr, sb, mb, use_s, use_m, P1, Lm2l.ptr, rows_ready ? p2l_off.ptr : nullptr,
+            rows_ready ? p2l_g64.ptr : nullptr, rows_ready && use_m ? p2l_f64.ptr : nullptr);
         note_launch();
     }
-    for (int l = 2; l <= tree.depth; ++l) {
-        int lo = sc.l2l_ptr[l], hi = sc.l2l_ptr[l + 1];
-        if (hi > lo) {
-            passes::l2l_kernel<double><<<(hi - lo + 3) / 4, 128, 0, st>>>(
-                tv, sc.l2l.ptr + lo, hi - lo, l, P1, l2l.ptr, Lm2l.ptr, L.ptr);
-            note_launch();
-        }
+    for (int l = 2; l <= tree.depth; ++l) {   // per level: FP64 work per cell once
+        const int lo = sc.l2l_ptr[l], n = sc.l2l_ptr[l + 1] - lo;
+        if (n <= 0) continue;
+        passes::l2l_kernel<double><<<(n + passes::kLevelWarps - 1) / passes::kLevelWarps, 32 * passes::kLevelWarps, 0, st>>>(
+            tv, sc.l2l.ptr + lo, n, l, P1, l2l.ptr, Lm2l.ptr, L.ptr);
+        note_launch();
     }
     return cudaGetLastError();
 }
 
-cudaError_t Fmm::Impl::eval_list64(const int4 *items, int n_items, const double *q64,
-                                   const int *own1, const int *own2, const int *perm,
-                                   const double *sb, const double *mb, int use_s, int use_m,
-                                   double *out, cudaStream_t st) {
-    if (n_items == 0) return cudaSuccess;
+evalnodes::NodeArgs<double> Fmm::Impl::node_args64(const int4 *items, const double *q64, const int *own1,
+                                                    const int *own2, const int *perm, const double *sb,
+                                                    const double *mb, int use_s, int use_m,
+                                                    double *out) const {
     evalnodes::NodeArgs<double> a;
     a.u_ptr = u_ptr.ptr;
     a.u_idx = u_idx.ptr;
@@ -392,6 +391,15 @@ cudaError_t Fmm::Impl::eval_list64(const int4 *items, int n_items, const double 
     a.use_s = use_s;
     a.use_m = use_m;
     a.out = out;
+    return a;
+}
+
+cudaError_t Fmm::Impl::eval_list64(const int4 *items, int n_items, const double *q64,
+                                   const int *own1, const int *own2, const int *perm,
+                                   const double *sb, const double *mb, int use_s, int use_m,
+                                   double *out, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    evalnodes::NodeArgs<double> a = node_args64(items, q64, own1, own2, perm, sb, mb, use_s, use_m, out);
     evalnodes::eval_nodes_kernel<double><<<n_items, 32 * evalnodes::kWarps, 0, st>>>(a);
     note_launch();
     return cudaGetLastError();
@@ -402,8 +410,138 @@ cudaError_t Fmm::Impl::apply_nodes(const double *x, double *y, bool single, cuda
     if (e != cudaSuccess) return e;
     int us = single ? 1 : 0, um = single ? 0 : 1;
     if ((e = passes(sbar.ptr, mbar.ptr, us, um, st, sched_nodes)) != cudaSuccess) return e;
+    if (near_ready && n_nt_items4 > 0) {
+        evalnodes::NodeArgs<double> a = node_args64(nt_items4.ptr, nt_xy.ptr, nt_own1.ptr, nt_own2.ptr,
+                                                    nt_perm.ptr, sbar.ptr, mbar.ptr, us, um, y);
+        evalnodes::near_apply_kernel<double><<<n_nt_items4, 32 * evalnodes::kWarps, 0, st>>>(
+            a, near_off.ptr, single ? near_g64.ptr : near_f64.ptr, single ? sbar.ptr : mbar.ptr,
+            far_ready ? far_off.ptr : nullptr, far_ready ? far64.ptr : nullptr);
+        note_launch();
+        return cudaGetLastError();
+    }
     return eval_list64(nt_items4.ptr, n_nt_items4, nt_xy.ptr, nt_own1.ptr, nt_own2.ptr, nt_perm.ptr,
                        sbar.ptr, mbar.ptr, us, um, y, st);
+}
+
+namespace {
+__global__ void narrow_real_kernel(const double *__restrict__ a, float *__restrict__ b, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+}  // namespace
+
+namespace {
+// dst[r][k] = (float2) src[r][k] for k < P1d (the low orders of each row)
+__global__ void narrow_rows_kernel(const double2 *__restrict__ src, int P1s, float2 *__restrict__ dst, int P1d,
+                                   long long nrows) {
+    const long long n = nrows * P1d;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / P1d;
+        const int k = int(i - r * P1d);
+        const double2 v = src[r * P1s + k];
+        dst[i] = make_float2((float)v.x, (float)v.y);
+    }
+}
+}  // namespace
+
+// The near-field coefficients of the node operator, once per drawing, when
+// they fit comfortably in device memory (else the near field is evaluated
+// from the geometry at every application).
+cudaError_t Fmm::Impl::build_near(cudaStream_t st) {
+    near_ready = false;
+    if (near_total <= 0 || n_nt_items4 == 0) return cudaSuccess;
+    const size_t need = (size_t)near_total * (2 * sizeof(double) + (fp32 ? sizeof(float) : 0));
+    size_t fr = 0, tot = 0;
+    cudaError_t e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) return e;
+    if (need > fr / 4) return cudaSuccess;
+    if ((e = near_g64.alloc((size_t)near_total)) != cudaSuccess) return e;
+    if ((e = near_f64.alloc((size_t)near_total)) != cudaSuccess) return e;
+    evalnodes::NodeArgs<double> a = node_args64(nt_items4.ptr, nt_xy.ptr, nt_own1.ptr, nt_own2.ptr,
+                                                nt_perm.ptr, nullptr, nullptr, 0, 0, nullptr);
+    evalnodes::near_coef_kernel<<<n_nt_items4, 32 * evalnodes::kWarps, 0, st>>>(a, near_off.ptr,
+                                                                               near_g64.ptr, near_f64.ptr);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (fp32) {
+        if ((e = near_g32.alloc((size_t)near_total)) != cudaSuccess) return e;
+        narrow_real_kernel<<<4 * n_sms, 256, 0, st>>>(near_g64.ptr, near_g32.ptr, near_total);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    near_ready = true;
+    // far-field coefficients (L2P and list-3 M2P at the nodes), when they fit too
+    const size_t need_far = (size_t)far_blocks * (P1 * sizeof(double2) + (fp32 ? P1i * sizeof(float2) : 0));
+    if ((e = cudaMemGetInfo(&fr, &tot)) != cudaSuccess) return e;
+    if (far_blocks <= 0 || need_far > fr / 4) return cudaSuccess;
+    if ((e = far64.alloc((size_t)far_blocks * P1)) != cudaSuccess) return e;
+    far_coef_launch(st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (fp32) {
+        if ((e = far32.alloc((size_t)far_blocks * P1i)) != cudaSuccess) return e;
+        narrow_rows_kernel<<<4 * n_sms, 256, 0, st>>>(far64.ptr, P1, far32.ptr, P1i, far_blocks);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    far_ready = true;
+    return cudaSuccess;
+}
+
+void Fmm::Impl::far_coef_launch(cudaStream_t st) {
+    evalnodes::NodeArgs<double> a = node_args64(nt_items4.ptr, nt_xy.ptr, nt_own1.ptr, nt_own2.ptr,
+                                                nt_perm.ptr, nullptr, nullptr, 0, 0, nullptr);
+    evalnodes::far_coef_kernel<<<n_nt_items4, 32 * evalnodes::kWarps, 0, st>>>(a, far_off.ptr, far64.ptr);
+    note_launch();
+}
+
+
+// Per-piece P2M and per-(cell, list-4 piece) P2L coefficients, formed once per
+// drawing in FP64 (and the P2M rows' low orders in FP32 for the inner
+// operator) and kept resident: the passes then stream them instead of
+// re-running the recurrences and logarithms (FP64 at 1/64 of the FP32 rate)
+// at every operator application.  The FP32 P2L recomputes: its rows would
+// cost more memory traffic than the arithmetic they save.  Skipped when the
+// rows would take more than a quarter of the free device memory.
+cudaError_t Fmm::Impl::build_rows(cudaStream_t st) {
+    rows_ready = false;
+    const long long np = (long long)tree.pc_seg.size();
+    if (np == 0) return cudaSuccess;
+    const size_t per64 = 2 * sizeof(double2) * (size_t)P1, per32 = fp32 ? sizeof(float2) * (size_t)P1i : 0;
+    const size_t need = (size_t)(np + p2l_rows) * per64 + (size_t)np * per32;
+    size_t fr = 0, tot = 0;
+    cudaError_t e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) return e;
+    if (need > fr / 4) return cudaSuccess;
+    if ((e = p2m_g64.alloc((size_t)np * P1)) != cudaSuccess || (e = p2m_f64.alloc((size_t)np * P1)) != cudaSuccess)
+        return e;
+    if (p2l_rows > 0 && ((e = p2l_g64.alloc((size_t)p2l_rows * P1)) != cudaSuccess ||
+                         (e = p2l_f64.alloc((size_t)p2l_rows * P1)) != cudaSuccess))
+        return e;
+    passes::TreeView<double> tv = view64();
+    passes::PiecesF64 ps{pc.ptr, cc.ptr};
+    if (n_p2m > 0) {
+        passes::p2m_kernel<double, passes::PiecesF64><<<n_p2m, passes::kChunk, passes::p2m_smem<double>(P1), st>>>(
+            tv, ps, p2m_leaves.ptr, nullptr, nullptr, 0, 0, P1, M.ptr, nullptr, nullptr, p2m_g64.ptr,
+            p2m_f64.ptr);
+        note_launch();
+    }
+    if (sched_all.n_p2l > 0 && p2l_rows > 0) {
+        passes::p2l_kernel<double, passes::PiecesF64><<<sched_all.n_p2l, passes::kChunk, passes::p2l_smem<double>(P1), st>>>(
+            tv, ps, sched_all.p2l.ptr, nullptr, nullptr, 0, 0, P1, Lm2l.ptr, p2l_off.ptr, nullptr, nullptr,
+            p2l_g64.ptr, p2l_f64.ptr);
+        note_launch();
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (fp32) {
+        if ((e = p2m_g32.alloc((size_t)np * P1i)) != cudaSuccess) return e;
+        narrow_rows_kernel<<<4 * n_sms, 256, 0, st>>>(p2m_g64.ptr, P1, p2m_g32.ptr, P1i, np);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    rows_ready = true;
+    return cudaSuccess;
 }
 
 Fmm::Fmm() : impl_(new Impl()) {}
@@ -521,7 +659,7 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         if (!T.is_leaf(c))
             for (int q = 0; q < 4; ++q) sub_nodes[c] += sub_nodes[T.child0[c] + q];
     // pass schedules
-    std::vector<int> m2m_cells;
+    std::vector<int> m2m_cells;        // inner cells of level >= 2 with pieces, by level
     I.m2m_ptr.assign(T.depth + 2, 0);
     for (int l = 0; l <= T.depth; ++l) {
         I.m2m_ptr[l] = int(m2m_cells.size());
@@ -531,7 +669,7 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     }
     I.m2m_ptr[T.depth + 1] = int(m2m_cells.size());
     auto make_sched = [&](Schedule &sc, bool nodes_only, std::vector<int> &m2l_c,
-                          std::vector<int> &p2l_c, std::vector<int> &l2l_c) {
+                          std::vector<int> &p2l_c, std::vector<int> &l2l_c, std::vector<int> &walk_c) {
         sc.l2l_ptr.assign(T.depth + 2, 0);
         for (int l = 0; l <= T.depth; ++l) {
             sc.l2l_ptr[l] = int(l2l_c.size());
@@ -541,15 +679,26 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
                 l2l_c.push_back(c);
                 if (T.v_ptr[c + 1] > T.v_ptr[c]) m2l_c.push_back(c);
                 if (T.x_ptr[c + 1] > T.x_ptr[c]) p2l_c.push_back(c);
+                if (T.is_leaf(c)) walk_c.push_back(c);
             }
         }
         sc.l2l_ptr[T.depth + 1] = int(l2l_c.size());
         sc.n_m2l = int(m2l_c.size());
         sc.n_p2l = int(p2l_c.size());
+        sc.n_walk = int(walk_c.size());
     };
-    std::vector<int> am2l, ap2l, al2l, nm2l, np2l, nl2l;
-    make_sched(I.sched_all, false, am2l, ap2l, al2l);
-    make_sched(I.sched_nodes, true, nm2l, np2l, nl2l);
+    std::vector<int> am2l, ap2l, al2l, aw, nm2l, np2l, nl2l, nw;
+    make_sched(I.sched_all, false, am2l, ap2l, al2l, aw);
+    make_sched(I.sched_nodes, true, nm2l, np2l, nl2l, nw);
+    // rows of the stored P2L coefficients: the pieces of each list-4 cell of
+    // the full schedule (the node schedule's cells are among them)
+    std::vector<long long> p2l_off(nC, -1);
+    long long p2l_rows = 0;
+    for (int c : ap2l) {
+        p2l_off[c] = p2l_rows;
+        for (int e = T.x_ptr[c]; e < T.x_ptr[c + 1]; ++e) p2l_rows += T.piece_count[T.x_idx[e]];
+    }
+    I.p2l_rows = p2l_rows;
     {
         cudaDeviceProp prop;
         int dev = 0;
@@ -578,18 +727,57 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     I.p2p_nodes = p2p;
     I.n_nt_leaves = int(leaves.size());
     std::vector<int4> items4;
-    for (int c : leaves)
-        for (int j = 0; j < cnt[c]; j += evalnodes::kNodeItem)
-            items4.push_back(make_int4(c, start[c] + j, std::min(evalnodes::kNodeItem, cnt[c] - j), 0));
+    std::vector<long long> near_off;   // first near-field coefficient of each item
+    long long near_total = 0;
+    std::vector<long long> far_off;    // first far-field block of each item
+    long long far_blocks = 0;
+    for (int c : leaves) {
+        int nU = 0;
+        for (int e = T.u_ptr[c]; e < T.u_ptr[c + 1]; ++e) nU += T.piece_count[T.u_idx[e]];
+        for (int j = 0; j < cnt[c]; j += evalnodes::kNodeItem) {
+            const int nt = std::min(evalnodes::kNodeItem, cnt[c] - j);
+            items4.push_back(make_int4(c, start[c] + j, nt, nU));
+            near_off.push_back(near_total);
+            near_total += (long long)nt * nU;
+            far_off.push_back(far_blocks);
+            far_blocks += (long long)nt * (1 + T.w_ptr[c + 1] - T.w_ptr[c]);
+        }
+    }
     I.n_nt_items4 = int(items4.size());
+    I.near_total = near_total;
+    I.far_blocks = far_blocks;
     std::vector<cd> m2m, l2l, m2l, base;
     build_tables(I.p, m2m, l2l, m2l);
     build_base_tables(I.p, base);
-    const int p_inner = std::min(I.p, 12);
+    const int p_inner = opt.p_inner > 0 ? std::min(opt.p_inner, I.p) : std::min(I.p, 12);
     I.P1i = p_inner + 1;
     std::vector<cd> m2mi, l2li, m2li, basei;
     build_tables(p_inner, m2mi, l2li, m2li);
     build_base_tables(p_inner, basei);
+    // the 56 (base, rotation, conjugation) variants in full for the
+    // low-order M2L: F[b + 7 r + 28 cj][l][k] = conj^cj(B_b[k][l]) i^(-r (k + l))
+    std::vector<cd> fulli(56 * (size_t)I.P1i * I.P1i);
+    {
+        const int Q = I.P1i;
+        const cd ipow[4] = {cd(1, 0), cd(0, -1), cd(-1, 0), cd(0, 1)};   // i^(-n)
+        for (int b = 0; b < 7; ++b)
+            for (int r = 0; r < 4; ++r)
+                for (int cj = 0; cj < 2; ++cj)
+                    for (int l = 0; l < Q; ++l)
+                        for (int k = 0; k < Q; ++k) {
+                            cd v = basei[(size_t)b * Q * Q + (size_t)k * Q + l];
+                            if (cj) v = std::conj(v);
+                            fulli[((size_t)(b + 7 * r + 28 * cj) * Q + l) * Q + k] = v * ipow[(r * (k + l)) & 3];
+                        }
+    }
+    auto to_ff = [](const std::vector<cd> &v) {   // float-float: hi, then the rest
+        std::vector<float4> f(v.size());
+        for (size_t i = 0; i < v.size(); ++i) {
+            const float hx = (float)v[i].real(), hy = (float)v[i].imag();
+            f[i] = make_float4(hx, hy, (float)(v[i].real() - hx), (float)(v[i].imag() - hy));
+        }
+        return f;
+    };
     auto to_f2 = [](const std::vector<cd> &v) {
         std::vector<float2> f(v.size());
         for (size_t i = 0; i < v.size(); ++i) f[i] = make_float2((float)v[i].real(), (float)v[i].imag());
@@ -629,25 +817,33 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     UP(I.nt_own2, own2);
     UP(I.nt_xy, txy);
     UP(I.nt_items4, items4);
+    UP(I.near_off, near_off);
+    UP(I.far_off, far_off);
+    UP(I.p2l_off, p2l_off);
     UP(I.iw64, iw64);
     UP(I.logw64, logw64);
     UP(I.plen64, plen64);
     UP(I.v_code, vcode);
     UP(I.m2m_cells, m2m_cells);
+    UP(I.level_d, T.level);
+    UP(I.sched_all.walk, aw);
+    UP(I.sched_all.l2l, al2l);
+    UP(I.sched_nodes.l2l, nl2l);
+    UP(I.sched_nodes.walk, nw);
     UP(I.sched_all.m2l, am2l);
     UP(I.sched_all.p2l, ap2l);
-    UP(I.sched_all.l2l, al2l);
     UP(I.sched_nodes.m2l, nm2l);
     UP(I.sched_nodes.p2l, np2l);
-    UP(I.sched_nodes.l2l, nl2l);
 #undef UP
     if ((e = upload_cd(I.m2m, m2m, st)) != cudaSuccess || (e = upload_cd(I.l2l, l2l, st)) != cudaSuccess ||
         (e = upload_cd(I.m2l, m2l, st)) != cudaSuccess || (e = I.M.alloc((size_t)nC * 3 * I.P1)) != cudaSuccess ||
         (e = I.L.alloc((size_t)nC * 3 * I.P1)) != cudaSuccess ||
         (e = upload_cd(I.base64, base, st)) != cudaSuccess ||
+        (e = upload(I.baseff, to_ff(base), st)) != cudaSuccess ||
         (e = upload(I.m2m32i, to_f2(m2mi), st)) != cudaSuccess ||
         (e = upload(I.l2l32i, to_f2(l2li), st)) != cudaSuccess ||
         (e = upload(I.base32i, to_f2(basei), st)) != cudaSuccess ||
+        (e = upload(I.m2lfull32i, to_f2(fulli), st)) != cudaSuccess ||
         (e = I.M32i.alloc((size_t)nC * 3 * I.P1i)) != cudaSuccess ||
         (e = I.L32i.alloc((size_t)nC * 3 * I.P1i)) != cudaSuccess ||
         (e = I.Lm2l32i.alloc((size_t)nC * 3 * I.P1i)) != cudaSuccess ||
@@ -685,12 +881,22 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
                 return DC_ERR_GEOMETRY;
             }
     }
+    cudaFuncSetAttribute(passes::m2l_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)passes::m2l_ff_smem(I.P1));
     cudaFuncSetAttribute(passes::m2l_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)passes::m2l_smem<double>(I.P1));
     cudaFuncSetAttribute(passes::p2l_kernel<double, passes::PiecesF64>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passes::p2l_smem<double>(I.P1));
     cudaFuncSetAttribute(passes::p2m_kernel<double, passes::PiecesF64>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passes::p2m_smem<double>(I.P1));
+    if ((e = I.build_rows(st)) != cudaSuccess) {
+        err = std::string("stored P2M / P2L coefficients: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
+    }
+    if ((e = I.build_near(st)) != cudaSuccess) {
+        err = std::string("near-field coefficients: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
+    }
     if (I.fp32) return I.build32(G, st, err);
     return DC_OK;
 }
@@ -711,6 +917,11 @@ cudaError_t Fmm::apply_single_layer(const double *x, double *y, cudaStream_t st)
 
 cudaError_t Fmm::apply_double_layer(const double *x, double *y, cudaStream_t st) {
     return impl_->apply_nodes(x, y, false, st);
+}
+
+cudaError_t Fmm::apply_inner(const double *x, double *y, cudaStream_t st) {
+    if (!impl_->fp32) return cudaErrorNotSupported;
+    return impl_->graph_matvec32(x, y, st);
 }
 
 namespace {
@@ -766,7 +977,8 @@ cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_option
         if (outer == max_outer || used >= opt.gmres_max_iter) break;
         if ((e = vec_mask3(I.ir_r.ptr, N, mask, st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(I.ir_d.ptr, 0, sizeof(double) * 3 * N, st)) != cudaSuccess) return e;
-        double inner_tol = I.fp32 ? std::max(1e-5, need) : std::max(0.5 * need, 1e-15);
+        const double floor32 = opt.inner_tol > 0.0 ? opt.inner_tol : 1e-5;
+        double inner_tol = I.fp32 ? std::max(floor32, need) : std::max(0.5 * need, 1e-15);
         GmresResult inner;
         op.fp32 = I.fp32;
         e = gmres_solve(w, op, N, I.ir_r.ptr, I.ir_d.ptr, inner_tol, opt.gmres_restart,

@@ -20,6 +20,10 @@ public:
     cudaError_t apply_single_layer(const double *x, double *y, cudaStream_t st);
     // y = F_H x at the nodes (double layer), for the right-hand side.
     cudaError_t apply_double_layer(const double *x, double *y, cudaStream_t st);
+    // The FP32 inner operator of the iterative refinement: y = G_H M^-1 x
+    // (order-12 expansions, block-Jacobi preconditioner M), through the
+    // captured graph.  cudaErrorNotSupported for the FP64 form.
+    cudaError_t apply_inner(const double *x, double *y, cudaStream_t st);
     // GMRES with this operator (Alg. 3 line 5); x holds x0 on entry.
     cudaError_t solve(GmresWork *w, const double *b, double *x, const dc_options &opt,
                       cudaStream_t st, GmresResult &res, std::string &err);

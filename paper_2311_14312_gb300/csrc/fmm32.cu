@@ -544,6 +544,9 @@ dc_status Fmm::Impl::build32(const Geometry &G, cudaStream_t st, std::string &er
     cudaMemsetAsync(heavyM.ptr, 0, heavyM.bytes(), st);
     cudaFuncSetAttribute(passes::m2l_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)passes::m2l_smem<float>(P1));
+    if (P1i <= passes::kM2LSmallP1)
+        cudaFuncSetAttribute(passes::m2l_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)passes::m2l_small_smem(P1i));
     cudaFuncSetAttribute(passes::p2l_kernel<float, passes::PiecesF32>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passes::p2l_smem<float>(P1));
     cudaFuncSetAttribute(passes::p2m_kernel<float, passes::PiecesF32>,
@@ -596,20 +599,24 @@ cudaError_t Fmm::Impl::passes32(const float *sb, const float *mb, int use_s, int
     if ((e = cudaMemsetAsync(Lm2l32i.ptr, 0, ebytes, st)) != cudaSuccess) return e;
     passes::TreeView<float> tv = view32();
     passes::PiecesF32 ps{pc32.ptr};
-    int th = P1 <= 32 ? 32 : 64;
     if (n_p2m > 0) {
         passes::p2m_kernel<float, passes::PiecesF32><<<n_p2m, passes::kChunk, passes::p2m_smem<float>(P1), st>>>(
-            tv, ps, p2m_leaves.ptr, sb, mb, use_s, use_m, P1, M32i.ptr);
+            tv, ps, p2m_leaves.ptr, sb, mb, use_s, use_m, P1, M32i.ptr, rows_ready && !use_m ? p2m_g32.ptr : nullptr);
         note_launch();
     }
     for (int l = tree.depth - 1; l >= 2; --l) {
-        int lo = m2m_ptr[l], hi = m2m_ptr[l + 1];
-        if (hi > lo) {
-            passes::m2m_kernel<float><<<hi - lo, th, 0, st>>>(tv, m2m_cells.ptr + lo, P1, m2m32i.ptr, M32i.ptr);
-            note_launch();
-        }
+        const int lo = m2m_ptr[l], n = m2m_ptr[l + 1] - lo;
+        if (n <= 0) continue;
+        passes::m2m_kernel<float><<<(n + passes::kLevelWarps - 1) / passes::kLevelWarps, 32 * passes::kLevelWarps, 0, st>>>(
+            child0.ptr, m2m_cells.ptr + lo, n, P1, m2m32i.ptr, M32i.ptr);
+        note_launch();
     }
-    if (sc.n_m2l > 0) {
+    if (sc.n_m2l > 0 && P1 <= passes::kM2LSmallP1) {
+        int grid = std::min((sc.n_m2l + passes::kM2LSmallWarps - 1) / passes::kM2LSmallWarps, 2 * n_sms);
+        passes::m2l_small_kernel<<<grid, 32 * passes::kM2LSmallWarps, passes::m2l_small_smem(P1), st>>>(
+            tv, sc.m2l.ptr, sc.n_m2l, P1, m2lfull32i.ptr, M32i.ptr, Lm2l32i.ptr);
+        note_launch();
+    } else if (sc.n_m2l > 0) {
         int grid = std::min((sc.n_m2l + passes::kM2LSlots - 1) / passes::kM2LSlots, 4 * n_sms);
         passes::m2l_kernel<float><<<grid, 32 * passes::kM2LSlots, passes::m2l_smem<float>(P1), st>>>(
             tv, sc.m2l.ptr, sc.n_m2l, P1, base32i.ptr, M32i.ptr, Lm2l32i.ptr);
@@ -620,13 +627,10 @@ cudaError_t Fmm::Impl::passes32(const float *sb, const float *mb, int use_s, int
             tv, ps, sc.p2l.ptr, sb, mb, use_s, use_m, P1, Lm2l32i.ptr);
         note_launch();
     }
-    for (int l = 2; l <= tree.depth; ++l) {
-        int lo = sc.l2l_ptr[l], hi = sc.l2l_ptr[l + 1];
-        if (hi > lo) {
-            passes::l2l_kernel<float><<<(hi - lo + 3) / 4, 128, 0, st>>>(
-                tv, sc.l2l.ptr + lo, hi - lo, l, P1, l2l32i.ptr, Lm2l32i.ptr, L32i.ptr);
-            note_launch();
-        }
+    if (sc.n_walk > 0) {
+        passes::walk_kernel<float><<<sc.n_walk, P1 <= 32 ? 32 : 64, passes::walk_smem<float>(P1), st>>>(
+            tv, sc.walk.ptr, level_d.ptr, P1, l2l32i.ptr, Lm2l32i.ptr, L32i.ptr);
+        note_launch();
     }
     return cudaGetLastError();
 }
@@ -687,7 +691,12 @@ cudaError_t Fmm::Impl::apply_nodes32(const double *x, double *y, bool single, cu
     a.P1 = P1i;
     a.M = M32i.ptr;
     a.L = L32i.ptr;
-    evalnodes::eval_nodes_kernel<float><<<n_nt_items4, 32 * evalnodes::kWarps, 0, st>>>(a);
+    if (near_ready && single)
+        evalnodes::near_apply_kernel<float><<<n_nt_items4, 32 * evalnodes::kWarps, 0, st>>>(
+            a, near_off.ptr, near_g32.ptr, sbar32.ptr, far_ready ? far_off.ptr : nullptr,
+            far_ready ? far32.ptr : nullptr);
+    else
+        evalnodes::eval_nodes_kernel<float><<<n_nt_items4, 32 * evalnodes::kWarps, 0, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }

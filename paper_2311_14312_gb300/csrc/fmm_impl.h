@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "dc_internal.h"
+#include "evalnodes.cuh"
 #include "fmm.h"
 #include "passes.cuh"
 #include "tree.h"
@@ -54,7 +55,8 @@ struct Tile {
 struct Schedule {
     DevBuf<int> m2l, p2l, l2l;        // cells with list 2 / list 4; cells per level
     std::vector<int> l2l_ptr;         // [depth + 2] offsets into l2l by level
-    int n_m2l = 0, n_p2l = 0;
+    DevBuf<int> walk;                 // leaves whose incoming expansion is needed
+    int n_m2l = 0, n_p2l = 0, n_walk = 0;
 };
 
 struct Fmm::Impl {
@@ -78,8 +80,32 @@ struct Fmm::Impl {
     DevBuf<double> pt_xy, pt_out;
     DevBuf<float2> pt_q32;
     DevBuf<Tile> pt_items;
-    DevBuf<int4> nt_items4, pt_items4;   // (leaf, first target, count, 0) work items
+    DevBuf<int4> nt_items4, pt_items4;   // (leaf, first target, count, list-1 pieces) work items
     int n_nt_items4 = 0;
+    // near-field coefficients of the node operator (formed once per drawing):
+    // single and double layer in FP64, single layer in FP32
+    DevBuf<long long> near_off;
+    long long near_total = 0;
+    bool near_ready = false;
+    DevBuf<double> near_g64, near_f64;
+    DevBuf<float> near_g32;
+    cudaError_t build_near(cudaStream_t st);
+    // far-field coefficients of the node targets: (1 + list-3 length) blocks
+    // of P1 (FP64) / P1i (FP32) complex values per target from block far_off[item]
+    DevBuf<long long> far_off;
+    long long far_blocks = 0;
+    bool far_ready = false;
+    DevBuf<double2> far64;
+    DevBuf<float2> far32;
+    void far_coef_launch(cudaStream_t st);
+    // stored P2M rows [pieces][P1] and P2L rows [p2l_rows][P1] (G and F parts,
+    // FP64; P2M G part at order p_inner in FP32), p2l_off[cell] = first row
+    bool rows_ready = false;
+    long long p2l_rows = 0;
+    DevBuf<long long> p2l_off;
+    DevBuf<double2> p2m_g64, p2m_f64, p2l_g64, p2l_f64;
+    DevBuf<float2> p2m_g32;
+    cudaError_t build_rows(cudaStream_t st);
     // FP64 tables and expansions
     DevBuf<double2> m2m, l2l, m2l, M, L;
     DevBuf<double> sbar, mbar;
@@ -100,14 +126,17 @@ struct Fmm::Impl {
     // pass schedules and tables of the templated passes
     Schedule sched_all, sched_nodes;
     DevBuf<int> m2m_cells, v_code;
-    std::vector<int> m2m_ptr;         // [depth + 2]: non-leaf cells with pieces, by level
+    std::vector<int> m2m_ptr;         // [depth + 2]: inner cells with pieces, by level
+    DevBuf<int> level_d;              // cell levels (downward walk)
     DevBuf<double2> base64, Lm2l;
+    DevBuf<float4> baseff;            // base M2L tables in float-float
     DevBuf<float2> base32, Lm2l32;
     // the FP32 operator inside GMRES runs at a lower order p_inner (its
     // accuracy only has to beat the inner tolerance; the FP64 residual at
     // order p decides convergence): own tables and expansions
     int P1i = 0;
     DevBuf<float2> m2m32i, l2l32i, base32i, M32i, L32i, Lm2l32i;
+    DevBuf<float2> m2lfull32i;        // [56][P1i][P1i] full M2L variants
     DevBuf<double> iw64, logw64, plen64;
     DevBuf<unsigned char> heavy;      // per piece: near field evaluated in FP64
     DevBuf<unsigned char> heavyL, heavyM;   // per cell: L2P / M2P evaluated in FP64
@@ -154,6 +183,9 @@ struct Fmm::Impl {
                                cudaStream_t st);
     cudaError_t eval_points32(int n_items, double *out, const double *sb64, const double *mb64,
                               cudaStream_t st);
+    evalnodes::NodeArgs<double> node_args64(const int4 *items, const double *q64, const int *own1,
+                                            const int *own2, const int *perm, const double *sb,
+                                            const double *mb, int use_s, int use_m, double *out) const;
     cudaError_t eval_list64(const int4 *items, int n_items, const double *q64, const int *own1,
                             const int *own2, const int *perm, const double *sb, const double *mb,
                             int use_s, int use_m, double *out, cudaStream_t st);

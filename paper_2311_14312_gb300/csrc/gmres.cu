@@ -7,8 +7,11 @@
 // ones, same stability as modified Gram-Schmidt in practice); Givens
 // rotations, the residual estimate and the triangular solve run on the
 // device.  Reductions are two-stage with a fixed order, so results are
-// bit-reproducible.  The host reads back three residual estimates per
-// iteration to decide convergence.
+// bit-reproducible.  The host learns of convergence from per-channel flags
+// copied back after every iteration, read kPollLag iterations late so that
+// the device queue never drains; iterations enqueued after the last channel
+// converged leave the solution unchanged (the Givens step ignores finished
+// channels).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -23,6 +26,9 @@ namespace {
 
 constexpr int kChunk = 4096;     // rows per partial dot-product block
 constexpr int kDotThreads = 256;
+constexpr int kPollRing = 4;     // pinned flag slots / events
+constexpr int kPollLag = 2;      // iterations between enqueue and flag read
+constexpr size_t kGivensSmem = 48 * 1024;   // Givens step staged in shared memory up to this
 
 // partial[(j * nchunk + chunk) * 3 + c] = sum over rows of the chunk of
 // V_j[i][c] * w[i][c]
@@ -63,22 +69,47 @@ __global__ void dots_finalize_kernel(const double *__restrict__ partial, int nch
     h[t] = accumulate ? h[t] + s : s;
 }
 
-// w[i][c] -= sum_{j < nj} h[j][c] V_j[i][c]
+// One Gram-Schmidt pass's coefficients: hpass = sum_chunk partial, and the
+// Hessenberg column hcol = hpass (first pass) or hcol + hpass (second).
+__global__ void dots_finalize2_kernel(const double *__restrict__ partial, int nchunk, int nj,
+                                      double *__restrict__ hpass, double *__restrict__ hcol, int first) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nj * 3) return;
+    int j = t / 3, c = t - 3 * j;
+    double s = 0.0;
+    for (int ch = 0; ch < nchunk; ++ch) s += partial[((size_t)j * nchunk + ch) * 3 + c];
+    hpass[t] = s;
+    hcol[t] = first ? s : hcol[t] + s;
+}
+
+// nrm[c] = sqrt(sum_chunk partial) (the norms of one [N][3] vector)
+__global__ void norm_finalize_kernel(const double *__restrict__ partial, int nchunk, double *__restrict__ nrm) {
+    int c = threadIdx.x;
+    if (c >= 3) return;
+    double s = 0.0;
+    for (int ch = 0; ch < nchunk; ++ch) s += partial[(size_t)ch * 3 + c];
+    nrm[c] = sqrt(fmax(s, 0.0));
+}
+
+// w[i][c] -= sum_{j < nj} h[j][c] V_j[i][c], one thread per element (t = 3 i + c)
 __global__ void orth_update_kernel(const double *__restrict__ V, size_t vstride,
                                    const double *__restrict__ h, int nj, double *__restrict__ w,
                                    int N) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    double a0 = w[3 * (size_t)i + 0], a1 = w[3 * (size_t)i + 1], a2 = w[3 * (size_t)i + 2];
-    for (int j = 0; j < nj; ++j) {
-        const double *v = V + (size_t)j * vstride + 3 * (size_t)i;
-        a0 -= h[3 * j + 0] * v[0];
-        a1 -= h[3 * j + 1] * v[1];
-        a2 -= h[3 * j + 2] * v[2];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * N) return;
+    const int c = t % 3;
+    double a = w[t];
+    int j = 0;
+    for (; j + 4 <= nj; j += 4) {
+        const double v0 = V[(size_t)j * vstride + t], v1 = V[(size_t)(j + 1) * vstride + t];
+        const double v2 = V[(size_t)(j + 2) * vstride + t], v3 = V[(size_t)(j + 3) * vstride + t];
+        a -= h[3 * j + c] * v0;
+        a -= h[3 * (j + 1) + c] * v1;
+        a -= h[3 * (j + 2) + c] * v2;
+        a -= h[3 * (j + 3) + c] * v3;
     }
-    w[3 * (size_t)i + 0] = a0;
-    w[3 * (size_t)i + 1] = a1;
-    w[3 * (size_t)i + 2] = a2;
+    for (; j < nj; ++j) a -= h[3 * j + c] * V[(size_t)j * vstride + t];
+    w[t] = a;
 }
 
 // out[i][c] = in[i][c] * (nrm[c] > 0 ? 1 / nrm[c] : 0)
@@ -157,6 +188,48 @@ __global__ void givens_kernel(GivensState g, const double *__restrict__ hcol,
     if (res <= thr[c] || !(hn > 0.0) || !(den > 0.0)) g.active[c] = 0;
 }
 
+// The same step with the column and the earlier rotations staged in shared
+// memory (one warp per channel: parallel loads, then the sequential chain).
+__global__ void givens_smem_kernel(GivensState g, const double *__restrict__ hcol,
+                                   const double *__restrict__ hnext, const double *__restrict__ thr,
+                                   int k, int m) {
+    extern __shared__ double gsm[];                  // [3][3][k + 1]
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (c >= 3 || !g.active[c]) return;
+    double *col = gsm + (size_t)c * 3 * (k + 1), *cs = col + (k + 1), *sn = cs + (k + 1);
+    const double *gcs = g.cs + c * m, *gsn = g.sn + c * m;
+    for (int j = lane; j <= k; j += 32) col[j] = hcol[3 * j + c];
+    for (int j = lane; j < k; j += 32) {
+        cs[j] = gcs[j];
+        sn[j] = gsn[j];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        for (int j = 0; j < k; ++j) {
+            double a = col[j], b = col[j + 1];
+            col[j] = cs[j] * a + sn[j] * b;
+            col[j + 1] = -sn[j] * a + cs[j] * b;
+        }
+        double *e = g.e + c * (m + 1);
+        double hn = hnext[c];
+        double den = hypot(col[k], hn);
+        double cc = (den > 0.0) ? col[k] / den : 1.0;
+        double ss = (den > 0.0) ? hn / den : 0.0;
+        g.cs[c * m + k] = cc;
+        g.sn[c * m + k] = ss;
+        col[k] = den;
+        e[k + 1] = -ss * e[k];
+        e[k] = cc * e[k];
+        double res = fabs(e[k + 1]);
+        g.resid[c] = res;
+        g.kc[c] = k + 1;
+        if (res <= thr[c] || !(hn > 0.0) || !(den > 0.0)) g.active[c] = 0;
+    }
+    __syncwarp();
+    double *R = g.R + (size_t)c * m * m + (size_t)k * m;
+    for (int j = lane; j <= k; j += 32) R[j] = col[j];
+}
+
 // Back substitution R y = e for each channel (kc[c] columns).
 __global__ void backsolve_kernel(GivensState g, int m) {
     int c = threadIdx.x;
@@ -196,8 +269,13 @@ struct GmresWork {
     DevBuf<double> R, cs, sn, e, y;
     DevBuf<int> flags;
     double *host = nullptr;   // pinned: resid[3], active-as-double[3], norms[3]
+    int *poll = nullptr;      // pinned [kPollRing][3] copies of the active flags
+    cudaEvent_t ev[kPollRing] = {};
     ~GmresWork() {
         if (host) cudaFreeHost(host);
+        if (poll) cudaFreeHost(poll);
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
     }
     cudaError_t ensure(int N_, int m_) {
         if (N_ == N && m_ == m) return cudaSuccess;
@@ -224,6 +302,9 @@ struct GmresWork {
         DC_TRY(y.alloc((size_t)3 * m));
         DC_TRY(flags.alloc(8));
         if (!host) DC_TRY(cudaMallocHost(reinterpret_cast<void **>(&host), 16 * sizeof(double)));
+        if (!poll) DC_TRY(cudaMallocHost(reinterpret_cast<void **>(&poll), kPollRing * 3 * sizeof(int)));
+        for (auto &e : ev)
+            if (!e) DC_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 #undef DC_TRY
         return cudaSuccess;
     }
@@ -248,6 +329,15 @@ __global__ void axpy_kernel(double *__restrict__ x, const double *__restrict__ d
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n3) x[t] += d[t];
 }
+// y[i][c] = a[c] x[i][c] + b[c] z[i][c] (z may be null: then b[c] alone)
+__global__ void combine3_kernel(const double *x, const double *z, double *y, int n3,
+                                double a0, double a1, double a2, double b0, double b1, double b2) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n3) return;
+    int c = t % 3;
+    double a = c == 0 ? a0 : (c == 1 ? a1 : a2), b = c == 0 ? b0 : (c == 1 ? b1 : b2);
+    y[t] = a * x[t] + b * (z ? z[t] : 1.0);
+}
 __global__ void mask3_kernel(double *__restrict__ v, int n3, int k0, int k1, int k2) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n3) return;
@@ -264,6 +354,14 @@ cudaError_t vec_residual(const double *b, const double *Ax, double *r, int n3, c
 
 cudaError_t vec_axpy(double *x, const double *d, int n3, cudaStream_t st) {
     axpy_kernel<<<(n3 + 255) / 256, 256, 0, st>>>(x, d, n3); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t vec_combine3(const double *x, const double *z, double *y, int N, const double a[3],
+                         const double b[3], cudaStream_t st) {
+    int n3 = 3 * N;
+    combine3_kernel<<<(n3 + 255) / 256, 256, 0, st>>>(x, z, y, n3, a[0], a[1], a[2], b[0], b[1], b[2]);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -299,6 +397,20 @@ cudaError_t vec_norms3(GmresWork *Wp, const double *v, int N, double host_out[3]
     if (e != cudaSuccess) return e;
     if ((e = norms(W, v, W.small.ptr + 16, st)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(host_out, W.small.ptr + 16, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                             st)) != cudaSuccess)
+        return e;
+    return cudaStreamSynchronize(st);
+}
+
+cudaError_t vec_dots3(GmresWork *Wp, const double *u, const double *v, int N, double host_out[3],
+                      cudaStream_t st) {
+    GmresWork &W = *Wp;
+    cudaError_t e = W.ensure(N, W.m > 0 ? W.m : 1);
+    if (e != cudaSuccess) return e;
+    dim3 grid(W.nchunk, 1);
+    dots_partial_kernel<<<grid, kDotThreads, 0, st>>>(u, 0, v, N, W.nchunk, W.partial.ptr); note_launch();
+    dots_finalize_kernel<<<1, 32, 0, st>>>(W.partial.ptr, W.nchunk, 1, W.small.ptr + 20, 0); note_launch();
+    if ((e = cudaMemcpyAsync(host_out, W.small.ptr + 20, 3 * sizeof(double), cudaMemcpyDeviceToHost,
                              st)) != cudaSuccess)
         return e;
     return cudaStreamSynchronize(st);
@@ -370,26 +482,39 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
                 dots_partial_kernel<<<grid, kDotThreads, 0, st>>>(W.V.ptr, vs, W.w.ptr, N,
                                                                   W.nchunk, W.partial.ptr); note_launch();
                 int t3 = (k + 1) * 3;
-                dots_finalize_kernel<<<(t3 + 127) / 128, 128, 0, st>>>(W.partial.ptr, W.nchunk,
-                                                                      k + 1, W.hpass.ptr, 0); note_launch();
-                orth_update_kernel<<<(N + th - 1) / th, th, 0, st>>>(W.V.ptr, vs, W.hpass.ptr,
-                                                                      k + 1, W.w.ptr, N); note_launch();
-                add_into_kernel<<<(t3 + 127) / 128, 128, 0, st>>>(W.hcol.ptr, W.hpass.ptr, t3,
-                                                                  pass == 0); note_launch();
+                dots_finalize2_kernel<<<(t3 + 127) / 128, 128, 0, st>>>(W.partial.ptr, W.nchunk, k + 1,
+                                                                       W.hpass.ptr, W.hcol.ptr, pass == 0); note_launch();
+                orth_update_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.V.ptr, vs, W.hpass.ptr,
+                                                                          k + 1, W.w.ptr, N); note_launch();
             }
-            if ((ce = norms(W, W.w.ptr, W.hnext.ptr, st)) != cudaSuccess) return ce;
+            {   // h_{k+1,k} = ||w|| per channel
+                dim3 grid(W.nchunk, 1);
+                dots_partial_kernel<<<grid, kDotThreads, 0, st>>>(W.w.ptr, 0, W.w.ptr, N, W.nchunk,
+                                                                  W.partial.ptr); note_launch();
+                norm_finalize_kernel<<<1, 32, 0, st>>>(W.partial.ptr, W.nchunk, W.hnext.ptr); note_launch();
+            }
             scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.w.ptr, W.hnext.ptr,
                                                                W.V.ptr + (size_t)(k + 1) * vs, N); note_launch();
-            givens_kernel<<<1, 32, 0, st>>>(gs, W.hcol.ptr, W.hnext.ptr, thr, k, m); note_launch();
+            const size_t gsm = (size_t)9 * (k + 1) * sizeof(double);
+            if (gsm <= kGivensSmem)
+                givens_smem_kernel<<<1, 96, gsm, st>>>(gs, W.hcol.ptr, W.hnext.ptr, thr, k, m);
+            else
+                givens_kernel<<<1, 32, 0, st>>>(gs, W.hcol.ptr, W.hnext.ptr, thr, k, m);
+            note_launch();
             total++;
-            int hact[3];
-            if ((ce = cudaMemcpyAsync(hact, gs.active, 3 * sizeof(int), cudaMemcpyDeviceToHost,
-                                      st)) != cudaSuccess)
+            const int slot = k % kPollRing;
+            if ((ce = cudaMemcpyAsync(W.poll + 3 * slot, gs.active, 3 * sizeof(int),
+                                      cudaMemcpyDeviceToHost, st)) != cudaSuccess)
                 return ce;
-            if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return ce;
-            if (!hact[0] && !hact[1] && !hact[2]) {
-                ++k;
-                break;
+            if ((ce = cudaEventRecord(W.ev[slot], st)) != cudaSuccess) return ce;
+            // flags of iteration k - kPollLag (slot reuse is safe: it was read
+            // kPollLag iterations ago, before this iteration was enqueued)
+            const int done = k - kPollLag;
+            if (done >= 0) {
+                const int ps = done % kPollRing;
+                if ((ce = cudaEventSynchronize(W.ev[ps])) != cudaSuccess) return ce;
+                const int *f = W.poll + 3 * ps;
+                if (!f[0] && !f[1] && !f[2]) break;
             }
         }
         backsolve_kernel<<<1, 32, 0, st>>>(gs, m); note_launch();

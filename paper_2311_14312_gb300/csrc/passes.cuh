@@ -6,7 +6,8 @@
 //               one thread per piece computing S_0..S_p by recurrence into
 //               shared memory, then one thread per coefficient summing the
 //               chunk in order (deterministic)
-//  m2m_kernel   per level, parent from 4 children (Eq. 71)
+//               (or from stored per-piece coefficient rows)
+//  m2m_kernel   per level, parent from its 4 children (Eq. 71)
 //  m2l_kernel   all cells at once, persistent blocks: list 2 (Eq. 69) with
 //               the 40 offset matrices reduced by the symmetries of the
 //               square to 7 base matrices held in shared memory:
@@ -15,6 +16,8 @@
 //  p2l_kernel   cells with a list 4: incoming coefficients of segments
 //               (Eq. 62/78/79), chunked like p2m
 //  l2l_kernel   per level: L = L_m2l + L2L(parent) (Eq. 73)
+//  walk_kernel  the same recursion for listed leaves only, walking down from
+//               each leaf's level-2 ancestor (one launch for all levels)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -127,11 +130,19 @@ template <typename T> struct TreeView {
 constexpr int kChunk = 64;
 
 // ---------------------------------------------------------------- P2M --
+// P2M of listed leaves, one block per leaf.
 template <typename T, typename PS>
 __global__ void __launch_bounds__(kChunk) p2m_kernel(TreeView<T> t, PS ps, const int *__restrict__ leaves,
                                                      const T *__restrict__ sb, const T *__restrict__ mb,
                                                      int use_s, int use_m, int P1,
-                                                     typename V2<T>::type *__restrict__ M) {
+                                                     typename V2<T>::type *__restrict__ M,
+                                                     const typename V2<T>::type *__restrict__ rows_g = nullptr,
+                                                     const typename V2<T>::type *__restrict__ rows_f = nullptr,
+                                                     typename V2<T>::type *__restrict__ out_g = nullptr,
+                                                     typename V2<T>::type *__restrict__ out_f = nullptr) {
+    // rows_g / rows_f: stored per-piece coefficients [pieces][P1] (then no
+    // recurrence runs); out_g / out_f: write those coefficients instead of
+    // forming expansions.
     using C = typename V2<T>::type;
     extern __shared__ unsigned char smem_raw[];
     C *S = reinterpret_cast<C *>(smem_raw);                 // [kChunk][P1 + 1], S_{-1} at 0
@@ -147,7 +158,8 @@ __global__ void __launch_bounds__(kChunk) p2m_kernel(TreeView<T> t, PS ps, const
     for (int base = 0; base < pn; base += kChunk) {
         int cnt = min(kChunk, pn - base);
         __syncthreads();
-        if (tid < cnt) {
+        if (tid < cnt && rows_g) sg[tid] = t.pseg[p0 + base + tid];
+        if (tid < cnt && !rows_g) {
             int i = p0 + base + tid;
             T ax, ay, bx, by;
             ps.rel(i, cell, 0, nullptr, ax, ay, bx, by);
@@ -171,10 +183,22 @@ __global__ void __launch_bounds__(kChunk) p2m_kernel(TreeView<T> t, PS ps, const
         if (tid < P1) {
             const int k = tid;
             for (int j = 0; j < cnt; ++j) {
-                const C *row = S + j * (P1 + 1);
-                C cg = cscl(row[k + 1], om[j] / (k + 1));
-                C t1 = cmul(wr[j], row[k]);
-                C cf = mk<T>(t1.y * om[j], -t1.x * om[j]);   // -i (w/r) S_{k-1} om
+                const size_t ri = (size_t)(p0 + base + j) * P1 + k;
+                C cg, cf;
+                if (rows_g) {
+                    cg = rows_g[ri];
+                    cf = rows_f ? rows_f[ri] : mk<T>(0, 0);
+                } else {
+                    const C *row = S + j * (P1 + 1);
+                    cg = cscl(row[k + 1], om[j] / (k + 1));
+                    C t1 = cmul(wr[j], row[k]);
+                    cf = mk<T>(t1.y * om[j], -t1.x * om[j]);   // -i (w/r) S_{k-1} om
+                }
+                if (out_g) {
+                    out_g[ri] = cg;
+                    out_f[ri] = cf;
+                    continue;
+                }
                 int seg = sg[j];
                 for (int c = 0; c < 3; ++c) {
                     T s = use_s ? sb[3 * (size_t)seg + c] : T(0);
@@ -185,20 +209,27 @@ __global__ void __launch_bounds__(kChunk) p2m_kernel(TreeView<T> t, PS ps, const
             }
         }
     }
+    if (out_g) return;
     if (tid < P1)
         for (int c = 0; c < 3; ++c) M[((size_t)cell * 3 + c) * P1 + tid] = acc[c];
 }
 
 // ---------------------------------------------------------------- M2M --
+// One level: each listed cell's expansion from its four children (Eq. 71),
+// one warp per cell, lane k holds coefficient k (P1 <= 32).
+constexpr int kLevelWarps = 4;
+
 template <typename T>
-__global__ void m2m_kernel(TreeView<T> t, const int *__restrict__ cells, int P1,
-                           const typename V2<T>::type *__restrict__ tab,
-                           typename V2<T>::type *__restrict__ M) {
+__global__ void __launch_bounds__(32 * kLevelWarps) m2m_kernel(const int *__restrict__ child0,
+                                                               const int *__restrict__ cells, int n, int P1,
+                                                               const typename V2<T>::type *__restrict__ tab,
+                                                               typename V2<T>::type *__restrict__ M) {
     using C = typename V2<T>::type;
-    const int cell = cells[blockIdx.x];
-    const int k = threadIdx.x;
-    const int ch0 = t.child0[cell];
-    if (k >= P1) return;
+    const int idx = blockIdx.x * kLevelWarps + (threadIdx.x >> 5);
+    const int k = threadIdx.x & 31;
+    if (idx >= n || k >= P1) return;
+    const int cell = cells[idx];
+    const int ch0 = child0[cell];
     C acc[3];
     for (int c = 0; c < 3; ++c) acc[c] = mk<T>(0, 0);
     for (int q = 0; q < 4; ++q) {
@@ -263,12 +294,255 @@ __global__ void __launch_bounds__(32 * kM2LSlots) m2l_kernel(TreeView<T> t, cons
     }
 }
 
+// M2L for low orders in FP32 (P1 <= 21, the inner operator of the
+// iterative refinement).  The 56 (base, rotation, conjugation) variants are
+// expanded into full tables in shared memory,
+//   F[b + 7 r + 28 cj][l][k] = (cj ? conj(B_b[k][l]) : B_b[k][l]) i^(-r (k + l)),
+// which is the same linear map as the symmetric form of m2l_kernel, so a pair
+// costs P1 x P1 complex multiply-adds per channel and no bookkeeping.  One
+// warp per target cell: for P1 <= 16 lane l + 16 h sums the terms k = h,
+// h + 2, ... of coefficient l and the halves are added at the end; above 16
+// lane l sums all k.  The source moments of each pair are staged in shared
+// memory (double buffered, the next pair's loads in flight during the
+// current pair's products).
+constexpr int kM2LSmallP1 = 21;
+constexpr int kM2LSmallWarps = 8;
+
+inline size_t m2l_small_smem(int P1) {
+    return (56 * (size_t)P1 * P1 + kM2LSmallWarps * 2 * 64) * sizeof(float2);
+}
+
+static __global__ void __launch_bounds__(32 * kM2LSmallWarps) m2l_small_kernel(TreeView<float> t, const int *__restrict__ cells,
+                                                                               int n_cells, int P1,
+                                                                               const float2 *__restrict__ full,
+                                                                               const float2 *__restrict__ M,
+                                                                               float2 *__restrict__ Lout) {
+    extern __shared__ unsigned char smem_raw[];
+    float2 *Tf = reinterpret_cast<float2 *>(smem_raw);            // [56][P1][P1]
+    float2 *stage = Tf + 56 * P1 * P1;                            // [warps][2][64]
+    for (int i = threadIdx.x; i < 56 * P1 * P1; i += blockDim.x) Tf[i] = full[i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int halves = P1 <= 16 ? 2 : 1;
+    const int l = halves == 2 ? (lane & 15) : lane, h = halves == 2 ? (lane >> 4) : 0;
+    const int lr = min(l, P1 - 1);
+    const int nM = 3 * P1;
+    float2 *buf = stage + warp * 2 * 64;
+    const float2 zero = make_float2(0.f, 0.f);
+    for (int ci = blockIdx.x * kM2LSmallWarps + warp; ci < n_cells; ci += gridDim.x * kM2LSmallWarps) {
+        const int cell = cells[ci];
+        const float mlogw = -t.logw[cell];
+        float2 acc[3] = {zero, zero, zero};
+        const int e0 = t.v_ptr[cell], e1 = t.v_ptr[cell + 1];
+        float2 pa = zero, pb = zero;
+        int code = 0;
+        if (e0 < e1) {
+            const float2 *ms = M + (size_t)t.v_idx[e0] * nM;
+            pa = lane < nM ? ms[lane] : zero;
+            pb = lane + 32 < nM ? ms[lane + 32] : zero;
+            code = t.v_code[e0];
+        }
+        int slot = 0;
+        for (int e = e0; e < e1; ++e) {
+            float2 *cur = buf + slot * 64;
+            cur[lane] = pa;
+            cur[lane + 32] = pb;
+            const int b = code & 7, r = (code >> 3) & 3, cj = code >> 5;
+            __syncwarp();
+            if (e + 1 < e1) {
+                const float2 *ms = M + (size_t)t.v_idx[e + 1] * nM;
+                pa = lane < nM ? ms[lane] : zero;
+                pb = lane + 32 < nM ? ms[lane + 32] : zero;
+                code = t.v_code[e + 1];
+            }
+            const float2 *Tl = Tf + ((size_t)(b + 7 * r + 28 * cj) * P1 + lr) * P1;
+            for (int k = h; k < P1; k += halves) {
+                const float2 tk = Tl[k];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) cfma(acc[c], tk, cur[c * P1 + k]);
+            }
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[c].x += mlogw * cur[c * P1].x;   // Mt_0 is real
+            slot ^= 1;
+        }
+        if (halves == 2)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, 16);
+                acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, 16);
+            }
+        if (h == 0 && l < P1)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Lout[((size_t)cell * 3 + c) * P1 + l] = acc[c];
+    }
+}
+
+// ------------------------------------------------ M2L in float-float --
+// The FP64 passes spend most of their time in M2L, and FP64 arithmetic runs
+// at 1/64 of the FP32 rate on this GPU.  This kernel computes the same sums
+// (the symmetric form of m2l_kernel) in float-float arithmetic: every value
+// is an unevaluated sum hi + lo of two floats, products are split exactly
+// with an FMA (TwoProduct) and the leading parts are accumulated with
+// Knuth's TwoSum, the error terms in a second float (the compensated dot
+// product of Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM J.
+// Sci. Comput. 26, 2005).  The result carries about 48 significant bits,
+// ample for the 1e-10 relative residual the FP64 passes serve.
+// A float-float complex value is a float4 (hi.re, hi.im, lo.re, lo.im).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// acc (re, im as hi/lo pairs) += t * m, all float-float complex
+__device__ __forceinline__ void ff_cfma(float4 &acc, const float4 t, const float4 m) {
+    // real part: t.re m.re - t.im m.im
+    float p1 = __fmul_rn(t.x, m.x), e1 = fmaf(t.x, m.x, -p1);
+    float p2 = __fmul_rn(-t.y, m.y), e2 = fmaf(-t.y, m.y, -p2);
+    float s, q1, q2;
+    two_sum(acc.x, p1, s, q1);
+    two_sum(s, p2, acc.x, q2);
+    float lo = fmaf(t.x, m.z, fmaf(t.z, m.x, fmaf(-t.y, m.w, -t.w * m.y)));
+    acc.z += ((q1 + q2) + (e1 + e2)) + lo;
+    // imaginary part: t.re m.im + t.im m.re
+    p1 = __fmul_rn(t.x, m.y);
+    e1 = fmaf(t.x, m.y, -p1);
+    p2 = __fmul_rn(t.y, m.x);
+    e2 = fmaf(t.y, m.x, -p2);
+    two_sum(acc.y, p1, s, q1);
+    two_sum(s, p2, acc.y, q2);
+    lo = fmaf(t.x, m.w, fmaf(t.z, m.y, fmaf(t.y, m.z, t.w * m.x)));
+    acc.w += ((q1 + q2) + (e1 + e2)) + lo;
+}
+
+// acc += v (float-float complex)
+__device__ __forceinline__ void ff_cadd(float4 &acc, const float4 v) {
+    float s, q;
+    two_sum(acc.x, v.x, s, q);
+    acc.x = s;
+    acc.z += q + v.z;
+    two_sum(acc.y, v.y, s, q);
+    acc.y = s;
+    acc.w += q + v.w;
+}
+
+__device__ __forceinline__ float4 ff_from(double2 v) {
+    const float hx = (float)v.x, hy = (float)v.y;
+    return make_float4(hx, hy, (float)(v.x - (double)hx), (float)(v.y - (double)hy));
+}
+
+// v times i^(-n) (exact: a permutation with signs), optionally conjugated first
+__device__ __forceinline__ float4 ff_rot(float4 v, int n) {
+    switch (n & 3) {
+        case 0: return v;
+        case 1: return make_float4(v.y, -v.x, v.w, -v.z);      // times -i
+        case 2: return make_float4(-v.x, -v.y, -v.z, -v.w);    // times -1
+        default: return make_float4(-v.y, v.x, -v.w, v.z);     // times i
+    }
+}
+__device__ __forceinline__ float4 ff_conj(float4 v) { return make_float4(v.x, -v.y, v.z, -v.w); }
+
+constexpr int kM2LffWarps = 8;
+
+inline size_t m2l_ff_smem(int P1) {
+    return (7 * (size_t)P1 * P1 + kM2LffWarps * 2 * 3 * 32) * sizeof(float4);
+}
+
+// One warp per target cell, lane l holds coefficient l (P1 <= 32).  base:
+// the 7 base matrices in float-float, transposed like m2l_kernel's
+// ([b][k][l]).  The source moments of a pair are staged rotated and
+// conjugated (m'_k = conj^cj(M_k i^(-r k))), double buffered.
+static __global__ void __launch_bounds__(32 * kM2LffWarps) m2l_ff_kernel(TreeView<double> t, const int *__restrict__ cells,
+                                                                         int n_cells, int P1,
+                                                                         const float4 *__restrict__ base,
+                                                                         const double2 *__restrict__ M,
+                                                                         double2 *__restrict__ Lout) {
+    extern __shared__ unsigned char smem_raw[];
+    float4 *B = reinterpret_cast<float4 *>(smem_raw);                 // [7][P1][P1]
+    float4 *stage = B + 7 * P1 * P1;                                  // [warps][2][3 * 32]
+    for (int i = threadIdx.x; i < 7 * P1 * P1; i += blockDim.x) B[i] = base[i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nM = 3 * P1;
+    const int lr = min(lane, P1 - 1);
+    float4 *buf = stage + warp * 2 * 96;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int ci = blockIdx.x * kM2LffWarps + warp; ci < n_cells; ci += gridDim.x * kM2LffWarps) {
+        const int cell = cells[ci];
+        const double mlogw = -t.logw[cell];
+        float4 acc[3] = {zero, zero, zero};
+        double acc0[3] = {0.0, 0.0, 0.0};    // the -log(w) Mt_0 term of l = 0, in FP64
+        const int e0 = t.v_ptr[cell], e1 = t.v_ptr[cell + 1];
+        double2 pf[3];
+        int code = 0;
+        auto fetch = [&](int e) {
+            const double2 *ms = M + (size_t)t.v_idx[e] * nM;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const int idx = lane + 32 * j;
+                pf[j] = idx < nM ? ms[idx] : make_double2(0.0, 0.0);
+            }
+            code = t.v_code[e];
+        };
+        if (e0 < e1) fetch(e0);
+        int slot = 0;
+        for (int e = e0; e < e1; ++e) {
+            const int b = code & 7, r = (code >> 3) & 3, cj = code >> 5;
+            float4 *cur = buf + slot * 96;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const int idx = lane + 32 * j;
+                if (idx < nM) {
+                    float4 v = ff_rot(ff_from(pf[j]), r * (idx % P1));
+                    cur[idx] = cj ? ff_conj(v) : v;
+                }
+            }
+            const double2 *ms0 = M + (size_t)t.v_idx[e] * nM;
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc0[c] += mlogw * ms0[c * P1].x;    // Mt_0 is real
+            __syncwarp();
+            if (e + 1 < e1) fetch(e + 1);
+            float4 part[3] = {zero, zero, zero};
+            const float4 *Tb = B + (size_t)b * P1 * P1;
+            for (int k = 0; k < P1; ++k) {
+                const float4 tk = Tb[k * P1 + lr];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) ff_cfma(part[c], tk, cur[c * P1 + k]);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float4 v = cj ? ff_conj(part[c]) : part[c];
+                ff_cadd(acc[c], ff_rot(v, r * lane));
+            }
+            slot ^= 1;
+        }
+        if (lane < P1)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double2 o;
+                o.x = ((double)acc[c].x + (double)acc[c].z) + (lane == 0 ? acc0[c] : 0.0);
+                o.y = (double)acc[c].y + (double)acc[c].w;
+                Lout[((size_t)cell * 3 + c) * P1 + lane] = o;
+            }
+    }
+}
+
 // ---------------------------------------------------------------- P2L --
 template <typename T, typename PS>
 __global__ void __launch_bounds__(kChunk) p2l_kernel(TreeView<T> t, PS ps, const int *__restrict__ cells,
                                                      const T *__restrict__ sb, const T *__restrict__ mb,
                                                      int use_s, int use_m, int P1,
-                                                     typename V2<T>::type *__restrict__ Lout) {
+                                                     typename V2<T>::type *__restrict__ Lout,
+                                                     const long long *__restrict__ row_off = nullptr,
+                                                     const typename V2<T>::type *__restrict__ rows_g = nullptr,
+                                                     const typename V2<T>::type *__restrict__ rows_f = nullptr,
+                                                     typename V2<T>::type *__restrict__ out_g = nullptr,
+                                                     typename V2<T>::type *__restrict__ out_f = nullptr) {
+    // Stored coefficients: row row_off[cell] + r, r counting the pieces of the
+    // cell's list 4 in order, P1 entries each.  rows_g / rows_f: use them (no
+    // geometry); out_g / out_f: write them instead of accumulating.
     using C = typename V2<T>::type;
     extern __shared__ unsigned char smem_raw[];
     C *G = reinterpret_cast<C *>(smem_raw);          // [kChunk][P1] sigma coefficients
@@ -279,13 +553,16 @@ __global__ void __launch_bounds__(kChunk) p2l_kernel(TreeView<T> t, PS ps, const
     const T iw = t.iw[cell], w = 1 / iw, logw = t.logw[cell];
     C acc[3];
     for (int c = 0; c < 3; ++c) acc[c] = mk<T>(0, 0);
+    const long long r0 = row_off ? row_off[cell] : 0;
+    int rr = 0;
     for (int e = t.x_ptr[cell]; e < t.x_ptr[cell + 1]; ++e) {
         const int src = t.x_idx[e];
         const int p0 = t.pstart[src], pn = t.pcount[src];
         for (int base = 0; base < pn; base += kChunk) {
             int cnt = min(kChunk, pn - base);
             __syncthreads();
-            if (tid < cnt) {
+            if (tid < cnt && rows_g) sg[tid] = t.pseg[p0 + base + tid];
+            if (tid < cnt && !rows_g) {
                 int i = p0 + base + tid;
                 T ax, ay, bx, by;
                 ps.rel(i, cell, e, t.x_off, ax, ay, bx, by);
@@ -329,7 +606,20 @@ __global__ void __launch_bounds__(kChunk) p2l_kernel(TreeView<T> t, PS ps, const
             __syncthreads();
             if (tid < P1) {
                 for (int j = 0; j < cnt; ++j) {
-                    C cg = G[j * P1 + tid], cf = F[j * P1 + tid];
+                    const size_t ri = (size_t)(r0 + rr + j) * P1 + tid;
+                    C cg, cf;
+                    if (rows_g) {
+                        cg = rows_g[ri];
+                        cf = rows_f ? rows_f[ri] : mk<T>(0, 0);
+                    } else {
+                        cg = G[j * P1 + tid];
+                        cf = F[j * P1 + tid];
+                    }
+                    if (out_g) {
+                        out_g[ri] = cg;
+                        out_f[ri] = cf;
+                        continue;
+                    }
                     int seg = sg[j];
                     for (int c = 0; c < 3; ++c) {
                         T s = use_s ? sb[3 * (size_t)seg + c] : T(0);
@@ -339,9 +629,10 @@ __global__ void __launch_bounds__(kChunk) p2l_kernel(TreeView<T> t, PS ps, const
                     }
                 }
             }
+            rr += cnt;
         }
     }
-    if (tid < P1)
+    if (tid < P1 && !out_g)
         for (int c = 0; c < 3; ++c) {
             C *o = Lout + ((size_t)cell * 3 + c) * P1 + tid;
             o->x += acc[c].x;
@@ -350,13 +641,16 @@ __global__ void __launch_bounds__(kChunk) p2l_kernel(TreeView<T> t, PS ps, const
 }
 
 // ---------------------------------------------------------------- L2L --
+// One level: L = L_m2l + L2L(parent) (Eq. 73) for the listed cells (the
+// parent term from level 3 on), one warp per cell, lane l holds coefficient l.
 template <typename T>
-__global__ void l2l_kernel(TreeView<T> t, const int *__restrict__ cells, int n, int level, int P1,
-                           const typename V2<T>::type *__restrict__ tab,
-                           const typename V2<T>::type *__restrict__ Lm2l,
-                           typename V2<T>::type *__restrict__ L) {
+__global__ void __launch_bounds__(32 * kLevelWarps) l2l_kernel(TreeView<T> t, const int *__restrict__ cells, int n,
+                                                               int level, int P1,
+                                                               const typename V2<T>::type *__restrict__ tab,
+                                                               const typename V2<T>::type *__restrict__ Lm2l,
+                                                               typename V2<T>::type *__restrict__ L) {
     using C = typename V2<T>::type;
-    const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int idx = blockIdx.x * kLevelWarps + (threadIdx.x >> 5);
     const int l = threadIdx.x & 31;
     if (idx >= n || l >= P1) return;
     const int cell = cells[idx];
@@ -372,6 +666,62 @@ __global__ void l2l_kernel(TreeView<T> t, const int *__restrict__ cells, int n, 
         }
     }
     for (int c = 0; c < 3; ++c) L[((size_t)cell * 3 + c) * P1 + l] = acc[c];
+}
+
+// Incoming expansion of each listed leaf by the recursion of Eq. 73 along its
+// ancestors: L = Lm2l(a_2) at the level-2 ancestor, then L = Lm2l(a) +
+// L2L(L) for each ancestor a below it and the leaf itself (the level-invariant
+// table of the child's quadrant).  Inner cells get no expansion: only leaves
+// hold targets.  One block per leaf, thread l holds coefficient l of the
+// three channels; blockDim >= P1.
+constexpr int kWalkMax = 48;    // ancestors kept (tree depth <= 40)
+
+template <typename T>
+__global__ void walk_kernel(TreeView<T> t, const int *__restrict__ leaves, const int *__restrict__ level,
+                            int P1, const typename V2<T>::type *__restrict__ tab,
+                            const typename V2<T>::type *__restrict__ Lm2l,
+                            typename V2<T>::type *__restrict__ L) {
+    using C = typename V2<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    C *cur = reinterpret_cast<C *>(smem_raw);   // [3][P1]
+    __shared__ int chain[kWalkMax];
+    __shared__ int n_chain;
+    const int leaf = leaves[blockIdx.x];
+    const int l = threadIdx.x;
+    if (l == 0) {
+        int n = 0;
+        for (int c = leaf; c >= 0 && level[c] >= 2 && n < kWalkMax; c = t.parent[c]) chain[n++] = c;
+        n_chain = n;
+    }
+    __syncthreads();
+    const int n = n_chain;
+    C acc[3];
+    for (int c = 0; c < 3; ++c) acc[c] = mk<T>(0, 0);
+    if (n > 0 && l < P1) {
+        const int top = chain[n - 1];
+        for (int c = 0; c < 3; ++c) acc[c] = Lm2l[((size_t)top * 3 + c) * P1 + l];
+    }
+    for (int i = n - 2; i >= 0; --i) {
+        __syncthreads();
+        if (l < P1)
+            for (int c = 0; c < 3; ++c) cur[c * P1 + l] = acc[c];
+        __syncthreads();
+        if (l < P1) {
+            const int a = chain[i];
+            for (int c = 0; c < 3; ++c) acc[c] = Lm2l[((size_t)a * 3 + c) * P1 + l];
+            const C *Tq = tab + ((size_t)t.quad[a] * P1 + l) * P1;
+            for (int k = l; k < P1; ++k) {
+                C tq = Tq[k];
+                for (int c = 0; c < 3; ++c) cfma(acc[c], tq, cur[c * P1 + k]);
+            }
+        }
+    }
+    if (l < P1)
+        for (int c = 0; c < 3; ++c) L[((size_t)leaf * 3 + c) * P1 + l] = acc[c];
+}
+
+template <typename T> inline size_t walk_smem(int P1) {
+    return 3 * (size_t)P1 * sizeof(typename V2<T>::type);
 }
 
 template <typename T> inline size_t p2m_smem(int P1) {
