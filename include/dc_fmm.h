@@ -133,6 +133,8 @@ typedef struct {
                               start per channel (0 otherwise)                */
     double ms_warm;        /* DC_X0_LEARNED: features, network and residual
                               check, host wall time (inside ms_solve)        */
+    int n_refine;          /* FMM forms: outer (iterative refinement) steps,
+                              each one FP64 residual and one inner GMRES     */
 } dc_solve_stats;
 
 typedef struct {
@@ -326,9 +328,10 @@ dc_status dc_aux_set_warm_start_model(dc_ctx *ctx, int hidden, const float *para
 /* Auxiliary: one application of the operator at the nodes, the call
  * FMM(S, sigma, q) of Sec. 5.5 (the matvec of GMRES):
  *   op 0: y = G_H x (single layer, Eq. 19), op 1: y = F_H x (double layer)
- * in the context's form.  With inner = 1 and DC_FORM_FMM32 (op 0 only) it
- * applies the FP32 operator of the inner GMRES instead, y = G_H M^-1 x with
- * M the block diagonal of G_H over panels (order-12 expansions).
+ * in the context's form.  With DC_FORM_FMM32 (op 0 only), inner = 1 applies
+ * the FP32 operator of the inner GMRES instead, y = G_H M^-1 x with M the
+ * block diagonal of G_H over panels (order p_inner), and inner = 2 the same
+ * FP32 operator without M^-1, y = G_H x.
  *   x, y  [n_nodes][3] double, device, caller-owned, distinct
  * Errors: DC_ERR_STATE before dc_build_tree, DC_ERR_ARG for a bad op or
  * pointer, DC_ERR_UNSUPPORTED for inner = 1 in other forms. */

@@ -57,7 +57,7 @@ class dc_solve_stats(ctypes.Structure):
                 ("ms_rhs", ctypes.c_double), ("ms_solve", ctypes.c_double),
                 ("p2p_pairs", ctypes.c_longlong), ("m2l_pairs", ctypes.c_longlong),
                 ("used_warm", ctypes.c_int), ("warm_resid", ctypes.c_double * 3),
-                ("ms_warm", ctypes.c_double)]
+                ("ms_warm", ctypes.c_double), ("n_refine", ctypes.c_int)]
 
 
 class dc_viewport(ctypes.Structure):
@@ -272,8 +272,9 @@ class Context:
 
     def apply_operator(self, x, y, op=0, inner=False):
         """dc_aux_apply_operator: y = G_H x (op 0) or F_H x (op 1) at the
-        nodes; x, y [n_nodes, 3] float64 torch CUDA tensors."""
-        self._check(_get_lib().dc_aux_apply_operator(self._h, int(op), int(bool(inner)), _ptr(x),
+        nodes; x, y [n_nodes, 3] float64 torch CUDA tensors; inner 1 / 2:
+        the FP32 inner operator with / without the preconditioner."""
+        self._check(_get_lib().dc_aux_apply_operator(self._h, int(op), int(inner), _ptr(x),
                                                      _ptr(y)))
         return y
 

@@ -455,6 +455,7 @@ dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats)
     dc::GmresResult gr;
     std::string msg;
     cudaError_t ce;
+    int n_refine = 0;
     if (ctx->opt.form == DC_FORM_DENSE64) {
         DenseOp op;
         op.A = ctx->AG.ptr;
@@ -462,7 +463,7 @@ dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats)
         ce = dc::gmres_solve(ctx->gw, op, N, ctx->b.ptr, ctx->sigma.ptr, ctx->opt.gmres_tol,
                              ctx->opt.gmres_restart, ctx->opt.gmres_max_iter, s, gr, msg);
     } else {
-        ce = ctx->fmm->solve(ctx->gw, ctx->b.ptr, ctx->sigma.ptr, ctx->opt, s, gr, msg);
+        ce = ctx->fmm->solve(ctx->gw, ctx->b.ptr, ctx->sigma.ptr, ctx->opt, s, gr, msg, &n_refine);
     }
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, msg.empty() ? "gmres" : msg.c_str());
     DC_CK(ctx, cudaStreamSynchronize(s), "gmres");
@@ -474,6 +475,7 @@ dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats)
         }
         stats->converged = gr.converged;
         stats->n_matvec = gr.n_matvec + 1;
+        stats->n_refine = n_refine;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         stats->ms_rhs = ms;
@@ -813,12 +815,15 @@ dc_status dc_aux_apply_operator(dc_ctx *ctx, int op, int inner, const double *x,
     if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "apply_operator: call build_tree first");
     if ((op != 0 && op != 1) || !x || !y || x == y)
         return fail(ctx, DC_ERR_ARG, "apply_operator: need op 0 or 1 and distinct x, y");
+    if (inner < 0 || inner > 2) return fail(ctx, DC_ERR_ARG, "apply_operator: inner must be 0, 1 or 2");
     if (inner && (ctx->opt.form != DC_FORM_FMM32 || op != 0))
         return fail(ctx, DC_ERR_UNSUPPORTED, "apply_operator: inner needs DC_FORM_FMM32 and op 0");
     cudaStream_t s = ctx->stream;
     const int N = ctx->dg.N;
     if (ctx->opt.form == DC_FORM_DENSE64) {
         DC_CK(ctx, dc::launch_dense_gemv(op == 0 ? ctx->AG.ptr : ctx->AF.ptr, N, x, y, s), "apply_operator");
+    } else if (inner == 2) {
+        DC_CK(ctx, ctx->fmm->apply_inner_raw(x, y, s), "apply_operator");
     } else if (inner) {
         DC_CK(ctx, ctx->fmm->apply_inner(x, y, s), "apply_operator");
     } else if (op == 0) {

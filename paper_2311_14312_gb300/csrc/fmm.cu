@@ -332,6 +332,8 @@ cudaError_t Fmm::Impl::passes(const double *sb, const double *mb, int use_s, int
             rows_ready ? p2m_g64.ptr : nullptr, rows_ready && use_m ? p2m_f64.ptr : nullptr);
         note_launch();
     }
+    // per level: in FP64 the chain through the parents does less arithmetic
+    // than translating every leaf to every ancestor
     for (int l = tree.depth - 1; l >= 2; --l) {
         const int lo = m2m_ptr[l], n = m2m_ptr[l + 1] - lo;
         if (n <= 0) continue;
@@ -668,6 +670,47 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
                 if (!T.is_leaf(c) && sub_pieces[c] > 0) m2m_cells.push_back(c);
     }
     I.m2m_ptr[T.depth + 1] = int(m2m_cells.size());
+    // leaf -> ancestor M2M pairs of every inner cell, chunked for the
+    // one-launch upward pass (cells with several chunks get partial slots)
+    std::vector<int4> mchunks, mred;
+    std::vector<int> pair_leaf;
+    int n_slots = 0;
+    {
+        std::vector<int> stack, lv;
+        for (int a : m2m_cells) {
+            lv.clear();
+            stack.assign(1, a);
+            while (!stack.empty()) {
+                const int c = stack.back();
+                stack.pop_back();
+                if (T.is_leaf(c)) {
+                    if (T.piece_count[c] > 0) lv.push_back(c);
+                } else {
+                    for (int q = 3; q >= 0; --q)
+                        if (sub_pieces[T.child0[c] + q] > 0) stack.push_back(T.child0[c] + q);
+                }
+            }
+            const int beg = int(pair_leaf.size());
+            pair_leaf.insert(pair_leaf.end(), lv.begin(), lv.end());
+            const int nch = (int(lv.size()) + passes::kMultiLeaves - 1) / passes::kMultiLeaves;
+            if (nch == 1) {
+                mchunks.push_back(make_int4(a, beg, int(lv.size()), -1));
+            } else if (nch > 1) {
+                mred.push_back(make_int4(a, n_slots, nch, 0));
+                for (int q = 0; q < nch; ++q) {
+                    const int b = beg + q * passes::kMultiLeaves;
+                    const int cnt = std::min(passes::kMultiLeaves, beg + int(lv.size()) - b);
+                    mchunks.push_back(make_int4(a, b, cnt, n_slots++));
+                }
+            }
+        }
+    }
+    I.n_mchunks = int(mchunks.size());
+    I.n_mred = int(mred.size());
+    I.n_mslots = n_slots;
+    std::vector<float> binom32(32 * 32, 0.f);
+    for (int k = 0; k < 32; ++k)
+        for (int j = 0; j <= k; ++j) binom32[k * 32 + j] = (float)binom(k, j);
     auto make_sched = [&](Schedule &sc, bool nodes_only, std::vector<int> &m2l_c,
                           std::vector<int> &p2l_c, std::vector<int> &l2l_c, std::vector<int> &walk_c) {
         sc.l2l_ptr.assign(T.depth + 2, 0);
@@ -825,6 +868,14 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     UP(I.plen64, plen64);
     UP(I.v_code, vcode);
     UP(I.m2m_cells, m2m_cells);
+    UP(I.mchunks, mchunks);
+    UP(I.mred, mred);
+    UP(I.pair_leaf, pair_leaf);
+    UP(I.binom32, binom32);
+    if (I.fp32 && (e = I.mpart32.alloc((size_t)std::max(n_slots, 1) * 3 * I.P1i)) != cudaSuccess) {
+        err = std::string("fmm allocation: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
+    }
     UP(I.level_d, T.level);
     UP(I.sched_all.walk, aw);
     UP(I.sched_all.l2l, al2l);
@@ -924,6 +975,11 @@ cudaError_t Fmm::apply_inner(const double *x, double *y, cudaStream_t st) {
     return impl_->graph_matvec32(x, y, st);
 }
 
+cudaError_t Fmm::apply_inner_raw(const double *x, double *y, cudaStream_t st) {
+    if (!impl_->fp32) return cudaErrorNotSupported;
+    return impl_->apply_nodes32(x, y, true, st);
+}
+
 namespace {
 // v -> A M^-1 v with M the panel-block preconditioner (right preconditioning).
 struct PrecOp : Operator {
@@ -939,7 +995,7 @@ struct PrecOp : Operator {
 }  // namespace
 
 cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_options &opt,
-                       cudaStream_t st, GmresResult &res, std::string &err) {
+                       cudaStream_t st, GmresResult &res, std::string &err, int *n_refine) {
     // Iterative refinement around right-preconditioned GMRES:
     //   r = b - A x            (FP64 FMM operator)
     //   z = GMRES(A' M^-1, 0, r, tol')   A' = FP64 or FP32 FMM operator,
@@ -957,7 +1013,9 @@ cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_option
     if (e != cudaSuccess) return e;
     const int max_outer = I.fp32 ? 12 : 4;
     int used = 0;
+    if (n_refine) *n_refine = 0;
     for (int outer = 0; outer <= max_outer; ++outer) {
+        if (n_refine) *n_refine = outer;
         if ((e = I.apply_nodes(x, I.ir_t.ptr, true, st)) != cudaSuccess) return e;
         res.n_matvec++;
         if ((e = vec_residual(b, I.ir_t.ptr, I.ir_r.ptr, 3 * N, st)) != cudaSuccess) return e;

@@ -24,9 +24,12 @@ public:
     // (order-12 expansions, block-Jacobi preconditioner M), through the
     // captured graph.  cudaErrorNotSupported for the FP64 form.
     cudaError_t apply_inner(const double *x, double *y, cudaStream_t st);
+    // The FP32 operator without the preconditioner, y = G_H x.
+    cudaError_t apply_inner_raw(const double *x, double *y, cudaStream_t st);
     // GMRES with this operator (Alg. 3 line 5); x holds x0 on entry.
+    // n_refine: outer refinement steps taken.
     cudaError_t solve(GmresWork *w, const double *b, double *x, const dc_options &opt,
-                      cudaStream_t st, GmresResult &res, std::string &err);
+                      cudaStream_t st, GmresResult &res, std::string &err, int *n_refine = nullptr);
     // Forms the expansions of segment densities sbar and mbar (Alg. 8 up and
     // down passes); render_grid / eval_points then evaluate them.
     cudaError_t prepare_eval(const double *sbar, const double *mbar, cudaStream_t st);

@@ -604,12 +604,15 @@ cudaError_t Fmm::Impl::passes32(const float *sb, const float *mb, int use_s, int
             tv, ps, p2m_leaves.ptr, sb, mb, use_s, use_m, P1, M32i.ptr, rows_ready && !use_m ? p2m_g32.ptr : nullptr);
         note_launch();
     }
-    for (int l = tree.depth - 1; l >= 2; --l) {
-        const int lo = m2m_ptr[l], n = m2m_ptr[l + 1] - lo;
-        if (n <= 0) continue;
-        passes::m2m_kernel<float><<<(n + passes::kLevelWarps - 1) / passes::kLevelWarps, 32 * passes::kLevelWarps, 0, st>>>(
-            child0.ptr, m2m_cells.ptr + lo, n, P1, m2m32i.ptr, M32i.ptr);
+    if (n_mchunks > 0) {   // every inner cell straight from its leaves
+        passes::m2m_multi_kernel<float><<<(n_mchunks + passes::kMultiWarps - 1) / passes::kMultiWarps,
+                                          32 * passes::kMultiWarps, 0, st>>>(
+            cc.ptr, iw32.ptr, mchunks.ptr, n_mchunks, pair_leaf.ptr, P1, binom32.ptr, M32i.ptr, mpart32.ptr);
         note_launch();
+        if (n_mred > 0) {
+            passes::m2m_reduce_kernel<float><<<(n_mred + 3) / 4, 128, 0, st>>>(mred.ptr, n_mred, P1, mpart32.ptr, M32i.ptr);
+            note_launch();
+        }
     }
     if (sc.n_m2l > 0 && P1 <= passes::kM2LSmallP1) {
         int grid = std::min((sc.n_m2l + passes::kM2LSmallWarps - 1) / passes::kM2LSmallWarps, 2 * n_sms);

@@ -127,6 +127,14 @@ struct Fmm::Impl {
     Schedule sched_all, sched_nodes;
     DevBuf<int> m2m_cells, v_code;
     std::vector<int> m2m_ptr;         // [depth + 2]: inner cells with pieces, by level
+    // one-launch upward pass of the FP32 operator: chunks (ancestor, first
+    // pair, pairs, slot), reductions (cell, first slot, slots), leaves of the
+    // pairs, C(k, j)
+    DevBuf<int4> mchunks, mred;
+    DevBuf<int> pair_leaf;
+    DevBuf<float> binom32;
+    DevBuf<float2> mpart32;
+    int n_mchunks = 0, n_mred = 0, n_mslots = 0;
     DevBuf<int> level_d;              // cell levels (downward walk)
     DevBuf<double2> base64, Lm2l;
     DevBuf<float4> baseff;            // base M2L tables in float-float

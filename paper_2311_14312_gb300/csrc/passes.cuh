@@ -8,6 +8,8 @@
 //               chunk in order (deterministic)
 //               (or from stored per-piece coefficient rows)
 //  m2m_kernel   per level, parent from its 4 children (Eq. 71)
+//  m2m_multi_kernel  every inner cell straight from its leaves (all levels
+//               in one launch, no chain of dependent levels)
 //  m2l_kernel   all cells at once, persistent blocks: list 2 (Eq. 69) with
 //               the 40 offset matrices reduced by the symmetries of the
 //               square to 7 base matrices held in shared memory:
@@ -241,6 +243,94 @@ __global__ void __launch_bounds__(32 * kLevelWarps) m2m_kernel(const int *__rest
         }
     }
     for (int c = 0; c < 3; ++c) M[((size_t)cell * 3 + c) * P1 + k] = acc[c];
+}
+
+// M2M from each leaf straight to every listed ancestor, all levels in one
+// launch: Eq. 71 with the shift d = (c_leaf - c_anc) / w_anc and the scale
+// rho = w_leaf / w_anc of the width-scaled basis,
+//   Mt_anc[k] += sum_{j <= k} C(k, j) d^(k - j) rho^j Mt_leaf[j].
+// No level waits for another (each leaf moment is translated once per
+// ancestor instead of through the chain of parents).  One warp per chunk of
+// up to kMultiLeaves (ancestor, leaf) pairs, lane k holds coefficient k; a
+// chunk writes the ancestor's expansion when it is the cell's only chunk,
+// else a partial sum that m2m_reduce_kernel adds up in chunk order.
+constexpr int kMultiLeaves = 16;
+constexpr int kMultiWarps = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kMultiWarps) m2m_multi_kernel(const double *__restrict__ cc,
+                                                                     const T *__restrict__ iw,
+                                                                     const int4 *__restrict__ chunks, int n_chunks,
+                                                                     const int *__restrict__ pair_leaf, int P1,
+                                                                     const T *__restrict__ binom,
+                                                                     typename V2<T>::type *__restrict__ M,
+                                                                     typename V2<T>::type *__restrict__ partial) {
+    using C = typename V2<T>::type;
+    __shared__ C zp[kMultiWarps][32];
+    __shared__ T rp[kMultiWarps][32];
+    __shared__ C ms[kMultiWarps][96];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ci = blockIdx.x * kMultiWarps + warp;
+    if (ci >= n_chunks) return;
+    const int4 ch = chunks[ci];          // (ancestor, first pair, pairs, partial slot or -1)
+    const int anc = ch.x;
+    const double ax = cc[2 * anc], ay = cc[2 * anc + 1];
+    const T iwa = iw[anc];
+    C acc[3];
+    for (int c = 0; c < 3; ++c) acc[c] = mk<T>(0, 0);
+    const int nM = 3 * P1;
+    for (int e = ch.y; e < ch.y + ch.z; ++e) {
+        const int leaf = pair_leaf[e];
+        // d^lane and rho^lane by binary powering (5 squarings)
+        const C d = mk<T>((T)((cc[2 * leaf] - ax) * (double)iwa), (T)((cc[2 * leaf + 1] - ay) * (double)iwa));
+        const T rho = iwa / iw[leaf];
+        C pz = mk<T>(1, 0), bz = d;
+        T pr = 1, br = rho;
+        for (int bit = 1; bit < 32; bit <<= 1) {
+            if (lane & bit) {
+                pz = cmul(pz, bz);
+                pr *= br;
+            }
+            bz = cmul(bz, bz);
+            br *= br;
+        }
+        __syncwarp();
+        zp[warp][lane] = pz;
+        rp[warp][lane] = pr;
+        const C *src = M + (size_t)leaf * nM;
+        for (int i = lane; i < nM; i += 32) ms[warp][i] = src[i];
+        __syncwarp();
+        if (lane < P1) {
+            const int k = lane;
+            const T *bk = binom + k * 32;
+            for (int j = 0; j <= k; ++j) {
+                const C co = cscl(zp[warp][k - j], bk[j] * rp[warp][j]);
+                for (int c = 0; c < 3; ++c) cfma(acc[c], co, ms[warp][c * P1 + j]);
+            }
+        }
+    }
+    if (lane < P1) {
+        C *dst = ch.w < 0 ? M + (size_t)anc * nM : partial + (size_t)ch.w * nM;
+        for (int c = 0; c < 3; ++c) dst[c * P1 + lane] = acc[c];
+    }
+}
+
+// Cells whose leaves span several chunks: M = sum of the chunk partials in
+// chunk order (deterministic).  red = (cell, first slot, slots).
+template <typename T>
+__global__ void m2m_reduce_kernel(const int4 *__restrict__ red, int n, int P1,
+                                  const typename V2<T>::type *__restrict__ partial,
+                                  typename V2<T>::type *__restrict__ M) {
+    using C = typename V2<T>::type;
+    const int i = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const int4 r = red[i];
+    const int nM = 3 * P1;
+    for (int t = lane; t < nM; t += 32) {
+        C a = mk<T>(0, 0);
+        for (int q = 0; q < r.z; ++q) a = cadd(a, partial[(size_t)(r.y + q) * nM + t]);
+        M[(size_t)r.x * nM + t] = a;
+    }
 }
 
 // ---------------------------------------------------------------- M2L --

@@ -20,13 +20,14 @@ from __future__ import annotations
 import argparse
 
 
-def _context():
+def _context(p_inner=0, inner_tol=0.0, leaf_size=64):
     from dc_synth import drawing_by_name
 
     from . import Context
     d = drawing_by_name("mixed200")
-    ctx = Context(form="fmm32", g=d.g, s_per_panel=d.s_per_panel, p=24, leaf_size=64,
-                  gmres_tol=1e-10, gmres_restart=200, gmres_max_iter=3000)
+    ctx = Context(form="fmm32", g=d.g, s_per_panel=d.s_per_panel, p=24, leaf_size=leaf_size,
+                  gmres_tol=1e-10, gmres_restart=200, gmres_max_iter=3000, p_inner=p_inner,
+                  inner_tol=inner_tol)
     ctx.build_drawing(d)
     st = ctx.solve_density()
     return ctx, st
@@ -53,12 +54,17 @@ def main(argv=None):
     ap.add_argument("what", choices=["render", "matvec", "solve"])
     ap.add_argument("--size", type=int, default=512)
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--p-inner", type=int, default=0, help="options.p_inner (0 = default)")
+    ap.add_argument("--inner-tol", type=float, default=0.0, help="options.inner_tol (0 = default)")
+    ap.add_argument("--leaf-size", type=int, default=64)
     a = ap.parse_args(argv)
-    ctx, st = _context()
+    ctx, st = _context(a.p_inner, a.inner_tol, a.leaf_size)
+    if a.what == "solve":      # a second solve: steady state (graphs and buffers exist)
+        st = ctx.solve_density()
     if a.what == "solve":
         sz = ctx.sizes()
         print(f"solve {st.ms_solve:.1f} ms (rhs {st.ms_rhs:.2f} ms) iters {list(st.iters)} "
-              f"matvecs {st.n_matvec} resid {max(st.rel_resid):.2e}")
+              f"matvecs {st.n_matvec} refinement steps {st.n_refine} resid {max(st.rel_resid):.2e}")
         print(f"tree: nodes {sz.n_nodes} segments {sz.n_segments} pieces {sz.n_pieces} cells "
               f"{sz.n_cells} leaves {sz.n_leaves} depth {sz.depth}; per matvec: near pairs "
               f"{st.p2p_pairs} M2L pairs {st.m2l_pairs}")
@@ -85,6 +91,16 @@ def main(argv=None):
         t_f = _time(lambda: ctx.apply_operator(x, y, 1, False), 3)
         print(f"solve {st.ms_solve:.1f} ms iters {list(st.iters)} matvecs {st.n_matvec}")
         print(f"inner FP32 operator {t_in:.4f} ms; FP64 G_H {t_g:.4f} ms; FP64 F_H {t_f:.4f} ms")
+        # accuracy of the FP32 operator (no preconditioner) against the FP64 one
+        sig = torch.from_numpy(ctx.get_density()).cuda()
+        for name, v in (("random", x), ("solution", sig)):
+            y64 = torch.empty_like(v)
+            y32 = torch.empty_like(v)
+            ctx.apply_operator(v, y64, 0, False)
+            ctx.apply_operator(v, y32, 0, 2)
+            rel = (torch.linalg.norm(y32 - y64, dim=0) / torch.linalg.norm(y64, dim=0)).cpu().numpy()
+            print(f"FP32 operator vs FP64 on the {name} density: relative error per channel "
+                  f"{[f'{r:.2e}' for r in rel]}")
 
 
 if __name__ == "__main__":
