@@ -107,7 +107,7 @@ typedef struct {
                               (0 = min(p, 12))                               */
     double inner_tol;      /* DC_FORM_FMM32: floor of the inner GMRES
                               tolerance per refinement step, in (0, 1)
-                              (0 = 1e-5)                                     */
+                              (0 = 1e-4)                                     */
 } dc_options;
 
 typedef struct {
@@ -329,13 +329,24 @@ dc_status dc_aux_set_warm_start_model(dc_ctx *ctx, int hidden, const float *para
  * FMM(S, sigma, q) of Sec. 5.5 (the matvec of GMRES):
  *   op 0: y = G_H x (single layer, Eq. 19), op 1: y = F_H x (double layer)
  * in the context's form.  With DC_FORM_FMM32 (op 0 only), inner = 1 applies
- * the FP32 operator of the inner GMRES instead, y = G_H M^-1 x with M the
- * block diagonal of G_H over panels (order p_inner), and inner = 2 the same
- * FP32 operator without M^-1, y = G_H x.
+ * the FP32 operator of the inner GMRES instead, y = G_H M x with M the
+ * two-level preconditioner (panel blocks of G_H inverted and a coarse space
+ * of panel constants; order p_inner), inner = 2 the same FP32 operator
+ * without M, y = G_H x, and (any FMM form) inner = 3 the preconditioner
+ * alone, y = M x.
  *   x, y  [n_nodes][3] double, device, caller-owned, distinct
- * Errors: DC_ERR_STATE before dc_build_tree, DC_ERR_ARG for a bad op or
- * pointer, DC_ERR_UNSUPPORTED for inner = 1 in other forms. */
+ * Errors: DC_ERR_STATE before dc_build_tree, DC_ERR_ARG for a bad op,
+ * inner or pointer, DC_ERR_UNSUPPORTED for inner 1..3 in other forms. */
 dc_status dc_aux_apply_operator(dc_ctx *ctx, int op, int inner, const double *x, double *y);
+
+/* Auxiliary: state of the FMM forms' two-level preconditioner (no
+ * counterpart in the paper; it changes the iteration count, not the
+ * solution): out[0] = 1 if the coarse level is in use (else the panel
+ * blocks alone), out[1] = coarse unknowns (panels), out[2] = near panel
+ * pairs, out[3] = max |(Ac^-1 Ac - I)_ij| over sampled entries of the
+ * coarse inverse.  Errors: DC_ERR_STATE before dc_build_tree or in the
+ * dense form. */
+dc_status dc_aux_precond_info(dc_ctx *ctx, double *out);
 
 int dc_abi_version(void);
 

@@ -78,7 +78,7 @@ EXPORTS = ["dc_default_options", "dc_create", "dc_destroy", "dc_build_tree", "dc
            "dc_abi_version", "dc_aux_tree_check", "dc_aux_kernel_launches",
            "dc_eval_points_noalloc", "dc_aux_mlp_param_count", "dc_aux_mlp_workspace_floats",
            "dc_aux_mlp_forward", "dc_aux_mlp_loss_grad", "dc_aux_mlp_adam", "dc_aux_feature_dims",
-           "dc_aux_panel_features", "dc_aux_set_warm_start_model", "dc_aux_apply_operator"]
+           "dc_aux_panel_features", "dc_aux_set_warm_start_model", "dc_aux_apply_operator", "dc_aux_precond_info"]
 
 
 def _load():
@@ -121,6 +121,7 @@ def _load():
     lib.dc_aux_panel_features.argtypes = [P, P, P]
     lib.dc_aux_set_warm_start_model.argtypes = [P, I, P, I]
     lib.dc_aux_apply_operator.argtypes = [P, I, I, P, P]
+    lib.dc_aux_precond_info.argtypes = [P, P]
     for name in EXPORTS:
         if name not in ("dc_destroy", "dc_last_error", "dc_status_string", "dc_abi_version",
                         "dc_aux_kernel_launches", "dc_aux_mlp_param_count",
@@ -273,10 +274,17 @@ class Context:
     def apply_operator(self, x, y, op=0, inner=False):
         """dc_aux_apply_operator: y = G_H x (op 0) or F_H x (op 1) at the
         nodes; x, y [n_nodes, 3] float64 torch CUDA tensors; inner 1 / 2:
-        the FP32 inner operator with / without the preconditioner."""
+        the FP32 inner operator with / without the preconditioner; inner 3:
+        the preconditioner alone."""
         self._check(_get_lib().dc_aux_apply_operator(self._h, int(op), int(inner), _ptr(x),
                                                      _ptr(y)))
         return y
+
+    def precond_info(self) -> dict:
+        """dc_aux_precond_info as a dict."""
+        out = np.zeros(4)
+        self._check(_get_lib().dc_aux_precond_info(self._h, _ptr(out)))
+        return dict(zip(["two_level", "panels", "near_pairs", "inverse_check"], out.tolist()))
 
     # ---------------------------------------------------- warm start --
     def feature_dims(self):

@@ -1,0 +1,426 @@
+// Two-level preconditioner for the single-layer system G_H sigma = b (Eq. 27):
+// the panel block-Jacobi smoother B (inverse self-interaction blocks) and a
+// coarse space of panel-wise constants, applied multiplicatively:
+//
+//   y = Ac^-1 R v            (R: sum over a panel's nodes, Ac ~ R G_H P)
+//   M v = P y + B (v - A~ P y)
+//
+// where P spreads y_j to the nodes of panel j and A~ P approximates G_H P:
+// exact for near panel pairs (closed forms, App. D) and the panel's
+// monopole, l_j G(q_a, c_j), for the others.  M is a fixed linear map, so
+// GMRES on G_H M still converges to the solution of Eq. 27; only the
+// iteration count changes.  Not in the paper (plain GMRES there).
+//
+// The coarse matrix Ac = R A~ P (panels x panels, FP32) is inverted once per
+// drawing by blocked Gauss-Jordan elimination without pivoting (it is
+// strongly diagonal: a panel's self term dominates its row).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "dc_internal.h"
+#include "segint.cuh"
+
+namespace dc {
+
+namespace {
+
+constexpr int kGJ = 32;                 // block size of the Gauss-Jordan inversion
+constexpr float kInv4Pi = 0.0795774715459476679f;
+
+// Monopole kernel of panel j at a node: -log|q - c| / 2pi, in FP32 from
+// FP32 positions (the near pairs subtract exactly this value).
+__device__ __forceinline__ float mono32(float2 q, float2 c) {
+    const float dx = q.x - c.x, dy = q.y - c.y;
+    const float r2 = fmaxf(dx * dx + dy * dy, 1e-30f);
+    return -kInv4Pi * __logf(r2);
+}
+
+// corr[e][m] = (G_H 1_j)(q_{i,m}) - l_j mono32(q_{i,m}, c_j) for the near pair
+// e = (i, j): the exact single layer of panel j with unit density (Lambda
+// reproduces constants) at the nodes of panel i, minus its monopole.
+__global__ void near_pairs_kernel(const int2 *__restrict__ pairs, const double *__restrict__ seg,
+                                  const double *__restrict__ segw, const double *__restrict__ nxy,
+                                  const int *__restrict__ nseg, const int *__restrict__ nseg2,
+                                  const float2 *__restrict__ q32, const float2 *__restrict__ c32,
+                                  const double *__restrict__ plen, int s, int g, double *__restrict__ corr) {
+    const int e = blockIdx.x, m = threadIdx.x;
+    if (m >= g) return;
+    const int2 pr = pairs[e];
+    const int a = pr.x * g + m, j = pr.y;
+    const double qx = nxy[2 * a], qy = nxy[2 * a + 1];
+    const int own1 = nseg[a], own2 = nseg2[a];
+    double acc = 0.0;
+    for (int kk = 0; kk < s; ++kk) {
+        const int k = j * s + kk;
+        const double *q = seg + 4 * (size_t)k;
+        double G, F;
+        seg_gf_f64(qx, qy, q[0], q[1], q[2], q[3], segw[k], k == own1 || k == own2, G, F);
+        acc += G;
+    }
+    corr[(size_t)e * g + m] = acc - plen[j] * (double)mono32(q32[a], c32[j]);
+}
+
+// Ac[i][j] = sum_m (l_j mono32(q_{i,m}, c_j) + corr), padded with the identity
+// to n_pad; one block per row.
+__global__ void coarse_matrix_kernel(const float2 *__restrict__ q32, const float2 *__restrict__ c32,
+                                     const float *__restrict__ plen32, const int *__restrict__ nptr,
+                                     const int2 *__restrict__ pairs, const double *__restrict__ corr,
+                                     int P, int g, int n_pad, float *__restrict__ Ac) {
+    const int i = blockIdx.x;
+    float *row = Ac + (size_t)i * n_pad;
+    if (i >= P) {
+        for (int j = threadIdx.x; j < n_pad; j += blockDim.x) row[j] = (i == j) ? 1.f : 0.f;
+        return;
+    }
+    for (int j = threadIdx.x; j < n_pad; j += blockDim.x) {
+        float v = 0.f;
+        if (j < P) {
+            const float2 c = c32[j];
+            for (int m = 0; m < g; ++m) v += mono32(q32[i * g + m], c);
+            v *= plen32[j];
+        }
+        row[j] = v;
+    }
+    __syncthreads();
+    for (int e = nptr[i]; e < nptr[i + 1]; ++e) {
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int m = 0; m < g; ++m) s += corr[(size_t)e * g + m];
+            row[pairs[e].y] += (float)s;
+        }
+        __syncthreads();
+    }
+}
+
+// Blocked Gauss-Jordan inversion in place (no pivoting), step k:
+// 1. A_kk <- A_kk^-1 (one block, shared memory)
+__global__ void gj_diag_kernel(float *__restrict__ A, int n, int k) {
+    __shared__ float a[kGJ][kGJ + 1];
+    const int t = threadIdx.x;          // column
+    float *D = A + (size_t)k * kGJ * n + k * kGJ;
+    for (int r = 0; r < kGJ; ++r) a[r][t] = D[(size_t)r * n + t];
+    __syncthreads();
+    for (int c = 0; c < kGJ; ++c) {
+        const float piv = a[c][c];
+        __syncthreads();
+        // row c scaled; column c of the inverse replaces column c
+        const float rc = (t == c) ? 1.f / piv : a[c][t] / piv;
+        __syncthreads();
+        a[c][t] = rc;
+        __syncthreads();
+        for (int r = 0; r < kGJ; ++r) {
+            if (r == c) continue;
+            const float f = a[r][c];
+            __syncthreads();
+            a[r][t] = (t == c) ? -f / piv : a[r][t] - f * rc;
+            __syncthreads();
+        }
+    }
+    for (int r = 0; r < kGJ; ++r) D[(size_t)r * n + t] = a[r][t];
+}
+
+// 2. A_kj <- A_kk A_kj for the columns j outside block k (one thread per column)
+__global__ void gj_row_kernel(float *__restrict__ A, int n, int k) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= n || col / kGJ == k) return;
+    float x[kGJ];
+    for (int r = 0; r < kGJ; ++r) x[r] = A[(size_t)(k * kGJ + r) * n + col];
+    for (int r = 0; r < kGJ; ++r) {
+        const float *d = A + (size_t)(k * kGJ + r) * n + k * kGJ;
+        float s = 0.f;
+        for (int t = 0; t < kGJ; ++t) s += d[t] * x[t];
+        A[(size_t)(k * kGJ + r) * n + col] = s;
+    }
+}
+
+// 3. A_ij <- A_ij - A_ik A_kj for rows i and columns j outside block k
+// (64 x 64 output tiles, the 32-wide inner dimension staged in shared memory)
+__global__ void __launch_bounds__(256) gj_update_kernel(float *__restrict__ A, int n, int k) {
+    __shared__ float Aik[64][kGJ + 1];
+    __shared__ float Akj[kGJ][64 + 1];
+    const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (int u = threadIdx.x; u < 64 * kGJ; u += 256) {
+        const int r = u / kGJ, c = u % kGJ;
+        Aik[r][c] = (i0 + r < n) ? A[(size_t)(i0 + r) * n + k * kGJ + c] : 0.f;
+        const int r2 = u / 64, c2 = u % 64;
+        Akj[r2][c2] = (j0 + c2 < n) ? A[(size_t)(k * kGJ + r2) * n + j0 + c2] : 0.f;
+    }
+    __syncthreads();
+    for (int a = 0; a < 4; ++a) {
+        const int i = i0 + ty * 4 + a;
+        if (i >= n || i / kGJ == k) continue;
+        for (int b = 0; b < 4; ++b) {
+            const int j = j0 + tx * 4 + b;
+            if (j >= n || j / kGJ == k) continue;
+            float s = 0.f;
+            for (int t = 0; t < kGJ; ++t) s += Aik[ty * 4 + a][t] * Akj[t][tx * 4 + b];
+            A[(size_t)i * n + j] -= s;
+        }
+    }
+}
+
+// 4. A_ik <- -A_ik A_kk for the rows i outside block k (one thread per row)
+__global__ void gj_col_kernel(float *__restrict__ A, int n, int k) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n || row / kGJ == k) return;
+    float x[kGJ];
+    for (int t = 0; t < kGJ; ++t) x[t] = A[(size_t)row * n + k * kGJ + t];
+    for (int c = 0; c < kGJ; ++c) {
+        float s = 0.f;
+        for (int t = 0; t < kGJ; ++t) s += x[t] * A[(size_t)(k * kGJ + t) * n + k * kGJ + c];
+        A[(size_t)row * n + k * kGJ + c] = -s;
+    }
+}
+
+// ------------------------------------------------------------------ apply --
+// s[j][c] = sum over panel j's nodes of v
+__global__ void restrict_kernel(const double *__restrict__ v, int P, int g, double *__restrict__ s) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * P) return;
+    const int j = t / 3, c = t % 3;
+    double a = 0.0;
+    for (int m = 0; m < g; ++m) a += v[3 * ((size_t)j * g + m) + c];
+    s[t] = a;
+}
+
+// y = Ac^-1 s (one warp per row, fixed-order reduction); ly[j] = l_j y_j (FP32)
+__global__ void coarse_solve_kernel(const float *__restrict__ Ainv, int n_pad, int P,
+                                    const double *__restrict__ s, const float *__restrict__ plen32,
+                                    double *__restrict__ y, float *__restrict__ ly) {
+    const int i = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= P) return;
+    const float *row = Ainv + (size_t)i * n_pad;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int j = lane; j < P; j += 32) {
+        const double w = row[j];
+        a0 += w * s[3 * j];
+        a1 += w * s[3 * j + 1];
+        a2 += w * s[3 * j + 2];
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+    }
+    if (lane == 0) {
+        y[3 * i] = a0;
+        y[3 * i + 1] = a1;
+        y[3 * i + 2] = a2;
+        const float l = plen32[i];
+        ly[3 * i] = l * (float)a0;
+        ly[3 * i + 1] = l * (float)a1;
+        ly[3 * i + 2] = l * (float)a2;
+    }
+}
+
+// The monopoles of all panels at every node, t_q[a] = sum over the panels
+// of part q of l_j y_j mono32(q_a, c_j): kSplit parts in parallel (tiles of
+// panels staged in shared memory), added in order by residual_kernel.
+constexpr int kTile = 256;
+constexpr int kSplit = 4;
+__global__ void __launch_bounds__(128) monopole_kernel(const float2 *__restrict__ q32,
+                                                       const float2 *__restrict__ c32,
+                                                       const float *__restrict__ ly, int P, int N,
+                                                       float *__restrict__ part) {
+    __shared__ float2 sc[kTile];
+    __shared__ float sl[3][kTile];
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int per = (P + kSplit - 1) / kSplit;
+    const int lo = blockIdx.y * per, hi = min(P, lo + per);
+    const float2 q = a < N ? q32[a] : make_float2(0.f, 0.f);
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+    for (int base = lo; base < hi; base += kTile) {
+        const int cnt = min(kTile, hi - base);
+        __syncthreads();
+        for (int u = threadIdx.x; u < cnt; u += blockDim.x) {
+            sc[u] = c32[base + u];
+            sl[0][u] = ly[3 * (base + u)];
+            sl[1][u] = ly[3 * (base + u) + 1];
+            sl[2][u] = ly[3 * (base + u) + 2];
+        }
+        __syncthreads();
+        for (int u = 0; u < cnt; ++u) {
+            const float k = mono32(q, sc[u]);
+            t0 += k * sl[0][u];
+            t1 += k * sl[1][u];
+            t2 += k * sl[2][u];
+        }
+    }
+    if (a >= N) return;
+    float *o = part + ((size_t)blockIdx.y * N + a) * 3;
+    o[0] = t0;
+    o[1] = t1;
+    o[2] = t2;
+}
+
+// r = v - A~ P y: the monopole parts plus the near-pair corrections
+__global__ void residual_kernel(const float *__restrict__ part, int g, const int *__restrict__ nptr,
+                                const int2 *__restrict__ pairs, const double *__restrict__ corr,
+                                const double *__restrict__ y, const double *__restrict__ v, int N,
+                                double *__restrict__ r) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= N) return;
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+    for (int q = 0; q < kSplit; ++q) {
+        const float *o = part + ((size_t)q * N + a) * 3;
+        c0 += o[0];
+        c1 += o[1];
+        c2 += o[2];
+    }
+    const int i = a / g, m = a - i * g;
+    for (int e = nptr[i]; e < nptr[i + 1]; ++e) {
+        const int j = pairs[e].y;
+        const double w = corr[(size_t)e * g + m];
+        c0 += w * y[3 * j];
+        c1 += w * y[3 * j + 1];
+        c2 += w * y[3 * j + 2];
+    }
+    r[3 * (size_t)a] = v[3 * (size_t)a] - c0;
+    r[3 * (size_t)a + 1] = v[3 * (size_t)a + 1] - c1;
+    r[3 * (size_t)a + 2] = v[3 * (size_t)a + 2] - c2;
+}
+
+// w = P y + B r (B: the panels' inverse self-interaction blocks)
+__global__ void smooth_kernel(const double *__restrict__ inv, int P, int g, const double *__restrict__ y,
+                              const double *__restrict__ r, double *__restrict__ w) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= P * g) return;
+    const int j = a / g, m = a - j * g;
+    const double *row = inv + ((size_t)j * g + m) * g;
+    const double *rs = r + (size_t)j * g * 3;
+    double a0 = y[3 * j], a1 = y[3 * j + 1], a2 = y[3 * j + 2];
+    for (int n = 0; n < g; ++n) {
+        const double b = row[n];
+        a0 += b * rs[3 * n];
+        a1 += b * rs[3 * n + 1];
+        a2 += b * rs[3 * n + 2];
+    }
+    w[3 * (size_t)a] = a0;
+    w[3 * (size_t)a + 1] = a1;
+    w[3 * (size_t)a + 2] = a2;
+}
+
+}  // namespace
+
+cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st) {
+    ready_ = false;
+    const int P = G.n_panels, g = G.g, s = G.s, N = G.n_nodes();
+    if (P < 2) return cudaSuccess;
+    P_ = P;
+    g_ = g;
+    // panel centroids (node average) and arc lengths
+    std::vector<double> cen(2 * P), pl(P);
+    std::vector<float2> c32(P), q32(N);
+    std::vector<float> pl32(P);
+    for (int j = 0; j < P; ++j) {
+        double sx = 0, sy = 0;
+        for (int m = 0; m < g; ++m) {
+            sx += G.node_xy[2 * (j * g + m)];
+            sy += G.node_xy[2 * (j * g + m) + 1];
+        }
+        cen[2 * j] = sx / g;
+        cen[2 * j + 1] = sy / g;
+        double L = 0.0;
+        for (int k = 0; k < s; ++k) {
+            const double *q = &G.seg_xy[4 * (size_t)(j * s + k)];
+            L += G.seg_w[j * s + k] * std::hypot(q[2] - q[0], q[3] - q[1]);
+        }
+        pl[j] = L;
+        c32[j] = make_float2((float)cen[2 * j], (float)cen[2 * j + 1]);
+        pl32[j] = (float)L;
+    }
+    for (int a = 0; a < N; ++a) q32[a] = make_float2((float)G.node_xy[2 * a], (float)G.node_xy[2 * a + 1]);
+    // near panel pairs (i, j), i's list in j order: |c_i - c_j| < 1.5 (l_i + l_j)
+    std::vector<int> nptr(P + 1, 0);
+    std::vector<int2> pairs;
+    for (int i = 0; i < P; ++i) {
+        nptr[i] = int(pairs.size());
+        for (int j = 0; j < P; ++j) {
+            const double dx = cen[2 * i] - cen[2 * j], dy = cen[2 * i + 1] - cen[2 * j + 1];
+            const double lim = 1.5 * (pl[i] + pl[j]);
+            if (dx * dx + dy * dy < lim * lim) pairs.push_back(make_int2(i, j));
+        }
+    }
+    nptr[P] = int(pairs.size());
+    n_pad_ = (P + kGJ - 1) / kGJ * kGJ;
+    cudaError_t e;
+    auto up = [&](auto &buf, const auto &v) -> cudaError_t {
+        cudaError_t r = buf.alloc(std::max<size_t>(v.size(), 1));
+        if (r != cudaSuccess || v.empty()) return r;
+        return cudaMemcpyAsync(buf.ptr, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice, st);
+    };
+    if ((e = up(c32_, c32)) != cudaSuccess || (e = up(q32_, q32)) != cudaSuccess ||
+        (e = up(plen_, pl)) != cudaSuccess || (e = up(plen32_, pl32)) != cudaSuccess ||
+        (e = up(nptr_, nptr)) != cudaSuccess || (e = up(pairs_, pairs)) != cudaSuccess)
+        return e;
+    if ((e = corr_.alloc(pairs.size() * (size_t)g)) != cudaSuccess ||
+        (e = Ainv_.alloc((size_t)n_pad_ * n_pad_)) != cudaSuccess || (e = s_.alloc(3 * (size_t)P)) != cudaSuccess ||
+        (e = y_.alloc(3 * (size_t)P)) != cudaSuccess || (e = ly_.alloc(3 * (size_t)P)) != cudaSuccess ||
+        (e = r_.alloc(3 * (size_t)N)) != cudaSuccess || (e = part_.alloc((size_t)kSplit * 3 * N)) != cudaSuccess)
+        return e;
+    near_pairs_kernel<<<(unsigned)pairs.size(), 32, 0, st>>>(pairs_.ptr, D.seg.ptr, D.segw.ptr, D.node_xy.ptr,
+                                                            D.node_seg.ptr, D.node_seg2.ptr, q32_.ptr, c32_.ptr,
+                                                            plen_.ptr, s, g, corr_.ptr);
+    note_launch();
+    coarse_matrix_kernel<<<n_pad_, 256, 0, st>>>(q32_.ptr, c32_.ptr, plen32_.ptr, nptr_.ptr, pairs_.ptr,
+                                                corr_.ptr, P, g, n_pad_, Ainv_.ptr);
+    note_launch();
+    // keep the coarse matrix for the check below
+    std::vector<float> Ac_h((size_t)n_pad_ * n_pad_);
+    if ((e = cudaMemcpyAsync(Ac_h.data(), Ainv_.ptr, Ac_h.size() * sizeof(float), cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+        return e;
+    const int nb = n_pad_ / kGJ;
+    dim3 ug((n_pad_ + 63) / 64, (n_pad_ + 63) / 64);
+    for (int k = 0; k < nb; ++k) {
+        gj_diag_kernel<<<1, kGJ, 0, st>>>(Ainv_.ptr, n_pad_, k);
+        gj_row_kernel<<<(n_pad_ + 127) / 128, 128, 0, st>>>(Ainv_.ptr, n_pad_, k);
+        gj_update_kernel<<<ug, 256, 0, st>>>(Ainv_.ptr, n_pad_, k);
+        gj_col_kernel<<<(n_pad_ + 127) / 128, 128, 0, st>>>(Ainv_.ptr, n_pad_, k);
+        note_launch(4);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // check the inverse on a few rows (a vanished or tiny pivot shows up as
+    // non-finite entries or a large error): keep the one-level
+    // preconditioner unless it is accurate
+    std::vector<float> Ai_h((size_t)n_pad_ * n_pad_);
+    if ((e = cudaMemcpyAsync(Ai_h.data(), Ainv_.ptr, Ai_h.size() * sizeof(float), cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    for (float v : Ai_h)
+        if (!std::isfinite(v)) return cudaSuccess;
+    double worst = 0.0;
+    const int checks[5] = {0, P / 4, P / 2, (3 * P) / 4, P - 1};
+    for (int ci = 0; ci < 5; ++ci) {
+        const int r = checks[ci];
+        for (int c = ci; c < n_pad_; c += 7) {
+            double acc = 0.0;
+            for (int k = 0; k < n_pad_; ++k) acc += (double)Ai_h[(size_t)r * n_pad_ + k] * Ac_h[(size_t)k * n_pad_ + c];
+            worst = std::max(worst, std::fabs(acc - (r == c ? 1.0 : 0.0)));
+        }
+    }
+    check_ = worst;
+    n_pairs_ = int(pairs.size());
+    if (!(worst < 1e-2)) return cudaSuccess;
+    ready_ = true;
+    return cudaSuccess;
+}
+
+cudaError_t TwoLevel::apply(const double *inv, const double *v, double *w, cudaStream_t st) {
+    const int P = P_, g = g_, N = P * g;
+    restrict_kernel<<<(3 * P + 255) / 256, 256, 0, st>>>(v, P, g, s_.ptr);
+    coarse_solve_kernel<<<(P + 3) / 4, 128, 0, st>>>(Ainv_.ptr, n_pad_, P, s_.ptr, plen32_.ptr, y_.ptr, ly_.ptr);
+    monopole_kernel<<<dim3((N + 127) / 128, kSplit), 128, 0, st>>>(q32_.ptr, c32_.ptr, ly_.ptr, P, N, part_.ptr);
+    residual_kernel<<<(N + 255) / 256, 256, 0, st>>>(part_.ptr, g, nptr_.ptr, pairs_.ptr, corr_.ptr, y_.ptr, v, N,
+                                                    r_.ptr);
+    smooth_kernel<<<(N + 255) / 256, 256, 0, st>>>(inv, P, g, y_.ptr, r_.ptr, w);
+    note_launch(5);
+    return cudaGetLastError();
+}
+
+}  // namespace dc

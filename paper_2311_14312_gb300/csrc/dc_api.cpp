@@ -815,13 +815,17 @@ dc_status dc_aux_apply_operator(dc_ctx *ctx, int op, int inner, const double *x,
     if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "apply_operator: call build_tree first");
     if ((op != 0 && op != 1) || !x || !y || x == y)
         return fail(ctx, DC_ERR_ARG, "apply_operator: need op 0 or 1 and distinct x, y");
-    if (inner < 0 || inner > 2) return fail(ctx, DC_ERR_ARG, "apply_operator: inner must be 0, 1 or 2");
-    if (inner && (ctx->opt.form != DC_FORM_FMM32 || op != 0))
+    if (inner < 0 || inner > 3) return fail(ctx, DC_ERR_ARG, "apply_operator: inner must be 0..3");
+    if (inner == 3 && (!ctx->fmm || op != 0))
+        return fail(ctx, DC_ERR_UNSUPPORTED, "apply_operator: inner 3 needs an FMM form and op 0");
+    if ((inner == 1 || inner == 2) && (ctx->opt.form != DC_FORM_FMM32 || op != 0))
         return fail(ctx, DC_ERR_UNSUPPORTED, "apply_operator: inner needs DC_FORM_FMM32 and op 0");
     cudaStream_t s = ctx->stream;
     const int N = ctx->dg.N;
     if (ctx->opt.form == DC_FORM_DENSE64) {
         DC_CK(ctx, dc::launch_dense_gemv(op == 0 ? ctx->AG.ptr : ctx->AF.ptr, N, x, y, s), "apply_operator");
+    } else if (inner == 3) {
+        DC_CK(ctx, ctx->fmm->apply_precond(x, y, s), "apply_operator");
     } else if (inner == 2) {
         DC_CK(ctx, ctx->fmm->apply_inner_raw(x, y, s), "apply_operator");
     } else if (inner) {
@@ -831,6 +835,15 @@ dc_status dc_aux_apply_operator(dc_ctx *ctx, int op, int inner, const double *x,
     } else {
         DC_CK(ctx, ctx->fmm->apply_double_layer(x, y, s), "apply_operator");
     }
+    return DC_OK;
+}
+
+dc_status dc_aux_precond_info(dc_ctx *ctx, double *out) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (!out) return fail(ctx, DC_ERR_ARG, "precond_info: NULL output");
+    if (ctx->state < 1 || !ctx->fmm) return fail(ctx, DC_ERR_STATE, "precond_info: needs an FMM form after build_tree");
+    ctx->fmm->precond_info(out);
     return DC_OK;
 }
 

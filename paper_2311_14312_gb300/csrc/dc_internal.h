@@ -150,6 +150,35 @@ private:
     DevBuf<int> nbr_;
 };
 
+// Two-level preconditioner (coarse.cu): M v = P y + B (v - A~ P y),
+// y = Ac^-1 R v, with B the panel blocks' inverses and a coarse space of
+// panel-wise constants.  build() forms the near-pair corrections and inverts
+// the coarse matrix; ready() is false when that failed (one level then).
+class TwoLevel {
+public:
+    cudaError_t build(const Geometry &G, const DevGeom &D, cudaStream_t st);
+    bool ready() const { return ready_; }
+    // panels, near pairs, max |(Ac^-1 Ac - I)_ij| over 5 sampled rows
+    void info(double out[4]) const {
+        out[0] = ready_ ? 1.0 : 0.0;
+        out[1] = P_;
+        out[2] = n_pairs_;
+        out[3] = check_;
+    }
+    // w = M v on [N][3] vectors; inv: the panel blocks' inverses
+    cudaError_t apply(const double *inv, const double *v, double *w, cudaStream_t st);
+
+private:
+    bool ready_ = false;
+    int P_ = 0, g_ = 0, n_pad_ = 0, n_pairs_ = 0;
+    double check_ = -1.0;
+    DevBuf<float2> c32_, q32_;
+    DevBuf<double> plen_, corr_, s_, y_, r_;
+    DevBuf<float> plen32_, ly_, Ainv_, part_;
+    DevBuf<int> nptr_;
+    DevBuf<int2> pairs_;
+};
+
 // --------------------------------------------------------------- GMRES --
 // Matrix-free operator y = A x on [N][3] FP64 vectors (all 3 channels).
 struct Operator {
@@ -162,6 +191,7 @@ struct GmresResult {
     double rel_resid[3] = {0, 0, 0};
     int converged = 0;
     int n_matvec = 0;
+    int stagnated = 0;   // stopped at the operator's own error level
 };
 
 struct GmresWork;   // device workspace (gmres.cu)

@@ -932,6 +932,11 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
                 return DC_ERR_GEOMETRY;
             }
     }
+    // two-level preconditioner (panel blocks + coarse space of panel constants)
+    if ((e = I.coarse.build(G, D, st)) != cudaSuccess) {
+        err = std::string("fmm coarse preconditioner: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
+    }
     cudaFuncSetAttribute(passes::m2l_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)passes::m2l_ff_smem(I.P1));
     cudaFuncSetAttribute(passes::m2l_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -970,9 +975,20 @@ cudaError_t Fmm::apply_double_layer(const double *x, double *y, cudaStream_t st)
     return impl_->apply_nodes(x, y, false, st);
 }
 
+// w = M v: the two-level preconditioner, or the panel blocks alone when the
+// coarse matrix could not be inverted.
+cudaError_t Fmm::Impl::precond(const double *v, double *w, cudaStream_t st) {
+    if (coarse.ready()) return coarse.apply(pinv.ptr, v, w, st);
+    return launch_block_apply(pinv.ptr, D->n_panels, D->g, v, w, st);
+}
+
 cudaError_t Fmm::apply_inner(const double *x, double *y, cudaStream_t st) {
     if (!impl_->fp32) return cudaErrorNotSupported;
     return impl_->graph_matvec32(x, y, st);
+}
+
+cudaError_t Fmm::apply_precond(const double *x, double *y, cudaStream_t st) {
+    return impl_->precond(x, y, st);
 }
 
 cudaError_t Fmm::apply_inner_raw(const double *x, double *y, cudaStream_t st) {
@@ -981,13 +997,13 @@ cudaError_t Fmm::apply_inner_raw(const double *x, double *y, cudaStream_t st) {
 }
 
 namespace {
-// v -> A M^-1 v with M the panel-block preconditioner (right preconditioning).
+// v -> A M v with M the two-level preconditioner (right preconditioning).
 struct PrecOp : Operator {
     Fmm::Impl *f;
     bool fp32 = false;
     cudaError_t apply(const double *v, double *y, cudaStream_t st) override {
         if (fp32) return f->graph_matvec32(v, y, st);
-        cudaError_t e = launch_block_apply(f->pinv.ptr, f->D->n_panels, f->D->g, v, f->ir_t.ptr, st);
+        cudaError_t e = f->precond(v, f->ir_t.ptr, st);
         if (e != cudaSuccess) return e;
         return f->apply_nodes(f->ir_t.ptr, y, true, st);
     }
@@ -998,9 +1014,11 @@ cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_option
                        cudaStream_t st, GmresResult &res, std::string &err, int *n_refine) {
     // Iterative refinement around right-preconditioned GMRES:
     //   r = b - A x            (FP64 FMM operator)
-    //   z = GMRES(A' M^-1, 0, r, tol')   A' = FP64 or FP32 FMM operator,
-    //                                    M = block diagonal of G_H (panels)
-    //   x += M^-1 z
+    //   z = GMRES(A' M, 0, r, tol')      A' = FP64 or FP32 FMM operator,
+    //                                    M = two-level preconditioner: panel
+    //                                    blocks of G_H inverted + a coarse
+    //                                    space of panel constants
+    //   x += M z
     // until ||r|| <= tol ||b|| per channel.  The preconditioner changes the
     // iteration, not the discrete solution of Eq. 27.
     Impl &I = *impl_;
@@ -1035,7 +1053,7 @@ cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_option
         if (outer == max_outer || used >= opt.gmres_max_iter) break;
         if ((e = vec_mask3(I.ir_r.ptr, N, mask, st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(I.ir_d.ptr, 0, sizeof(double) * 3 * N, st)) != cudaSuccess) return e;
-        const double floor32 = opt.inner_tol > 0.0 ? opt.inner_tol : 1e-5;
+        const double floor32 = opt.inner_tol > 0.0 ? opt.inner_tol : 1e-4;
         double inner_tol = I.fp32 ? std::max(floor32, need) : std::max(0.5 * need, 1e-15);
         GmresResult inner;
         op.fp32 = I.fp32;
@@ -1049,7 +1067,7 @@ cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_option
         }
         used += std::max(mx, 1);
         res.n_matvec += inner.n_matvec;
-        if ((e = launch_block_apply(I.pinv.ptr, I.D->n_panels, I.D->g, I.ir_d.ptr, I.ir_t.ptr, st)) !=
+        if ((e = I.precond(I.ir_d.ptr, I.ir_t.ptr, st)) !=
             cudaSuccess)
             return e;
         if ((e = vec_axpy(x, I.ir_t.ptr, 3 * N, st)) != cudaSuccess) return e;
@@ -1247,6 +1265,7 @@ void Fmm::fill_sizes(dc_sizes *out) const {
 }
 
 long long Fmm::p2p_pairs_nodes() const { return impl_->p2p_nodes; }
+void Fmm::precond_info(double out[4]) const { impl_->coarse.info(out); }
 long long Fmm::m2l_pairs() const { return impl_->m2l_cnt; }
 long long Fmm::last_render_p2p_pairs() const { return impl_->render_pairs; }
 long long Fmm::last_render_m2p_pairs() const { return impl_->render_m2p; }

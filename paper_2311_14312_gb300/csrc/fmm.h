@@ -20,10 +20,12 @@ public:
     cudaError_t apply_single_layer(const double *x, double *y, cudaStream_t st);
     // y = F_H x at the nodes (double layer), for the right-hand side.
     cudaError_t apply_double_layer(const double *x, double *y, cudaStream_t st);
-    // The FP32 inner operator of the iterative refinement: y = G_H M^-1 x
-    // (order-12 expansions, block-Jacobi preconditioner M), through the
-    // captured graph.  cudaErrorNotSupported for the FP64 form.
+    // The FP32 inner operator of the iterative refinement: y = G_H M x
+    // (order p_inner, two-level preconditioner M), through the captured
+    // graph.  cudaErrorNotSupported for the FP64 form.
     cudaError_t apply_inner(const double *x, double *y, cudaStream_t st);
+    // The preconditioner alone, y = M x.
+    cudaError_t apply_precond(const double *x, double *y, cudaStream_t st);
     // The FP32 operator without the preconditioner, y = G_H x.
     cudaError_t apply_inner_raw(const double *x, double *y, cudaStream_t st);
     // GMRES with this operator (Alg. 3 line 5); x holds x0 on entry.
@@ -42,6 +44,8 @@ public:
     dc_status eval_points(const double *xy, int n, const double *sbar, const double *mbar,
                           void *out, int out_dtype, cudaStream_t st, std::string &err);
     void fill_sizes(dc_sizes *out) const;
+    // two-level preconditioner: ready, panels, near pairs, inverse check
+    void precond_info(double out[4]) const;
     long long p2p_pairs_nodes() const;
     long long m2l_pairs() const;
     long long last_render_p2p_pairs() const;

@@ -714,7 +714,7 @@ cudaError_t Fmm::Impl::graph_matvec32(const double *x, double *y, cudaStream_t s
             return e;
         long long before = kernel_launches();
         if ((e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
-        cudaError_t e1 = launch_block_apply(pinv.ptr, D->n_panels, D->g, g_in.ptr, ir_t.ptr, cap_stream);
+        cudaError_t e1 = precond(g_in.ptr, ir_t.ptr, cap_stream);
         cudaError_t e2 = (e1 == cudaSuccess) ? apply_nodes32(ir_t.ptr, g_out.ptr, true, cap_stream) : e1;
         e = cudaStreamEndCapture(cap_stream, &g32);
         g32_kernels = int(kernel_launches() - before);

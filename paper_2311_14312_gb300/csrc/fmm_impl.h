@@ -122,6 +122,8 @@ struct Fmm::Impl {
     int n_nt_items = 0;
     DevBuf<double> ir_r, ir_d, ir_t;   // refinement residual, correction, scratch
     DevBuf<double> pinv;          // [panels][g][g] inverse self-interaction blocks
+    TwoLevel coarse;              // coarse space of panel constants
+    cudaError_t precond(const double *v, double *w, cudaStream_t st);
     DevBuf<int> pinfo;
     // pass schedules and tables of the templated passes
     Schedule sched_all, sched_nodes;

@@ -448,6 +448,12 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
         return ce;
     int total = 0;
     bool done_all = false;
+    // a cycle that ends with every channel converged by the Givens estimate
+    // while the recomputed residual has not even halved since the cycle
+    // began means the operator's own error (an inexact, e.g. FP32, matvec)
+    // is reached: stop, the caller's refinement takes over
+    bool est_done = false;
+    double prev_beta[3] = {0, 0, 0};
     while (true) {
         // r = b - A x ; beta = ||r||
         if ((ce = A.apply(x, W.Ax.ptr, st)) != cudaSuccess) return ce;
@@ -469,6 +475,17 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
             break;
         }
         if (total >= max_iter) break;
+        if (est_done) {
+            bool progress = false;
+            for (int c = 0; c < 3; ++c)
+                if (hbeta[c] > hthr[c] && hbeta[c] < 0.5 * prev_beta[c]) progress = true;
+            if (!progress) {
+                res.stagnated = 1;
+                break;
+            }
+        }
+        for (int c = 0; c < 3; ++c) prev_beta[c] = hbeta[c];
+        est_done = false;
         cycle_start_kernel<<<1, 32, 0, st>>>(gs, beta, thr, m); note_launch();
         scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.r.ptr, beta, W.V.ptr, N); note_launch();
         int k = 0;
@@ -514,7 +531,10 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
                 const int ps = done % kPollRing;
                 if ((ce = cudaEventSynchronize(W.ev[ps])) != cudaSuccess) return ce;
                 const int *f = W.poll + 3 * ps;
-                if (!f[0] && !f[1] && !f[2]) break;
+                if (!f[0] && !f[1] && !f[2]) {
+                    est_done = true;
+                    break;
+                }
             }
         }
         backsolve_kernel<<<1, 32, 0, st>>>(gs, m); note_launch();

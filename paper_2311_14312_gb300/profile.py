@@ -65,6 +65,7 @@ def main(argv=None):
         sz = ctx.sizes()
         print(f"solve {st.ms_solve:.1f} ms (rhs {st.ms_rhs:.2f} ms) iters {list(st.iters)} "
               f"matvecs {st.n_matvec} refinement steps {st.n_refine} resid {max(st.rel_resid):.2e}")
+        print("preconditioner:", ctx.precond_info())
         print(f"tree: nodes {sz.n_nodes} segments {sz.n_segments} pieces {sz.n_pieces} cells "
               f"{sz.n_cells} leaves {sz.n_leaves} depth {sz.depth}; per matvec: near pairs "
               f"{st.p2p_pairs} M2L pairs {st.m2l_pairs}")
@@ -91,6 +92,19 @@ def main(argv=None):
         t_f = _time(lambda: ctx.apply_operator(x, y, 1, False), 3)
         print(f"solve {st.ms_solve:.1f} ms iters {list(st.iters)} matvecs {st.n_matvec}")
         print(f"inner FP32 operator {t_in:.4f} ms; FP64 G_H {t_g:.4f} ms; FP64 F_H {t_f:.4f} ms")
+        # the preconditioned FP32 operator against FP64 G_H applied to M v
+        for name, v in (("random", x), ):
+            y1 = torch.empty_like(v)
+            w = torch.empty_like(v)
+            y2 = torch.empty_like(v)
+            ctx.apply_operator(v, y1, 0, 1)
+            ctx.apply_operator(v, w, 0, 3)
+            ctx.apply_operator(w, y2, 0, 0)
+            rel = (torch.linalg.norm(y1 - y2, dim=0) / torch.linalg.norm(y2, dim=0)).cpu().numpy()
+            print(f"G_H M (FP32 graph) vs FP64 G_H (M v) on the {name} vector: relative error per channel "
+                  f"{[f'{r:.2e}' for r in rel]}; |v| {torch.linalg.norm(v).item():.3e} |M v| "
+                  f"{torch.linalg.norm(w).item():.3e} |G_H M v| {torch.linalg.norm(y2).item():.3e} "
+                  f"finite {bool(torch.isfinite(y1).all())}")
         # accuracy of the FP32 operator (no preconditioner) against the FP64 one
         sig = torch.from_numpy(ctx.get_density()).cuda()
         for name, v in (("random", x), ("solution", sig)):
