@@ -194,6 +194,8 @@ __global__ void coarse_solve_kernel(const float *__restrict__ Ainv, int n_pad, i
     const int i = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (i >= P) return;
     const float *row = Ainv + (size_t)i * n_pad;
+    // FP64 sums: M amplifies by ~1e4-1e5, and its rounding must stay well
+    // below the FP32 operator's own error
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
     for (int j = lane; j < P; j += 32) {
         const double w = row[j];

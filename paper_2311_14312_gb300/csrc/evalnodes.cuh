@@ -364,7 +364,6 @@ __global__ void __launch_bounds__(32 * kWarps) near_apply_kernel(NodeArgs<T> a, 
                                                                   const T *__restrict__ dens,
                                                                   const long long *__restrict__ far_off = nullptr,
                                                                   const typename passes::V2<T>::type *__restrict__ far = nullptr) {
-    __shared__ T sd[3][kStageN];
     const int4 it = a.items[blockIdx.x];
     const int leaf = it.x, t0 = it.y, nt = it.z, nU = it.w;
     const long long base = off[blockIdx.x];
@@ -382,30 +381,27 @@ __global__ void __launch_bounds__(32 * kWarps) near_apply_kernel(NodeArgs<T> a, 
         row[j] = coef + base + (long long)(ok ? tl : 0) * nU;
         acc[j][0] = acc[j][1] = acc[j][2] = T(0);
     }
-    int pl0 = 0;
-    for (int e = a.u_ptr[leaf]; e < a.u_ptr[leaf + 1]; ++e) {
-        const int src = a.u_idx[e];
-        const int p0 = a.pstart[src], pn = a.pcount[src];
-        for (int b = 0; b < pn; b += kStageN) {
-            const int cnt = min(kStageN, pn - b);
-            __syncthreads();
-            for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
-                const int seg = a.pseg[p0 + b + s];
-                for (int c = 0; c < 3; ++c) sd[c][s] = dens[3 * (size_t)seg + c];
+    // lanes walk the list-1 pieces in list order (each lane keeps its own
+    // cursor into the sources); no block-wide staging or barriers
+    if (warp < nt) {
+        const int e1 = a.u_ptr[leaf + 1];
+        int e = a.u_ptr[leaf], ebeg = 0, eend = e < e1 ? a.pcount[a.u_idx[e]] : 0;
+        for (int pl = lane; pl < nU; pl += 32) {
+            while (pl >= eend) {
+                ebeg = eend;
+                ++e;
+                eend += a.pcount[a.u_idx[e]];
             }
-            __syncthreads();
-            for (int s = lane; s < cnt; s += 32) {
-                const T d0 = sd[0][s], d1 = sd[1][s], d2 = sd[2][s];
+            const int seg = a.pseg[a.pstart[a.u_idx[e]] + (pl - ebeg)];
+            const T d0 = dens[3 * (size_t)seg], d1 = dens[3 * (size_t)seg + 1], d2 = dens[3 * (size_t)seg + 2];
 #pragma unroll
-                for (int j = 0; j < kPer; ++j) {
-                    if (warp + kWarps * j >= nt) break;
-                    const T cfv = row[j][pl0 + s];
-                    acc[j][0] += cfv * d0;
-                    acc[j][1] += cfv * d1;
-                    acc[j][2] += cfv * d2;
-                }
+            for (int j = 0; j < kPer; ++j) {
+                if (warp + kWarps * j >= nt) break;
+                const T cfv = row[j][pl];
+                acc[j][0] += cfv * d0;
+                acc[j][1] += cfv * d1;
+                acc[j][2] += cfv * d2;
             }
-            pl0 += cnt;
         }
     }
     if (far)

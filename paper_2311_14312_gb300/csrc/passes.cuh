@@ -153,6 +153,9 @@ __global__ void __launch_bounds__(kChunk) p2m_kernel(TreeView<T> t, PS ps, const
     int *sg = reinterpret_cast<int *>(wr + kChunk);         // [kChunk]
     const int cell = leaves[blockIdx.x];
     const int tid = threadIdx.x;
+    // phase 2: thread tid sums coefficient k = tid % P1 over the pieces
+    // j = grp, grp + ngrp, ... of each chunk (grp = tid / P1)
+    const int ngrp = kChunk / P1, grp = tid / P1, k = tid - grp * P1;
     const T iw = t.iw[cell];
     C acc[3];
     for (int c = 0; c < 3; ++c) acc[c] = mk<T>(0, 0);
@@ -175,16 +178,15 @@ __global__ void __launch_bounds__(kChunk) p2m_kernel(TreeView<T> t, PS ps, const
             row[0] = mk<T>(0, 0);              // S_{-1}
             C s = mk<T>(1, 0), ap = mk<T>(1, 0);
             row[1] = s;                         // S_0
-            for (int k = 1; k < P1; ++k) {
+            for (int q = 1; q < P1; ++q) {
                 ap = cmul(ap, a);
                 s = cadd(cmul(b, s), ap);
-                row[k + 1] = s;
+                row[q + 1] = s;
             }
         }
         __syncthreads();
-        if (tid < P1) {
-            const int k = tid;
-            for (int j = 0; j < cnt; ++j) {
+        if (grp < ngrp) {
+            for (int j = grp; j < cnt; j += ngrp) {
                 const size_t ri = (size_t)(p0 + base + j) * P1 + k;
                 C cg, cf;
                 if (rows_g) {
@@ -212,8 +214,17 @@ __global__ void __launch_bounds__(kChunk) p2m_kernel(TreeView<T> t, PS ps, const
         }
     }
     if (out_g) return;
+    // the groups' partial sums, added in group order
+    __syncthreads();
+    if (grp < ngrp)
+        for (int c = 0; c < 3; ++c) S[(grp * 3 + c) * P1 + k] = acc[c];
+    __syncthreads();
     if (tid < P1)
-        for (int c = 0; c < 3; ++c) M[((size_t)cell * 3 + c) * P1 + tid] = acc[c];
+        for (int c = 0; c < 3; ++c) {
+            C a = S[c * P1 + tid];
+            for (int q = 1; q < ngrp; ++q) a = cadd(a, S[(q * 3 + c) * P1 + tid]);
+            M[((size_t)cell * 3 + c) * P1 + tid] = a;
+        }
 }
 
 // ---------------------------------------------------------------- M2M --
@@ -254,7 +265,7 @@ __global__ void __launch_bounds__(32 * kLevelWarps) m2m_kernel(const int *__rest
 // up to kMultiLeaves (ancestor, leaf) pairs, lane k holds coefficient k; a
 // chunk writes the ancestor's expansion when it is the cell's only chunk,
 // else a partial sum that m2m_reduce_kernel adds up in chunk order.
-constexpr int kMultiLeaves = 16;
+constexpr int kMultiLeaves = 8;
 constexpr int kMultiWarps = 4;
 
 template <typename T>
@@ -533,6 +544,72 @@ __device__ __forceinline__ float4 ff_rot(float4 v, int n) {
 }
 __device__ __forceinline__ float4 ff_conj(float4 v) { return make_float4(v.x, -v.y, v.z, -v.w); }
 
+// Per-level M2M (Eq. 71) and L2L (Eq. 73) of the FP64 passes in float-float
+// (the tables of m2m_kernel / l2l_kernel stored as float-float): one warp per
+// cell, lane k holds coefficient k; the FP64 inputs (children's moments, the
+// parent's local expansion) are converted once per cell into shared memory,
+// so the inner loops run on the FP32 pipes only.
+static __global__ void __launch_bounds__(128) m2m_ff_kernel(const int *__restrict__ child0,
+                                                            const int *__restrict__ cells, int n, int P1,
+                                                            const float4 *__restrict__ tab,
+                                                            double2 *__restrict__ M) {
+    __shared__ float4 sm[4][4 * 3 * 32];
+    const int w = threadIdx.x >> 5, k = threadIdx.x & 31;
+    const int idx = blockIdx.x * 4 + w;
+    if (idx >= n) return;
+    const int cell = cells[idx];
+    const int ch0 = child0[cell];
+    const int nM = 3 * P1;
+    const double2 *src = M + (size_t)ch0 * nM;          // the 4 children are contiguous
+    for (int i = k; i < 4 * nM; i += 32) sm[w][i] = ff_from(src[i]);
+    __syncwarp();
+    if (k >= P1) return;
+    float4 acc[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+                     make_float4(0.f, 0.f, 0.f, 0.f)};
+    for (int q = 0; q < 4; ++q) {
+        const float4 *Tq = tab + ((size_t)q * P1 + k) * P1;
+        const float4 *mq = sm[w] + q * nM;
+        for (int j = 0; j <= k; ++j) {
+            const float4 tq = Tq[j];
+            for (int c = 0; c < 3; ++c) ff_cfma(acc[c], tq, mq[c * P1 + j]);
+        }
+    }
+    for (int c = 0; c < 3; ++c)
+        M[((size_t)cell * 3 + c) * P1 + k] =
+            make_double2((double)acc[c].x + (double)acc[c].z, (double)acc[c].y + (double)acc[c].w);
+}
+
+static __global__ void __launch_bounds__(128) l2l_ff_kernel(TreeView<double> t, const int *__restrict__ cells, int n,
+                                                            int level, int P1, const float4 *__restrict__ tab,
+                                                            const double2 *__restrict__ Lm2l,
+                                                            double2 *__restrict__ L) {
+    __shared__ float4 sp[4][3 * 32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int idx = blockIdx.x * 4 + w;
+    if (idx >= n) return;
+    const int cell = cells[idx];
+    const int nM = 3 * P1;
+    const bool up = level >= 3;
+    if (up) {
+        const double2 *src = L + (size_t)t.parent[cell] * nM;
+        for (int i = l; i < nM; i += 32) sp[w][i] = ff_from(src[i]);
+    }
+    __syncwarp();
+    if (l >= P1) return;
+    float4 acc[3];
+    for (int c = 0; c < 3; ++c) acc[c] = ff_from(Lm2l[((size_t)cell * 3 + c) * P1 + l]);
+    if (up) {
+        const float4 *Tq = tab + ((size_t)t.quad[cell] * P1 + l) * P1;
+        for (int k = l; k < P1; ++k) {
+            const float4 tq = Tq[k];
+            for (int c = 0; c < 3; ++c) ff_cfma(acc[c], tq, sp[w][c * P1 + k]);
+        }
+    }
+    for (int c = 0; c < 3; ++c)
+        L[((size_t)cell * 3 + c) * P1 + l] =
+            make_double2((double)acc[c].x + (double)acc[c].z, (double)acc[c].y + (double)acc[c].w);
+}
+
 constexpr int kM2LffWarps = 8;
 
 inline size_t m2l_ff_smem(int P1) {
@@ -640,6 +717,8 @@ __global__ void __launch_bounds__(kChunk) p2l_kernel(TreeView<T> t, PS ps, const
     int *sg = reinterpret_cast<int *>(F + kChunk * P1);
     const int cell = cells[blockIdx.x];
     const int tid = threadIdx.x;
+    const int ngrp = kChunk / P1, grp = tid / P1, l = tid - grp * P1;   // as in p2m_kernel
+    const bool want_f = use_m || out_g;
     const T iw = t.iw[cell], w = 1 / iw, logw = t.logw[cell];
     C acc[3];
     for (int c = 0; c < 3; ++c) acc[c] = mk<T>(0, 0);
@@ -671,7 +750,7 @@ __global__ void __launch_bounds__(kChunk) p2l_kernel(TreeView<T> t, PS ps, const
                     C wb = cmul(mk<T>(wv.x, -wv.y), mk<T>(b.x * w, b.y * w));
                     C t2 = cmul(wb, lba);
                     g[0] = mk<T>(om * (len * (1 - la.x) - t2.x), om * (-len * la.y - t2.y));
-                    f[0] = mk<T>(-om * lba.y, om * lba.x);
+                    if (want_f) f[0] = mk<T>(-om * lba.y, om * lba.x);
                 }
                 if (P1 > 1) {
                     C t2 = cmul(mk<T>(wv.x, -wv.y), lba);
@@ -683,27 +762,27 @@ __global__ void __launch_bounds__(kChunk) p2l_kernel(TreeView<T> t, PS ps, const
                 C gb = cscl(ab, om * len);                  // G factor, times T_{l-2} / (l (l-1))
                 // T_m = sum_j al^j be^(m-j): T_0 = 1, T_m = al T_{m-1} + be^m
                 C Tm = mk<T>(1, 0), bp = mk<T>(1, 0);       // T_0
-                if (P1 > 1) f[1] = fb;                       // l = 1: T_0 / 1
-                for (int l = 2; l < P1; ++l) {
-                    // here Tm = T_{l-2}
-                    g[l] = cscl(cmul(gb, Tm), T(1) / (T(l) * (l - 1)));
+                if (P1 > 1 && want_f) f[1] = fb;             // l = 1: T_0 / 1
+                for (int q = 2; q < P1; ++q) {
+                    // here Tm = T_{q-2}
+                    g[q] = cscl(cmul(gb, Tm), T(1) / (T(q) * (q - 1)));
                     bp = cmul(bp, be);
-                    Tm = cadd(cmul(al, Tm), bp);             // T_{l-1}
-                    f[l] = cscl(cmul(fb, Tm), T(1) / T(l));
+                    Tm = cadd(cmul(al, Tm), bp);             // T_{q-1}
+                    if (want_f) f[q] = cscl(cmul(fb, Tm), T(1) / T(q));
                 }
                 sg[tid] = t.pseg[i];
             }
             __syncthreads();
-            if (tid < P1) {
-                for (int j = 0; j < cnt; ++j) {
-                    const size_t ri = (size_t)(r0 + rr + j) * P1 + tid;
+            if (grp < ngrp) {
+                for (int j = grp; j < cnt; j += ngrp) {
+                    const size_t ri = (size_t)(r0 + rr + j) * P1 + l;
                     C cg, cf;
                     if (rows_g) {
                         cg = rows_g[ri];
                         cf = rows_f ? rows_f[ri] : mk<T>(0, 0);
                     } else {
-                        cg = G[j * P1 + tid];
-                        cf = F[j * P1 + tid];
+                        cg = G[j * P1 + l];
+                        cf = use_m || out_g ? F[j * P1 + l] : mk<T>(0, 0);
                     }
                     if (out_g) {
                         out_g[ri] = cg;
@@ -722,11 +801,19 @@ __global__ void __launch_bounds__(kChunk) p2l_kernel(TreeView<T> t, PS ps, const
             rr += cnt;
         }
     }
-    if (tid < P1 && !out_g)
+    if (out_g) return;
+    // the groups' partial sums, added in group order
+    __syncthreads();
+    if (grp < ngrp)
+        for (int c = 0; c < 3; ++c) G[(grp * 3 + c) * P1 + l] = acc[c];
+    __syncthreads();
+    if (tid < P1)
         for (int c = 0; c < 3; ++c) {
+            C a = G[c * P1 + tid];
+            for (int q = 1; q < ngrp; ++q) a = cadd(a, G[(q * 3 + c) * P1 + tid]);
             C *o = Lout + ((size_t)cell * 3 + c) * P1 + tid;
-            o->x += acc[c].x;
-            o->y += acc[c].y;
+            o->x += a.x;
+            o->y += a.y;
         }
 }
 
