@@ -177,32 +177,47 @@ __global__ void gj_col_kernel(float *__restrict__ A, int n, int k) {
 }
 
 // ------------------------------------------------------------------ apply --
-// s[j][c] = sum over panel j's nodes of v
-__global__ void restrict_kernel(const double *__restrict__ v, int P, int g, double *__restrict__ s) {
+// s[j][c] = sum over panel j's nodes of v, as a float-float pair (hi, lo)
+__global__ void restrict_kernel(const double *__restrict__ v, int P, int g, float2 *__restrict__ s) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * P) return;
     const int j = t / 3, c = t % 3;
     double a = 0.0;
     for (int m = 0; m < g; ++m) a += v[3 * ((size_t)j * g + m) + c];
-    s[t] = a;
+    const float hi = (float)a;
+    s[t] = make_float2(hi, (float)(a - (double)hi));
+}
+
+// acc (hi, lo) += w * (x.hi + x.lo): the product's leading part split exactly
+// (FMA TwoProduct), summed by TwoSum; the small terms go to lo (the
+// compensated dot product of Ogita, Rump and Oishi)
+__device__ __forceinline__ void dot2_step(float &hi, float &lo, float w, float2 x) {
+    const float p = __fmul_rn(w, x.x);
+    const float pe = fmaf(w, x.x, -p);
+    const float sum = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(sum, hi);
+    const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(p, bb));
+    hi = sum;
+    lo += se + pe + w * x.y;
 }
 
 // y = Ac^-1 s (one warp per row, fixed-order reduction); ly[j] = l_j y_j (FP32)
 __global__ void coarse_solve_kernel(const float *__restrict__ Ainv, int n_pad, int P,
-                                    const double *__restrict__ s, const float *__restrict__ plen32,
+                                    const float2 *__restrict__ s, const float *__restrict__ plen32,
                                     double *__restrict__ y, float *__restrict__ ly) {
     const int i = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (i >= P) return;
     const float *row = Ainv + (size_t)i * n_pad;
-    // FP64 sums: M amplifies by ~1e4-1e5, and its rounding must stay well
-    // below the FP32 operator's own error
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    // compensated (float-float) sums: M amplifies by ~1e4-1e5, and its
+    // rounding must stay well below the FP32 operator's own error
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
     for (int j = lane; j < P; j += 32) {
-        const double w = row[j];
-        a0 += w * s[3 * j];
-        a1 += w * s[3 * j + 1];
-        a2 += w * s[3 * j + 2];
+        const float w = row[j];
+        dot2_step(h0, l0, w, s[3 * j]);
+        dot2_step(h1, l1, w, s[3 * j + 1]);
+        dot2_step(h2, l2, w, s[3 * j + 2]);
     }
+    double a0 = (double)h0 + (double)l0, a1 = (double)h1 + (double)l1, a2 = (double)h2 + (double)l2;
     for (int off = 16; off > 0; off >>= 1) {
         a0 += __shfl_xor_sync(0xffffffffu, a0, off);
         a1 += __shfl_xor_sync(0xffffffffu, a1, off);

@@ -173,8 +173,9 @@ private:
     int P_ = 0, g_ = 0, n_pad_ = 0, n_pairs_ = 0;
     double check_ = -1.0;
     DevBuf<float2> c32_, q32_;
-    DevBuf<double> plen_, corr_, s_, y_, r_;
+    DevBuf<double> plen_, corr_, y_, r_;
     DevBuf<float> plen32_, ly_, Ainv_, part_;
+    DevBuf<float2> s_;
     DevBuf<int> nptr_;
     DevBuf<int2> pairs_;
 };

@@ -332,13 +332,12 @@ cudaError_t Fmm::Impl::passes(const double *sb, const double *mb, int use_s, int
             rows_ready ? p2m_g64.ptr : nullptr, rows_ready && use_m ? p2m_f64.ptr : nullptr);
         note_launch();
     }
-    // per level: in FP64 the chain through the parents does less arithmetic
-    // than translating every leaf to every ancestor
+    // per level, in float-float: the chain through the parents does less
+    // arithmetic than translating every leaf to every ancestor
     for (int l = tree.depth - 1; l >= 2; --l) {
         const int lo = m2m_ptr[l], n = m2m_ptr[l + 1] - lo;
         if (n <= 0) continue;
-        passes::m2m_kernel<double><<<(n + passes::kLevelWarps - 1) / passes::kLevelWarps, 32 * passes::kLevelWarps, 0, st>>>(
-            child0.ptr, m2m_cells.ptr + lo, n, P1, m2m.ptr, M.ptr);
+        passes::m2m_ff_kernel<<<(n + 3) / 4, 128, 0, st>>>(child0.ptr, m2m_cells.ptr + lo, n, P1, m2mff.ptr, M.ptr);
         note_launch();
     }
     if (sc.n_m2l > 0) {
@@ -356,8 +355,7 @@ cudaError_t Fmm::Impl::passes(const double *sb, const double *mb, int use_s, int
     for (int l = 2; l <= tree.depth; ++l) {   // per level: FP64 work per cell once
         const int lo = sc.l2l_ptr[l], n = sc.l2l_ptr[l + 1] - lo;
         if (n <= 0) continue;
-        passes::l2l_kernel<double><<<(n + passes::kLevelWarps - 1) / passes::kLevelWarps, 32 * passes::kLevelWarps, 0, st>>>(
-            tv, sc.l2l.ptr + lo, n, l, P1, l2l.ptr, Lm2l.ptr, L.ptr);
+        passes::l2l_ff_kernel<<<(n + 3) / 4, 128, 0, st>>>(tv, sc.l2l.ptr + lo, n, l, P1, l2lff.ptr, Lm2l.ptr, L.ptr);
         note_launch();
     }
     return cudaGetLastError();
@@ -868,6 +866,20 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     UP(I.plen64, plen64);
     UP(I.v_code, vcode);
     UP(I.m2m_cells, m2m_cells);
+    {   // list-1 pieces of every leaf, flattened in list order
+        std::vector<int> ufp(nC + 1, 0), ufi;
+        for (int c = 0; c < nC; ++c) {
+            ufp[c] = int(ufi.size());
+            if (!T.is_leaf(c)) continue;
+            for (int e = T.u_ptr[c]; e < T.u_ptr[c + 1]; ++e) {
+                const int src = T.u_idx[e];
+                for (int q = 0; q < T.piece_count[src]; ++q) ufi.push_back(T.piece_start[src] + q);
+            }
+        }
+        ufp[nC] = int(ufi.size());
+        UP(I.uf_ptr, ufp);
+        UP(I.uf_idx, ufi);
+    }
     UP(I.mchunks, mchunks);
     UP(I.mred, mred);
     UP(I.pair_leaf, pair_leaf);
@@ -891,6 +903,8 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         (e = I.L.alloc((size_t)nC * 3 * I.P1)) != cudaSuccess ||
         (e = upload_cd(I.base64, base, st)) != cudaSuccess ||
         (e = upload(I.baseff, to_ff(base), st)) != cudaSuccess ||
+        (e = upload(I.m2mff, to_ff(m2m), st)) != cudaSuccess ||
+        (e = upload(I.l2lff, to_ff(l2l), st)) != cudaSuccess ||
         (e = upload(I.m2m32i, to_f2(m2mi), st)) != cudaSuccess ||
         (e = upload(I.l2l32i, to_f2(l2li), st)) != cudaSuccess ||
         (e = upload(I.base32i, to_f2(basei), st)) != cudaSuccess ||

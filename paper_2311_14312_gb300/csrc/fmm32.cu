@@ -129,7 +129,7 @@ __global__ void heavy_kernel(const double *__restrict__ sb, const double *__rest
 
 // -------------------------------------------------------------- eval --
 constexpr int kEvThreads = 256;
-constexpr int kStage = 128;
+constexpr int kStage = 256;
 
 struct EvalArgs32 {
     DevTree32 t;
@@ -291,15 +291,15 @@ __global__ void __launch_bounds__(kEvThreads, 2) eval32_kernel(EvalArgs32 a) {
         u1 = e1 * kInv2PiF;
         u2 = e2 * kInv2PiF;
     }
-    // P2P over list 1 (App. D)
-    for (int e = t.u_ptr[leaf]; e < t.u_ptr[leaf + 1]; ++e) {
-        const int src = t.u_idx[e];
-        const int p0 = t.pstart[src], pn = t.pcount[src];
-        for (int base = 0; base < pn; base += kStage) {
-            int cnt = min(kStage, pn - base);
+    // P2P over list 1 (App. D): the leaf's list-1 pieces, flattened in list
+    // order, staged kStage at a time
+    const int f_end = t.uf_ptr[leaf + 1];
+    for (int f0 = t.uf_ptr[leaf]; f0 < f_end; f0 += kStage) {
+        {
+            int cnt = min(kStage, f_end - f0);
             __syncthreads();
             for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
-                int i = p0 + base + s;
+                int i = t.uf_idx[f0 + s];
                 const double *P = a.t64.pc + 4 * (size_t)i;
                 split2(P[0] - cxB, sx1h[s], sx1l[s]);
                 split2(P[1] - cyB, sy1h[s], sy1l[s]);
@@ -461,6 +461,8 @@ DevTree32 Fmm::Impl::dt32() const {
     t.u_off = uoff32.ptr;
     t.w_off = woff32.ptr;
     t.x_off = xoff32.ptr;
+    t.uf_ptr = uf_ptr.ptr;
+    t.uf_idx = uf_idx.ptr;
     return t;
 }
 

@@ -42,6 +42,7 @@ struct DevTree32 {
     const float2 *u_off;    // per list-1 entry: centre(source) - centre(target)
     const float2 *w_off;    // per list-3 entry
     const float2 *x_off;    // per list-4 entry
+    const int *uf_ptr, *uf_idx;   // list-1 pieces of each leaf, flattened (list order)
 };
 
 // A unit of evaluation work inside one leaf: a pixel rectangle (r0, c0,
@@ -128,6 +129,7 @@ struct Fmm::Impl {
     // pass schedules and tables of the templated passes
     Schedule sched_all, sched_nodes;
     DevBuf<int> m2m_cells, v_code;
+    DevBuf<int> uf_ptr, uf_idx;       // list-1 pieces per leaf, flattened
     std::vector<int> m2m_ptr;         // [depth + 2]: inner cells with pieces, by level
     // one-launch upward pass of the FP32 operator: chunks (ancestor, first
     // pair, pairs, slot), reductions (cell, first slot, slots), leaves of the
@@ -140,6 +142,7 @@ struct Fmm::Impl {
     DevBuf<int> level_d;              // cell levels (downward walk)
     DevBuf<double2> base64, Lm2l;
     DevBuf<float4> baseff;            // base M2L tables in float-float
+    DevBuf<float4> m2mff, l2lff;      // M2M / L2L tables in float-float
     DevBuf<float2> base32, Lm2l32;
     // the FP32 operator inside GMRES runs at a lower order p_inner (its
     // accuracy only has to beat the inner tolerance; the FP64 residual at
