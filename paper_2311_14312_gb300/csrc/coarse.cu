@@ -201,21 +201,23 @@ __device__ __forceinline__ void dot2_step(float &hi, float &lo, float w, float2 
     lo += se + pe + w * x.y;
 }
 
-// y = Ac^-1 s (one warp per row, fixed-order reduction); ly[j] = l_j y_j (FP32)
-__global__ void coarse_solve_kernel(const float *__restrict__ Ainv, int n_pad, int P,
-                                    const float2 *__restrict__ s, const float *__restrict__ plen32,
-                                    double *__restrict__ y, float *__restrict__ ly) {
-    const int i = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (i >= P) return;
+// y = Ac^-1 s (fixed-order reduction); ly[j] = l_j y_j (FP32)
+__global__ void __launch_bounds__(128) coarse_solve_kernel(const float *__restrict__ Ainv, int n_pad, int P,
+                                                           const float2 *__restrict__ s,
+                                                           const float *__restrict__ plen32,
+                                                           double *__restrict__ y, float *__restrict__ ly) {
+    // one block of 128 threads per row; compensated (float-float) sums: M
+    // amplifies by ~1e4-1e5, and its rounding must stay well below the FP32
+    // operator's own error
+    __shared__ double red[4][3];
+    const int i = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
     const float *row = Ainv + (size_t)i * n_pad;
-    // compensated (float-float) sums: M amplifies by ~1e4-1e5, and its
-    // rounding must stay well below the FP32 operator's own error
     float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
-    for (int j = lane; j < P; j += 32) {
-        const float w = row[j];
-        dot2_step(h0, l0, w, s[3 * j]);
-        dot2_step(h1, l1, w, s[3 * j + 1]);
-        dot2_step(h2, l2, w, s[3 * j + 2]);
+    for (int j = t; j < P; j += 128) {
+        const float wj = row[j];
+        dot2_step(h0, l0, wj, s[3 * j]);
+        dot2_step(h1, l1, wj, s[3 * j + 1]);
+        dot2_step(h2, l2, wj, s[3 * j + 2]);
     }
     double a0 = (double)h0 + (double)l0, a1 = (double)h1 + (double)l1, a2 = (double)h2 + (double)l2;
     for (int off = 16; off > 0; off >>= 1) {
@@ -224,13 +226,15 @@ __global__ void coarse_solve_kernel(const float *__restrict__ Ainv, int n_pad, i
         a2 += __shfl_xor_sync(0xffffffffu, a2, off);
     }
     if (lane == 0) {
-        y[3 * i] = a0;
-        y[3 * i + 1] = a1;
-        y[3 * i + 2] = a2;
-        const float l = plen32[i];
-        ly[3 * i] = l * (float)a0;
-        ly[3 * i + 1] = l * (float)a1;
-        ly[3 * i + 2] = l * (float)a2;
+        red[w][0] = a0;
+        red[w][1] = a1;
+        red[w][2] = a2;
+    }
+    __syncthreads();
+    if (t < 3) {
+        const double v = red[0][t] + red[1][t] + red[2][t] + red[3][t];
+        y[3 * i + t] = v;
+        ly[3 * i + t] = plen32[i] * (float)v;
     }
 }
 
@@ -431,7 +435,7 @@ cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st
 cudaError_t TwoLevel::apply(const double *inv, const double *v, double *w, cudaStream_t st) {
     const int P = P_, g = g_, N = P * g;
     restrict_kernel<<<(3 * P + 255) / 256, 256, 0, st>>>(v, P, g, s_.ptr);
-    coarse_solve_kernel<<<(P + 3) / 4, 128, 0, st>>>(Ainv_.ptr, n_pad_, P, s_.ptr, plen32_.ptr, y_.ptr, ly_.ptr);
+    coarse_solve_kernel<<<P, 128, 0, st>>>(Ainv_.ptr, n_pad_, P, s_.ptr, plen32_.ptr, y_.ptr, ly_.ptr);
     monopole_kernel<<<dim3((N + 127) / 128, kSplit), 128, 0, st>>>(q32_.ptr, c32_.ptr, ly_.ptr, P, N, part_.ptr);
     residual_kernel<<<(N + 255) / 256, 256, 0, st>>>(part_.ptr, g, nptr_.ptr, pairs_.ptr, corr_.ptr, y_.ptr, v, N,
                                                     r_.ptr);

@@ -30,6 +30,7 @@ template <typename T> struct NodeArgs {
     const int4 *items;             // (leaf, first target, count, list-1 pieces)
     const double *q64;             // [n][2] sorted targets
     const int *own1, *own2, *perm; // own segments (may be null), output order
+    const int *uf_ptr, *uf_seg;    // segments of each leaf's list-1 pieces, flattened
     int P1;
     const typename passes::V2<T>::type *M, *L;
     const T *sb, *mb;
@@ -381,18 +382,12 @@ __global__ void __launch_bounds__(32 * kWarps) near_apply_kernel(NodeArgs<T> a, 
         row[j] = coef + base + (long long)(ok ? tl : 0) * nU;
         acc[j][0] = acc[j][1] = acc[j][2] = T(0);
     }
-    // lanes walk the list-1 pieces in list order (each lane keeps its own
-    // cursor into the sources); no block-wide staging or barriers
+    // lanes walk the leaf's list-1 pieces in list order (their segments,
+    // flattened per leaf); no block-wide staging or barriers
     if (warp < nt) {
-        const int e1 = a.u_ptr[leaf + 1];
-        int e = a.u_ptr[leaf], ebeg = 0, eend = e < e1 ? a.pcount[a.u_idx[e]] : 0;
+        const int *segs = a.uf_seg + a.uf_ptr[leaf];
         for (int pl = lane; pl < nU; pl += 32) {
-            while (pl >= eend) {
-                ebeg = eend;
-                ++e;
-                eend += a.pcount[a.u_idx[e]];
-            }
-            const int seg = a.pseg[a.pstart[a.u_idx[e]] + (pl - ebeg)];
+            const int seg = segs[pl];
             const T d0 = dens[3 * (size_t)seg], d1 = dens[3 * (size_t)seg + 1], d2 = dens[3 * (size_t)seg + 2];
 #pragma unroll
             for (int j = 0; j < kPer; ++j) {

@@ -391,6 +391,8 @@ evalnodes::NodeArgs<double> Fmm::Impl::node_args64(const int4 *items, const doub
     a.use_s = use_s;
     a.use_m = use_m;
     a.out = out;
+    a.uf_ptr = uf_ptr.ptr;
+    a.uf_seg = uf_seg.ptr;
     return a;
 }
 
@@ -867,18 +869,22 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     UP(I.v_code, vcode);
     UP(I.m2m_cells, m2m_cells);
     {   // list-1 pieces of every leaf, flattened in list order
-        std::vector<int> ufp(nC + 1, 0), ufi;
+        std::vector<int> ufp(nC + 1, 0), ufi, ufs;
         for (int c = 0; c < nC; ++c) {
             ufp[c] = int(ufi.size());
             if (!T.is_leaf(c)) continue;
             for (int e = T.u_ptr[c]; e < T.u_ptr[c + 1]; ++e) {
                 const int src = T.u_idx[e];
-                for (int q = 0; q < T.piece_count[src]; ++q) ufi.push_back(T.piece_start[src] + q);
+                for (int q = 0; q < T.piece_count[src]; ++q) {
+                    ufi.push_back(T.piece_start[src] + q);
+                    ufs.push_back(T.pc_seg[T.piece_start[src] + q]);
+                }
             }
         }
         ufp[nC] = int(ufi.size());
         UP(I.uf_ptr, ufp);
         UP(I.uf_idx, ufi);
+        UP(I.uf_seg, ufs);
     }
     UP(I.mchunks, mchunks);
     UP(I.mred, mred);

@@ -696,6 +696,8 @@ cudaError_t Fmm::Impl::apply_nodes32(const double *x, double *y, bool single, cu
     a.P1 = P1i;
     a.M = M32i.ptr;
     a.L = L32i.ptr;
+    a.uf_ptr = uf_ptr.ptr;
+    a.uf_seg = uf_seg.ptr;
     if (near_ready && single)
         evalnodes::near_apply_kernel<float><<<n_nt_items4, 32 * evalnodes::kWarps, 0, st>>>(
             a, near_off.ptr, near_g32.ptr, sbar32.ptr, far_ready ? far_off.ptr : nullptr,

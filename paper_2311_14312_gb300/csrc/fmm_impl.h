@@ -129,7 +129,7 @@ struct Fmm::Impl {
     // pass schedules and tables of the templated passes
     Schedule sched_all, sched_nodes;
     DevBuf<int> m2m_cells, v_code;
-    DevBuf<int> uf_ptr, uf_idx;       // list-1 pieces per leaf, flattened
+    DevBuf<int> uf_ptr, uf_idx, uf_seg;   // list-1 pieces per leaf, flattened, and their segments
     std::vector<int> m2m_ptr;         // [depth + 2]: inner cells with pieces, by level
     // one-launch upward pass of the FP32 operator: chunks (ancestor, first
     // pair, pairs, slot), reductions (cell, first slot, slots), leaves of the

@@ -112,6 +112,50 @@ __global__ void orth_update_kernel(const double *__restrict__ V, size_t vstride,
     w[t] = a;
 }
 
+// The same update for the last Gram-Schmidt pass, with the squares of the
+// result summed per block and channel (blocks of kOrthThreads = 3 x 64
+// elements, so an element's channel is its index mod 3): npart[block][c].
+constexpr int kOrthThreads = 192;
+__global__ void __launch_bounds__(kOrthThreads) orth_update_norm_kernel(const double *__restrict__ V, size_t vstride,
+                                                                         const double *__restrict__ h, int nj,
+                                                                         double *__restrict__ w, int N,
+                                                                         double *__restrict__ npart) {
+    __shared__ double sq[kOrthThreads];
+    const int t = blockIdx.x * kOrthThreads + threadIdx.x;
+    double a = 0.0;
+    if (t < 3 * N) {
+        const int c = t % 3;
+        a = w[t];
+        int j = 0;
+        for (; j + 4 <= nj; j += 4) {
+            const double v0 = V[(size_t)j * vstride + t], v1 = V[(size_t)(j + 1) * vstride + t];
+            const double v2 = V[(size_t)(j + 2) * vstride + t], v3 = V[(size_t)(j + 3) * vstride + t];
+            a -= h[3 * j + c] * v0;
+            a -= h[3 * (j + 1) + c] * v1;
+            a -= h[3 * (j + 2) + c] * v2;
+            a -= h[3 * (j + 3) + c] * v3;
+        }
+        for (; j < nj; ++j) a -= h[3 * j + c] * V[(size_t)j * vstride + t];
+        w[t] = a;
+    }
+    sq[threadIdx.x] = a * a;
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int u = threadIdx.x; u < kOrthThreads; u += 3) s += sq[u];
+        npart[3 * blockIdx.x + threadIdx.x] = s;
+    }
+}
+
+// nrm[c] = sqrt(sum over the blocks of npart[block][c])
+__global__ void npart_finalize_kernel(const double *__restrict__ npart, int nb, double *__restrict__ nrm) {
+    int c = threadIdx.x;
+    if (c >= 3) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += npart[3 * b + c];
+    nrm[c] = sqrt(fmax(s, 0.0));
+}
+
 // out[i][c] = in[i][c] * (nrm[c] > 0 ? 1 / nrm[c] : 0)
 __global__ void scale_kernel(const double *__restrict__ in, const double *__restrict__ nrm,
                              double *__restrict__ out, int N) {
@@ -265,7 +309,7 @@ __global__ void solution_update_kernel(GivensState g, const double *__restrict__
 
 struct GmresWork {
     int N = 0, m = 0, nchunk = 0;
-    DevBuf<double> V, w, r, Ax, partial, hcol, hpass, hnext, small;
+    DevBuf<double> V, w, r, Ax, partial, hcol, hpass, hnext, small, npart;
     DevBuf<double> R, cs, sn, e, y;
     DevBuf<int> flags;
     double *host = nullptr;   // pinned: resid[3], active-as-double[3], norms[3]
@@ -291,6 +335,7 @@ struct GmresWork {
         DC_TRY(r.alloc((size_t)N * 3));
         DC_TRY(Ax.alloc((size_t)N * 3));
         DC_TRY(partial.alloc((size_t)(m + 1) * nchunk * 3));
+        DC_TRY(npart.alloc((size_t)3 * ((3 * (size_t)N + kOrthThreads - 1) / kOrthThreads)));
         DC_TRY(hcol.alloc((size_t)(m + 1) * 3));
         DC_TRY(hpass.alloc((size_t)(m + 1) * 3));
         DC_TRY(hnext.alloc(3));
@@ -501,14 +546,15 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
                 int t3 = (k + 1) * 3;
                 dots_finalize2_kernel<<<(t3 + 127) / 128, 128, 0, st>>>(W.partial.ptr, W.nchunk, k + 1,
                                                                        W.hpass.ptr, W.hcol.ptr, pass == 0); note_launch();
-                orth_update_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.V.ptr, vs, W.hpass.ptr,
-                                                                          k + 1, W.w.ptr, N); note_launch();
-            }
-            {   // h_{k+1,k} = ||w|| per channel
-                dim3 grid(W.nchunk, 1);
-                dots_partial_kernel<<<grid, kDotThreads, 0, st>>>(W.w.ptr, 0, W.w.ptr, N, W.nchunk,
-                                                                  W.partial.ptr); note_launch();
-                norm_finalize_kernel<<<1, 32, 0, st>>>(W.partial.ptr, W.nchunk, W.hnext.ptr); note_launch();
+                if (pass == 0) {
+                    orth_update_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.V.ptr, vs, W.hpass.ptr,
+                                                                              k + 1, W.w.ptr, N); note_launch();
+                } else {   // and h_{k+1,k} = ||w|| per channel
+                    const int nb = (3 * N + kOrthThreads - 1) / kOrthThreads;
+                    orth_update_norm_kernel<<<nb, kOrthThreads, 0, st>>>(W.V.ptr, vs, W.hpass.ptr, k + 1,
+                                                                         W.w.ptr, N, W.npart.ptr); note_launch();
+                    npart_finalize_kernel<<<1, 32, 0, st>>>(W.npart.ptr, nb, W.hnext.ptr); note_launch();
+                }
             }
             scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.w.ptr, W.hnext.ptr,
                                                                W.V.ptr + (size_t)(k + 1) * vs, N); note_launch();

@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(32 * kM2LSlots) m2l_kernel(TreeView<T> t, cons
 // memory (double buffered, the next pair's loads in flight during the
 // current pair's products).
 constexpr int kM2LSmallP1 = 21;
-constexpr int kM2LSmallWarps = 8;
+constexpr int kM2LSmallWarps = 16;
 
 inline size_t m2l_small_smem(int P1) {
     return (56 * (size_t)P1 * P1 + kM2LSmallWarps * 2 * 64) * sizeof(float2);

@@ -13,7 +13,8 @@ the chosen FP32 form with order 24 and leaf size 64, solves it, then:
           "inner" and the FP64 single layer 4 times inside the range "fp64"
           (profilers can filter on them), the FP64 double layer 4 times,
           and prints the mean device time of each;
-  solve   prints the solve statistics and tree sizes.
+  solve   solves again inside the NVTX range "solve" and prints the solve
+          statistics, the preconditioner state and the tree sizes.
 """
 from __future__ import annotations
 
@@ -59,8 +60,10 @@ def main(argv=None):
     ap.add_argument("--leaf-size", type=int, default=64)
     a = ap.parse_args(argv)
     ctx, st = _context(a.p_inner, a.inner_tol, a.leaf_size)
-    if a.what == "solve":      # a second solve: steady state (graphs and buffers exist)
+    if a.what == "solve":      # a second solve, inside the NVTX range "solve": steady state
+        torch.cuda.nvtx.range_push("solve")
         st = ctx.solve_density()
+        torch.cuda.nvtx.range_pop()
     if a.what == "solve":
         sz = ctx.sizes()
         print(f"solve {st.ms_solve:.1f} ms (rhs {st.ms_rhs:.2f} ms) iters {list(st.iters)} "
