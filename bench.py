@@ -126,6 +126,17 @@ def traffic_for_eval_kernel():
     return None
 
 
+def whole_job_rate(t_step_ms: float, npx: int, ws: int, device: str):
+    """(slowest rank's step time, whole-job Mpixels/s): every rank renders npx
+    pixels per step (replicas), the job's step time is the maximum over ranks."""
+    if ws > 1:
+        import torch
+        t = torch.tensor([t_step_ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_step_ms = float(t.item())
+    return t_step_ms, ws * npx / (t_step_ms * 1e-3) / 1e6
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -252,12 +263,7 @@ def run_ours(args):
     barrier()
     launches = P.kernel_launches() - launches0
     clk = clocks.stop()
-    t_step = statistics.mean(step_ms)
-    if ws > 1:
-        t = torch.tensor([t_step], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(t.item())
-    value = ws * npx / (t_step * 1e-3) / 1e6
+    t_step, value = whole_job_rate(statistics.mean(step_ms), npx, ws, "cuda")
 
     # ---- roofline of the dominant kernel (pixel evaluation), live events
     rs = ctx.render_viewport(vp, rgb, rgb8, stats=True)

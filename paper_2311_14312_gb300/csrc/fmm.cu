@@ -674,6 +674,7 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     // one-launch upward pass (cells with several chunks get partial slots)
     std::vector<int4> mchunks, mred;
     std::vector<int> pair_leaf;
+    std::vector<float4> pair_geo;
     int n_slots = 0;
     {
         std::vector<int> stack, lv;
@@ -692,6 +693,10 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
             }
             const int beg = int(pair_leaf.size());
             pair_leaf.insert(pair_leaf.end(), lv.begin(), lv.end());
+            const double wa = T.width(a), ax = T.cx(a), ay = T.cy(a);
+            for (int lf : lv)
+                pair_geo.push_back(make_float4((float)((T.cx(lf) - ax) / wa), (float)((T.cy(lf) - ay) / wa),
+                                               (float)(T.width(lf) / wa), 0.f));
             const int nch = (int(lv.size()) + passes::kMultiLeaves - 1) / passes::kMultiLeaves;
             if (nch == 1) {
                 mchunks.push_back(make_int4(a, beg, int(lv.size()), -1));
@@ -821,6 +826,14 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         }
         return f;
     };
+    auto lam_hilo = [](const std::vector<double> &v) {   // (hi, lo) float pairs
+        std::vector<float2> f(v.size());
+        for (size_t i = 0; i < v.size(); ++i) {
+            const float h = (float)v[i];
+            f[i] = make_float2(h, (float)(v[i] - (double)h));
+        }
+        return f;
+    };
     auto to_f2 = [](const std::vector<cd> &v) {
         std::vector<float2> f(v.size());
         for (size_t i = 0; i < v.size(); ++i) f[i] = make_float2((float)v[i].real(), (float)v[i].imag());
@@ -889,12 +902,26 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     UP(I.mchunks, mchunks);
     UP(I.mred, mred);
     UP(I.pair_leaf, pair_leaf);
+    UP(I.pair_geo, pair_geo);
     UP(I.binom32, binom32);
     if (I.fp32 && (e = I.mpart32.alloc((size_t)std::max(n_slots, 1) * 3 * I.P1i)) != cudaSuccess) {
         err = std::string("fmm allocation: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
     }
     UP(I.level_d, T.level);
+    I.walk_nmax = std::min(passes::kWalkMax, std::max(1, T.depth - 1));
+    auto make_chains = [&](const std::vector<int> &walk) {
+        std::vector<int> ch(walk.size() * (size_t)(I.walk_nmax + 1), -1);
+        for (size_t w = 0; w < walk.size(); ++w) {
+            int *row = &ch[w * (I.walk_nmax + 1)];
+            int n = 0;
+            for (int c = walk[w]; c >= 0 && T.level[c] >= 2 && n < I.walk_nmax; c = T.parent[c]) row[1 + n++] = c;
+            row[0] = n;
+        }
+        return ch;
+    };
+    UP(I.sched_all.chains, make_chains(aw));
+    UP(I.sched_nodes.chains, make_chains(nw));
     UP(I.sched_all.walk, aw);
     UP(I.sched_all.l2l, al2l);
     UP(I.sched_nodes.l2l, nl2l);
@@ -915,6 +942,7 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         (e = upload(I.l2l32i, to_f2(l2li), st)) != cudaSuccess ||
         (e = upload(I.base32i, to_f2(basei), st)) != cudaSuccess ||
         (e = upload(I.m2lfull32i, to_f2(fulli), st)) != cudaSuccess ||
+        (e = upload(I.lam_ff, lam_hilo(G.lambda), st)) != cudaSuccess ||
         (e = I.M32i.alloc((size_t)nC * 3 * I.P1i)) != cudaSuccess ||
         (e = I.L32i.alloc((size_t)nC * 3 * I.P1i)) != cudaSuccess ||
         (e = I.Lm2l32i.alloc((size_t)nC * 3 * I.P1i)) != cudaSuccess ||

@@ -60,23 +60,46 @@ __global__ void d2f_kernel(const double *__restrict__ a, const double *__restric
     }
 }
 
-__global__ void interp32_kernel(const double *__restrict__ lam, const double *__restrict__ nv,
-                                float *__restrict__ sv, int S, int s, int g) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= S) return;
-    int panel = k / s, kk = k - panel * s;
-    const double *row = lam + (size_t)kk * g;
+// sigma_bar = Lambda sigma per panel in float-float (the FP64 node values
+// converted once per panel into shared memory; Lambda stored as hi/lo
+// floats), rounded to FP32 at the end: one block per panel, one thread per
+// segment.  The node values can be large and cancelling (the coarse part of
+// the preconditioned vector), so the sums keep more than FP32 accuracy.
+__device__ __forceinline__ void dot2ff(float &hi, float &lo, float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    const float pe = fmaf(a.x, b.x, -p);
+    const float sum = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(sum, hi);
+    const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(p, bb));
+    hi = sum;
+    lo += se + pe + fmaf(a.x, b.y, a.y * b.x);
+}
+
+__global__ void interp32_kernel(const float2 *__restrict__ lam, const double *__restrict__ nv,
+                                float *__restrict__ sv, int s, int g) {
+    __shared__ float2 v[3 * kMaxG];
+    const int panel = blockIdx.x, kk = threadIdx.x;
     const double *src = nv + (size_t)panel * g * 3;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    for (int m = 0; m < g; ++m) {
-        double l = __ldg(row + m);
-        a0 += l * __ldg(src + 3 * m + 0);
-        a1 += l * __ldg(src + 3 * m + 1);
-        a2 += l * __ldg(src + 3 * m + 2);
+    for (int i = kk; i < 3 * g; i += blockDim.x) {
+        const double x = src[i];
+        const float h = (float)x;
+        v[i] = make_float2(h, (float)(x - (double)h));
     }
-    sv[3 * (size_t)k + 0] = (float)a0;
-    sv[3 * (size_t)k + 1] = (float)a1;
-    sv[3 * (size_t)k + 2] = (float)a2;
+    __syncthreads();
+    for (int q = kk; q < s; q += blockDim.x) {
+        const float2 *row = lam + (size_t)q * g;
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+        for (int m = 0; m < g; ++m) {
+            const float2 l = row[m];
+            dot2ff(h0, l0, l, v[3 * m]);
+            dot2ff(h1, l1, l, v[3 * m + 1]);
+            dot2ff(h2, l2, l, v[3 * m + 2]);
+        }
+        const size_t k = (size_t)panel * s + q;
+        sv[3 * k + 0] = h0 + l0;
+        sv[3 * k + 1] = h1 + l1;
+        sv[3 * k + 2] = h2 + l2;
+    }
 }
 
 // ---------------------------------------------- render preparation --
@@ -558,8 +581,10 @@ dc_status Fmm::Impl::build32(const Geometry &G, cudaStream_t st, std::string &er
 
 cudaError_t Fmm::Impl::interp32(const double *node_vals, float *seg_vals, cudaStream_t st) {
     int th = 256;
-    interp32_kernel<<<(D->S + th - 1) / th, th, 0, st>>>(D->lambda.ptr, node_vals, seg_vals, D->S,
-                                                        D->s, D->g); note_launch();
+    (void)th;
+    interp32_kernel<<<D->n_panels, std::min(256, (D->s + 31) / 32 * 32), 0, st>>>(lam_ff.ptr, node_vals, seg_vals,
+                                                                               D->s, D->g);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -609,7 +634,7 @@ cudaError_t Fmm::Impl::passes32(const float *sb, const float *mb, int use_s, int
     if (n_mchunks > 0) {   // every inner cell straight from its leaves
         passes::m2m_multi_kernel<float><<<(n_mchunks + passes::kMultiWarps - 1) / passes::kMultiWarps,
                                           32 * passes::kMultiWarps, 0, st>>>(
-            cc.ptr, iw32.ptr, mchunks.ptr, n_mchunks, pair_leaf.ptr, P1, binom32.ptr, M32i.ptr, mpart32.ptr);
+            pair_geo.ptr, mchunks.ptr, n_mchunks, pair_leaf.ptr, P1, binom32.ptr, M32i.ptr, mpart32.ptr);
         note_launch();
         if (n_mred > 0) {
             passes::m2m_reduce_kernel<float><<<(n_mred + 3) / 4, 128, 0, st>>>(mred.ptr, n_mred, P1, mpart32.ptr, M32i.ptr);
@@ -633,8 +658,9 @@ cudaError_t Fmm::Impl::passes32(const float *sb, const float *mb, int use_s, int
         note_launch();
     }
     if (sc.n_walk > 0) {
-        passes::walk_kernel<float><<<sc.n_walk, P1 <= 32 ? 32 : 64, passes::walk_smem<float>(P1), st>>>(
-            tv, sc.walk.ptr, level_d.ptr, P1, l2l32i.ptr, Lm2l32i.ptr, L32i.ptr);
+        passes::walk_kernel<float><<<sc.n_walk, std::max(32, (std::max(P1, walk_nmax) + 31) / 32 * 32),
+                                     passes::walk_smem<float>(P1, walk_nmax), st>>>(
+            tv, sc.walk.ptr, sc.chains.ptr, P1, walk_nmax, l2l32i.ptr, Lm2l32i.ptr, L32i.ptr);
         note_launch();
     }
     return cudaGetLastError();

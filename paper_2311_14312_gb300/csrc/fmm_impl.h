@@ -57,6 +57,7 @@ struct Schedule {
     DevBuf<int> m2l, p2l, l2l;        // cells with list 2 / list 4; cells per level
     std::vector<int> l2l_ptr;         // [depth + 2] offsets into l2l by level
     DevBuf<int> walk;                 // leaves whose incoming expansion is needed
+    DevBuf<int> chains;               // per walk leaf: length, then itself and its ancestors to level 2
     int n_m2l = 0, n_p2l = 0, n_walk = 0;
 };
 
@@ -136,10 +137,12 @@ struct Fmm::Impl {
     // pairs, C(k, j)
     DevBuf<int4> mchunks, mred;
     DevBuf<int> pair_leaf;
+    DevBuf<float4> pair_geo;          // per pair: shift d (x, y), scale rho
     DevBuf<float> binom32;
     DevBuf<float2> mpart32;
     int n_mchunks = 0, n_mred = 0, n_mslots = 0;
-    DevBuf<int> level_d;              // cell levels (downward walk)
+    DevBuf<int> level_d;              // cell levels
+    int walk_nmax = 1;                // longest walk chain (levels 2 .. depth)
     DevBuf<double2> base64, Lm2l;
     DevBuf<float4> baseff;            // base M2L tables in float-float
     DevBuf<float4> m2mff, l2lff;      // M2M / L2L tables in float-float
@@ -150,6 +153,7 @@ struct Fmm::Impl {
     int P1i = 0;
     DevBuf<float2> m2m32i, l2l32i, base32i, M32i, L32i, Lm2l32i;
     DevBuf<float2> m2lfull32i;        // [56][P1i][P1i] full M2L variants
+    DevBuf<float2> lam_ff;            // Lambda [s][g] as (hi, lo) floats
     DevBuf<double> iw64, logw64, plen64;
     DevBuf<unsigned char> heavy;      // per piece: near field evaluated in FP64
     DevBuf<unsigned char> heavyL, heavyM;   // per cell: L2P / M2P evaluated in FP64

@@ -147,13 +147,15 @@ __global__ void __launch_bounds__(kOrthThreads) orth_update_norm_kernel(const do
     }
 }
 
-// nrm[c] = sqrt(sum over the blocks of npart[block][c])
+// nrm[c] = sqrt(sum over the blocks of npart[block][c]): warp c sums its
+// channel (lanes over blocks, then a fixed butterfly)
 __global__ void npart_finalize_kernel(const double *__restrict__ npart, int nb, double *__restrict__ nrm) {
-    int c = threadIdx.x;
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (c >= 3) return;
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += npart[3 * b + c];
-    nrm[c] = sqrt(fmax(s, 0.0));
+    for (int b = lane; b < nb; b += 32) s += npart[3 * b + c];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) nrm[c] = sqrt(fmax(s, 0.0));
 }
 
 // out[i][c] = in[i][c] * (nrm[c] > 0 ? 1 / nrm[c] : 0)
@@ -553,7 +555,7 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
                     const int nb = (3 * N + kOrthThreads - 1) / kOrthThreads;
                     orth_update_norm_kernel<<<nb, kOrthThreads, 0, st>>>(W.V.ptr, vs, W.hpass.ptr, k + 1,
                                                                          W.w.ptr, N, W.npart.ptr); note_launch();
-                    npart_finalize_kernel<<<1, 32, 0, st>>>(W.npart.ptr, nb, W.hnext.ptr); note_launch();
+                    npart_finalize_kernel<<<1, 96, 0, st>>>(W.npart.ptr, nb, W.hnext.ptr); note_launch();
                 }
             }
             scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.w.ptr, W.hnext.ptr,

@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(32 * kLevelWarps) m2m_kernel(const int *__rest
 
 // M2M from each leaf straight to every listed ancestor, all levels in one
 // launch: Eq. 71 with the shift d = (c_leaf - c_anc) / w_anc and the scale
-// rho = w_leaf / w_anc of the width-scaled basis,
+// rho = w_leaf / w_anc of the width-scaled basis (pair_geo = (d, rho, 0)),
 //   Mt_anc[k] += sum_{j <= k} C(k, j) d^(k - j) rho^j Mt_leaf[j].
 // No level waits for another (each leaf moment is translated once per
 // ancestor instead of through the chain of parents).  One warp per chunk of
@@ -269,8 +269,7 @@ constexpr int kMultiLeaves = 8;
 constexpr int kMultiWarps = 4;
 
 template <typename T>
-__global__ void __launch_bounds__(32 * kMultiWarps) m2m_multi_kernel(const double *__restrict__ cc,
-                                                                     const T *__restrict__ iw,
+__global__ void __launch_bounds__(32 * kMultiWarps) m2m_multi_kernel(const float4 *__restrict__ pair_geo,
                                                                      const int4 *__restrict__ chunks, int n_chunks,
                                                                      const int *__restrict__ pair_leaf, int P1,
                                                                      const T *__restrict__ binom,
@@ -285,16 +284,16 @@ __global__ void __launch_bounds__(32 * kMultiWarps) m2m_multi_kernel(const doubl
     if (ci >= n_chunks) return;
     const int4 ch = chunks[ci];          // (ancestor, first pair, pairs, partial slot or -1)
     const int anc = ch.x;
-    const double ax = cc[2 * anc], ay = cc[2 * anc + 1];
-    const T iwa = iw[anc];
     C acc[3];
     for (int c = 0; c < 3; ++c) acc[c] = mk<T>(0, 0);
     const int nM = 3 * P1;
     for (int e = ch.y; e < ch.y + ch.z; ++e) {
         const int leaf = pair_leaf[e];
-        // d^lane and rho^lane by binary powering (5 squarings)
-        const C d = mk<T>((T)((cc[2 * leaf] - ax) * (double)iwa), (T)((cc[2 * leaf + 1] - ay) * (double)iwa));
-        const T rho = iwa / iw[leaf];
+        // d^lane and rho^lane by binary powering (5 squarings); the pair's
+        // shift d and scale rho were formed once per drawing
+        const float4 geo = pair_geo[e];
+        const C d = mk<T>((T)geo.x, (T)geo.y);
+        const T rho = (T)geo.z;
         C pz = mk<T>(1, 0), bz = d;
         T pr = 1, br = rho;
         for (int bit = 1; bit < 32; bit <<= 1) {
@@ -854,39 +853,44 @@ __global__ void __launch_bounds__(32 * kLevelWarps) l2l_kernel(TreeView<T> t, co
 constexpr int kWalkMax = 48;    // ancestors kept (tree depth <= 40)
 
 template <typename T>
-__global__ void walk_kernel(TreeView<T> t, const int *__restrict__ leaves, const int *__restrict__ level,
-                            int P1, const typename V2<T>::type *__restrict__ tab,
+__global__ void walk_kernel(TreeView<T> t, const int *__restrict__ leaves, const int *__restrict__ chains,
+                            int P1, int n_max, const typename V2<T>::type *__restrict__ tab,
                             const typename V2<T>::type *__restrict__ Lm2l,
                             typename V2<T>::type *__restrict__ L) {
     using C = typename V2<T>::type;
     extern __shared__ unsigned char smem_raw[];
     C *cur = reinterpret_cast<C *>(smem_raw);   // [3][P1]
-    __shared__ int chain[kWalkMax];
+    C *pre = cur + 3 * P1;                       // [n][3][P1]: the chain's Lm2l, loaded up front
+    __shared__ int chain[kWalkMax], quad[kWalkMax];
     __shared__ int n_chain;
     const int leaf = leaves[blockIdx.x];
     const int l = threadIdx.x;
-    if (l == 0) {
-        int n = 0;
-        for (int c = leaf; c >= 0 && level[c] >= 2 && n < kWalkMax; c = t.parent[c]) chain[n++] = c;
-        n_chain = n;
+    // chains[blockIdx.x * (n_max + 1)]: length, then the leaf and its
+    // ancestors down to level 2 (formed once per drawing)
+    const int *ch = chains + (size_t)blockIdx.x * (n_max + 1);
+    if (l == 0) n_chain = ch[0];
+    if (l < n_max) {
+        const int c = ch[1 + l];
+        chain[l] = c;
+        quad[l] = c >= 0 ? t.quad[c] : 0;
     }
     __syncthreads();
     const int n = n_chain;
+    if (l < P1)
+        for (int i = 0; i < n; ++i)
+            for (int c = 0; c < 3; ++c) pre[(i * 3 + c) * P1 + l] = Lm2l[((size_t)chain[i] * 3 + c) * P1 + l];
     C acc[3];
     for (int c = 0; c < 3; ++c) acc[c] = mk<T>(0, 0);
-    if (n > 0 && l < P1) {
-        const int top = chain[n - 1];
-        for (int c = 0; c < 3; ++c) acc[c] = Lm2l[((size_t)top * 3 + c) * P1 + l];
-    }
+    if (n > 0 && l < P1)
+        for (int c = 0; c < 3; ++c) acc[c] = pre[((n - 1) * 3 + c) * P1 + l];
     for (int i = n - 2; i >= 0; --i) {
         __syncthreads();
         if (l < P1)
             for (int c = 0; c < 3; ++c) cur[c * P1 + l] = acc[c];
         __syncthreads();
         if (l < P1) {
-            const int a = chain[i];
-            for (int c = 0; c < 3; ++c) acc[c] = Lm2l[((size_t)a * 3 + c) * P1 + l];
-            const C *Tq = tab + ((size_t)t.quad[a] * P1 + l) * P1;
+            for (int c = 0; c < 3; ++c) acc[c] = pre[(i * 3 + c) * P1 + l];
+            const C *Tq = tab + ((size_t)quad[i] * P1 + l) * P1;
             for (int k = l; k < P1; ++k) {
                 C tq = Tq[k];
                 for (int c = 0; c < 3; ++c) cfma(acc[c], tq, cur[c * P1 + k]);
@@ -897,8 +901,9 @@ __global__ void walk_kernel(TreeView<T> t, const int *__restrict__ leaves, const
         for (int c = 0; c < 3; ++c) L[((size_t)leaf * 3 + c) * P1 + l] = acc[c];
 }
 
-template <typename T> inline size_t walk_smem(int P1) {
-    return 3 * (size_t)P1 * sizeof(typename V2<T>::type);
+// n_max: the longest chain (levels 2 .. deepest), at most kWalkMax
+template <typename T> inline size_t walk_smem(int P1, int n_max) {
+    return 3 * (size_t)P1 * (1 + n_max) * sizeof(typename V2<T>::type);
 }
 
 template <typename T> inline size_t p2m_smem(int P1) {
