@@ -460,7 +460,7 @@ dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats)
         DenseOp op;
         op.A = ctx->AG.ptr;
         op.N = N;
-        ce = dc::gmres_solve(ctx->gw, op, N, ctx->b.ptr, ctx->sigma.ptr, ctx->opt.gmres_tol,
+        ce = dc::gmres_solve(ctx->gw, op, N, ctx->b.ptr, ctx->sigma.ptr, false, ctx->opt.gmres_tol,
                              ctx->opt.gmres_restart, ctx->opt.gmres_max_iter, s, gr, msg);
     } else {
         ce = ctx->fmm->solve(ctx->gw, ctx->b.ptr, ctx->sigma.ptr, ctx->opt, s, gr, msg, &n_refine);

@@ -202,8 +202,9 @@ void gmres_work_destroy(GmresWork *w);
 // Restarted GMRES for the 3 channels at once (Sec. 5.5), FP64 Arnoldi by
 // classical Gram-Schmidt with one re-orthogonalisation pass, Givens
 // rotations and the least-squares update on the device.  x holds x0 on
-// entry and the solution on exit.
-cudaError_t gmres_solve(GmresWork *w, Operator &A, int N, const double *b, double *x,
+// entry and the solution on exit; x0_zero: x is zero on entry (the first
+// residual is b, no operator application).
+cudaError_t gmres_solve(GmresWork *w, Operator &A, int N, const double *b, double *x, bool x0_zero,
                         double tol, int restart, int max_iter, cudaStream_t st,
                         GmresResult &res, std::string &err);
 

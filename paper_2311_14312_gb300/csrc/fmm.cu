@@ -1105,7 +1105,7 @@ cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_option
         double inner_tol = I.fp32 ? std::max(floor32, need) : std::max(0.5 * need, 1e-15);
         GmresResult inner;
         op.fp32 = I.fp32;
-        e = gmres_solve(w, op, N, I.ir_r.ptr, I.ir_d.ptr, inner_tol, opt.gmres_restart,
+        e = gmres_solve(w, op, N, I.ir_r.ptr, I.ir_d.ptr, true, inner_tol, opt.gmres_restart,
                         opt.gmres_max_iter - used, st, inner, err);
         if (e != cudaSuccess) return e;
         int mx = 0;

@@ -27,7 +27,7 @@ namespace {
 constexpr int kChunk = 4096;     // rows per partial dot-product block
 constexpr int kDotThreads = 256;
 constexpr int kPollRing = 4;     // pinned flag slots / events
-constexpr int kPollLag = 2;      // iterations between enqueue and flag read
+constexpr int kPollLag = 1;      // iterations between enqueue and flag read
 constexpr size_t kGivensSmem = 48 * 1024;   // Givens step staged in shared memory up to this
 
 // partial[(j * nchunk + chunk) * 3 + c] = sum over rows of the chunk of
@@ -463,7 +463,7 @@ cudaError_t vec_dots3(GmresWork *Wp, const double *u, const double *v, int N, do
     return cudaStreamSynchronize(st);
 }
 
-cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, double *x, double tol,
+cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, double *x, bool x0_zero, double tol,
                         int restart, int max_iter, cudaStream_t st, GmresResult &res,
                         std::string &err) {
     GmresWork &W = *Wp;
@@ -501,11 +501,19 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
     // is reached: stop, the caller's refinement takes over
     bool est_done = false;
     double prev_beta[3] = {0, 0, 0};
+    bool first = true;
     while (true) {
-        // r = b - A x ; beta = ||r||
-        if ((ce = A.apply(x, W.Ax.ptr, st)) != cudaSuccess) return ce;
-        res.n_matvec++;
-        residual_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(b, W.Ax.ptr, W.r.ptr, 3 * N); note_launch();
+        // r = b - A x ; beta = ||r||  (r = b for a zero start)
+        if (first && x0_zero) {
+            if ((ce = cudaMemcpyAsync(W.r.ptr, b, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, st)) !=
+                cudaSuccess)
+                return ce;
+        } else {
+            if ((ce = A.apply(x, W.Ax.ptr, st)) != cudaSuccess) return ce;
+            res.n_matvec++;
+            residual_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(b, W.Ax.ptr, W.r.ptr, 3 * N); note_launch();
+        }
+        first = false;
         if ((ce = norms(W, W.r.ptr, beta, st)) != cudaSuccess) return ce;
         double hbeta[3];
         if ((ce = cudaMemcpyAsync(hbeta, beta, 3 * sizeof(double), cudaMemcpyDeviceToHost, st)) !=
