@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "dc_internal.h"
+#include "ffarith.cuh"
 #include "segint.cuh"
 
 namespace dc {
@@ -28,15 +29,19 @@ namespace dc {
 namespace {
 
 constexpr int kGJ = 32;                 // block size of the Gauss-Jordan inversion
-constexpr float kInv4Pi = 0.0795774715459476679f;
+// -log|q - c| / 2pi = kMonoLog2 * log2(|q - c|^2)
+constexpr float kMonoLog2 = -0.0551589000381629f;   // -ln 2 / 4pi
 
-// Monopole kernel of panel j at a node: -log|q - c| / 2pi, in FP32 from
-// FP32 positions (the near pairs subtract exactly this value).
-__device__ __forceinline__ float mono32(float2 q, float2 c) {
+// log2 |q - c|^2 in FP32 from FP32 positions; the 1e-30 keeps a node that
+// sits on a centroid finite and changes no other value.
+__device__ __forceinline__ float mono_lg2(float2 q, float2 c) {
     const float dx = q.x - c.x, dy = q.y - c.y;
-    const float r2 = fmaxf(dx * dx + dy * dy, 1e-30f);
-    return -kInv4Pi * __logf(r2);
+    return __log2f(fmaf(dx, dx, fmaf(dy, dy, 1e-30f)));
 }
+
+// Monopole kernel of panel j at a node: -log|q - c| / 2pi (the near pairs
+// subtract exactly this value).
+__device__ __forceinline__ float mono32(float2 q, float2 c) { return kMonoLog2 * mono_lg2(q, c); }
 
 // corr[e][m] = (G_H 1_j)(q_{i,m}) - l_j mono32(q_{i,m}, c_j) for the near pair
 // e = (i, j): the exact single layer of panel j with unit density (Lambda
@@ -201,11 +206,14 @@ __device__ __forceinline__ void dot2_step(float &hi, float &lo, float w, float2 
     lo += se + pe + w * x.y;
 }
 
-// y = Ac^-1 s (fixed-order reduction); ly[j] = l_j y_j (FP32)
+// y = Ac^-1 s (fixed-order reduction); pan[j] = (c_j, k l_j y_j for
+// channels 0, 1), pan2[j] = k l_j y_j for channel 2, k = kMonoLog2 (FP32)
 __global__ void __launch_bounds__(128) coarse_solve_kernel(const float *__restrict__ Ainv, int n_pad, int P,
                                                            const float2 *__restrict__ s,
                                                            const float *__restrict__ plen32,
-                                                           double *__restrict__ y, float *__restrict__ ly) {
+                                                           const float2 *__restrict__ c32,
+                                                           double *__restrict__ y, float4 *__restrict__ pan,
+                                                           float *__restrict__ pan2) {
     // one block of 128 threads per row; compensated (float-float) sums: M
     // amplifies by ~1e4-1e5, and its rounding must stay well below the FP32
     // operator's own error
@@ -231,98 +239,126 @@ __global__ void __launch_bounds__(128) coarse_solve_kernel(const float *__restri
         red[w][2] = a2;
     }
     __syncthreads();
-    if (t < 3) {
-        const double v = red[0][t] + red[1][t] + red[2][t] + red[3][t];
-        y[3 * i + t] = v;
-        ly[3 * i + t] = plen32[i] * (float)v;
+    if (t == 0) {
+        double v[3];
+        for (int c = 0; c < 3; ++c) {
+            v[c] = red[0][c] + red[1][c] + red[2][c] + red[3][c];
+            y[3 * i + c] = v[c];
+        }
+        const float k = kMonoLog2 * plen32[i];
+        const float2 c = c32[i];
+        pan[i] = make_float4(c.x, c.y, k * (float)v[0], k * (float)v[1]);
+        pan2[i] = k * (float)v[2];
     }
 }
 
 // The monopoles of all panels at every node, t_q[a] = sum over the panels
 // of part q of l_j y_j mono32(q_a, c_j): kSplit parts in parallel (tiles of
-// panels staged in shared memory), added in order by residual_kernel.
+// panels staged in shared memory), added in order by residual_kernel.  Each
+// thread takes kMonoNodes nodes, so one pair of shared-memory loads serves
+// kMonoNodes logarithms.
 constexpr int kTile = 256;
-constexpr int kSplit = 4;
-__global__ void __launch_bounds__(128) monopole_kernel(const float2 *__restrict__ q32,
-                                                       const float2 *__restrict__ c32,
-                                                       const float *__restrict__ ly, int P, int N,
-                                                       float *__restrict__ part) {
-    __shared__ float2 sc[kTile];
-    __shared__ float sl[3][kTile];
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+constexpr int kSplit = 8;
+constexpr int kMonoNodes = 2;
+constexpr int kMonoThreads = 128;
+__global__ void __launch_bounds__(kMonoThreads) monopole_kernel(const float2 *__restrict__ q32,
+                                                                const float4 *__restrict__ pan,
+                                                                const float *__restrict__ pan2, int P, int N,
+                                                                float *__restrict__ part) {
+    __shared__ float4 sp[kTile];
+    __shared__ float sp2[kTile];
+    const int a0 = blockIdx.x * (kMonoThreads * kMonoNodes) + threadIdx.x;
     const int per = (P + kSplit - 1) / kSplit;
     const int lo = blockIdx.y * per, hi = min(P, lo + per);
-    const float2 q = a < N ? q32[a] : make_float2(0.f, 0.f);
-    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+    float2 q[kMonoNodes];
+    float t[kMonoNodes][3];
+#pragma unroll
+    for (int n = 0; n < kMonoNodes; ++n) {
+        const int a = a0 + n * kMonoThreads;
+        q[n] = a < N ? q32[a] : make_float2(0.f, 0.f);
+        t[n][0] = t[n][1] = t[n][2] = 0.f;
+    }
     for (int base = lo; base < hi; base += kTile) {
         const int cnt = min(kTile, hi - base);
         __syncthreads();
-        for (int u = threadIdx.x; u < cnt; u += blockDim.x) {
-            sc[u] = c32[base + u];
-            sl[0][u] = ly[3 * (base + u)];
-            sl[1][u] = ly[3 * (base + u) + 1];
-            sl[2][u] = ly[3 * (base + u) + 2];
+        for (int u = threadIdx.x; u < cnt; u += kMonoThreads) {
+            sp[u] = pan[base + u];
+            sp2[u] = pan2[base + u];
         }
         __syncthreads();
         for (int u = 0; u < cnt; ++u) {
-            const float k = mono32(q, sc[u]);
-            t0 += k * sl[0][u];
-            t1 += k * sl[1][u];
-            t2 += k * sl[2][u];
+            const float4 p = sp[u];
+            const float p2 = sp2[u];
+            const float2 c = make_float2(p.x, p.y);
+#pragma unroll
+            for (int n = 0; n < kMonoNodes; ++n) {
+                const float k = mono_lg2(q[n], c);
+                t[n][0] += k * p.z;
+                t[n][1] += k * p.w;
+                t[n][2] += k * p2;
+            }
         }
     }
-    if (a >= N) return;
-    float *o = part + ((size_t)blockIdx.y * N + a) * 3;
-    o[0] = t0;
-    o[1] = t1;
-    o[2] = t2;
+#pragma unroll
+    for (int n = 0; n < kMonoNodes; ++n) {
+        const int a = a0 + n * kMonoThreads;
+        if (a >= N) continue;
+        float *o = part + ((size_t)blockIdx.y * N + a) * 3;
+        o[0] = t[n][0];
+        o[1] = t[n][1];
+        o[2] = t[n][2];
+    }
 }
 
-// r = v - A~ P y: the monopole parts plus the near-pair corrections
-__global__ void residual_kernel(const float *__restrict__ part, int g, const int *__restrict__ nptr,
-                                const int2 *__restrict__ pairs, const double *__restrict__ corr,
-                                const double *__restrict__ y, const double *__restrict__ v, int N,
-                                double *__restrict__ r) {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= N) return;
-    double c0 = 0.0, c1 = 0.0, c2 = 0.0;
-    for (int q = 0; q < kSplit; ++q) {
-        const float *o = part + ((size_t)q * N + a) * 3;
-        c0 += o[0];
-        c1 += o[1];
-        c2 += o[2];
+// Per panel i (one block): r = v - A~ P y at its nodes (the monopole parts,
+// added in part order, plus the near-pair corrections), w = P y + B r with
+// B_i the panel's inverse self-interaction block, written when w is given,
+// and, when lam is given, sigma_bar = Lambda w for the panel's s segments in
+// float-float (w converted to hi/lo pairs once, Lambda stored as hi/lo
+// floats), rounded to FP32.
+constexpr int kPanelThreads = 128;
+__global__ void __launch_bounds__(kPanelThreads) panel_apply_kernel(
+    const float *__restrict__ part, int N, int g, int s, const int *__restrict__ nptr,
+    const int2 *__restrict__ pairs, const double *__restrict__ corr, const double *__restrict__ y,
+    const double *__restrict__ v, const double *__restrict__ inv, double *__restrict__ w,
+    const float2 *__restrict__ lam, float *__restrict__ sv) {
+    __shared__ double rs[3 * kMaxG];
+    __shared__ float2 ws[3 * kMaxG];
+    const int i = blockIdx.x, t = threadIdx.x;
+    if (t < 3 * g) {
+        const int m = t / 3, c = t - 3 * m;
+        const size_t a = (size_t)i * g + m;
+        double acc = 0.0;
+        for (int q = 0; q < kSplit; ++q) acc += part[((size_t)q * N + a) * 3 + c];
+        for (int e = nptr[i]; e < nptr[i + 1]; ++e) acc += corr[(size_t)e * g + m] * y[3 * pairs[e].y + c];
+        rs[t] = v[3 * a + c] - acc;
     }
-    const int i = a / g, m = a - i * g;
-    for (int e = nptr[i]; e < nptr[i + 1]; ++e) {
-        const int j = pairs[e].y;
-        const double w = corr[(size_t)e * g + m];
-        c0 += w * y[3 * j];
-        c1 += w * y[3 * j + 1];
-        c2 += w * y[3 * j + 2];
+    __syncthreads();
+    if (t < 3 * g) {
+        const int m = t / 3, c = t - 3 * m;
+        const double *row = inv + ((size_t)i * g + m) * g;
+        double acc = y[3 * i + c];
+        for (int n = 0; n < g; ++n) acc += row[n] * rs[3 * n + c];
+        if (w) w[3 * ((size_t)i * g + m) + c] = acc;
+        const float h = (float)acc;
+        ws[t] = make_float2(h, (float)(acc - (double)h));
     }
-    r[3 * (size_t)a] = v[3 * (size_t)a] - c0;
-    r[3 * (size_t)a + 1] = v[3 * (size_t)a + 1] - c1;
-    r[3 * (size_t)a + 2] = v[3 * (size_t)a + 2] - c2;
-}
-
-// w = P y + B r (B: the panels' inverse self-interaction blocks)
-__global__ void smooth_kernel(const double *__restrict__ inv, int P, int g, const double *__restrict__ y,
-                              const double *__restrict__ r, double *__restrict__ w) {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= P * g) return;
-    const int j = a / g, m = a - j * g;
-    const double *row = inv + ((size_t)j * g + m) * g;
-    const double *rs = r + (size_t)j * g * 3;
-    double a0 = y[3 * j], a1 = y[3 * j + 1], a2 = y[3 * j + 2];
-    for (int n = 0; n < g; ++n) {
-        const double b = row[n];
-        a0 += b * rs[3 * n];
-        a1 += b * rs[3 * n + 1];
-        a2 += b * rs[3 * n + 2];
+    if (!lam) return;
+    __syncthreads();
+    for (int q = t; q < s; q += kPanelThreads) {
+        const float2 *lr = lam + (size_t)q * g;
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+        for (int m = 0; m < g; ++m) {
+            const float2 l = lr[m];
+            dot2ff(h0, l0, l, ws[3 * m]);
+            dot2ff(h1, l1, l, ws[3 * m + 1]);
+            dot2ff(h2, l2, l, ws[3 * m + 2]);
+        }
+        const size_t k = (size_t)i * s + q;
+        sv[3 * k + 0] = h0 + l0;
+        sv[3 * k + 1] = h1 + l1;
+        sv[3 * k + 2] = h2 + l2;
     }
-    w[3 * (size_t)a] = a0;
-    w[3 * (size_t)a + 1] = a1;
-    w[3 * (size_t)a + 2] = a2;
 }
 
 }  // namespace
@@ -380,8 +416,8 @@ cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st
         return e;
     if ((e = corr_.alloc(pairs.size() * (size_t)g)) != cudaSuccess ||
         (e = Ainv_.alloc((size_t)n_pad_ * n_pad_)) != cudaSuccess || (e = s_.alloc(3 * (size_t)P)) != cudaSuccess ||
-        (e = y_.alloc(3 * (size_t)P)) != cudaSuccess || (e = ly_.alloc(3 * (size_t)P)) != cudaSuccess ||
-        (e = r_.alloc(3 * (size_t)N)) != cudaSuccess || (e = part_.alloc((size_t)kSplit * 3 * N)) != cudaSuccess)
+        (e = y_.alloc(3 * (size_t)P)) != cudaSuccess || (e = pan_.alloc((size_t)P)) != cudaSuccess || (e = pan2_.alloc((size_t)P)) != cudaSuccess ||
+        (e = part_.alloc((size_t)kSplit * 3 * N)) != cudaSuccess)
         return e;
     near_pairs_kernel<<<(unsigned)pairs.size(), 32, 0, st>>>(pairs_.ptr, D.seg.ptr, D.segw.ptr, D.node_xy.ptr,
                                                             D.node_seg.ptr, D.node_seg2.ptr, q32_.ptr, c32_.ptr,
@@ -432,15 +468,18 @@ cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st
     return cudaSuccess;
 }
 
-cudaError_t TwoLevel::apply(const double *inv, const double *v, double *w, cudaStream_t st) {
+cudaError_t TwoLevel::apply(const double *inv, const double *v, double *w, cudaStream_t st, const float2 *lam, int s,
+                            float *sv) {
     const int P = P_, g = g_, N = P * g;
     restrict_kernel<<<(3 * P + 255) / 256, 256, 0, st>>>(v, P, g, s_.ptr);
-    coarse_solve_kernel<<<P, 128, 0, st>>>(Ainv_.ptr, n_pad_, P, s_.ptr, plen32_.ptr, y_.ptr, ly_.ptr);
-    monopole_kernel<<<dim3((N + 127) / 128, kSplit), 128, 0, st>>>(q32_.ptr, c32_.ptr, ly_.ptr, P, N, part_.ptr);
-    residual_kernel<<<(N + 255) / 256, 256, 0, st>>>(part_.ptr, g, nptr_.ptr, pairs_.ptr, corr_.ptr, y_.ptr, v, N,
-                                                    r_.ptr);
-    smooth_kernel<<<(N + 255) / 256, 256, 0, st>>>(inv, P, g, y_.ptr, r_.ptr, w);
-    note_launch(5);
+    coarse_solve_kernel<<<P, 128, 0, st>>>(Ainv_.ptr, n_pad_, P, s_.ptr, plen32_.ptr, c32_.ptr, y_.ptr, pan_.ptr,
+                                          pan2_.ptr);
+    const int per_block = kMonoThreads * kMonoNodes;
+    monopole_kernel<<<dim3((N + per_block - 1) / per_block, kSplit), kMonoThreads, 0, st>>>(q32_.ptr, pan_.ptr,
+                                                                                         pan2_.ptr, P, N, part_.ptr);
+    panel_apply_kernel<<<P, kPanelThreads, 0, st>>>(part_.ptr, N, g, s, nptr_.ptr, pairs_.ptr, corr_.ptr, y_.ptr, v,
+                                                    inv, w, lam, sv);
+    note_launch(4);
     return cudaGetLastError();
 }
 

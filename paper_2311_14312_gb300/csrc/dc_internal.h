@@ -165,16 +165,20 @@ public:
         out[2] = n_pairs_;
         out[3] = check_;
     }
-    // w = M v on [N][3] vectors; inv: the panel blocks' inverses
-    cudaError_t apply(const double *inv, const double *v, double *w, cudaStream_t st);
+    // w = M v on [N][3] vectors (w may be null); inv: the panel blocks'
+    // inverses.  With lam (Lambda as hi/lo floats, [s][g]) and sv: also
+    // sv = Lambda (M v) per panel, [S][3] FP32.
+    cudaError_t apply(const double *inv, const double *v, double *w, cudaStream_t st, const float2 *lam = nullptr,
+                      int s = 0, float *sv = nullptr);
 
 private:
     bool ready_ = false;
     int P_ = 0, g_ = 0, n_pad_ = 0, n_pairs_ = 0;
     double check_ = -1.0;
     DevBuf<float2> c32_, q32_;
-    DevBuf<double> plen_, corr_, y_, r_;
-    DevBuf<float> plen32_, ly_, Ainv_, part_;
+    DevBuf<double> plen_, corr_, y_;
+    DevBuf<float> plen32_, pan2_, Ainv_, part_;
+    DevBuf<float4> pan_;
     DevBuf<float2> s_;
     DevBuf<int> nptr_;
     DevBuf<int2> pairs_;

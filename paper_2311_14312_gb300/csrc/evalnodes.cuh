@@ -117,10 +117,10 @@ __device__ __forceinline__ void reduce_write(const NodeArgs<T> &a, int t0, int n
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
         if (warp + kWarps * j >= nt) break;
-        const int o = a.perm[t0 + warp + kWarps * j];
-        a.out[3 * (size_t)o + 0] = (double)acc[j][0];
-        a.out[3 * (size_t)o + 1] = (double)acc[j][1];
-        a.out[3 * (size_t)o + 2] = (double)acc[j][2];
+        const size_t o = 3 * (size_t)a.perm[t0 + warp + kWarps * j];
+        a.out[o + 0] = (double)acc[j][0];
+        a.out[o + 1] = (double)acc[j][1];
+        a.out[o + 2] = (double)acc[j][2];
     }
 }
 
@@ -329,7 +329,8 @@ static __global__ void __launch_bounds__(32 * kWarps) far_coef_kernel(NodeArgs<d
 }
 
 // Far field from stored coefficients into the lane sums: lanes split the
-// (block, k) terms of each target.
+// (block, k) terms; each term's three expansion coefficients are loaded once
+// and applied to all of the warp's targets.
 template <typename T>
 __device__ __forceinline__ void far_rows_into(const NodeArgs<T> &a, const typename passes::V2<T>::type *__restrict__ cf,
                                               long long base, int leaf, int nt, int warp, int lane,
@@ -338,71 +339,97 @@ __device__ __forceinline__ void far_rows_into(const NodeArgs<T> &a, const typena
     const int P1 = a.P1;
     const int w0 = a.w_ptr[leaf], nb = 1 + a.w_ptr[leaf + 1] - w0;
     const int nterm = nb * P1;
+    const C *rows = cf + base;
+#pragma unroll 2
+    for (int u = lane; u < nterm; u += 32) {
+        const int b = u / P1, k = u - b * P1;
+        const int src = b == 0 ? leaf : a.w_idx[w0 + b - 1];
+        const C *X = (b == 0 ? a.L : a.M) + (size_t)src * 3 * P1 + k;
+        C co[kPer];
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-        const int tl = warp + kWarps * j;
-        if (tl >= nt) break;
-        const C *row = cf + base + (long long)tl * nterm;
-        for (int u = lane; u < nterm; u += 32) {
-            const int b = u / P1, k = u - b * P1;
-            const int src = b == 0 ? leaf : a.w_idx[w0 + b - 1];
-            const C *X = (b == 0 ? a.L : a.M) + (size_t)src * 3 * P1 + k;
-            const C co = row[u];
-            const C x0 = X[0], x1 = X[P1], x2 = X[2 * P1];
-            acc[j][0] += co.x * x0.x - co.y * x0.y;
-            acc[j][1] += co.x * x1.x - co.y * x1.y;
-            acc[j][2] += co.x * x2.x - co.y * x2.y;
+        for (int j = 0; j < kPer; ++j) {
+            const int tl = warp + kWarps * j;
+            co[j] = tl < nt ? rows[(long long)tl * nterm + u] : C{T(0), T(0)};
+        }
+        const C x0 = X[0], x1 = X[P1], x2 = X[2 * P1];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            acc[j][0] += co[j].x * x0.x - co[j].y * x0.y;
+            acc[j][1] += co[j].x * x1.x - co[j].y * x1.y;
+            acc[j][2] += co[j].x * x2.x - co[j].y * x2.y;
         }
     }
 }
 
 // Node operator with the near field from stored coefficients (near_coef_kernel
 // layout): y = sum_pl coef * dens[seg(pl)] + far field (L2P, list-3 M2P),
-// the far field from stored coefficients too when far != nullptr.
+// the far field from stored coefficients too when far != nullptr.  Lanes
+// walk the leaf's list-1 pieces kBatch at a time, issuing every load of a
+// batch (segment numbers, coefficients, then densities) before the first
+// multiply-add, so that a warp keeps several requests in flight.
+constexpr int kBatch = 4;
+
 template <typename T>
-__global__ void __launch_bounds__(32 * kWarps) near_apply_kernel(NodeArgs<T> a, const long long *__restrict__ off,
+__global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 8 : 4) near_apply_kernel(NodeArgs<T> a, const long long *__restrict__ off,
                                                                   const T *__restrict__ coef,
                                                                   const T *__restrict__ dens,
                                                                   const long long *__restrict__ far_off = nullptr,
                                                                   const typename passes::V2<T>::type *__restrict__ far = nullptr) {
     const int4 it = a.items[blockIdx.x];
     const int leaf = it.x, t0 = it.y, nt = it.z, nU = it.w;
-    const long long base = off[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const double cx = a.cc64[2 * leaf], cy = a.cc64[2 * leaf + 1];
-    T qx[kPer], qy[kPer], acc[kPer][3];
-    const T *row[kPer];
+    T acc[kPer][3];
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-        const int tl = warp + kWarps * j;
-        const int ti = t0 + tl;
-        bool ok = tl < nt;
-        qx[j] = ok ? (T)(a.q64[2 * ti] - cx) : T(0);
-        qy[j] = ok ? (T)(a.q64[2 * ti + 1] - cy) : T(0);
-        row[j] = coef + base + (long long)(ok ? tl : 0) * nU;
-        acc[j][0] = acc[j][1] = acc[j][2] = T(0);
-    }
-    // lanes walk the leaf's list-1 pieces in list order (their segments,
-    // flattened per leaf); no block-wide staging or barriers
+    for (int j = 0; j < kPer; ++j) acc[j][0] = acc[j][1] = acc[j][2] = T(0);
     if (warp < nt) {
+        const T *rows = coef + off[blockIdx.x];
         const int *segs = a.uf_seg + a.uf_ptr[leaf];
-        for (int pl = lane; pl < nU; pl += 32) {
-            const int seg = segs[pl];
-            const T d0 = dens[3 * (size_t)seg], d1 = dens[3 * (size_t)seg + 1], d2 = dens[3 * (size_t)seg + 2];
+        for (int p0 = 0; p0 < nU; p0 += 32 * kBatch) {
+            int sg[kBatch];
+            T cv[kBatch][kPer];
 #pragma unroll
-            for (int j = 0; j < kPer; ++j) {
-                if (warp + kWarps * j >= nt) break;
-                const T cfv = row[j][pl];
-                acc[j][0] += cfv * d0;
-                acc[j][1] += cfv * d1;
-                acc[j][2] += cfv * d2;
+            for (int i = 0; i < kBatch; ++i) {
+                const int pl = p0 + lane + 32 * i;
+                sg[i] = pl < nU ? segs[pl] : -1;
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) {
+                    const int tl = warp + kWarps * j;
+                    cv[i][j] = (pl < nU && tl < nt) ? rows[(long long)tl * nU + pl] : T(0);
+                }
             }
+            T d[kBatch][3];
+#pragma unroll
+            for (int i = 0; i < kBatch; ++i) {
+                const bool ok = sg[i] >= 0;
+                const size_t o = 3 * (size_t)(ok ? sg[i] : 0);
+                d[i][0] = ok ? dens[o] : T(0);
+                d[i][1] = ok ? dens[o + 1] : T(0);
+                d[i][2] = ok ? dens[o + 2] : T(0);
+            }
+#pragma unroll
+            for (int i = 0; i < kBatch; ++i)
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) {
+                    acc[j][0] += cv[i][j] * d[i][0];
+                    acc[j][1] += cv[i][j] * d[i][1];
+                    acc[j][2] += cv[i][j] * d[i][2];
+                }
         }
     }
-    if (far)
+    if (far) {
         far_rows_into<T>(a, far, far_off[blockIdx.x] * a.P1, leaf, nt, warp, lane, acc);
-    else
+    } else {
+        const double cx = a.cc64[2 * leaf], cy = a.cc64[2 * leaf + 1];
+        T qx[kPer], qy[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int tl = warp + kWarps * j;
+            const int ti = t0 + (tl < nt ? tl : 0);
+            qx[j] = tl < nt ? (T)(a.q64[2 * ti] - cx) : T(0);
+            qy[j] = tl < nt ? (T)(a.q64[2 * ti + 1] - cy) : T(0);
+        }
         far_into<T>(a, leaf, t0, nt, warp, lane, qx, qy, acc);
+    }
     reduce_write<T>(a, t0, nt, warp, lane, acc);
 }
 

@@ -347,9 +347,14 @@ cudaError_t Fmm::Impl::passes(const double *sb, const double *mb, int use_s, int
         note_launch();
     }
     if (sc.n_p2l > 0) {
-        passes::p2l_kernel<double, passes::PiecesF64><<<sc.n_p2l, passes::kChunk, passes::p2l_smem<double>(P1), st>>>(
-            tv, ps, sc.p2l.ptr, sb, mb, use_s, use_m, P1, Lm2l.ptr, rows_ready ? p2l_off.ptr : nullptr,
-            rows_ready ? p2l_g64.ptr : nullptr, rows_ready && use_m ? p2l_f64.ptr : nullptr);
+        if (rows_ready)
+            passes::p2l_flat_kernel<double, passes::PiecesF64>
+                <<<sc.n_p2l, passes::kChunk, passes::p2l_flat_smem<double>(P1), st>>>(
+                    tv, ps, sc.p2l.ptr, p2l_off.ptr, p2l_cnt.ptr, p2l_item.ptr, sb, mb, use_s, use_m, P1, Lm2l.ptr,
+                    p2l_g64.ptr, use_m ? p2l_f64.ptr : nullptr);
+        else
+            passes::p2l_kernel<double, passes::PiecesF64><<<sc.n_p2l, passes::kChunk, passes::p2l_smem<double>(P1), st>>>(
+                tv, ps, sc.p2l.ptr, sb, mb, use_s, use_m, P1, Lm2l.ptr);
         note_launch();
     }
     for (int l = 2; l <= tree.depth; ++l) {   // per level: FP64 work per cell once
@@ -741,10 +746,17 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     // rows of the stored P2L coefficients: the pieces of each list-4 cell of
     // the full schedule (the node schedule's cells are among them)
     std::vector<long long> p2l_off(nC, -1);
+    std::vector<int> p2l_cnt(nC, 0);
+    std::vector<int2> p2l_item;   // (piece, list-4 entry) per row
     long long p2l_rows = 0;
     for (int c : ap2l) {
         p2l_off[c] = p2l_rows;
-        for (int e = T.x_ptr[c]; e < T.x_ptr[c + 1]; ++e) p2l_rows += T.piece_count[T.x_idx[e]];
+        for (int e = T.x_ptr[c]; e < T.x_ptr[c + 1]; ++e) {
+            const int src = T.x_idx[e];
+            for (int k = 0; k < T.piece_count[src]; ++k) p2l_item.push_back(make_int2(T.piece_start[src] + k, e));
+            p2l_rows += T.piece_count[src];
+        }
+        p2l_cnt[c] = int(p2l_rows - p2l_off[c]);
     }
     I.p2l_rows = p2l_rows;
     {
@@ -876,6 +888,8 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     UP(I.near_off, near_off);
     UP(I.far_off, far_off);
     UP(I.p2l_off, p2l_off);
+    UP(I.p2l_cnt, p2l_cnt);
+    UP(I.p2l_item, p2l_item);
     UP(I.iw64, iw64);
     UP(I.logw64, logw64);
     UP(I.plen64, plen64);
@@ -993,6 +1007,8 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passes::p2l_smem<double>(I.P1));
     cudaFuncSetAttribute(passes::p2m_kernel<double, passes::PiecesF64>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passes::p2m_smem<double>(I.P1));
+    cudaFuncSetAttribute(passes::p2l_flat_kernel<double, passes::PiecesF64>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passes::p2l_flat_smem<double>(I.P1));
     if ((e = I.build_rows(st)) != cudaSuccess) {
         err = std::string("stored P2M / P2L coefficients: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;

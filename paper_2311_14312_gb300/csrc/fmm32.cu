@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "evalnodes.cuh"
+#include "ffarith.cuh"
 #include "fmm_impl.h"
 #include "segint.cuh"
 
@@ -65,16 +66,6 @@ __global__ void d2f_kernel(const double *__restrict__ a, const double *__restric
 // floats), rounded to FP32 at the end: one block per panel, one thread per
 // segment.  The node values can be large and cancelling (the coarse part of
 // the preconditioned vector), so the sums keep more than FP32 accuracy.
-__device__ __forceinline__ void dot2ff(float &hi, float &lo, float2 a, float2 b) {
-    const float p = __fmul_rn(a.x, b.x);
-    const float pe = fmaf(a.x, b.x, -p);
-    const float sum = __fadd_rn(hi, p);
-    const float bb = __fsub_rn(sum, hi);
-    const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(p, bb));
-    hi = sum;
-    lo += se + pe + fmaf(a.x, b.y, a.y * b.x);
-}
-
 __global__ void interp32_kernel(const float2 *__restrict__ lam, const double *__restrict__ nv,
                                 float *__restrict__ sv, int s, int g) {
     __shared__ float2 v[3 * kMaxG];
@@ -576,6 +567,8 @@ dc_status Fmm::Impl::build32(const Geometry &G, cudaStream_t st, std::string &er
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passes::p2l_smem<float>(P1));
     cudaFuncSetAttribute(passes::p2m_kernel<float, passes::PiecesF32>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passes::p2m_smem<float>(P1));
+    cudaFuncSetAttribute(passes::p2l_flat_kernel<float, passes::PiecesF32>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passes::p2l_flat_smem<float>(P1));
     return DC_OK;
 }
 
@@ -621,11 +614,11 @@ cudaError_t Fmm::Impl::passes32(const float *sb, const float *mb, int use_s, int
     const int P1 = P1i;
     size_t ebytes = (size_t)nC * 3 * P1 * sizeof(float2);
     cudaError_t e;
+    passes::TreeView<float> tv = view32();
+    passes::PiecesF32 ps{pc32.ptr};
     if ((e = cudaMemsetAsync(M32i.ptr, 0, ebytes, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(L32i.ptr, 0, ebytes, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(Lm2l32i.ptr, 0, ebytes, st)) != cudaSuccess) return e;
-    passes::TreeView<float> tv = view32();
-    passes::PiecesF32 ps{pc32.ptr};
     if (n_p2m > 0) {
         passes::p2m_kernel<float, passes::PiecesF32><<<n_p2m, passes::kChunk, passes::p2m_smem<float>(P1), st>>>(
             tv, ps, p2m_leaves.ptr, sb, mb, use_s, use_m, P1, M32i.ptr, rows_ready && !use_m ? p2m_g32.ptr : nullptr);
@@ -653,8 +646,8 @@ cudaError_t Fmm::Impl::passes32(const float *sb, const float *mb, int use_s, int
         note_launch();
     }
     if (sc.n_p2l > 0) {
-        passes::p2l_kernel<float, passes::PiecesF32><<<sc.n_p2l, passes::kChunk, passes::p2l_smem<float>(P1), st>>>(
-            tv, ps, sc.p2l.ptr, sb, mb, use_s, use_m, P1, Lm2l32i.ptr);
+        passes::p2l_flat_kernel<float, passes::PiecesF32><<<sc.n_p2l, passes::kChunk, passes::p2l_flat_smem<float>(P1), st>>>(
+            tv, ps, sc.p2l.ptr, p2l_off.ptr, p2l_cnt.ptr, p2l_item.ptr, sb, mb, use_s, use_m, P1, Lm2l32i.ptr);
         note_launch();
     }
     if (sc.n_walk > 0) {
@@ -690,9 +683,10 @@ cudaError_t Fmm::Impl::prepare_render32(const double *sb, const double *mb, cuda
 cudaError_t Fmm::Impl::apply_nodes32(const double *x, double *y, bool single, cudaStream_t st) {
     cudaError_t e = interp32(x, single ? sbar32.ptr : mbar32.ptr, st);
     if (e != cudaSuccess) return e;
-    int us = single ? 1 : 0, um = single ? 0 : 1;
-    if ((e = passes32(sbar32.ptr, mbar32.ptr, us, um, st, sched_nodes)) != cudaSuccess) return e;
-    if (n_nt_items4 == 0) return cudaSuccess;
+    return nodes32_from_segments(y, single, st);
+}
+
+evalnodes::NodeArgs<float> Fmm::Impl::node_args32(double *y, bool single) const {
     evalnodes::NodeArgs<float> a;
     a.u_ptr = u_ptr.ptr;
     a.u_idx = u_idx.ptr;
@@ -711,25 +705,32 @@ cudaError_t Fmm::Impl::apply_nodes32(const double *x, double *y, bool single, cu
     a.own1 = nt_own1.ptr;
     a.own2 = nt_own2.ptr;
     a.perm = nt_perm.ptr;
-    a.P1 = P1;
-    a.M = M32.ptr;
-    a.L = L32.ptr;
     a.sb = sbar32.ptr;
     a.mb = mbar32.ptr;
-    a.use_s = us;
-    a.use_m = um;
+    a.use_s = single ? 1 : 0;
+    a.use_m = single ? 0 : 1;
     a.out = y;
     a.P1 = P1i;
     a.M = M32i.ptr;
     a.L = L32i.ptr;
     a.uf_ptr = uf_ptr.ptr;
     a.uf_seg = uf_seg.ptr;
+    return a;
+}
+
+cudaError_t Fmm::Impl::nodes32_from_segments(double *y, bool single, cudaStream_t st) {
+    cudaError_t e;
+    int us = single ? 1 : 0, um = single ? 0 : 1;
+    if ((e = passes32(sbar32.ptr, mbar32.ptr, us, um, st, sched_nodes)) != cudaSuccess) return e;
+    if (n_nt_items4 == 0) return cudaSuccess;
+    const evalnodes::NodeArgs<float> a = node_args32(y, single);
+    const dim3 grid(n_nt_items4), block(32 * evalnodes::kWarps);
     if (near_ready && single)
-        evalnodes::near_apply_kernel<float><<<n_nt_items4, 32 * evalnodes::kWarps, 0, st>>>(
+        evalnodes::near_apply_kernel<float><<<grid, block, 0, st>>>(
             a, near_off.ptr, near_g32.ptr, sbar32.ptr, far_ready ? far_off.ptr : nullptr,
             far_ready ? far32.ptr : nullptr);
     else
-        evalnodes::eval_nodes_kernel<float><<<n_nt_items4, 32 * evalnodes::kWarps, 0, st>>>(a);
+        evalnodes::eval_nodes_kernel<float><<<grid, block, 0, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }
@@ -744,8 +745,15 @@ cudaError_t Fmm::Impl::graph_matvec32(const double *x, double *y, cudaStream_t s
             return e;
         long long before = kernel_launches();
         if ((e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
-        cudaError_t e1 = precond(g_in.ptr, ir_t.ptr, cap_stream);
-        cudaError_t e2 = (e1 == cudaSuccess) ? apply_nodes32(ir_t.ptr, g_out.ptr, true, cap_stream) : e1;
+        // M v straight to the segments (sigma_bar = Lambda M v) when the
+        // two-level preconditioner is in use, else M v at the nodes first
+        cudaError_t e1 = coarse.ready()
+                             ? coarse.apply(pinv.ptr, g_in.ptr, nullptr, cap_stream, lam_ff.ptr, D->s, sbar32.ptr)
+                             : precond(g_in.ptr, ir_t.ptr, cap_stream);
+        cudaError_t e2 = e1;
+        if (e1 == cudaSuccess)
+            e2 = coarse.ready() ? nodes32_from_segments(g_out.ptr, true, cap_stream)
+                                : apply_nodes32(ir_t.ptr, g_out.ptr, true, cap_stream);
         e = cudaStreamEndCapture(cap_stream, &g32);
         g32_kernels = int(kernel_launches() - before);
         note_launch(-g32_kernels);   // counted again at every graph launch

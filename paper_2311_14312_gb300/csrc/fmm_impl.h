@@ -105,6 +105,8 @@ struct Fmm::Impl {
     bool rows_ready = false;
     long long p2l_rows = 0;
     DevBuf<long long> p2l_off;
+    DevBuf<int> p2l_cnt;          // [cells] rows of the cell's list 4
+    DevBuf<int2> p2l_item;        // [p2l_rows] (piece, list-4 entry), row order
     DevBuf<double2> p2m_g64, p2m_f64, p2l_g64, p2l_f64;
     DevBuf<float2> p2m_g32;
     cudaError_t build_rows(cudaStream_t st);
@@ -195,6 +197,10 @@ struct Fmm::Impl {
     cudaError_t prepare_render32(const double *sb, const double *mb, cudaStream_t st);
     cudaError_t apply_nodes32(const double *x, double *y, bool single, cudaStream_t st);
     cudaError_t interp32(const double *node_vals, float *seg_vals, cudaStream_t st);
+    // the FP32 operator at the nodes from segment values already in
+    // sbar32 (single) or mbar32
+    cudaError_t nodes32_from_segments(double *y, bool single, cudaStream_t st);
+    evalnodes::NodeArgs<float> node_args32(double *y, bool single) const;
     cudaError_t render_tiles32(int n_tiles, void *rgb, int rgb_dtype,
                                unsigned char *rgb8, const double *sb64, const double *mb64,
                                cudaStream_t st);

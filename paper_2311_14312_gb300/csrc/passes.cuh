@@ -402,14 +402,24 @@ __global__ void __launch_bounds__(32 * kM2LSlots) m2l_kernel(TreeView<T> t, cons
 // costs P1 x P1 complex multiply-adds per channel and no bookkeeping.  One
 // warp per target cell: for P1 <= 16 lane l + 16 h sums the terms k = h,
 // h + 2, ... of coefficient l and the halves are added at the end; above 16
-// lane l sums all k.  The source moments of each pair are staged in shared
-// memory (double buffered, the next pair's loads in flight during the
-// current pair's products).
+// lane l sums all k.  The source moments of the pairs are copied into a
+// per-warp ring of kM2LDepth shared-memory slots by asynchronous copies
+// (cp.async), kM2LDepth - 1 pairs ahead of the products.
 constexpr int kM2LSmallP1 = 21;
 constexpr int kM2LSmallWarps = 16;
+constexpr int kM2LDepth = 4;
 
 inline size_t m2l_small_smem(int P1) {
-    return (56 * (size_t)P1 * P1 + kM2LSmallWarps * 2 * 64) * sizeof(float2);
+    return (56 * (size_t)P1 * P1 + kM2LSmallWarps * kM2LDepth * 64) * sizeof(float2);
+}
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 static __global__ void __launch_bounds__(32 * kM2LSmallWarps) m2l_small_kernel(TreeView<float> t, const int *__restrict__ cells,
@@ -419,7 +429,7 @@ static __global__ void __launch_bounds__(32 * kM2LSmallWarps) m2l_small_kernel(T
                                                                                float2 *__restrict__ Lout) {
     extern __shared__ unsigned char smem_raw[];
     float2 *Tf = reinterpret_cast<float2 *>(smem_raw);            // [56][P1][P1]
-    float2 *stage = Tf + 56 * P1 * P1;                            // [warps][2][64]
+    float2 *stage = Tf + 56 * P1 * P1;                            // [warps][kM2LDepth][64]
     for (int i = threadIdx.x; i < 56 * P1 * P1; i += blockDim.x) Tf[i] = full[i];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -427,34 +437,35 @@ static __global__ void __launch_bounds__(32 * kM2LSmallWarps) m2l_small_kernel(T
     const int l = halves == 2 ? (lane & 15) : lane, h = halves == 2 ? (lane >> 4) : 0;
     const int lr = min(l, P1 - 1);
     const int nM = 3 * P1;
-    float2 *buf = stage + warp * 2 * 64;
+    float2 *buf = stage + warp * kM2LDepth * 64;
     const float2 zero = make_float2(0.f, 0.f);
+    // copy the moments of list-2 entry e into ring slot (e - e0) mod depth
+    auto issue = [&](int e, int e0) {
+        float2 *dst = buf + ((e - e0) % kM2LDepth) * 64;
+        const float2 *ms = M + (size_t)t.v_idx[e] * nM;
+        if (lane < nM) cp_async8(dst + lane, ms + lane);
+        if (lane + 32 < nM) cp_async8(dst + lane + 32, ms + lane + 32);
+    };
     for (int ci = blockIdx.x * kM2LSmallWarps + warp; ci < n_cells; ci += gridDim.x * kM2LSmallWarps) {
         const int cell = cells[ci];
         const float mlogw = -t.logw[cell];
         float2 acc[3] = {zero, zero, zero};
         const int e0 = t.v_ptr[cell], e1 = t.v_ptr[cell + 1];
-        float2 pa = zero, pb = zero;
-        int code = 0;
-        if (e0 < e1) {
-            const float2 *ms = M + (size_t)t.v_idx[e0] * nM;
-            pa = lane < nM ? ms[lane] : zero;
-            pb = lane + 32 < nM ? ms[lane + 32] : zero;
-            code = t.v_code[e0];
+#pragma unroll
+        for (int d = 0; d < kM2LDepth - 1; ++d) {
+            if (e0 + d < e1) issue(e0 + d, e0);
+            cp_async_commit();
         }
-        int slot = 0;
         for (int e = e0; e < e1; ++e) {
-            float2 *cur = buf + slot * 64;
-            cur[lane] = pa;
-            cur[lane + 32] = pb;
+            // the slot refilled here was read in the previous iteration,
+            // which ended with __syncwarp
+            if (e + kM2LDepth - 1 < e1) issue(e + kM2LDepth - 1, e0);
+            cp_async_commit();
+            cp_async_wait<kM2LDepth - 1>();        // entry e has landed (own copies)
+            __syncwarp();                           // and every lane's copies are visible
+            const float2 *cur = buf + ((e - e0) % kM2LDepth) * 64;
+            const int code = t.v_code[e];
             const int b = code & 7, r = (code >> 3) & 3, cj = code >> 5;
-            __syncwarp();
-            if (e + 1 < e1) {
-                const float2 *ms = M + (size_t)t.v_idx[e + 1] * nM;
-                pa = lane < nM ? ms[lane] : zero;
-                pb = lane + 32 < nM ? ms[lane + 32] : zero;
-                code = t.v_code[e + 1];
-            }
             const float2 *Tl = Tf + ((size_t)(b + 7 * r + 28 * cj) * P1 + lr) * P1;
             for (int k = h; k < P1; k += halves) {
                 const float2 tk = Tl[k];
@@ -464,7 +475,7 @@ static __global__ void __launch_bounds__(32 * kM2LSmallWarps) m2l_small_kernel(T
             if (lane == 0)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) acc[c].x += mlogw * cur[c * P1].x;   // Mt_0 is real
-            slot ^= 1;
+            __syncwarp();
         }
         if (halves == 2)
 #pragma unroll
@@ -476,6 +487,7 @@ static __global__ void __launch_bounds__(32 * kM2LSmallWarps) m2l_small_kernel(T
 #pragma unroll
             for (int c = 0; c < 3; ++c) Lout[((size_t)cell * 3 + c) * P1 + l] = acc[c];
     }
+    cp_async_wait<0>();
 }
 
 // ------------------------------------------------ M2L in float-float --
@@ -696,6 +708,50 @@ static __global__ void __launch_bounds__(32 * kM2LffWarps) m2l_ff_kernel(TreeVie
 }
 
 // ---------------------------------------------------------------- P2L --
+// Incoming (local) coefficients of one segment piece for a list-4 cell
+// (Eq. 62 for the single layer, Eq. 78/79 for the double layer): a, b the
+// piece's end points relative to the cell centre (unscaled), len its chord
+// length, om its arc weight, iw = 1/w and logw = log w of the cell.  Writes
+// g[0..P1) and, when want_f, f[0..P1).
+template <typename T>
+__device__ __forceinline__ void p2l_piece_coefs(T ax, T ay, T bx, T by, T len, T om, T iw, T w, T logw, int P1,
+                                                bool want_f, typename V2<T>::type *g, typename V2<T>::type *f) {
+    using C = typename V2<T>::type;
+    C a = mk<T>(ax * iw, ay * iw), b = mk<T>(bx * iw, by * iw);   // scaled
+    C wv = mk<T>((bx - ax) / len, (by - ay) / len);
+    // log(b/a) on the continuous branch (|arg| < pi: separated)
+    C d = mk<T>(b.x - a.x, b.y - a.y), s = mk<T>(b.x + a.x, b.y + a.y);
+    T aa = a.x * a.x + a.y * a.y;
+    C lba = mk<T>(T(0.5) * tlog1p((d.x * s.x + d.y * s.y) / aa),
+                  tatan2(a.x * b.y - a.y * b.x, a.x * b.x + a.y * b.y));
+    // l = 0: omega [ l (1 - log a) - conj(w) b w_cell log(b/a) ] and i log(b/a)
+    {
+        C la = mk<T>(T(0.5) * tlog(aa) + logw, tatan2(a.y, a.x));
+        C wb = cmul(mk<T>(wv.x, -wv.y), mk<T>(b.x * w, b.y * w));
+        C t2 = cmul(wb, lba);
+        g[0] = mk<T>(om * (len * (1 - la.x) - t2.x), om * (-len * la.y - t2.y));
+        if (want_f) f[0] = mk<T>(-om * lba.y, om * lba.x);
+    }
+    if (P1 > 1) {
+        C t2 = cmul(mk<T>(wv.x, -wv.y), lba);
+        g[1] = cscl(t2, om * w);
+    }
+    C al = cinv(a), be = cinv(b), ab = cmul(al, be);
+    C iwv = mk<T>(-wv.y, wv.x);                 // i w
+    C fb = cscl(cmul(iwv, ab), om * len * iw);  // F factor, times T_{l-1} / l
+    C gb = cscl(ab, om * len);                  // G factor, times T_{l-2} / (l (l-1))
+    // T_m = sum_j al^j be^(m-j): T_0 = 1, T_m = al T_{m-1} + be^m
+    C Tm = mk<T>(1, 0), bp = mk<T>(1, 0);       // T_0
+    if (P1 > 1 && want_f) f[1] = fb;             // l = 1: T_0 / 1
+    for (int q = 2; q < P1; ++q) {
+        // here Tm = T_{q-2}
+        g[q] = cscl(cmul(gb, Tm), T(1) / (T(q) * (q - 1)));
+        bp = cmul(bp, be);
+        Tm = cadd(cmul(al, Tm), bp);             // T_{q-1}
+        if (want_f) f[q] = cscl(cmul(fb, Tm), T(1) / T(q));
+    }
+}
+
 template <typename T, typename PS>
 __global__ void __launch_bounds__(kChunk) p2l_kernel(TreeView<T> t, PS ps, const int *__restrict__ cells,
                                                      const T *__restrict__ sb, const T *__restrict__ mb,
@@ -734,41 +790,8 @@ __global__ void __launch_bounds__(kChunk) p2l_kernel(TreeView<T> t, PS ps, const
                 int i = p0 + base + tid;
                 T ax, ay, bx, by;
                 ps.rel(i, cell, e, t.x_off, ax, ay, bx, by);
-                C a = mk<T>(ax * iw, ay * iw), b = mk<T>(bx * iw, by * iw);   // scaled
-                T len = t.plen[i], om = t.pw[i];
-                C wv = mk<T>((bx - ax) / len, (by - ay) / len);
-                // log(b/a) on the continuous branch (|arg| < pi: separated)
-                C d = mk<T>(b.x - a.x, b.y - a.y), s = mk<T>(b.x + a.x, b.y + a.y);
-                T aa = a.x * a.x + a.y * a.y;
-                C lba = mk<T>(T(0.5) * tlog1p((d.x * s.x + d.y * s.y) / aa),
-                              tatan2(a.x * b.y - a.y * b.x, a.x * b.x + a.y * b.y));
-                C *g = G + tid * P1, *f = F + tid * P1;
-                // l = 0: omega [ l (1 - log a) - conj(w) b w_cell log(b/a) ] and i log(b/a)
-                {
-                    C la = mk<T>(T(0.5) * tlog(aa) + logw, tatan2(a.y, a.x));
-                    C wb = cmul(mk<T>(wv.x, -wv.y), mk<T>(b.x * w, b.y * w));
-                    C t2 = cmul(wb, lba);
-                    g[0] = mk<T>(om * (len * (1 - la.x) - t2.x), om * (-len * la.y - t2.y));
-                    if (want_f) f[0] = mk<T>(-om * lba.y, om * lba.x);
-                }
-                if (P1 > 1) {
-                    C t2 = cmul(mk<T>(wv.x, -wv.y), lba);
-                    g[1] = cscl(t2, om * w);
-                }
-                C al = cinv(a), be = cinv(b), ab = cmul(al, be);
-                C iwv = mk<T>(-wv.y, wv.x);                 // i w
-                C fb = cscl(cmul(iwv, ab), om * len * iw);  // F factor, times T_{l-1} / l
-                C gb = cscl(ab, om * len);                  // G factor, times T_{l-2} / (l (l-1))
-                // T_m = sum_j al^j be^(m-j): T_0 = 1, T_m = al T_{m-1} + be^m
-                C Tm = mk<T>(1, 0), bp = mk<T>(1, 0);       // T_0
-                if (P1 > 1 && want_f) f[1] = fb;             // l = 1: T_0 / 1
-                for (int q = 2; q < P1; ++q) {
-                    // here Tm = T_{q-2}
-                    g[q] = cscl(cmul(gb, Tm), T(1) / (T(q) * (q - 1)));
-                    bp = cmul(bp, be);
-                    Tm = cadd(cmul(al, Tm), bp);             // T_{q-1}
-                    if (want_f) f[q] = cscl(cmul(fb, Tm), T(1) / T(q));
-                }
+                p2l_piece_coefs<T>(ax, ay, bx, by, t.plen[i], t.pw[i], iw, w, logw, P1, want_f, G + tid * P1,
+                                   F + tid * P1);
                 sg[tid] = t.pseg[i];
             }
             __syncthreads();
@@ -909,6 +932,94 @@ template <typename T> inline size_t walk_smem(int P1, int n_max) {
 template <typename T> inline size_t p2m_smem(int P1) {
     using C = typename V2<T>::type;
     return kChunk * (P1 + 1) * sizeof(C) + kChunk * sizeof(T) + kChunk * sizeof(C) + kChunk * sizeof(int);
+}
+// P2L over a flat list of each cell's list-4 pieces: item[r] = (piece,
+// list-4 entry) for rows r = row_off[cell] .. row_off[cell] + row_cnt[cell],
+// in the row order of the stored coefficients.  Chunks of kChunk pieces span
+// the cell's source leaves, and each piece's densities are staged in shared
+// memory next to its coefficients (recomputed, or read from rows_g / rows_f),
+// so the accumulation reads no global memory.
+template <typename T, typename PS>
+__global__ void __launch_bounds__(kChunk) p2l_flat_kernel(TreeView<T> t, PS ps, const int *__restrict__ cells,
+                                                          const long long *__restrict__ row_off,
+                                                          const int *__restrict__ row_cnt,
+                                                          const int2 *__restrict__ item,
+                                                          const T *__restrict__ sb, const T *__restrict__ mb,
+                                                          int use_s, int use_m, int P1,
+                                                          typename V2<T>::type *__restrict__ Lout,
+                                                          const typename V2<T>::type *__restrict__ rows_g = nullptr,
+                                                          const typename V2<T>::type *__restrict__ rows_f = nullptr) {
+    using C = typename V2<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    C *G = reinterpret_cast<C *>(smem_raw);          // [kChunk][P1] sigma coefficients
+    C *F = G + kChunk * P1;                          // [kChunk][P1] mu coefficients
+    T *D = reinterpret_cast<T *>(F + kChunk * P1);   // [kChunk][6] sigma, mu of the piece's segment
+    const int cell = cells[blockIdx.x];
+    const int tid = threadIdx.x;
+    const int ngrp = kChunk / P1, grp = tid / P1, l = tid - grp * P1;
+    const bool want_f = use_m != 0;
+    const T iw = t.iw[cell], w = 1 / iw, logw = t.logw[cell];
+    C acc[3];
+    for (int c = 0; c < 3; ++c) acc[c] = mk<T>(0, 0);
+    const long long r0 = row_off[cell];
+    const int n = row_cnt[cell];
+    for (int base = 0; base < n; base += kChunk) {
+        const int cnt = min(kChunk, n - base);
+        __syncthreads();
+        if (tid < cnt) {
+            const int2 it = item[r0 + base + tid];
+            const int i = it.x;
+            const size_t seg = (size_t)t.pseg[i];
+            T *dd = D + 6 * tid;
+            for (int c = 0; c < 3; ++c) {
+                dd[c] = use_s ? sb[3 * seg + c] : T(0);
+                dd[3 + c] = use_m ? mb[3 * seg + c] : T(0);
+            }
+            if (!rows_g) {
+                T ax, ay, bx, by;
+                ps.rel(i, cell, it.y, t.x_off, ax, ay, bx, by);
+                p2l_piece_coefs<T>(ax, ay, bx, by, t.plen[i], t.pw[i], iw, w, logw, P1, want_f, G + tid * P1,
+                                   F + tid * P1);
+            }
+        }
+        __syncthreads();
+        if (grp < ngrp) {
+            for (int j = grp; j < cnt; j += ngrp) {
+                C cg, cf = mk<T>(0, 0);
+                if (rows_g) {
+                    const size_t ri = (size_t)(r0 + base + j) * P1 + l;
+                    cg = rows_g[ri];
+                    if (use_m && rows_f) cf = rows_f[ri];
+                } else {
+                    cg = G[j * P1 + l];
+                    if (use_m) cf = F[j * P1 + l];
+                }
+                const T *dd = D + 6 * j;
+                for (int c = 0; c < 3; ++c) {
+                    acc[c].x += dd[c] * cg.x + dd[3 + c] * cf.x;
+                    acc[c].y += dd[c] * cg.y + dd[3 + c] * cf.y;
+                }
+            }
+        }
+    }
+    // the groups' partial sums, added in group order
+    __syncthreads();
+    if (grp < ngrp)
+        for (int c = 0; c < 3; ++c) G[(grp * 3 + c) * P1 + l] = acc[c];
+    __syncthreads();
+    if (tid < P1)
+        for (int c = 0; c < 3; ++c) {
+            C a = G[c * P1 + tid];
+            for (int q = 1; q < ngrp; ++q) a = cadd(a, G[(q * 3 + c) * P1 + tid]);
+            C *o = Lout + ((size_t)cell * 3 + c) * P1 + tid;
+            o->x += a.x;
+            o->y += a.y;
+        }
+}
+
+template <typename T> inline size_t p2l_flat_smem(int P1) {
+    using C = typename V2<T>::type;
+    return 2 * kChunk * P1 * sizeof(C) + 6 * kChunk * sizeof(T);
 }
 template <typename T> inline size_t p2l_smem(int P1) {
     using C = typename V2<T>::type;
