@@ -107,7 +107,7 @@ typedef struct {
                               (0 = min(p, 12))                               */
     double inner_tol;      /* DC_FORM_FMM32: floor of the inner GMRES
                               tolerance per refinement step, in (0, 1)
-                              (0 = 1e-4)                                     */
+                              (0 = 3e-5)                                     */
 } dc_options;
 
 typedef struct {

@@ -334,6 +334,19 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
     }
     DC_CK(ctx, ctx->pfeat.build(G, s), "panel features");
     ctx->warm_a1_valid = false;
+    {   // G_H 1, once per drawing: the first residual of the paper's start
+        // x0 = 1 and the learned start's least-residual projection use it
+        const int N = ctx->dg.N;
+        const double zero[3] = {0, 0, 0}, one[3] = {1, 1, 1};
+        DC_CK(ctx, ctx->warm_ax.ensure(size_t(3) * N), "alloc G_H 1");
+        DC_CK(ctx, ctx->warm_a1.ensure(size_t(3) * N), "alloc G_H 1");
+        DC_CK(ctx, dc::vec_combine3(ctx->warm_ax.ptr, nullptr, ctx->warm_ax.ptr, N, zero, one, s), "G_H 1");
+        if (ctx->opt.form == DC_FORM_DENSE64)
+            DC_CK(ctx, dc::launch_dense_gemv(ctx->AG.ptr, N, ctx->warm_ax.ptr, ctx->warm_a1.ptr, s), "G_H 1");
+        else
+            DC_CK(ctx, ctx->fmm->apply_single_layer(ctx->warm_ax.ptr, ctx->warm_a1.ptr, s), "G_H 1");
+        ctx->warm_a1_valid = true;
+    }
     DC_CK(ctx, cudaStreamSynchronize(s), "build_tree");
     ctx->state = 1;
     return DC_OK;
@@ -362,12 +375,7 @@ dc_status warm_start(dc_ctx *ctx, dc_solve_stats *stats) {
         if (ctx->opt.form == DC_FORM_DENSE64) return dc::launch_dense_gemv(ctx->AG.ptr, N, x, y, s);
         return ctx->fmm->apply_single_layer(x, y, s);
     };
-    if (!ctx->warm_a1_valid) {          // G_H 1, once per drawing
-        const double zero[3] = {0, 0, 0}, one[3] = {1, 1, 1};
-        DC_CK(ctx, dc::vec_combine3(ctx->b.ptr, nullptr, ctx->warm_ax.ptr, N, zero, one, s), "warm start");
-        DC_CK(ctx, apply(ctx->warm_ax.ptr, ctx->warm_a1.ptr), "warm start");
-        ctx->warm_a1_valid = true;
-    }
+    if (!ctx->warm_a1_valid) return fail(ctx, DC_ERR_STATE, "solve_density: G_H 1 missing");
     DC_CK(ctx, apply(ctx->sigma.ptr, ctx->warm_ax.ptr), "warm start");
     double pp[3], p1[3], q1[3], pb[3], qb[3], bb[3];
     const double *Ap = ctx->warm_ax.ptr, *A1 = ctx->warm_a1.ptr, *b = ctx->b.ptr;
@@ -396,6 +404,8 @@ dc_status warm_start(dc_ctx *ctx, dc_solve_stats *stats) {
         if (stats) stats->warm_resid[c] = bb[c] > 0.0 ? std::sqrt(r2 / bb[c]) : 0.0;
     }
     DC_CK(ctx, dc::vec_combine3(ctx->sigma.ptr, nullptr, ctx->sigma.ptr, N, al, be, s), "warm start");
+    // G_H x0 = alpha G_H sigma_p + beta G_H 1, for the first residual
+    DC_CK(ctx, dc::vec_combine3(ctx->warm_ax.ptr, ctx->warm_a1.ptr, ctx->warm_ax.ptr, N, al, be, s), "warm start");
     if (stats) stats->used_warm = mask;
     return DC_OK;
 }
@@ -445,12 +455,14 @@ dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats)
         if (stats)
             stats->ms_warm =
                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
-    } else {
-        std::vector<double> ones(size_t(3) * N, 1.0);
-        DC_CK(ctx, cudaMemcpyAsync(ctx->sigma.ptr, ones.data(), n3b, cudaMemcpyHostToDevice, s),
-              "x0");
-        DC_CK(ctx, cudaStreamSynchronize(s), "x0");
+    } else {   // the paper's x0 = 1
+        const double zero[3] = {0, 0, 0}, one[3] = {1, 1, 1};
+        DC_CK(ctx, dc::vec_combine3(ctx->sigma.ptr, nullptr, ctx->sigma.ptr, N, zero, one, s), "x0");
     }
+    // G_H x0 where it is known without an operator application
+    const double *Ax0 = nullptr;
+    if (ctx->opt.x0_mode == DC_X0_ONES && ctx->warm_a1_valid) Ax0 = ctx->warm_a1.ptr;
+    if (ctx->opt.x0_mode == DC_X0_LEARNED) Ax0 = ctx->warm_ax.ptr;
     ctx->seg_density_valid = false;
     dc::GmresResult gr;
     std::string msg;
@@ -460,10 +472,10 @@ dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats)
         DenseOp op;
         op.A = ctx->AG.ptr;
         op.N = N;
-        ce = dc::gmres_solve(ctx->gw, op, N, ctx->b.ptr, ctx->sigma.ptr, false, ctx->opt.gmres_tol,
+        ce = dc::gmres_solve(ctx->gw, op, N, ctx->b.ptr, ctx->sigma.ptr, false, false, ctx->opt.gmres_tol,
                              ctx->opt.gmres_restart, ctx->opt.gmres_max_iter, s, gr, msg);
     } else {
-        ce = ctx->fmm->solve(ctx->gw, ctx->b.ptr, ctx->sigma.ptr, ctx->opt, s, gr, msg, &n_refine);
+        ce = ctx->fmm->solve(ctx->gw, ctx->b.ptr, ctx->sigma.ptr, ctx->opt, s, gr, msg, &n_refine, Ax0);
     }
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, msg.empty() ? "gmres" : msg.c_str());
     DC_CK(ctx, cudaStreamSynchronize(s), "gmres");

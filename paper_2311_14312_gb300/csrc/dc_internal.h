@@ -207,9 +207,11 @@ void gmres_work_destroy(GmresWork *w);
 // classical Gram-Schmidt with one re-orthogonalisation pass, Givens
 // rotations and the least-squares update on the device.  x holds x0 on
 // entry and the solution on exit; x0_zero: x is zero on entry (the first
-// residual is b, no operator application).
+// residual is b, no operator application); trust_estimate: stop as soon as
+// a cycle's Givens residual estimate meets tol (the caller checks the true
+// residual itself), rel_resid then holds the estimate.
 cudaError_t gmres_solve(GmresWork *w, Operator &A, int N, const double *b, double *x, bool x0_zero,
-                        double tol, int restart, int max_iter, cudaStream_t st,
+                        bool trust_estimate, double tol, int restart, int max_iter, cudaStream_t st,
                         GmresResult &res, std::string &err);
 
 // Allocation-free FP64 direct sum at points (noalloc.cu): segment densities
@@ -224,7 +226,8 @@ cudaError_t vec_residual(const double *b, const double *Ax, double *r, int n3, c
 cudaError_t vec_axpy(double *x, const double *d, int n3, cudaStream_t st);
 // zero the channels c with keep[c] == 0
 cudaError_t vec_mask3(double *v, int N, const int keep[3], cudaStream_t st);
-// y[:, c] = a[c] x[:, c] + b[c] z[:, c] (z == nullptr: a vector of ones); y may alias x
+// y[:, c] = a[c] x[:, c] + b[c] z[:, c] (z == nullptr: a vector of ones; a[c] == 0:
+// x[:, c] is not read); y may alias x
 cudaError_t vec_combine3(const double *x, const double *z, double *y, int N, const double a[3],
                          const double b[3], cudaStream_t st);
 // host_out[c] = u[:, c] . v[:, c] (synchronises the stream)

@@ -329,8 +329,8 @@ static __global__ void __launch_bounds__(32 * kWarps) far_coef_kernel(NodeArgs<d
 }
 
 // Far field from stored coefficients into the lane sums: lanes split the
-// (block, k) terms; each term's three expansion coefficients are loaded once
-// and applied to all of the warp's targets.
+// (block, k) terms; in FP32 each term's three expansion coefficients are
+// loaded once and applied to all of the warp's targets.
 template <typename T>
 __device__ __forceinline__ void far_rows_into(const NodeArgs<T> &a, const typename passes::V2<T>::type *__restrict__ cf,
                                               long long base, int leaf, int nt, int warp, int lane,
@@ -340,6 +340,25 @@ __device__ __forceinline__ void far_rows_into(const NodeArgs<T> &a, const typena
     const int w0 = a.w_ptr[leaf], nb = 1 + a.w_ptr[leaf + 1] - w0;
     const int nterm = nb * P1;
     const C *rows = cf + base;
+    if (sizeof(T) == 8) {   // FP64: one target at a time (fewer registers)
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int tl = warp + kWarps * j;
+            if (tl >= nt) break;
+            const C *row = rows + (long long)tl * nterm;
+            for (int u = lane; u < nterm; u += 32) {
+                const int b = u / P1, k = u - b * P1;
+                const int src = b == 0 ? leaf : a.w_idx[w0 + b - 1];
+                const C *X = (b == 0 ? a.L : a.M) + (size_t)src * 3 * P1 + k;
+                const C co = row[u];
+                const C x0 = X[0], x1 = X[P1], x2 = X[2 * P1];
+                acc[j][0] += co.x * x0.x - co.y * x0.y;
+                acc[j][1] += co.x * x1.x - co.y * x1.y;
+                acc[j][2] += co.x * x2.x - co.y * x2.y;
+            }
+        }
+        return;
+    }
 #pragma unroll 2
     for (int u = lane; u < nterm; u += 32) {
         const int b = u / P1, k = u - b * P1;
@@ -364,10 +383,11 @@ __device__ __forceinline__ void far_rows_into(const NodeArgs<T> &a, const typena
 // Node operator with the near field from stored coefficients (near_coef_kernel
 // layout): y = sum_pl coef * dens[seg(pl)] + far field (L2P, list-3 M2P),
 // the far field from stored coefficients too when far != nullptr.  Lanes
-// walk the leaf's list-1 pieces kBatch at a time, issuing every load of a
-// batch (segment numbers, coefficients, then densities) before the first
+// walk the leaf's list-1 pieces four at a time (FP32; one at a time in
+// FP64, whose registers allow no more), issuing every load of a batch
+// (segment numbers, coefficients, then densities) before the first
 // multiply-add, so that a warp keeps several requests in flight.
-constexpr int kBatch = 4;
+template <typename T> struct NearBatch { static constexpr int value = 4; };
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 8 : 4) near_apply_kernel(NodeArgs<T> a, const long long *__restrict__ off,
@@ -381,14 +401,31 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 8 : 4) near_appl
     T acc[kPer][3];
 #pragma unroll
     for (int j = 0; j < kPer; ++j) acc[j][0] = acc[j][1] = acc[j][2] = T(0);
-    if (warp < nt) {
+    if (warp < nt && sizeof(T) == 8) {   // FP64: one piece at a time per lane
         const T *rows = coef + off[blockIdx.x];
         const int *segs = a.uf_seg + a.uf_ptr[leaf];
-        for (int p0 = 0; p0 < nU; p0 += 32 * kBatch) {
-            int sg[kBatch];
-            T cv[kBatch][kPer];
+        for (int pl = lane; pl < nU; pl += 32) {
+            const size_t o = 3 * (size_t)segs[pl];
+            const T d0 = dens[o], d1 = dens[o + 1], d2 = dens[o + 2];
 #pragma unroll
-            for (int i = 0; i < kBatch; ++i) {
+            for (int j = 0; j < kPer; ++j) {
+                const int tl = warp + kWarps * j;
+                if (tl >= nt) break;
+                const T cfv = rows[(long long)tl * nU + pl];
+                acc[j][0] += cfv * d0;
+                acc[j][1] += cfv * d1;
+                acc[j][2] += cfv * d2;
+            }
+        }
+    } else if (warp < nt) {
+        const T *rows = coef + off[blockIdx.x];
+        const int *segs = a.uf_seg + a.uf_ptr[leaf];
+        constexpr int kB = NearBatch<T>::value;
+        for (int p0 = 0; p0 < nU; p0 += 32 * kB) {
+            int sg[kB];
+            T cv[kB][kPer];
+#pragma unroll
+            for (int i = 0; i < kB; ++i) {
                 const int pl = p0 + lane + 32 * i;
                 sg[i] = pl < nU ? segs[pl] : -1;
 #pragma unroll
@@ -397,9 +434,9 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 8 : 4) near_appl
                     cv[i][j] = (pl < nU && tl < nt) ? rows[(long long)tl * nU + pl] : T(0);
                 }
             }
-            T d[kBatch][3];
+            T d[kB][3];
 #pragma unroll
-            for (int i = 0; i < kBatch; ++i) {
+            for (int i = 0; i < kB; ++i) {
                 const bool ok = sg[i] >= 0;
                 const size_t o = 3 * (size_t)(ok ? sg[i] : 0);
                 d[i][0] = ok ? dens[o] : T(0);
@@ -407,7 +444,7 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 8 : 4) near_appl
                 d[i][2] = ok ? dens[o + 2] : T(0);
             }
 #pragma unroll
-            for (int i = 0; i < kBatch; ++i)
+            for (int i = 0; i < kB; ++i)
 #pragma unroll
                 for (int j = 0; j < kPer; ++j) {
                     acc[j][0] += cv[i][j] * d[i][0];

@@ -337,7 +337,8 @@ cudaError_t Fmm::Impl::passes(const double *sb, const double *mb, int use_s, int
     for (int l = tree.depth - 1; l >= 2; --l) {
         const int lo = m2m_ptr[l], n = m2m_ptr[l + 1] - lo;
         if (n <= 0) continue;
-        passes::m2m_ff_kernel<<<(n + 3) / 4, 128, 0, st>>>(child0.ptr, m2m_cells.ptr + lo, n, P1, m2mff.ptr, M.ptr);
+        passes::m2m_ff_kernel<<<(n + 3) / 4, 128, passes::mlff_smem(P1), st>>>(child0.ptr, m2m_cells.ptr + lo, n, P1,
+                                                                            m2mff.ptr, M.ptr);
         note_launch();
     }
     if (sc.n_m2l > 0) {
@@ -1009,6 +1010,8 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passes::p2m_smem<double>(I.P1));
     cudaFuncSetAttribute(passes::p2l_flat_kernel<double, passes::PiecesF64>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passes::p2l_flat_smem<double>(I.P1));
+    cudaFuncSetAttribute(passes::m2m_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)passes::mlff_smem(I.P1));
     if ((e = I.build_rows(st)) != cudaSuccess) {
         err = std::string("stored P2M / P2L coefficients: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
@@ -1075,7 +1078,8 @@ struct PrecOp : Operator {
 }  // namespace
 
 cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_options &opt,
-                       cudaStream_t st, GmresResult &res, std::string &err, int *n_refine) {
+                       cudaStream_t st, GmresResult &res, std::string &err, int *n_refine,
+                       const double *Ax0) {
     // Iterative refinement around right-preconditioned GMRES:
     //   r = b - A x            (FP64 FMM operator)
     //   z = GMRES(A' M, 0, r, tol')      A' = FP64 or FP32 FMM operator,
@@ -1098,9 +1102,13 @@ cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_option
     if (n_refine) *n_refine = 0;
     for (int outer = 0; outer <= max_outer; ++outer) {
         if (n_refine) *n_refine = outer;
-        if ((e = I.apply_nodes(x, I.ir_t.ptr, true, st)) != cudaSuccess) return e;
-        res.n_matvec++;
-        if ((e = vec_residual(b, I.ir_t.ptr, I.ir_r.ptr, 3 * N, st)) != cudaSuccess) return e;
+        const double *Ax = Ax0;
+        if (outer > 0 || !Ax0) {
+            if ((e = I.apply_nodes(x, I.ir_t.ptr, true, st)) != cudaSuccess) return e;
+            res.n_matvec++;
+            Ax = I.ir_t.ptr;
+        }
+        if ((e = vec_residual(b, Ax, I.ir_r.ptr, 3 * N, st)) != cudaSuccess) return e;
         if ((e = vec_norms3(w, I.ir_r.ptr, N, rn, st)) != cudaSuccess) return e;
         int mask[3], any = 0;
         double need = 1.0;
@@ -1117,11 +1125,11 @@ cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_option
         if (outer == max_outer || used >= opt.gmres_max_iter) break;
         if ((e = vec_mask3(I.ir_r.ptr, N, mask, st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(I.ir_d.ptr, 0, sizeof(double) * 3 * N, st)) != cudaSuccess) return e;
-        const double floor32 = opt.inner_tol > 0.0 ? opt.inner_tol : 1e-4;
+        const double floor32 = opt.inner_tol > 0.0 ? opt.inner_tol : 3e-5;
         double inner_tol = I.fp32 ? std::max(floor32, need) : std::max(0.5 * need, 1e-15);
         GmresResult inner;
         op.fp32 = I.fp32;
-        e = gmres_solve(w, op, N, I.ir_r.ptr, I.ir_d.ptr, true, inner_tol, opt.gmres_restart,
+        e = gmres_solve(w, op, N, I.ir_r.ptr, I.ir_d.ptr, true, true, inner_tol, opt.gmres_restart,
                         opt.gmres_max_iter - used, st, inner, err);
         if (e != cudaSuccess) return e;
         int mx = 0;

@@ -29,9 +29,12 @@ public:
     // The FP32 operator without the preconditioner, y = G_H x.
     cudaError_t apply_inner_raw(const double *x, double *y, cudaStream_t st);
     // GMRES with this operator (Alg. 3 line 5); x holds x0 on entry.
-    // n_refine: outer refinement steps taken.
+    // n_refine: outer refinement steps taken.  Ax0: G_H x0 when the caller
+    // has it (the first residual then needs no operator application), else
+    // nullptr.
     cudaError_t solve(GmresWork *w, const double *b, double *x, const dc_options &opt,
-                      cudaStream_t st, GmresResult &res, std::string &err, int *n_refine = nullptr);
+                      cudaStream_t st, GmresResult &res, std::string &err, int *n_refine = nullptr,
+                      const double *Ax0 = nullptr);
     // Forms the expansions of segment densities sbar and mbar (Alg. 8 up and
     // down passes); render_grid / eval_points then evaluate them.
     cudaError_t prepare_eval(const double *sbar, const double *mbar, cudaStream_t st);

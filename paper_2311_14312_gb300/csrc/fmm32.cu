@@ -630,7 +630,8 @@ cudaError_t Fmm::Impl::passes32(const float *sb, const float *mb, int use_s, int
             pair_geo.ptr, mchunks.ptr, n_mchunks, pair_leaf.ptr, P1, binom32.ptr, M32i.ptr, mpart32.ptr);
         note_launch();
         if (n_mred > 0) {
-            passes::m2m_reduce_kernel<float><<<(n_mred + 3) / 4, 128, 0, st>>>(mred.ptr, n_mred, P1, mpart32.ptr, M32i.ptr);
+            passes::m2m_reduce_kernel<float><<<n_mred, passes::kReduceThreads, 0, st>>>(mred.ptr, n_mred, P1, mpart32.ptr,
+                                                                                     M32i.ptr);
             note_launch();
         }
     }

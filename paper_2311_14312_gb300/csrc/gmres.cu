@@ -24,7 +24,7 @@ namespace dc {
 
 namespace {
 
-constexpr int kChunk = 4096;     // rows per partial dot-product block
+constexpr int kChunk = 1024;     // rows per partial dot-product block
 constexpr int kDotThreads = 256;
 constexpr int kPollRing = 4;     // pinned flag slots / events
 constexpr int kPollLag = 1;      // iterations between enqueue and flag read
@@ -58,6 +58,52 @@ __global__ void dots_partial_kernel(const double *__restrict__ V, size_t vstride
         partial[((size_t)j * nchunk + chunk) * 3 + threadIdx.x] = red[threadIdx.x][0];
 }
 
+// One Gram-Schmidt pass's dot products h_j = V_j . w for j < nj, fused
+// with their finalisation: block (chunk, j) writes its partial sums, and the
+// last block of column j to finish (counted in count[j], which it resets)
+// adds the partials in chunk order into hpass[j] and the Hessenberg column
+// hcol[j] (= hpass on the first pass, += on the second).  Deterministic.
+__global__ void __launch_bounds__(kDotThreads) gs_dots_kernel(const double *__restrict__ V, size_t vstride,
+                                                              const double *__restrict__ w, int N, int nchunk,
+                                                              double *__restrict__ partial,
+                                                              unsigned *__restrict__ count,
+                                                              double *__restrict__ hpass, double *__restrict__ hcol,
+                                                              int first) {
+    const int chunk = blockIdx.x, j = blockIdx.y;
+    const double *v = V + (size_t)j * vstride;
+    const int lo = chunk * kChunk, hi = min(N, lo + kChunk);
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int i = lo + threadIdx.x; i < hi; i += kDotThreads)
+        for (int c = 0; c < 3; ++c) a[c] += v[3 * (size_t)i + c] * w[3 * (size_t)i + c];
+    __shared__ double red[kDotThreads / 32][3];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int c = 0; c < 3; ++c)
+        for (int off = 16; off > 0; off >>= 1) a[c] += __shfl_xor_sync(0xffffffffu, a[c], off);
+    if (lane == 0)
+        for (int c = 0; c < 3; ++c) red[wp][c] = a[c];
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int q = 0; q < kDotThreads / 32; ++q) t += red[q][threadIdx.x];
+        partial[((size_t)j * nchunk + chunk) * 3 + threadIdx.x] = t;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&count[j], 1u) == (unsigned)(nchunk - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < 3) {
+        const int c = threadIdx.x;
+        double t = 0.0;
+        for (int ch = 0; ch < nchunk; ++ch) t += __ldcg(partial + ((size_t)j * nchunk + ch) * 3 + c);
+        hpass[3 * j + c] = t;
+        hcol[3 * j + c] = first ? t : hcol[3 * j + c] + t;
+    }
+    if (threadIdx.x == 0) count[j] = 0u;
+}
+
 // h[j][c] (= or +=) sum_chunk partial
 __global__ void dots_finalize_kernel(const double *__restrict__ partial, int nchunk, int nj,
                                      double *__restrict__ h, int accumulate) {
@@ -67,19 +113,6 @@ __global__ void dots_finalize_kernel(const double *__restrict__ partial, int nch
     double s = 0.0;
     for (int ch = 0; ch < nchunk; ++ch) s += partial[((size_t)j * nchunk + ch) * 3 + c];
     h[t] = accumulate ? h[t] + s : s;
-}
-
-// One Gram-Schmidt pass's coefficients: hpass = sum_chunk partial, and the
-// Hessenberg column hcol = hpass (first pass) or hcol + hpass (second).
-__global__ void dots_finalize2_kernel(const double *__restrict__ partial, int nchunk, int nj,
-                                      double *__restrict__ hpass, double *__restrict__ hcol, int first) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nj * 3) return;
-    int j = t / 3, c = t - 3 * j;
-    double s = 0.0;
-    for (int ch = 0; ch < nchunk; ++ch) s += partial[((size_t)j * nchunk + ch) * 3 + c];
-    hpass[t] = s;
-    hcol[t] = first ? s : hcol[t] + s;
 }
 
 // nrm[c] = sqrt(sum_chunk partial) (the norms of one [N][3] vector)
@@ -314,6 +347,7 @@ struct GmresWork {
     DevBuf<double> V, w, r, Ax, partial, hcol, hpass, hnext, small, npart;
     DevBuf<double> R, cs, sn, e, y;
     DevBuf<int> flags;
+    DevBuf<unsigned> count;   // [m + 1] blocks done per column (gs_dots_kernel), kept at zero
     double *host = nullptr;   // pinned: resid[3], active-as-double[3], norms[3]
     int *poll = nullptr;      // pinned [kPollRing][3] copies of the active flags
     cudaEvent_t ev[kPollRing] = {};
@@ -337,6 +371,7 @@ struct GmresWork {
         DC_TRY(r.alloc((size_t)N * 3));
         DC_TRY(Ax.alloc((size_t)N * 3));
         DC_TRY(partial.alloc((size_t)(m + 1) * nchunk * 3));
+        DC_TRY(count.alloc((size_t)(m + 1)));
         DC_TRY(npart.alloc((size_t)3 * ((3 * (size_t)N + kOrthThreads - 1) / kOrthThreads)));
         DC_TRY(hcol.alloc((size_t)(m + 1) * 3));
         DC_TRY(hpass.alloc((size_t)(m + 1) * 3));
@@ -383,7 +418,8 @@ __global__ void combine3_kernel(const double *x, const double *z, double *y, int
     if (t >= n3) return;
     int c = t % 3;
     double a = c == 0 ? a0 : (c == 1 ? a1 : a2), b = c == 0 ? b0 : (c == 1 ? b1 : b2);
-    y[t] = a * x[t] + b * (z ? z[t] : 1.0);
+    // a = 0 ignores x (it may hold anything, even non-finite values)
+    y[t] = (a != 0.0 ? a * x[t] : 0.0) + b * (z ? z[t] : 1.0);
 }
 __global__ void mask3_kernel(double *__restrict__ v, int n3, int k0, int k1, int k2) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -463,7 +499,8 @@ cudaError_t vec_dots3(GmresWork *Wp, const double *u, const double *v, int N, do
     return cudaStreamSynchronize(st);
 }
 
-cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, double *x, bool x0_zero, double tol,
+cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, double *x, bool x0_zero, bool trust_estimate,
+                        double tol,
                         int restart, int max_iter, cudaStream_t st, GmresResult &res,
                         std::string &err) {
     GmresWork &W = *Wp;
@@ -477,6 +514,9 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
     }
     const size_t vs = (size_t)N * 3;
     const int th = 256;
+    // the column counters of gs_dots_kernel start at zero (each last block
+    // resets its own; this guards against a launch that failed midway)
+    if ((ce = cudaMemsetAsync(W.count.ptr, 0, W.count.bytes(), st)) != cudaSuccess) return ce;
     GivensState gs = W.gs();
     double *bnorm = W.small.ptr;        // [3]
     double *thr = W.small.ptr + 3;      // [3]
@@ -551,11 +591,9 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
             // CGS2: two passes of h = V^T w, w -= V h
             for (int pass = 0; pass < 2; ++pass) {
                 dim3 grid(W.nchunk, k + 1);
-                dots_partial_kernel<<<grid, kDotThreads, 0, st>>>(W.V.ptr, vs, W.w.ptr, N,
-                                                                  W.nchunk, W.partial.ptr); note_launch();
-                int t3 = (k + 1) * 3;
-                dots_finalize2_kernel<<<(t3 + 127) / 128, 128, 0, st>>>(W.partial.ptr, W.nchunk, k + 1,
-                                                                       W.hpass.ptr, W.hcol.ptr, pass == 0); note_launch();
+                gs_dots_kernel<<<grid, kDotThreads, 0, st>>>(W.V.ptr, vs, W.w.ptr, N, W.nchunk, W.partial.ptr,
+                                                             W.count.ptr, W.hpass.ptr, W.hcol.ptr, pass == 0);
+                note_launch();
                 if (pass == 0) {
                     orth_update_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.V.ptr, vs, W.hpass.ptr,
                                                                               k + 1, W.w.ptr, N); note_launch();
@@ -601,6 +639,18 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
             return ce;
         if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return ce;
         for (int c = 0; c < 3; ++c) res.iters[c] += hkc[c];
+        if (est_done && trust_estimate) {
+            // the caller recomputes the residual with its own (more exact)
+            // operator: stop at the Givens estimate
+            double hres[3];
+            if ((ce = cudaMemcpyAsync(hres, gs.resid, 3 * sizeof(double), cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess)
+                return ce;
+            if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return ce;
+            for (int c = 0; c < 3; ++c) res.rel_resid[c] = hb[c] > 0 ? hres[c] / hb[c] : 0.0;
+            done_all = true;
+            break;
+        }
     }
     res.converged = done_all ? 1 : 0;
     return cudaGetLastError();

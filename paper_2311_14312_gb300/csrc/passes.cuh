@@ -262,10 +262,13 @@ __global__ void __launch_bounds__(32 * kLevelWarps) m2m_kernel(const int *__rest
 //   Mt_anc[k] += sum_{j <= k} C(k, j) d^(k - j) rho^j Mt_leaf[j].
 // No level waits for another (each leaf moment is translated once per
 // ancestor instead of through the chain of parents).  One warp per chunk of
-// up to kMultiLeaves (ancestor, leaf) pairs, lane k holds coefficient k; a
-// chunk writes the ancestor's expansion when it is the cell's only chunk,
-// else a partial sum that m2m_reduce_kernel adds up in chunk order.
-constexpr int kMultiLeaves = 8;
+// up to kMultiLeaves (ancestor, leaf) pairs; a chunk writes the ancestor's
+// expansion when it is the cell's only chunk, else a partial sum that
+// m2m_reduce_kernel adds up in chunk order.  For P1 <= 16 the half-warps
+// take alternate pairs (lane k + 16 h holds coefficient k of pair 2 i + h)
+// and are added at the end; above 16 lane k holds coefficient k of every
+// pair.  The binomial table is staged in shared memory.
+constexpr int kMultiLeaves = 16;
 constexpr int kMultiWarps = 4;
 
 template <typename T>
@@ -278,26 +281,33 @@ __global__ void __launch_bounds__(32 * kMultiWarps) m2m_multi_kernel(const float
     using C = typename V2<T>::type;
     __shared__ C zp[kMultiWarps][32];
     __shared__ T rp[kMultiWarps][32];
-    __shared__ C ms[kMultiWarps][96];
+    __shared__ C ms[kMultiWarps][2][96];
+    __shared__ T sbin[32 * 32];
+    for (int i = threadIdx.x; i < P1 * 32; i += blockDim.x) sbin[i] = binom[i];
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ci = blockIdx.x * kMultiWarps + warp;
     if (ci >= n_chunks) return;
     const int4 ch = chunks[ci];          // (ancestor, first pair, pairs, partial slot or -1)
     const int anc = ch.x;
+    const int halves = P1 <= 16 ? 2 : 1;
+    const int span = 32 / halves;                       // lanes per pair
+    const int h = halves == 2 ? lane >> 4 : 0, k = lane - h * span;
     C acc[3];
     for (int c = 0; c < 3; ++c) acc[c] = mk<T>(0, 0);
     const int nM = 3 * P1;
-    for (int e = ch.y; e < ch.y + ch.z; ++e) {
-        const int leaf = pair_leaf[e];
-        // d^lane and rho^lane by binary powering (5 squarings); the pair's
-        // shift d and scale rho were formed once per drawing
-        const float4 geo = pair_geo[e];
+    for (int e0 = ch.y; e0 < ch.y + ch.z; e0 += halves) {
+        const int e = e0 + h;
+        const bool has = e < ch.y + ch.z;
+        // d^k and rho^k by binary powering (the pair's shift d and scale rho
+        // were formed once per drawing)
+        const float4 geo = has ? pair_geo[e] : make_float4(0.f, 0.f, 0.f, 0.f);
         const C d = mk<T>((T)geo.x, (T)geo.y);
         const T rho = (T)geo.z;
         C pz = mk<T>(1, 0), bz = d;
         T pr = 1, br = rho;
         for (int bit = 1; bit < 32; bit <<= 1) {
-            if (lane & bit) {
+            if (k & bit) {
                 pz = cmul(pz, bz);
                 pr *= br;
             }
@@ -305,41 +315,63 @@ __global__ void __launch_bounds__(32 * kMultiWarps) m2m_multi_kernel(const float
             br *= br;
         }
         __syncwarp();
-        zp[warp][lane] = pz;
+        zp[warp][lane] = pz;                         // [h][k] = lane
         rp[warp][lane] = pr;
-        const C *src = M + (size_t)leaf * nM;
-        for (int i = lane; i < nM; i += 32) ms[warp][i] = src[i];
+        if (has) {
+            const C *src = M + (size_t)pair_leaf[e] * nM;
+            for (int i = k; i < nM; i += span) ms[warp][h][i] = src[i];
+        }
         __syncwarp();
-        if (lane < P1) {
-            const int k = lane;
-            const T *bk = binom + k * 32;
+        if (has && k < P1) {
+            const T *bk = sbin + k * 32;
+            const C *z = zp[warp] + h * span;
+            const T *r = rp[warp] + h * span;
+            const C *m = ms[warp][h];
             for (int j = 0; j <= k; ++j) {
-                const C co = cscl(zp[warp][k - j], bk[j] * rp[warp][j]);
-                for (int c = 0; c < 3; ++c) cfma(acc[c], co, ms[warp][c * P1 + j]);
+                const C co = cscl(z[k - j], bk[j] * r[j]);
+                for (int c = 0; c < 3; ++c) cfma(acc[c], co, m[c * P1 + j]);
             }
         }
     }
-    if (lane < P1) {
+    if (halves == 2)
+        for (int c = 0; c < 3; ++c) {
+            acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, 16);
+            acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, 16);
+        }
+    if (h == 0 && k < P1) {
         C *dst = ch.w < 0 ? M + (size_t)anc * nM : partial + (size_t)ch.w * nM;
-        for (int c = 0; c < 3; ++c) dst[c * P1 + lane] = acc[c];
+        for (int c = 0; c < 3; ++c) dst[c * P1 + k] = acc[c];
     }
 }
 
 // Cells whose leaves span several chunks: M = sum of the chunk partials in
-// chunk order (deterministic).  red = (cell, first slot, slots).
+// chunk order (deterministic).  red = (cell, first slot, slots).  One block
+// per cell: slice s of the kReduceThreads / (3 P1) slices sums the slots
+// s, s + S, ... of every coefficient, and the slices are added in order.
+constexpr int kReduceThreads = 256;
+
 template <typename T>
-__global__ void m2m_reduce_kernel(const int4 *__restrict__ red, int n, int P1,
-                                  const typename V2<T>::type *__restrict__ partial,
-                                  typename V2<T>::type *__restrict__ M) {
+__global__ void __launch_bounds__(kReduceThreads) m2m_reduce_kernel(const int4 *__restrict__ red, int n, int P1,
+                                                                    const typename V2<T>::type *__restrict__ partial,
+                                                                    typename V2<T>::type *__restrict__ M) {
     using C = typename V2<T>::type;
-    const int i = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (i >= n) return;
-    const int4 r = red[i];
+    __shared__ C part[kReduceThreads];
+    const int4 r = red[blockIdx.x];
     const int nM = 3 * P1;
-    for (int t = lane; t < nM; t += 32) {
+    const int S = kReduceThreads / nM;
+    const int s = threadIdx.x / nM, i = threadIdx.x - s * nM;
+    if (s < S) {
         C a = mk<T>(0, 0);
-        for (int q = 0; q < r.z; ++q) a = cadd(a, partial[(size_t)(r.y + q) * nM + t]);
-        M[(size_t)r.x * nM + t] = a;
+        const C *p = partial + (size_t)r.y * nM + i;
+#pragma unroll 4
+        for (int q = s; q < r.z; q += S) a = cadd(a, p[(size_t)q * nM]);
+        part[s * nM + i] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < nM) {
+        C a = part[threadIdx.x];
+        for (int q = 1; q < S; ++q) a = cadd(a, part[q * nM + threadIdx.x]);
+        M[(size_t)r.x * nM + threadIdx.x] = a;
     }
 }
 
@@ -439,10 +471,18 @@ static __global__ void __launch_bounds__(32 * kM2LSmallWarps) m2l_small_kernel(T
     const int nM = 3 * P1;
     float2 *buf = stage + warp * kM2LDepth * 64;
     const float2 zero = make_float2(0.f, 0.f);
+    // the first 32 entries of the list (source, symmetry code) are loaded
+    // up front, one per lane, and passed around by shuffles
+    int my_src = 0, my_code = 0;
+    auto entry_src = [&](int e, int e0) {
+        const int r = e - e0;
+        const int v = __shfl_sync(0xffffffffu, my_src, r & 31);
+        return r < 32 ? v : t.v_idx[e];
+    };
     // copy the moments of list-2 entry e into ring slot (e - e0) mod depth
-    auto issue = [&](int e, int e0) {
+    auto issue = [&](int e, int e0, int src) {
         float2 *dst = buf + ((e - e0) % kM2LDepth) * 64;
-        const float2 *ms = M + (size_t)t.v_idx[e] * nM;
+        const float2 *ms = M + (size_t)src * nM;
         if (lane < nM) cp_async8(dst + lane, ms + lane);
         if (lane + 32 < nM) cp_async8(dst + lane + 32, ms + lane + 32);
     };
@@ -451,20 +491,27 @@ static __global__ void __launch_bounds__(32 * kM2LSmallWarps) m2l_small_kernel(T
         const float mlogw = -t.logw[cell];
         float2 acc[3] = {zero, zero, zero};
         const int e0 = t.v_ptr[cell], e1 = t.v_ptr[cell + 1];
+        if (e0 + lane < e1) {
+            my_src = t.v_idx[e0 + lane];
+            my_code = t.v_code[e0 + lane];
+        }
 #pragma unroll
         for (int d = 0; d < kM2LDepth - 1; ++d) {
-            if (e0 + d < e1) issue(e0 + d, e0);
+            if (e0 + d < e1) issue(e0 + d, e0, entry_src(e0 + d, e0));   // warp-uniform branch
             cp_async_commit();
         }
         for (int e = e0; e < e1; ++e) {
             // the slot refilled here was read in the previous iteration,
             // which ended with __syncwarp
-            if (e + kM2LDepth - 1 < e1) issue(e + kM2LDepth - 1, e0);
+            const int en = e + kM2LDepth - 1;
+            if (en < e1) issue(en, e0, entry_src(en, e0));             // warp-uniform branch
             cp_async_commit();
+            const int re = e - e0;
+            const int cv = __shfl_sync(0xffffffffu, my_code, re & 31);
+            const int code = re < 32 ? cv : t.v_code[e];
             cp_async_wait<kM2LDepth - 1>();        // entry e has landed (own copies)
             __syncwarp();                           // and every lane's copies are visible
             const float2 *cur = buf + ((e - e0) % kM2LDepth) * 64;
-            const int code = t.v_code[e];
             const int b = code & 7, r = (code >> 3) & 3, cj = code >> 5;
             const float2 *Tl = Tf + ((size_t)(b + 7 * r + 28 * cj) * P1 + lr) * P1;
             for (int k = h; k < P1; k += halves) {
@@ -560,34 +607,73 @@ __device__ __forceinline__ float4 ff_conj(float4 v) { return make_float4(v.x, -v
 // cell, lane k holds coefficient k; the FP64 inputs (children's moments, the
 // parent's local expansion) are converted once per cell into shared memory,
 // so the inner loops run on the FP32 pipes only.
+// M2M lanes: coefficient k and P1 - 1 - k share a lane (k + 1 and P1 - k
+// terms, P1 + 1 together), and the two half-warps take children 0, 1 and
+// 2, 3, so 2 ceil(P1 / 2) lanes carry equal loads; the halves' sums are
+// added at the end.  The four quadrant tables are staged in shared memory.
+__device__ __forceinline__ float4 ff_shfl_xor(float4 v, int m) {
+    return make_float4(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m),
+                       __shfl_xor_sync(0xffffffffu, v.z, m), __shfl_xor_sync(0xffffffffu, v.w, m));
+}
+
+__device__ __forceinline__ double2 ff_to_double(float4 a) {
+    return make_double2((double)a.x + (double)a.z, (double)a.y + (double)a.w);
+}
+
+// shared memory of m2m_ff_kernel: the four quadrant tables and each warp's
+// staged children
+inline size_t mlff_smem(int P1) { return (4 * (size_t)P1 * P1 + 4 * 4 * 3 * (size_t)P1) * sizeof(float4); }
+
 static __global__ void __launch_bounds__(128) m2m_ff_kernel(const int *__restrict__ child0,
                                                             const int *__restrict__ cells, int n, int P1,
                                                             const float4 *__restrict__ tab,
                                                             double2 *__restrict__ M) {
-    __shared__ float4 sm[4][4 * 3 * 32];
-    const int w = threadIdx.x >> 5, k = threadIdx.x & 31;
-    const int idx = blockIdx.x * 4 + w;
-    if (idx >= n) return;
-    const int cell = cells[idx];
-    const int ch0 = child0[cell];
+    extern __shared__ unsigned char smem_raw[];
+    float4 *tabs = reinterpret_cast<float4 *>(smem_raw);   // [4][P1][P1]
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nM = 3 * P1;
-    const double2 *src = M + (size_t)ch0 * nM;          // the 4 children are contiguous
-    for (int i = k; i < 4 * nM; i += 32) sm[w][i] = ff_from(src[i]);
-    __syncwarp();
-    if (k >= P1) return;
-    float4 acc[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
-                     make_float4(0.f, 0.f, 0.f, 0.f)};
-    for (int q = 0; q < 4; ++q) {
-        const float4 *Tq = tab + ((size_t)q * P1 + k) * P1;
-        const float4 *mq = sm[w] + q * nM;
-        for (int j = 0; j <= k; ++j) {
-            const float4 tq = Tq[j];
-            for (int c = 0; c < 3; ++c) ff_cfma(acc[c], tq, mq[c * P1 + j]);
-        }
+    float4 *smw = tabs + 4 * P1 * P1 + w * 4 * nM;          // this warp's 4 children
+    for (int i = threadIdx.x; i < 4 * P1 * P1; i += blockDim.x) tabs[i] = tab[i];
+    const int idx = blockIdx.x * 4 + w;
+    const bool live = idx < n;
+    const int cell = live ? cells[idx] : 0;
+    if (live) {
+        const double2 *src = M + (size_t)child0[cell] * nM;   // the 4 children are contiguous
+        for (int i = lane; i < 4 * nM; i += 32) smw[i] = ff_from(src[i]);
     }
-    for (int c = 0; c < 3; ++c)
-        M[((size_t)cell * 3 + c) * P1 + k] =
-            make_double2((double)acc[c].x + (double)acc[c].z, (double)acc[c].y + (double)acc[c].w);
+    __syncthreads();
+    if (!live) return;
+    tab = tabs;
+    const int kk = lane & 15, h = lane >> 4;
+    const int k1 = kk, k2 = P1 - 1 - kk;
+    const bool on = k1 <= k2, two = k1 < k2;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 a1[3] = {z, z, z}, a2[3] = {z, z, z};
+    if (on)
+        for (int q = 2 * h; q < 2 * h + 2; ++q) {
+            const float4 *mq = smw + q * nM;
+            const float4 *T1 = tab + ((size_t)q * P1 + k1) * P1;
+            for (int j = 0; j <= k1; ++j) {
+                const float4 tq = T1[j];
+                for (int c = 0; c < 3; ++c) ff_cfma(a1[c], tq, mq[c * P1 + j]);
+            }
+            if (two) {
+                const float4 *T2 = tab + ((size_t)q * P1 + k2) * P1;
+                for (int j = 0; j <= k2; ++j) {
+                    const float4 tq = T2[j];
+                    for (int c = 0; c < 3; ++c) ff_cfma(a2[c], tq, mq[c * P1 + j]);
+                }
+            }
+        }
+    for (int c = 0; c < 3; ++c) {
+        ff_cadd(a1[c], ff_shfl_xor(a1[c], 16));
+        ff_cadd(a2[c], ff_shfl_xor(a2[c], 16));
+    }
+    if (h != 0 || !on) return;
+    for (int c = 0; c < 3; ++c) {
+        M[((size_t)cell * 3 + c) * P1 + k1] = ff_to_double(a1[c]);
+        if (two) M[((size_t)cell * 3 + c) * P1 + k2] = ff_to_double(a2[c]);
+    }
 }
 
 static __global__ void __launch_bounds__(128) l2l_ff_kernel(TreeView<double> t, const int *__restrict__ cells, int n,
@@ -871,8 +957,10 @@ __global__ void __launch_bounds__(32 * kLevelWarps) l2l_kernel(TreeView<T> t, co
 // ancestors: L = Lm2l(a_2) at the level-2 ancestor, then L = Lm2l(a) +
 // L2L(L) for each ancestor a below it and the leaf itself (the level-invariant
 // table of the child's quadrant).  Inner cells get no expansion: only leaves
-// hold targets.  One block per leaf, thread l holds coefficient l of the
-// three channels; blockDim >= P1.
+// hold targets.  One block per leaf (blockDim >= P1, a multiple of 32); the
+// chain's Lm2l is staged in shared memory up front.  For P1 <= 16 lane l + 16 h sums the terms k = l + h, l + h + 2, ...
+// of coefficient l and the halves are added by a shuffle; above 16 thread l
+// sums all k >= l.
 constexpr int kWalkMax = 48;    // ancestors kept (tree depth <= 40)
 
 template <typename T>
@@ -883,44 +971,56 @@ __global__ void walk_kernel(TreeView<T> t, const int *__restrict__ leaves, const
     using C = typename V2<T>::type;
     extern __shared__ unsigned char smem_raw[];
     C *cur = reinterpret_cast<C *>(smem_raw);   // [3][P1]
-    C *pre = cur + 3 * P1;                       // [n][3][P1]: the chain's Lm2l, loaded up front
+    C *pre = cur + 3 * P1;                       // [n][3][P1]: the chain's Lm2l
     __shared__ int chain[kWalkMax], quad[kWalkMax];
     __shared__ int n_chain;
     const int leaf = leaves[blockIdx.x];
-    const int l = threadIdx.x;
+    const int tid = threadIdx.x;
     // chains[blockIdx.x * (n_max + 1)]: length, then the leaf and its
     // ancestors down to level 2 (formed once per drawing)
     const int *ch = chains + (size_t)blockIdx.x * (n_max + 1);
-    if (l == 0) n_chain = ch[0];
-    if (l < n_max) {
-        const int c = ch[1 + l];
-        chain[l] = c;
-        quad[l] = c >= 0 ? t.quad[c] : 0;
+    if (tid == 0) n_chain = ch[0];
+    if (tid < n_max) {
+        const int c = ch[1 + tid];
+        chain[tid] = c;
+        quad[tid] = c >= 0 ? t.quad[c] : 0;
     }
     __syncthreads();
     const int n = n_chain;
-    if (l < P1)
-        for (int i = 0; i < n; ++i)
-            for (int c = 0; c < 3; ++c) pre[(i * 3 + c) * P1 + l] = Lm2l[((size_t)chain[i] * 3 + c) * P1 + l];
+    const int nM = 3 * P1;
+    for (int i = tid; i < n * nM; i += blockDim.x) {
+        const int a = i / nM;
+        pre[i] = Lm2l[(size_t)chain[a] * nM + (i - a * nM)];
+    }
+    __syncthreads();
+    const int halves = P1 <= 16 ? 2 : 1;
+    const int l = halves == 2 ? (tid & 31 & 15) + (tid >> 5) * 32 : tid;
+    const int h = halves == 2 ? ((tid & 31) >> 4) : 0;
+    const bool on = l < P1;
     C acc[3];
     for (int c = 0; c < 3; ++c) acc[c] = mk<T>(0, 0);
-    if (n > 0 && l < P1)
+    if (n > 0 && on && h == 0)
         for (int c = 0; c < 3; ++c) acc[c] = pre[((n - 1) * 3 + c) * P1 + l];
     for (int i = n - 2; i >= 0; --i) {
         __syncthreads();
-        if (l < P1)
+        if (on && h == 0)
             for (int c = 0; c < 3; ++c) cur[c * P1 + l] = acc[c];
         __syncthreads();
-        if (l < P1) {
-            for (int c = 0; c < 3; ++c) acc[c] = pre[(i * 3 + c) * P1 + l];
+        for (int c = 0; c < 3; ++c) acc[c] = (on && h == 0) ? pre[(i * 3 + c) * P1 + l] : mk<T>(0, 0);
+        if (on) {
             const C *Tq = tab + ((size_t)quad[i] * P1 + l) * P1;
-            for (int k = l; k < P1; ++k) {
-                C tq = Tq[k];
-                for (int c = 0; c < 3; ++c) cfma(acc[c], tq, cur[c * P1 + k]);
+            for (int k = l + h; k < P1; k += halves) {
+                const C tk = Tq[k];
+                for (int c = 0; c < 3; ++c) cfma(acc[c], tk, cur[c * P1 + k]);
             }
         }
+        if (halves == 2)
+            for (int c = 0; c < 3; ++c) {
+                acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, 16);
+                acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, 16);
+            }
     }
-    if (l < P1)
+    if (on && h == 0)
         for (int c = 0; c < 3; ++c) L[((size_t)leaf * 3 + c) * P1 + l] = acc[c];
 }
 
