@@ -142,7 +142,8 @@ __global__ void heavy_kernel(const double *__restrict__ sb, const double *__rest
 }
 
 // -------------------------------------------------------------- eval --
-constexpr int kEvThreads = 256;
+constexpr int kEvThreads = kEvalTile * kEvalTile;
+constexpr int kEvBlocksPerSM = 512 / kEvThreads;   // register budget of up to 128 per thread
 constexpr int kStage = 256;
 
 struct EvalArgs32 {
@@ -181,7 +182,7 @@ __device__ __forceinline__ void split2(double v, float &hi, float &lo) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kEvThreads, 2) eval32_kernel(EvalArgs32 a) {
+__global__ void __launch_bounds__(kEvThreads, kEvBlocksPerSM) eval32_kernel(EvalArgs32 a) {
     // staged pieces of one list-1 leaf, in the target leaf's frame, each
     // coordinate as a (hi, lo) float pair so differences keep full accuracy
     __shared__ float sx1h[kStage], sx1l[kStage], sy1h[kStage], sy1l[kStage];

@@ -51,6 +51,13 @@ struct Tile {
     int leaf, r0, c0, nr, nc, vp;   // vp: viewport index (pixel tiles)
 };
 
+// Pixel tiles of the render: kEvalTile x kEvalTile pixels of one leaf per
+// block of the evaluation kernel, one thread per pixel.
+#ifndef DC_EVAL_TILE
+#define DC_EVAL_TILE 8
+#endif
+constexpr int kEvalTile = DC_EVAL_TILE;
+
 // Cells that need incoming expansions for one set of targets (all cells for
 // pixels; the cells above the nodes for the matvec), by pass.
 struct Schedule {
@@ -173,6 +180,12 @@ struct Fmm::Impl {
     cudaGraphExec_t g32_exec = nullptr;
     int g32_kernels = 0;
     DevBuf<double> g_in, g_out;
+    // the render's tile plan (tiles, vps) for the viewports plan_vps
+    bool plan_valid = false;
+    std::vector<VpDev> plan_vps;
+    int plan_tiles = 0;
+    long long plan_pairs = 0, plan_m2p = 0;
+    double plan_flops = 0.0;
     cudaError_t graph_matvec32(const double *x, double *y, cudaStream_t st);
     ~Impl() {
         if (ev0) cudaEventDestroy(ev0);

@@ -2,9 +2,11 @@
 // (Sec. 5.5: x = GMRES(f, x0, y, eps) with the FMM or dense operator as f).
 //
 // Each channel has its own Krylov space; vectors are [N][3] FP64 with the
-// channel fastest.  Arnoldi uses classical Gram-Schmidt with one
-// re-orthogonalisation pass (two dot-product sweeps instead of k sequential
-// ones, same stability as modified Gram-Schmidt in practice); Givens
+// channel fastest.  Arnoldi uses classical Gram-Schmidt with a second
+// (re-orthogonalisation) pass when the first one cancelled more than a
+// factor 1/sqrt(2) of the vector's norm in some channel (the DGKS
+// criterion; the flag is set and read on the device, so a skipped pass costs
+// three empty launches); Givens
 // rotations, the residual estimate and the triangular solve run on the
 // device.  Reductions are two-stage with a fixed order, so results are
 // bit-reproducible.  The host learns of convergence from per-channel flags
@@ -68,7 +70,8 @@ __global__ void __launch_bounds__(kDotThreads) gs_dots_kernel(const double *__re
                                                               double *__restrict__ partial,
                                                               unsigned *__restrict__ count,
                                                               double *__restrict__ hpass, double *__restrict__ hcol,
-                                                              int first) {
+                                                              int first, const int *__restrict__ skip) {
+    if (skip && *skip) return;   // a second pass that is not needed
     const int chunk = blockIdx.x, j = blockIdx.y;
     const double *v = V + (size_t)j * vstride;
     const int lo = chunk * kChunk, hi = min(N, lo + kChunk);
@@ -124,41 +127,24 @@ __global__ void norm_finalize_kernel(const double *__restrict__ partial, int nch
     nrm[c] = sqrt(fmax(s, 0.0));
 }
 
-// w[i][c] -= sum_{j < nj} h[j][c] V_j[i][c], one thread per element (t = 3 i + c)
-__global__ void orth_update_kernel(const double *__restrict__ V, size_t vstride,
-                                   const double *__restrict__ h, int nj, double *__restrict__ w,
-                                   int N) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 3 * N) return;
-    const int c = t % 3;
-    double a = w[t];
-    int j = 0;
-    for (; j + 4 <= nj; j += 4) {
-        const double v0 = V[(size_t)j * vstride + t], v1 = V[(size_t)(j + 1) * vstride + t];
-        const double v2 = V[(size_t)(j + 2) * vstride + t], v3 = V[(size_t)(j + 3) * vstride + t];
-        a -= h[3 * j + c] * v0;
-        a -= h[3 * (j + 1) + c] * v1;
-        a -= h[3 * (j + 2) + c] * v2;
-        a -= h[3 * (j + 3) + c] * v3;
-    }
-    for (; j < nj; ++j) a -= h[3 * j + c] * V[(size_t)j * vstride + t];
-    w[t] = a;
-}
-
-// The same update for the last Gram-Schmidt pass, with the squares of the
-// result summed per block and channel (blocks of kOrthThreads = 3 x 64
-// elements, so an element's channel is its index mod 3): npart[block][c].
+// The same update with the squares of the result summed per block and
+// channel, and (before != 0) those of w before the update too (blocks of
+// kOrthThreads = 3 x 64 elements, so an element's channel is its index mod
+// 3): npart[block][c] after, npart[block][3 + c] before.  skip: a second
+// pass that is not needed returns at once.
 constexpr int kOrthThreads = 192;
 __global__ void __launch_bounds__(kOrthThreads) orth_update_norm_kernel(const double *__restrict__ V, size_t vstride,
                                                                          const double *__restrict__ h, int nj,
                                                                          double *__restrict__ w, int N,
-                                                                         double *__restrict__ npart) {
-    __shared__ double sq[kOrthThreads];
+                                                                         double *__restrict__ npart, int before,
+                                                                         const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    __shared__ double sq[2][kOrthThreads];
     const int t = blockIdx.x * kOrthThreads + threadIdx.x;
-    double a = 0.0;
+    double a = 0.0, a0 = 0.0;
     if (t < 3 * N) {
         const int c = t % 3;
-        a = w[t];
+        a = a0 = w[t];
         int j = 0;
         for (; j + 4 <= nj; j += 4) {
             const double v0 = V[(size_t)j * vstride + t], v1 = V[(size_t)(j + 1) * vstride + t];
@@ -171,24 +157,48 @@ __global__ void __launch_bounds__(kOrthThreads) orth_update_norm_kernel(const do
         for (; j < nj; ++j) a -= h[3 * j + c] * V[(size_t)j * vstride + t];
         w[t] = a;
     }
-    sq[threadIdx.x] = a * a;
+    sq[0][threadIdx.x] = a * a;
+    sq[1][threadIdx.x] = a0 * a0;
     __syncthreads();
     if (threadIdx.x < 3) {
-        double s = 0.0;
-        for (int u = threadIdx.x; u < kOrthThreads; u += 3) s += sq[u];
-        npart[3 * blockIdx.x + threadIdx.x] = s;
+        double s = 0.0, s0 = 0.0;
+        for (int u = threadIdx.x; u < kOrthThreads; u += 3) {
+            s += sq[0][u];
+            s0 += sq[1][u];
+        }
+        npart[6 * blockIdx.x + threadIdx.x] = s;
+        if (before) npart[6 * blockIdx.x + 3 + threadIdx.x] = s0;
     }
 }
 
 // nrm[c] = sqrt(sum over the blocks of npart[block][c]): warp c sums its
-// channel (lanes over blocks, then a fixed butterfly)
-__global__ void npart_finalize_kernel(const double *__restrict__ npart, int nb, double *__restrict__ nrm) {
+// channel (lanes over blocks, then a fixed butterfly).  skip_out (first
+// pass): set when no channel lost more than a factor 1/sqrt(2) of its norm
+// in the projection, so that the second pass is not needed (the criterion
+// of Daniel, Gragg, Kaufman and Stewart); skip_in: a skipped second pass
+// leaves nrm as it is.
+__global__ void npart_finalize_kernel(const double *__restrict__ npart, int nb, double *__restrict__ nrm,
+                                      int *__restrict__ skip_out, const int *__restrict__ skip_in) {
+    if (skip_in && *skip_in) return;
+    __shared__ int keep[3];
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (c >= 3) return;
-    double s = 0.0;
-    for (int b = lane; b < nb; b += 32) s += npart[3 * b + c];
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) nrm[c] = sqrt(fmax(s, 0.0));
+    if (c < 3) {
+        double s = 0.0, s0 = 0.0;
+        for (int b = lane; b < nb; b += 32) {
+            s += npart[6 * b + c];
+            if (skip_out) s0 += npart[6 * b + 3 + c];
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, off);
+            s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+        }
+        if (lane == 0) {
+            nrm[c] = sqrt(fmax(s, 0.0));
+            keep[c] = s >= 0.5 * s0;
+        }
+    }
+    __syncthreads();
+    if (skip_out && threadIdx.x == 0) *skip_out = keep[0] && keep[1] && keep[2];
 }
 
 // out[i][c] = in[i][c] * (nrm[c] > 0 ? 1 / nrm[c] : 0)
@@ -372,7 +382,7 @@ struct GmresWork {
         DC_TRY(Ax.alloc((size_t)N * 3));
         DC_TRY(partial.alloc((size_t)(m + 1) * nchunk * 3));
         DC_TRY(count.alloc((size_t)(m + 1)));
-        DC_TRY(npart.alloc((size_t)3 * ((3 * (size_t)N + kOrthThreads - 1) / kOrthThreads)));
+        DC_TRY(npart.alloc((size_t)6 * ((3 * (size_t)N + kOrthThreads - 1) / kOrthThreads)));
         DC_TRY(hcol.alloc((size_t)(m + 1) * 3));
         DC_TRY(hpass.alloc((size_t)(m + 1) * 3));
         DC_TRY(hnext.alloc(3));
@@ -589,20 +599,24 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
             if ((ce = A.apply(vk, W.w.ptr, st)) != cudaSuccess) return ce;
             res.n_matvec++;
             // CGS2: two passes of h = V^T w, w -= V h
+            // classical Gram-Schmidt, h = V^T w, w -= V h, and h_{k+1,k} =
+            // ||w|| per channel; the second pass runs only when the first
+            // one cancelled too much of w (its kernels read the flag)
+            int *skip = W.flags.ptr + 6;   // after active[3], kc[3]
             for (int pass = 0; pass < 2; ++pass) {
                 dim3 grid(W.nchunk, k + 1);
                 gs_dots_kernel<<<grid, kDotThreads, 0, st>>>(W.V.ptr, vs, W.w.ptr, N, W.nchunk, W.partial.ptr,
-                                                             W.count.ptr, W.hpass.ptr, W.hcol.ptr, pass == 0);
+                                                             W.count.ptr, W.hpass.ptr, W.hcol.ptr, pass == 0,
+                                                             pass == 0 ? nullptr : skip);
                 note_launch();
-                if (pass == 0) {
-                    orth_update_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.V.ptr, vs, W.hpass.ptr,
-                                                                              k + 1, W.w.ptr, N); note_launch();
-                } else {   // and h_{k+1,k} = ||w|| per channel
-                    const int nb = (3 * N + kOrthThreads - 1) / kOrthThreads;
-                    orth_update_norm_kernel<<<nb, kOrthThreads, 0, st>>>(W.V.ptr, vs, W.hpass.ptr, k + 1,
-                                                                         W.w.ptr, N, W.npart.ptr); note_launch();
-                    npart_finalize_kernel<<<1, 96, 0, st>>>(W.npart.ptr, nb, W.hnext.ptr); note_launch();
-                }
+                const int nb = (3 * N + kOrthThreads - 1) / kOrthThreads;
+                orth_update_norm_kernel<<<nb, kOrthThreads, 0, st>>>(W.V.ptr, vs, W.hpass.ptr, k + 1, W.w.ptr, N,
+                                                                     W.npart.ptr, pass == 0,
+                                                                     pass == 0 ? nullptr : skip);
+                note_launch();
+                npart_finalize_kernel<<<1, 96, 0, st>>>(W.npart.ptr, nb, W.hnext.ptr, pass == 0 ? skip : nullptr,
+                                                        pass == 0 ? nullptr : skip);
+                note_launch();
             }
             scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.w.ptr, W.hnext.ptr,
                                                                W.V.ptr + (size_t)(k + 1) * vs, N); note_launch();

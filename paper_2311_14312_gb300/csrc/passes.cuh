@@ -453,6 +453,28 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+template <typename V> __device__ __forceinline__ void cp_async_any(V *smem, const V *gmem) {
+    if (sizeof(V) == 16) cp_async16(smem, gmem);
+    else cp_async8(smem, gmem);
+}
+
+// dst[i] = src[i] for i < n (shared <- global), thread t of a block of
+// `stride` threads, by asynchronous copies so that every element is in
+// flight at once; the caller then runs cp_async_commit(), cp_async_wait<0>()
+// and __syncthreads().  Elements of 8 or 16 bytes, both arrays aligned.
+template <typename V>
+__device__ __forceinline__ void stage_async(V *dst, const V *src, int n, int t, int stride) {
+    static_assert(sizeof(V) == 8 || sizeof(V) == 16, "8- or 16-byte elements");
+    for (int i = t; i < n; i += stride) {
+        if (sizeof(V) == 16) cp_async16(dst + i, src + i);
+        else cp_async8(dst + i, src + i);
+    }
+}
 
 static __global__ void __launch_bounds__(32 * kM2LSmallWarps) m2l_small_kernel(TreeView<float> t, const int *__restrict__ cells,
                                                                                int n_cells, int P1,
@@ -462,7 +484,9 @@ static __global__ void __launch_bounds__(32 * kM2LSmallWarps) m2l_small_kernel(T
     extern __shared__ unsigned char smem_raw[];
     float2 *Tf = reinterpret_cast<float2 *>(smem_raw);            // [56][P1][P1]
     float2 *stage = Tf + 56 * P1 * P1;                            // [warps][kM2LDepth][64]
-    for (int i = threadIdx.x; i < 56 * P1 * P1; i += blockDim.x) Tf[i] = full[i];
+    stage_async(Tf, full, 56 * P1 * P1, threadIdx.x, blockDim.x);
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int halves = P1 <= 16 ? 2 : 1;
@@ -633,14 +657,29 @@ static __global__ void __launch_bounds__(128) m2m_ff_kernel(const int *__restric
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nM = 3 * P1;
     float4 *smw = tabs + 4 * P1 * P1 + w * 4 * nM;          // this warp's 4 children
-    for (int i = threadIdx.x; i < 4 * P1 * P1; i += blockDim.x) tabs[i] = tab[i];
+    stage_async(tabs, tab, 4 * P1 * P1, threadIdx.x, blockDim.x);
+    cp_async_commit();
     const int idx = blockIdx.x * 4 + w;
     const bool live = idx < n;
     const int cell = live ? cells[idx] : 0;
     if (live) {
         const double2 *src = M + (size_t)child0[cell] * nM;   // the 4 children are contiguous
-        for (int i = lane; i < 4 * nM; i += 32) smw[i] = ff_from(src[i]);
+        // four loads in flight per lane, then the conversions
+        for (int i0 = lane; i0 < 4 * nM; i0 += 4 * 32) {
+            double2 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + 32 * u;
+                v[u] = i < 4 * nM ? src[i] : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + 32 * u;
+                if (i < 4 * nM) smw[i] = ff_from(v[u]);
+            }
+        }
     }
+    cp_async_wait<0>();
     __syncthreads();
     if (!live) return;
     tab = tabs;
@@ -725,7 +764,9 @@ static __global__ void __launch_bounds__(32 * kM2LffWarps) m2l_ff_kernel(TreeVie
     extern __shared__ unsigned char smem_raw[];
     float4 *B = reinterpret_cast<float4 *>(smem_raw);                 // [7][P1][P1]
     float4 *stage = B + 7 * P1 * P1;                                  // [warps][2][3 * 32]
-    for (int i = threadIdx.x; i < 7 * P1 * P1; i += blockDim.x) B[i] = base[i];
+    stage_async(B, base, 7 * P1 * P1, threadIdx.x, blockDim.x);
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nM = 3 * P1;
@@ -990,8 +1031,10 @@ __global__ void walk_kernel(TreeView<T> t, const int *__restrict__ leaves, const
     const int nM = 3 * P1;
     for (int i = tid; i < n * nM; i += blockDim.x) {
         const int a = i / nM;
-        pre[i] = Lm2l[(size_t)chain[a] * nM + (i - a * nM)];
+        if (sizeof(C) == 8 || sizeof(C) == 16) cp_async_any(pre + i, Lm2l + (size_t)chain[a] * nM + (i - a * nM));
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     const int halves = P1 <= 16 ? 2 : 1;
     const int l = halves == 2 ? (tid & 31 & 15) + (tid >> 5) * 32 : tid;
