@@ -108,7 +108,16 @@ typedef struct {
     double inner_tol;      /* DC_FORM_FMM32: floor of the inner GMRES
                               tolerance per refinement step, in (0, 1)
                               (0 = 3e-5)                                     */
+    int m2l_engine;        /* DC_FORM_FMM32: M2L of the inner operator on
+                              DC_M2L_TENSOR (tcgen05 TF32 with a three-term
+                              split; p_inner <= 15, else CUDA cores) or
+                              DC_M2L_CUDA_CORES                              */
 } dc_options;
+
+enum {
+    DC_M2L_TENSOR = 0,
+    DC_M2L_CUDA_CORES = 1
+};
 
 typedef struct {
     int n_curves, n_panels, n_nodes, n_segments;
@@ -159,7 +168,8 @@ typedef struct {
 
 /* Fills *opt with defaults: DC_FORM_FMM32, g 16, s 80, p 24, leaf 64,
  * depth 30, tol 1e-10, restart 200, max_iter 2000, x0 ones, domain [0,1]^2,
- * p_inner 0 and inner_tol 0 (the built-in choices). */
+ * p_inner 0 and inner_tol 0 (the built-in choices), m2l_engine
+ * DC_M2L_TENSOR. */
 dc_status dc_default_options(dc_options *opt);
 
 /* Creates a context bound to the current CUDA device.  *out is set to NULL

@@ -31,6 +31,7 @@ DC_FORM_DENSE64, DC_FORM_FMM64, DC_FORM_FMM32 = 0, 1, 2
 DC_X0_ONES, DC_X0_ZEROS, DC_X0_USER, DC_X0_LEARNED = 0, 1, 2, 3
 DC_MEM_DEVICE, DC_MEM_HOST = 0, 1
 DC_F32, DC_F64 = 0, 1
+DC_M2L_TENSOR, DC_M2L_CUDA_CORES = 0, 1
 
 FORMS = {"dense64": DC_FORM_DENSE64, "fmm64": DC_FORM_FMM64, "fmm32": DC_FORM_FMM32}
 
@@ -41,7 +42,7 @@ class dc_options(ctypes.Structure):
                 ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
                 ("gmres_max_iter", ctypes.c_int), ("x0_mode", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("domain", ctypes.c_double * 4),
-                ("p_inner", ctypes.c_int), ("inner_tol", ctypes.c_double)]
+                ("p_inner", ctypes.c_int), ("inner_tol", ctypes.c_double), ("m2l_engine", ctypes.c_int)]
 
 
 class dc_sizes(ctypes.Structure):

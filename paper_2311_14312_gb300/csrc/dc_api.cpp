@@ -110,6 +110,10 @@ dc_status check_options(const dc_options &o, std::string &msg) {
         msg = "options: p_inner must be 0 (default) or in [1, p]";
         return DC_ERR_ARG;
     }
+    if (o.m2l_engine != DC_M2L_TENSOR && o.m2l_engine != DC_M2L_CUDA_CORES) {
+        msg = "options: m2l_engine must be DC_M2L_TENSOR or DC_M2L_CUDA_CORES";
+        return DC_ERR_ARG;
+    }
     if (!(o.inner_tol >= 0.0 && o.inner_tol < 1.0)) {
         msg = "options: inner_tol must be 0 (default) or in (0, 1)";
         return DC_ERR_ARG;

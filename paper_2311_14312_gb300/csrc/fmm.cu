@@ -28,6 +28,7 @@
 #include "evalnodes.cuh"
 #include "fmm_impl.h"
 #include "passes.cuh"
+#include "passes_tc.cuh"
 #include "segint.cuh"
 
 namespace dc {
@@ -831,6 +832,50 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
                             fulli[((size_t)(b + 7 * r + 28 * cj) * Q + l) * Q + k] = v * ipow[(r * (k + l)) & 3];
                         }
     }
+    // tensor-core M2L of the inner operator (p_i <= 15): G_v = the realified
+    // F_v as TF32 hi / lo tiles in the canonical K-major layout, and the list-2
+    // entries of the node schedule grouped by variant into tiles of up to
+    // kTcPairs pairs
+    std::vector<float> tc_tab;
+    std::vector<int> tc_entries;
+    std::vector<int4> tc_tiles;
+    if (I.fp32 && I.P1i <= passes::kTcMaxP1 && opt.m2l_engine == DC_M2L_TENSOR) {
+        const int Q = I.P1i;
+        auto tf32 = [](float x) {   // round to nearest (ties away) at 10 mantissa bits
+            uint32_t u;
+            std::memcpy(&u, &x, 4);
+            if ((u & 0x7F800000u) != 0x7F800000u) u = (u + 0x1000u) & 0xFFFFE000u;
+            float r;
+            std::memcpy(&r, &u, 4);
+            return r;
+        };
+        tc_tab.assign((size_t)56 * 2 * 32 * passes::kTcK, 0.f);
+        for (int v = 0; v < 56; ++v)
+            for (int l = 0; l < Q; ++l)
+                for (int k = 0; k < Q; ++k) {
+                    const cd F = fulli[((size_t)v * Q + l) * Q + k];
+                    const double g[2][2] = {{F.real(), -F.imag()}, {F.imag(), F.real()}};
+                    for (int a = 0; a < 2; ++a)
+                        for (int b = 0; b < 2; ++b) {
+                            const float gf = (float)g[a][b], hi = tf32(gf), lo = tf32(gf - hi);
+                            const size_t o = (size_t)passes::tc_offset(2 * l + a, 2 * k + b) / 4;
+                            tc_tab[(size_t)v * 2 * 32 * passes::kTcK + o] = hi;
+                            tc_tab[(size_t)v * 2 * 32 * passes::kTcK + 32 * passes::kTcK + o] = lo;
+                        }
+                }
+        std::vector<std::vector<int>> byv(56);
+        for (int c : nm2l)
+            for (int e = T.v_ptr[c]; e < T.v_ptr[c + 1]; ++e) {
+                const int code = vcode[e];
+                byv[(code & 7) + 7 * ((code >> 3) & 3) + 28 * (code >> 5)].push_back(e);
+            }
+        for (int v = 0; v < 56; ++v) {
+            const int first = int(tc_entries.size()), n = int(byv[v].size());
+            tc_entries.insert(tc_entries.end(), byv[v].begin(), byv[v].end());
+            for (int i = 0; i < n; i += passes::kTcPairs)
+                tc_tiles.push_back(make_int4(v, first + i, std::min(passes::kTcPairs, n - i), 0));
+        }
+    }
     auto to_ff = [](const std::vector<cd> &v) {   // float-float: hi, then the rest
         std::vector<float4> f(v.size());
         for (size_t i = 0; i < v.size(); ++i) {
@@ -945,6 +990,17 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     UP(I.sched_all.p2l, ap2l);
     UP(I.sched_nodes.m2l, nm2l);
     UP(I.sched_nodes.p2l, np2l);
+    if (!tc_tiles.empty()) {
+        UP(I.tc_tab, tc_tab);
+        UP(I.tc_entries, tc_entries);
+        UP(I.tc_tiles, tc_tiles);
+        I.n_tc_tiles = int(tc_tiles.size());
+        if ((e = I.tc_y.alloc(T.v_idx.size() * 3 * 2 * (size_t)I.P1i)) != cudaSuccess ||
+            (e = I.tc_err.alloc(1)) != cudaSuccess || (e = cudaMemsetAsync(I.tc_err.ptr, 0, sizeof(int), st)) != cudaSuccess) {
+            err = std::string("fmm allocation: ") + cudaGetErrorString(e);
+            return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
+        }
+    }
 #undef UP
     if ((e = upload_cd(I.m2m, m2m, st)) != cudaSuccess || (e = upload_cd(I.l2l, l2l, st)) != cudaSuccess ||
         (e = upload_cd(I.m2l, m2l, st)) != cudaSuccess || (e = I.M.alloc((size_t)nC * 3 * I.P1)) != cudaSuccess ||
@@ -1143,6 +1199,16 @@ cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_option
             cudaSuccess)
             return e;
         if ((e = vec_axpy(x, I.ir_t.ptr, 3 * N, st)) != cudaSuccess) return e;
+    }
+    if (I.tc_err.ptr) {   // the tensor-core M2L reports MMAs that did not complete in time
+        int flag = 0;
+        if ((e = cudaMemcpyAsync(&flag, I.tc_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return e;
+        if (flag) {
+            err = "tensor-core M2L: the MMAs did not complete within the wait limit";
+            return cudaErrorLaunchTimeout;
+        }
     }
     return cudaGetLastError();
 }

@@ -19,6 +19,7 @@
 
 #include "evalnodes.cuh"
 #include "ffarith.cuh"
+#include "passes_tc.cuh"
 #include "fmm_impl.h"
 #include "segint.cuh"
 
@@ -636,7 +637,14 @@ cudaError_t Fmm::Impl::passes32(const float *sb, const float *mb, int use_s, int
             note_launch();
         }
     }
-    if (sc.n_m2l > 0 && P1 <= passes::kM2LSmallP1) {
+    if (sc.n_m2l > 0 && n_tc_tiles > 0 && &sc == &sched_nodes) {   // tensor cores
+        passes::m2l_tc_kernel<<<std::min(n_tc_tiles, passes::kTcBlocksPerSM * n_sms), passes::kTcThreads, 0, st>>>(
+            tc_tiles.ptr, n_tc_tiles, tc_entries.ptr, tv.v_idx, P1, tc_tab.ptr, M32i.ptr, tc_y.ptr, tc_err.ptr);
+        passes::m2l_tc_reduce_kernel<<<(sc.n_m2l + passes::kTcReduceWarps - 1) / passes::kTcReduceWarps,
+                                       32 * passes::kTcReduceWarps, 0, st>>>(tv, sc.m2l.ptr, sc.n_m2l, P1,
+                                                                             tc_y.ptr, M32i.ptr, Lm2l32i.ptr);
+        note_launch(2);
+    } else if (sc.n_m2l > 0 && P1 <= passes::kM2LSmallP1) {
         int grid = std::min((sc.n_m2l + passes::kM2LSmallWarps - 1) / passes::kM2LSmallWarps, 2 * n_sms);
         passes::m2l_small_kernel<<<grid, 32 * passes::kM2LSmallWarps, passes::m2l_small_smem(P1), st>>>(
             tv, sc.m2l.ptr, sc.n_m2l, P1, m2lfull32i.ptr, M32i.ptr, Lm2l32i.ptr);

@@ -162,6 +162,13 @@ struct Fmm::Impl {
     int P1i = 0;
     DevBuf<float2> m2m32i, l2l32i, base32i, M32i, L32i, Lm2l32i;
     DevBuf<float2> m2lfull32i;        // [56][P1i][P1i] full M2L variants
+    // tensor-core M2L of the inner operator (passes_tc.cuh): G_v tiles, the
+    // node schedule's list-2 entries grouped by variant, the tiles, the
+    // per-entry rows Y and the wait-limit flag
+    DevBuf<float> tc_tab, tc_y;
+    DevBuf<int> tc_entries, tc_err;
+    DevBuf<int4> tc_tiles;
+    int n_tc_tiles = 0;
     DevBuf<float2> lam_ff;            // Lambda [s][g] as (hi, lo) floats
     DevBuf<double> iw64, logw64, plen64;
     DevBuf<unsigned char> heavy;      // per piece: near field evaluated in FP64

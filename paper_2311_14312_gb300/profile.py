@@ -21,14 +21,14 @@ from __future__ import annotations
 import argparse
 
 
-def _context(p_inner=0, inner_tol=0.0, leaf_size=64):
+def _context(p_inner=0, inner_tol=0.0, leaf_size=64, m2l_engine=0):
     from dc_synth import drawing_by_name
 
     from . import Context
     d = drawing_by_name("mixed200")
     ctx = Context(form="fmm32", g=d.g, s_per_panel=d.s_per_panel, p=24, leaf_size=leaf_size,
                   gmres_tol=1e-10, gmres_restart=200, gmres_max_iter=3000, p_inner=p_inner,
-                  inner_tol=inner_tol)
+                  inner_tol=inner_tol, m2l_engine=m2l_engine)
     ctx.build_drawing(d)
     st = ctx.solve_density()
     return ctx, st
@@ -58,8 +58,9 @@ def main(argv=None):
     ap.add_argument("--p-inner", type=int, default=0, help="options.p_inner (0 = default)")
     ap.add_argument("--inner-tol", type=float, default=0.0, help="options.inner_tol (0 = default)")
     ap.add_argument("--leaf-size", type=int, default=64)
+    ap.add_argument("--m2l-engine", type=int, default=0, help="options.m2l_engine (0 tensor cores, 1 CUDA cores)")
     a = ap.parse_args(argv)
-    ctx, st = _context(a.p_inner, a.inner_tol, a.leaf_size)
+    ctx, st = _context(a.p_inner, a.inner_tol, a.leaf_size, a.m2l_engine)
     if a.what == "solve":      # a second solve, inside the NVTX range "solve": steady state
         torch.cuda.nvtx.range_push("solve")
         st = ctx.solve_density()

@@ -46,10 +46,10 @@ def test_struct_layouts_match_header(dcmod):
 int main(void){
  printf("%zu %zu %zu %zu %zu\n", sizeof(dc_options), sizeof(dc_sizes), sizeof(dc_solve_stats),
         sizeof(dc_viewport), sizeof(dc_render_stats));
- printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", offsetof(dc_options, stream), offsetof(dc_options, domain),
+ printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", offsetof(dc_options, stream), offsetof(dc_options, domain),
         offsetof(dc_solve_stats, p2p_pairs), offsetof(dc_render_stats, eval_flops),
         offsetof(dc_solve_stats, warm_resid), offsetof(dc_solve_stats, ms_warm),
-        offsetof(dc_options, p_inner), offsetof(dc_options, inner_tol));
+        offsetof(dc_options, p_inner), offsetof(dc_options, inner_tol), offsetof(dc_options, m2l_engine));
  return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
@@ -67,7 +67,8 @@ int main(void){
     assert offs == [P.dc_options.stream.offset, P.dc_options.domain.offset,
                     P.dc_solve_stats.p2p_pairs.offset, P.dc_render_stats.eval_flops.offset,
                     P.dc_solve_stats.warm_resid.offset, P.dc_solve_stats.ms_warm.offset,
-                    P.dc_options.p_inner.offset, P.dc_options.inner_tol.offset]
+                    P.dc_options.p_inner.offset, P.dc_options.inner_tol.offset,
+                    P.dc_options.m2l_engine.offset]
 
 
 def test_defaults_and_status_strings(dcmod):
