@@ -45,6 +45,7 @@ struct dc_ctx {
     DevBuf<float> warm_params, warm_feat, warm_pred, warm_work;
     DevBuf<double> warm_ax, warm_a1;   // G_H x_pred, G_H 1
     bool warm_a1_valid = false;
+    double build_ms[11] = {};   // dc_aux_build_timings
     dc::PanelFeatures pfeat;
     ~dc_ctx() {
         if (gw) dc::gmres_work_destroy(gw);
@@ -284,9 +285,19 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
     ctx->state = 0;
     ctx->seg_density_valid = false;
     std::string msg;
+    for (double &v : ctx->build_ms) v = 0.0;
+    const auto t_start = std::chrono::steady_clock::now();
+    auto t_prev = t_start;
+    auto lap = [&](int i) {   // the stream drained first
+        cudaStreamSynchronize(ctx->stream);
+        const auto t = std::chrono::steady_clock::now();
+        ctx->build_ms[i] = std::chrono::duration<double, std::milli>(t - t_prev).count();
+        t_prev = t;
+    };
     dc_status st = dc::discretise(n_curves, ctrl, panel_ptr, panel_start, colours, ctx->opt.g,
                                   ctx->opt.s_per_panel, ctx->geo, msg);
     if (st != DC_OK) return fail(ctx, st, msg);
+    lap(0);
     const dc::Geometry &G = ctx->geo;
     dc::DevGeom &D = ctx->dg;
     D.N = G.n_nodes();
@@ -319,6 +330,7 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
     DC_CK(ctx, ctx->sbar.alloc(s3), "alloc");
     DC_CK(ctx, ctx->mbar.alloc(s3), "alloc");
     DC_CK(ctx, dc::launch_mu(D, ctx->mu.ptr, s), "mu");
+    lap(1);
     ctx->AG.release();
     ctx->AF.release();
     ctx->fmm.reset();
@@ -335,8 +347,11 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
             ctx->fmm.reset();
             return fail(ctx, st, msg);
         }
+        ctx->fmm->build_timings(ctx->build_ms + 2);
     }
+    t_prev = std::chrono::steady_clock::now();
     DC_CK(ctx, ctx->pfeat.build(G, s), "panel features");
+    lap(8);
     ctx->warm_a1_valid = false;
     {   // G_H 1, once per drawing: the first residual of the paper's start
         // x0 = 1 and the learned start's least-residual projection use it
@@ -351,7 +366,9 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
             DC_CK(ctx, ctx->fmm->apply_single_layer(ctx->warm_ax.ptr, ctx->warm_a1.ptr, s), "G_H 1");
         ctx->warm_a1_valid = true;
     }
+    lap(9);
     DC_CK(ctx, cudaStreamSynchronize(s), "build_tree");
+    ctx->build_ms[10] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     ctx->state = 1;
     return DC_OK;
 }
@@ -851,6 +868,15 @@ dc_status dc_aux_apply_operator(dc_ctx *ctx, int op, int inner, const double *x,
     } else {
         DC_CK(ctx, ctx->fmm->apply_double_layer(x, y, s), "apply_operator");
     }
+    return DC_OK;
+}
+
+dc_status dc_aux_build_timings(dc_ctx *ctx, double *out) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (!out) return fail(ctx, DC_ERR_ARG, "build_timings: NULL output");
+    if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "build_timings: call build_tree first");
+    for (int i = 0; i < 11; ++i) out[i] = ctx->build_ms[i];
     return DC_OK;
 }
 

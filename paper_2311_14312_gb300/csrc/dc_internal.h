@@ -189,6 +189,12 @@ private:
 struct Operator {
     virtual ~Operator() = default;
     virtual cudaError_t apply(const double *x, double *y, cudaStream_t st) = 0;
+    // Optional: an operator that reads its input from a buffer of its own
+    // and writes its output to another (a captured graph) returns both, and
+    // apply_buffers() applies it there without copies.
+    virtual double *in_buffer() { return nullptr; }
+    virtual double *out_buffer() { return nullptr; }
+    virtual cudaError_t apply_buffers(cudaStream_t) { return cudaErrorNotSupported; }
 };
 
 struct GmresResult {

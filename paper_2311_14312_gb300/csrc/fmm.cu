@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -568,6 +569,13 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         return DC_ERR_ARG;
     }
     I.fp32 = (opt.form == DC_FORM_FMM32);
+    auto t_prev = std::chrono::steady_clock::now();
+    auto phase = [&](int i) {   // wall time of build phase i (the stream drained first)
+        cudaStreamSynchronize(st);
+        const auto t = std::chrono::steady_clock::now();
+        I.build_ms[i] = std::chrono::duration<double, std::milli>(t - t_prev).count();
+        t_prev = t;
+    };
     if (!build_quadtree(G.seg_xy, opt.domain, opt.leaf_size, opt.max_depth, I.tree, err))
         return DC_ERR_GEOMETRY;
     if (I.P1 > 32) {
@@ -743,6 +751,7 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         sc.n_walk = int(walk_c.size());
     };
     std::vector<int> am2l, ap2l, al2l, aw, nm2l, np2l, nl2l, nw;
+    phase(0);   // quadtree, lists, tables, multi-level M2M chunks
     make_sched(I.sched_all, false, am2l, ap2l, al2l, aw);
     make_sched(I.sched_nodes, true, nm2l, np2l, nl2l, nw);
     // rows of the stored P2L coefficients: the pieces of each list-4 cell of
@@ -1052,6 +1061,7 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
             }
     }
     // two-level preconditioner (panel blocks + coarse space of panel constants)
+    phase(1);   // schedules, node items, uploads
     if ((e = I.coarse.build(G, D, st)) != cudaSuccess) {
         err = std::string("fmm coarse preconditioner: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
@@ -1068,16 +1078,24 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)passes::p2l_flat_smem<double>(I.P1));
     cudaFuncSetAttribute(passes::m2m_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)passes::mlff_smem(I.P1));
+    phase(2);   // two-level preconditioner
     if ((e = I.build_rows(st)) != cudaSuccess) {
         err = std::string("stored P2M / P2L coefficients: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
     }
+    phase(3);   // stored P2M / P2L rows
     if ((e = I.build_near(st)) != cudaSuccess) {
         err = std::string("near-field coefficients: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
     }
-    if (I.fp32) return I.build32(G, st, err);
-    return DC_OK;
+    phase(4);   // near / far coefficients
+    dc_status r = I.fp32 ? I.build32(G, st, err) : DC_OK;
+    phase(5);   // FP32 form
+    return r;
+}
+
+void Fmm::build_timings(double out[6]) const {
+    for (int i = 0; i < 6; ++i) out[i] = impl_->build_ms[i];
 }
 
 cudaError_t Fmm::prepare_eval(const double *sbar, const double *mbar, cudaStream_t st) {
@@ -1130,6 +1148,10 @@ struct PrecOp : Operator {
         if (e != cudaSuccess) return e;
         return f->apply_nodes(f->ir_t.ptr, y, true, st);
     }
+    // the FP32 graph's own input and output: no copies in the Arnoldi loop
+    double *in_buffer() override { return fp32 && f->graph_ensure() == cudaSuccess ? f->g_in.ptr : nullptr; }
+    double *out_buffer() override { return fp32 && f->graph_ensure() == cudaSuccess ? f->g_out.ptr : nullptr; }
+    cudaError_t apply_buffers(cudaStream_t st) override { return f->graph_launch(st); }
 };
 }  // namespace
 

@@ -47,6 +47,9 @@ public:
     dc_status eval_points(const double *xy, int n, const double *sbar, const double *mbar,
                           void *out, int out_dtype, cudaStream_t st, std::string &err);
     void fill_sizes(dc_sizes *out) const;
+    // wall ms of the build phases: tree and lists, schedules and uploads,
+    // preconditioner, stored P2M / P2L rows, near / far coefficients, FP32 form
+    void build_timings(double out[6]) const;
     // two-level preconditioner: ready, panels, near pairs, inverse check
     void precond_info(double out[4]) const;
     long long p2p_pairs_nodes() const;

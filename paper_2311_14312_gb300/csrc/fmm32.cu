@@ -144,8 +144,16 @@ __global__ void heavy_kernel(const double *__restrict__ sb, const double *__rest
 
 // -------------------------------------------------------------- eval --
 constexpr int kEvThreads = kEvalTile * kEvalTile;
-constexpr int kEvBlocksPerSM = 512 / kEvThreads;   // register budget of up to 128 per thread
-constexpr int kStage = 256;
+// resident blocks per SM the register budget is set for, and pieces staged
+// in shared memory per round
+#ifndef DC_EVAL_MINBLOCKS
+#define DC_EVAL_MINBLOCKS 12
+#endif
+#ifndef DC_EVAL_STAGE
+#define DC_EVAL_STAGE 128
+#endif
+constexpr int kEvBlocksPerSM = DC_EVAL_MINBLOCKS;
+constexpr int kStage = DC_EVAL_STAGE;
 
 struct EvalArgs32 {
     DevTree32 t;
@@ -745,35 +753,48 @@ cudaError_t Fmm::Impl::nodes32_from_segments(double *y, bool single, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t Fmm::Impl::graph_matvec32(const double *x, double *y, cudaStream_t st) {
-    const size_t bytes = sizeof(double) * 3 * (size_t)D->N;
+// Captures the FP32 preconditioned matvec (g_in -> g_out) once.
+cudaError_t Fmm::Impl::graph_ensure() {
+    if (g32_exec) return cudaSuccess;
     cudaError_t e;
-    if (!g32_exec) {
-        if ((e = g_in.ensure(3 * (size_t)D->N)) != cudaSuccess) return e;
-        if ((e = g_out.ensure(3 * (size_t)D->N)) != cudaSuccess) return e;
-        if (!cap_stream && (e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
-            return e;
-        long long before = kernel_launches();
-        if ((e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
-        // M v straight to the segments (sigma_bar = Lambda M v) when the
-        // two-level preconditioner is in use, else M v at the nodes first
-        cudaError_t e1 = coarse.ready()
-                             ? coarse.apply(pinv.ptr, g_in.ptr, nullptr, cap_stream, lam_ff.ptr, D->s, sbar32.ptr)
-                             : precond(g_in.ptr, ir_t.ptr, cap_stream);
-        cudaError_t e2 = e1;
-        if (e1 == cudaSuccess)
-            e2 = coarse.ready() ? nodes32_from_segments(g_out.ptr, true, cap_stream)
-                                : apply_nodes32(ir_t.ptr, g_out.ptr, true, cap_stream);
-        e = cudaStreamEndCapture(cap_stream, &g32);
-        g32_kernels = int(kernel_launches() - before);
-        note_launch(-g32_kernels);   // counted again at every graph launch
-        if (e2 != cudaSuccess) return e2;
-        if (e != cudaSuccess) return e;
-        if ((e = cudaGraphInstantiate(&g32_exec, g32, 0)) != cudaSuccess) return e;
-    }
-    if ((e = cudaMemcpyAsync(g_in.ptr, x, bytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+    if ((e = g_in.ensure(3 * (size_t)D->N)) != cudaSuccess) return e;
+    if ((e = g_out.ensure(3 * (size_t)D->N)) != cudaSuccess) return e;
+    if (!cap_stream && (e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return e;
+    long long before = kernel_launches();
+    if ((e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    // M v straight to the segments (sigma_bar = Lambda M v) when the
+    // two-level preconditioner is in use, else M v at the nodes first
+    cudaError_t e1 = coarse.ready()
+                         ? coarse.apply(pinv.ptr, g_in.ptr, nullptr, cap_stream, lam_ff.ptr, D->s, sbar32.ptr)
+                         : precond(g_in.ptr, ir_t.ptr, cap_stream);
+    cudaError_t e2 = e1;
+    if (e1 == cudaSuccess)
+        e2 = coarse.ready() ? nodes32_from_segments(g_out.ptr, true, cap_stream)
+                            : apply_nodes32(ir_t.ptr, g_out.ptr, true, cap_stream);
+    e = cudaStreamEndCapture(cap_stream, &g32);
+    g32_kernels = int(kernel_launches() - before);
+    note_launch(-g32_kernels);   // counted again at every graph launch
+    if (e2 != cudaSuccess) return e2;
+    if (e != cudaSuccess) return e;
+    return cudaGraphInstantiate(&g32_exec, g32, 0);
+}
+
+// g_out = A32 M g_in (the captured graph)
+cudaError_t Fmm::Impl::graph_launch(cudaStream_t st) {
+    cudaError_t e = graph_ensure();
+    if (e != cudaSuccess) return e;
     if ((e = cudaGraphLaunch(g32_exec, st)) != cudaSuccess) return e;
     note_launch(g32_kernels);
+    return cudaSuccess;
+}
+
+cudaError_t Fmm::Impl::graph_matvec32(const double *x, double *y, cudaStream_t st) {
+    const size_t bytes = sizeof(double) * 3 * (size_t)D->N;
+    cudaError_t e = graph_ensure();
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(g_in.ptr, x, bytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+    if ((e = graph_launch(st)) != cudaSuccess) return e;
     return cudaMemcpyAsync(y, g_out.ptr, bytes, cudaMemcpyDeviceToDevice, st);
 }
 

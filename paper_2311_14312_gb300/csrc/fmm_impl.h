@@ -187,6 +187,7 @@ struct Fmm::Impl {
     cudaGraphExec_t g32_exec = nullptr;
     int g32_kernels = 0;
     DevBuf<double> g_in, g_out;
+    double build_ms[6] = {0, 0, 0, 0, 0, 0};   // wall time of the build phases
     // the render's tile plan (tiles, vps) for the viewports plan_vps
     bool plan_valid = false;
     std::vector<VpDev> plan_vps;
@@ -194,6 +195,8 @@ struct Fmm::Impl {
     long long plan_pairs = 0, plan_m2p = 0;
     double plan_flops = 0.0;
     cudaError_t graph_matvec32(const double *x, double *y, cudaStream_t st);
+    cudaError_t graph_ensure();
+    cudaError_t graph_launch(cudaStream_t st);
     ~Impl() {
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);

@@ -210,12 +210,14 @@ __global__ void npart_finalize_kernel(const double *__restrict__ npart, int nb, 
 
 // out[i][c] = in[i][c] * (nrm[c] > 0 ? 1 / nrm[c] : 0)
 __global__ void scale_kernel(const double *__restrict__ in, const double *__restrict__ nrm,
-                             double *__restrict__ out, int N) {
+                             double *__restrict__ out, int N, double *__restrict__ out2 = nullptr) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * N) return;
     int c = t % 3;
     double n = nrm[c];
-    out[t] = (n > 0.0) ? in[t] / n : 0.0;
+    const double v = (n > 0.0) ? in[t] / n : 0.0;
+    out[t] = v;
+    if (out2) out2[t] = v;   // the operator's input buffer, when it has one
 }
 
 // r = b - Ax
@@ -599,11 +601,17 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
         for (int c = 0; c < 3; ++c) prev_beta[c] = hbeta[c];
         est_done = false;
         cycle_start_kernel<<<1, 32, 0, st>>>(gs, beta, thr, m); note_launch();
-        scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.r.ptr, beta, W.V.ptr, N); note_launch();
+        // an operator with its own input / output buffers reads v_k from the
+        // former (written by the scale kernels) and leaves A v_k in the latter
+        double *in_buf = A.in_buffer(), *out_buf = A.out_buffer();
+        const bool bufs = in_buf && out_buf;
+        double *wv = bufs ? out_buf : W.w.ptr;
+        scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.r.ptr, beta, W.V.ptr, N, bufs ? in_buf : nullptr);
+        note_launch();
         int k = 0;
         for (; k < m && total < max_iter; ++k) {
             double *vk = W.V.ptr + (size_t)k * vs;
-            if ((ce = A.apply(vk, W.w.ptr, st)) != cudaSuccess) return ce;
+            if ((ce = bufs ? A.apply_buffers(st) : A.apply(vk, wv, st)) != cudaSuccess) return ce;
             res.n_matvec++;
             // CGS2: two passes of h = V^T w, w -= V h
             // classical Gram-Schmidt, h = V^T w, w -= V h, and h_{k+1,k} =
@@ -612,12 +620,12 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
             int *skip = W.flags.ptr + 6;   // after active[3], kc[3]
             for (int pass = 0; pass < 2; ++pass) {
                 dim3 grid(W.nchunk, k + 1);
-                gs_dots_kernel<<<grid, kDotThreads, 0, st>>>(W.V.ptr, vs, W.w.ptr, N, W.nchunk, W.partial.ptr,
+                gs_dots_kernel<<<grid, kDotThreads, 0, st>>>(W.V.ptr, vs, wv, N, W.nchunk, W.partial.ptr,
                                                              W.count.ptr, W.hpass.ptr, W.hcol.ptr, pass == 0,
                                                              pass == 0 ? nullptr : skip);
                 note_launch();
                 const int nb = (3 * N + kOrthThreads - 1) / kOrthThreads;
-                orth_update_norm_kernel<<<nb, kOrthThreads, 0, st>>>(W.V.ptr, vs, W.hpass.ptr, k + 1, W.w.ptr, N,
+                orth_update_norm_kernel<<<nb, kOrthThreads, 0, st>>>(W.V.ptr, vs, W.hpass.ptr, k + 1, wv, N,
                                                                      W.npart.ptr, pass == 0,
                                                                      pass == 0 ? nullptr : skip);
                 note_launch();
@@ -625,8 +633,8 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
                                                         pass == 0 ? nullptr : skip);
                 note_launch();
             }
-            scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.w.ptr, W.hnext.ptr,
-                                                               W.V.ptr + (size_t)(k + 1) * vs, N); note_launch();
+            scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(wv, W.hnext.ptr, W.V.ptr + (size_t)(k + 1) * vs, N,
+                                                               bufs ? in_buf : nullptr); note_launch();
             const size_t gsm = (size_t)9 * (k + 1) * sizeof(double);
             if (gsm <= kGivensSmem)
                 givens_smem_kernel<<<1, 96, gsm, st>>>(gs, W.hcol.ptr, W.hnext.ptr, thr, k, m);
