@@ -29,6 +29,7 @@ namespace dc {
 namespace {
 
 constexpr int kGJ = 32;                 // block size of the Gauss-Jordan inversion
+constexpr int kMaxCoarse = 12288;       // largest coarse system inverted (panels, padded)
 // -log|q - c| / 2pi = kMonoLog2 * log2(|q - c|^2)
 constexpr float kMonoLog2 = -0.0551589000381629f;   // -ln 2 / 4pi
 
@@ -361,12 +362,40 @@ __global__ void __launch_bounds__(kPanelThreads) panel_apply_kernel(
     }
 }
 
+// |(Ai Ac)[r][c] - delta_rc| for the sampled rows r = rows[blockIdx.y] and
+// columns c = blockIdx.y + 7 blockIdx.x (FP64 sums), and bad[0] set when an
+// entry of Ai is not finite (checked by the first row's blocks).
+__global__ void inverse_check_kernel(const float *__restrict__ Ai, const float *__restrict__ Ac, int n,
+                                     int4 rows4, int row5, double *__restrict__ err, int *__restrict__ bad) {
+    const int rows[5] = {rows4.x, rows4.y, rows4.z, rows4.w, row5};
+    const int ci = blockIdx.y, c = ci + 7 * blockIdx.x, r = rows[ci];
+    const int ncol = gridDim.x;
+    double acc = 0.0;
+    if (c < n)
+        for (int k = threadIdx.x; k < n; k += blockDim.x) acc += (double)Ai[(size_t)r * n + k] * Ac[(size_t)k * n + c];
+    if (ci == 0)   // every entry of Ai once across the first row's blocks
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)n * n; i += (size_t)ncol * blockDim.x)
+            if (!isfinite(Ai[i])) atomicOr(bad, 1);
+    __shared__ double red[4];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double v = red[0] + red[1] + red[2] + red[3];
+        err[(size_t)ci * ncol + blockIdx.x] = c < n ? fabs(v - (r == c ? 1.0 : 0.0)) : 0.0;
+    }
+}
+
 }  // namespace
 
 cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st) {
     ready_ = false;
     const int P = G.n_panels, g = G.g, s = G.s, N = G.n_nodes();
     if (P < 2) return cudaSuccess;
+    // the dense coarse inverse (FP32, n_pad^2) is kept below ~600 MB; larger
+    // drawings use the panel blocks alone
+    n_pad_ = (P + kGJ - 1) / kGJ * kGJ;
+    if (n_pad_ > kMaxCoarse) return cudaSuccess;
     P_ = P;
     g_ = g;
     // panel centroids (node average) and arc lengths
@@ -403,7 +432,7 @@ cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st
         }
     }
     nptr[P] = int(pairs.size());
-    n_pad_ = (P + kGJ - 1) / kGJ * kGJ;
+
     cudaError_t e;
     auto up = [&](auto &buf, const auto &v) -> cudaError_t {
         cudaError_t r = buf.alloc(std::max<size_t>(v.size(), 1));
@@ -427,9 +456,9 @@ cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st
                                                 corr_.ptr, P, g, n_pad_, Ainv_.ptr);
     note_launch();
     // keep the coarse matrix for the check below
-    std::vector<float> Ac_h((size_t)n_pad_ * n_pad_);
-    if ((e = cudaMemcpyAsync(Ac_h.data(), Ainv_.ptr, Ac_h.size() * sizeof(float), cudaMemcpyDeviceToHost, st)) !=
-        cudaSuccess)
+    DevBuf<float> Ac;
+    if ((e = Ac.alloc((size_t)n_pad_ * n_pad_)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(Ac.ptr, Ainv_.ptr, Ac.bytes(), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return e;
     const int nb = n_pad_ / kGJ;
     dim3 ug((n_pad_ + 63) / 64, (n_pad_ + 63) / 64);
@@ -441,26 +470,28 @@ cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st
         note_launch(4);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // check the inverse on a few rows (a vanished or tiny pivot shows up as
-    // non-finite entries or a large error): keep the one-level
-    // preconditioner unless it is accurate
-    std::vector<float> Ai_h((size_t)n_pad_ * n_pad_);
-    if ((e = cudaMemcpyAsync(Ai_h.data(), Ainv_.ptr, Ai_h.size() * sizeof(float), cudaMemcpyDeviceToHost, st)) !=
-        cudaSuccess)
+    // check the inverse on a few rows, on the device (a vanished or tiny
+    // pivot shows up as non-finite entries or a large error): keep the
+    // one-level preconditioner unless it is accurate
+    const int ncol = (n_pad_ + 6) / 7;
+    DevBuf<double> errs;
+    DevBuf<int> bad;
+    if ((e = errs.alloc((size_t)5 * ncol)) != cudaSuccess || (e = bad.alloc(1)) != cudaSuccess ||
+        (e = cudaMemsetAsync(bad.ptr, 0, sizeof(int), st)) != cudaSuccess)
         return e;
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-    for (float v : Ai_h)
-        if (!std::isfinite(v)) return cudaSuccess;
+    inverse_check_kernel<<<dim3(ncol, 5), 128, 0, st>>>(Ainv_.ptr, Ac.ptr, n_pad_,
+                                                       make_int4(0, P / 4, P / 2, (3 * P) / 4), P - 1, errs.ptr,
+                                                       bad.ptr);
+    note_launch();
+    std::vector<double> errs_h((size_t)5 * ncol);
+    int bad_h = 0;
+    if ((e = cudaMemcpyAsync(errs_h.data(), errs.ptr, errs.bytes(), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&bad_h, bad.ptr, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return e;
+    if (bad_h) return cudaSuccess;
     double worst = 0.0;
-    const int checks[5] = {0, P / 4, P / 2, (3 * P) / 4, P - 1};
-    for (int ci = 0; ci < 5; ++ci) {
-        const int r = checks[ci];
-        for (int c = ci; c < n_pad_; c += 7) {
-            double acc = 0.0;
-            for (int k = 0; k < n_pad_; ++k) acc += (double)Ai_h[(size_t)r * n_pad_ + k] * Ac_h[(size_t)k * n_pad_ + c];
-            worst = std::max(worst, std::fabs(acc - (r == c ? 1.0 : 0.0)));
-        }
-    }
+    for (double v : errs_h) worst = std::max(worst, v);
     check_ = worst;
     n_pairs_ = int(pairs.size());
     if (!(worst < 1e-2)) return cudaSuccess;

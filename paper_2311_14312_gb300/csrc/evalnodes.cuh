@@ -470,5 +470,97 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 8 : 4) near_appl
     reduce_write<T>(a, t0, nt, warp, lane, acc);
 }
 
+// The FP64 node operator from stored coefficients with float-float
+// arithmetic on the FP32 pipes: near-field coefficients (hi, lo) per
+// (node, piece), segment densities (hi, lo) per channel, far-field
+// coefficients and the L / M expansions as float-float complex values
+// (float4: re hi, im hi, re lo, im lo).  Same work split as
+// near_apply_kernel; lane sums are combined by a fixed butterfly with exact
+// two-sums; the result is written in FP64.
+static __device__ __forceinline__ void ffa_fma(float2 &acc, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    const float e = fmaf(ah, bh, -p);
+    const float sum = __fadd_rn(acc.x, p);
+    const float bb = __fsub_rn(sum, acc.x);
+    const float q = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(sum, bb)), __fsub_rn(p, bb));
+    acc.x = sum;
+    acc.y += q + e + fmaf(ah, bl, al * bh);
+}
+
+static __global__ void __launch_bounds__(32 * kWarps) near_apply_ff_kernel(NodeArgs<double> a, const long long *__restrict__ off,
+                                                                     const float2 *__restrict__ coef,
+                                                                     const float2 *__restrict__ dens,
+                                                                     const long long *__restrict__ far_off,
+                                                                     const float4 *__restrict__ far,
+                                                                     const float4 *__restrict__ Lff,
+                                                                     const float4 *__restrict__ Mff) {
+    const int4 it = a.items[blockIdx.x];
+    const int leaf = it.x, t0 = it.y, nt = it.z, nU = it.w;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 acc[kPer][3];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) acc[j][0] = acc[j][1] = acc[j][2] = make_float2(0.f, 0.f);
+    if (warp < nt) {
+        const float2 *rows = coef + off[blockIdx.x];
+        const int *segs = a.uf_seg + a.uf_ptr[leaf];
+        for (int pl = lane; pl < nU; pl += 32) {
+            const size_t o = 3 * (size_t)segs[pl];
+            const float2 d0 = dens[o], d1 = dens[o + 1], d2 = dens[o + 2];
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                const int tl = warp + kWarps * j;
+                if (tl >= nt) break;
+                const float2 cf = rows[(long long)tl * nU + pl];
+                ffa_fma(acc[j][0], cf.x, cf.y, d0.x, d0.y);
+                ffa_fma(acc[j][1], cf.x, cf.y, d1.x, d1.y);
+                ffa_fma(acc[j][2], cf.x, cf.y, d2.x, d2.y);
+            }
+        }
+    }
+    {   // far field: Re(co x) = co.re x.re - co.im x.im
+        const int P1 = a.P1;
+        const int w0 = a.w_ptr[leaf], nb = 1 + a.w_ptr[leaf + 1] - w0;
+        const int nterm = nb * P1;
+        const float4 *rows = far + far_off[blockIdx.x] * P1;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int tl = warp + kWarps * j;
+            if (tl >= nt) break;
+            const float4 *row = rows + (long long)tl * nterm;
+            for (int u = lane; u < nterm; u += 32) {
+                const int b = u / P1, k = u - b * P1;
+                const int src = b == 0 ? leaf : a.w_idx[w0 + b - 1];
+                const float4 *X = (b == 0 ? Lff : Mff) + (size_t)src * 3 * P1 + k;
+                const float4 co = row[u];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float4 x = X[c * P1];
+                    ffa_fma(acc[j][c], co.x, co.z, x.x, x.z);
+                    ffa_fma(acc[j][c], -co.y, -co.w, x.y, x.w);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j)
+        for (int c = 0; c < 3; ++c)
+            for (int o = 16; o > 0; o >>= 1) {
+                const float h2 = __shfl_xor_sync(0xffffffffu, acc[j][c].x, o);
+                const float l2 = __shfl_xor_sync(0xffffffffu, acc[j][c].y, o);
+                const float sum = __fadd_rn(acc[j][c].x, h2);
+                const float bb = __fsub_rn(sum, acc[j][c].x);
+                const float q = __fadd_rn(__fsub_rn(acc[j][c].x, __fsub_rn(sum, bb)), __fsub_rn(h2, bb));
+                acc[j][c].x = sum;
+                acc[j][c].y += l2 + q;
+            }
+    if (lane != 0) return;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        if (warp + kWarps * j >= nt) break;
+        const size_t o = 3 * (size_t)a.perm[t0 + warp + kWarps * j];
+        for (int c = 0; c < 3; ++c) a.out[o + c] = (double)acc[j][c].x + (double)acc[j][c].y;
+    }
+}
+
 }  // namespace evalnodes
 }  // namespace dc

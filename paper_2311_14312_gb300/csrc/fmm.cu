@@ -329,9 +329,12 @@ cudaError_t Fmm::Impl::passes(const double *sb, const double *mb, int use_s, int
     passes::TreeView<double> tv = view64();
     passes::PiecesF64 ps{pc.ptr, cc.ptr};
     if (n_p2m > 0) {
-        passes::p2m_kernel<double, passes::PiecesF64><<<n_p2m, passes::kChunk, passes::p2m_smem<double>(P1), st>>>(
-            tv, ps, p2m_leaves.ptr, sb, mb, use_s, use_m, P1, M.ptr,
-            rows_ready ? p2m_g64.ptr : nullptr, rows_ready && use_m ? p2m_f64.ptr : nullptr);
+        if (rows_ready)
+            passes::p2m_rows_ff_kernel<<<n_p2m, passes::kChunk, 0, st>>>(tv, p2m_leaves.ptr, sb, mb, use_s, use_m, P1,
+                                                                       M.ptr, p2m_gff.ptr, p2m_fff.ptr);
+        else
+            passes::p2m_kernel<double, passes::PiecesF64><<<n_p2m, passes::kChunk, passes::p2m_smem<double>(P1), st>>>(
+                tv, ps, p2m_leaves.ptr, sb, mb, use_s, use_m, P1, M.ptr);
         note_launch();
     }
     // per level, in float-float: the chain through the parents does less
@@ -351,10 +354,9 @@ cudaError_t Fmm::Impl::passes(const double *sb, const double *mb, int use_s, int
     }
     if (sc.n_p2l > 0) {
         if (rows_ready)
-            passes::p2l_flat_kernel<double, passes::PiecesF64>
-                <<<sc.n_p2l, passes::kChunk, passes::p2l_flat_smem<double>(P1), st>>>(
-                    tv, ps, sc.p2l.ptr, p2l_off.ptr, p2l_cnt.ptr, p2l_item.ptr, sb, mb, use_s, use_m, P1, Lm2l.ptr,
-                    p2l_g64.ptr, use_m ? p2l_f64.ptr : nullptr);
+            passes::p2l_rows_ff_kernel<<<sc.n_p2l, passes::kChunk, 0, st>>>(
+                tv, sc.p2l.ptr, p2l_off.ptr, p2l_cnt.ptr, p2l_item.ptr, sb, mb, use_s, use_m, P1, Lm2l.ptr,
+                p2l_gff.ptr, p2l_fff.ptr);
         else
             passes::p2l_kernel<double, passes::PiecesF64><<<sc.n_p2l, passes::kChunk, passes::p2l_smem<double>(P1), st>>>(
                 tv, ps, sc.p2l.ptr, sb, mb, use_s, use_m, P1, Lm2l.ptr);
@@ -404,6 +406,17 @@ evalnodes::NodeArgs<double> Fmm::Impl::node_args64(const int4 *items, const doub
     return a;
 }
 
+namespace {
+// b[i] = a[i] as (hi, lo) floats
+__global__ void d2ff_kernel(const double *__restrict__ a, float2 *__restrict__ b, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = a[i];
+        const float h = (float)v;
+        b[i] = make_float2(h, (float)(v - (double)h));
+    }
+}
+}  // namespace
+
 cudaError_t Fmm::Impl::eval_list64(const int4 *items, int n_items, const double *q64,
                                    const int *own1, const int *own2, const int *perm,
                                    const double *sb, const double *mb, int use_s, int use_m,
@@ -420,6 +433,23 @@ cudaError_t Fmm::Impl::apply_nodes(const double *x, double *y, bool single, cuda
     if (e != cudaSuccess) return e;
     int us = single ? 1 : 0, um = single ? 0 : 1;
     if ((e = passes(sbar.ptr, mbar.ptr, us, um, st, sched_nodes)) != cudaSuccess) return e;
+    if (near_ready && far_ready && n_nt_items4 > 0) {   // float-float from stored coefficients
+        const long long nS = 3LL * D->S;
+        const size_t nE = (size_t)tree.n_cells() * 3 * P1;
+        if ((e = dens_ff.ensure((size_t)nS)) != cudaSuccess || (e = Lff.ensure(nE)) != cudaSuccess ||
+            (e = Mff.ensure(nE)) != cudaSuccess)
+            return e;
+        d2ff_kernel<<<4 * n_sms, 256, 0, st>>>(single ? sbar.ptr : mbar.ptr, dens_ff.ptr, nS);
+        passes::rows_to_ff_kernel<<<4 * n_sms, 256, 0, st>>>(L.ptr, Lff.ptr, nE);
+        passes::rows_to_ff_kernel<<<4 * n_sms, 256, 0, st>>>(M.ptr, Mff.ptr, nE);
+        evalnodes::NodeArgs<double> a = node_args64(nt_items4.ptr, nt_xy.ptr, nt_own1.ptr, nt_own2.ptr,
+                                                    nt_perm.ptr, sbar.ptr, mbar.ptr, us, um, y);
+        evalnodes::near_apply_ff_kernel<<<n_nt_items4, 32 * evalnodes::kWarps, 0, st>>>(
+            a, near_off.ptr, single ? near_gff.ptr : near_fff.ptr, dens_ff.ptr, far_off.ptr, farff.ptr, Lff.ptr,
+            Mff.ptr);
+        note_launch(4);
+        return cudaGetLastError();
+    }
     if (near_ready && n_nt_items4 > 0) {
         evalnodes::NodeArgs<double> a = node_args64(nt_items4.ptr, nt_xy.ptr, nt_own1.ptr, nt_own2.ptr,
                                                     nt_perm.ptr, sbar.ptr, mbar.ptr, us, um, y);
@@ -496,6 +526,19 @@ cudaError_t Fmm::Impl::build_near(cudaStream_t st) {
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     far_ready = true;
+    // the FP64 node operator reads both in float-float (same sizes)
+    if ((e = near_gff.alloc((size_t)near_total)) != cudaSuccess ||
+        (e = near_fff.alloc((size_t)near_total)) != cudaSuccess ||
+        (e = farff.alloc((size_t)far_blocks * P1)) != cudaSuccess)
+        return e;
+    d2ff_kernel<<<4 * n_sms, 256, 0, st>>>(near_g64.ptr, near_gff.ptr, near_total);
+    d2ff_kernel<<<4 * n_sms, 256, 0, st>>>(near_f64.ptr, near_fff.ptr, near_total);
+    passes::rows_to_ff_kernel<<<4 * n_sms, 256, 0, st>>>(far64.ptr, farff.ptr, (size_t)far_blocks * P1);
+    note_launch(3);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    near_g64.release();
+    near_f64.release();
+    far64.release();
     return cudaSuccess;
 }
 
@@ -550,6 +593,19 @@ cudaError_t Fmm::Impl::build_rows(cudaStream_t st) {
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    // the FP64 passes read the rows as float-float (same size)
+    auto to_ff = [&](DevBuf<double2> &src, DevBuf<float4> &dst) -> cudaError_t {
+        cudaError_t r = dst.alloc(src.n);
+        if (r != cudaSuccess || src.n == 0) return r;
+        passes::rows_to_ff_kernel<<<4 * n_sms, 256, 0, st>>>(src.ptr, dst.ptr, src.n);
+        note_launch();
+        r = cudaStreamSynchronize(st);
+        src.release();
+        return r;
+    };
+    if ((e = to_ff(p2m_g64, p2m_gff)) != cudaSuccess || (e = to_ff(p2m_f64, p2m_fff)) != cudaSuccess ||
+        (e = to_ff(p2l_g64, p2l_gff)) != cudaSuccess || (e = to_ff(p2l_f64, p2l_fff)) != cudaSuccess)
+        return e;
     rows_ready = true;
     return cudaSuccess;
 }

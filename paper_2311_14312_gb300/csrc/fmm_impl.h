@@ -96,7 +96,9 @@ struct Fmm::Impl {
     DevBuf<long long> near_off;
     long long near_total = 0;
     bool near_ready = false;
-    DevBuf<double> near_g64, near_f64;
+    DevBuf<double> near_g64, near_f64;   // while they are built (near and far both stored: float-float)
+    DevBuf<float2> near_gff, near_fff, dens_ff;
+    DevBuf<float4> farff, Lff, Mff;
     DevBuf<float> near_g32;
     cudaError_t build_near(cudaStream_t st);
     // far-field coefficients of the node targets: (1 + list-3 length) blocks
@@ -114,7 +116,8 @@ struct Fmm::Impl {
     DevBuf<long long> p2l_off;
     DevBuf<int> p2l_cnt;          // [cells] rows of the cell's list 4
     DevBuf<int2> p2l_item;        // [p2l_rows] (piece, list-4 entry), row order
-    DevBuf<double2> p2m_g64, p2m_f64, p2l_g64, p2l_f64;
+    DevBuf<double2> p2m_g64, p2m_f64, p2l_g64, p2l_f64;   // FP64 rows while they are built
+    DevBuf<float4> p2m_gff, p2m_fff, p2l_gff, p2l_fff;    // the same rows in float-float
     DevBuf<float2> p2m_g32;
     cudaError_t build_rows(cudaStream_t st);
     // FP64 tables and expansions

@@ -14,6 +14,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
+#include <string>
+#include <thread>
+#include <vector>
 
 #include "dc_internal.h"
 
@@ -219,72 +223,106 @@ dc_status discretise(int n_curves, const double *ctrl, const int *panel_ptr,
         for (int m = 0; m < g; ++m) out.lambda[size_t(k) * g + m] = (bw[m] / (xb - gx[m])) / den;
     }
 
-    std::vector<double> vx(s + 1), vy(s + 1);
+    // curves are independent: host threads take contiguous ranges of them
+    // (each writes only its curves' nodes and segments), then the bounding
+    // boxes and the first error in curve order are merged
+    struct Part {
+        double bb[4] = {1e300, 1e300, -1e300, -1e300};
+        dc_status st = DC_OK;
+        std::string err;
+    };
+    auto work = [&](int c0, int c1, Part &pt) {
+        std::vector<double> vx(s + 1), vy(s + 1);
+        double *bb = pt.bb;
+        for (int ci = c0; ci < c1; ++ci) {
+            Cubic cu;
+            std::memcpy(cu.c, ctrl + 8 * size_t(ci), sizeof(cu.c));
+            ArcLength al(&cu);
+            double L = al.total();
+            out.curve_len[ci] = L;
+            if (!(L > 0.0)) {
+                pt.err = "build_tree: curve " + std::to_string(ci) + " has zero length";
+                pt.st = DC_ERR_GEOMETRY;
+                return;
+            }
+            const double *col = colours + 12 * size_t(ci);
+            for (int pj = panel_ptr[ci]; pj < panel_ptr[ci + 1]; ++pj) {
+                double fa = panel_start[pj];
+                double fb = (pj + 1 < panel_ptr[ci + 1]) ? panel_start[pj + 1] : 1.0;
+                double sa = fa * L, sb = fb * L, h = (sb - sa) / s;
+                for (int k = 0; k <= s; ++k) {
+                    double t;
+                    if (k == 0) t = (fa == 0.0) ? 0.0 : al.invert(sa);
+                    else if (k == s) t = (fb == 1.0) ? 1.0 : al.invert(sb);
+                    else t = al.invert(sa + k * h);
+                    cu.point(t, vx[k], vy[k]);
+                }
+                for (int k = 0; k < s; ++k) {
+                    size_t sid = size_t(pj) * s + k;
+                    double *q = &out.seg_xy[4 * sid];
+                    q[0] = vx[k];
+                    q[1] = vy[k];
+                    q[2] = vx[k + 1];
+                    q[3] = vy[k + 1];
+                    double chord = std::hypot(vx[k + 1] - vx[k], vy[k + 1] - vy[k]);
+                    if (!(chord > 0.0)) {
+                        pt.err = "build_tree: zero-length segment on curve " + std::to_string(ci);
+                        pt.st = DC_ERR_GEOMETRY;
+                        return;
+                    }
+                    out.seg_w[sid] = h / chord;
+                    bb[0] = std::min(bb[0], std::min(q[0], q[2]));
+                    bb[1] = std::min(bb[1], std::min(q[1], q[3]));
+                    bb[2] = std::max(bb[2], std::max(q[0], q[2]));
+                    bb[3] = std::max(bb[3], std::max(q[1], q[3]));
+                }
+                for (int m = 0; m < g; ++m) {
+                    size_t nid = size_t(pj) * g + m;
+                    double pos = 0.5 * (gx[m] + 1.0) * s;   // in segment units
+                    int k = std::min(s - 1, int(std::floor(pos)));
+                    double tau = pos - k;
+                    int alt = -1;
+                    if (tau < 1e-12 && k > 0) alt = pj * s + k - 1;
+                    if (tau > 1.0 - 1e-12 && k + 1 < s) alt = pj * s + k + 1;
+                    out.node_xy[2 * nid] = vx[k] + tau * (vx[k + 1] - vx[k]);
+                    out.node_xy[2 * nid + 1] = vy[k] + tau * (vy[k + 1] - vy[k]);
+                    out.node_seg[nid] = pj * s + k;
+                    out.node_seg2[nid] = alt;
+                    out.node_curve[nid] = ci;
+                    double tn = al.invert(sa + 0.5 * (gx[m] + 1.0) * (sb - sa));
+                    out.node_t[nid] = tn;
+                    for (int c = 0; c < 3; ++c) {
+                        // colours[ci][side][end][rgb], linear in t
+                        double p0 = col[0 * 6 + 0 * 3 + c], p1 = col[0 * 6 + 1 * 3 + c];
+                        double m0 = col[1 * 6 + 0 * 3 + c], m1 = col[1 * 6 + 1 * 3 + c];
+                        out.u_plus[3 * nid + c] = (1.0 - tn) * p0 + tn * p1;
+                        out.u_minus[3 * nid + c] = (1.0 - tn) * m0 + tn * m1;
+                    }
+                }
+            }
+        }
+    };
+    const int hw = int(std::max(1u, std::thread::hardware_concurrency()));
+    const int nt = std::max(1, std::min({hw, 16, n_curves / 4}));
+    std::vector<Part> parts(nt);
+    {
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nt; ++t)
+            pool.emplace_back(work, int((long long)n_curves * t / nt), int((long long)n_curves * (t + 1) / nt),
+                              std::ref(parts[t]));
+        work(0, int((long long)n_curves / nt), parts[0]);
+        for (auto &th : pool) th.join();
+    }
     double bb[4] = {1e300, 1e300, -1e300, -1e300};
-    for (int ci = 0; ci < n_curves; ++ci) {
-        Cubic cu;
-        std::memcpy(cu.c, ctrl + 8 * size_t(ci), sizeof(cu.c));
-        ArcLength al(&cu);
-        double L = al.total();
-        out.curve_len[ci] = L;
-        if (!(L > 0.0)) {
-            err = "build_tree: curve " + std::to_string(ci) + " has zero length";
-            return DC_ERR_GEOMETRY;
+    for (const Part &pt : parts) {
+        if (pt.st != DC_OK) {
+            err = pt.err;
+            return pt.st;
         }
-        const double *col = colours + 12 * size_t(ci);
-        for (int pj = panel_ptr[ci]; pj < panel_ptr[ci + 1]; ++pj) {
-            double fa = panel_start[pj];
-            double fb = (pj + 1 < panel_ptr[ci + 1]) ? panel_start[pj + 1] : 1.0;
-            double sa = fa * L, sb = fb * L, h = (sb - sa) / s;
-            for (int k = 0; k <= s; ++k) {
-                double t;
-                if (k == 0) t = (fa == 0.0) ? 0.0 : al.invert(sa);
-                else if (k == s) t = (fb == 1.0) ? 1.0 : al.invert(sb);
-                else t = al.invert(sa + k * h);
-                cu.point(t, vx[k], vy[k]);
-            }
-            for (int k = 0; k < s; ++k) {
-                size_t sid = size_t(pj) * s + k;
-                double *q = &out.seg_xy[4 * sid];
-                q[0] = vx[k];
-                q[1] = vy[k];
-                q[2] = vx[k + 1];
-                q[3] = vy[k + 1];
-                double chord = std::hypot(vx[k + 1] - vx[k], vy[k + 1] - vy[k]);
-                if (!(chord > 0.0)) {
-                    err = "build_tree: zero-length segment on curve " + std::to_string(ci);
-                    return DC_ERR_GEOMETRY;
-                }
-                out.seg_w[sid] = h / chord;
-                bb[0] = std::min(bb[0], std::min(q[0], q[2]));
-                bb[1] = std::min(bb[1], std::min(q[1], q[3]));
-                bb[2] = std::max(bb[2], std::max(q[0], q[2]));
-                bb[3] = std::max(bb[3], std::max(q[1], q[3]));
-            }
-            for (int m = 0; m < g; ++m) {
-                size_t nid = size_t(pj) * g + m;
-                double pos = 0.5 * (gx[m] + 1.0) * s;   // in segment units
-                int k = std::min(s - 1, int(std::floor(pos)));
-                double tau = pos - k;
-                int alt = -1;
-                if (tau < 1e-12 && k > 0) alt = pj * s + k - 1;
-                if (tau > 1.0 - 1e-12 && k + 1 < s) alt = pj * s + k + 1;
-                out.node_xy[2 * nid] = vx[k] + tau * (vx[k + 1] - vx[k]);
-                out.node_xy[2 * nid + 1] = vy[k] + tau * (vy[k + 1] - vy[k]);
-                out.node_seg[nid] = pj * s + k;
-                out.node_seg2[nid] = alt;
-                out.node_curve[nid] = ci;
-                double tn = al.invert(sa + 0.5 * (gx[m] + 1.0) * (sb - sa));
-                out.node_t[nid] = tn;
-                for (int c = 0; c < 3; ++c) {
-                    // colours[ci][side][end][rgb], linear in t
-                    double p0 = col[0 * 6 + 0 * 3 + c], p1 = col[0 * 6 + 1 * 3 + c];
-                    double m0 = col[1 * 6 + 0 * 3 + c], m1 = col[1 * 6 + 1 * 3 + c];
-                    out.u_plus[3 * nid + c] = (1.0 - tn) * p0 + tn * p1;
-                    out.u_minus[3 * nid + c] = (1.0 - tn) * m0 + tn * m1;
-                }
-            }
-        }
+        bb[0] = std::min(bb[0], pt.bb[0]);
+        bb[1] = std::min(bb[1], pt.bb[1]);
+        bb[2] = std::max(bb[2], pt.bb[2]);
+        bb[3] = std::max(bb[3], pt.bb[3]);
     }
     std::memcpy(out.bbox, bb, sizeof(bb));
     return DC_OK;

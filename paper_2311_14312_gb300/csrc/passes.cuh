@@ -746,6 +746,152 @@ static __global__ void __launch_bounds__(128) l2l_ff_kernel(TreeView<double> t, 
             make_double2((double)acc[c].x + (double)acc[c].z, (double)acc[c].y + (double)acc[c].w);
 }
 
+// ------------------------------------- stored rows in float-float --
+// P2M and list-4 P2L of the FP64 passes from stored per-piece coefficient
+// rows kept as float-float complex values (float4: re hi, im hi, re lo,
+// im lo) and densities converted to float-float once per piece: the sums run
+// on the FP32 pipes (FP64 arithmetic is 1/64 of the FP32 rate here) with
+// about 2^-44 relative error per term, and the results are written as FP64.
+
+// hi + lo += (ah + al) (bh + bl)
+__device__ __forceinline__ void ff_fma(float &hi, float &lo, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    const float e = fmaf(ah, bh, -p);
+    float sum, q;
+    two_sum(hi, p, sum, q);
+    hi = sum;
+    lo += q + e + fmaf(ah, bl, al * bh);
+}
+
+__device__ __forceinline__ float2 ff_of(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
+// acc (complex float-float) += row (complex float-float) * d (real float-float)
+__device__ __forceinline__ void ff_row_fma(float4 &acc, float4 row, float2 d) {
+    ff_fma(acc.x, acc.z, row.x, row.z, d.x, d.y);
+    ff_fma(acc.y, acc.w, row.y, row.w, d.x, d.y);
+}
+
+// M[leaf] = sum over the leaf's pieces of rows_g sigma_bar + rows_f mu_bar
+// (rows_f only when use_m); block per leaf as p2m_kernel.
+static __global__ void __launch_bounds__(kChunk) p2m_rows_ff_kernel(TreeView<double> t, const int *__restrict__ leaves,
+                                                                    const double *__restrict__ sb,
+                                                                    const double *__restrict__ mb, int use_s,
+                                                                    int use_m, int P1, double2 *__restrict__ M,
+                                                                    const float4 *__restrict__ rows_g,
+                                                                    const float4 *__restrict__ rows_f) {
+    __shared__ float2 D[kChunk * 6];
+    __shared__ float4 part[3 * kChunk];
+    const int cell = leaves[blockIdx.x];
+    const int tid = threadIdx.x;
+    const int ngrp = kChunk / P1, grp = tid / P1, k = tid - grp * P1;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 acc[3] = {z, z, z};
+    const int p0 = t.pstart[cell], pn = t.pcount[cell];
+    for (int base = 0; base < pn; base += kChunk) {
+        const int cnt = min(kChunk, pn - base);
+        __syncthreads();
+        if (tid < cnt) {
+            const size_t seg = (size_t)t.pseg[p0 + base + tid];
+            for (int c = 0; c < 3; ++c) {
+                D[tid * 6 + c] = ff_of(use_s ? sb[3 * seg + c] : 0.0);
+                D[tid * 6 + 3 + c] = ff_of(use_m ? mb[3 * seg + c] : 0.0);
+            }
+        }
+        __syncthreads();
+        if (grp < ngrp)
+#pragma unroll 2
+            for (int j = grp; j < cnt; j += ngrp) {
+                const size_t ri = (size_t)(p0 + base + j) * P1 + k;
+                const float4 cg = rows_g[ri];
+                const float4 cf = use_m ? rows_f[ri] : z;
+                for (int c = 0; c < 3; ++c) {
+                    ff_row_fma(acc[c], cg, D[j * 6 + c]);
+                    if (use_m) ff_row_fma(acc[c], cf, D[j * 6 + 3 + c]);
+                }
+            }
+    }
+    __syncthreads();
+    if (grp < ngrp)
+        for (int c = 0; c < 3; ++c) part[(grp * 3 + c) * P1 + k] = acc[c];
+    __syncthreads();
+    if (tid < P1)
+        for (int c = 0; c < 3; ++c) {
+            float4 a = part[c * P1 + tid];
+            for (int q = 1; q < ngrp; ++q) ff_cadd(a, part[(q * 3 + c) * P1 + tid]);
+            M[((size_t)cell * 3 + c) * P1 + tid] =
+                make_double2((double)a.x + (double)a.z, (double)a.y + (double)a.w);
+        }
+}
+
+// Lout[cell] += sum over the cell's list-4 rows (row_off, row_cnt, item as
+// in p2l_flat_kernel) of rows_g sigma_bar + rows_f mu_bar.
+static __global__ void __launch_bounds__(kChunk) p2l_rows_ff_kernel(TreeView<double> t, const int *__restrict__ cells,
+                                                                    const long long *__restrict__ row_off,
+                                                                    const int *__restrict__ row_cnt,
+                                                                    const int2 *__restrict__ item,
+                                                                    const double *__restrict__ sb,
+                                                                    const double *__restrict__ mb, int use_s,
+                                                                    int use_m, int P1, double2 *__restrict__ Lout,
+                                                                    const float4 *__restrict__ rows_g,
+                                                                    const float4 *__restrict__ rows_f) {
+    __shared__ float2 D[kChunk * 6];
+    __shared__ float4 part[3 * kChunk];
+    const int cell = cells[blockIdx.x];
+    const int tid = threadIdx.x;
+    const int ngrp = kChunk / P1, grp = tid / P1, l = tid - grp * P1;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 acc[3] = {z, z, z};
+    const long long r0 = row_off[cell];
+    const int n = row_cnt[cell];
+    for (int base = 0; base < n; base += kChunk) {
+        const int cnt = min(kChunk, n - base);
+        __syncthreads();
+        if (tid < cnt) {
+            const size_t seg = (size_t)t.pseg[item[r0 + base + tid].x];
+            for (int c = 0; c < 3; ++c) {
+                D[tid * 6 + c] = ff_of(use_s ? sb[3 * seg + c] : 0.0);
+                D[tid * 6 + 3 + c] = ff_of(use_m ? mb[3 * seg + c] : 0.0);
+            }
+        }
+        __syncthreads();
+        if (grp < ngrp)
+#pragma unroll 2
+            for (int j = grp; j < cnt; j += ngrp) {
+                const size_t ri = (size_t)(r0 + base + j) * P1 + l;
+                const float4 cg = rows_g[ri];
+                const float4 cf = use_m ? rows_f[ri] : z;
+                for (int c = 0; c < 3; ++c) {
+                    ff_row_fma(acc[c], cg, D[j * 6 + c]);
+                    if (use_m) ff_row_fma(acc[c], cf, D[j * 6 + 3 + c]);
+                }
+            }
+    }
+    __syncthreads();
+    if (grp < ngrp)
+        for (int c = 0; c < 3; ++c) part[(grp * 3 + c) * P1 + l] = acc[c];
+    __syncthreads();
+    if (tid < P1)
+        for (int c = 0; c < 3; ++c) {
+            float4 a = part[c * P1 + tid];
+            for (int q = 1; q < ngrp; ++q) ff_cadd(a, part[(q * 3 + c) * P1 + tid]);
+            double2 *o = Lout + ((size_t)cell * 3 + c) * P1 + tid;
+            o->x += (double)a.x + (double)a.z;
+            o->y += (double)a.y + (double)a.w;
+        }
+}
+
+// float-float copies of FP64 complex rows
+static __global__ void rows_to_ff_kernel(const double2 *__restrict__ in, float4 *__restrict__ out, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 v = in[i];
+        const float hx = (float)v.x, hy = (float)v.y;
+        out[i] = make_float4(hx, hy, (float)(v.x - (double)hx), (float)(v.y - (double)hy));
+    }
+}
+
 constexpr int kM2LffWarps = 8;
 
 inline size_t m2l_ff_smem(int P1) {

@@ -13,6 +13,9 @@
 // closed boxes share at least a point (corners included).
 #include "tree.h"
 
+#include <atomic>
+#include <thread>
+
 #include <algorithm>
 #include <cmath>
 #include <unordered_set>
@@ -108,15 +111,18 @@ bool build_quadtree(const std::vector<double> &seg_xy, const double domain[4], i
     int lev = 0;
     int first = 0;   // first cell of the current level
     while (true) {
-        int n_level = int(cur.size());
-        std::vector<std::vector<Piece>> nxt;
-        int next_first = t.n_cells();
+        const int n_level = int(cur.size());
+        const int next_first = t.n_cells();
+        // which cells of this level split (their children are numbered in
+        // cell order), then the pieces of each splitting cell are cut at its
+        // midlines into the children's lists, cells in parallel
+        std::vector<int> split(n_level, -1);
+        int n_split = 0;
         for (int j = 0; j < n_level; ++j) {
-            int c = first + j;
-            std::vector<Piece> &pcs = cur[j];
-            if (int(pcs.size()) > leaf_size && lev < max_depth) {
-                int c0 = t.n_cells();
-                t.child0[c] = c0;
+            const int c = first + j;
+            if (int(cur[j].size()) > leaf_size && lev < max_depth) {
+                split[j] = n_split++;
+                t.child0[c] = t.n_cells();
                 for (int q = 0; q < 4; ++q) {
                     t.level.push_back(lev + 1);
                     t.parent.push_back(c);
@@ -124,40 +130,82 @@ bool build_quadtree(const std::vector<double> &seg_xy, const double domain[4], i
                     t.ix.push_back(2 * t.ix[c] + (q & 1));
                     t.iy.push_back(2 * t.iy[c] + (q >> 1));
                 }
-                leaf_pieces.resize(t.n_cells());
-                size_t base = nxt.size();
-                nxt.resize(base + 4);
-                double xm = t.cx(c), ym = t.cy(c);
-                for (const Piece &p : pcs) {
-                    const double *q = &seg_xy[4 * size_t(p.seg)];
-                    double dx = q[2] - q[0], dy = q[3] - q[1];
-                    double cuts[4];
-                    int nc = 0;
-                    cuts[nc++] = p.ta;
-                    if (dx != 0.0) {
-                        double tx = (xm - q[0]) / dx;
-                        if (tx > p.ta && tx < p.tb) cuts[nc++] = tx;
-                    }
-                    if (dy != 0.0) {
-                        double ty = (ym - q[1]) / dy;
-                        if (ty > p.ta && ty < p.tb) cuts[nc++] = ty;
-                    }
-                    cuts[nc++] = p.tb;
-                    std::sort(cuts, cuts + nc);
-                    for (int i = 0; i + 1 < nc; ++i) {
-                        double u = cuts[i], v = cuts[i + 1];
-                        if (!(v > u)) continue;
-                        double tm = 0.5 * (u + v);
-                        double px = q[0] + tm * dx, py = q[1] + tm * dy;
-                        int qd = (px >= xm ? 1 : 0) + (py >= ym ? 2 : 0);
-                        nxt[base + qd].push_back({p.seg, u, v});
-                    }
-                }
-                std::vector<Piece>().swap(pcs);
             } else {
-                leaf_pieces[c].swap(pcs);
+                leaf_pieces[c].swap(cur[j]);
             }
         }
+        leaf_pieces.resize(t.n_cells());
+        std::vector<std::vector<Piece>> nxt(4 * (size_t)n_split);
+        // work items: pieces [a, b) of splitting cell j (large cells are
+        // cut in chunks); each item fills its own four lists, which are
+        // concatenated per cell in item order (deterministic)
+        struct Item {
+            int j, a, b;
+            std::vector<Piece> kids[4];
+        };
+        constexpr int kChunkPieces = 8192;
+        std::vector<Item> items;
+        for (int j = 0; j < n_level; ++j) {
+            if (split[j] < 0) continue;
+            const int n = int(cur[j].size());
+            for (int a0 = 0; a0 < n; a0 += kChunkPieces) items.push_back({j, a0, std::min(n, a0 + kChunkPieces), {}});
+        }
+        auto cut = [&](Item &it) {
+            const int c = first + it.j;
+            const std::vector<Piece> &pcs = cur[it.j];
+            for (int q = 0; q < 4; ++q) it.kids[q].reserve((it.b - it.a) / 2 + 4);
+            const double xm = t.cx(c), ym = t.cy(c);
+            for (int pi = it.a; pi < it.b; ++pi) {
+                const Piece &p = pcs[pi];
+                const double *q = &seg_xy[4 * size_t(p.seg)];
+                double dx = q[2] - q[0], dy = q[3] - q[1];
+                double cuts[4];
+                int nc = 0;
+                cuts[nc++] = p.ta;
+                if (dx != 0.0) {
+                    double tx = (xm - q[0]) / dx;
+                    if (tx > p.ta && tx < p.tb) cuts[nc++] = tx;
+                }
+                if (dy != 0.0) {
+                    double ty = (ym - q[1]) / dy;
+                    if (ty > p.ta && ty < p.tb) cuts[nc++] = ty;
+                }
+                cuts[nc++] = p.tb;
+                for (int i = 1; i < nc; ++i)   // at most four values: insertion sort
+                    for (int k = i; k > 0 && cuts[k] < cuts[k - 1]; --k) std::swap(cuts[k], cuts[k - 1]);
+                for (int i = 0; i + 1 < nc; ++i) {
+                    double u = cuts[i], v = cuts[i + 1];
+                    if (!(v > u)) continue;
+                    double tm = 0.5 * (u + v);
+                    double px = q[0] + tm * dx, py = q[1] + tm * dy;
+                    int qd = (px >= xm ? 1 : 0) + (py >= ym ? 2 : 0);
+                    it.kids[qd].push_back({p.seg, u, v});
+                }
+            }
+        };
+        const int hw = int(std::max(1u, std::thread::hardware_concurrency()));
+        const int nt = std::max(1, std::min({hw, 16, int(items.size())}));
+        if (nt <= 1 || items.size() < 4) {
+            for (Item &it : items) cut(it);
+        } else {
+            std::atomic<int> next{0};
+            auto run = [&]() {
+                for (int i = next++; i < int(items.size()); i = next++) cut(items[i]);
+            };
+            std::vector<std::thread> pool;
+            for (int k = 1; k < nt; ++k) pool.emplace_back(run);
+            run();
+            for (auto &th : pool) th.join();
+        }
+        for (Item &it : items) {
+            std::vector<Piece> *kids = &nxt[4 * (size_t)split[it.j]];
+            for (int q = 0; q < 4; ++q) {
+                if (kids[q].empty()) kids[q].swap(it.kids[q]);
+                else kids[q].insert(kids[q].end(), it.kids[q].begin(), it.kids[q].end());
+            }
+        }
+        for (int j = 0; j < n_level; ++j)
+            if (split[j] >= 0) std::vector<Piece>().swap(cur[j]);
         if (nxt.empty()) break;
         ++lev;
         t.level_start.push_back(next_first);
