@@ -6,9 +6,9 @@
 // (re-orthogonalisation) pass when the first one cancelled more than 90% of
 // the vector's norm in some channel (a looser form of the criterion of
 // Daniel, Gragg, Kaufman and Stewart; the flag is set and read on the
-// device, so a skipped pass costs three empty launches); Givens
-// rotations, the residual estimate and the triangular solve run on the
-// device.  Reductions are two-stage with a fixed order, so results are
+// device, so a skipped pass costs two empty launches); Givens rotations
+// (run by the last block of the orthogonalisation), the residual estimate
+// and the triangular solve run on the device.  Reductions are two-stage with a fixed order, so results are
 // bit-reproducible.  The host learns of convergence from per-channel flags
 // copied back after every iteration, read kPollLag iterations late so that
 // the device queue never drains; iterations enqueued after the last channel
@@ -30,7 +30,7 @@ constexpr int kChunk = 1024;     // rows per partial dot-product block
 constexpr int kDotThreads = 256;
 constexpr int kPollRing = 4;     // pinned flag slots / events
 constexpr int kPollLag = 1;      // iterations between enqueue and flag read
-constexpr size_t kGivensSmem = 48 * 1024;   // Givens step staged in shared memory up to this
+constexpr size_t kGivensSmem = 40 * 1024;   // Givens step staged in shared memory up to this
 // second Gram-Schmidt pass when ||w after||^2 < kReorthEta2 ||w before||^2
 // (0.01: more than 90% of the norm cancelled; on the bench drawing the
 // solve took 23.1 ms with the classical 1/2, 22.5 ms with 0.01 and 22.7 ms
@@ -135,79 +135,6 @@ __global__ void norm_finalize_kernel(const double *__restrict__ partial, int nch
     nrm[c] = sqrt(fmax(s, 0.0));
 }
 
-// The same update with the squares of the result summed per block and
-// channel, and (before != 0) those of w before the update too (blocks of
-// kOrthThreads = 3 x 64 elements, so an element's channel is its index mod
-// 3): npart[block][c] after, npart[block][3 + c] before.  skip: a second
-// pass that is not needed returns at once.
-constexpr int kOrthThreads = 192;
-__global__ void __launch_bounds__(kOrthThreads) orth_update_norm_kernel(const double *__restrict__ V, size_t vstride,
-                                                                         const double *__restrict__ h, int nj,
-                                                                         double *__restrict__ w, int N,
-                                                                         double *__restrict__ npart, int before,
-                                                                         const int *__restrict__ skip) {
-    if (skip && *skip) return;
-    __shared__ double sq[2][kOrthThreads];
-    const int t = blockIdx.x * kOrthThreads + threadIdx.x;
-    double a = 0.0, a0 = 0.0;
-    if (t < 3 * N) {
-        const int c = t % 3;
-        a = a0 = w[t];
-        int j = 0;
-        for (; j + 4 <= nj; j += 4) {
-            const double v0 = V[(size_t)j * vstride + t], v1 = V[(size_t)(j + 1) * vstride + t];
-            const double v2 = V[(size_t)(j + 2) * vstride + t], v3 = V[(size_t)(j + 3) * vstride + t];
-            a -= h[3 * j + c] * v0;
-            a -= h[3 * (j + 1) + c] * v1;
-            a -= h[3 * (j + 2) + c] * v2;
-            a -= h[3 * (j + 3) + c] * v3;
-        }
-        for (; j < nj; ++j) a -= h[3 * j + c] * V[(size_t)j * vstride + t];
-        w[t] = a;
-    }
-    sq[0][threadIdx.x] = a * a;
-    sq[1][threadIdx.x] = a0 * a0;
-    __syncthreads();
-    if (threadIdx.x < 3) {
-        double s = 0.0, s0 = 0.0;
-        for (int u = threadIdx.x; u < kOrthThreads; u += 3) {
-            s += sq[0][u];
-            s0 += sq[1][u];
-        }
-        npart[6 * blockIdx.x + threadIdx.x] = s;
-        if (before) npart[6 * blockIdx.x + 3 + threadIdx.x] = s0;
-    }
-}
-
-// nrm[c] = sqrt(sum over the blocks of npart[block][c]): warp c sums its
-// channel (lanes over blocks, then a fixed butterfly).  skip_out (first
-// pass): set when no channel's squared norm fell below kReorthEta2 times
-// its value before the projection, so that the second pass is not needed;
-// skip_in: a skipped second pass leaves nrm as it is.
-__global__ void npart_finalize_kernel(const double *__restrict__ npart, int nb, double *__restrict__ nrm,
-                                      int *__restrict__ skip_out, const int *__restrict__ skip_in) {
-    if (skip_in && *skip_in) return;
-    __shared__ int keep[3];
-    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (c < 3) {
-        double s = 0.0, s0 = 0.0;
-        for (int b = lane; b < nb; b += 32) {
-            s += npart[6 * b + c];
-            if (skip_out) s0 += npart[6 * b + 3 + c];
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-            s += __shfl_xor_sync(0xffffffffu, s, off);
-            s0 += __shfl_xor_sync(0xffffffffu, s0, off);
-        }
-        if (lane == 0) {
-            nrm[c] = sqrt(fmax(s, 0.0));
-            keep[c] = s >= kReorthEta2 * s0;
-        }
-    }
-    __syncthreads();
-    if (skip_out && threadIdx.x == 0) *skip_out = keep[0] && keep[1] && keep[2];
-}
-
 // out[i][c] = in[i][c] * (nrm[c] > 0 ? 1 / nrm[c] : 0)
 __global__ void scale_kernel(const double *__restrict__ in, const double *__restrict__ nrm,
                              double *__restrict__ out, int N, double *__restrict__ out2 = nullptr) {
@@ -257,49 +184,28 @@ __global__ void cycle_start_kernel(GivensState g, const double *__restrict__ bet
     g.resid[c] = beta[c];
 }
 
-// Column k of the Hessenberg matrix: hcol[0..k] and hnext; rotate, record.
-__global__ void givens_kernel(GivensState g, const double *__restrict__ hcol,
-                              const double *__restrict__ hnext, const double *__restrict__ thr,
-                              int k, int m) {
-    int c = threadIdx.x;
-    if (c >= 3 || !g.active[c]) return;
-    double *col = g.R + (size_t)c * m * m + (size_t)k * m;
-    for (int j = 0; j <= k; ++j) col[j] = hcol[3 * j + c];
-    double *cs = g.cs + c * m, *sn = g.sn + c * m, *e = g.e + c * (m + 1);
-    for (int j = 0; j < k; ++j) {
-        double a = col[j], b = col[j + 1];
-        col[j] = cs[j] * a + sn[j] * b;
-        col[j + 1] = -sn[j] * a + cs[j] * b;
-    }
-    double hn = hnext[c];
-    double den = hypot(col[k], hn);
-    double cc = (den > 0.0) ? col[k] / den : 1.0;
-    double ss = (den > 0.0) ? hn / den : 0.0;
-    cs[k] = cc;
-    sn[k] = ss;
-    col[k] = den;
-    e[k + 1] = -ss * e[k];
-    e[k] = cc * e[k];
-    double res = fabs(e[k + 1]);
-    g.resid[c] = res;
-    g.kc[c] = k + 1;
-    if (res <= thr[c] || !(hn > 0.0) || !(den > 0.0)) g.active[c] = 0;
-}
-
-// The same step with the column and the earlier rotations staged in shared
-// memory (one warp per channel: parallel loads, then the sequential chain).
-__global__ void givens_smem_kernel(GivensState g, const double *__restrict__ hcol,
-                                   const double *__restrict__ hnext, const double *__restrict__ thr,
-                                   int k, int m) {
-    extern __shared__ double gsm[];                  // [3][3][k + 1]
-    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (c >= 3 || !g.active[c]) return;
-    double *col = gsm + (size_t)c * 3 * (k + 1), *cs = col + (k + 1), *sn = cs + (k + 1);
+// One Givens step for channel c by one warp (lane 0 runs the sequential
+// chain), the new column and the earlier rotations staged in smem (3 (k + 1)
+// doubles) when it is given, else read from global memory.
+__device__ void givens_step_warp(GivensState g, const double *__restrict__ hcol, const double *__restrict__ hnext,
+                                 const double *__restrict__ thr, int k, int m, int c, int lane, double *smem) {
+    if (!g.active[c]) return;
     const double *gcs = g.cs + c * m, *gsn = g.sn + c * m;
-    for (int j = lane; j <= k; j += 32) col[j] = hcol[3 * j + c];
-    for (int j = lane; j < k; j += 32) {
-        cs[j] = gcs[j];
-        sn[j] = gsn[j];
+    double *col, *cs, *sn;
+    if (smem) {
+        col = smem;
+        cs = col + (k + 1);
+        sn = cs + (k + 1);
+        for (int j = lane; j <= k; j += 32) col[j] = hcol[3 * j + c];
+        for (int j = lane; j < k; j += 32) {
+            cs[j] = gcs[j];
+            sn[j] = gsn[j];
+        }
+    } else {
+        col = g.R + (size_t)c * m * m + (size_t)k * m;
+        cs = g.cs + c * m;
+        sn = g.sn + c * m;
+        for (int j = lane; j <= k; j += 32) col[j] = hcol[3 * j + c];
     }
     __syncwarp();
     if (lane == 0) {
@@ -324,8 +230,92 @@ __global__ void givens_smem_kernel(GivensState g, const double *__restrict__ hco
         if (res <= thr[c] || !(hn > 0.0) || !(den > 0.0)) g.active[c] = 0;
     }
     __syncwarp();
-    double *R = g.R + (size_t)c * m * m + (size_t)k * m;
-    for (int j = lane; j <= k; j += 32) R[j] = col[j];
+    if (smem) {
+        double *R = g.R + (size_t)c * m * m + (size_t)k * m;
+        for (int j = lane; j <= k; j += 32) R[j] = col[j];
+    }
+}
+
+constexpr int kOrthThreads = 192;   // 3 x 64 elements per block: an element's channel is its index mod 3
+
+// One Gram-Schmidt pass's update w -= V h with the squared norms of the
+// result (and, on the first pass, of w before it) summed per block; the last
+// block to finish (counter, which it resets) adds the block sums in block
+// order, sets hnext = ||w|| per channel, on the first pass decides whether
+// the second one is needed (skip), and runs the Givens step when this is the
+// last pass of the iteration.  pass 1 returns at once when skip is set.
+// Dynamic shared memory: 9 (k + 1) doubles for the Givens step, or none (the
+// step then works in global memory).
+__global__ void __launch_bounds__(kOrthThreads) orth_norm_givens_kernel(
+    const double *__restrict__ V, size_t vstride, const double *__restrict__ h, int nj, double *__restrict__ w,
+    int N, double *__restrict__ npart, int pass, int *__restrict__ skip, unsigned *__restrict__ counter,
+    double *__restrict__ hnext, GivensState g, const double *__restrict__ hcol, const double *__restrict__ thr,
+    int k, int m, int staged) {
+    if (pass == 1 && *skip) return;
+    extern __shared__ double gsm[];
+    __shared__ double sq[2][kOrthThreads];
+    __shared__ bool last;
+    __shared__ int keep[3];
+    const int t = blockIdx.x * kOrthThreads + threadIdx.x;
+    double a = 0.0, a0 = 0.0;
+    if (t < 3 * N) {
+        const int c = t % 3;
+        a = a0 = w[t];
+        int j = 0;
+        for (; j + 4 <= nj; j += 4) {
+            const double v0 = V[(size_t)j * vstride + t], v1 = V[(size_t)(j + 1) * vstride + t];
+            const double v2 = V[(size_t)(j + 2) * vstride + t], v3 = V[(size_t)(j + 3) * vstride + t];
+            a -= h[3 * j + c] * v0;
+            a -= h[3 * (j + 1) + c] * v1;
+            a -= h[3 * (j + 2) + c] * v2;
+            a -= h[3 * (j + 3) + c] * v3;
+        }
+        for (; j < nj; ++j) a -= h[3 * j + c] * V[(size_t)j * vstride + t];
+        w[t] = a;
+    }
+    sq[0][threadIdx.x] = a * a;
+    sq[1][threadIdx.x] = a0 * a0;
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double s1 = 0.0, s0 = 0.0;
+        for (int u = threadIdx.x; u < kOrthThreads; u += 3) {
+            s1 += sq[0][u];
+            s0 += sq[1][u];
+        }
+        npart[6 * blockIdx.x + threadIdx.x] = s1;
+        npart[6 * blockIdx.x + 3 + threadIdx.x] = s0;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1u;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (c < 3) {
+        double s1 = 0.0, s0 = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) {
+            s1 += __ldcg(npart + 6 * b + c);
+            s0 += __ldcg(npart + 6 * b + 3 + c);
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+            s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+        }
+        if (lane == 0) {
+            hnext[c] = sqrt(fmax(s1, 0.0));
+            keep[c] = s1 >= kReorthEta2 * s0;
+        }
+    }
+    __syncthreads();
+    bool givens = true;
+    if (pass == 0) {
+        givens = keep[0] && keep[1] && keep[2];   // no second pass: this is the last
+        if (threadIdx.x == 0) *skip = givens ? 1 : 0;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    __threadfence();
+    if (givens && c < 3) givens_step_warp(g, hcol, hnext, thr, k, m, c, lane, staged ? gsm + (size_t)c * 3 * (k + 1) : nullptr);
 }
 
 // Back substitution R y = e for each channel (kc[c] columns).
@@ -390,7 +380,7 @@ struct GmresWork {
         DC_TRY(r.alloc((size_t)N * 3));
         DC_TRY(Ax.alloc((size_t)N * 3));
         DC_TRY(partial.alloc((size_t)(m + 1) * nchunk * 3));
-        DC_TRY(count.alloc((size_t)(m + 1)));
+        DC_TRY(count.alloc((size_t)(m + 2)));   // gs_dots columns, then the orth_norm_givens counter
         DC_TRY(npart.alloc((size_t)6 * ((3 * (size_t)N + kOrthThreads - 1) / kOrthThreads)));
         DC_TRY(hcol.alloc((size_t)(m + 1) * 3));
         DC_TRY(hpass.alloc((size_t)(m + 1) * 3));
@@ -618,28 +608,21 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
             // ||w|| per channel; the second pass runs only when the first
             // one cancelled too much of w (its kernels read the flag)
             int *skip = W.flags.ptr + 6;   // after active[3], kc[3]
+            const size_t gsm = (size_t)9 * (k + 1) * sizeof(double);
+            const int staged = gsm <= kGivensSmem ? 1 : 0;
+            const int nb = (3 * N + kOrthThreads - 1) / kOrthThreads;
             for (int pass = 0; pass < 2; ++pass) {
                 dim3 grid(W.nchunk, k + 1);
                 gs_dots_kernel<<<grid, kDotThreads, 0, st>>>(W.V.ptr, vs, wv, N, W.nchunk, W.partial.ptr,
                                                              W.count.ptr, W.hpass.ptr, W.hcol.ptr, pass == 0,
                                                              pass == 0 ? nullptr : skip);
-                note_launch();
-                const int nb = (3 * N + kOrthThreads - 1) / kOrthThreads;
-                orth_update_norm_kernel<<<nb, kOrthThreads, 0, st>>>(W.V.ptr, vs, W.hpass.ptr, k + 1, wv, N,
-                                                                     W.npart.ptr, pass == 0,
-                                                                     pass == 0 ? nullptr : skip);
-                note_launch();
-                npart_finalize_kernel<<<1, 96, 0, st>>>(W.npart.ptr, nb, W.hnext.ptr, pass == 0 ? skip : nullptr,
-                                                        pass == 0 ? nullptr : skip);
-                note_launch();
+                orth_norm_givens_kernel<<<nb, kOrthThreads, staged ? gsm : 0, st>>>(
+                    W.V.ptr, vs, W.hpass.ptr, k + 1, wv, N, W.npart.ptr, pass, skip, W.count.ptr + (m + 1),
+                    W.hnext.ptr, gs, W.hcol.ptr, thr, k, m, staged);
+                note_launch(2);
             }
             scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(wv, W.hnext.ptr, W.V.ptr + (size_t)(k + 1) * vs, N,
-                                                               bufs ? in_buf : nullptr); note_launch();
-            const size_t gsm = (size_t)9 * (k + 1) * sizeof(double);
-            if (gsm <= kGivensSmem)
-                givens_smem_kernel<<<1, 96, gsm, st>>>(gs, W.hcol.ptr, W.hnext.ptr, thr, k, m);
-            else
-                givens_kernel<<<1, 32, 0, st>>>(gs, W.hcol.ptr, W.hnext.ptr, thr, k, m);
+                                                               bufs ? in_buf : nullptr);
             note_launch();
             total++;
             const int slot = k % kPollRing;

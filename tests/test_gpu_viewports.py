@@ -57,3 +57,34 @@ def test_64_uneven_viewports_in_one_call(dcmod, cuda_ok, oracle_mod, form, tol):
         off += npx
     print(f"{form}: {len(vps)} viewports, {n} pixels, max error on sampled pixels {max(errs):.2e}")
     assert max(errs) <= tol
+
+
+def test_render_replays_under_cuda_graph_capture(dcmod, cuda_ok):
+    """After a first call has planned the tiles, a render of the same
+    viewports issues only asynchronous work on the context's stream: it can
+    be captured into a CUDA graph (the FP64 passes, the FP32 copies of the
+    expansions and the one evaluation launch over all viewports) and
+    replayed; the replay reproduces the direct render bit for bit."""
+    import torch
+    d = drawing_by_name("mixed16")
+    s = torch.cuda.Stream()
+    ctx = dcmod.Context(stream=s.cuda_stream, form="fmm32", g=d.g, s_per_panel=d.s_per_panel, leaf_size=32,
+                        gmres_tol=1e-10, gmres_restart=300)
+    ctx.build_drawing(d)
+    ctx.solve_density()
+    vps = viewports(64, seed=62)
+    n = sum(v[4] * v[5] for v in vps)
+    direct = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(s):
+        ctx.render_viewport(vps, direct)                 # plans the tiles
+    s.synchronize()
+    out = torch.full((n, 3), float("nan"), dtype=torch.float32, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ctx.render_viewport(vps, out)
+    out.fill_(float("nan"))
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all()
+    assert torch.equal(out, direct)
