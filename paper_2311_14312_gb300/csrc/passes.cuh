@@ -893,6 +893,10 @@ static __global__ void rows_to_ff_kernel(const double2 *__restrict__ in, float4 
 }
 
 constexpr int kM2LffWarps = 8;
+#ifndef DC_M2LFF_FULL
+#define DC_M2LFF_FULL 12
+#endif
+constexpr int kM2LffFull = DC_M2LFF_FULL;   // source moments summed in float-float; the rest in FP32
 
 inline size_t m2l_ff_smem(int P1) {
     return (7 * (size_t)P1 * P1 + kM2LffWarps * 2 * 3 * 32) * sizeof(float4);
@@ -956,14 +960,30 @@ static __global__ void __launch_bounds__(32 * kM2LffWarps) m2l_ff_kernel(TreeVie
             __syncwarp();
             if (e + 1 < e1) fetch(e + 1);
             float4 part[3] = {zero, zero, zero};
+            float2 tail[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             const float4 *Tb = B + (size_t)b * P1 * P1;
-            for (int k = 0; k < P1; ++k) {
+            const int kff = min(P1, kM2LffFull);
+            for (int k = 0; k < kff; ++k) {
                 const float4 tk = Tb[k * P1 + lr];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) ff_cfma(part[c], tk, cur[c * P1 + k]);
             }
+            // moments k >= kM2LffFull in FP32: their terms carry at most a few
+            // 1e-6 of the sum (the source moments of a well-separated cell
+            // fall off like (sqrt(2) / 4)^k against the first), so FP32
+            // rounding of them stays near 1e-14 of the result
+            for (int k = kff; k < P1; ++k) {
+                const float4 tk = Tb[k * P1 + lr];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float4 m = cur[c * P1 + k];
+                    tail[c].x = fmaf(tk.x, m.x, fmaf(-tk.y, m.y, tail[c].x));
+                    tail[c].y = fmaf(tk.x, m.y, fmaf(tk.y, m.x, tail[c].y));
+                }
+            }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
+                ff_cadd(part[c], make_float4(tail[c].x, tail[c].y, 0.f, 0.f));
                 float4 v = cj ? ff_conj(part[c]) : part[c];
                 ff_cadd(acc[c], ff_rot(v, r * lane));
             }
