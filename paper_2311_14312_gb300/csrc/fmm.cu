@@ -591,11 +591,6 @@ cudaError_t Fmm::Impl::build_rows(cudaStream_t st) {
         if ((e = p2m_g32.alloc((size_t)np * P1i)) != cudaSuccess) return e;
         narrow_rows_kernel<<<4 * n_sms, 256, 0, st>>>(p2m_g64.ptr, P1, p2m_g32.ptr, P1i, np);
         note_launch();
-        if (p2l_rows > 0) {   // the inner operator's P2L from rows too (single layer)
-            if ((e = p2l_g32.alloc((size_t)p2l_rows * P1i)) != cudaSuccess) return e;
-            narrow_rows_kernel<<<4 * n_sms, 256, 0, st>>>(p2l_g64.ptr, P1, p2l_g32.ptr, P1i, p2l_rows);
-            note_launch();
-        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // the FP64 passes read the rows as float-float (same size)

@@ -664,10 +664,8 @@ cudaError_t Fmm::Impl::passes32(const float *sb, const float *mb, int use_s, int
         note_launch();
     }
     if (sc.n_p2l > 0) {
-        const bool rows = rows_ready && !use_m && p2l_g32.ptr;   // stored single-layer rows
         passes::p2l_flat_kernel<float, passes::PiecesF32><<<sc.n_p2l, passes::kChunk, passes::p2l_flat_smem<float>(P1), st>>>(
-            tv, ps, sc.p2l.ptr, p2l_off.ptr, p2l_cnt.ptr, p2l_item.ptr, sb, mb, use_s, use_m, P1, Lm2l32i.ptr,
-            rows ? p2l_g32.ptr : nullptr);
+            tv, ps, sc.p2l.ptr, p2l_off.ptr, p2l_cnt.ptr, p2l_item.ptr, sb, mb, use_s, use_m, P1, Lm2l32i.ptr);
         note_launch();
     }
     if (sc.n_walk > 0) {

@@ -118,7 +118,7 @@ struct Fmm::Impl {
     DevBuf<int2> p2l_item;        // [p2l_rows] (piece, list-4 entry), row order
     DevBuf<double2> p2m_g64, p2m_f64, p2l_g64, p2l_f64;   // FP64 rows while they are built
     DevBuf<float4> p2m_gff, p2m_fff, p2l_gff, p2l_fff;    // the same rows in float-float
-    DevBuf<float2> p2m_g32, p2l_g32;   // single-layer rows at order p_inner (FP32 inner operator)
+    DevBuf<float2> p2m_g32;
     cudaError_t build_rows(cudaStream_t st);
     // FP64 tables and expansions
     DevBuf<double2> m2m, l2l, m2l, M, L;
