@@ -222,11 +222,23 @@ __global__ void __launch_bounds__(128) coarse_solve_kernel(const float *__restri
     const int i = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
     const float *row = Ainv + (size_t)i * n_pad;
     float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
-    for (int j = t; j < P; j += 128) {
-        const float wj = row[j];
-        dot2_step(h0, l0, wj, s[3 * j]);
-        dot2_step(h1, l1, wj, s[3 * j + 1]);
-        dot2_step(h2, l2, wj, s[3 * j + 2]);
+    for (int j0 = t; j0 < P; j0 += 4 * 128) {
+        // four columns' loads in flight per thread (a missing column adds exact zeros)
+        float wv[4];
+        float2 xv[4][3];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + 128 * u;
+            const bool ok = j < P;
+            wv[u] = ok ? row[j] : 0.f;
+            for (int c = 0; c < 3; ++c) xv[u][c] = ok ? s[3 * j + c] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            dot2_step(h0, l0, wv[u], xv[u][0]);
+            dot2_step(h1, l1, wv[u], xv[u][1]);
+            dot2_step(h2, l2, wv[u], xv[u][2]);
+        }
     }
     double a0 = (double)h0 + (double)l0, a1 = (double)h1 + (double)l1, a2 = (double)h2 + (double)l2;
     for (int off = 16; off > 0; off >>= 1) {
@@ -331,7 +343,18 @@ __global__ void __launch_bounds__(kPanelThreads) panel_apply_kernel(
         const size_t a = (size_t)i * g + m;
         double acc = 0.0;
         for (int q = 0; q < kSplit; ++q) acc += part[((size_t)q * N + a) * 3 + c];
-        for (int e = nptr[i]; e < nptr[i + 1]; ++e) acc += corr[(size_t)e * g + m] * y[3 * pairs[e].y + c];
+        for (int e0 = nptr[i]; e0 < nptr[i + 1]; e0 += 4) {   // four pairs' loads in flight
+            double cv[4], yv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u;
+                const bool ok = e < nptr[i + 1];
+                cv[u] = ok ? corr[(size_t)e * g + m] : 0.0;
+                yv[u] = ok ? y[3 * pairs[e].y + c] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc += cv[u] * yv[u];
+        }
         rs[t] = v[3 * a + c] - acc;
     }
     __syncthreads();

@@ -102,21 +102,30 @@ __global__ void interp32_kernel(const float2 *__restrict__ lam, const double *__
 constexpr double kBigCoef = 50.0;
 __global__ void big_coef_kernel(const double2 *__restrict__ L, const double2 *__restrict__ M, int n,
                                 int P1, unsigned char *__restrict__ hL, unsigned char *__restrict__ hM) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per cell, lanes over the coefficients (coalesced); magnitudes in FP32, since this
+    // is a threshold test and FP64 hypot runs at 1/64 of the FP32 rate
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (c >= n) return;
-    double bl = 0.0, bm = 0.0;
+    float bl = 0.f, bm = 0.f;
     for (int ch = 0; ch < 3; ++ch) {
         const double2 *l = L + ((size_t)c * 3 + ch) * P1, *m = M + ((size_t)c * 3 + ch) * P1;
-        double sl = 0.0, sm = 9.0 * hypot(m[0].x, m[0].y);
-        for (int k = 0; k < P1; ++k) {
-            sl += hypot(l[k].x, l[k].y);
-            sm += hypot(m[k].x, m[k].y);
+        float sl = 0.f, sm = 0.f;
+        for (int k = lane; k < P1; k += 32) {
+            const double2 lk = l[k], mk = m[k];
+            sl += hypotf((float)lk.x, (float)lk.y);
+            sm += (k == 0 ? 10.f : 1.f) * hypotf((float)mk.x, (float)mk.y);
         }
-        bl = fmax(bl, sl);
-        bm = fmax(bm, sm);
+        for (int o = 16; o > 0; o >>= 1) {
+            sl += __shfl_xor_sync(0xffffffffu, sl, o);
+            sm += __shfl_xor_sync(0xffffffffu, sm, o);
+        }
+        bl = fmaxf(bl, sl);
+        bm = fmaxf(bm, sm);
     }
-    hL[c] = bl > kBigCoef;
-    hM[c] = bm > kBigCoef;
+    if (lane == 0) {
+        hL[c] = bl > kBigCoef;
+        hM[c] = bm > kBigCoef;
+    }
 }
 
 template <typename From, typename To>
@@ -693,7 +702,7 @@ cudaError_t Fmm::Impl::prepare_render32(const double *sb, const double *mb, cuda
         note_launch();
     }
     int nC = tree.n_cells();
-    big_coef_kernel<<<(nC + th - 1) / th, th, 0, st>>>(L.ptr, M.ptr, nC, P1, heavyL.ptr, heavyM.ptr);
+    big_coef_kernel<<<(unsigned)(((size_t)nC * 32 + th - 1) / th), th, 0, st>>>(L.ptr, M.ptr, nC, P1, heavyL.ptr, heavyM.ptr);
     note_launch();
     return cudaGetLastError();
 }
