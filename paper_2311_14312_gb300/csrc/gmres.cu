@@ -1,8 +1,9 @@
 // K8: restarted GMRES on the device for the three colour channels at once
 // (Sec. 5.5: x = GMRES(f, x0, y, eps) with the FMM or dense operator as f).
 //
-// Each channel has its own Krylov space; vectors are [N][3] FP64 with the
-// channel fastest.  Arnoldi uses classical Gram-Schmidt with a second
+// Each channel has its own Krylov space; vectors are [N][3] with the channel
+// fastest, FP64 except the basis of inner solves of a refinement, which is
+// kept in FP32 (their tolerance is far above FP32 rounding).  Arnoldi uses classical Gram-Schmidt with a second
 // (re-orthogonalisation) pass when the first one cancelled more than 90% of
 // the vector's norm in some channel (a looser form of the criterion of
 // Daniel, Gragg, Kaufman and Stewart; the flag is set and read on the
@@ -39,6 +40,10 @@ constexpr size_t kGivensSmem = 40 * 1024;   // Givens step staged in shared memo
 #define DC_REORTH_ETA2 0.01
 #endif
 constexpr double kReorthEta2 = DC_REORTH_ETA2;
+#ifndef DC_BASIS32_MIN_TOL
+#define DC_BASIS32_MIN_TOL 1e-6
+#endif
+constexpr double kBasis32MinTol = DC_BASIS32_MIN_TOL;   // FP32 Krylov basis from this tolerance up
 
 // partial[(j * nchunk + chunk) * 3 + c] = sum over rows of the chunk of
 // V_j[i][c] * w[i][c]
@@ -73,7 +78,8 @@ __global__ void dots_partial_kernel(const double *__restrict__ V, size_t vstride
 // last block of column j to finish (counted in count[j], which it resets)
 // adds the partials in chunk order into hpass[j] and the Hessenberg column
 // hcol[j] (= hpass on the first pass, += on the second).  Deterministic.
-__global__ void __launch_bounds__(kDotThreads) gs_dots_kernel(const double *__restrict__ V, size_t vstride,
+template <typename B>
+__global__ void __launch_bounds__(kDotThreads) gs_dots_kernel(const B *__restrict__ V, size_t vstride,
                                                               const double *__restrict__ w, int N, int nchunk,
                                                               double *__restrict__ partial,
                                                               unsigned *__restrict__ count,
@@ -81,11 +87,13 @@ __global__ void __launch_bounds__(kDotThreads) gs_dots_kernel(const double *__re
                                                               int first, const int *__restrict__ skip) {
     if (skip && *skip) return;   // a second pass that is not needed
     const int chunk = blockIdx.x, j = blockIdx.y;
-    const double *v = V + (size_t)j * vstride;
+    const B *v = V + (size_t)j * vstride;
     const int lo = chunk * kChunk, hi = min(N, lo + kChunk);
-    double a[3] = {0.0, 0.0, 0.0};
+    // a thread's few products are summed in the basis type, the rest in FP64
+    B ab[3] = {B(0), B(0), B(0)};
     for (int i = lo + threadIdx.x; i < hi; i += kDotThreads)
-        for (int c = 0; c < 3; ++c) a[c] += v[3 * (size_t)i + c] * w[3 * (size_t)i + c];
+        for (int c = 0; c < 3; ++c) ab[c] += v[3 * (size_t)i + c] * (B)w[3 * (size_t)i + c];
+    double a[3] = {(double)ab[0], (double)ab[1], (double)ab[2]};
     __shared__ double red[kDotThreads / 32][3];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -135,7 +143,8 @@ __global__ void norm_finalize_kernel(const double *__restrict__ partial, int nch
     nrm[c] = sqrt(fmax(s, 0.0));
 }
 
-// out[i][c] = in[i][c] * (nrm[c] > 0 ? 1 / nrm[c] : 0)
+// out[i][c] = in[i][c] / nrm[c] (0 where nrm[c] is 0); out2, the operator's
+// input buffer when it has one, gets the same (stored) value
 __global__ void scale_kernel(const double *__restrict__ in, const double *__restrict__ nrm,
                              double *__restrict__ out, int N, double *__restrict__ out2 = nullptr) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -144,7 +153,24 @@ __global__ void scale_kernel(const double *__restrict__ in, const double *__rest
     double n = nrm[c];
     const double v = (n > 0.0) ? in[t] / n : 0.0;
     out[t] = v;
-    if (out2) out2[t] = v;   // the operator's input buffer, when it has one
+    if (out2) out2[t] = v;
+}
+
+// The same for an FP32 basis: one reciprocal per channel and block, the
+// element rounded to FP32 and the operator's buffer given that FP32 value
+__global__ void scale32_kernel(const double *__restrict__ in, const double *__restrict__ nrm,
+                               float *__restrict__ out, int N, double *__restrict__ out2) {
+    __shared__ double inv[3];
+    if (threadIdx.x < 3) {
+        const double n = nrm[threadIdx.x];
+        inv[threadIdx.x] = n > 0.0 ? 1.0 / n : 0.0;
+    }
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * N) return;
+    const float v = (float)(in[t] * inv[t % 3]);
+    out[t] = v;
+    if (out2) out2[t] = (double)v;
 }
 
 // r = b - Ax
@@ -246,8 +272,9 @@ constexpr int kOrthThreads = 192;   // 3 x 64 elements per block: an element's c
 // last pass of the iteration.  pass 1 returns at once when skip is set.
 // Dynamic shared memory: 9 (k + 1) doubles for the Givens step, or none (the
 // step then works in global memory).
+template <typename B>
 __global__ void __launch_bounds__(kOrthThreads) orth_norm_givens_kernel(
-    const double *__restrict__ V, size_t vstride, const double *__restrict__ h, int nj, double *__restrict__ w,
+    const B *__restrict__ V, size_t vstride, const double *__restrict__ h, int nj, double *__restrict__ w,
     int N, double *__restrict__ npart, int pass, int *__restrict__ skip, unsigned *__restrict__ counter,
     double *__restrict__ hnext, GivensState g, const double *__restrict__ hcol, const double *__restrict__ thr,
     int k, int m, int staged) {
@@ -261,16 +288,31 @@ __global__ void __launch_bounds__(kOrthThreads) orth_norm_givens_kernel(
     if (t < 3 * N) {
         const int c = t % 3;
         a = a0 = w[t];
-        int j = 0;
-        for (; j + 4 <= nj; j += 4) {
-            const double v0 = V[(size_t)j * vstride + t], v1 = V[(size_t)(j + 1) * vstride + t];
-            const double v2 = V[(size_t)(j + 2) * vstride + t], v3 = V[(size_t)(j + 3) * vstride + t];
-            a -= h[3 * j + c] * v0;
-            a -= h[3 * (j + 1) + c] * v1;
-            a -= h[3 * (j + 2) + c] * v2;
-            a -= h[3 * (j + 3) + c] * v3;
+        if constexpr (sizeof(B) == 8) {
+            int j = 0;
+            for (; j + 4 <= nj; j += 4) {
+                const double v0 = V[(size_t)j * vstride + t], v1 = V[(size_t)(j + 1) * vstride + t];
+                const double v2 = V[(size_t)(j + 2) * vstride + t], v3 = V[(size_t)(j + 3) * vstride + t];
+                a -= h[3 * j + c] * v0;
+                a -= h[3 * (j + 1) + c] * v1;
+                a -= h[3 * (j + 2) + c] * v2;
+                a -= h[3 * (j + 3) + c] * v3;
+            }
+            for (; j < nj; ++j) a -= h[3 * j + c] * V[(size_t)j * vstride + t];
+        } else {
+            // FP32 basis: (V h)[t] summed in FP32, eight loads in flight
+            float sv = 0.f;
+            int j = 0;
+            for (; j + 8 <= nj; j += 8) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = V[(size_t)(j + u) * vstride + t];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) sv = fmaf((float)h[3 * (j + u) + c], v[u], sv);
+            }
+            for (; j < nj; ++j) sv = fmaf((float)h[3 * j + c], V[(size_t)j * vstride + t], sv);
+            a -= (double)sv;
         }
-        for (; j < nj; ++j) a -= h[3 * j + c] * V[(size_t)j * vstride + t];
         w[t] = a;
     }
     sq[0][threadIdx.x] = a * a;
@@ -336,7 +378,8 @@ __global__ void backsolve_kernel(GivensState g, int m) {
 }
 
 // x[i][c] += sum_{j < kc[c]} y[c][j] V_j[i][c]
-__global__ void solution_update_kernel(GivensState g, const double *__restrict__ V, size_t vstride,
+template <typename B>
+__global__ void solution_update_kernel(GivensState g, const B *__restrict__ V, size_t vstride,
                                        double *__restrict__ x, int N, int m) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -344,7 +387,7 @@ __global__ void solution_update_kernel(GivensState g, const double *__restrict__
         int n = g.kc[c];
         const double *y = g.y + c * m;
         double a = x[3 * (size_t)i + c];
-        for (int j = 0; j < n; ++j) a += y[j] * V[(size_t)j * vstride + 3 * (size_t)i + c];
+        for (int j = 0; j < n; ++j) a += y[j] * (double)V[(size_t)j * vstride + 3 * (size_t)i + c];
         x[3 * (size_t)i + c] = a;
     }
 }
@@ -354,6 +397,7 @@ __global__ void solution_update_kernel(GivensState g, const double *__restrict__
 struct GmresWork {
     int N = 0, m = 0, nchunk = 0;
     DevBuf<double> V, w, r, Ax, partial, hcol, hpass, hnext, small, npart;
+    DevBuf<float> V32;   // the basis of solves that keep it in FP32
     DevBuf<double> R, cs, sn, e, y;
     DevBuf<int> flags;
     DevBuf<unsigned> count;   // [m + 1] blocks done per column (gs_dots_kernel), kept at zero
@@ -376,6 +420,7 @@ struct GmresWork {
     if ((e_ = (x)) != cudaSuccess) \
         return e_;
         DC_TRY(V.alloc((size_t)(m + 1) * N * 3));
+        DC_TRY(V32.alloc((size_t)(m + 1) * N * 3));
         DC_TRY(w.alloc((size_t)N * 3));
         DC_TRY(r.alloc((size_t)N * 3));
         DC_TRY(Ax.alloc((size_t)N * 3));
@@ -542,6 +587,13 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
     if ((ce = cudaMemcpyAsync(thr, hthr, 3 * sizeof(double), cudaMemcpyHostToDevice, st)) !=
         cudaSuccess)
         return ce;
+    // An inner solve (stopped by the Givens estimate at a tolerance far above
+    // FP32 rounding, on an operator with its own input / output buffers)
+    // keeps its basis in FP32: half the bytes, and the Gram-Schmidt products
+    // at the FP32 rate; the operator is applied to the stored FP32 vectors,
+    // so the Arnoldi relation holds for them.  Other solves keep FP64.
+    const bool bufs = A.in_buffer() && A.out_buffer();
+    const bool b32 = bufs && trust_estimate && tol >= kBasis32MinTol;
     int total = 0;
     bool done_all = false;
     // a cycle that ends with every channel converged by the Givens estimate
@@ -594,9 +646,9 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
         // an operator with its own input / output buffers reads v_k from the
         // former (written by the scale kernels) and leaves A v_k in the latter
         double *in_buf = A.in_buffer(), *out_buf = A.out_buffer();
-        const bool bufs = in_buf && out_buf;
         double *wv = bufs ? out_buf : W.w.ptr;
-        scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.r.ptr, beta, W.V.ptr, N, bufs ? in_buf : nullptr);
+        if (b32) scale32_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.r.ptr, beta, W.V32.ptr, N, in_buf);
+        else scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(W.r.ptr, beta, W.V.ptr, N, bufs ? in_buf : nullptr);
         note_launch();
         int k = 0;
         for (; k < m && total < max_iter; ++k) {
@@ -613,16 +665,29 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
             const int nb = (3 * N + kOrthThreads - 1) / kOrthThreads;
             for (int pass = 0; pass < 2; ++pass) {
                 dim3 grid(W.nchunk, k + 1);
-                gs_dots_kernel<<<grid, kDotThreads, 0, st>>>(W.V.ptr, vs, wv, N, W.nchunk, W.partial.ptr,
-                                                             W.count.ptr, W.hpass.ptr, W.hcol.ptr, pass == 0,
-                                                             pass == 0 ? nullptr : skip);
-                orth_norm_givens_kernel<<<nb, kOrthThreads, staged ? gsm : 0, st>>>(
-                    W.V.ptr, vs, W.hpass.ptr, k + 1, wv, N, W.npart.ptr, pass, skip, W.count.ptr + (m + 1),
-                    W.hnext.ptr, gs, W.hcol.ptr, thr, k, m, staged);
+                if (b32) {
+                    gs_dots_kernel<float><<<grid, kDotThreads, 0, st>>>(
+                        W.V32.ptr, vs, wv, N, W.nchunk, W.partial.ptr, W.count.ptr, W.hpass.ptr, W.hcol.ptr,
+                        pass == 0, pass == 0 ? nullptr : skip);
+                    orth_norm_givens_kernel<float><<<nb, kOrthThreads, staged ? gsm : 0, st>>>(
+                        W.V32.ptr, vs, W.hpass.ptr, k + 1, wv, N, W.npart.ptr, pass, skip, W.count.ptr + (m + 1),
+                        W.hnext.ptr, gs, W.hcol.ptr, thr, k, m, staged);
+                } else {
+                    gs_dots_kernel<double><<<grid, kDotThreads, 0, st>>>(
+                        W.V.ptr, vs, wv, N, W.nchunk, W.partial.ptr, W.count.ptr, W.hpass.ptr, W.hcol.ptr,
+                        pass == 0, pass == 0 ? nullptr : skip);
+                    orth_norm_givens_kernel<double><<<nb, kOrthThreads, staged ? gsm : 0, st>>>(
+                        W.V.ptr, vs, W.hpass.ptr, k + 1, wv, N, W.npart.ptr, pass, skip, W.count.ptr + (m + 1),
+                        W.hnext.ptr, gs, W.hcol.ptr, thr, k, m, staged);
+                }
                 note_launch(2);
             }
-            scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(wv, W.hnext.ptr, W.V.ptr + (size_t)(k + 1) * vs, N,
-                                                               bufs ? in_buf : nullptr);
+            if (b32)
+                scale32_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(wv, W.hnext.ptr,
+                                                                     W.V32.ptr + (size_t)(k + 1) * vs, N, in_buf);
+            else
+                scale_kernel<<<(3 * N + th - 1) / th, th, 0, st>>>(wv, W.hnext.ptr, W.V.ptr + (size_t)(k + 1) * vs,
+                                                                   N, bufs ? in_buf : nullptr);
             note_launch();
             total++;
             const int slot = k % kPollRing;
@@ -644,7 +709,9 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
             }
         }
         backsolve_kernel<<<1, 32, 0, st>>>(gs, m); note_launch();
-        solution_update_kernel<<<(N + th - 1) / th, th, 0, st>>>(gs, W.V.ptr, vs, x, N, m); note_launch();
+        if (b32) solution_update_kernel<float><<<(N + th - 1) / th, th, 0, st>>>(gs, W.V32.ptr, vs, x, N, m);
+        else solution_update_kernel<double><<<(N + th - 1) / th, th, 0, st>>>(gs, W.V.ptr, vs, x, N, m);
+        note_launch();
         int hkc[3];
         if ((ce = cudaMemcpyAsync(hkc, gs.kc, 3 * sizeof(int), cudaMemcpyDeviceToHost, st)) !=
             cudaSuccess)
