@@ -31,6 +31,7 @@ constexpr int kChunk = 1024;     // rows per partial dot-product block
 constexpr int kDotThreads = 256;
 constexpr int kPollRing = 4;     // pinned flag slots / events
 constexpr int kPollLag = 1;      // iterations between enqueue and flag read
+constexpr double kPredictMargin = 4.0;   // see the convergence look-ahead in gmres_solve
 constexpr size_t kGivensSmem = 40 * 1024;   // Givens step staged in shared memory up to this
 // second Gram-Schmidt pass when ||w after||^2 < kReorthEta2 ||w before||^2
 // (0.01: more than 90% of the norm cancelled; on the bench drawing the
@@ -403,10 +404,12 @@ struct GmresWork {
     DevBuf<unsigned> count;   // [m + 1] blocks done per column (gs_dots_kernel), kept at zero
     double *host = nullptr;   // pinned: resid[3], active-as-double[3], norms[3]
     int *poll = nullptr;      // pinned [kPollRing][3] copies of the active flags
+    double *pollr = nullptr;  // pinned [kPollRing][3] copies of the residual estimates
     cudaEvent_t ev[kPollRing] = {};
     ~GmresWork() {
         if (host) cudaFreeHost(host);
         if (poll) cudaFreeHost(poll);
+        if (pollr) cudaFreeHost(pollr);
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
     }
@@ -439,6 +442,7 @@ struct GmresWork {
         DC_TRY(flags.alloc(8));
         if (!host) DC_TRY(cudaMallocHost(reinterpret_cast<void **>(&host), 16 * sizeof(double)));
         if (!poll) DC_TRY(cudaMallocHost(reinterpret_cast<void **>(&poll), kPollRing * 3 * sizeof(int)));
+        if (!pollr) DC_TRY(cudaMallocHost(reinterpret_cast<void **>(&pollr), kPollRing * 3 * sizeof(double)));
         for (auto &e : ev)
             if (!e) DC_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 #undef DC_TRY
@@ -694,6 +698,9 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
             if ((ce = cudaMemcpyAsync(W.poll + 3 * slot, gs.active, 3 * sizeof(int),
                                       cudaMemcpyDeviceToHost, st)) != cudaSuccess)
                 return ce;
+            if (trust_estimate && (ce = cudaMemcpyAsync(W.pollr + 3 * slot, gs.resid, 3 * sizeof(double),
+                                                        cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                return ce;
             if ((ce = cudaEventRecord(W.ev[slot], st)) != cudaSuccess) return ce;
             // flags of iteration k - kPollLag (slot reuse is safe: it was read
             // kPollLag iterations ago, before this iteration was enqueued)
@@ -705,6 +712,28 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
                 if (!f[0] && !f[1] && !f[2]) {
                     est_done = true;
                     break;
+                }
+                // When the estimates of iterations done - 1 and done, extrapolated
+                // geometrically, put every active channel within kPredictMargin of
+                // its threshold at iteration k, wait for k before enqueuing k + 1:
+                // a wrong guess costs one host round trip, a right one saves an
+                // iteration that would only be discarded.
+                if (trust_estimate && done >= 1 && k + 1 < m && total < max_iter) {
+                    const double *r1 = W.pollr + 3 * ps, *r0 = W.pollr + 3 * ((done - 1) % kPollRing);
+                    bool near = true;
+                    for (int c = 0; c < 3; ++c) {
+                        if (!f[c]) continue;
+                        const double q = r0[c] > 0.0 ? fmin(1.0, r1[c] / r0[c]) : 1.0;
+                        if (!(r1[c] * q <= kPredictMargin * hthr[c])) near = false;
+                    }
+                    if (near) {
+                        if ((ce = cudaEventSynchronize(W.ev[slot])) != cudaSuccess) return ce;
+                        const int *fk = W.poll + 3 * slot;
+                        if (!fk[0] && !fk[1] && !fk[2]) {
+                            est_done = true;
+                            break;
+                        }
+                    }
                 }
             }
         }

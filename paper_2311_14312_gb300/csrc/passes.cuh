@@ -736,7 +736,16 @@ static __global__ void __launch_bounds__(128) l2l_ff_kernel(TreeView<double> t, 
     for (int c = 0; c < 3; ++c) acc[c] = ff_from(Lm2l[((size_t)cell * 3 + c) * P1 + l]);
     if (up) {
         const float4 *Tq = tab + ((size_t)t.quad[cell] * P1 + l) * P1;
-        for (int k = l; k < P1; ++k) {
+        int k = l;
+        for (; k + 4 <= P1; k += 4) {   // four table loads in flight
+            float4 tq[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) tq[u] = Tq[k + u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                for (int c = 0; c < 3; ++c) ff_cfma(acc[c], tq[u], sp[w][c * P1 + k + u]);
+        }
+        for (; k < P1; ++k) {
             const float4 tq = Tq[k];
             for (int c = 0; c < 3; ++c) ff_cfma(acc[c], tq, sp[w][c * P1 + k]);
         }
