@@ -270,9 +270,15 @@ __global__ void __launch_bounds__(128) coarse_solve_kernel(const float *__restri
 // panels staged in shared memory), added in order by residual_kernel.  Each
 // thread takes kMonoNodes nodes, so one pair of shared-memory loads serves
 // kMonoNodes logarithms.
+#ifndef DC_MONO_SPLIT
+#define DC_MONO_SPLIT 8
+#endif
+#ifndef DC_MONO_NODES
+#define DC_MONO_NODES 2
+#endif
 constexpr int kTile = 256;
-constexpr int kSplit = 8;
-constexpr int kMonoNodes = 2;
+constexpr int kSplit = DC_MONO_SPLIT;
+constexpr int kMonoNodes = DC_MONO_NODES;
 constexpr int kMonoThreads = 128;
 __global__ void __launch_bounds__(kMonoThreads) monopole_kernel(const float2 *__restrict__ q32,
                                                                 const float4 *__restrict__ pan,
