@@ -131,8 +131,8 @@ typedef struct {
     double rel_resid[3];   /* final ||b - A x|| / ||b|| (GMRES estimate)     */
     int converged;         /* 1 if every channel met gmres_tol               */
     int n_matvec;          /* operator applications, right-hand side included */
-    double ms_rhs;         /* right-hand side (Alg. 3 line 4), device time   */
-    double ms_solve;       /* x0 set-up and GMRES (Alg. 3 line 5), host wall
+    double ms_rhs;         /* right-hand side (Alg. 3), device time   */
+    double ms_solve;       /* x0 set-up and GMRES (Alg. 3), host wall
                               time                                           */
     long long p2p_pairs;   /* near-field (target, piece) pairs per matvec    */
     long long m2l_pairs;   /* cell pairs in M2L per matvec                   */
@@ -179,7 +179,7 @@ dc_status dc_create(dc_ctx **out, const dc_options *opt);
 /* Frees every device and host resource of the context (NULL is a no-op). */
 void dc_destroy(dc_ctx *ctx);
 
-/* Discretises the drawing and builds the solver state (Alg. 3 lines 1-2:
+/* Discretises the drawing and builds the solver state (Alg. 3:
  * quadtree(S) and pre_FMM(S, q, Q), Sec. 5.3).
  *   ctrl         host [n_curves][4][2] control points C0..C3 (App. B)
  *   panel_ptr    host [n_curves + 1]; curve i owns panels
@@ -197,14 +197,14 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl,
                         const int *panel_ptr, const double *panel_start,
                         const double *colours);
 
-/* Solves for the density (Alg. 3 lines 3-5): mu = u+ - u-,
+/* Solves for the density (Alg. 3): mu = u+ - u-,
  * b = (u+ + u-)/2 - F_H mu, sigma = GMRES(G_H, x0, b, tol) with FP64
  * Arnoldi.  x0: host [n_nodes][3] used when x0_mode == DC_X0_USER (else
  * may be NULL).  stats may be NULL.  Returns DC_ERR_NOCONV (density kept,
  * stats filled) if gmres_max_iter is reached first. */
 dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats);
 
-/* Renders n_vp viewports (Alg. 4 line 3): u = single layer of sigma plus
+/* Renders n_vp viewports (Alg. 4): u = single layer of sigma plus
  * double layer of mu at every pixel centre.
  *   rgb       [sum_v height_v width_v][3] of rgb_dtype, viewports
  *             concatenated in order, pixels row-major; may be NULL

@@ -239,7 +239,7 @@ class Solution:
 
 
 def rhs(drawing, disc: Discretisation, AF=None):
-    """b = (u+ + u-)/2 - F_H mu with mu = u+ - u- (Alg. 3 lines 3-4)."""
+    """b = (u+ + u-)/2 - F_H mu with mu = u+ - u- (Alg. 3)."""
     up, um = boundary_values(drawing, disc)
     mu = up - um
     if AF is None:

@@ -1,8 +1,8 @@
 // C ABI of libdc_fmm (declarations and contracts in include/dc_fmm.h).
 //
 // The entry points follow the paper's problem statement: build the
-// discretisation and quadtree (Alg. 3 lines 1-2), solve for the density
-// (Alg. 3 lines 3-5), render viewports (Alg. 4 line 3).
+// discretisation and quadtree (Alg. 3), solve for the density
+// (Alg. 3), render viewports (Alg. 4).
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -140,7 +140,7 @@ struct DenseOp : dc::Operator {
     }
 };
 
-// FMM operator y = G_H x (Alg. 3 line 5, the matvec of GMRES).
+// FMM operator y = G_H x (Alg. 3, the matvec of GMRES).
 struct FmmOp : dc::Operator {
     dc::Fmm *fmm;
     cudaError_t apply(const double *x, double *y, cudaStream_t st) override {
@@ -453,7 +453,7 @@ dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats)
         }
     } guard{e0, e1};
     DC_CK(ctx, cudaEventRecord(e0, s), "event");
-    // b = (u+ + u-)/2 - F_H mu  (Alg. 3 line 4)
+    // b = (u+ + u-)/2 - F_H mu  (Alg. 3)
     if (ctx->opt.form == DC_FORM_DENSE64) {
         DC_CK(ctx, dc::launch_dense_gemv(ctx->AF.ptr, N, ctx->mu.ptr, ctx->fmu.ptr, s), "rhs");
     } else {

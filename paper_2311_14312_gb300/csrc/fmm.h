@@ -13,7 +13,7 @@ class Fmm {
 public:
     Fmm();
     ~Fmm();
-    // quadtree(S) and pre_FMM(S, q, Q) (Alg. 3 lines 1-2).
+    // quadtree(S) and pre_FMM(S, q, Q) (Alg. 3).
     dc_status build(const dc_options &opt, const Geometry &G, const DevGeom &D,
                     cudaStream_t st, std::string &err);
     // y = G_H x at the nodes (single layer of the interpolated density).
@@ -28,7 +28,7 @@ public:
     cudaError_t apply_precond(const double *x, double *y, cudaStream_t st);
     // The FP32 operator without the preconditioner, y = G_H x.
     cudaError_t apply_inner_raw(const double *x, double *y, cudaStream_t st);
-    // GMRES with this operator (Alg. 3 line 5); x holds x0 on entry.
+    // GMRES with this operator (Alg. 3); x holds x0 on entry.
     // n_refine: outer refinement steps taken.  Ax0: G_H x0 when the caller
     // has it (the first residual then needs no operator application), else
     // nullptr.

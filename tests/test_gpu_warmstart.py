@@ -91,7 +91,7 @@ def test_adam_matches_oracle(dcmod, cuda_ok, M):
 
 def _initial_residuals(P, ctx, d):
     """||b - G_H x|| / ||b|| per channel for x = 0 and x = 1, through the ABI
-    (b = (u+ + u-)/2 - F_H mu, Alg. 3 line 4)."""
+    (b = (u+ + u-)/2 - F_H mu, Alg. 3)."""
     import torch
     _, _, up, um = ctx.nodes()
     mu = torch.from_numpy(up - um).cuda()
