@@ -102,30 +102,33 @@ __global__ void coarse_matrix_kernel(const float2 *__restrict__ q32, const float
 }
 
 // Blocked Gauss-Jordan inversion in place (no pivoting), step k:
-// 1. A_kk <- A_kk^-1 (one block, shared memory)
+// 1. A_kk <- A_kk^-1 (one warp; lane t holds column t in registers and reads
+//    the pivot column by shuffles, with the same operations per element as
+//    the textbook in-place elimination)
 __global__ void gj_diag_kernel(float *__restrict__ A, int n, int k) {
-    __shared__ float a[kGJ][kGJ + 1];
+    static_assert(kGJ == 32, "one lane per column of the diagonal block");
     const int t = threadIdx.x;          // column
     float *D = A + (size_t)k * kGJ * n + k * kGJ;
-    for (int r = 0; r < kGJ; ++r) a[r][t] = D[(size_t)r * n + t];
-    __syncthreads();
+    float a[kGJ];
+#pragma unroll
+    for (int r = 0; r < kGJ; ++r) a[r] = D[(size_t)r * n + t];
+#pragma unroll
     for (int c = 0; c < kGJ; ++c) {
-        const float piv = a[c][c];
-        __syncthreads();
+        const float piv = __shfl_sync(0xffffffffu, a[c], c);
+        float f[kGJ];
+#pragma unroll
+        for (int r = 0; r < kGJ; ++r) f[r] = __shfl_sync(0xffffffffu, a[r], c);   // column c before the step
         // row c scaled; column c of the inverse replaces column c
-        const float rc = (t == c) ? 1.f / piv : a[c][t] / piv;
-        __syncthreads();
-        a[c][t] = rc;
-        __syncthreads();
+        const float rc = (t == c) ? 1.f / piv : a[c] / piv;
+        a[c] = rc;
+#pragma unroll
         for (int r = 0; r < kGJ; ++r) {
             if (r == c) continue;
-            const float f = a[r][c];
-            __syncthreads();
-            a[r][t] = (t == c) ? -f / piv : a[r][t] - f * rc;
-            __syncthreads();
+            a[r] = (t == c) ? -f[r] / piv : a[r] - f[r] * rc;
         }
     }
-    for (int r = 0; r < kGJ; ++r) D[(size_t)r * n + t] = a[r][t];
+#pragma unroll
+    for (int r = 0; r < kGJ; ++r) D[(size_t)r * n + t] = a[r];
 }
 
 // 2. A_kj <- A_kk A_kj for the columns j outside block k (one thread per column)
