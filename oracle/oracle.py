@@ -238,15 +238,6 @@ class Solution:
     AG: np.ndarray | None = None
 
 
-def rhs(drawing, disc: Discretisation, AF=None):
-    """b = (u+ + u-)/2 - F_H mu with mu = u+ - u- (Alg. 3)."""
-    up, um = boundary_values(drawing, disc)
-    mu = up - um
-    if AF is None:
-        _, AF = hybrid_rows(disc)
-    return 0.5 * (up + um) - AF @ mu, mu
-
-
 def solve_values(disc: Discretisation, u_plus: np.ndarray, u_minus: np.ndarray,
                  keep_matrix=False) -> Solution:
     """Solve Eq. 27 for sigma given u+ and u- at the nodes: mu = u+ - u-,

@@ -1,0 +1,71 @@
+"""The bench drawing at full size, in the launch configuration bench.py times
+(200 curves, 27,888 nodes x 3 channels, 139,440 segments; p = 24, leaf 64,
+GMRES tolerance 1e-10; 2048 x 2048 render of [0,1]^2 with FP32 and 8-bit
+output), against stored values the oracle wrote from its dense LU solve of
+Eq. 27 (tests/golden/make_golden_mixed200.py):
+
+  * sigma at 512 seeded nodes: max error <= 1e-6 of max |sigma|;
+  * u at 4096 pixel centres (half of them within 0.003 of a segment vertex):
+    max colour error <= 1e-5;
+  * 8-bit output identical wherever the oracle's colour is farther than 1e-5
+    from a rounding boundary of floor(255 u + 1/2) (pixels inside that band
+    are counted and still held to the 1e-5 bar).
+
+Both FMM forms run: the chosen FP32 form and the plain FP64 FMM.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from dc_synth import drawing_by_name
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+W = H = 2048
+BENCH_OPTS = dict(p=24, leaf_size=64, gmres_tol=1e-10, gmres_restart=200, gmres_max_iter=3000)
+SIGMA_REL = 1e-6
+COLOUR_ABS = 1e-5
+
+
+def _load():
+    s = np.loadtxt(os.path.join(HERE, "mixed200_sigma.txt"))
+    p = np.loadtxt(os.path.join(HERE, "mixed200_pixels.txt"))
+    return (s[:, 0].astype(np.int64), s[:, 1:], p[:, 0].astype(np.int64),
+            p[:, 1].astype(bool), p[:, 2:])
+
+
+def _quantise(u):
+    return np.floor(255.0 * np.clip(u, 0.0, 1.0) + 0.5)
+
+
+@pytest.mark.parametrize("form", ["fmm32", "fmm64"])
+def test_bench_drawing_matches_oracle_lu(dcmod, cuda_ok, form):
+    import torch
+    nodes, sig_ref, pix, near, u_ref = _load()
+    d = drawing_by_name("mixed200")
+    ctx = dcmod.Context(form=form, g=d.g, s_per_panel=d.s_per_panel, **BENCH_OPTS)
+    ctx.build_drawing(d)
+    st = ctx.solve_density()
+    assert st.converged == 1
+    sig = ctx.get_density()[nodes]
+    sig_err = np.abs(sig - sig_ref).max() / np.abs(sig_ref).max()
+    dt = torch.float32 if form == "fmm32" else torch.float64
+    rgb = torch.empty((W * H, 3), dtype=dt, device="cuda")
+    rgb8 = torch.empty((W * H, 3), dtype=torch.uint8, device="cuda")
+    ctx.render_viewport([(0.0, 0.0, 1.0, 1.0, W, H)], rgb, rgb8)
+    torch.cuda.synchronize()
+    got = rgb.cpu().numpy()[pix].astype(np.float64)
+    got8 = rgb8.cpu().numpy()[pix].astype(np.float64)
+    err = np.abs(got - u_ref)
+    v = 255.0 * np.clip(u_ref, 0.0, 1.0)
+    band = np.abs(v - np.floor(v) - 0.5) <= 255.0 * COLOUR_ABS
+    mism = int(((got8 != _quantise(u_ref)) & ~band).sum())
+    print(f"{form}: sigma max rel err {sig_err:.2e}; colour max err {err.max():.2e} "
+          f"(near {err[near].max():.2e}, far {err[~near].max():.2e}); 8-bit mismatches "
+          f"outside the band {mism}, band entries {int(band.sum())}; iters {list(st.iters)}")
+    assert sig_err <= SIGMA_REL
+    assert err.max() <= COLOUR_ABS
+    assert mism == 0
+    ctx.close()

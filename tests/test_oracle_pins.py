@@ -410,3 +410,70 @@ def test_layer_potential_brute_force_curved(oracle_mod):
     un = oracle_mod.layer_potential(disc, disc.node_xy, 0 * ones, ones,
                                     disc.node_seg, disc.node_seg2)[:, 0]
     np.testing.assert_allclose(AF.sum(1), un, rtol=1e-12, atol=1e-15)
+
+
+# ----------------------------------------- boundary colours and pixels ----
+def test_boundary_colours_straight_line_hand_values(oracle_mod):
+    """One straight cubic with evenly spaced control points (t equals the
+    arc-length fraction), one panel of g = 3 nodes: the middle node sits at
+    t = 1/2, so u+ and u- there are the means of each side's end colours,
+    worked out by hand.  A swapped side or end changes these numbers."""
+    a, b = np.array([0.2, 0.5]), np.array([0.8, 0.5])
+    ctrl = np.array([[a + (b - a) * k / 3 for k in range(4)]])
+    col = np.zeros((1, 2, 2, 3))
+    col[0, 0, 0] = [0.2, 0.4, 0.6]      # "+" side (right of travel), t = 0
+    col[0, 0, 1] = [0.6, 0.0, 1.0]      # "+" side, t = 1
+    col[0, 1, 0] = [1.0, 0.9, 0.1]      # "-" side, t = 0
+    col[0, 1, 1] = [0.0, 0.3, 0.7]      # "-" side, t = 1
+    d = Drawing("line", ctrl, np.zeros(1, bool), col, np.array([0, 1], np.int32),
+                np.array([0.0]), g=3, s_per_panel=15)
+    disc = oracle_mod.discretise(d)
+    up, um = oracle_mod.boundary_values(d, disc)
+    np.testing.assert_allclose(disc.node_xy[1], [0.5, 0.5], atol=1e-15)
+    np.testing.assert_allclose(up[1], [0.4, 0.2, 0.8], atol=1e-14)
+    np.testing.assert_allclose(um[1], [0.5, 0.6, 0.4], atol=1e-14)
+    # first node: Gauss-Legendre root -sqrt(3/5) maps to t = (1 - sqrt(3/5)) / 2
+    t0 = (1.0 - np.sqrt(0.6)) / 2.0
+    np.testing.assert_allclose(up[0], [0.2 + 0.4 * t0, 0.4 - 0.4 * t0, 0.6 + 0.4 * t0], atol=1e-14)
+
+
+def _linear_field(P):
+    A = np.array([[0.8, -0.3, 0.1], [0.2, 0.5, 0.05], [-0.4, 0.9, 0.6]])
+    return np.atleast_2d(P) @ A[:, :2].T + A[:, 2]
+
+
+def test_boundary_colours_side_and_end_by_harmonic_interior(oracle_mod):
+    """A counter-clockwise square (straight edges, so the polyline is exact)
+    whose inside ("-", left of travel) colours are a linear function f at the
+    corners: linear in t along each edge, this is f itself on the boundary,
+    so the interior field is f (Dirichlet problem, Sec. 3), converging with
+    refinement.  The outside ("+") colour is an unrelated constant 0.9.
+    Reading the sides or the ends the other way round leaves O(0.1) errors."""
+    corners = np.array([[0.2, 0.2], [0.7, 0.2], [0.7, 0.7], [0.2, 0.7]])
+    P = np.random.default_rng(1).uniform(0.3, 0.6, (100, 2))
+    errs = []
+    for panels, g, nseg in ((4, 8, 40), (8, 16, 80)):
+        d = square_drawing(panels=panels, g=g, nseg=nseg)
+        col = np.full((4, 2, 2, 3), 0.9)
+        for i in range(4):
+            col[i, 1, 0] = _linear_field(corners[i])[0]
+            col[i, 1, 1] = _linear_field(corners[(i + 1) % 4])[0]
+        d.colours = col
+        disc = oracle_mod.discretise(d)
+        sol = oracle_mod.solve(d, disc)
+        u = oracle_mod.layer_potential(disc, P, sol.sigma, sol.mu)
+        errs.append(np.abs(u - _linear_field(P)).max())
+    assert errs[0] < 3e-6 and errs[1] < 1e-8, errs
+
+
+def test_pixel_centres_hand_values(oracle_mod):
+    """Pixel (r, c) of a w x h grid over [x0, x1] x [y0, y1] has its centre at
+    (x0 + (c + 1/2) dx, y0 + (r + 1/2) dy), rows counted from y0 (Alg. 4's
+    pixel grid, row 0 at the bottom)."""
+    np.testing.assert_allclose(oracle_mod.pixel_centres((0, 0, 1, 1), 2, 1),
+                               [[0.25, 0.5], [0.75, 0.5]], atol=0)
+    np.testing.assert_allclose(oracle_mod.pixel_centres((0, 0, 1, 1), 1, 2),
+                               [[0.5, 0.25], [0.5, 0.75]], atol=0)
+    # 3 x 2 grid over [1, 4] x [2, 6]: dx = 1, dy = 2
+    np.testing.assert_allclose(oracle_mod.pixel_centres((1, 2, 4, 6), 3, 2, [0, 2, 4, 5]),
+                               [[1.5, 3.0], [3.5, 3.0], [2.5, 5.0], [3.5, 5.0]], atol=0)
