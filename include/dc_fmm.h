@@ -241,7 +241,11 @@ dc_status dc_eval_points(dc_ctx *ctx, int n, const void *xy, int xy_where,
  * call before any stream capture.  All calls share the one array and it
  * keeps the last call's contents, so calls that overlap on the GPU (other
  * streams or contexts without ordering between them) race on it.
- * Errors: DC_ERR_STATE without a density, DC_ERR_ARG for bad sizes. */
+ * The cached address belongs to the device's primary context and does not
+ * survive a cudaDeviceReset (rebuild the context after one).
+ * Errors: DC_ERR_STATE without a density or when the current CUDA device is
+ * not the context's, DC_ERR_ARG for bad sizes, DC_ERR_CUDA when the symbol
+ * lookup or a launch fails. */
 dc_status dc_eval_points_noalloc(dc_ctx *ctx, int n, const double *xy_dev, double *out_dev);
 
 /* Copies the current density sigma at the nodes to host [n_nodes][3]. */
@@ -366,6 +370,21 @@ dc_status dc_aux_precond_info(dc_ctx *ctx, double *out);
  * total.  out: host array of 11 doubles (zero where a phase does not
  * apply).  Errors: DC_ERR_STATE before dc_build_tree. */
 dc_status dc_aux_build_timings(dc_ctx *ctx, double *out);
+
+/* Auxiliary test hook (no counterpart in the paper) for the bounded device
+ * waits of DC_FORM_FMM32 with m2l_engine DC_M2L_TENSOR: from the next
+ * operator application on, the CTA of the tensor-core M2L that takes tile
+ * `tile` (0-based, in the kernel's tile order) issues neither its MMAs nor
+ * their commit, so its wait on the commit runs out after about 20 ms; the
+ * kernel then sets the context's wait-limit flag, frees its tensor memory
+ * and returns.  The running GMRES cycle ends at its next Givens step and
+ * dc_solve_density returns DC_ERR_TIMEOUT.  The flag is cleared at the start
+ * of every solve; tile = -1 switches the hook off, and the next solve is then
+ * clean.  Nothing faults: no MMA is in flight when the memory is freed.
+ * Errors: DC_ERR_ARG for tile < -1, DC_ERR_STATE before dc_build_tree or in
+ * the dense form, DC_ERR_UNSUPPORTED when the inner operator's M2L does not
+ * run on the tensor cores (p_inner > 15 or DC_M2L_CUDA_CORES). */
+dc_status dc_aux_test_skip_mma_tile(dc_ctx *ctx, int tile);
 
 int dc_abi_version(void);
 

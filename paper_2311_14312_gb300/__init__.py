@@ -80,7 +80,7 @@ EXPORTS = ["dc_default_options", "dc_create", "dc_destroy", "dc_build_tree", "dc
            "dc_eval_points_noalloc", "dc_aux_mlp_param_count", "dc_aux_mlp_workspace_floats",
            "dc_aux_mlp_forward", "dc_aux_mlp_loss_grad", "dc_aux_mlp_adam", "dc_aux_feature_dims",
            "dc_aux_panel_features", "dc_aux_set_warm_start_model", "dc_aux_apply_operator", "dc_aux_precond_info",
-           "dc_aux_build_timings"]
+           "dc_aux_build_timings", "dc_aux_test_skip_mma_tile"]
 
 
 def _load():
@@ -125,6 +125,7 @@ def _load():
     lib.dc_aux_apply_operator.argtypes = [P, I, I, P, P]
     lib.dc_aux_precond_info.argtypes = [P, P]
     lib.dc_aux_build_timings.argtypes = [P, P]
+    lib.dc_aux_test_skip_mma_tile.argtypes = [P, I]
     for name in EXPORTS:
         if name not in ("dc_destroy", "dc_last_error", "dc_status_string", "dc_abi_version",
                         "dc_aux_kernel_launches", "dc_aux_mlp_param_count",
@@ -288,6 +289,11 @@ class Context:
         out = np.zeros(4)
         self._check(_get_lib().dc_aux_precond_info(self._h, _ptr(out)))
         return dict(zip(["two_level", "panels", "near_pairs", "inverse_check"], out.tolist()))
+
+    def test_skip_mma_tile(self, tile: int):
+        """dc_aux_test_skip_mma_tile: hold back the MMAs of one tensor-core
+        M2L tile (its bounded wait then runs out); -1 switches it off."""
+        self._check(_get_lib().dc_aux_test_skip_mma_tile(self._h, int(tile)))
 
     def build_timings(self) -> dict:
         """dc_aux_build_timings as a dict of wall ms per build phase."""

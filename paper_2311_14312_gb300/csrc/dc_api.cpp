@@ -64,6 +64,7 @@ dc_status fail(dc_ctx *ctx, dc_status st, const std::string &msg) {
 dc_status cuda_fail(dc_ctx *ctx, cudaError_t e, const char *where) {
     std::string m = std::string(where) + ": " + cudaGetErrorString(e);
     if (e == cudaErrorMemoryAllocation) return fail(ctx, DC_ERR_OOM, m);
+    if (e == cudaErrorTimeout) return fail(ctx, DC_ERR_TIMEOUT, where);   // a bounded device wait gave up
     return fail(ctx, DC_ERR_CUDA, m);
 }
 
@@ -550,6 +551,10 @@ dc_status dc_eval_points_noalloc(dc_ctx *ctx, int n, const double *xy_dev, doubl
     if (n < 0 || (n > 0 && (!xy_dev || !out_dev)))
         return fail(ctx, DC_ERR_ARG, "eval_points_noalloc: bad arguments");
     if (n == 0) return DC_OK;
+    int cur = -1;
+    DC_CK(ctx, cudaGetDevice(&cur), "eval_points_noalloc");
+    if (cur != ctx->device)
+        return fail(ctx, DC_ERR_STATE, "eval_points_noalloc: the current CUDA device is not the context's device");
     std::string msg;
     cudaError_t e = dc::eval_points_noalloc(ctx->dg, ctx->sigma.ptr, ctx->mu.ptr, xy_dev, n, out_dev,
                                             ctx->stream, msg);
@@ -886,6 +891,19 @@ dc_status dc_aux_precond_info(dc_ctx *ctx, double *out) {
     if (!out) return fail(ctx, DC_ERR_ARG, "precond_info: NULL output");
     if (ctx->state < 1 || !ctx->fmm) return fail(ctx, DC_ERR_STATE, "precond_info: needs an FMM form after build_tree");
     ctx->fmm->precond_info(out);
+    return DC_OK;
+}
+
+dc_status dc_aux_test_skip_mma_tile(dc_ctx *ctx, int tile) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (tile < -1) return fail(ctx, DC_ERR_ARG, "test_skip_mma_tile: tile must be >= -1");
+    if (ctx->state < 1 || !ctx->fmm) return fail(ctx, DC_ERR_STATE, "test_skip_mma_tile: needs an FMM form after build_tree");
+    cudaError_t e = ctx->fmm->set_mma_skip_tile(tile, ctx->stream);
+    if (e == cudaErrorNotSupported)
+        return fail(ctx, DC_ERR_UNSUPPORTED, "test_skip_mma_tile: the inner operator does not run its M2L on the tensor cores");
+    DC_CK(ctx, e, "test_skip_mma_tile");
+    DC_CK(ctx, cudaStreamSynchronize(ctx->stream), "test_skip_mma_tile");
     return DC_OK;
 }
 

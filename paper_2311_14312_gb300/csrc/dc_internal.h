@@ -195,6 +195,9 @@ struct Operator {
     virtual double *in_buffer() { return nullptr; }
     virtual double *out_buffer() { return nullptr; }
     virtual cudaError_t apply_buffers(cudaStream_t) { return cudaErrorNotSupported; }
+    // Optional: a device int that the operator's kernels set when a bounded
+    // wait ran out; GMRES then ends its cycle at the next Givens step.
+    virtual const int *fault_flag() { return nullptr; }
 };
 
 struct GmresResult {

@@ -34,6 +34,10 @@
 
 namespace dc {
 
+// initial state of the tensor-core M2L's flags: no wait ran out, no tile
+// held back by the test hook
+static const int kTcErrInit[2] = {0, -1};
+
 namespace {
 
 using cd = std::complex<double>;
@@ -1061,7 +1065,9 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         UP(I.tc_tiles, tc_tiles);
         I.n_tc_tiles = int(tc_tiles.size());
         if ((e = I.tc_y.alloc(T.v_idx.size() * 3 * 2 * (size_t)I.P1i)) != cudaSuccess ||
-            (e = I.tc_err.alloc(1)) != cudaSuccess || (e = cudaMemsetAsync(I.tc_err.ptr, 0, sizeof(int), st)) != cudaSuccess) {
+            (e = I.tc_err.alloc(2)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(I.tc_err.ptr, kTcErrInit, sizeof(kTcErrInit), cudaMemcpyHostToDevice, st)) !=
+                cudaSuccess) {
             err = std::string("fmm allocation: ") + cudaGetErrorString(e);
             return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
         }
@@ -1181,7 +1187,11 @@ cudaError_t Fmm::Impl::precond(const double *v, double *w, cudaStream_t st) {
 
 cudaError_t Fmm::apply_inner(const double *x, double *y, cudaStream_t st) {
     if (!impl_->fp32) return cudaErrorNotSupported;
-    return impl_->graph_matvec32(x, y, st);
+    cudaError_t e;
+    std::string msg;
+    if (impl_->tc_err.ptr && (e = cudaMemsetAsync(impl_->tc_err.ptr, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if ((e = impl_->graph_matvec32(x, y, st)) != cudaSuccess) return e;
+    return impl_->check_tc_wait(st, msg);
 }
 
 cudaError_t Fmm::apply_precond(const double *x, double *y, cudaStream_t st) {
@@ -1190,7 +1200,11 @@ cudaError_t Fmm::apply_precond(const double *x, double *y, cudaStream_t st) {
 
 cudaError_t Fmm::apply_inner_raw(const double *x, double *y, cudaStream_t st) {
     if (!impl_->fp32) return cudaErrorNotSupported;
-    return impl_->apply_nodes32(x, y, true, st);
+    cudaError_t e;
+    std::string msg;
+    if (impl_->tc_err.ptr && (e = cudaMemsetAsync(impl_->tc_err.ptr, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if ((e = impl_->apply_nodes32(x, y, true, st)) != cudaSuccess) return e;
+    return impl_->check_tc_wait(st, msg);
 }
 
 namespace {
@@ -1208,12 +1222,14 @@ struct PrecOp : Operator {
     double *in_buffer() override { return fp32 && f->graph_ensure() == cudaSuccess ? f->g_in.ptr : nullptr; }
     double *out_buffer() override { return fp32 && f->graph_ensure() == cudaSuccess ? f->g_out.ptr : nullptr; }
     cudaError_t apply_buffers(cudaStream_t st) override { return f->graph_launch(st); }
+    const int *fault_flag() override { return fp32 ? f->tc_err.ptr : nullptr; }
 };
 }  // namespace
 
 cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_options &opt,
                        cudaStream_t st, GmresResult &res, std::string &err, int *n_refine,
                        const double *Ax0) {
+    cudaError_t e0;
     // Iterative refinement around right-preconditioned GMRES:
     //   r = b - A x            (FP64 FMM operator)
     //   z = GMRES(A' M, 0, r, tol')      A' = FP64 or FP32 FMM operator,
@@ -1228,6 +1244,8 @@ cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_option
     PrecOp op;
     op.f = &I;
     res = GmresResult();
+    // the tensor-core M2L's wait-limit flag starts clear in every solve
+    if (I.tc_err.ptr && (e0 = cudaMemsetAsync(I.tc_err.ptr, 0, sizeof(int), st)) != cudaSuccess) return e0;
     double bn[3], rn[3];
     cudaError_t e = vec_norms3(w, b, N, bn, st);
     if (e != cudaSuccess) return e;
@@ -1266,6 +1284,7 @@ cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_option
         e = gmres_solve(w, op, N, I.ir_r.ptr, I.ir_d.ptr, true, true, inner_tol, opt.gmres_restart,
                         opt.gmres_max_iter - used, st, inner, err);
         if (e != cudaSuccess) return e;
+        if ((e = I.check_tc_wait(st, err)) != cudaSuccess) return e;
         int mx = 0;
         for (int c = 0; c < 3; ++c) {
             res.iters[c] += inner.iters[c];
@@ -1278,17 +1297,29 @@ cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_option
             return e;
         if ((e = vec_axpy(x, I.ir_t.ptr, 3 * N, st)) != cudaSuccess) return e;
     }
-    if (I.tc_err.ptr) {   // the tensor-core M2L reports MMAs that did not complete in time
-        int flag = 0;
-        if ((e = cudaMemcpyAsync(&flag, I.tc_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-            (e = cudaStreamSynchronize(st)) != cudaSuccess)
-            return e;
-        if (flag) {
-            err = "tensor-core M2L: the MMAs did not complete within the wait limit";
-            return cudaErrorLaunchTimeout;
-        }
-    }
     return cudaGetLastError();
+}
+
+// cudaErrorTimeout when the tensor-core M2L's bounded wait ran out since the
+// flag was last cleared (the library reports it as DC_ERR_TIMEOUT).
+cudaError_t Fmm::Impl::check_tc_wait(cudaStream_t st, std::string &err) {
+    if (!tc_err.ptr) return cudaSuccess;
+    int flag = 0;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(&flag, tc_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return e;
+    if (flag) {
+        err = "tensor-core M2L: the MMAs of a tile did not complete within the wait limit";
+        return cudaErrorTimeout;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t Fmm::set_mma_skip_tile(int tile, cudaStream_t st) {
+    Impl &I = *impl_;
+    if (!I.tc_err.ptr) return cudaErrorNotSupported;
+    return cudaMemcpyAsync(I.tc_err.ptr + 1, &tile, sizeof(int), cudaMemcpyHostToDevice, st);
 }
 
 namespace {

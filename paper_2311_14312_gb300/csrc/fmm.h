@@ -28,6 +28,9 @@ public:
     cudaError_t apply_precond(const double *x, double *y, cudaStream_t st);
     // The FP32 operator without the preconditioner, y = G_H x.
     cudaError_t apply_inner_raw(const double *x, double *y, cudaStream_t st);
+    // Test hook of the tensor-core M2L: the CTA that takes `tile` issues no
+    // MMA for it, so its bounded wait runs out (-1 = off).
+    cudaError_t set_mma_skip_tile(int tile, cudaStream_t st);
     // GMRES with this operator (Alg. 3); x holds x0 on entry.
     // n_refine: outer refinement steps taken.  Ax0: G_H x0 when the caller
     // has it (the first residual then needs no operator application), else

@@ -221,6 +221,7 @@ struct Fmm::Impl {
     // render preparation of the FP32 form: FP64 passes, FP32 copies of the
     // expansions, heavy-piece flags from the FP64 segment densities
     cudaError_t prepare_render32(const double *sb, const double *mb, cudaStream_t st);
+    cudaError_t check_tc_wait(cudaStream_t st, std::string &err);
     cudaError_t apply_nodes32(const double *x, double *y, bool single, cudaStream_t st);
     cudaError_t interp32(const double *node_vals, float *seg_vals, cudaStream_t st);
     // the FP32 operator at the nodes from segment values already in

@@ -197,6 +197,7 @@ struct GivensState {
     int *active;    // [3]
     int *kc;        // [3] columns used in this cycle
     double *resid;  // [3] current |e[k+1]|
+    const int *fault = nullptr;   // the operator's wait-limit flag, or null
 };
 
 // Start of a cycle: e = (beta, 0, ...); active = beta > thr.
@@ -255,6 +256,7 @@ __device__ void givens_step_warp(GivensState g, const double *__restrict__ hcol,
         g.resid[c] = res;
         g.kc[c] = k + 1;
         if (res <= thr[c] || !(hn > 0.0) || !(den > 0.0)) g.active[c] = 0;
+        if (g.fault && *g.fault) g.active[c] = 0;   // the operator gave up a wait: end the cycle
     }
     __syncwarp();
     if (smem) {
@@ -576,6 +578,7 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
     // resets its own; this guards against a launch that failed midway)
     if ((ce = cudaMemsetAsync(W.count.ptr, 0, W.count.bytes(), st)) != cudaSuccess) return ce;
     GivensState gs = W.gs();
+    gs.fault = A.fault_flag();
     double *bnorm = W.small.ptr;        // [3]
     double *thr = W.small.ptr + 3;      // [3]
     double *beta = W.small.ptr + 12;    // [3] (slots 8..10 hold resid)

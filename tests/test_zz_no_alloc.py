@@ -57,12 +57,18 @@ def test_noalloc_matches_eval_points_on_consecutive_calls(dcmod, cuda_ok):
     # the first call on a device looks up the scratch array (the runtime may
     # load the array's module then); memory is compared after it
     noalloc(ctx, points(9, 4))
+    # every tensor is allocated before the first reading, so only the
+    # library's two calls fall between the readings
+    out1 = torch.full((xy1.shape[0], 3), float("nan"), dtype=torch.float64, device="cuda")
+    out2 = torch.full((xy2.shape[0], 3), float("nan"), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
-    got1 = noalloc(ctx, xy1)
-    got2 = noalloc(ctx, xy2)
+    ctx.eval_points_noalloc(xy1, out1)
+    ctx.eval_points_noalloc(xy2, out2)
+    torch.cuda.synchronize()
     free1 = torch.cuda.mem_get_info()[0]
-    np.testing.assert_allclose(got1, ref1, rtol=TOL, atol=TOL)
-    np.testing.assert_allclose(got2, ref2, rtol=TOL, atol=TOL)
+    np.testing.assert_allclose(out1.cpu().numpy(), ref1, rtol=TOL, atol=TOL)
+    np.testing.assert_allclose(out2.cpu().numpy(), ref2, rtol=TOL, atol=TOL)
     assert free1 == free0          # nothing was allocated on the device
 
 
