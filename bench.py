@@ -35,9 +35,39 @@ WORKLOAD = "mixed200"
 WIDTH = HEIGHT = 2048
 VIEWPORT = (0.0, 0.0, 1.0, 1.0)
 FORM_OPTS = dict(p=24, leaf_size=64, gmres_tol=1e-10, gmres_restart=200, gmres_max_iter=3000)
-# FP32 vector-unit peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops
-# per FMA x 2.07 GHz maximum SM clock.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# nominal dense tensor rates (NVIDIA's GB300 figures without sparsity): the
+# TF32 peak is the measured BF16 peak times their ratio
+NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
+FALLBACK_BF16_TFLOPS = 1900.0
+
+
+def measured_peaks() -> dict:
+    """The driver-written measured peaks of this machine's GPUs, if present."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def cpu_model() -> str:
+    """CPU model name from /proc/cpuinfo (x86 'model name'; Arm machines give
+    implementer / part numbers only, reported as such)."""
+    try:
+        txt = open("/proc/cpuinfo").read()
+    except Exception:
+        return "unknown"
+    for key in ("model name", "Model name"):
+        for ln in txt.splitlines():
+            if ln.startswith(key):
+                return ln.split(":", 1)[1].strip()
+    impl = part = None
+    for ln in txt.splitlines():
+        if ln.startswith("CPU implementer") and impl is None:
+            impl = ln.split(":", 1)[1].strip()
+        if ln.startswith("CPU part") and part is None:
+            part = ln.split(":", 1)[1].strip()
+    return f"Arm implementer {impl} part {part}" if impl else "unknown"
 
 
 def parse():
@@ -145,18 +175,18 @@ def dist_env():
 
 
 # ----------------------------------------------------------- oracle leg --
-def oracle_sample(seconds: float, seed: int = 1):
-    """Oracle direct-sum render of sampled pixels of the same viewport with
-    a seeded density: (pixels, seconds, threads).  The oracle cannot solve
-    27,888 unknowns in bounded time (dense LU), so only its render leg is
-    timed; the density values do not change its cost."""
-    import numpy as np
-
-    from dc_synth import drawing_by_name, pixel_sample, random_node_values
+def _oracle_setup():
+    from dc_synth import drawing_by_name
     from oracle import oracle as O
-
     d = drawing_by_name(WORKLOAD)
-    disc = O.discretise(d)
+    return O, d, O.discretise(d)
+
+
+def oracle_render_sample(O, disc, seconds: float, seed: int = 1):
+    """Oracle direct-sum render (Eq. 23, Alg. 4) of sampled pixels of the
+    viewport with a seeded density (its cost does not depend on the values):
+    (pixels, seconds)."""
+    from dc_synth import pixel_sample, random_node_values
     sig = random_node_values(disc.n_nodes, seed=seed, scale=0.1)
     mu = random_node_values(disc.n_nodes, seed=seed + 1, scale=0.1)
     probe = pixel_sample(WIDTH, HEIGHT, 64, seed=seed)
@@ -167,36 +197,69 @@ def oracle_sample(seconds: float, seed: int = 1):
     idx = pixel_sample(WIDTH, HEIGHT, count, seed=seed + 2)
     t0 = time.perf_counter()
     O.layer_potential(disc, O.pixel_centres(VIEWPORT, WIDTH, HEIGHT, idx), sig, mu)
-    dt = time.perf_counter() - t0
-    return count, dt, O.num_threads(), np
+    return count, time.perf_counter() - t0
+
+
+def oracle_solve_sample(O, disc, rows: int = 512, lu_n: int = 4096):
+    """Bounded sample of the oracle's solve (Alg. 3 by dense LU): dense rows
+    of G_H and F_H (Eq. 19, 27) for `rows` seeded collocation nodes, and a
+    LAPACK LU solve of an lu_n x lu_n system with three right-hand sides.
+    Returns the full-size estimate: assembly x N / rows, LU x (N / lu_n)^3
+    (LU costs 2/3 n^3 flops), in seconds, and the sample's own seconds."""
+    import numpy as np
+    N = disc.n_nodes
+    sel = np.sort(np.random.default_rng(5).choice(N, min(rows, N), replace=False))
+    t0 = time.perf_counter()
+    O.hybrid_rows(disc, sel)
+    t_rows = time.perf_counter() - t0
+    A = np.random.default_rng(6).standard_normal((lu_n, lu_n)) + lu_n * np.eye(lu_n)
+    b = np.ones((lu_n, 3))
+    t0 = time.perf_counter()
+    np.linalg.solve(A, b)
+    t_lu = time.perf_counter() - t0
+    est = t_rows * N / len(sel) + t_lu * (N / lu_n) ** 3
+    return est, t_rows + t_lu
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores: the whole solve (dense
+    assembly of G_H and F_H for all 27,888 nodes and a LAPACK LU solve of the
+    three channels, Alg. 3) is timed in full once; every step renders a
+    bounded sample of the 2048^2 pixels by direct summation, and the step
+    time is the solve plus the full frame's render extrapolated from that
+    step's sample."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    vals = []
-    per = max(2.0, args.cpu_seconds / max(1, args.steps))
+    O, d, disc = _oracle_setup()
     for _ in range(args.warmup):
-        oracle_sample(0.5)
-    cores = 1
-    total_px, total_t = 0, 0.0
+        oracle_render_sample(O, disc, 0.3)
+    t0 = time.perf_counter()
+    O.solve(d, disc)
+    t_solve = time.perf_counter() - t0
+    per = max(1.0, args.cpu_seconds / max(1, args.steps))
+    npx = WIDTH * HEIGHT
+    step_s = []
+    total_px = 0
     for k in range(args.steps):
-        n, dt, cores, _ = oracle_sample(per, seed=100 + k)
-        vals.append(n / dt / 1e6)
+        n, dt = oracle_render_sample(O, disc, per, seed=100 + k)
         total_px += n
-        total_t += dt
-    v = total_px / total_t / 1e6
-    sample = (f"oracle FP64 direct-sum render of {total_px} sampled pixels of the "
-              f"{WIDTH}x{HEIGHT} viewport in {args.steps} steps (render leg only: the oracle "
-              f"cannot solve 27,888 unknowns in bounded time)")
+        step_s.append(t_solve + dt * npx / n)
+    t_step = statistics.mean(step_s)
+    v = npx / t_step / 1e6
+    cores = O.num_threads()
+    sample = (f"oracle FP64 on {cores} host threads ({cpu_model()}): dense assembly of G_H and F_H "
+              f"for all {disc.n_nodes} nodes + LAPACK LU of 3 channels measured in full once "
+              f"({t_solve:.1f} s); the {WIDTH}x{HEIGHT} render extrapolated per step from a direct-sum "
+              f"sample ({total_px} pixels over {args.steps} steps)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
+            "ms_per_step": 1e3 * t_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "width": WIDTH, "height": HEIGHT},
+            "solve_s": t_solve,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "cpu": cpu_model(), "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -265,9 +328,19 @@ def run_ours(args):
     clk = clocks.stop()
     t_step, value = whole_job_rate(statistics.mean(step_ms), npx, ws, "cuda")
 
-    # ---- roofline of the dominant kernel (pixel evaluation), live events
+    # ---- roofline of the dominant kernel (pixel evaluation), live events;
+    # its peak is the FP32 FMA rate measured on this GPU
     rs = ctx.render_viewport(vp, rgb, rgb8, stats=True)
     achieved = rs.eval_flops / (rs.ms_eval * 1e-3) / 1e12 if rs.ms_eval > 0 else None
+    fp32 = P.fp32_peak()
+    props = torch.cuda.get_device_properties(local)
+    # ---- the inner operator's tensor-core M2L (Eq. 69), live events
+    mp = measured_peaks()
+    bf16 = mp.get("bf16_tflops")
+    tf32_peak = (bf16 if bf16 else FALLBACK_BF16_TFLOPS) * NOMINAL_TF32_OVER_BF16
+    m2l = ctx.time_inner_m2l(20)
+    m2l_ms = m2l["ms_main"] + m2l["ms_reduce"]
+    m2l_ach = m2l["flops"] / (m2l_ms * 1e-3) / 1e12 if m2l_ms > 0 else None
     st = ctx.solve_density()
     chosen = rgb.float().cpu().numpy()
 
@@ -327,11 +400,17 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1:
-        n, dt, cores, _ = oracle_sample(args.cpu_seconds)
-        cpu = {"value": n / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"oracle FP64 direct-sum render of {n} sampled pixels of the "
-                         f"{WIDTH}x{HEIGHT} viewport ({dt:.1f} s; render leg only, the oracle "
-                         f"cannot solve 27,888 unknowns in bounded time)"}
+        O, _, disc = _oracle_setup()
+        est_solve, t_solve_sample = oracle_solve_sample(O, disc)
+        n, dt = oracle_render_sample(O, disc, max(2.0, args.cpu_seconds - t_solve_sample))
+        t_step = est_solve + dt * npx / n
+        cpu = {"value": npx / t_step / 1e6, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+               "cpu": cpu_model(),
+               "sample": f"oracle FP64, extrapolated step {t_step:.0f} s: dense rows of G_H/F_H for 512 "
+                         f"of {disc.n_nodes} nodes (x{disc.n_nodes / 512:.1f}) and LAPACK LU of a "
+                         f"4096^2 system (x(N/4096)^3) for the solve ({est_solve:.0f} s), direct-sum "
+                         f"render of {n} sampled pixels of {WIDTH}x{HEIGHT} ({dt:.1f} s, x{npx / n:.0f}); "
+                         f"bench.py --impl reference times the whole solve"}
 
     if rank == 0:
         line = {
@@ -349,11 +428,24 @@ def run_ours(args):
             "gmres_iters": list(st.iters), "gmres_rel_resid": max(st.rel_resid),
             "plain_form": plain,
             "roofline": {"bound": "alu", "kernel": "eval32_kernel<0> (L2P + M2P + P2P per pixel)",
-                         "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": (achieved / FP32_PEAK_TFLOPS) if achieved else None,
+                         "achieved": achieved, "peak": fp32["tflops"], "unit": "TFLOP/s",
+                         "frac": (achieved / fp32["tflops"]) if achieved else None,
+                         "peak_source": f"measured: FP32 FMA chains on this GPU ({props.multi_processor_count} "
+                                        f"SMs), best of 3 launches",
                          "traffic": traffic_for_eval_kernel(),
                          "eval_ms": rs.ms_eval, "eval_flops": rs.eval_flops,
                          "p2p_pairs": rs.p2p_pairs, "m2p_pairs": rs.m2p_pairs},
+            "roofline_m2l": {"bound": "tensor",
+                             "kernel": ("m2l_tc_kernel + m2l_tc_reduce_kernel (inner operator, p_i = 12, "
+                                        "tcgen05 kind::tf32, three-term split)")
+                             if m2l["engine"] == P.DC_M2L_TENSOR else "m2l_small_kernel (CUDA cores)",
+                             "achieved": m2l_ach, "peak": tf32_peak, "unit": "TFLOP/s",
+                             "frac": (m2l_ach / tf32_peak) if m2l_ach else None,
+                             "peak_source": ("measured bf16 burst x nominal TF32/BF16 ratio 1.1/2.25"
+                                             if bf16 else "fallback 1.9 PFLOP/s bf16 x 1.1/2.25"),
+                             "ms": m2l_ms, "ms_main": m2l["ms_main"], "ms_reduce": m2l["ms_reduce"],
+                             "algorithmic_flops": m2l["flops"], "tensor_pipe_flops": m2l["tensor_flops"],
+                             "pairs": m2l["pairs"]},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                     "includes": "build_tree from host arrays + solve + render to pinned host"},

@@ -371,6 +371,31 @@ dc_status dc_aux_precond_info(dc_ctx *ctx, double *out);
  * apply).  Errors: DC_ERR_STATE before dc_build_tree. */
 dc_status dc_aux_build_timings(dc_ctx *ctx, double *out);
 
+/* Auxiliary measurement (no counterpart in the paper): the FP32 vector peak
+ * of the current device, timed with CUDA events on `stream` (cudaStream_t,
+ * NULL = legacy default stream): 8 independent fused multiply-add chains per
+ * thread, 8 blocks of 256 threads per SM, best of three timed launches.
+ *   out  host double[2]: out[0] TFLOP/s (2 flops per FMA), out[1] ms of the
+ *        best launch
+ * Errors: DC_ERR_ARG for NULL out, DC_ERR_CUDA. */
+dc_status dc_aux_fp32_peak(void *stream, double *out);
+
+/* Auxiliary measurement: device time of the M2L kernels (Eq. 69 over list
+ * 2, Alg. 8) of the FP32 inner operator (DC_FORM_FMM32), `reps` launches
+ * each after one warm-up, CUDA events on the context's stream.
+ *   out  host double[6]: out[0] ms per launch of the main kernel (tcgen05
+ *        tiles, or the CUDA-core kernel), out[1] ms of the tensor path's
+ *        per-target reduction (0 on the CUDA cores), out[2] algorithmic
+ *        flops per application: 8 (p_i + 1)^2 per list-2 pair and channel,
+ *        out[3] flops the tensor pipe executes per application (0 on the
+ *        CUDA cores), out[4] engine (DC_M2L_TENSOR / DC_M2L_CUDA_CORES),
+ *        out[5] list-2 pairs
+ * The kernels read and overwrite the context's inner expansions (the next
+ * solve recomputes them).  Errors: DC_ERR_ARG, DC_ERR_STATE before
+ * dc_build_tree or in other forms, DC_ERR_UNSUPPORTED without list-2
+ * pairs, DC_ERR_TIMEOUT when a bounded wait ran out, DC_ERR_CUDA. */
+dc_status dc_aux_time_inner_m2l(dc_ctx *ctx, int reps, double *out);
+
 /* Auxiliary test hook (no counterpart in the paper) for the bounded device
  * waits of DC_FORM_FMM32 with m2l_engine DC_M2L_TENSOR: from the next
  * operator application on, the CTA of the tensor-core M2L that takes tile

@@ -80,7 +80,8 @@ EXPORTS = ["dc_default_options", "dc_create", "dc_destroy", "dc_build_tree", "dc
            "dc_eval_points_noalloc", "dc_aux_mlp_param_count", "dc_aux_mlp_workspace_floats",
            "dc_aux_mlp_forward", "dc_aux_mlp_loss_grad", "dc_aux_mlp_adam", "dc_aux_feature_dims",
            "dc_aux_panel_features", "dc_aux_set_warm_start_model", "dc_aux_apply_operator", "dc_aux_precond_info",
-           "dc_aux_build_timings", "dc_aux_test_skip_mma_tile"]
+           "dc_aux_build_timings", "dc_aux_test_skip_mma_tile", "dc_aux_fp32_peak",
+           "dc_aux_time_inner_m2l"]
 
 
 def _load():
@@ -126,6 +127,8 @@ def _load():
     lib.dc_aux_precond_info.argtypes = [P, P]
     lib.dc_aux_build_timings.argtypes = [P, P]
     lib.dc_aux_test_skip_mma_tile.argtypes = [P, I]
+    lib.dc_aux_fp32_peak.argtypes = [P, P]
+    lib.dc_aux_time_inner_m2l.argtypes = [P, I, P]
     for name in EXPORTS:
         if name not in ("dc_destroy", "dc_last_error", "dc_status_string", "dc_abi_version",
                         "dc_aux_kernel_launches", "dc_aux_mlp_param_count",
@@ -295,6 +298,12 @@ class Context:
         M2L tile (its bounded wait then runs out); -1 switches it off."""
         self._check(_get_lib().dc_aux_test_skip_mma_tile(self._h, int(tile)))
 
+    def time_inner_m2l(self, reps: int = 20) -> dict:
+        """dc_aux_time_inner_m2l as a dict."""
+        out = np.zeros(6)
+        self._check(_get_lib().dc_aux_time_inner_m2l(self._h, int(reps), _ptr(out)))
+        return dict(zip(["ms_main", "ms_reduce", "flops", "tensor_flops", "engine", "pairs"], out.tolist()))
+
     def build_timings(self) -> dict:
         """dc_aux_build_timings as a dict of wall ms per build phase."""
         out = np.zeros(11)
@@ -357,6 +366,15 @@ def aux_tree_check(seg_xy, domain=(0.0, 0.0, 1.0, 1.0), leaf_size=64, max_depth=
         raise DcError(st, "dc_aux_tree_check failed")
     keys = ["cells", "leaves", "depth", "pieces", "bad_pairs", "clip_rel_err"]
     return dict(zip(keys, out.tolist()))
+
+
+def fp32_peak(stream=None) -> dict:
+    """dc_aux_fp32_peak: measured FP32 FMA peak of the current device."""
+    out = np.zeros(2)
+    st = _get_lib().dc_aux_fp32_peak(_stream(stream), _ptr(out))
+    if st != DC_OK:
+        raise DcError(st, "dc_aux_fp32_peak failed")
+    return {"tflops": float(out[0]), "ms": float(out[1])}
 
 
 def kernel_launches() -> int:

@@ -894,6 +894,27 @@ dc_status dc_aux_precond_info(dc_ctx *ctx, double *out) {
     return DC_OK;
 }
 
+dc_status dc_aux_fp32_peak(void *stream, double *out) {
+    if (!out) return DC_ERR_ARG;
+    double tf = 0.0, ms = 0.0;
+    if (dc::measure_fp32_peak(static_cast<cudaStream_t>(stream), &tf, &ms) != cudaSuccess) return DC_ERR_CUDA;
+    out[0] = tf;
+    out[1] = ms;
+    return DC_OK;
+}
+
+dc_status dc_aux_time_inner_m2l(dc_ctx *ctx, int reps, double *out) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (!out || reps < 1) return fail(ctx, DC_ERR_ARG, "time_inner_m2l: need out and reps >= 1");
+    if (ctx->state < 1 || !ctx->fmm) return fail(ctx, DC_ERR_STATE, "time_inner_m2l: needs an FMM form after build_tree");
+    cudaError_t e = ctx->fmm->time_inner_m2l(reps, ctx->stream, out);
+    if (e == cudaErrorNotSupported)
+        return fail(ctx, DC_ERR_UNSUPPORTED, "time_inner_m2l: the context has no FP32 inner operator with list-2 pairs");
+    DC_CK(ctx, e, "time_inner_m2l");
+    return DC_OK;
+}
+
 dc_status dc_aux_test_skip_mma_tile(dc_ctx *ctx, int tile) {
     if (!ctx) return DC_ERR_ARG;
     ctx->err.clear();

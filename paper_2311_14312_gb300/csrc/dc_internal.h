@@ -45,6 +45,8 @@ void gauss_legendre_rule(int n, double *x, double *w);
 
 // Process-wide count of kernels launched by this library (dc_api.cpp).
 void note_launch(int n = 1);
+// FP32 FMA-chain peak of the current device in TFLOP/s (peaks.cu)
+cudaError_t measure_fp32_peak(cudaStream_t st, double *tflops, double *ms_out);
 long long kernel_launches();
 
 // ---------------------------------------------------------- device util --

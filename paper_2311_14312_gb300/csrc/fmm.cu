@@ -1058,6 +1058,8 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     UP(I.sched_all.m2l, am2l);
     UP(I.sched_all.p2l, ap2l);
     UP(I.sched_nodes.m2l, nm2l);
+    I.m2l_pairs_nodes = 0;
+    for (int c : nm2l) I.m2l_pairs_nodes += T.v_ptr[c + 1] - T.v_ptr[c];
     UP(I.sched_nodes.p2l, np2l);
     if (!tc_tiles.empty()) {
         UP(I.tc_tab, tc_tab);
@@ -1314,6 +1316,10 @@ cudaError_t Fmm::Impl::check_tc_wait(cudaStream_t st, std::string &err) {
         return cudaErrorTimeout;
     }
     return cudaSuccess;
+}
+
+cudaError_t Fmm::time_inner_m2l(int reps, cudaStream_t st, double out[6]) {
+    return impl_->time_inner_m2l(reps, st, out);
 }
 
 cudaError_t Fmm::set_mma_skip_tile(int tile, cudaStream_t st) {

@@ -627,6 +627,69 @@ passes::TreeView<float> Fmm::Impl::view32() const {
     return v;
 }
 
+// M2L (list 2) of the FP32 passes at order P1i: part 0 is the main kernel
+// (tcgen05 tiles for the node schedule when built, else the CUDA-core
+// m2l_small_kernel), part 1 the tensor path's per-target reduction (nothing
+// on the CUDA cores).
+cudaError_t Fmm::Impl::launch_m2l32(const Schedule &sc, int part, cudaStream_t st) {
+    const int P1 = P1i;
+    passes::TreeView<float> tv = view32();
+    if (n_tc_tiles > 0 && &sc == &sched_nodes) {   // tensor cores
+        if (part == 0) {
+            passes::m2l_tc_kernel<<<std::min(n_tc_tiles, passes::kTcBlocksPerSM * n_sms), passes::kTcThreads, 0, st>>>(
+                tc_tiles.ptr, n_tc_tiles, tc_entries.ptr, tv.v_idx, P1, tc_tab.ptr, M32i.ptr, tc_y.ptr, tc_err.ptr);
+        } else {
+            passes::m2l_tc_reduce_kernel<<<(sc.n_m2l + passes::kTcReduceWarps - 1) / passes::kTcReduceWarps,
+                                           32 * passes::kTcReduceWarps, 0, st>>>(tv, sc.m2l.ptr, sc.n_m2l, P1,
+                                                                                 tc_y.ptr, M32i.ptr, Lm2l32i.ptr);
+        }
+        note_launch();
+    } else if (part == 0) {
+        int grid = std::min((sc.n_m2l + passes::kM2LSmallWarps - 1) / passes::kM2LSmallWarps, 2 * n_sms);
+        passes::m2l_small_kernel<<<grid, 32 * passes::kM2LSmallWarps, passes::m2l_small_smem(P1), st>>>(
+            tv, sc.m2l.ptr, sc.n_m2l, P1, m2lfull32i.ptr, M32i.ptr, Lm2l32i.ptr);
+        note_launch();
+    }
+    return cudaGetLastError();
+}
+
+// Average device time of the inner operator's M2L kernels over `reps`
+// launches each (CUDA events on st, one warm-up launch first):
+//   out[0] ms of part 0, out[1] ms of part 1 (0 on the CUDA cores),
+//   out[2] algorithmic flops per application, 8 P1i^2 per (pair, channel)
+//          (one complex multiply-add = 8 real flops),
+//   out[3] flops the tensor pipe executes per application (three TF32
+//          products of 128 x 32 x 32 per tile; 0 on the CUDA cores),
+//   out[4] engine (DC_M2L_TENSOR / DC_M2L_CUDA_CORES), out[5] list-2 pairs.
+cudaError_t Fmm::Impl::time_inner_m2l(int reps, cudaStream_t st, double out[6]) {
+    const Schedule &sc = sched_nodes;
+    for (int i = 0; i < 6; ++i) out[i] = 0.0;
+    if (!fp32 || sc.n_m2l == 0) return cudaErrorNotSupported;
+    if (!(n_tc_tiles > 0) && !(P1i <= passes::kM2LSmallP1)) return cudaErrorNotSupported;
+    cudaError_t e;
+    if (!ev0 && (e = cudaEventCreate(&ev0)) != cudaSuccess) return e;
+    if (!ev1 && (e = cudaEventCreate(&ev1)) != cudaSuccess) return e;
+    const int parts = n_tc_tiles > 0 ? 2 : 1;
+    for (int part = 0; part < parts; ++part) {
+        if ((e = launch_m2l32(sc, part, st)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(ev0, st)) != cudaSuccess) return e;
+        for (int r = 0; r < reps; ++r)
+            if ((e = launch_m2l32(sc, part, st)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(ev1, st)) != cudaSuccess) return e;
+        if ((e = cudaEventSynchronize(ev1)) != cudaSuccess) return e;
+        float ms = 0.f;
+        if ((e = cudaEventElapsedTime(&ms, ev0, ev1)) != cudaSuccess) return e;
+        out[part] = ms / reps;
+    }
+    const long long pairs = m2l_pairs_nodes;
+    out[2] = 8.0 * P1i * P1i * 3.0 * (double)pairs;
+    out[3] = n_tc_tiles > 0 ? 3.0 * 2.0 * 128.0 * 32.0 * 32.0 * n_tc_tiles : 0.0;
+    out[4] = n_tc_tiles > 0 ? DC_M2L_TENSOR : DC_M2L_CUDA_CORES;
+    out[5] = (double)pairs;
+    std::string msg;
+    return check_tc_wait(st, msg);
+}
+
 cudaError_t Fmm::Impl::passes32(const float *sb, const float *mb, int use_s, int use_m,
                                 cudaStream_t st, const Schedule &sc) {
     const int nC = tree.n_cells();
@@ -654,18 +717,9 @@ cudaError_t Fmm::Impl::passes32(const float *sb, const float *mb, int use_s, int
             note_launch();
         }
     }
-    if (sc.n_m2l > 0 && n_tc_tiles > 0 && &sc == &sched_nodes) {   // tensor cores
-        passes::m2l_tc_kernel<<<std::min(n_tc_tiles, passes::kTcBlocksPerSM * n_sms), passes::kTcThreads, 0, st>>>(
-            tc_tiles.ptr, n_tc_tiles, tc_entries.ptr, tv.v_idx, P1, tc_tab.ptr, M32i.ptr, tc_y.ptr, tc_err.ptr);
-        passes::m2l_tc_reduce_kernel<<<(sc.n_m2l + passes::kTcReduceWarps - 1) / passes::kTcReduceWarps,
-                                       32 * passes::kTcReduceWarps, 0, st>>>(tv, sc.m2l.ptr, sc.n_m2l, P1,
-                                                                             tc_y.ptr, M32i.ptr, Lm2l32i.ptr);
-        note_launch(2);
-    } else if (sc.n_m2l > 0 && P1 <= passes::kM2LSmallP1) {
-        int grid = std::min((sc.n_m2l + passes::kM2LSmallWarps - 1) / passes::kM2LSmallWarps, 2 * n_sms);
-        passes::m2l_small_kernel<<<grid, 32 * passes::kM2LSmallWarps, passes::m2l_small_smem(P1), st>>>(
-            tv, sc.m2l.ptr, sc.n_m2l, P1, m2lfull32i.ptr, M32i.ptr, Lm2l32i.ptr);
-        note_launch();
+    if (sc.n_m2l > 0 && ((n_tc_tiles > 0 && &sc == &sched_nodes) || P1 <= passes::kM2LSmallP1)) {
+        if ((e = launch_m2l32(sc, 0, st)) != cudaSuccess) return e;
+        if ((e = launch_m2l32(sc, 1, st)) != cudaSuccess) return e;
     } else if (sc.n_m2l > 0) {
         int grid = std::min((sc.n_m2l + passes::kM2LSlots - 1) / passes::kM2LSlots, 4 * n_sms);
         passes::m2l_kernel<float><<<grid, 32 * passes::kM2LSlots, passes::m2l_smem<float>(P1), st>>>(

@@ -172,6 +172,7 @@ struct Fmm::Impl {
     DevBuf<int> tc_entries, tc_err;
     DevBuf<int4> tc_tiles;
     int n_tc_tiles = 0;
+    long long m2l_pairs_nodes = 0;    // list-2 pairs of the node schedule
     DevBuf<float2> lam_ff;            // Lambda [s][g] as (hi, lo) floats
     DevBuf<double> iw64, logw64, plen64;
     DevBuf<unsigned char> heavy;      // per piece: near field evaluated in FP64
@@ -222,6 +223,8 @@ struct Fmm::Impl {
     // expansions, heavy-piece flags from the FP64 segment densities
     cudaError_t prepare_render32(const double *sb, const double *mb, cudaStream_t st);
     cudaError_t check_tc_wait(cudaStream_t st, std::string &err);
+    cudaError_t launch_m2l32(const Schedule &sc, int part, cudaStream_t st);
+    cudaError_t time_inner_m2l(int reps, cudaStream_t st, double out[6]);
     cudaError_t apply_nodes32(const double *x, double *y, bool single, cudaStream_t st);
     cudaError_t interp32(const double *node_vals, float *seg_vals, cudaStream_t st);
     // the FP32 operator at the nodes from segment values already in
