@@ -403,10 +403,10 @@ def run_ours(args):
         O, _, disc = _oracle_setup()
         est_solve, t_solve_sample = oracle_solve_sample(O, disc)
         n, dt = oracle_render_sample(O, disc, max(2.0, args.cpu_seconds - t_solve_sample))
-        t_step = est_solve + dt * npx / n
-        cpu = {"value": npx / t_step / 1e6, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+        t_cpu = est_solve + dt * npx / n
+        cpu = {"value": npx / t_cpu / 1e6, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                "cpu": cpu_model(),
-               "sample": f"oracle FP64, extrapolated step {t_step:.0f} s: dense rows of G_H/F_H for 512 "
+               "sample": f"oracle FP64, extrapolated step {t_cpu:.0f} s: dense rows of G_H/F_H for 512 "
                          f"of {disc.n_nodes} nodes (x{disc.n_nodes / 512:.1f}) and LAPACK LU of a "
                          f"4096^2 system (x(N/4096)^3) for the solve ({est_solve:.0f} s), direct-sum "
                          f"render of {n} sampled pixels of {WIDTH}x{HEIGHT} ({dt:.1f} s, x{npx / n:.0f}); "

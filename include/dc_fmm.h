@@ -254,6 +254,80 @@ dc_status dc_get_density(dc_ctx *ctx, double *sigma_out);
 /* Sets the density from host [n_nodes][3] (instead of solving). */
 dc_status dc_set_density(dc_ctx *ctx, const double *sigma_in);
 
+/* ---------------------------------------------------------------------
+ * Adaptive subdivision with local re-solve (Sec. 6.1 Adaptive Subdivision,
+ * Alg. 5; Sec. 6.3 local update of the density, Eq. 40-41, Alg. 6-7).
+ * --------------------------------------------------------------------- */
+typedef enum {
+    DC_RESOLVE_LOCAL = 0,   /* label_curves (Eq. 40-41), then the local system
+                               of Sec. 6.3 on the re-solving panels only      */
+    DC_RESOLVE_GLOBAL = 1,  /* re-solve every panel from the warm start       */
+    DC_RESOLVE_NONE = 2     /* keep the warm start as the density             */
+} dc_resolve_mode;
+
+typedef struct {
+    double eps_coef;       /* epsilon_2 of Alg. 5: a panel is split when the
+                              largest magnitude, over the colour channels, of
+                              its density's highest-order Legendre coefficient
+                              (Legendre polynomials with P_k(1) = 1, on the
+                              panel's arc-length coordinate) exceeds it      */
+    double eps_len;        /* epsilon_1 of Alg. 5: panels whose arc length
+                              (world units) is below it are never split; tie
+                              it to the pixel size of the target viewport     */
+    int resolve;           /* dc_resolve_mode                                 */
+    double label_ratio;    /* the 0.9 of Eq. 41 (0 = 0.9), in [0, 1)          */
+} dc_subdivide_options;
+
+typedef struct {
+    int n_split;           /* panels split (Alg. 5)                           */
+    int n_panels_before, n_panels_after;
+    int n_resolve_panels;  /* panels whose density was re-solved (r)          */
+    int n_label_matvec;    /* operator applications of label_curves (three
+                              unit densities each, one per colour channel)    */
+    int iters[3];          /* GMRES iterations of the (local) re-solve        */
+    double rel_resid[3];   /* ||[b - G_H sigma]_r|| / ||b_r|| after it         */
+    int converged;         /* 1 if every channel is within 10 gmres_tol       */
+    double ms_test, ms_rebuild, ms_label, ms_solve;   /* host wall time       */
+} dc_subdivide_stats;
+
+/* One round of adaptive subdivision (Alg. 5) and the re-solve of the
+ * density (Alg. 7) on the current density:
+ *  1. per panel, the highest Legendre coefficient of sigma (device); split
+ *     every panel with |c_{g-1}| > eps_coef and arc length >= eps_len into
+ *     its two halves in arc-length fraction;
+ *  2. update_quadtree / update_pre_FMM: the drawing is rebuilt on the refined
+ *     panels (the same work as dc_build_tree; the curves and colours are the
+ *     ones last given to it);
+ *  3. warm start (Sec. 6.1): the old panels' Legendre expansions evaluated at
+ *     the new nodes;
+ *  4. label_curves (Eq. 40-41, DC_RESOLVE_LOCAL): for each new half panel
+ *     alpha, v = G_H 1_alpha at every node; a panel beta is re-solved when
+ *     max v - min v over its nodes exceeds label_ratio times that over alpha
+ *     (the new halves are always re-solved);
+ *  5. the local system (G_H)_rr sigma_r = b_r - (G_H)_rc sigma_c (Sec. 6.3)
+ *     with b = (u+ + u-)/2 - F_H mu of the refined discretisation, the other
+ *     panels' densities fixed at the warm start, by GMRES (tolerance
+ *     gmres_tol relative to ||b_r||) on the correction of the warm start
+ *     with the operator FMM(S_r, ., q_r) of the context's form (the FP64
+ *     operator in the FMM forms) and the panels' inverse self-interaction
+ *     blocks as a right preconditioner.
+ * A call that splits nothing changes nothing.  Needs a density (DC_ERR_STATE
+ * otherwise); DC_ERR_ARG for bad options; errors of the rebuild as in
+ * dc_build_tree.  stats may be NULL. */
+dc_status dc_subdivide(dc_ctx *ctx, const dc_subdivide_options *opt, dc_subdivide_stats *stats);
+
+/* The current panels (after dc_subdivide, the refined ones), host outputs
+ * in dc_build_tree's format: panel_ptr [n_curves + 1], panel_start
+ * [panel_ptr[n_curves]] (either may be NULL; sizes from dc_get_sizes). */
+dc_status dc_get_panels(dc_ctx *ctx, int *panel_ptr, double *panel_start);
+
+/* Auxiliary: per-panel results of the last dc_subdivide, host outputs (any
+ * may be NULL): top_old [panels before] the test value of step 1,
+ * split_old [panels before] 1 where split, resolve_new [panels after] 1
+ * where the density was re-solved.  Errors: DC_ERR_STATE before a call. */
+dc_status dc_aux_subdivision_info(dc_ctx *ctx, double *top_old, unsigned char *split_old,
+                                  unsigned char *resolve_new);
+
 /* Node data after dc_build_tree, host outputs (any may be NULL):
  *   xy [n_nodes][2] collocation points on the solve polyline,
  *   t  [n_nodes] Bezier parameter of each node,

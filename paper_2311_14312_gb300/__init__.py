@@ -32,6 +32,8 @@ DC_X0_ONES, DC_X0_ZEROS, DC_X0_USER, DC_X0_LEARNED = 0, 1, 2, 3
 DC_MEM_DEVICE, DC_MEM_HOST = 0, 1
 DC_F32, DC_F64 = 0, 1
 DC_M2L_TENSOR, DC_M2L_CUDA_CORES = 0, 1
+DC_RESOLVE_LOCAL, DC_RESOLVE_GLOBAL, DC_RESOLVE_NONE = 0, 1, 2
+RESOLVE = {"local": DC_RESOLVE_LOCAL, "global": DC_RESOLVE_GLOBAL, "none": DC_RESOLVE_NONE}
 
 FORMS = {"dense64": DC_FORM_DENSE64, "fmm64": DC_FORM_FMM64, "fmm32": DC_FORM_FMM32}
 
@@ -61,6 +63,20 @@ class dc_solve_stats(ctypes.Structure):
                 ("ms_warm", ctypes.c_double), ("n_refine", ctypes.c_int)]
 
 
+class dc_subdivide_options(ctypes.Structure):
+    _fields_ = [("eps_coef", ctypes.c_double), ("eps_len", ctypes.c_double), ("resolve", ctypes.c_int),
+                ("label_ratio", ctypes.c_double)]
+
+
+class dc_subdivide_stats(ctypes.Structure):
+    _fields_ = [("n_split", ctypes.c_int), ("n_panels_before", ctypes.c_int),
+                ("n_panels_after", ctypes.c_int), ("n_resolve_panels", ctypes.c_int),
+                ("n_label_matvec", ctypes.c_int), ("iters", ctypes.c_int * 3),
+                ("rel_resid", ctypes.c_double * 3), ("converged", ctypes.c_int),
+                ("ms_test", ctypes.c_double), ("ms_rebuild", ctypes.c_double),
+                ("ms_label", ctypes.c_double), ("ms_solve", ctypes.c_double)]
+
+
 class dc_viewport(ctypes.Structure):
     _fields_ = [("x0", ctypes.c_double), ("y0", ctypes.c_double), ("x1", ctypes.c_double),
                 ("y1", ctypes.c_double), ("width", ctypes.c_int), ("height", ctypes.c_int)]
@@ -81,7 +97,7 @@ EXPORTS = ["dc_default_options", "dc_create", "dc_destroy", "dc_build_tree", "dc
            "dc_aux_mlp_forward", "dc_aux_mlp_loss_grad", "dc_aux_mlp_adam", "dc_aux_feature_dims",
            "dc_aux_panel_features", "dc_aux_set_warm_start_model", "dc_aux_apply_operator", "dc_aux_precond_info",
            "dc_aux_build_timings", "dc_aux_test_skip_mma_tile", "dc_aux_fp32_peak",
-           "dc_aux_time_inner_m2l"]
+           "dc_aux_time_inner_m2l", "dc_subdivide", "dc_get_panels", "dc_aux_subdivision_info"]
 
 
 def _load():
@@ -129,6 +145,9 @@ def _load():
     lib.dc_aux_test_skip_mma_tile.argtypes = [P, I]
     lib.dc_aux_fp32_peak.argtypes = [P, P]
     lib.dc_aux_time_inner_m2l.argtypes = [P, I, P]
+    lib.dc_subdivide.argtypes = [P, ctypes.POINTER(dc_subdivide_options), ctypes.POINTER(dc_subdivide_stats)]
+    lib.dc_get_panels.argtypes = [P, P, P]
+    lib.dc_aux_subdivision_info.argtypes = [P, P, P, P]
     for name in EXPORTS:
         if name not in ("dc_destroy", "dc_last_error", "dc_status_string", "dc_abi_version",
                         "dc_aux_kernel_launches", "dc_aux_mlp_param_count",
@@ -297,6 +316,31 @@ class Context:
         """dc_aux_test_skip_mma_tile: hold back the MMAs of one tensor-core
         M2L tile (its bounded wait then runs out); -1 switches it off."""
         self._check(_get_lib().dc_aux_test_skip_mma_tile(self._h, int(tile)))
+
+    # ---------------------------------------------------- subdivision --
+    def subdivide(self, eps_coef, eps_len=0.0, resolve="local", label_ratio=0.0) -> dc_subdivide_stats:
+        """dc_subdivide: one round of Alg. 5 and the re-solve of Alg. 7."""
+        o = dc_subdivide_options(float(eps_coef), float(eps_len), RESOLVE.get(resolve, resolve),
+                                 float(label_ratio))
+        st = dc_subdivide_stats()
+        self._check(_get_lib().dc_subdivide(self._h, ctypes.byref(o), ctypes.byref(st)))
+        return st
+
+    def panels(self):
+        """dc_get_panels: (panel_ptr, panel_start) of the current panels."""
+        sz = self.sizes()
+        ptr = np.zeros(sz.n_curves + 1, np.int32)
+        start = np.zeros(sz.n_panels)
+        self._check(_get_lib().dc_get_panels(self._h, _ptr(ptr), _ptr(start)))
+        return ptr, start
+
+    def subdivision_info(self, n_before: int):
+        """dc_aux_subdivision_info: (top_old, split_old, resolve_new)."""
+        top = np.zeros(n_before)
+        split = np.zeros(n_before, np.uint8)
+        res = np.zeros(self.sizes().n_panels, np.uint8)
+        self._check(_get_lib().dc_aux_subdivision_info(self._h, _ptr(top), _ptr(split), _ptr(res)))
+        return top, split.astype(bool), res.astype(bool)
 
     def time_inner_m2l(self, reps: int = 20) -> dict:
         """dc_aux_time_inner_m2l as a dict."""

@@ -47,6 +47,17 @@ struct dc_ctx {
     bool warm_a1_valid = false;
     double build_ms[11] = {};   // dc_aux_build_timings
     dc::PanelFeatures pfeat;
+    // the drawing as given to dc_build_tree (host copies), for dc_subdivide
+    int in_ncurves = 0;
+    std::vector<double> in_ctrl, in_start, in_col;
+    std::vector<int> in_ptr;
+    // adaptive subdivision (Alg. 5-7): device scratch and the last call's
+    // per-panel results
+    DevBuf<double> ad_sig_old, ad_r0, ad_tmp, ad_tmp2, ad_q, ad_E, ad_top, ad_range;
+    DevBuf<int2> ad_pmap;
+    DevBuf<unsigned char> ad_mask;
+    std::vector<double> last_top;
+    std::vector<unsigned char> last_split, last_resolve;
     ~dc_ctx() {
         if (gw) dc::gmres_work_destroy(gw);
     }
@@ -146,6 +157,29 @@ struct FmmOp : dc::Operator {
     dc::Fmm *fmm;
     cudaError_t apply(const double *x, double *y, cudaStream_t st) override {
         return fmm->apply_single_layer(x, y, st);
+    }
+};
+
+// The operator of the local system of Sec. 6.3 (Eq. 27 restricted to the
+// re-solving panels r): v -> mask (G_H B (mask v)), with B the panels'
+// inverse self-interaction blocks as a right preconditioner in the FMM forms
+// (block diagonal, so it keeps the restriction) and none in the dense form.
+struct MaskedOp : dc::Operator {
+    dc_ctx *ctx = nullptr;
+    const unsigned char *pmask = nullptr;
+    double *t1 = nullptr, *t2 = nullptr;
+    cudaError_t apply(const double *x, double *y, cudaStream_t st) override {
+        const int N = ctx->dg.N, g = ctx->dg.g;
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(t1, x, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+        if ((e = dc::launch_node_mask(t1, pmask, N, g, st)) != cudaSuccess) return e;
+        if (ctx->opt.form == DC_FORM_DENSE64) {
+            if ((e = dc::launch_dense_gemv(ctx->AG.ptr, N, t1, y, st)) != cudaSuccess) return e;
+        } else {
+            if ((e = ctx->fmm->apply_block_jacobi(t1, t2, st)) != cudaSuccess) return e;
+            if ((e = ctx->fmm->apply_single_layer(t2, y, st)) != cudaSuccess) return e;
+        }
+        return dc::launch_node_mask(y, pmask, N, g, st);
     }
 };
 
@@ -298,6 +332,17 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
     dc_status st = dc::discretise(n_curves, ctrl, panel_ptr, panel_start, colours, ctx->opt.g,
                                   ctx->opt.s_per_panel, ctx->geo, msg);
     if (st != DC_OK) return fail(ctx, st, msg);
+    {   // keep the inputs for dc_subdivide (copies first: they may alias)
+        const int np = panel_ptr[n_curves];
+        std::vector<double> c(ctrl, ctrl + 8 * (size_t)n_curves), ps(panel_start, panel_start + np),
+            col(colours, colours + 12 * (size_t)n_curves);
+        std::vector<int> pp(panel_ptr, panel_ptr + n_curves + 1);
+        ctx->in_ncurves = n_curves;
+        ctx->in_ctrl.swap(c);
+        ctx->in_start.swap(ps);
+        ctx->in_col.swap(col);
+        ctx->in_ptr.swap(pp);
+    }
     lap(0);
     const dc::Geometry &G = ctx->geo;
     dc::DevGeom &D = ctx->dg;
@@ -891,6 +936,246 @@ dc_status dc_aux_precond_info(dc_ctx *ctx, double *out) {
     if (!out) return fail(ctx, DC_ERR_ARG, "precond_info: NULL output");
     if (ctx->state < 1 || !ctx->fmm) return fail(ctx, DC_ERR_STATE, "precond_info: needs an FMM form after build_tree");
     ctx->fmm->precond_info(out);
+    return DC_OK;
+}
+
+// ------------------------------------------------ adaptive subdivision --
+dc_status dc_get_panels(dc_ctx *ctx, int *panel_ptr, double *panel_start) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "get_panels: call build_tree first");
+    if (panel_ptr) std::memcpy(panel_ptr, ctx->in_ptr.data(), sizeof(int) * ctx->in_ptr.size());
+    if (panel_start) std::memcpy(panel_start, ctx->in_start.data(), sizeof(double) * ctx->in_start.size());
+    return DC_OK;
+}
+
+dc_status dc_aux_subdivision_info(dc_ctx *ctx, double *top_old, unsigned char *split_old,
+                                  unsigned char *resolve_new) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (ctx->last_top.empty()) return fail(ctx, DC_ERR_STATE, "subdivision_info: no dc_subdivide call yet");
+    if (top_old) std::memcpy(top_old, ctx->last_top.data(), sizeof(double) * ctx->last_top.size());
+    if (split_old) std::memcpy(split_old, ctx->last_split.data(), ctx->last_split.size());
+    if (resolve_new) std::memcpy(resolve_new, ctx->last_resolve.data(), ctx->last_resolve.size());
+    return DC_OK;
+}
+
+dc_status dc_subdivide(dc_ctx *ctx, const dc_subdivide_options *o, dc_subdivide_stats *stats) {
+    using clk = std::chrono::steady_clock;
+    auto ms_since = [](clk::time_point a) { return std::chrono::duration<double, std::milli>(clk::now() - a).count(); };
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (!o) return fail(ctx, DC_ERR_ARG, "subdivide: NULL options");
+    if (ctx->state < 2) return fail(ctx, DC_ERR_STATE, "subdivide: needs a density (solve_density or set_density)");
+    if (!std::isfinite(o->eps_coef) || o->eps_coef < 0.0 || !std::isfinite(o->eps_len) || o->eps_len < 0.0 ||
+        o->resolve < DC_RESOLVE_LOCAL || o->resolve > DC_RESOLVE_NONE || !(o->label_ratio >= 0.0) ||
+        !(o->label_ratio < 1.0))
+        return fail(ctx, DC_ERR_ARG, "subdivide: need eps_coef, eps_len >= 0, a dc_resolve_mode and 0 <= label_ratio < 1");
+    dc_subdivide_stats S;
+    std::memset(&S, 0, sizeof(S));
+    const double ratio = o->label_ratio > 0.0 ? o->label_ratio : 0.9;
+    cudaStream_t s = ctx->stream;
+    const int g = ctx->dg.g, P_old = ctx->dg.n_panels, N_old = ctx->dg.N, sp = ctx->dg.s;
+    auto t0 = clk::now();
+    // ---- Alg. 5: the highest Legendre coefficient of sigma per panel (device)
+    std::vector<double> q(g);
+    dc::legendre_top_row(g, q.data());
+    DC_CK(ctx, ctx->ad_q.ensure(g), "subdivide: alloc");
+    DC_CK(ctx, ctx->ad_top.ensure(P_old), "subdivide: alloc");
+    DC_CK(ctx, cudaMemcpyAsync(ctx->ad_q.ptr, q.data(), sizeof(double) * g, cudaMemcpyHostToDevice, s), "subdivide");
+    DC_CK(ctx, dc::launch_legendre_top(ctx->sigma.ptr, P_old, g, ctx->ad_q.ptr, ctx->ad_top.ptr, s), "subdivide: test");
+    std::vector<double> top(P_old);
+    DC_CK(ctx, cudaMemcpyAsync(top.data(), ctx->ad_top.ptr, sizeof(double) * P_old, cudaMemcpyDeviceToHost, s),
+          "subdivide");
+    DC_CK(ctx, cudaStreamSynchronize(s), "subdivide");
+    // panel arc length: sum over its segments of chord x (arc / chord) weight
+    std::vector<unsigned char> split(P_old, 0);
+    int n_split = 0;
+    for (int p = 0; p < P_old; ++p) {
+        double len = 0.0;
+        for (int k = 0; k < sp; ++k) {
+            const double *e = &ctx->geo.seg_xy[4 * ((size_t)p * sp + k)];
+            len += std::hypot(e[2] - e[0], e[3] - e[1]) * ctx->geo.seg_w[(size_t)p * sp + k];
+        }
+        if (top[p] > o->eps_coef && len >= o->eps_len) {
+            split[p] = 1;
+            ++n_split;
+        }
+    }
+    S.n_split = n_split;
+    S.n_panels_before = S.n_panels_after = P_old;
+    S.ms_test = ms_since(t0);
+    ctx->last_top = top;
+    ctx->last_split = split;
+    if (n_split == 0) {
+        ctx->last_resolve.assign(P_old, 0);
+        S.converged = 1;
+        if (stats) *stats = S;
+        return DC_OK;
+    }
+    // ---- the refined panels: each split panel becomes its two halves in
+    // arc-length fraction
+    const int nc = ctx->in_ncurves;
+    std::vector<int> new_ptr(nc + 1, 0);
+    std::vector<double> new_start;
+    std::vector<int2> pmap;
+    for (int i = 0; i < nc; ++i) {
+        for (int p = ctx->in_ptr[i]; p < ctx->in_ptr[i + 1]; ++p) {
+            const double a = ctx->in_start[p], b = p + 1 < ctx->in_ptr[i + 1] ? ctx->in_start[p + 1] : 1.0;
+            if (split[p]) {
+                new_start.push_back(a);
+                pmap.push_back(make_int2(p, 1));
+                new_start.push_back(0.5 * (a + b));
+                pmap.push_back(make_int2(p, 2));
+            } else {
+                new_start.push_back(a);
+                pmap.push_back(make_int2(p, 0));
+            }
+        }
+        new_ptr[i + 1] = int(new_start.size());
+    }
+    DC_CK(ctx, ctx->ad_sig_old.ensure(size_t(3) * N_old), "subdivide: alloc");
+    DC_CK(ctx, cudaMemcpyAsync(ctx->ad_sig_old.ptr, ctx->sigma.ptr, sizeof(double) * 3 * N_old,
+                               cudaMemcpyDeviceToDevice, s), "subdivide");
+    // ---- update_quadtree / update_pre_FMM: the whole build on the refined
+    // panels
+    auto t1 = clk::now();
+    {
+        const std::vector<double> ctrl = ctx->in_ctrl, col = ctx->in_col;
+        dc_status st = dc_build_tree(ctx, nc, ctrl.data(), new_ptr.data(), new_start.data(), col.data());
+        if (st != DC_OK) return st;
+    }
+    S.ms_rebuild = ms_since(t1);
+    const int P_new = ctx->dg.n_panels, N_new = ctx->dg.N;
+    S.n_panels_after = P_new;
+    // ---- warm start (Sec. 6.1): the old Legendre expansions at the new nodes
+    std::vector<double> E((size_t)3 * g * g);
+    dc::split_matrices(g, E.data());
+    DC_CK(ctx, ctx->ad_E.ensure(E.size()), "subdivide: alloc");
+    DC_CK(ctx, ctx->ad_pmap.ensure(pmap.size()), "subdivide: alloc");
+    DC_CK(ctx, cudaMemcpyAsync(ctx->ad_E.ptr, E.data(), sizeof(double) * E.size(), cudaMemcpyHostToDevice, s),
+          "subdivide");
+    DC_CK(ctx, cudaMemcpyAsync(ctx->ad_pmap.ptr, pmap.data(), sizeof(int2) * pmap.size(), cudaMemcpyHostToDevice, s),
+          "subdivide");
+    DC_CK(ctx, dc::launch_split_interp(ctx->ad_sig_old.ptr, ctx->ad_pmap.ptr, ctx->ad_E.ptr, g, P_new,
+                                       ctx->sigma.ptr, s), "subdivide: warm start");
+    // ---- right-hand side of the refined system (Alg. 3), FP64
+    auto apply_G = [&](const double *x, double *y) -> cudaError_t {
+        if (ctx->opt.form == DC_FORM_DENSE64) return dc::launch_dense_gemv(ctx->AG.ptr, N_new, x, y, s);
+        return ctx->fmm->apply_single_layer(x, y, s);
+    };
+    if (ctx->opt.form == DC_FORM_DENSE64)
+        DC_CK(ctx, dc::launch_dense_gemv(ctx->AF.ptr, N_new, ctx->mu.ptr, ctx->fmu.ptr, s), "subdivide: rhs");
+    else
+        DC_CK(ctx, ctx->fmm->apply_double_layer(ctx->mu.ptr, ctx->fmu.ptr, s), "subdivide: rhs");
+    DC_CK(ctx, dc::launch_rhs(ctx->dg, ctx->fmu.ptr, ctx->b.ptr, s), "subdivide: rhs");
+    const size_t n3 = size_t(3) * N_new;
+    DC_CK(ctx, ctx->ad_r0.ensure(n3), "subdivide: alloc");
+    DC_CK(ctx, ctx->ad_tmp.ensure(n3), "subdivide: alloc");
+    DC_CK(ctx, ctx->ad_tmp2.ensure(n3), "subdivide: alloc");
+    DC_CK(ctx, ctx->ad_range.ensure(size_t(3) * P_new), "subdivide: alloc");
+    // ---- label_curves (Eq. 40-41): unit density on each new half panel,
+    // three per operator application (one per colour channel)
+    auto t2 = clk::now();
+    std::vector<unsigned char> res(P_new, 0);
+    if (o->resolve == DC_RESOLVE_GLOBAL) {
+        res.assign(P_new, 1);
+    } else if (o->resolve == DC_RESOLVE_LOCAL) {
+        std::vector<int> alpha;
+        for (int p = 0; p < P_new; ++p)
+            if (pmap[p].y != 0) {
+                alpha.push_back(p);
+                res[p] = 1;
+            }
+        std::vector<double> range((size_t)3 * P_new);
+        for (size_t j = 0; j < alpha.size(); j += 3) {
+            int three[3];
+            for (int c = 0; c < 3; ++c) three[c] = j + c < alpha.size() ? alpha[j + c] : -1;
+            DC_CK(ctx, dc::launch_unit_density(ctx->ad_tmp.ptr, N_new, g, three, s), "subdivide: labels");
+            DC_CK(ctx, apply_G(ctx->ad_tmp.ptr, ctx->ad_tmp2.ptr), "subdivide: labels");
+            DC_CK(ctx, dc::launch_panel_range(ctx->ad_tmp2.ptr, P_new, g, ctx->ad_range.ptr, s), "subdivide: labels");
+            DC_CK(ctx, cudaMemcpyAsync(range.data(), ctx->ad_range.ptr, sizeof(double) * range.size(),
+                                       cudaMemcpyDeviceToHost, s), "subdivide: labels");
+            DC_CK(ctx, cudaStreamSynchronize(s), "subdivide: labels");
+            S.n_label_matvec++;
+            for (int c = 0; c < 3; ++c) {
+                if (three[c] < 0) continue;
+                const double da = range[3 * (size_t)three[c] + c];
+                for (int b = 0; b < P_new; ++b)
+                    if (range[3 * (size_t)b + c] > ratio * da) res[b] = 1;
+            }
+        }
+    }
+    S.ms_label = ms_since(t2);
+    for (int p = 0; p < P_new; ++p) S.n_resolve_panels += res[p];
+    ctx->last_resolve = res;
+    // ---- the local system (Sec. 6.3): (G_H)_rr sigma_r = b_r - (G_H)_rc sigma_c,
+    // solved for the correction delta_r of the warm start sigma0:
+    //   (G_H)_rr delta_r = [b - G_H sigma0]_r
+    auto t3 = clk::now();
+    if (o->resolve != DC_RESOLVE_NONE) {
+        DC_CK(ctx, ctx->ad_mask.ensure(P_new), "subdivide: alloc");
+        DC_CK(ctx, cudaMemcpyAsync(ctx->ad_mask.ptr, res.data(), P_new, cudaMemcpyHostToDevice, s), "subdivide");
+        DC_CK(ctx, apply_G(ctx->sigma.ptr, ctx->ad_tmp.ptr), "subdivide: residual");
+        DC_CK(ctx, dc::vec_residual(ctx->b.ptr, ctx->ad_tmp.ptr, ctx->ad_r0.ptr, int(n3), s), "subdivide: residual");
+        DC_CK(ctx, dc::launch_node_mask(ctx->ad_r0.ptr, ctx->ad_mask.ptr, N_new, g, s), "subdivide: residual");
+        DC_CK(ctx, cudaMemcpyAsync(ctx->ad_tmp2.ptr, ctx->b.ptr, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s),
+              "subdivide");
+        DC_CK(ctx, dc::launch_node_mask(ctx->ad_tmp2.ptr, ctx->ad_mask.ptr, N_new, g, s), "subdivide");
+        double nb[3], nr[3];
+        DC_CK(ctx, dc::vec_norms3(ctx->gw, ctx->ad_tmp2.ptr, N_new, nb, s), "subdivide");
+        DC_CK(ctx, dc::vec_norms3(ctx->gw, ctx->ad_r0.ptr, N_new, nr, s), "subdivide");
+        double rel = 1.0;
+        bool need = false;
+        for (int c = 0; c < 3; ++c)
+            if (nr[c] > ctx->opt.gmres_tol * nb[c]) {
+                need = true;
+                rel = std::min(rel, ctx->opt.gmres_tol * nb[c] / nr[c]);
+            }
+        if (need) {
+            MaskedOp op;
+            op.ctx = ctx;
+            op.pmask = ctx->ad_mask.ptr;
+            DevBuf<double> z, t1b, t2b;
+            DC_CK(ctx, z.alloc(n3), "subdivide: alloc");
+            DC_CK(ctx, t1b.alloc(n3), "subdivide: alloc");
+            DC_CK(ctx, t2b.alloc(n3), "subdivide: alloc");
+            op.t1 = t1b.ptr;
+            op.t2 = t2b.ptr;
+            DC_CK(ctx, cudaMemsetAsync(z.ptr, 0, sizeof(double) * n3, s), "subdivide");
+            dc::GmresResult gr;
+            std::string msg;
+            cudaError_t ce = dc::gmres_solve(ctx->gw, op, N_new, ctx->ad_r0.ptr, z.ptr, true, false,
+                                             std::max(rel, 1e-15), ctx->opt.gmres_restart,
+                                             ctx->opt.gmres_max_iter, s, gr, msg);
+            if (ce != cudaSuccess) return cuda_fail(ctx, ce, msg.empty() ? "subdivide: gmres" : msg.c_str());
+            for (int c = 0; c < 3; ++c) S.iters[c] = gr.iters[c];
+            // delta = B z on r (the right preconditioner), sigma = sigma0 + delta
+            if (ctx->opt.form == DC_FORM_DENSE64) {
+                DC_CK(ctx, cudaMemcpyAsync(ctx->ad_tmp.ptr, z.ptr, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s),
+                      "subdivide");
+            } else {
+                DC_CK(ctx, dc::launch_node_mask(z.ptr, ctx->ad_mask.ptr, N_new, g, s), "subdivide");
+                DC_CK(ctx, ctx->fmm->apply_block_jacobi(z.ptr, ctx->ad_tmp.ptr, s), "subdivide");
+            }
+            DC_CK(ctx, dc::launch_node_mask(ctx->ad_tmp.ptr, ctx->ad_mask.ptr, N_new, g, s), "subdivide");
+            DC_CK(ctx, dc::vec_axpy(ctx->sigma.ptr, ctx->ad_tmp.ptr, int(n3), s), "subdivide");
+        }
+        // the local system's residual after the re-solve
+        DC_CK(ctx, apply_G(ctx->sigma.ptr, ctx->ad_tmp.ptr), "subdivide: residual");
+        DC_CK(ctx, dc::vec_residual(ctx->b.ptr, ctx->ad_tmp.ptr, ctx->ad_r0.ptr, int(n3), s), "subdivide: residual");
+        DC_CK(ctx, dc::launch_node_mask(ctx->ad_r0.ptr, ctx->ad_mask.ptr, N_new, g, s), "subdivide: residual");
+        DC_CK(ctx, dc::vec_norms3(ctx->gw, ctx->ad_r0.ptr, N_new, nr, s), "subdivide");
+        S.converged = 1;
+        for (int c = 0; c < 3; ++c) {
+            S.rel_resid[c] = nb[c] > 0.0 ? nr[c] / nb[c] : 0.0;
+            if (S.rel_resid[c] > 10.0 * ctx->opt.gmres_tol) S.converged = 0;
+        }
+    }
+    S.ms_solve = ms_since(t3);
+    ctx->state = 2;
+    ctx->seg_density_valid = false;
+    if (stats) *stats = S;
     return DC_OK;
 }
 

@@ -49,6 +49,17 @@ void note_launch(int n = 1);
 cudaError_t measure_fp32_peak(cudaStream_t st, double *tflops, double *ms_out);
 long long kernel_launches();
 
+// Adaptive subdivision and local re-solve (adaptive.cu; Sec. 6.1, 6.3)
+void legendre_top_row(int g, double *q);          // last row of the Legendre transform
+void split_matrices(int g, double *E);            // [3][g][g]: keep, left half, right half
+cudaError_t launch_legendre_top(const double *sigma, int n_panels, int g, const double *q, double *top,
+                                cudaStream_t st);
+cudaError_t launch_split_interp(const double *sig_old, const int2 *pmap, const double *E, int g, int n_new,
+                                double *sig_new, cudaStream_t st);
+cudaError_t launch_unit_density(double *x, int N, int g, const int panels[3], cudaStream_t st);
+cudaError_t launch_panel_range(const double *v, int n_panels, int g, double *out, cudaStream_t st);
+cudaError_t launch_node_mask(double *v, const unsigned char *pmask, int N, int g, cudaStream_t st);
+
 // ---------------------------------------------------------- device util --
 template <typename T>
 struct DevBuf {

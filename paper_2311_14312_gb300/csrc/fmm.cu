@@ -1196,6 +1196,10 @@ cudaError_t Fmm::apply_inner(const double *x, double *y, cudaStream_t st) {
     return impl_->check_tc_wait(st, msg);
 }
 
+cudaError_t Fmm::apply_block_jacobi(const double *x, double *y, cudaStream_t st) {
+    return launch_block_apply(impl_->pinv.ptr, impl_->D->n_panels, impl_->D->g, x, y, st);
+}
+
 cudaError_t Fmm::apply_precond(const double *x, double *y, cudaStream_t st) {
     return impl_->precond(x, y, st);
 }

@@ -31,6 +31,9 @@ public:
     // Test hook of the tensor-core M2L: the CTA that takes `tile` issues no
     // MMA for it, so its bounded wait runs out (-1 = off).
     cudaError_t set_mma_skip_tile(int tile, cudaStream_t st);
+    // y = B x with B the panels' inverse self-interaction blocks of G_H (the
+    // first level of the two-level preconditioner alone).
+    cudaError_t apply_block_jacobi(const double *x, double *y, cudaStream_t st);
     // Device time of the inner operator's M2L kernels (fmm32.cu).
     cudaError_t time_inner_m2l(int reps, cudaStream_t st, double out[6]);
     // GMRES with this operator (Alg. 3); x holds x0 on entry.
