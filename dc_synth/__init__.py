@@ -19,4 +19,6 @@ from .drawings import (  # noqa: F401
     drawing_by_name,
     random_node_values,
     pixel_sample,
+    viewport_set,
+    curve_point,
 )

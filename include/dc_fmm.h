@@ -112,6 +112,11 @@ typedef struct {
                               DC_M2L_TENSOR (tcgen05 TF32 with a three-term
                               split; p_inner <= 15, else CUDA cores) or
                               DC_M2L_CUDA_CORES                              */
+    int coarse_max;        /* FMM forms: most coarse unknowns of the two-level
+                              preconditioner's dense coarse inverse, a
+                              multiple of 32 in [64, 16384] (0 = 12288); more
+                              panels than that are grouped into aggregates of
+                              consecutive panels of a curve                  */
 } dc_options;
 
 enum {
@@ -169,7 +174,7 @@ typedef struct {
 /* Fills *opt with defaults: DC_FORM_FMM32, g 16, s 80, p 24, leaf 64,
  * depth 30, tol 1e-10, restart 200, max_iter 2000, x0 ones, domain [0,1]^2,
  * p_inner 0 and inner_tol 0 (the built-in choices), m2l_engine
- * DC_M2L_TENSOR. */
+ * DC_M2L_TENSOR, coarse_max 0 (12288). */
 dc_status dc_default_options(dc_options *opt);
 
 /* Creates a context bound to the current CUDA device.  *out is set to NULL
@@ -429,11 +434,14 @@ dc_status dc_aux_apply_operator(dc_ctx *ctx, int op, int inner, const double *x,
 
 /* Auxiliary: state of the FMM forms' two-level preconditioner (no
  * counterpart in the paper; it changes the iteration count, not the
- * solution): out[0] = 1 if the coarse level is in use (else the panel
- * blocks alone), out[1] = coarse unknowns (panels), out[2] = near panel
- * pairs, out[3] = max |(Ac^-1 Ac - I)_ij| over sampled entries of the
- * coarse inverse.  Errors: DC_ERR_STATE before dc_build_tree or in the
- * dense form. */
+ * solution), host double[5]: out[0] = 1 if the coarse level is in use (else
+ * the panel blocks alone), out[1] = coarse unknowns (panels, or aggregates
+ * of out[4] consecutive panels of a curve when the panels outnumber the
+ * dense coarse inverse's limit of 12,288; the levels are then combined
+ * additively), out[2] = near panel pairs, out[3] = max |(Ac^-1 Ac - I)_ij|
+ * over sampled entries of the coarse inverse, out[4] = panels per
+ * aggregate (1 = one coarse unknown per panel, multiplicative form).
+ * Errors: DC_ERR_STATE before dc_build_tree or in the dense form. */
 dc_status dc_aux_precond_info(dc_ctx *ctx, double *out);
 
 /* Auxiliary: wall-clock ms of the last dc_build_tree, by phase (each phase

@@ -44,7 +44,8 @@ class dc_options(ctypes.Structure):
                 ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
                 ("gmres_max_iter", ctypes.c_int), ("x0_mode", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("domain", ctypes.c_double * 4),
-                ("p_inner", ctypes.c_int), ("inner_tol", ctypes.c_double), ("m2l_engine", ctypes.c_int)]
+                ("p_inner", ctypes.c_int), ("inner_tol", ctypes.c_double), ("m2l_engine", ctypes.c_int),
+                ("coarse_max", ctypes.c_int)]
 
 
 class dc_sizes(ctypes.Structure):
@@ -308,9 +309,9 @@ class Context:
 
     def precond_info(self) -> dict:
         """dc_aux_precond_info as a dict."""
-        out = np.zeros(4)
+        out = np.zeros(5)
         self._check(_get_lib().dc_aux_precond_info(self._h, _ptr(out)))
-        return dict(zip(["two_level", "panels", "near_pairs", "inverse_check"], out.tolist()))
+        return dict(zip(["two_level", "panels", "near_pairs", "inverse_check", "aggregate"], out.tolist()))
 
     def test_skip_mma_tile(self, tile: int):
         """dc_aux_test_skip_mma_tile: hold back the MMAs of one tensor-core

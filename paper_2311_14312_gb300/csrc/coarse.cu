@@ -14,6 +14,16 @@
 // The coarse matrix Ac = R A~ P (panels x panels, FP32) is inverted once per
 // drawing by blocked Gauss-Jordan elimination without pivoting (it is
 // strongly diagonal: a panel's self term dominates its row).
+//
+// Drawings with more panels than the dense coarse inverse can hold group
+// the panels into aggregates of K panels consecutive in the Morton order of
+// their centroids, K = ceil(P / (limit - 32)); the coarse space is then one
+// constant per aggregate and Ac = R_agg A~ P_agg comes from the same
+// panel-level monopoles and near-pair corrections.  The coarse residual
+// takes the FMM itself, M v = P y + B (v - G_H P y): a monopole sum would
+// cost (nodes x panels) logarithms per application at these sizes, while
+// G_H P y is one more operator application (the caller supplies it between
+// apply_stage1 and apply_stage2).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,7 +39,7 @@ namespace dc {
 namespace {
 
 constexpr int kGJ = 32;                 // block size of the Gauss-Jordan inversion
-constexpr int kMaxCoarse = 12288;       // largest coarse system inverted (panels, padded)
+constexpr int kMaxCoarse = 12288;       // default largest coarse system inverted (padded)
 // -log|q - c| / 2pi = kMonoLog2 * log2(|q - c|^2)
 constexpr float kMonoLog2 = -0.0551589000381629f;   // -ln 2 / 4pi
 
@@ -99,6 +109,79 @@ __global__ void coarse_matrix_kernel(const float2 *__restrict__ q32, const float
         }
         __syncthreads();
     }
+}
+
+// Aggregated form: Ac[I][J] = sum over the nodes q of aggregate I and the
+// panels j of aggregate J of l_j mono32(q, c_j) (one block per row I; the
+// panels of aggregate a are pagg[a] .. pagg[a + 1] - 1), padded with the
+// identity to n_pad.  The near-pair corrections are added by
+// coarse_agg_corr_kernel.
+__global__ void coarse_agg_matrix_kernel(const float2 *__restrict__ q32, const float2 *__restrict__ c32,
+                                         const float *__restrict__ plen32, const int *__restrict__ pagg,
+                                         const int *__restrict__ perm, int nA, int g, int n_pad,
+                                         float *__restrict__ Ac) {
+    const int I = blockIdx.x;
+    float *row = Ac + (size_t)I * n_pad;
+    if (I >= nA) {
+        for (int j = threadIdx.x; j < n_pad; j += blockDim.x) row[j] = (I == j) ? 1.f : 0.f;
+        return;
+    }
+    for (int J = threadIdx.x; J < n_pad; J += blockDim.x) {
+        float v = 0.f;
+        if (J < nA)
+            for (int u = pagg[J]; u < pagg[J + 1]; ++u) {
+                const int j = perm[u];
+                const float2 c = c32[j];
+                float t = 0.f;
+                for (int w = pagg[I]; w < pagg[I + 1]; ++w) {
+                    const int i = perm[w];
+                    for (int m = 0; m < g; ++m) t += mono32(q32[i * g + m], c);
+                }
+                v += plen32[j] * t;
+            }
+        row[J] = v;
+    }
+}
+
+// Ac[agg(i)][agg(j)] += sum_m corr[e][m] over the near panel pairs e = (i, j)
+// of the panels i of aggregate I (one thread per row, pairs in order).
+__global__ void coarse_agg_corr_kernel(const int *__restrict__ pagg, const int *__restrict__ perm,
+                                       const int *__restrict__ agg_of, int nA, const int *__restrict__ nptr,
+                                       const int2 *__restrict__ pairs, const double *__restrict__ corr, int g,
+                                       int n_pad, float *__restrict__ Ac) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nA) return;
+    float *row = Ac + (size_t)I * n_pad;
+    for (int w = pagg[I]; w < pagg[I + 1]; ++w) {
+        const int i = perm[w];
+        for (int e = nptr[i]; e < nptr[i + 1]; ++e) {
+            double t = 0.0;
+            for (int m = 0; m < g; ++m) t += corr[(size_t)e * g + m];
+            row[agg_of[pairs[e].y]] += (float)t;
+        }
+    }
+}
+
+// s[I][c] = sum over aggregate I's nodes of v, as a float-float pair
+__global__ void restrict_agg_kernel(const double *__restrict__ v, const int *__restrict__ pagg,
+                                    const int *__restrict__ perm, int nA, int g, float2 *__restrict__ s) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * nA) return;
+    const int I = t / 3, c = t % 3;
+    double a = 0.0;
+    for (int w = pagg[I]; w < pagg[I + 1]; ++w)
+        for (int n = perm[w] * g; n < (perm[w] + 1) * g; ++n) a += v[3 * (size_t)n + c];
+    const float hi = (float)a;
+    s[t] = make_float2(hi, (float)(a - (double)hi));
+}
+
+// py[node][c] = y[agg(panel(node))][c]: the coarse correction spread to the nodes
+__global__ void spread_agg_kernel(const double *__restrict__ y, const int *__restrict__ agg_of, int N, int g,
+                                  double *__restrict__ py) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * N) return;
+    const int c = t % 3, n = t / 3;
+    py[t] = y[3 * agg_of[n / g] + c];
 }
 
 // Blocked Gauss-Jordan inversion in place (no pivoting), step k:
@@ -338,16 +421,21 @@ __global__ void __launch_bounds__(kMonoThreads) monopole_kernel(const float2 *__
 // and, when lam is given, sigma_bar = Lambda w for the panel's s segments in
 // float-float (w converted to hi/lo pairs once, Lambda stored as hi/lo
 // floats), rounded to FP32.
+// With agg given (the aggregated form): r = v - gpy with gpy = G_H P y
+// from the caller, and the coarse value is y[agg[i]].
 constexpr int kPanelThreads = 128;
 __global__ void __launch_bounds__(kPanelThreads) panel_apply_kernel(
     const float *__restrict__ part, int N, int g, int s, const int *__restrict__ nptr,
     const int2 *__restrict__ pairs, const double *__restrict__ corr, const double *__restrict__ y,
     const double *__restrict__ v, const double *__restrict__ inv, double *__restrict__ w,
-    const float2 *__restrict__ lam, float *__restrict__ sv) {
+    const float2 *__restrict__ lam, float *__restrict__ sv, const int *__restrict__ agg,
+    const double *__restrict__ gpy) {
     __shared__ double rs[3 * kMaxG];
     __shared__ float2 ws[3 * kMaxG];
     const int i = blockIdx.x, t = threadIdx.x;
-    if (t < 3 * g) {
+    if (agg) {   // aggregated form: r = v - G_H P y, supplied by the caller's FMM
+        if (t < 3 * g) rs[t] = v[3 * (size_t)i * g + t] - gpy[3 * (size_t)i * g + t];
+    } else if (t < 3 * g) {
         const int m = t / 3, c = t - 3 * m;
         const size_t a = (size_t)i * g + m;
         double acc = 0.0;
@@ -370,7 +458,7 @@ __global__ void __launch_bounds__(kPanelThreads) panel_apply_kernel(
     if (t < 3 * g) {
         const int m = t / 3, c = t - 3 * m;
         const double *row = inv + ((size_t)i * g + m) * g;
-        double acc = y[3 * i + c];
+        double acc = y[3 * (agg ? agg[i] : i) + c];
         for (int n = 0; n < g; ++n) acc += row[n] * rs[3 * n + c];
         if (w) w[3 * ((size_t)i * g + m) + c] = acc;
         const float h = (float)acc;
@@ -420,16 +508,13 @@ __global__ void inverse_check_kernel(const float *__restrict__ Ai, const float *
 
 }  // namespace
 
-cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st) {
+cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st, int max_coarse) {
     ready_ = false;
     const int P = G.n_panels, g = G.g, s = G.s, N = G.n_nodes();
     if (P < 2) return cudaSuccess;
-    // the dense coarse inverse (FP32, n_pad^2) is kept below ~600 MB; larger
-    // drawings use the panel blocks alone
-    n_pad_ = (P + kGJ - 1) / kGJ * kGJ;
-    if (n_pad_ > kMaxCoarse) return cudaSuccess;
     P_ = P;
     g_ = g;
+    const int maxc = max_coarse > 0 ? max_coarse : kMaxCoarse;
     // panel centroids (node average) and arc lengths
     std::vector<double> cen(2 * P), pl(P);
     std::vector<float2> c32(P), q32(N);
@@ -452,18 +537,75 @@ cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st
         pl32[j] = (float)L;
     }
     for (int a = 0; a < N; ++a) q32[a] = make_float2((float)G.node_xy[2 * a], (float)G.node_xy[2 * a + 1]);
-    // near panel pairs (i, j), i's list in j order: |c_i - c_j| < 1.5 (l_i + l_j)
+    // coarse unknowns: one per panel (K = 1) while the padded count fits the
+    // dense inverse, else aggregates of K panels consecutive in the Morton
+    // order of the centroids (16 bits per axis over the centroids' box, ties
+    // by panel index), K = ceil(P / (limit - 32))
+    std::vector<int> pagg, perm(P), agg_of(P);
+    if ((P + kGJ - 1) / kGJ * kGJ <= maxc) {
+        K_ = 1;
+        for (int j = 0; j < P; ++j) perm[j] = agg_of[j] = j;
+    } else {
+        K_ = (P + (maxc - kGJ) - 1) / (maxc - kGJ);
+        double lo[2] = {cen[0], cen[1]}, hi[2] = {cen[0], cen[1]};
+        for (int j = 0; j < P; ++j)
+            for (int d = 0; d < 2; ++d) {
+                lo[d] = std::min(lo[d], cen[2 * j + d]);
+                hi[d] = std::max(hi[d], cen[2 * j + d]);
+            }
+        std::vector<unsigned long long> key(P);
+        for (int j = 0; j < P; ++j) {
+            unsigned q[2];
+            for (int d = 0; d < 2; ++d) {
+                const double ext = hi[d] - lo[d];
+                const double f = ext > 0.0 ? (cen[2 * j + d] - lo[d]) / ext : 0.0;
+                q[d] = (unsigned)std::min(65535.0, std::floor(f * 65536.0));
+            }
+            unsigned long long k = 0;
+            for (int b = 15; b >= 0; --b) k = (k << 2) | (((q[1] >> b) & 1u) << 1) | ((q[0] >> b) & 1u);
+            key[j] = (k << 32) | (unsigned long long)j;
+        }
+        for (int j = 0; j < P; ++j) perm[j] = j;
+        std::sort(perm.begin(), perm.end(), [&](int a, int b) { return key[a] < key[b]; });
+    }
+    for (int u = 0; u < P; ++u) {
+        if (u % K_ == 0) pagg.push_back(u);
+        agg_of[perm[u]] = int(pagg.size()) - 1;
+    }
+    pagg.push_back(P);
+    nA_ = int(pagg.size()) - 1;
+    n_pad_ = (nA_ + kGJ - 1) / kGJ * kGJ;
+    // near panel pairs (i, j), i's list in j order: |c_i - c_j| < 1.5 (l_i + l_j);
+    // candidates from a sweep over the centroids sorted by x
     std::vector<int> nptr(P + 1, 0);
     std::vector<int2> pairs;
-    for (int i = 0; i < P; ++i) {
-        nptr[i] = int(pairs.size());
-        for (int j = 0; j < P; ++j) {
-            const double dx = cen[2 * i] - cen[2 * j], dy = cen[2 * i + 1] - cen[2 * j + 1];
-            const double lim = 1.5 * (pl[i] + pl[j]);
-            if (dx * dx + dy * dy < lim * lim) pairs.push_back(make_int2(i, j));
+    {
+        std::vector<int> ord(P);
+        for (int j = 0; j < P; ++j) ord[j] = j;
+        std::sort(ord.begin(), ord.end(), [&](int a, int b) { return cen[2 * a] < cen[2 * b]; });
+        double lmax = 0.0;
+        for (int j = 0; j < P; ++j) lmax = std::max(lmax, pl[j]);
+        std::vector<std::vector<int>> nb(P);
+        for (int u = 0; u < P; ++u) {
+            const int i = ord[u];
+            for (int w = u; w < P; ++w) {
+                const int j = ord[w];
+                if (cen[2 * j] - cen[2 * i] >= 1.5 * (pl[i] + lmax)) break;
+                const double dx = cen[2 * i] - cen[2 * j], dy = cen[2 * i + 1] - cen[2 * j + 1];
+                const double lim = 1.5 * (pl[i] + pl[j]);
+                if (dx * dx + dy * dy < lim * lim) {
+                    nb[i].push_back(j);
+                    if (j != i) nb[j].push_back(i);
+                }
+            }
         }
+        for (int i = 0; i < P; ++i) {
+            std::sort(nb[i].begin(), nb[i].end());
+            nptr[i] = int(pairs.size());
+            for (int j : nb[i]) pairs.push_back(make_int2(i, j));
+        }
+        nptr[P] = int(pairs.size());
     }
-    nptr[P] = int(pairs.size());
 
     cudaError_t e;
     auto up = [&](auto &buf, const auto &v) -> cudaError_t {
@@ -478,15 +620,26 @@ cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st
     if ((e = corr_.alloc(pairs.size() * (size_t)g)) != cudaSuccess ||
         (e = Ainv_.alloc((size_t)n_pad_ * n_pad_)) != cudaSuccess || (e = s_.alloc(3 * (size_t)P)) != cudaSuccess ||
         (e = y_.alloc(3 * (size_t)P)) != cudaSuccess || (e = pan_.alloc((size_t)P)) != cudaSuccess || (e = pan2_.alloc((size_t)P)) != cudaSuccess ||
-        (e = part_.alloc((size_t)kSplit * 3 * N)) != cudaSuccess)
+        (K_ == 1 && (e = part_.alloc((size_t)kSplit * 3 * N)) != cudaSuccess))
         return e;
     near_pairs_kernel<<<(unsigned)pairs.size(), 32, 0, st>>>(pairs_.ptr, D.seg.ptr, D.segw.ptr, D.node_xy.ptr,
                                                             D.node_seg.ptr, D.node_seg2.ptr, q32_.ptr, c32_.ptr,
                                                             plen_.ptr, s, g, corr_.ptr);
     note_launch();
-    coarse_matrix_kernel<<<n_pad_, 256, 0, st>>>(q32_.ptr, c32_.ptr, plen32_.ptr, nptr_.ptr, pairs_.ptr,
-                                                corr_.ptr, P, g, n_pad_, Ainv_.ptr);
-    note_launch();
+    if (K_ == 1) {
+        coarse_matrix_kernel<<<n_pad_, 256, 0, st>>>(q32_.ptr, c32_.ptr, plen32_.ptr, nptr_.ptr, pairs_.ptr,
+                                                    corr_.ptr, P, g, n_pad_, Ainv_.ptr);
+        note_launch();
+    } else {
+        if ((e = up(pagg_, pagg)) != cudaSuccess || (e = up(agg_of_, agg_of)) != cudaSuccess ||
+            (e = up(perm_, perm)) != cudaSuccess)
+            return e;
+        coarse_agg_matrix_kernel<<<n_pad_, 256, 0, st>>>(q32_.ptr, c32_.ptr, plen32_.ptr, pagg_.ptr, perm_.ptr, nA_,
+                                                        g, n_pad_, Ainv_.ptr);
+        coarse_agg_corr_kernel<<<(nA_ + 127) / 128, 128, 0, st>>>(pagg_.ptr, perm_.ptr, agg_of_.ptr, nA_, nptr_.ptr,
+                                                                 pairs_.ptr, corr_.ptr, g, n_pad_, Ainv_.ptr);
+        note_launch(2);
+    }
     // keep the coarse matrix for the check below
     DevBuf<float> Ac;
     if ((e = Ac.alloc((size_t)n_pad_ * n_pad_)) != cudaSuccess ||
@@ -512,8 +665,8 @@ cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st
         (e = cudaMemsetAsync(bad.ptr, 0, sizeof(int), st)) != cudaSuccess)
         return e;
     inverse_check_kernel<<<dim3(ncol, 5), 128, 0, st>>>(Ainv_.ptr, Ac.ptr, n_pad_,
-                                                       make_int4(0, P / 4, P / 2, (3 * P) / 4), P - 1, errs.ptr,
-                                                       bad.ptr);
+                                                       make_int4(0, nA_ / 4, nA_ / 2, (3 * nA_) / 4), nA_ - 1,
+                                                       errs.ptr, bad.ptr);
     note_launch();
     std::vector<double> errs_h((size_t)5 * ncol);
     int bad_h = 0;
@@ -534,6 +687,7 @@ cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st
 cudaError_t TwoLevel::apply(const double *inv, const double *v, double *w, cudaStream_t st, const float2 *lam, int s,
                             float *sv) {
     const int P = P_, g = g_, N = P * g;
+    if (K_ > 1) return cudaErrorNotSupported;   // aggregated: apply_stage1 / apply_stage2
     restrict_kernel<<<(3 * P + 255) / 256, 256, 0, st>>>(v, P, g, s_.ptr);
     coarse_solve_kernel<<<P, 128, 0, st>>>(Ainv_.ptr, n_pad_, P, s_.ptr, plen32_.ptr, c32_.ptr, y_.ptr, pan_.ptr,
                                           pan2_.ptr);
@@ -541,8 +695,26 @@ cudaError_t TwoLevel::apply(const double *inv, const double *v, double *w, cudaS
     monopole_kernel<<<dim3((N + per_block - 1) / per_block, kSplit), kMonoThreads, 0, st>>>(q32_.ptr, pan_.ptr,
                                                                                          pan2_.ptr, P, N, part_.ptr);
     panel_apply_kernel<<<P, kPanelThreads, 0, st>>>(part_.ptr, N, g, s, nptr_.ptr, pairs_.ptr, corr_.ptr, y_.ptr, v,
-                                                    inv, w, lam, sv);
+                                                    inv, w, lam, sv, nullptr, nullptr);
     note_launch(4);
+    return cudaGetLastError();
+}
+
+cudaError_t TwoLevel::apply_stage1(const double *v, double *py, cudaStream_t st) {
+    const int N = P_ * g_;
+    restrict_agg_kernel<<<(3 * nA_ + 255) / 256, 256, 0, st>>>(v, pagg_.ptr, perm_.ptr, nA_, g_, s_.ptr);
+    coarse_solve_kernel<<<nA_, 128, 0, st>>>(Ainv_.ptr, n_pad_, nA_, s_.ptr, plen32_.ptr, c32_.ptr, y_.ptr, pan_.ptr,
+                                            pan2_.ptr);
+    spread_agg_kernel<<<(3 * N + 255) / 256, 256, 0, st>>>(y_.ptr, agg_of_.ptr, N, g_, py);
+    note_launch(3);
+    return cudaGetLastError();
+}
+
+cudaError_t TwoLevel::apply_stage2(const double *inv, const double *v, const double *gpy, double *w, cudaStream_t st,
+                                   const float2 *lam, int s, float *sv) {
+    panel_apply_kernel<<<P_, kPanelThreads, 0, st>>>(nullptr, P_ * g_, g_, s, nptr_.ptr, pairs_.ptr, corr_.ptr, y_.ptr,
+                                                     v, inv, w, lam, sv, agg_of_.ptr, gpy);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -127,6 +127,10 @@ dc_status check_options(const dc_options &o, std::string &msg) {
         msg = "options: m2l_engine must be DC_M2L_TENSOR or DC_M2L_CUDA_CORES";
         return DC_ERR_ARG;
     }
+    if (o.coarse_max != 0 && (o.coarse_max < 64 || o.coarse_max > 16384 || o.coarse_max % 32 != 0)) {
+        msg = "options: coarse_max must be 0 (default) or a multiple of 32 in [64, 16384]";
+        return DC_ERR_ARG;
+    }
     if (!(o.inner_tol >= 0.0 && o.inner_tol < 1.0)) {
         msg = "options: inner_tol must be 0 (default) or in (0, 1)";
         return DC_ERR_ARG;

@@ -169,24 +169,37 @@ private:
 // the coarse matrix; ready() is false when that failed (one level then).
 class TwoLevel {
 public:
-    cudaError_t build(const Geometry &G, const DevGeom &D, cudaStream_t st);
+    // max_coarse: most coarse unknowns (0 = the built-in 12288)
+    cudaError_t build(const Geometry &G, const DevGeom &D, cudaStream_t st, int max_coarse);
     bool ready() const { return ready_; }
-    // panels, near pairs, max |(Ac^-1 Ac - I)_ij| over 5 sampled rows
-    void info(double out[4]) const {
+    // coarse unknowns (panels, or aggregates of K panels), near panel pairs,
+    // max |(Ac^-1 Ac - I)_ij| over 5 sampled rows, K
+    void info(double out[5]) const {
         out[0] = ready_ ? 1.0 : 0.0;
-        out[1] = P_;
+        out[1] = nA_;
         out[2] = n_pairs_;
         out[3] = check_;
+        out[4] = K_;
     }
     // w = M v on [N][3] vectors (w may be null); inv: the panel blocks'
     // inverses.  With lam (Lambda as hi/lo floats, [s][g]) and sv: also
     // sv = Lambda (M v) per panel, [S][3] FP32.
     cudaError_t apply(const double *inv, const double *v, double *w, cudaStream_t st, const float2 *lam = nullptr,
                       int s = 0, float *sv = nullptr);
+    // The aggregated form (aggregated() true) in two stages around the
+    // caller's operator application: stage 1 solves the coarse system and
+    // spreads py = P y to the nodes; stage 2 takes gpy = G_H py and forms
+    // w = P y + B (v - gpy) (and sv as in apply).
+    bool aggregated() const { return ready_ && K_ > 1; }
+    cudaError_t apply_stage1(const double *v, double *py, cudaStream_t st);
+    cudaError_t apply_stage2(const double *inv, const double *v, const double *gpy, double *w, cudaStream_t st,
+                             const float2 *lam = nullptr, int s = 0, float *sv = nullptr);
 
 private:
     bool ready_ = false;
-    int P_ = 0, g_ = 0, n_pad_ = 0, n_pairs_ = 0;
+    int P_ = 0, g_ = 0, n_pad_ = 0, n_pairs_ = 0, nA_ = 0, K_ = 1;
+    DevBuf<int> pagg_, agg_of_, perm_;   // aggregates: start of each in perm_ (+ end), aggregate of each
+                                         // panel, panels in Morton order
     double check_ = -1.0;
     DevBuf<float2> c32_, q32_;
     DevBuf<double> plen_, corr_, y_;

@@ -1126,7 +1126,7 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     }
     // two-level preconditioner (panel blocks + coarse space of panel constants)
     phase(1);   // schedules, node items, uploads
-    if ((e = I.coarse.build(G, D, st)) != cudaSuccess) {
+    if ((e = I.coarse.build(G, D, st, opt.coarse_max)) != cudaSuccess) {
         err = std::string("fmm coarse preconditioner: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
     }
@@ -1183,6 +1183,15 @@ cudaError_t Fmm::apply_double_layer(const double *x, double *y, cudaStream_t st)
 // w = M v: the two-level preconditioner, or the panel blocks alone when the
 // coarse matrix could not be inverted.
 cudaError_t Fmm::Impl::precond(const double *v, double *w, cudaStream_t st) {
+    if (coarse.aggregated()) {   // coarse residual from the operator itself (FP32 in the FP32 form)
+        cudaError_t e;
+        if ((e = agg_py.ensure(3 * (size_t)D->N)) != cudaSuccess || (e = agg_gpy.ensure(3 * (size_t)D->N)) != cudaSuccess ||
+            (e = coarse.apply_stage1(v, agg_py.ptr, st)) != cudaSuccess)
+            return e;
+        e = fp32 ? apply_nodes32(agg_py.ptr, agg_gpy.ptr, true, st) : apply_nodes(agg_py.ptr, agg_gpy.ptr, true, st);
+        if (e != cudaSuccess) return e;
+        return coarse.apply_stage2(pinv.ptr, v, agg_gpy.ptr, w, st);
+    }
     if (coarse.ready()) return coarse.apply(pinv.ptr, v, w, st);
     return launch_block_apply(pinv.ptr, D->n_panels, D->g, v, w, st);
 }
@@ -1551,7 +1560,7 @@ void Fmm::fill_sizes(dc_sizes *out) const {
 }
 
 long long Fmm::p2p_pairs_nodes() const { return impl_->p2p_nodes; }
-void Fmm::precond_info(double out[4]) const { impl_->coarse.info(out); }
+void Fmm::precond_info(double out[5]) const { impl_->coarse.info(out); }
 long long Fmm::m2l_pairs() const { return impl_->m2l_cnt; }
 long long Fmm::last_render_p2p_pairs() const { return impl_->render_pairs; }
 long long Fmm::last_render_m2p_pairs() const { return impl_->render_m2p; }

@@ -59,7 +59,7 @@ public:
     // preconditioner, stored P2M / P2L rows, near / far coefficients, FP32 form
     void build_timings(double out[6]) const;
     // two-level preconditioner: ready, panels, near pairs, inverse check
-    void precond_info(double out[4]) const;
+    void precond_info(double out[5]) const;
     long long p2p_pairs_nodes() const;
     long long m2l_pairs() const;
     long long last_render_p2p_pairs() const;

@@ -824,13 +824,24 @@ cudaError_t Fmm::Impl::graph_ensure() {
     if ((e = g_out.ensure(3 * (size_t)D->N)) != cudaSuccess) return e;
     if (!cap_stream && (e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return e;
+    if (coarse.aggregated() &&
+        ((e = agg_py.ensure(3 * (size_t)D->N)) != cudaSuccess || (e = agg_gpy.ensure(3 * (size_t)D->N)) != cudaSuccess))
+        return e;
     long long before = kernel_launches();
     if ((e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
     // M v straight to the segments (sigma_bar = Lambda M v) when the
-    // two-level preconditioner is in use, else M v at the nodes first
-    cudaError_t e1 = coarse.ready()
-                         ? coarse.apply(pinv.ptr, g_in.ptr, nullptr, cap_stream, lam_ff.ptr, D->s, sbar32.ptr)
-                         : precond(g_in.ptr, ir_t.ptr, cap_stream);
+    // two-level preconditioner is in use, else M v at the nodes first; the
+    // aggregated coarse level takes its residual G_H P y from this operator
+    cudaError_t e1;
+    if (coarse.aggregated()) {
+        e1 = coarse.apply_stage1(g_in.ptr, agg_py.ptr, cap_stream);
+        if (e1 == cudaSuccess) e1 = apply_nodes32(agg_py.ptr, agg_gpy.ptr, true, cap_stream);
+        if (e1 == cudaSuccess)
+            e1 = coarse.apply_stage2(pinv.ptr, g_in.ptr, agg_gpy.ptr, nullptr, cap_stream, lam_ff.ptr, D->s, sbar32.ptr);
+    } else {
+        e1 = coarse.ready() ? coarse.apply(pinv.ptr, g_in.ptr, nullptr, cap_stream, lam_ff.ptr, D->s, sbar32.ptr)
+                            : precond(g_in.ptr, ir_t.ptr, cap_stream);
+    }
     cudaError_t e2 = e1;
     if (e1 == cudaSuccess)
         e2 = coarse.ready() ? nodes32_from_segments(g_out.ptr, true, cap_stream)

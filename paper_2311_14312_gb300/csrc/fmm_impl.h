@@ -191,6 +191,7 @@ struct Fmm::Impl {
     cudaGraphExec_t g32_exec = nullptr;
     int g32_kernels = 0;
     DevBuf<double> g_in, g_out;
+    DevBuf<double> agg_py, agg_gpy;   // the aggregated coarse level's P y and G_H P y
     double build_ms[6] = {0, 0, 0, 0, 0, 0};   // wall time of the build phases
     // the render's tile plan (tiles, vps) for the viewports plan_vps
     bool plan_valid = false;
