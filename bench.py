@@ -41,6 +41,16 @@ NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
 FALLBACK_BF16_TFLOPS = 1900.0
 
 
+# The large cases: the 2000-curve drawing rendered into 64 uneven viewports
+# (256..4096 px, zoom 1..1e6, centred on curve points) in one call, and the
+# 20k-curve drawing with near-touching pairs rendered at 8192^2.
+LARGE = {
+    "batched2000": dict(tol=1e-10, viewports="64 seeded viewports (seed 20231129)"),
+    "near20k": dict(tol=1e-8, viewports="[0,1]^2 at 8192x8192"),
+}
+LARGE_DOMAIN = (-0.5, -0.5, 1.5, 1.5)
+
+
 def measured_peaks() -> dict:
     """The driver-written measured peaks of this machine's GPUs, if present."""
     try:
@@ -79,6 +89,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 FMM comparison")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, *LARGE],
+                    help="mixed200 (the headline) or one of the large cases, measured on their own")
     return ap.parse_args()
 
 
@@ -458,10 +470,101 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_large(args):
+    """A large case on one GPU: every step solves (GMRES to the case's
+    tolerance) and renders all of its viewports; the inputs (1.4-7 M
+    segments, 0.7-4.6 GB of output) exceed L2.  The plain FP64 FMM form runs
+    once on the same inputs."""
+    import numpy as np
+    import torch
+
+    import paper_2311_14312_gb300 as P
+    from dc_synth import drawing_by_name, viewport_set
+
+    cfg = LARGE[args.workload]
+    torch.cuda.set_device(0)
+    d = drawing_by_name(args.workload)
+    vps = (viewport_set(d, seed=20231129, n=64) if args.workload == "batched2000"
+           else [(0.0, 0.0, 1.0, 1.0, 8192, 8192)])
+    npx = sum(v[4] * v[5] for v in vps)
+    opts = dict(p=24, leaf_size=64, gmres_tol=cfg["tol"], gmres_restart=200, gmres_max_iter=3000,
+                domain=LARGE_DOMAIN)
+    ctx = P.Context(form="fmm32", g=d.g, s_per_panel=d.s_per_panel, **opts)
+    t0 = time.perf_counter()
+    ctx.build_drawing(d)
+    build_s = time.perf_counter() - t0
+    rgb = torch.empty((npx, 3), dtype=torch.float32, device="cuda")
+    rgb8 = torch.empty((npx, 3), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ctx.solve_density()
+        ctx.render_viewport(vps, rgb, rgb8)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = P.kernel_launches()
+    step_ms, solve_ms, render_ms = [], [], []
+    for _ in range(args.steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        st = ctx.solve_density()
+        e1.record(stream)
+        ctx.render_viewport(vps, rgb, rgb8)
+        e2.record(stream)
+        e2.synchronize()
+        step_ms.append(e0.elapsed_time(e2))
+        solve_ms.append(e0.elapsed_time(e1))
+        render_ms.append(e1.elapsed_time(e2))
+    launches = P.kernel_launches() - launches0
+    clk = clocks.stop()
+    rs = ctx.render_viewport(vps, rgb, rgb8, stats=True)
+    fp32 = P.fp32_peak()
+    achieved = rs.eval_flops / (rs.ms_eval * 1e-3) / 1e12 if rs.ms_eval > 0 else None
+    # the plain FP64 FMM form on the same inputs, once (its pixels: the
+    # chosen form's colour differences on a sample of pixels)
+    chosen = rgb[::97].float().cpu().numpy()
+    ctx.close()
+    pctx = P.Context(form="fmm64", g=d.g, s_per_panel=d.s_per_panel, **opts)
+    pctx.build_drawing(d)
+    del rgb8
+    prgb = torch.empty((npx, 3), dtype=torch.float32, device="cuda")
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    pst = pctx.solve_density()
+    e1.record(stream)
+    pctx.render_viewport(vps, prgb)
+    e2.record(stream)
+    e2.synchronize()
+    ref = prgb[::97].float().cpu().numpy()
+    plain = {"form": "fmm64", "solve_ms": e0.elapsed_time(e1), "render_ms": e1.elapsed_time(e2),
+             "mpix_s": npx / (e0.elapsed_time(e2) * 1e-3) / 1e6, "gmres_iters": list(pst.iters),
+             "chosen_max_abs_err_vs_plain_every_97th_pixel": float(np.abs(chosen - ref).max())}
+    pctx.close()
+    t_step = statistics.mean(step_ms)
+    line = {"metric": METRIC, "value": npx / (t_step * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "curves": d.n_curves, "nodes": d.n_nodes,
+                       "segments": d.n_segments, "viewports": cfg["viewports"], "pixels": npx, "form": "fmm32",
+                       **{k: v for k, v in opts.items() if k != "domain"},
+                       "l2": "inputs and outputs larger than L2"},
+            "build_s": build_s, "solve_ms": statistics.mean(solve_ms), "render_ms": statistics.mean(render_ms),
+            "render_mpix_s": npx / (statistics.mean(render_ms) * 1e-3) / 1e6, "gmres_iters": list(st.iters),
+            "gmres_rel_resid": max(st.rel_resid), "plain_form": plain,
+            "roofline": {"bound": "alu", "kernel": "eval32_kernel<0> (L2P + M2P + P2P per pixel)",
+                         "achieved": achieved, "peak": fp32["tflops"], "unit": "TFLOP/s",
+                         "frac": (achieved / fp32["tflops"]) if achieved else None, "traffic": None,
+                         "eval_ms": rs.ms_eval, "p2p_pairs": rs.p2p_pairs, "m2p_pairs": rs.m2p_pairs},
+            "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != WORKLOAD:
+        run_large(args)
     else:
         run_ours(args)
 

@@ -99,7 +99,10 @@ __global__ void interp32_kernel(const float2 *__restrict__ lam, const double *__
 // strongly singular densities) are evaluated in FP64: the FP32 rounding of
 // a coefficient is ~6e-8 of its size.  hL: sum_l |Lt_l| > kBigCoef; hM:
 // 10 |Mt_0| + sum_k |Mt_k| > kBigCoef (max over channels).
-constexpr double kBigCoef = 50.0;
+#ifndef DC_BIG_COEF
+#define DC_BIG_COEF 50.0
+#endif
+constexpr double kBigCoef = DC_BIG_COEF;
 __global__ void big_coef_kernel(const double2 *__restrict__ L, const double2 *__restrict__ M, int n,
                                 int P1, unsigned char *__restrict__ hL, unsigned char *__restrict__ hM) {
     // one warp per cell, lanes over the coefficients (coalesced); magnitudes in FP32, since this
@@ -128,6 +131,41 @@ __global__ void big_coef_kernel(const double2 *__restrict__ L, const double2 *__
     }
 }
 
+// The near field of the pixel kernel works in each leaf's frame scaled by
+// 1 / rho (rho the leaf width, a power of two); this adds the part
+// it leaves out to the leaf's local coefficient L_0 in FP64:
+//   L_0 += 2 pi log(rho) sum_i ssg_i rho len'_i,
+// i over the leaf's list-1 pieces that are not heavy, with the pixel
+// kernel's own FP32 values ssg_i = (-w_i / 2 pi) sigma_bar_c and len'_i =
+// len_i / rho, so that the centred sums plus L_0 equal the plain sums.  The
+// large log(rho) terms meet the far field's constant here, in FP64, instead
+// of in the FP32 near-field sums.  One warp per cell, a fixed order.
+__global__ void near_centre_kernel(const int *__restrict__ uf_ptr, const int *__restrict__ uf_idx,
+                                   const int *__restrict__ pseg, const float *__restrict__ pw,
+                                   const float *__restrict__ plen, const unsigned char *__restrict__ heavy,
+                                   const float *__restrict__ sb, const float *__restrict__ iw, int nC, int P1,
+                                   double2 *__restrict__ L) {
+    const int cell = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (cell >= nC || uf_ptr[cell + 1] == uf_ptr[cell]) return;
+    const float iwf = iw[cell];
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int f = uf_ptr[cell] + lane; f < uf_ptr[cell + 1]; f += 32) {
+        const int i = uf_idx[f];
+        if (heavy && heavy[i]) continue;
+        const int seg = pseg[i];
+        const float wgt = -pw[i] * 0.15915494309189533577f;
+        const double lenp = (double)(plen[i] * iwf);
+        for (int ch = 0; ch < 3; ++ch) acc[ch] += (double)(wgt * sb[3 * (size_t)seg + ch]) * lenp;
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int ch = 0; ch < 3; ++ch) acc[ch] += __shfl_xor_sync(0xffffffffu, acc[ch], o);
+    if (lane == 0) {
+        const double iwd = (double)iwf;
+        const double k = -6.283185307179586477 * log(iwd) / iwd;   // 2 pi rho log(rho)
+        for (int ch = 0; ch < 3; ++ch) L[((size_t)cell * 3 + ch) * P1].x += k * acc[ch];
+    }
+}
+
 template <typename From, typename To>
 __global__ void narrow_kernel(const From *__restrict__ a, To *__restrict__ b, size_t n) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -139,7 +177,10 @@ __global__ void narrow_kernel(const From *__restrict__ a, To *__restrict__ b, si
 
 // heavy[i] = 1 when max_c |sigma_bar| w len or |mu_bar| w len of piece i
 // exceeds kHeavy: its near-field terms are then summed in FP64.
-constexpr double kHeavy = 1.0;
+#ifndef DC_HEAVY
+#define DC_HEAVY 1.0
+#endif
+constexpr double kHeavy = DC_HEAVY;
 __global__ void heavy_kernel(const double *__restrict__ sb, const double *__restrict__ mb,
                              const int *__restrict__ pseg, const double *__restrict__ pw,
                              const double *__restrict__ plen, unsigned char *__restrict__ heavy, int np) {
@@ -162,6 +203,7 @@ constexpr int kEvThreads = kEvalTile * kEvalTile;
 #define DC_EVAL_STAGE 128
 #endif
 constexpr int kEvBlocksPerSM = DC_EVAL_MINBLOCKS;
+
 constexpr int kStage = DC_EVAL_STAGE;
 
 struct EvalArgs32 {
@@ -181,6 +223,7 @@ struct EvalArgs32 {
     const double *sb64, *mb64;
     const unsigned char *heavy, *hL, *hM;
     const double2 *M64, *L64;
+
     // list mode
     const float2 *q32;
     const double *q64;
@@ -320,9 +363,26 @@ __global__ void __launch_bounds__(kEvThreads, kEvBlocksPerSM) eval32_kernel(Eval
             e1 += m1.x - lz * Ms[P1].x;
             e2 += m2.x - lz * Ms[2 * P1].x;
         }
-        u0 = e0 * kInv2PiF;
-        u1 = e1 * kInv2PiF;
-        u2 = e2 * kInv2PiF;
+        // the far field goes to the FP64 sums: the FP32 near-field sums then
+        // start from zero instead of from a value the near field may cancel
+        h0 += (double)e0 * kInv2Pi;
+        h1 += (double)e1 * kInv2Pi;
+        h2 += (double)e2 * kInv2Pi;
+    }
+    // The near field works in the leaf's frame scaled by 1 / rho, rho the
+    // leaf width: its logarithms are then log(r / rho), O(1) for the pieces
+    // of list 1, so the single-layer terms (weights times rho) stay O(len)
+    // and their FP32 rounding does not pile up where large densities cancel.
+    // The constant rest, log(rho) times the weighted lengths, was added to
+    // the leaf's local coefficient L_0 in FP64 (near_centre_kernel).
+    // Quadtree widths are powers of two, so scaling a (hi, lo) pair by the
+    // FP32 1 / width is exact.
+    {
+        const float iwq = t.iw[leaf];
+        qxh *= iwq;
+        qxl *= iwq;
+        qyh *= iwq;
+        qyl *= iwq;
     }
     // P2P over list 1 (App. D): the leaf's list-1 pieces, flattened in list
     // order, staged kStage at a time
@@ -334,15 +394,25 @@ __global__ void __launch_bounds__(kEvThreads, kEvBlocksPerSM) eval32_kernel(Eval
             for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
                 int i = t.uf_idx[f0 + s];
                 const double *P = a.t64.pc + 4 * (size_t)i;
-                split2(P[0] - cxB, sx1h[s], sx1l[s]);
-                split2(P[1] - cyB, sy1h[s], sy1l[s]);
-                split2(P[2] - cxB, sx2h[s], sx2l[s]);
-                split2(P[3] - cyB, sy2h[s], sy2l[s]);
-                slen[s] = t.plen[i];
+                const float iwf = t.iw[leaf], rho = 1.f / iwf;   // exact powers of two
+                float h, l;
+                split2(P[0] - cxB, h, l);
+                sx1h[s] = h * iwf;
+                sx1l[s] = l * iwf;
+                split2(P[1] - cyB, h, l);
+                sy1h[s] = h * iwf;
+                sy1l[s] = l * iwf;
+                split2(P[2] - cxB, h, l);
+                sx2h[s] = h * iwf;
+                sx2l[s] = l * iwf;
+                split2(P[3] - cyB, h, l);
+                sy2h[s] = h * iwf;
+                sy2l[s] = l * iwf;
+                slen[s] = t.plen[i] * iwf;
                 int seg = t.pseg[i];
                 float wgt = -t.pw[i] * kInv2PiF;
                 for (int ch = 0; ch < 3; ++ch) {
-                    ssg[ch][s] = a.use_s ? wgt * a.sb[3 * (size_t)seg + ch] : 0.f;
+                    ssg[ch][s] = a.use_s ? (wgt * a.sb[3 * (size_t)seg + ch]) * rho : 0.f;
                     smg[ch][s] = a.use_m ? wgt * a.mb[3 * (size_t)seg + ch] : 0.f;
                 }
                 sseg[s] = seg;
@@ -400,7 +470,11 @@ __global__ void __launch_bounds__(kEvThreads, kEvBlocksPerSM) eval32_kernel(Eval
                         const double *P = a.t64.pc + 4 * (size_t)sidx[s];
                         double il64, ph64;
                         seg_ilog_phi_f64(qx64, qy64, P[0], P[1], P[2], P[3], false, il64, ph64);
-                        ilog = (float)il64;
+                        // world units to the scaled frame: il / rho - len' log(rho)
+                        // (FP32 from here: these pieces are rare, and nothing
+                        // double-precision is kept live across the loop for them)
+                        const float iwr = __ldg(t.iw + leaf);
+                        ilog = (float)il64 * iwr + len * __logf(iwr);
                         phi = (float)ph64;
                     } else {
                         float ilen = 1.f / len;
@@ -744,20 +818,21 @@ cudaError_t Fmm::Impl::prepare_render32(const double *sb, const double *mb, cuda
     cudaError_t e = to_f32_density(sb, mb, st);
     if (e != cudaSuccess) return e;
     if ((e = passes(sb, mb, 1, 1, st, sched_all)) != cudaSuccess) return e;
-    size_t n = (size_t)tree.n_cells() * 3 * P1;
-    int th = 256;
-    narrow_kernel<double2, float2><<<(unsigned)((n + th - 1) / th), th, 0, st>>>(M.ptr, M32.ptr, n);
-    note_launch();
-    narrow_kernel<double2, float2><<<(unsigned)((n + th - 1) / th), th, 0, st>>>(L.ptr, L32.ptr, n);
-    note_launch();
-    int np = int(tree.pc_seg.size());
+    const int th = 256, np = int(tree.pc_seg.size()), nC = tree.n_cells();
     if (np > 0) {
         heavy_kernel<<<(np + th - 1) / th, th, 0, st>>>(sb, mb, pseg.ptr, pw.ptr, plen64.ptr, heavy.ptr, np);
         note_launch();
     }
-    int nC = tree.n_cells();
+    near_centre_kernel<<<(unsigned)(((size_t)nC * 32 + th - 1) / th), th, 0, st>>>(
+        uf_ptr.ptr, uf_idx.ptr, pseg.ptr, pw32.ptr, plen32.ptr, np > 0 ? heavy.ptr : nullptr, sbar32.ptr, iw32.ptr, nC,
+        P1, L.ptr);
+    note_launch();
     big_coef_kernel<<<(unsigned)(((size_t)nC * 32 + th - 1) / th), th, 0, st>>>(L.ptr, M.ptr, nC, P1, heavyL.ptr, heavyM.ptr);
     note_launch();
+    const size_t n = (size_t)nC * 3 * P1;
+    narrow_kernel<double2, float2><<<(unsigned)((n + th - 1) / th), th, 0, st>>>(M.ptr, M32.ptr, n);
+    narrow_kernel<double2, float2><<<(unsigned)((n + th - 1) / th), th, 0, st>>>(L.ptr, L32.ptr, n);
+    note_launch(2);
     return cudaGetLastError();
 }
 
@@ -879,6 +954,7 @@ cudaError_t Fmm::Impl::render_tiles32(int n_tiles, void *rgb, int rgb_dtype,
     a.sb64 = sb64;
     a.mb64 = mb64;
     a.heavy = heavy.ptr;
+
     a.t = dt32();
     a.t64 = dt();
     a.items = tiles.ptr;
@@ -907,6 +983,7 @@ cudaError_t Fmm::Impl::eval_points32(int n_items, double *out, const double *sb6
     a.sb64 = sb64;
     a.mb64 = mb64;
     a.heavy = heavy.ptr;
+
     a.hL = heavyL.ptr;
     a.hM = heavyM.ptr;
     a.M64 = M.ptr;
