@@ -117,6 +117,16 @@ typedef struct {
                               multiple of 32 in [64, 16384] (0 = 12288); more
                               panels than that are grouped into aggregates of
                               consecutive panels of a curve                  */
+    double adapt_ratio;    /* dc_build_tree with panel_ptr and panel_start both
+                              NULL splits panels adaptively: bisect (in
+                              arc-length fraction) while a panel is longer than
+                              adapt_ratio x its distance to the nearest other
+                              curve (0 = 0.2) ...                            */
+    int adapt_max_level;   /* ... for at most this many bisections (0 = 8) ... */
+    int adapt_min_panels;  /* ... with at least this many panels per curve
+                              (0 = 2) ...                                    */
+    double adapt_max_len;  /* ... and no panel longer than this (0 = 0.5);
+                              measured on 256-point polylines per curve      */
 } dc_options;
 
 enum {
@@ -133,7 +143,7 @@ typedef struct {
 
 typedef struct {
     int iters[3];          /* GMRES iterations per colour channel            */
-    double rel_resid[3];   /* final ||b - A x|| / ||b|| (GMRES estimate)     */
+    double rel_resid[3];   /* final ||b - A x|| / ||b|| as GMRES reports it   */
     int converged;         /* 1 if every channel met gmres_tol               */
     int n_matvec;          /* operator applications, right-hand side included */
     double ms_rhs;         /* right-hand side (Alg. 3), device time   */
@@ -149,6 +159,11 @@ typedef struct {
                               check, host wall time (inside ms_solve)        */
     int n_refine;          /* FMM forms: outer (iterative refinement) steps,
                               each one FP64 residual and one inner GMRES     */
+    double true_rel_resid[3]; /* ||b - G_H sigma|| / ||b|| per channel with
+                              the form's FP64 operator applied to the
+                              returned sigma (FMM forms: the refinement's
+                              last outer residual; dense form: GMRES's last
+                              recomputed residual), never a Givens estimate */
 } dc_solve_stats;
 
 typedef struct {
@@ -192,6 +207,9 @@ void dc_destroy(dc_ctx *ctx);
  *   panel_start  host [panel_ptr[n_curves]]: arc-length fraction in [0,1)
  *                where each panel starts, strictly increasing per curve,
  *                first = 0 (panels end where the next starts, or at 1)
+ *                panel_ptr and panel_start both NULL: the library splits
+ *                the panels itself by the options' adapt_* rule (the panels
+ *                chosen are returned by dc_get_panels)
  *   colours      host [n_curves][2][2][3]: [side: 0 = u+ (right of travel),
  *                1 = u- (left)][end: colour at t = 0, t = 1][rgb]; colours
  *                are linear in the Bezier parameter t between the ends
@@ -361,6 +379,17 @@ const char *dc_status_string(dc_status st);
  * Errors: DC_ERR_ARG for bad sizes or non-finite input. */
 dc_status dc_aux_tree_check(int n_seg, const double *seg_xy, const double *domain,
                             int leaf_size, int max_depth, double *out);
+
+/* Auxiliary, host only (no GPU): the adaptive panel rule dc_build_tree
+ * applies when given no panels (see adapt_ratio in dc_options), with
+ * explicit parameters (ratio > 0, max_level in [0, 30], min_panels >= 1,
+ * max_len > 0).  ctrl host [n_curves][4][2]; outputs panel_ptr
+ * [n_curves + 1] and *n_panels always, panel_start [*n_panels] when it fits
+ * in capacity (else DC_ERR_ARG with *n_panels set, so a second call can size
+ * the array).  Errors: DC_ERR_ARG, DC_ERR_GEOMETRY for a zero-length curve. */
+dc_status dc_aux_adaptive_panels(int n_curves, const double *ctrl, double ratio, int max_level,
+                                 int min_panels, double max_len, int capacity, int *panel_ptr,
+                                 double *panel_start, int *n_panels);
 
 /* ---------------------------------------------------------------------
  * Learned warm start (no counterpart in the paper: its warm start, Sec. 6.1,

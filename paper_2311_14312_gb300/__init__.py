@@ -45,7 +45,9 @@ class dc_options(ctypes.Structure):
                 ("gmres_max_iter", ctypes.c_int), ("x0_mode", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("domain", ctypes.c_double * 4),
                 ("p_inner", ctypes.c_int), ("inner_tol", ctypes.c_double), ("m2l_engine", ctypes.c_int),
-                ("coarse_max", ctypes.c_int)]
+                ("coarse_max", ctypes.c_int), ("adapt_ratio", ctypes.c_double),
+                ("adapt_max_level", ctypes.c_int), ("adapt_min_panels", ctypes.c_int),
+                ("adapt_max_len", ctypes.c_double)]
 
 
 class dc_sizes(ctypes.Structure):
@@ -61,7 +63,8 @@ class dc_solve_stats(ctypes.Structure):
                 ("ms_rhs", ctypes.c_double), ("ms_solve", ctypes.c_double),
                 ("p2p_pairs", ctypes.c_longlong), ("m2l_pairs", ctypes.c_longlong),
                 ("used_warm", ctypes.c_int), ("warm_resid", ctypes.c_double * 3),
-                ("ms_warm", ctypes.c_double), ("n_refine", ctypes.c_int)]
+                ("ms_warm", ctypes.c_double), ("n_refine", ctypes.c_int),
+                ("true_rel_resid", ctypes.c_double * 3)]
 
 
 class dc_subdivide_options(ctypes.Structure):
@@ -98,7 +101,8 @@ EXPORTS = ["dc_default_options", "dc_create", "dc_destroy", "dc_build_tree", "dc
            "dc_aux_mlp_forward", "dc_aux_mlp_loss_grad", "dc_aux_mlp_adam", "dc_aux_feature_dims",
            "dc_aux_panel_features", "dc_aux_set_warm_start_model", "dc_aux_apply_operator", "dc_aux_precond_info",
            "dc_aux_build_timings", "dc_aux_test_skip_mma_tile", "dc_aux_fp32_peak",
-           "dc_aux_time_inner_m2l", "dc_subdivide", "dc_get_panels", "dc_aux_subdivision_info"]
+           "dc_aux_time_inner_m2l", "dc_subdivide", "dc_get_panels", "dc_aux_subdivision_info",
+           "dc_aux_adaptive_panels"]
 
 
 def _load():
@@ -149,6 +153,7 @@ def _load():
     lib.dc_subdivide.argtypes = [P, ctypes.POINTER(dc_subdivide_options), ctypes.POINTER(dc_subdivide_stats)]
     lib.dc_get_panels.argtypes = [P, P, P]
     lib.dc_aux_subdivision_info.argtypes = [P, P, P, P]
+    lib.dc_aux_adaptive_panels.argtypes = [I, P, D, I, I, D, I, P, P, P]
     for name in EXPORTS:
         if name not in ("dc_destroy", "dc_last_error", "dc_status_string", "dc_abi_version",
                         "dc_aux_kernel_launches", "dc_aux_mlp_param_count",
@@ -244,6 +249,14 @@ class Context:
         col = np.ascontiguousarray(colours, dtype=np.float64)
         self._check(_get_lib().dc_build_tree(self._h, int(ctrl.shape[0]), _ptr(ctrl), _ptr(ptr),
                                       _ptr(start), _ptr(col)))
+        return self
+
+    def build_curves(self, ctrl, colours):
+        """dc_build_tree with the library's adaptive panel rule (panel_ptr
+        and panel_start NULL)."""
+        ctrl = np.ascontiguousarray(ctrl, dtype=np.float64)
+        col = np.ascontiguousarray(colours, dtype=np.float64)
+        self._check(_get_lib().dc_build_tree(self._h, int(ctrl.shape[0]), _ptr(ctrl), None, None, _ptr(col)))
         return self
 
     def build_drawing(self, drawing):
@@ -420,6 +433,24 @@ def fp32_peak(stream=None) -> dict:
     if st != DC_OK:
         raise DcError(st, "dc_aux_fp32_peak failed")
     return {"tflops": float(out[0]), "ms": float(out[1])}
+
+
+def aux_adaptive_panels(ctrl, ratio=0.2, max_level=8, min_panels=2, max_len=0.5):
+    """Host-only adaptive panel rule (dc_aux_adaptive_panels):
+    (panel_ptr, panel_start)."""
+    ctrl = np.ascontiguousarray(ctrl, dtype=np.float64)
+    n = int(ctrl.shape[0])
+    ptr = np.zeros(n + 1, np.int32)
+    cnt = ctypes.c_int()
+    lib = _get_lib()
+    lib.dc_aux_adaptive_panels(n, _ptr(ctrl), float(ratio), int(max_level), int(min_panels), float(max_len), 0,
+                               _ptr(ptr), None, ctypes.byref(cnt))
+    start = np.zeros(max(cnt.value, 1))
+    st = lib.dc_aux_adaptive_panels(n, _ptr(ctrl), float(ratio), int(max_level), int(min_panels), float(max_len),
+                                    cnt.value, _ptr(ptr), _ptr(start), ctypes.byref(cnt))
+    if st != DC_OK:
+        raise DcError(st, "dc_aux_adaptive_panels failed")
+    return ptr, start[:cnt.value]
 
 
 def kernel_launches() -> int:

@@ -127,6 +127,11 @@ dc_status check_options(const dc_options &o, std::string &msg) {
         msg = "options: m2l_engine must be DC_M2L_TENSOR or DC_M2L_CUDA_CORES";
         return DC_ERR_ARG;
     }
+    if (!(o.adapt_ratio >= 0.0) || o.adapt_max_level < 0 || o.adapt_max_level > 30 || o.adapt_min_panels < 0 ||
+        o.adapt_min_panels > 1024 || !(o.adapt_max_len >= 0.0)) {
+        msg = "options: adapt_ratio, adapt_max_len >= 0, adapt_max_level in [0, 30], adapt_min_panels in [0, 1024]";
+        return DC_ERR_ARG;
+    }
     if (o.coarse_max != 0 && (o.coarse_max < 64 || o.coarse_max > 16384 || o.coarse_max % 32 != 0)) {
         msg = "options: coarse_max must be 0 (default) or a multiple of 32 in [64, 16384]";
         return DC_ERR_ARG;
@@ -333,6 +338,21 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
         ctx->build_ms[i] = std::chrono::duration<double, std::milli>(t - t_prev).count();
         t_prev = t;
     };
+    std::vector<int> auto_ptr;
+    std::vector<double> auto_start;
+    if (!panel_ptr && !panel_start) {   // the adaptive panel rule of the options
+        if (n_curves < 1 || !ctrl) return fail(ctx, DC_ERR_ARG, "build_tree: need curves");
+        for (int i = 0; i < 8 * n_curves; ++i)
+            if (!std::isfinite(ctrl[i])) return fail(ctx, DC_ERR_ARG, "build_tree: non-finite control point");
+        const dc_options &o = ctx->opt;
+        dc_status sa = dc::adaptive_panels(n_curves, ctrl, o.adapt_ratio > 0 ? o.adapt_ratio : 0.2,
+                                           o.adapt_max_level > 0 ? o.adapt_max_level : 8,
+                                           o.adapt_min_panels > 0 ? o.adapt_min_panels : 2,
+                                           o.adapt_max_len > 0 ? o.adapt_max_len : 0.5, auto_ptr, auto_start, msg);
+        if (sa != DC_OK) return fail(ctx, sa, msg);
+        panel_ptr = auto_ptr.data();
+        panel_start = auto_start.data();
+    }
     dc_status st = dc::discretise(n_curves, ctrl, panel_ptr, panel_start, colours, ctx->opt.g,
                                   ctx->opt.s_per_panel, ctx->geo, msg);
     if (st != DC_OK) return fail(ctx, st, msg);
@@ -555,6 +575,7 @@ dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats)
         for (int c = 0; c < 3; ++c) {
             stats->iters[c] = gr.iters[c];
             stats->rel_resid[c] = gr.rel_resid[c];
+            stats->true_rel_resid[c] = gr.true_rel_resid[c];
         }
         stats->converged = gr.converged;
         stats->n_matvec = gr.n_matvec + 1;
@@ -1180,6 +1201,25 @@ dc_status dc_subdivide(dc_ctx *ctx, const dc_subdivide_options *o, dc_subdivide_
     ctx->state = 2;
     ctx->seg_density_valid = false;
     if (stats) *stats = S;
+    return DC_OK;
+}
+
+dc_status dc_aux_adaptive_panels(int n_curves, const double *ctrl, double ratio, int max_level, int min_panels,
+                                 double max_len, int capacity, int *panel_ptr, double *panel_start, int *n_panels) {
+    if (n_curves < 1 || !ctrl || !panel_ptr || !n_panels || capacity < 0 || (capacity > 0 && !panel_start) ||
+        !(ratio > 0.0) || max_level < 0 || max_level > 30 || min_panels < 1 || !(max_len > 0.0))
+        return DC_ERR_ARG;
+    for (int i = 0; i < 8 * n_curves; ++i)
+        if (!std::isfinite(ctrl[i])) return DC_ERR_ARG;
+    std::vector<int> ptr;
+    std::vector<double> start;
+    std::string msg;
+    dc_status st = dc::adaptive_panels(n_curves, ctrl, ratio, max_level, min_panels, max_len, ptr, start, msg);
+    if (st != DC_OK) return st;
+    *n_panels = int(start.size());
+    std::memcpy(panel_ptr, ptr.data(), sizeof(int) * ptr.size());
+    if ((int)start.size() > capacity) return DC_ERR_ARG;
+    std::memcpy(panel_start, start.data(), sizeof(double) * start.size());
     return DC_OK;
 }
 

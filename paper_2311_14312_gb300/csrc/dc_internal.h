@@ -40,6 +40,10 @@ dc_status discretise(int n_curves, const double *ctrl, const int *panel_ptr,
                      const double *panel_start, const double *colours, int g,
                      int s, Geometry &out, std::string &err);
 
+// Adaptive panel split (panels.cpp): ptr [n_curves + 1], start [panels].
+dc_status adaptive_panels(int n_curves, const double *ctrl, double ratio, int max_level, int min_panels,
+                          double max_len, std::vector<int> &ptr, std::vector<double> &start, std::string &err);
+
 // Gauss-Legendre nodes on [-1, 1] (ascending) and weights.
 void gauss_legendre_rule(int n, double *x, double *w);
 
@@ -228,6 +232,7 @@ struct Operator {
 
 struct GmresResult {
     int iters[3] = {0, 0, 0};
+    double true_rel_resid[3] = {0, 0, 0};   // recomputed b - A x, never an estimate
     double rel_resid[3] = {0, 0, 0};
     int converged = 0;
     int n_matvec = 0;

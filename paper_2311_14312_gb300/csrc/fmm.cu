@@ -1281,6 +1281,7 @@ cudaError_t Fmm::solve(GmresWork *w, const double *b, double *x, const dc_option
         double need = 1.0;
         for (int c = 0; c < 3; ++c) {
             res.rel_resid[c] = bn[c] > 0 ? rn[c] / bn[c] : 0.0;
+            res.true_rel_resid[c] = res.rel_resid[c];
             mask[c] = rn[c] > opt.gmres_tol * bn[c];
             any |= mask[c];
             if (mask[c]) need = std::min(need, opt.gmres_tol * bn[c] / rn[c]);

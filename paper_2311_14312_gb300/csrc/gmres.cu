@@ -631,6 +631,7 @@ cudaError_t gmres_solve(GmresWork *Wp, Operator &A, int N, const double *b, doub
         bool any = false;
         for (int c = 0; c < 3; ++c) {
             res.rel_resid[c] = hb[c] > 0 ? hbeta[c] / hb[c] : 0.0;
+            res.true_rel_resid[c] = res.rel_resid[c];
             if (hbeta[c] > hthr[c]) any = true;
         }
         if (!any) {
