@@ -127,6 +127,10 @@ typedef struct {
                               (0 = 2) ...                                    */
     double adapt_max_len;  /* ... and no panel longer than this (0 = 0.5);
                               measured on 256-point polylines per curve      */
+    int eval_tile;         /* DC_FORM_FMM32: pixel tile of one block of the
+                              render's evaluation kernel: 0 = 8 x 8 (default),
+                              1 = 16 x 8, 2 = 16 x 16, 3 = 32 x 8 (width x
+                              height)                                         */
 } dc_options;
 
 enum {
@@ -270,6 +274,36 @@ dc_status dc_eval_points(dc_ctx *ctx, int n, const void *xy, int xy_where,
  * not the context's, DC_ERR_ARG for bad sizes, DC_ERR_CUDA when the symbol
  * lookup or a launch fails. */
 dc_status dc_eval_points_noalloc(dc_ctx *ctx, int n, const double *xy_dev, double *out_dev);
+
+/* ---------------------------------------------------------------------
+ * Autotuning of the chosen form (no counterpart in the paper, which gives
+ * neither the leaf size b nor K): candidates are the cross product of leaf
+ * sizes x inner orders p_inner x pixel tile shapes (eval_tile); each is
+ * built on the context's drawing, warmed up, and timed (solve + render of
+ * the viewports, CUDA events on the context's stream, best of `repeats`);
+ * its FP32 pixels are compared with a plain FP64 FMM render of the same
+ * drawing at the context's order p.
+ * --------------------------------------------------------------------- */
+typedef struct {
+    int leaf_size, p_inner, eval_tile;
+    double ms;             /* solve + render device time, -1 if it failed    */
+    double max_err;        /* max colour difference to the FP64 reference    */
+    int converged;
+} dc_autotune_row;
+
+/* Runs the search on the drawing last given to dc_build_tree (DC_FORM_FMM32
+ * only).  An empty list (n = 0, pointer may be NULL) keeps the context's
+ * current value for that option.  rows [max(n_leaf,1) x max(n_pinner,1) x
+ * max(n_tile,1)], leaf-major then p_inner then tile; *best = the index of
+ * the fastest row that converged with max_err <= tol (-1 if none).  The
+ * context is left built with the chosen options (its own if none) and has
+ * no density: solve again.  A learned or user start is replaced by x0 = 1
+ * during the search.  Errors: DC_ERR_STATE before dc_build_tree,
+ * DC_ERR_UNSUPPORTED in other forms, DC_ERR_ARG, errors of the reference
+ * solve. */
+dc_status dc_autotune(dc_ctx *ctx, int n_vp, const dc_viewport *vps, int n_leaf, const int *leaf_sizes,
+                      int n_pinner, const int *p_inners, int n_tile, const int *eval_tiles, double tol,
+                      int repeats, dc_autotune_row *rows, int *best);
 
 /* Copies the current density sigma at the nodes to host [n_nodes][3]. */
 dc_status dc_get_density(dc_ctx *ctx, double *sigma_out);

@@ -47,7 +47,7 @@ class dc_options(ctypes.Structure):
                 ("p_inner", ctypes.c_int), ("inner_tol", ctypes.c_double), ("m2l_engine", ctypes.c_int),
                 ("coarse_max", ctypes.c_int), ("adapt_ratio", ctypes.c_double),
                 ("adapt_max_level", ctypes.c_int), ("adapt_min_panels", ctypes.c_int),
-                ("adapt_max_len", ctypes.c_double)]
+                ("adapt_max_len", ctypes.c_double), ("eval_tile", ctypes.c_int)]
 
 
 class dc_sizes(ctypes.Structure):
@@ -81,6 +81,11 @@ class dc_subdivide_stats(ctypes.Structure):
                 ("ms_label", ctypes.c_double), ("ms_solve", ctypes.c_double)]
 
 
+class dc_autotune_row(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int), ("p_inner", ctypes.c_int), ("eval_tile", ctypes.c_int),
+                ("ms", ctypes.c_double), ("max_err", ctypes.c_double), ("converged", ctypes.c_int)]
+
+
 class dc_viewport(ctypes.Structure):
     _fields_ = [("x0", ctypes.c_double), ("y0", ctypes.c_double), ("x1", ctypes.c_double),
                 ("y1", ctypes.c_double), ("width", ctypes.c_int), ("height", ctypes.c_int)]
@@ -102,7 +107,7 @@ EXPORTS = ["dc_default_options", "dc_create", "dc_destroy", "dc_build_tree", "dc
            "dc_aux_panel_features", "dc_aux_set_warm_start_model", "dc_aux_apply_operator", "dc_aux_precond_info",
            "dc_aux_build_timings", "dc_aux_test_skip_mma_tile", "dc_aux_fp32_peak",
            "dc_aux_time_inner_m2l", "dc_subdivide", "dc_get_panels", "dc_aux_subdivision_info",
-           "dc_aux_adaptive_panels"]
+           "dc_aux_adaptive_panels", "dc_autotune"]
 
 
 def _load():
@@ -154,6 +159,8 @@ def _load():
     lib.dc_get_panels.argtypes = [P, P, P]
     lib.dc_aux_subdivision_info.argtypes = [P, P, P, P]
     lib.dc_aux_adaptive_panels.argtypes = [I, P, D, I, I, D, I, P, P, P]
+    lib.dc_autotune.argtypes = [P, I, ctypes.POINTER(dc_viewport), I, P, I, P, I, P, D, I,
+                                ctypes.POINTER(dc_autotune_row), P]
     for name in EXPORTS:
         if name not in ("dc_destroy", "dc_last_error", "dc_status_string", "dc_abi_version",
                         "dc_aux_kernel_launches", "dc_aux_mlp_param_count",
@@ -355,6 +362,25 @@ class Context:
         res = np.zeros(self.sizes().n_panels, np.uint8)
         self._check(_get_lib().dc_aux_subdivision_info(self._h, _ptr(top), _ptr(split), _ptr(res)))
         return top, split.astype(bool), res.astype(bool)
+
+    def autotune(self, viewports, leaf_sizes=(), p_inners=(), eval_tiles=(), tol=1e-5, repeats=2):
+        """dc_autotune: (best row index or -1, list of row dicts).  The
+        context is left built with the chosen options and no density."""
+        n = len(viewports)
+        arr = (dc_viewport * n)()
+        for i, v in enumerate(viewports):
+            arr[i] = dc_viewport(float(v[0]), float(v[1]), float(v[2]), float(v[3]), int(v[4]), int(v[5]))
+        L = np.ascontiguousarray(leaf_sizes, dtype=np.int32)
+        Pi = np.ascontiguousarray(p_inners, dtype=np.int32)
+        T = np.ascontiguousarray(eval_tiles, dtype=np.int32)
+        nrows = max(len(L), 1) * max(len(Pi), 1) * max(len(T), 1)
+        rows = (dc_autotune_row * nrows)()
+        best = ctypes.c_int(-1)
+        self._check(_get_lib().dc_autotune(self._h, n, arr, len(L), _ptr(L) if len(L) else None, len(Pi),
+                                           _ptr(Pi) if len(Pi) else None, len(T), _ptr(T) if len(T) else None,
+                                           float(tol), int(repeats), rows, ctypes.byref(best)))
+        keys = ["leaf_size", "p_inner", "eval_tile", "ms", "max_err", "converged"]
+        return best.value, [{k: getattr(r, k) for k in keys} for r in rows]
 
     def time_inner_m2l(self, reps: int = 20) -> dict:
         """dc_aux_time_inner_m2l as a dict."""

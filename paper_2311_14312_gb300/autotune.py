@@ -1,69 +1,83 @@
-"""Search over the tunable options of the chosen FP32 form for one drawing and
-set of viewports: leaf size b (pieces per quadtree leaf) and the inner
-operator's order p_inner, timing solve + render on the device and keeping
-only candidates whose pixels stay within a colour tolerance of a plain FP64
-FMM reference (order 30).  Host-side search through the public ABI; every
-candidate runs the library's kernels.
+"""Option search of the chosen FP32 form for one drawing and set of viewports
+(leaf size b, inner order p_inner, pixel tile shape eval_tile), run by the
+library (dc_autotune: each candidate built, timed with CUDA events over
+solve + render, and checked against a plain FP64 FMM render), with the
+result kept in a JSON cache keyed by the drawing, the viewports, the
+candidate lists, the tolerance and the GPU's name, so a later call for the
+same inputs on the same kind of GPU returns at once.
 
     from paper_2311_14312_gb300 import autotune
-    best, table = autotune.autotune(drawing, [(0, 0, 1, 1, 1024, 1024)])
+    best, table, cached = autotune.autotune(drawing, [(0, 0, 1, 1, 1024, 1024)])
+
+The cache file is $DC_AUTOTUNE_CACHE, else ~/.cache/paper_2311_14312_gb300/
+autotune.json; cache=False skips it.
 """
 from __future__ import annotations
 
-import itertools
+import hashlib
+import json
+import os
+
+import numpy as np
 
 
-def _time_step(ctx, vps, rgb, repeats):
-    import torch
-    s = torch.cuda.current_stream()
-    ctx.solve_density()                       # warm-up: graphs, buffers
-    ctx.render_viewport(vps, rgb)
-    torch.cuda.synchronize()
-    best = float("inf")
-    for _ in range(repeats):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        ctx.solve_density()
-        ctx.render_viewport(vps, rgb)
-        e1.record(s)
-        e1.synchronize()
-        best = min(best, e0.elapsed_time(e1))
-    return best
+def cache_path() -> str:
+    p = os.environ.get("DC_AUTOTUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "paper_2311_14312_gb300", "autotune.json")
+
+
+def cache_key(drawing, viewports, leaf_sizes, p_inners, eval_tiles, p, tol, gmres_tol, gpu: str) -> str:
+    h = hashlib.sha1()
+    for a in (drawing.ctrl, drawing.colours, drawing.panel_ptr, drawing.panel_start):
+        h.update(np.ascontiguousarray(a).tobytes())
+    h.update(json.dumps([int(drawing.g), int(drawing.s_per_panel), [list(map(float, v[:4])) + [int(v[4]), int(v[5])]
+                                                                     for v in viewports],
+                         list(map(int, leaf_sizes)), list(map(int, p_inners)), list(map(int, eval_tiles)),
+                         int(p), float(tol), float(gmres_tol), gpu]).encode())
+    return h.hexdigest()
+
+
+def _load(path: str) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def autotune(drawing, viewports, leaf_sizes=(32, 48, 64, 96, 128), p_inners=(10, 12, 14),
-             p=24, tol=1e-5, repeats=2, gmres_tol=1e-10):
-    """(best options dict, list of (options, ms or None, max colour error)).
-    A candidate whose pixels differ from the reference by more than tol, or
-    whose solve does not converge, is recorded with ms None."""
+             eval_tiles=(0, 1, 2, 3), p=24, tol=1e-5, repeats=2, gmres_tol=1e-10, cache=True):
+    """(best options dict or None, table of row dicts, True if from the cache).
+    Rows that fail, do not converge or miss tol are kept with their values;
+    the best is the fastest of the others."""
     import torch
 
-    from . import Context, DcError
-    n = sum(v[4] * v[5] for v in viewports)
-    ref = torch.empty((n, 3), dtype=torch.float64, device="cuda")
-    rc = Context(form="fmm64", g=drawing.g, s_per_panel=drawing.s_per_panel, p=30, leaf_size=32,
-                 gmres_tol=1e-12, gmres_restart=400, gmres_max_iter=4000)
-    rc.build_drawing(drawing)
-    rc.solve_density()
-    rc.render_viewport(viewports, ref)
-    rc.close()
-    table = []
-    rgb = torch.empty((n, 3), dtype=torch.float64, device="cuda")
-    for leaf, pi in itertools.product(leaf_sizes, p_inners):
-        opts = dict(p=p, leaf_size=leaf, p_inner=min(pi, p), gmres_tol=gmres_tol, gmres_restart=200,
-                    gmres_max_iter=3000)
-        try:
-            ctx = Context(form="fmm32", g=drawing.g, s_per_panel=drawing.s_per_panel, **opts)
-            ctx.build_drawing(drawing)
-            ms = _time_step(ctx, viewports, rgb, repeats)
-            torch.cuda.synchronize()
-            err = float((rgb - ref).abs().max().item())
-            ctx.close()
-        except DcError:
-            table.append((opts, None, float("inf")))
-            continue
-        table.append((opts, ms if err <= tol else None, err))
-    ok = [t for t in table if t[1] is not None]
-    best = min(ok, key=lambda t: t[1])[0] if ok else None
-    return best, table
+    from . import Context
+    gpu = torch.cuda.get_device_name() if torch.cuda.is_available() else "none"
+    key = cache_key(drawing, viewports, leaf_sizes, p_inners, eval_tiles, p, tol, gmres_tol, gpu)
+    path = cache_path()
+    if cache:
+        hit = _load(path).get(key)
+        if hit is not None:
+            return hit["best"], hit["table"], True
+    ctx = Context(form="fmm32", g=drawing.g, s_per_panel=drawing.s_per_panel, p=p, gmres_tol=gmres_tol,
+                  gmres_restart=200, gmres_max_iter=3000)
+    ctx.build_drawing(drawing)
+    idx, table = ctx.autotune(viewports, leaf_sizes, p_inners, eval_tiles, tol=tol, repeats=repeats)
+    ctx.close()
+    best = None
+    if idx >= 0:
+        r = table[idx]
+        best = dict(p=p, leaf_size=r["leaf_size"], p_inner=r["p_inner"], eval_tile=r["eval_tile"],
+                    gmres_tol=gmres_tol)
+    if cache:
+        os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+        data = _load(path)
+        data[key] = {"best": best, "table": table, "gpu": gpu}
+        tmp = f"{path}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(data, f)
+        os.replace(tmp, path)
+    return best, table, False

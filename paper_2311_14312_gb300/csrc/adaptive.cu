@@ -75,6 +75,17 @@ __global__ void panel_range_kernel(const double *__restrict__ v, int n_panels, i
     out[t] = hi - lo;
 }
 
+// out = max |a - b| over n values (a FP32, b FP64), as the bits of a
+// non-negative float (their integer order is the float order)
+__global__ void max_diff_kernel(const float *__restrict__ a, const double *__restrict__ b, long long n,
+                                unsigned *__restrict__ out) {
+    float m = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, (float)fabs((double)a[i] - b[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
 __global__ void node_mask_kernel(double *__restrict__ v, const unsigned char *__restrict__ pmask, int N, int g) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * N) return;
@@ -109,6 +120,14 @@ cudaError_t launch_unit_density(double *x, int N, int g, const int panels[3], cu
 
 cudaError_t launch_panel_range(const double *v, int n_panels, int g, double *out, cudaStream_t st) {
     panel_range_kernel<<<blocks(3LL * n_panels), kThreads, 0, st>>>(v, n_panels, g, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max_diff(const float *a, const double *b, long long n, unsigned *out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    max_diff_kernel<<<4 * 152, kThreads, 0, st>>>(a, b, n, out);
     note_launch();
     return cudaGetLastError();
 }

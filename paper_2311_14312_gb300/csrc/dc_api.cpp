@@ -132,6 +132,10 @@ dc_status check_options(const dc_options &o, std::string &msg) {
         msg = "options: adapt_ratio, adapt_max_len >= 0, adapt_max_level in [0, 30], adapt_min_panels in [0, 1024]";
         return DC_ERR_ARG;
     }
+    if (o.eval_tile < 0 || o.eval_tile > 3) {
+        msg = "options: eval_tile must be in [0, 3]";
+        return DC_ERR_ARG;
+    }
     if (o.coarse_max != 0 && (o.coarse_max < 64 || o.coarse_max > 16384 || o.coarse_max % 32 != 0)) {
         msg = "options: coarse_max must be 0 (default) or a multiple of 32 in [64, 16384]";
         return DC_ERR_ARG;
@@ -1220,6 +1224,125 @@ dc_status dc_aux_adaptive_panels(int n_curves, const double *ctrl, double ratio,
     std::memcpy(panel_ptr, ptr.data(), sizeof(int) * ptr.size());
     if ((int)start.size() > capacity) return DC_ERR_ARG;
     std::memcpy(panel_start, start.data(), sizeof(double) * start.size());
+    return DC_OK;
+}
+
+// ------------------------------------------------------------- autotune --
+dc_status dc_autotune(dc_ctx *ctx, int n_vp, const dc_viewport *vps, int n_leaf, const int *leaf_sizes,
+                      int n_pinner, const int *p_inners, int n_tile, const int *eval_tiles, double tol,
+                      int repeats, dc_autotune_row *rows, int *best) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "autotune: call build_tree first");
+    if (ctx->opt.form != DC_FORM_FMM32) return fail(ctx, DC_ERR_UNSUPPORTED, "autotune: needs DC_FORM_FMM32");
+    if (n_vp < 1 || !vps || n_leaf < 0 || n_pinner < 0 || n_tile < 0 || (n_leaf > 0 && !leaf_sizes) ||
+        (n_pinner > 0 && !p_inners) || (n_tile > 0 && !eval_tiles) || !(tol > 0.0) || repeats < 1 || !rows || !best)
+        return fail(ctx, DC_ERR_ARG, "autotune: bad arguments");
+    long long npx = 0;
+    for (int v = 0; v < n_vp; ++v) npx += (long long)vps[v].width * vps[v].height;
+    if (npx <= 0) return fail(ctx, DC_ERR_ARG, "autotune: no pixels");
+    const dc_options orig = ctx->opt;
+    const int nc = ctx->in_ncurves;
+    const std::vector<double> ctrl = ctx->in_ctrl, start = ctx->in_start, col = ctx->in_col;
+    const std::vector<int> pptr = ctx->in_ptr;
+    auto rebuild = [&](const dc_options &o) -> dc_status {
+        ctx->opt = o;
+        return dc_build_tree(ctx, nc, ctrl.data(), pptr.data(), start.data(), col.data());
+    };
+    cudaStream_t s = ctx->stream;
+    // reference pixels: the plain FP64 FMM form of the same drawing and order
+    DevBuf<double> ref;
+    DevBuf<float> out;
+    DevBuf<unsigned> dmax;
+    DC_CK(ctx, ref.alloc(3 * (size_t)npx), "autotune: alloc");
+    DC_CK(ctx, out.alloc(3 * (size_t)npx), "autotune: alloc");
+    DC_CK(ctx, dmax.alloc(1), "autotune: alloc");
+    {
+        dc_options ro = orig;
+        ro.form = DC_FORM_FMM64;
+        if (ro.x0_mode == DC_X0_USER || ro.x0_mode == DC_X0_LEARNED) ro.x0_mode = DC_X0_ONES;
+        dc_ctx *rc = nullptr;
+        dc_status st = dc_create(&rc, &ro);
+        if (st != DC_OK) return fail(ctx, st, std::string("autotune: reference context: ") + dc_last_error(nullptr));
+        st = dc_build_tree(rc, nc, ctrl.data(), pptr.data(), start.data(), col.data());
+        if (st == DC_OK) st = dc_solve_density(rc, nullptr, nullptr);
+        if (st == DC_OK) st = dc_render_viewport(rc, n_vp, vps, ref.ptr, DC_F64, nullptr, DC_MEM_DEVICE, nullptr);
+        if (st == DC_OK && cudaStreamSynchronize(rc->stream) != cudaSuccess) st = DC_ERR_CUDA;
+        const std::string msg = st == DC_OK ? "" : rc->err;
+        dc_destroy(rc);
+        if (st != DC_OK) return fail(ctx, st, "autotune: reference: " + msg);
+    }
+    const int nl = std::max(n_leaf, 1), np = std::max(n_pinner, 1), nt = std::max(n_tile, 1);
+    cudaEvent_t e0, e1;
+    DC_CK(ctx, cudaEventCreate(&e0), "event");
+    DC_CK(ctx, cudaEventCreate(&e1), "event");
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } guard{e0, e1};
+    int k = 0, chosen = -1;
+    for (int il = 0; il < nl; ++il)
+        for (int ip = 0; ip < np; ++ip) {
+            dc_options o = orig;
+            if (o.x0_mode == DC_X0_USER) o.x0_mode = DC_X0_ONES;
+            if (n_leaf > 0) o.leaf_size = leaf_sizes[il];
+            if (n_pinner > 0) o.p_inner = std::min(p_inners[ip], o.p);
+            std::string why;
+            dc_status bst = check_options(o, why);
+            if (bst == DC_OK) bst = rebuild(o);
+            for (int it = 0; it < nt; ++it, ++k) {
+                dc_autotune_row &r = rows[k];
+                r.leaf_size = o.leaf_size;
+                r.p_inner = o.p_inner;
+                r.eval_tile = n_tile > 0 ? eval_tiles[it] : o.eval_tile;
+                r.ms = -1.0;
+                r.max_err = INFINITY;
+                r.converged = 0;
+                if (bst != DC_OK || r.eval_tile < 0 || r.eval_tile > 3) continue;
+                ctx->opt.eval_tile = r.eval_tile;
+                ctx->fmm->set_eval_tile(r.eval_tile);
+                dc_solve_stats ss;
+                dc_status st = dc_solve_density(ctx, nullptr, &ss);   // warm-up: graphs, buffers, tile plan
+                if (st == DC_OK)
+                    st = dc_render_viewport(ctx, n_vp, vps, out.ptr, DC_F32, nullptr, DC_MEM_DEVICE, nullptr);
+                if (st != DC_OK) continue;
+                float bestms = INFINITY;
+                for (int rep = 0; rep < repeats && st == DC_OK; ++rep) {
+                    DC_CK(ctx, cudaEventRecord(e0, s), "event");
+                    st = dc_solve_density(ctx, nullptr, &ss);
+                    if (st == DC_OK)
+                        st = dc_render_viewport(ctx, n_vp, vps, out.ptr, DC_F32, nullptr, DC_MEM_DEVICE, nullptr);
+                    DC_CK(ctx, cudaEventRecord(e1, s), "event");
+                    DC_CK(ctx, cudaEventSynchronize(e1), "event");
+                    float ms = 0.f;
+                    DC_CK(ctx, cudaEventElapsedTime(&ms, e0, e1), "event");
+                    bestms = std::min(bestms, ms);
+                }
+                if (st != DC_OK) continue;
+                DC_CK(ctx, dc::launch_max_diff(out.ptr, ref.ptr, 3 * npx, dmax.ptr, s), "autotune: compare");
+                unsigned bits = 0;
+                DC_CK(ctx, cudaMemcpyAsync(&bits, dmax.ptr, sizeof(bits), cudaMemcpyDeviceToHost, s), "autotune");
+                DC_CK(ctx, cudaStreamSynchronize(s), "autotune");
+                float err;
+                std::memcpy(&err, &bits, sizeof(err));
+                r.ms = bestms;
+                r.max_err = err;
+                r.converged = ss.converged;
+                if (r.converged && err <= tol && (chosen < 0 || r.ms < rows[chosen].ms)) chosen = k;
+            }
+        }
+    *best = chosen;
+    dc_options fin = orig;
+    if (chosen >= 0) {
+        fin.leaf_size = rows[chosen].leaf_size;
+        fin.p_inner = rows[chosen].p_inner;
+        fin.eval_tile = rows[chosen].eval_tile;
+    }
+    dc_status st = rebuild(fin);
+    if (st != DC_OK) return st;
     return DC_OK;
 }
 

@@ -1336,6 +1336,8 @@ cudaError_t Fmm::time_inner_m2l(int reps, cudaStream_t st, double out[6]) {
     return impl_->time_inner_m2l(reps, st, out);
 }
 
+void Fmm::set_eval_tile(int t) { impl_->opt.eval_tile = t; }
+
 cudaError_t Fmm::set_mma_skip_tile(int tile, cudaStream_t st) {
     Impl &I = *impl_;
     if (!I.tc_err.ptr) return cudaErrorNotSupported;
@@ -1415,7 +1417,7 @@ dc_status Fmm::render_viewports(const VpDev *vpl, int n_vp, const double *sbar, 
     cudaError_t e;
     // the tile plan of the last call is kept on the device: the same
     // viewports (bit for bit) reuse it without rebuilding or uploading
-    const bool same = I.plan_valid && int(I.plan_vps.size()) == n_vp &&
+    const bool same = I.plan_valid && I.plan_tile == I.opt.eval_tile && int(I.plan_vps.size()) == n_vp &&
                       (n_vp == 0 || std::memcmp(I.plan_vps.data(), vpl, sizeof(VpDev) * n_vp) == 0);
     if (same) {
         I.render_pairs += I.plan_pairs;
@@ -1430,7 +1432,8 @@ dc_status Fmm::render_viewports(const VpDev *vpl, int n_vp, const double *sbar, 
         return DC_ERR_CUDA;
     }
     std::vector<Tile> tiles;
-    const int TS = kEvalTile;
+    int TW = kEvalTile, TH = kEvalTile;
+    if (I.fp32) tile_shape(I.opt.eval_tile, TW, TH);
     long long pairs = 0;
     const long long m2p0 = I.render_m2p;
     const double flops0 = I.render_flops;
@@ -1452,9 +1455,9 @@ dc_status Fmm::render_viewports(const VpDev *vpl, int n_vp, const double *sbar, 
             long long wn = T.w_ptr[c + 1] - T.w_ptr[c];
             I.render_m2p += wn * npx;
             I.render_flops += 45.0 * double(up * npx) + 24.0 * I.P1 * double((1 + wn) * npx);
-            for (int r = r0; r < r1; r += TS)
-                for (int cc = c0; cc < c1; cc += TS)
-                    tiles.push_back({c, r, cc, std::min(TS, r1 - r), std::min(TS, c1 - cc), v});
+            for (int r = r0; r < r1; r += TH)
+                for (int cc = c0; cc < c1; cc += TW)
+                    tiles.push_back({c, r, cc, std::min(TH, r1 - r), std::min(TW, c1 - cc), v});
         }
     }
     I.render_pairs += pairs;
@@ -1465,6 +1468,7 @@ dc_status Fmm::render_viewports(const VpDev *vpl, int n_vp, const double *sbar, 
         return DC_ERR_CUDA;
     }
     I.plan_vps = vv;
+    I.plan_tile = I.opt.eval_tile;
     I.plan_tiles = int(tiles.size());
     I.plan_pairs = pairs;
     I.plan_m2p = I.render_m2p - m2p0;

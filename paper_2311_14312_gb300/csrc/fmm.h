@@ -31,6 +31,7 @@ public:
     // Test hook of the tensor-core M2L: the CTA that takes `tile` issues no
     // MMA for it, so its bounded wait runs out (-1 = off).
     cudaError_t set_mma_skip_tile(int tile, cudaStream_t st);
+    void set_eval_tile(int t);   // pixel tile shape of the FP32 render (options.eval_tile)
     // y = B x with B the panels' inverse self-interaction blocks of G_H (the
     // first level of the two-level preconditioner alone).
     cudaError_t apply_block_jacobi(const double *x, double *y, cudaStream_t st);

@@ -193,9 +193,11 @@ __global__ void heavy_kernel(const double *__restrict__ sb, const double *__rest
 }
 
 // -------------------------------------------------------------- eval --
-constexpr int kEvThreads = kEvalTile * kEvalTile;
-// resident blocks per SM the register budget is set for, and pieces staged
-// in shared memory per round
+// The pixel tile of one block is TW x TH pixels (options.eval_tile picks
+// the shape); every shape is compiled for the same resident threads per SM
+// (kEvThreadsPerSM), so the register budget does not depend on the shape.
+// resident blocks per SM of 64-thread tiles the register budget is set for,
+// and pieces staged in shared memory per round
 #ifndef DC_EVAL_MINBLOCKS
 #define DC_EVAL_MINBLOCKS 12
 #endif
@@ -203,6 +205,7 @@ constexpr int kEvThreads = kEvalTile * kEvalTile;
 #define DC_EVAL_STAGE 128
 #endif
 constexpr int kEvBlocksPerSM = DC_EVAL_MINBLOCKS;
+constexpr int kEvThreadsPerSM = 64 * kEvBlocksPerSM;
 
 constexpr int kStage = DC_EVAL_STAGE;
 
@@ -242,8 +245,8 @@ __device__ __forceinline__ void split2(double v, float &hi, float &lo) {
     lo = (float)(v - (double)hi);
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kEvThreads, kEvBlocksPerSM) eval32_kernel(EvalArgs32 a) {
+template <int MODE, int TW, int TH>
+__global__ void __launch_bounds__(TW * TH, kEvThreadsPerSM / (TW * TH)) eval32_kernel(EvalArgs32 a) {
     // staged pieces of one list-1 leaf, in the target leaf's frame, each
     // coordinate as a (hi, lo) float pair so differences keep full accuracy
     __shared__ float sx1h[kStage], sx1l[kStage], sy1h[kStage], sy1l[kStage];
@@ -973,7 +976,13 @@ cudaError_t Fmm::Impl::render_tiles32(int n_tiles, void *rgb, int rgb_dtype,
     a.rgb = rgb;
     a.rgb_dtype = rgb_dtype;
     a.rgb8 = rgb8;
-    eval32_kernel<0><<<n_tiles, kEvThreads, 0, st>>>(a); note_launch();
+    switch (opt.eval_tile) {   // tile shapes of tile_shape()
+    case 1: eval32_kernel<0, 16, 8><<<n_tiles, 128, 0, st>>>(a); break;
+    case 2: eval32_kernel<0, 16, 16><<<n_tiles, 256, 0, st>>>(a); break;
+    case 3: eval32_kernel<0, 32, 8><<<n_tiles, 256, 0, st>>>(a); break;
+    default: eval32_kernel<0, 8, 8><<<n_tiles, 64, 0, st>>>(a); break;
+    }
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1002,7 +1011,7 @@ cudaError_t Fmm::Impl::eval_points32(int n_items, double *out, const double *sb6
     a.q64 = pt_xy.ptr;
     a.perm = pt_perm.ptr;
     a.out = out;
-    eval32_kernel<1><<<n_items, 64, 0, st>>>(a); note_launch();
+    eval32_kernel<1, 8, 8><<<n_items, 64, 0, st>>>(a); note_launch();
     return cudaGetLastError();
 }
 

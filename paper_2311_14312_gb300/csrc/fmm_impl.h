@@ -57,6 +57,13 @@ struct Tile {
 #define DC_EVAL_TILE 8
 #endif
 constexpr int kEvalTile = DC_EVAL_TILE;
+// pixel tile width x height of the FP32 evaluation kernel for options.eval_tile
+inline void tile_shape(int eval_tile, int &w, int &h) {
+    static const int W[4] = {8, 16, 16, 32}, H[4] = {8, 8, 16, 8};
+    const int k = (eval_tile >= 0 && eval_tile < 4) ? eval_tile : 0;
+    w = W[k];
+    h = H[k];
+}
 
 // Cells that need incoming expansions for one set of targets (all cells for
 // pixels; the cells above the nodes for the matvec), by pass.
@@ -196,7 +203,7 @@ struct Fmm::Impl {
     // the render's tile plan (tiles, vps) for the viewports plan_vps
     bool plan_valid = false;
     std::vector<VpDev> plan_vps;
-    int plan_tiles = 0;
+    int plan_tiles = 0, plan_tile = 0;
     long long plan_pairs = 0, plan_m2p = 0;
     double plan_flops = 0.0;
     cudaError_t graph_matvec32(const double *x, double *y, cudaStream_t st);

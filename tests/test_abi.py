@@ -50,10 +50,10 @@ int main(void){
         offsetof(dc_solve_stats, p2p_pairs), offsetof(dc_render_stats, eval_flops),
         offsetof(dc_solve_stats, warm_resid), offsetof(dc_solve_stats, ms_warm),
         offsetof(dc_options, p_inner), offsetof(dc_options, inner_tol), offsetof(dc_options, m2l_engine));
- printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(dc_subdivide_options), sizeof(dc_subdivide_stats),
+ printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dc_subdivide_options), sizeof(dc_subdivide_stats),
         offsetof(dc_subdivide_options, label_ratio), offsetof(dc_subdivide_stats, ms_solve),
         offsetof(dc_options, coarse_max), offsetof(dc_solve_stats, true_rel_resid),
-        offsetof(dc_options, adapt_max_len));
+        offsetof(dc_options, adapt_max_len), offsetof(dc_options, eval_tile));
  return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
@@ -77,7 +77,7 @@ int main(void){
     assert sub == [ctypes.sizeof(P.dc_subdivide_options), ctypes.sizeof(P.dc_subdivide_stats),
                    P.dc_subdivide_options.label_ratio.offset, P.dc_subdivide_stats.ms_solve.offset,
                    P.dc_options.coarse_max.offset, P.dc_solve_stats.true_rel_resid.offset,
-                   P.dc_options.adapt_max_len.offset]
+                   P.dc_options.adapt_max_len.offset, P.dc_options.eval_tile.offset]
 
 
 def test_defaults_and_status_strings(dcmod):
