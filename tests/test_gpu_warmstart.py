@@ -171,3 +171,39 @@ def test_trained_warm_start_cuts_the_initial_residual(dcmod, cuda_ok, M):
     assert np.all(np.array(sw.warm_resid) < np.minimum(1.0, ones))
     ref = cold.get_density()
     np.testing.assert_allclose(warm.get_density(), ref, rtol=0, atol=1e-8 * np.abs(ref).max())
+
+
+def test_learned_mode_in_the_chosen_form(dcmod, cuda_ok):
+    """DC_X0_LEARNED in the FP32 form (refinement around the FP32 inner
+    GMRES): a briefly trained network's start lowers the initial residual
+    below the paper's x0 = 1, and the solve reaches the same density."""
+    from paper_2311_14312_gb300 import warmstart
+    import torch
+    kw = dict(form="fmm32", p=24, leaf_size=32, gmres_tol=1e-10)
+    feats, targs = [], []
+    for i in range(8):
+        d = drawing_by_name("mixed16", seed=200 + i)
+        c = dcmod.Context(g=d.g, s_per_panel=d.s_per_panel, **kw)
+        c.build_drawing(d)
+        c.solve_density()
+        f, t = warmstart.collect(c)
+        feats.append(f)
+        targs.append(t)
+        c.close()
+    params, hist = warmstart.train(torch.cat(feats), torch.cat(targs), hidden=64, steps=1000, batch=512,
+                                   lr=2e-3, seed=6, log_every=500)
+    d = drawing_by_name("mixed16")
+    cold = dcmod.Context(g=d.g, s_per_panel=d.s_per_panel, **kw)
+    cold.build_drawing(d)
+    sc = cold.solve_density()
+    warm = dcmod.Context(g=d.g, s_per_panel=d.s_per_panel, x0_mode=dcmod.DC_X0_LEARNED, **kw)
+    warm.build_drawing(d)
+    warm.set_warm_start_model(64, params)
+    sw = warm.solve_density()
+    ones = _initial_residuals(dcmod, warm, d)
+    print(f"fmm32: initial residual x0 = 1 {[round(float(r), 4) for r in ones]}, learned "
+          f"{[round(r, 4) for r in sw.warm_resid]}; iterations cold {list(sc.iters)} warm {list(sw.iters)}")
+    assert sc.converged == 1 and sw.converged == 1
+    assert np.all(np.array(sw.warm_resid) < np.minimum(1.0, ones))
+    ref = cold.get_density()
+    assert np.abs(warm.get_density() - ref).max() <= 1e-8 * np.abs(ref).max()
