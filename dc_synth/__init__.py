@@ -21,4 +21,7 @@ from .drawings import (  # noqa: F401
     pixel_sample,
     viewport_set,
     curve_point,
+    circle_loops,
+    curve_tangent,
 )
+from . import harmonic  # noqa: F401

@@ -419,6 +419,48 @@ def drawing_by_name(name: str, seed: int | None = None) -> Drawing:
     raise KeyError(name)
 
 
+# Cubic Bezier quarter arcs: control arm 4/3 tan(pi/8) of the radius (the
+# standard tangent-matching construction; radial error below 3e-4 r).
+_ARC_ARM = 4.0 / 3.0 * np.tan(np.pi / 8.0)
+
+
+def circle_loops(loops, panels_per_arc: int = 4, g: int = 8, s_per_panel: int | None = None,
+                 seed: int = 0, name: str = "loops") -> Drawing:
+    """Closed loops of four cubic quarter arcs each, for regions bounded by
+    curves: ``loops`` lists (cx, cy, r, ccw); ccw = True traverses the loop
+    counter-clockwise (an outer boundary), False clockwise (a hole).  Panels
+    are equal arc-length quarters of each arc; colours are seeded uniform."""
+    ctrl = []
+    for cx, cy, r, ccw in loops:
+        c = np.array([cx, cy], float)
+        arcs = []
+        for k in range(4):
+            a0, a1 = 0.5 * np.pi * k, 0.5 * np.pi * (k + 1)
+            p0 = c + r * np.array([np.cos(a0), np.sin(a0)])
+            p3 = c + r * np.array([np.cos(a1), np.sin(a1)])
+            p1 = p0 + _ARC_ARM * r * np.array([-np.sin(a0), np.cos(a0)])
+            p2 = p3 - _ARC_ARM * r * np.array([-np.sin(a1), np.cos(a1)])
+            arcs.append(np.array([p0, p1, p2, p3]))
+        if not ccw:
+            arcs = [a[::-1] for a in arcs[::-1]]
+        ctrl.extend(arcs)
+    ctrl = np.asarray(ctrl)
+    n = ctrl.shape[0]
+    ptr, start = _uniform_panels(n, panels_per_arc)
+    rng = np.random.default_rng(seed)
+    return Drawing(name, ctrl, np.zeros(n, bool), _colours(rng, n), ptr, start,
+                   g=g, s_per_panel=s_per_panel or 5 * g, meta={"loops": list(loops)})
+
+
+def curve_tangent(drawing: Drawing, i, t) -> np.ndarray:
+    """dB/dt of curve(s) i at Bezier parameter(s) t (input generation only)."""
+    c = drawing.ctrl[np.asarray(i)]
+    t = np.asarray(t, float)[..., None]
+    u = 1.0 - t
+    return 3 * u * u * (c[..., 1, :] - c[..., 0, :]) + 6 * u * t * (c[..., 2, :] - c[..., 1, :]) \
+        + 3 * t * t * (c[..., 3, :] - c[..., 2, :])
+
+
 def curve_point(drawing: Drawing, i: int, t: float) -> np.ndarray:
     """Point of curve i at Bezier parameter t (input generation only)."""
     c = drawing.ctrl[i]
