@@ -231,6 +231,34 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl,
  * stats filled) if gmres_max_iter is reached first. */
 dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats);
 
+/* Mixed Dirichlet / Neumann conditions on closed curves (Sec. 4.3).  The
+ * region is the one the curves bound: every curve closed and traversed
+ * counter-clockwise (outer boundary) or clockwise (holes), so that the
+ * right-hand normal n points out of the region.  On each Dirichlet panel u
+ * is given, on each Neumann panel psi = du/dn.  Green's third identity
+ * seen from inside gives at the nodes
+ *     u / 2 = G_H psi - F_H u,
+ * solved for psi on the Dirichlet panels and u on the Neumann panels by
+ * FP64 GMRES, right-preconditioned by the panels' inverse G_H blocks on the
+ * Dirichlet panels (identity in the dense form) and -2 on the Neumann
+ * panels.  Both FMM forms apply G_H and F_H with the FP64 passes.
+ * Afterwards sigma = psi and mu = -u at every node, so dc_render_viewport
+ * and dc_eval_points give u inside the region and 0 outside.
+ *   neumann   host [n_panels]: nonzero = Neumann panel
+ *   psi_star  host [n_nodes][3]: du/dn, read on the Neumann panels only
+ *   u_star    host [n_nodes][3]: u, read on the Dirichlet panels only;
+ *             NULL = the drawing's colours on the left of the curves
+ * stats (may be NULL): iters, rel_resid, true_rel_resid, converged,
+ * n_matvec (G_H and F_H applications), ms_solve.
+ * Errors: DC_ERR_STATE before dc_build_tree, DC_ERR_ARG for NULL inputs,
+ * non-finite values or no Dirichlet panel at all, DC_ERR_GEOMETRY when the
+ * total signed area of the curves is not positive (a necessary condition
+ * of the orientation; closedness is the caller's), DC_ERR_NOCONV as in
+ * dc_solve_density (the densities are kept).  The next dc_solve_density
+ * restores mu = u+ - u- from the colours. */
+dc_status dc_solve_mixed(dc_ctx *ctx, const unsigned char *neumann, const double *psi_star,
+                         const double *u_star, dc_solve_stats *stats);
+
 /* Renders n_vp viewports (Alg. 4): u = single layer of sigma plus
  * double layer of mu at every pixel centre.
  *   rgb       [sum_v height_v width_v][3] of rgb_dtype, viewports

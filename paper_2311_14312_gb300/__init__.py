@@ -107,7 +107,7 @@ EXPORTS = ["dc_default_options", "dc_create", "dc_destroy", "dc_build_tree", "dc
            "dc_aux_panel_features", "dc_aux_set_warm_start_model", "dc_aux_apply_operator", "dc_aux_precond_info",
            "dc_aux_build_timings", "dc_aux_test_skip_mma_tile", "dc_aux_fp32_peak",
            "dc_aux_time_inner_m2l", "dc_subdivide", "dc_get_panels", "dc_aux_subdivision_info",
-           "dc_aux_adaptive_panels", "dc_autotune"]
+           "dc_aux_adaptive_panels", "dc_autotune", "dc_solve_mixed"]
 
 
 def _load():
@@ -122,6 +122,7 @@ def _load():
     lib.dc_destroy.restype = None
     lib.dc_build_tree.argtypes = [P, I, P, P, P, P]
     lib.dc_solve_density.argtypes = [P, P, ctypes.POINTER(dc_solve_stats)]
+    lib.dc_solve_mixed.argtypes = [P, P, P, P, ctypes.POINTER(dc_solve_stats)]
     lib.dc_render_viewport.argtypes = [P, I, ctypes.POINTER(dc_viewport), P, I, P, I,
                                        ctypes.POINTER(dc_render_stats)]
     lib.dc_eval_points.argtypes = [P, I, P, I, P, I, I]
@@ -288,6 +289,22 @@ class Context:
         x = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
         allow = (DC_ERR_NOCONV,) if allow_noconv else ()
         self._check(_get_lib().dc_solve_density(self._h, _ptr(x), ctypes.byref(stats)), allow)
+        return stats
+
+    def solve_mixed(self, neumann, psi, u=None, allow_noconv=False) -> dc_solve_stats:
+        """Mixed Dirichlet / Neumann solve (Sec. 4.3) on closed curves:
+        neumann [n_panels] bool, psi [n_nodes, 3] = du/dn on the Neumann
+        panels, u [n_nodes, 3] on the Dirichlet panels (None: the colours on
+        the left of the curves)."""
+        stats = dc_solve_stats()
+        nm = np.ascontiguousarray(np.asarray(neumann, dtype=bool).astype(np.uint8))
+        ps = np.ascontiguousarray(psi, dtype=np.float64)
+        uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+        n = self.sizes()
+        if nm.shape != (n.n_panels,) or ps.shape != (n.n_nodes, 3) or (uu is not None and uu.shape != ps.shape):
+            raise ValueError("solve_mixed: neumann must be [n_panels], psi and u [n_nodes, 3]")
+        allow = (DC_ERR_NOCONV,) if allow_noconv else ()
+        self._check(_get_lib().dc_solve_mixed(self._h, _ptr(nm), _ptr(ps), _ptr(uu), ctypes.byref(stats)), allow)
         return stats
 
     def get_density(self) -> np.ndarray:

@@ -17,6 +17,9 @@
 //    per channel (the two sides of Eq. 41).
 //  * node_mask_kernel: zeroes node values outside a per-panel mask (the
 //    restriction to the re-solving panels of the local system).
+//  * blend_kernel: node values taken from one vector or another by a
+//    per-panel mask, each scaled (the Dirichlet / Neumann parts of the mixed
+//    problem of Sec. 4.3 and its block-diagonal preconditioner).
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -86,6 +89,15 @@ __global__ void max_diff_kernel(const float *__restrict__ a, const double *__res
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
+// out = pmask[panel] ? beta b : alpha a at every node and channel
+__global__ void blend_kernel(double *__restrict__ out, const double *__restrict__ a, double alpha,
+                             const double *__restrict__ b, double beta, const unsigned char *__restrict__ pmask,
+                             int N, int g) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * N) return;
+    out[t] = pmask[(t / 3) / g] ? beta * b[t] : alpha * a[t];
+}
+
 __global__ void node_mask_kernel(double *__restrict__ v, const unsigned char *__restrict__ pmask, int N, int g) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * N) return;
@@ -128,6 +140,13 @@ cudaError_t launch_max_diff(const float *a, const double *b, long long n, unsign
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     max_diff_kernel<<<4 * 152, kThreads, 0, st>>>(a, b, n, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend(double *out, const double *a, double alpha, const double *b, double beta,
+                         const unsigned char *pmask, int N, int g, cudaStream_t st) {
+    blend_kernel<<<blocks(3LL * N), kThreads, 0, st>>>(out, a, alpha, b, beta, pmask, N, g);
     note_launch();
     return cudaGetLastError();
 }

@@ -38,6 +38,7 @@ struct dc_ctx {
     DevBuf<double> stage64;
     DevBuf<double> AG, AF;         // dense form
     bool seg_density_valid = false;
+    bool mu_custom = false;        // mu set by dc_solve_mixed (restored from the colours by the next solve)
     dc::GmresWork *gw = nullptr;
     std::unique_ptr<dc::Fmm> fmm;  // FMM forms
     // learned warm start: network parameters, feature tables, buffers
@@ -193,6 +194,51 @@ struct MaskedOp : dc::Operator {
             if ((e = ctx->fmm->apply_single_layer(t2, y, st)) != cudaSuccess) return e;
         }
         return dc::launch_node_mask(y, pmask, N, g, st);
+    }
+};
+
+// The block operator of the mixed problem (Sec. 4.3) with its right
+// preconditioner: x holds psi on the Dirichlet panels and u on the Neumann
+// panels; y = A M x with
+//   M x = B x on Dirichlet panels (the panels' inverse G_H blocks; identity
+//         in the dense form), -2 x on Neumann panels,
+//   A z = G_H (m_d z) - F_H (m_n z) - (m_n z) / 2.
+struct MixedOp : dc::Operator {
+    dc_ctx *ctx = nullptr;
+    const unsigned char *nmask = nullptr, *dmask = nullptr;   // per panel
+    double *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;
+    cudaError_t precond(const double *x, double *out, cudaStream_t st) {
+        const int N = ctx->dg.N, g = ctx->dg.g;
+        cudaError_t e;
+        const double *bx = x;
+        if (ctx->opt.form != DC_FORM_DENSE64) {
+            if ((e = ctx->fmm->apply_block_jacobi(x, t3, st)) != cudaSuccess) return e;
+            bx = t3;
+        }
+        return dc::launch_blend(out, bx, 1.0, x, -2.0, nmask, N, g, st);
+    }
+    cudaError_t apply_A(const double *z, double *y, cudaStream_t st) {
+        const int N = ctx->dg.N, g = ctx->dg.g;
+        const bool dense = ctx->opt.form == DC_FORM_DENSE64;
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(t2, z, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+            (e = dc::launch_node_mask(t2, dmask, N, g, st)) != cudaSuccess)
+            return e;
+        e = dense ? dc::launch_dense_gemv(ctx->AG.ptr, N, t2, y, st) : ctx->fmm->apply_single_layer(t2, y, st);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(t2, z, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+            (e = dc::launch_node_mask(t2, nmask, N, g, st)) != cudaSuccess)
+            return e;
+        e = dense ? dc::launch_dense_gemv(ctx->AF.ptr, N, t2, t3, st) : ctx->fmm->apply_double_layer(t2, t3, st);
+        if (e != cudaSuccess) return e;
+        const double one[3] = {1, 1, 1}, m1[3] = {-1, -1, -1}, mh[3] = {-0.5, -0.5, -0.5};
+        if ((e = dc::vec_combine3(y, t3, y, N, one, m1, st)) != cudaSuccess) return e;
+        return dc::vec_combine3(y, t2, y, N, one, mh, st);
+    }
+    cudaError_t apply(const double *x, double *y, cudaStream_t st) override {
+        cudaError_t e = precond(x, t1, st);
+        if (e != cudaSuccess) return e;
+        return apply_A(t1, y, st);
     }
 };
 
@@ -527,6 +573,10 @@ dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats)
         }
     } guard{e0, e1};
     DC_CK(ctx, cudaEventRecord(e0, s), "event");
+    if (ctx->mu_custom) {   // dc_solve_mixed set mu; the two-sided problem takes it from the colours
+        DC_CK(ctx, dc::launch_mu(ctx->dg, ctx->mu.ptr, s), "mu");
+        ctx->mu_custom = false;
+    }
     // b = (u+ + u-)/2 - F_H mu  (Alg. 3)
     if (ctx->opt.form == DC_FORM_DENSE64) {
         DC_CK(ctx, dc::launch_dense_gemv(ctx->AF.ptr, N, ctx->mu.ptr, ctx->fmu.ptr, s), "rhs");
@@ -1344,6 +1394,98 @@ dc_status dc_autotune(dc_ctx *ctx, int n_vp, const dc_viewport *vps, int n_leaf,
     dc_status st = rebuild(fin);
     if (st != DC_OK) return st;
     return DC_OK;
+}
+
+// ------------------------------------------------ mixed conditions (4.3) --
+dc_status dc_solve_mixed(dc_ctx *ctx, const unsigned char *neumann, const double *psi_star,
+                         const double *u_star, dc_solve_stats *stats) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "solve_mixed: call build_tree first");
+    if (!neumann || !psi_star) return fail(ctx, DC_ERR_ARG, "solve_mixed: need the Neumann panels and psi");
+    const int N = ctx->dg.N, g = ctx->dg.g, P = ctx->dg.n_panels;
+    const size_t n3 = size_t(3) * N;
+    for (size_t i = 0; i < n3; ++i)
+        if (!std::isfinite(psi_star[i]) || (u_star && !std::isfinite(u_star[i])))
+            return fail(ctx, DC_ERR_ARG, "solve_mixed: non-finite boundary data");
+    // the region must lie on the left of the curves: positive total signed
+    // area of the solve polyline (a necessary condition; loops are not traced)
+    double area = 0.0;
+    for (size_t k = 0; k < ctx->geo.seg_xy.size() / 4; ++k) {
+        const double *e = &ctx->geo.seg_xy[4 * k];
+        area += 0.5 * (e[0] * e[3] - e[2] * e[1]);
+    }
+    if (!(area > 0.0))
+        return fail(ctx, DC_ERR_GEOMETRY, "solve_mixed: the curves must bound the region counter-clockwise");
+    std::vector<unsigned char> nm(P), dm(P);
+    int n_neu = 0;
+    for (int p = 0; p < P; ++p) {
+        nm[p] = neumann[p] ? 1 : 0;
+        dm[p] = 1 - nm[p];
+        n_neu += nm[p];
+    }
+    if (n_neu == P) return fail(ctx, DC_ERR_ARG, "solve_mixed: at least one panel needs a Dirichlet value");
+    cudaStream_t s = ctx->stream;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    auto t0 = std::chrono::steady_clock::now();
+    DevBuf<unsigned char> dn, dd;
+    DevBuf<double> ud, psin, b, z, x, t1, t2, t3;
+    DC_CK(ctx, dn.alloc(P), "solve_mixed: alloc");
+    DC_CK(ctx, dd.alloc(P), "solve_mixed: alloc");
+    for (auto *bp : {&ud, &psin, &b, &z, &x, &t1, &t2, &t3}) DC_CK(ctx, bp->alloc(n3), "solve_mixed: alloc");
+    DC_CK(ctx, cudaMemcpyAsync(dn.ptr, nm.data(), P, cudaMemcpyHostToDevice, s), "solve_mixed");
+    DC_CK(ctx, cudaMemcpyAsync(dd.ptr, dm.data(), P, cudaMemcpyHostToDevice, s), "solve_mixed");
+    DC_CK(ctx, cudaMemcpyAsync(psin.ptr, psi_star, n3 * sizeof(double), cudaMemcpyHostToDevice, s), "solve_mixed");
+    if (u_star)
+        DC_CK(ctx, cudaMemcpyAsync(ud.ptr, u_star, n3 * sizeof(double), cudaMemcpyHostToDevice, s), "solve_mixed");
+    else
+        DC_CK(ctx, cudaMemcpyAsync(ud.ptr, ctx->dg.u_minus.ptr, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s),
+              "solve_mixed");
+    DC_CK(ctx, dc::launch_node_mask(ud.ptr, dd.ptr, N, g, s), "solve_mixed");
+    DC_CK(ctx, dc::launch_node_mask(psin.ptr, dn.ptr, N, g, s), "solve_mixed");
+    MixedOp op;
+    op.ctx = ctx;
+    op.nmask = dn.ptr;
+    op.dmask = dd.ptr;
+    op.t1 = t1.ptr;
+    op.t2 = t2.ptr;
+    op.t3 = t3.ptr;
+    // b = u_d / 2 + F_H u_d - G_H psi_n
+    const bool dense = ctx->opt.form == DC_FORM_DENSE64;
+    DC_CK(ctx, dense ? dc::launch_dense_gemv(ctx->AF.ptr, N, ud.ptr, b.ptr, s)
+                     : ctx->fmm->apply_double_layer(ud.ptr, b.ptr, s), "solve_mixed: rhs");
+    DC_CK(ctx, dense ? dc::launch_dense_gemv(ctx->AG.ptr, N, psin.ptr, t1.ptr, s)
+                     : ctx->fmm->apply_single_layer(psin.ptr, t1.ptr, s), "solve_mixed: rhs");
+    {
+        const double one[3] = {1, 1, 1}, half[3] = {0.5, 0.5, 0.5}, m1[3] = {-1, -1, -1};
+        DC_CK(ctx, dc::vec_combine3(b.ptr, ud.ptr, b.ptr, N, one, half, s), "solve_mixed: rhs");
+        DC_CK(ctx, dc::vec_combine3(b.ptr, t1.ptr, b.ptr, N, one, m1, s), "solve_mixed: rhs");
+    }
+    DC_CK(ctx, cudaMemsetAsync(z.ptr, 0, n3 * sizeof(double), s), "solve_mixed");
+    dc::GmresResult gr;
+    std::string msg;
+    cudaError_t ce = dc::gmres_solve(ctx->gw, op, N, b.ptr, z.ptr, true, false, ctx->opt.gmres_tol,
+                                     ctx->opt.gmres_restart, ctx->opt.gmres_max_iter, s, gr, msg);
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, msg.empty() ? "solve_mixed: gmres" : msg.c_str());
+    DC_CK(ctx, op.precond(z.ptr, x.ptr, s), "solve_mixed");
+    // sigma = psi (psi_d from x, psi* given), mu = -u (u_n from x, u* given)
+    DC_CK(ctx, dc::launch_blend(ctx->sigma.ptr, x.ptr, 1.0, psin.ptr, 1.0, dn.ptr, N, g, s), "solve_mixed");
+    DC_CK(ctx, dc::launch_blend(ctx->mu.ptr, ud.ptr, -1.0, x.ptr, -1.0, dn.ptr, N, g, s), "solve_mixed");
+    DC_CK(ctx, cudaStreamSynchronize(s), "solve_mixed");
+    ctx->mu_custom = true;
+    ctx->seg_density_valid = false;
+    ctx->state = 2;
+    if (stats) {
+        for (int c = 0; c < 3; ++c) {
+            stats->iters[c] = gr.iters[c];
+            stats->rel_resid[c] = gr.rel_resid[c];
+            stats->true_rel_resid[c] = gr.true_rel_resid[c];
+        }
+        stats->converged = gr.converged;
+        stats->n_matvec = 2 * gr.n_matvec + 2;
+        stats->ms_solve = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return gr.converged ? DC_OK : fail(ctx, DC_ERR_NOCONV, "solve_mixed: GMRES did not reach gmres_tol");
 }
 
 dc_status dc_aux_fp32_peak(void *stream, double *out) {

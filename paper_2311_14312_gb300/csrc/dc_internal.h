@@ -63,6 +63,9 @@ cudaError_t launch_split_interp(const double *sig_old, const int2 *pmap, const d
 cudaError_t launch_unit_density(double *x, int N, int g, const int panels[3], cudaStream_t st);
 cudaError_t launch_panel_range(const double *v, int n_panels, int g, double *out, cudaStream_t st);
 cudaError_t launch_node_mask(double *v, const unsigned char *pmask, int N, int g, cudaStream_t st);
+// out = pmask[panel] ? beta b : alpha a
+cudaError_t launch_blend(double *out, const double *a, double alpha, const double *b, double beta,
+                         const unsigned char *pmask, int N, int g, cudaStream_t st);
 // *out = max |a_i - b_i| (FP32 bits, device)
 cudaError_t launch_max_diff(const float *a, const double *b, long long n, unsigned *out, cudaStream_t st);
 
