@@ -131,6 +131,12 @@ typedef struct {
                               render's evaluation kernel: 0 = 8 x 8 (default),
                               1 = 16 x 8, 2 = 16 x 16, 3 = 32 x 8 (width x
                               height)                                         */
+    int aa_levels;         /* quadtree anti-aliasing of the render (Sec. 7):
+                              0 = off (centre samples, default); m in [1, 6]:
+                              a pixel whose closed square meets a segment is
+                              split into quarter cells while they meet one,
+                              down to 2^-m of the pixel, and takes the
+                              area-weighted mean of the cells' centre values */
 } dc_options;
 
 enum {
@@ -188,6 +194,9 @@ typedef struct {
     double eval_flops;     /* algorithmic flops of the evaluation kernels:
                               45 per near-field pair, 24 (p + 1) per L2P and
                               per list-3 M2P (3 colour channels)              */
+    long long aa_pixels;   /* pixels refined by the anti-aliasing (aa_levels) */
+    long long aa_samples;  /* their samples                                  */
+    double ms_aa;          /* device time of the anti-aliasing pass          */
 } dc_render_stats;
 
 /* Fills *opt with defaults: DC_FORM_FMM32, g 16, s 80, p 24, leaf 64,

@@ -111,3 +111,30 @@ def render_aa(disc: O.Discretisation, sigma, mu, viewport, width: int, height: i
     out = np.zeros((len(pixels), 3))
     np.add.at(out, own, W[:, None] * u)
     return out, edge, tie, nsamp
+
+
+def edge_pixels(disc: O.Discretisation, viewport, width: int, height: int):
+    """Row-major indices of the pixels whose closed square meets a segment
+    (the pixels Sec. 7 refines), and of those whose decision is a tie.
+    Every (segment, pixel) pair within one pixel of the segment's box is
+    tested with ``meets``."""
+    seg = np.ascontiguousarray(disc.seg_xy, np.float64)
+    vx0, vy0, vx1, vy1 = viewport
+    dx, dy = (vx1 - vx0) / width, (vy1 - vy0) / height
+    lox, hix = np.minimum(seg[:, 0], seg[:, 2]), np.maximum(seg[:, 0], seg[:, 2])
+    loy, hiy = np.minimum(seg[:, 1], seg[:, 3]), np.maximum(seg[:, 1], seg[:, 3])
+    c0 = np.clip(np.floor((lox - vx0) / dx) - 1, 0, width - 1).astype(np.int64)
+    c1 = np.clip(np.floor((hix - vx0) / dx) + 1, 0, width - 1).astype(np.int64)
+    r0 = np.clip(np.floor((loy - vy0) / dy) - 1, 0, height - 1).astype(np.int64)
+    r1 = np.clip(np.floor((hiy - vy0) / dy) + 1, 0, height - 1).astype(np.int64)
+    inside = (np.floor((hix - vx0) / dx) + 1 >= 0) & (np.floor((lox - vx0) / dx) - 1 <= width - 1) \
+        & (np.floor((hiy - vy0) / dy) + 1 >= 0) & (np.floor((loy - vy0) / dy) - 1 <= height - 1)
+    nc, nr = c1 - c0 + 1, r1 - r0 + 1
+    k = np.where(inside, nc * nr, 0)
+    sid = np.repeat(np.arange(len(seg)), k)
+    j = np.arange(k.sum()) - np.repeat(np.cumsum(k) - k, k)
+    c = c0[sid] + j % nc[sid]
+    r = r0[sid] + j // nc[sid]
+    m, t = meets(seg[sid], vx0 + c * dx, vy0 + r * dy, vx0 + (c + 1) * dx, vy0 + (r + 1) * dy)
+    pix = r * width + c
+    return np.unique(pix[m]), np.unique(pix[t])

@@ -47,7 +47,8 @@ class dc_options(ctypes.Structure):
                 ("p_inner", ctypes.c_int), ("inner_tol", ctypes.c_double), ("m2l_engine", ctypes.c_int),
                 ("coarse_max", ctypes.c_int), ("adapt_ratio", ctypes.c_double),
                 ("adapt_max_level", ctypes.c_int), ("adapt_min_panels", ctypes.c_int),
-                ("adapt_max_len", ctypes.c_double), ("eval_tile", ctypes.c_int)]
+                ("adapt_max_len", ctypes.c_double), ("eval_tile", ctypes.c_int),
+                ("aa_levels", ctypes.c_int)]
 
 
 class dc_sizes(ctypes.Structure):
@@ -95,7 +96,8 @@ class dc_render_stats(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double), ("ms_eval", ctypes.c_double),
                 ("pixels", ctypes.c_longlong), ("p2p_pairs", ctypes.c_longlong),
                 ("m2p_pairs", ctypes.c_longlong), ("m2l_pairs", ctypes.c_longlong),
-                ("eval_flops", ctypes.c_double)]
+                ("eval_flops", ctypes.c_double), ("aa_pixels", ctypes.c_longlong),
+                ("aa_samples", ctypes.c_longlong), ("ms_aa", ctypes.c_double)]
 
 
 EXPORTS = ["dc_default_options", "dc_create", "dc_destroy", "dc_build_tree", "dc_solve_density",

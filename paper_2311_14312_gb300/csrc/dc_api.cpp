@@ -38,7 +38,8 @@ struct dc_ctx {
     DevBuf<double> stage64;
     DevBuf<double> AG, AF;         // dense form
     bool seg_density_valid = false;
-    bool mu_custom = false;        // mu set by dc_solve_mixed (restored from the colours by the next solve)
+    bool mu_custom = false;
+    dc::AaWork aa;                 // anti-aliasing buffers (options.aa_levels)        // mu set by dc_solve_mixed (restored from the colours by the next solve)
     dc::GmresWork *gw = nullptr;
     std::unique_ptr<dc::Fmm> fmm;  // FMM forms
     // learned warm start: network parameters, feature tables, buffers
@@ -135,6 +136,10 @@ dc_status check_options(const dc_options &o, std::string &msg) {
     }
     if (o.eval_tile < 0 || o.eval_tile > 3) {
         msg = "options: eval_tile must be in [0, 3]";
+        return DC_ERR_ARG;
+    }
+    if (o.aa_levels < 0 || o.aa_levels > 6) {
+        msg = "options: aa_levels must be in [0, 6]";
         return DC_ERR_ARG;
     }
     if (o.coarse_max != 0 && (o.coarse_max < 64 || o.coarse_max > 16384 || o.coarse_max % 32 != 0)) {
@@ -825,6 +830,45 @@ dc_status dc_render_viewport(dc_ctx *ctx, int n_vp, const dc_viewport *vps, void
                                                   rgb_dtype, drgb8, s, msg);
         if (fs != DC_OK) return fail(ctx, fs, msg);
     }
+    // quadtree anti-aliasing (Sec. 7): refined pixels overwrite their centre samples
+    double aa_ms = 0.0;
+    if (ctx->opt.aa_levels > 0 && (drgb || drgb8)) {
+        if (n_vp > 65535) return fail(ctx, DC_ERR_ARG, "render_viewport: anti-aliasing takes at most 65535 viewports");
+        cudaEvent_t a0 = nullptr, a1 = nullptr;
+        if (stats) {
+            DC_CK(ctx, cudaEventCreate(&a0), "event");
+            DC_CK(ctx, cudaEventCreate(&a1), "event");
+            DC_CK(ctx, cudaEventRecord(a0, s), "event");
+        }
+        std::string msg;
+        cudaError_t ce = ctx->aa.prepare(ctx->dg, vl.data(), n_vp, total, ctx->opt.aa_levels, s, msg);
+        if (ce != cudaSuccess) {
+            if (!msg.empty()) return fail(ctx, DC_ERR_ARG, msg);
+            return cuda_fail(ctx, ce, "anti-aliasing");
+        }
+        if (ctx->aa.n_samples > 0) {
+            if (ctx->opt.form == DC_FORM_DENSE64) {
+                DC_CK(ctx,
+                      dc::launch_dense_eval_points(ctx->dg, ctx->sbar.ptr, ctx->mbar.ptr, ctx->aa.sxy.ptr,
+                                                   ctx->aa.n_samples, ctx->aa.u.ptr, s),
+                      "anti-aliasing samples");
+            } else {
+                dc_status fs = ctx->fmm->eval_points_dev(ctx->aa.sxy.ptr, ctx->aa.n_samples, ctx->sbar.ptr,
+                                                         ctx->mbar.ptr, ctx->aa.u.ptr, s, msg);
+                if (fs != DC_OK) return fail(ctx, fs, msg);
+            }
+            DC_CK(ctx, ctx->aa.finish(drgb, rgb_dtype, drgb8, s), "anti-aliasing");
+        }
+        if (stats) {
+            DC_CK(ctx, cudaEventRecord(a1, s), "event");
+            DC_CK(ctx, cudaEventSynchronize(a1), "event");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a0, a1);
+            aa_ms = ms;
+            cudaEventDestroy(a0);
+            cudaEventDestroy(a1);
+        }
+    }
     if (out_where == DC_MEM_HOST) {
         if (rgb)
             DC_CK(ctx,
@@ -844,6 +888,11 @@ dc_status dc_render_viewport(dc_ctx *ctx, int n_vp, const dc_viewport *vps, void
         cudaEventDestroy(e1);
         stats->ms = ms;
         stats->pixels = total;
+        if (ctx->opt.aa_levels > 0) {
+            stats->aa_pixels = ctx->aa.n_edge;
+            stats->aa_samples = ctx->aa.n_samples;
+            stats->ms_aa = aa_ms;
+        }
         if (ctx->fmm) {
             stats->p2p_pairs = ctx->fmm->last_render_p2p_pairs();
             stats->m2p_pairs = ctx->fmm->last_render_m2p_pairs();

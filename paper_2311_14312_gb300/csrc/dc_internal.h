@@ -117,6 +117,33 @@ struct VpDev {
     long long offset;         // first output pixel of this viewport
 };
 
+// Exclusive scan of int counts on the device (aa.cu): out[i] = sum of
+// in[0..i); the total lands in total.ptr[0] (device).  in may equal out.
+struct ScanWork {
+    static constexpr int kLevels = 6;
+    DevBuf<long long> lv[kLevels];
+    DevBuf<long long> total;
+};
+cudaError_t scan_exclusive(const int *in, int *out, long long n, ScanWork &w, cudaStream_t st);
+
+// Quadtree anti-aliasing of a render (Sec. 7; aa.cu).  prepare() finds the
+// pixels whose closed square meets a segment, splits their cells and lists
+// the samples (sxy [n_samples][2], weights sw); the caller evaluates the
+// colours at sxy into u [n_samples][3]; finish() writes each refined
+// pixel's weighted sum over the render's outputs.  cudaErrorInvalidValue
+// with err set for calls beyond the index ranges.
+struct AaWork {
+    DevBuf<VpDev> vps;
+    DevBuf<int> cnt, off, ids, ns, soff;
+    DevBuf<long long> edge;
+    DevBuf<double> sxy, sw, u;
+    ScanWork scan;
+    int n_edge = 0, n_samples = 0;
+    cudaError_t prepare(const DevGeom &G, const VpDev *vps_host, int n_vp, long long total_px, int levels,
+                        cudaStream_t st, std::string &err);
+    cudaError_t finish(void *rgb, int rgb_dtype, unsigned char *rgb8, cudaStream_t st);
+};
+
 // ------------------------------------------------------- kernel entry --
 // K1: values at segments from values at nodes (sigma_bar = Lambda sigma).
 cudaError_t launch_interp(const DevGeom &G, const double *node_vals, double *seg_vals,

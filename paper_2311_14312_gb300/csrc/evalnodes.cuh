@@ -41,9 +41,10 @@ template <typename T> struct NodeArgs {
 __device__ __forceinline__ float elog(float x) { return __logf(x); }
 __device__ __forceinline__ double elog(double x) { return log(x); }
 
-// Far field into the lane sums: target j's L2P (Eq. 64) on lane 8 j mod 32,
-// its list-3 M2P terms (Eq. 61) split over the lanes.  qx, qy: targets
-// relative to the leaf centre.
+// Far field into the lane sums: every target's L2P (Eq. 64) on lane 0, its
+// list-3 M2P terms (Eq. 61) split over the lanes, so a target's result does
+// not depend on its slot in the work item (the order of points within a
+// leaf may vary).  qx, qy: targets relative to the leaf centre.
 constexpr int kPer = kNodeItem / kWarps;   // targets per warp
 
 template <typename T>
@@ -60,7 +61,7 @@ __device__ __forceinline__ void far_into(const NodeArgs<T> &a, int leaf, int t0,
         if (warp + kWarps * j >= nt) break;
         const int ti = t0 + warp + kWarps * j;
         T e0 = 0, e1 = 0, e2 = 0;
-        if (lane == ((8 * j) & 31)) {
+        if (lane == 0) {
             C z = passes::mk<T>(qx[j] * iwl, qy[j] * iwl);
             C s0 = Lc[P1 - 1], s1 = Lc[2 * P1 - 1], s2 = Lc[3 * P1 - 1];
             for (int k = P1 - 2; k >= 0; --k) {

@@ -1553,6 +1553,32 @@ dc_status Fmm::eval_points(const double *xy, int n, const double *sbar, const do
     return DC_OK;
 }
 
+dc_status Fmm::eval_points_dev(const double *xy, int n, const double *sbar, const double *mbar, double *out,
+                               cudaStream_t st, std::string &err) {
+    Impl &I = *impl_;
+    if (n <= 0) return DC_OK;
+    const Tree &T = I.tree;
+    int n_items = 0;
+    bool outside = false;
+    const int item = I.fp32 ? 64 : evalnodes::kNodeItem;
+    cudaError_t e = I.psort.run(xy, n, I.child0.ptr, I.cc.ptr, T.n_cells(), T.x0, T.y0, T.w0, item, I.fp32, st,
+                                n_items, outside);
+    if (e == cudaSuccess && outside) {
+        err = "eval_points: point outside the quadtree root; widen options.domain";
+        return DC_ERR_ARG;
+    }
+    if (e == cudaSuccess)
+        e = I.fp32 ? I.eval_points32_at(I.psort.items32.ptr, n_items, I.psort.sxy.ptr, I.psort.perm.ptr, out, sbar,
+                                        mbar, st)
+                   : I.eval_list64(I.psort.items64.ptr, n_items, I.psort.sxy.ptr, nullptr, nullptr,
+                                   I.psort.perm.ptr, sbar, mbar, 1, 1, out, st);
+    if (e != cudaSuccess) {
+        err = cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
+    }
+    return DC_OK;
+}
+
 void Fmm::fill_sizes(dc_sizes *out) const {
     const Tree &T = impl_->tree;
     out->n_pieces = int(T.pc_seg.size());

@@ -55,6 +55,11 @@ public:
                                std::string &err);
     dc_status eval_points(const double *xy, int n, const double *sbar, const double *mbar,
                           void *out, int out_dtype, cudaStream_t st, std::string &err);
+    // The same at device points xy [n][2], FP64 output out [n][3], with the
+    // points located and sorted by leaf on the device (no host round trip);
+    // after prepare_eval.
+    dc_status eval_points_dev(const double *xy, int n, const double *sbar, const double *mbar, double *out,
+                              cudaStream_t st, std::string &err);
     void fill_sizes(dc_sizes *out) const;
     // wall ms of the build phases: tree and lists, schedules and uploads,
     // preconditioner, stored P2M / P2L rows, near / far coefficients, FP32 form

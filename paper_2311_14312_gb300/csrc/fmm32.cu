@@ -988,6 +988,12 @@ cudaError_t Fmm::Impl::render_tiles32(int n_tiles, void *rgb, int rgb_dtype,
 
 cudaError_t Fmm::Impl::eval_points32(int n_items, double *out, const double *sb64,
                                      const double *mb64, cudaStream_t st) {
+    return eval_points32_at(pt_items.ptr, n_items, pt_xy.ptr, pt_perm.ptr, out, sb64, mb64, st);
+}
+
+cudaError_t Fmm::Impl::eval_points32_at(const Tile *items, int n_items, const double *q64, const int *perm,
+                                        double *out, const double *sb64, const double *mb64, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
     EvalArgs32 a{};
     a.sb64 = sb64;
     a.mb64 = mb64;
@@ -999,7 +1005,7 @@ cudaError_t Fmm::Impl::eval_points32(int n_items, double *out, const double *sb6
     a.L64 = L.ptr;
     a.t = dt32();
     a.t64 = dt();
-    a.items = pt_items.ptr;
+    a.items = items;
     a.P1 = P1;
     a.M = M32.ptr;
     a.L = L32.ptr;
@@ -1007,9 +1013,9 @@ cudaError_t Fmm::Impl::eval_points32(int n_items, double *out, const double *sb6
     a.mb = mbar32.ptr;
     a.use_s = 1;
     a.use_m = 1;
-    a.q32 = pt_q32.ptr;
-    a.q64 = pt_xy.ptr;
-    a.perm = pt_perm.ptr;
+    a.q32 = nullptr;
+    a.q64 = q64;
+    a.perm = perm;
     a.out = out;
     eval32_kernel<1, 8, 8><<<n_items, 64, 0, st>>>(a); note_launch();
     return cudaGetLastError();

@@ -75,6 +75,21 @@ struct Schedule {
     int n_m2l = 0, n_p2l = 0, n_walk = 0;
 };
 
+// Arbitrary points sorted into the leaves that hold them, on the device
+// (aa.cu): leaf of each point by descent from the root, counting sort by
+// leaf, work items of at most `item` points of one leaf (Tile for the FP32
+// kernel, int4 (leaf, first, count, 0) for the FP64 one).  perm maps sorted
+// positions to the caller's order; sxy holds the sorted points.
+struct PointSort {
+    DevBuf<int> leaf_of, cnt, start, ioff, perm, flag;
+    DevBuf<double> sxy;
+    DevBuf<Tile> items32;
+    DevBuf<int4> items64;
+    ScanWork scan;
+    cudaError_t run(const double *xy, int n, const int *child0, const double *cc, int n_cells, double x0,
+                    double y0, double w0, int item, bool f32, cudaStream_t st, int &n_items, bool &outside);
+};
+
 struct Fmm::Impl {
     dc_options opt{};
     int p = 0, P1 = 0;
@@ -244,6 +259,9 @@ struct Fmm::Impl {
                                cudaStream_t st);
     cudaError_t eval_points32(int n_items, double *out, const double *sb64, const double *mb64,
                               cudaStream_t st);
+    cudaError_t eval_points32_at(const Tile *items, int n_items, const double *q64, const int *perm,
+                                 double *out, const double *sb64, const double *mb64, cudaStream_t st);
+    PointSort psort;
     evalnodes::NodeArgs<double> node_args64(const int4 *items, const double *q64, const int *own1,
                                             const int *own2, const int *perm, const double *sb,
                                             const double *mb, int use_s, int use_m, double *out) const;

@@ -54,6 +54,8 @@ int main(void){
         offsetof(dc_subdivide_options, label_ratio), offsetof(dc_subdivide_stats, ms_solve),
         offsetof(dc_options, coarse_max), offsetof(dc_solve_stats, true_rel_resid),
         offsetof(dc_options, adapt_max_len), offsetof(dc_options, eval_tile));
+ printf("%zu %zu %zu\n", offsetof(dc_options, aa_levels), offsetof(dc_render_stats, aa_pixels),
+        offsetof(dc_render_stats, ms_aa));
  return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
@@ -78,6 +80,9 @@ int main(void){
                    P.dc_subdivide_options.label_ratio.offset, P.dc_subdivide_stats.ms_solve.offset,
                    P.dc_options.coarse_max.offset, P.dc_solve_stats.true_rel_resid.offset,
                    P.dc_options.adapt_max_len.offset, P.dc_options.eval_tile.offset]
+    aa = list(map(int, lines[3].split()))
+    assert aa == [P.dc_options.aa_levels.offset, P.dc_render_stats.aa_pixels.offset,
+                  P.dc_render_stats.ms_aa.offset]
 
 
 def test_defaults_and_status_strings(dcmod):
