@@ -878,6 +878,7 @@ evalnodes::NodeArgs<float> Fmm::Impl::node_args32(double *y, bool single) const 
 }
 
 cudaError_t Fmm::Impl::nodes32_from_segments(double *y, bool single, cudaStream_t st) {
+    if (single && split_ok()) return nodes32_split(y, st, false);
     cudaError_t e;
     int us = single ? 1 : 0, um = single ? 0 : 1;
     if ((e = passes32(sbar32.ptr, mbar32.ptr, us, um, st, sched_nodes)) != cudaSuccess) return e;
@@ -894,17 +895,100 @@ cudaError_t Fmm::Impl::nodes32_from_segments(double *y, bool single, cudaStream_
     return cudaGetLastError();
 }
 
+// The inner node operator with the list-4 P2L (it needs only the segment
+// densities) as a branch of its own on side beside P2M -> M2M ->
+// tensor-core M2L on st; the M2L reduction adds onto the P2L terms once the
+// branch is done, then the walk and the node evaluation.  (A third branch
+// for the near field measured slower: its blocks delay the chain's.)
+bool Fmm::Impl::split_ok() const {
+    return graph_split && n_tc_tiles > 0 && sched_nodes.n_m2l > 0 && near_ready && n_nt_items4 > 0;
+}
+
+cudaError_t Fmm::Impl::nodes32_split(double *y, cudaStream_t st, bool fork) {
+    const Schedule &sc = sched_nodes;
+    const int nC = tree.n_cells();
+    const int P1 = P1i;
+    const size_t ebytes = (size_t)nC * 3 * P1 * sizeof(float2);
+    cudaError_t e;
+    passes::TreeView<float> tv = view32();
+    passes::PiecesF32 ps{pc32.ptr};
+    if ((e = cudaMemsetAsync(M32i.ptr, 0, ebytes, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(L32i.ptr, 0, ebytes, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(Lm2l32i.ptr, 0, ebytes, st)) != cudaSuccess)
+        return e;
+    const cudaStream_t s1 = fork ? side : st;
+    if (fork && (e = cudaEventRecord(fork_ev[0], st)) != cudaSuccess) return e;
+    const evalnodes::NodeArgs<float> a = node_args32(y, true);
+    const dim3 grid(n_nt_items4), block(32 * evalnodes::kWarps);
+    // branch: list 4
+    if (fork && (e = cudaStreamWaitEvent(s1, fork_ev[0], 0)) != cudaSuccess) return e;
+    if (sc.n_p2l > 0) {
+        passes::p2l_flat_kernel<float, passes::PiecesF32><<<sc.n_p2l, passes::kChunk, passes::p2l_flat_smem<float>(P1),
+                                                            s1>>>(tv, ps, sc.p2l.ptr, p2l_off.ptr, p2l_cnt.ptr,
+                                                                  p2l_item.ptr, sbar32.ptr, mbar32.ptr, 1, 0, P1,
+                                                                  Lm2l32i.ptr);
+        note_launch();
+    }
+    if (fork && (e = cudaEventRecord(fork_ev[1], s1)) != cudaSuccess) return e;
+    // main branch
+    if (n_p2m > 0) {
+        passes::p2m_kernel<float, passes::PiecesF32><<<n_p2m, passes::kChunk, passes::p2m_smem<float>(P1), st>>>(
+            tv, ps, p2m_leaves.ptr, sbar32.ptr, mbar32.ptr, 1, 0, P1, M32i.ptr, rows_ready ? p2m_g32.ptr : nullptr);
+        note_launch();
+    }
+    if (n_mchunks > 0) {
+        passes::m2m_multi_kernel<float><<<(n_mchunks + passes::kMultiWarps - 1) / passes::kMultiWarps,
+                                          32 * passes::kMultiWarps, 0, st>>>(
+            pair_geo.ptr, mchunks.ptr, n_mchunks, pair_leaf.ptr, P1, binom32.ptr, M32i.ptr, mpart32.ptr);
+        note_launch();
+        if (n_mred > 0) {
+            passes::m2m_reduce_kernel<float><<<n_mred, passes::kReduceThreads, 0, st>>>(mred.ptr, n_mred, P1,
+                                                                                     mpart32.ptr, M32i.ptr);
+            note_launch();
+        }
+    }
+    if (sc.n_m2l > 0 && (e = launch_m2l32(sc, 0, st)) != cudaSuccess) return e;
+    if (fork && (e = cudaStreamWaitEvent(st, fork_ev[1], 0)) != cudaSuccess) return e;
+    if (sc.n_m2l > 0 && (e = launch_m2l32(sc, 1, st)) != cudaSuccess) return e;
+    if (sc.n_walk > 0) {
+        passes::walk_kernel<float><<<sc.n_walk, std::max(32, (std::max(P1, walk_nmax) + 31) / 32 * 32),
+                                     passes::walk_smem<float>(P1, walk_nmax), st>>>(
+            tv, sc.walk.ptr, sc.chains.ptr, P1, walk_nmax, l2l32i.ptr, Lm2l32i.ptr, L32i.ptr);
+        note_launch();
+    }
+    evalnodes::near_apply_kernel<float><<<grid, block, 0, st>>>(a, near_off.ptr, near_g32.ptr, sbar32.ptr,
+                                                                far_ready ? far_off.ptr : nullptr,
+                                                                far_ready ? far32.ptr : nullptr);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // Captures the FP32 preconditioned matvec (g_in -> g_out) once.
 cudaError_t Fmm::Impl::graph_ensure() {
     if (g32_exec) return cudaSuccess;
     cudaError_t e;
     if ((e = g_in.ensure(3 * (size_t)D->N)) != cudaSuccess) return e;
     if ((e = g_out.ensure(3 * (size_t)D->N)) != cudaSuccess) return e;
-    if (!cap_stream && (e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    // the chain P2M -> M2M -> M2L -> walk is the critical path: its nodes run
+    // at the highest priority, the parallel branches at the lowest
+    int prio_lo = 0, prio_hi = 0;
+    if ((e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi)) != cudaSuccess) return e;
+    if (!cap_stream && (e = cudaStreamCreateWithPriority(&cap_stream, cudaStreamNonBlocking, prio_hi)) != cudaSuccess)
         return e;
     if (coarse.aggregated() &&
         ((e = agg_py.ensure(3 * (size_t)D->N)) != cudaSuccess || (e = agg_gpy.ensure(3 * (size_t)D->N)) != cudaSuccess))
         return e;
+    // the branches: tensor-core M2L (its reduction adds onto the P2L terms)
+    // and the near field from stored coefficients
+    const bool split = split_ok();
+    if (split) {
+        if (!side && (e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_lo)) != cudaSuccess) return e;
+        for (auto &ev : fork_ev)
+            if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+    }
+    auto node_op = [&](double *y) {
+        return split ? nodes32_split(y, cap_stream, true) : nodes32_from_segments(y, true, cap_stream);
+    };
     long long before = kernel_launches();
     if ((e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
     // M v straight to the segments (sigma_bar = Lambda M v) when the
@@ -913,7 +997,8 @@ cudaError_t Fmm::Impl::graph_ensure() {
     cudaError_t e1;
     if (coarse.aggregated()) {
         e1 = coarse.apply_stage1(g_in.ptr, agg_py.ptr, cap_stream);
-        if (e1 == cudaSuccess) e1 = apply_nodes32(agg_py.ptr, agg_gpy.ptr, true, cap_stream);
+        if (e1 == cudaSuccess) e1 = interp32(agg_py.ptr, sbar32.ptr, cap_stream);
+        if (e1 == cudaSuccess) e1 = node_op(agg_gpy.ptr);
         if (e1 == cudaSuccess)
             e1 = coarse.apply_stage2(pinv.ptr, g_in.ptr, agg_gpy.ptr, nullptr, cap_stream, lam_ff.ptr, D->s, sbar32.ptr);
     } else {
@@ -922,14 +1007,13 @@ cudaError_t Fmm::Impl::graph_ensure() {
     }
     cudaError_t e2 = e1;
     if (e1 == cudaSuccess)
-        e2 = coarse.ready() ? nodes32_from_segments(g_out.ptr, true, cap_stream)
-                            : apply_nodes32(ir_t.ptr, g_out.ptr, true, cap_stream);
+        e2 = coarse.ready() ? node_op(g_out.ptr) : apply_nodes32(ir_t.ptr, g_out.ptr, true, cap_stream);
     e = cudaStreamEndCapture(cap_stream, &g32);
     g32_kernels = int(kernel_launches() - before);
     note_launch(-g32_kernels);   // counted again at every graph launch
     if (e2 != cudaSuccess) return e2;
     if (e != cudaSuccess) return e;
-    return cudaGraphInstantiate(&g32_exec, g32, 0);
+    return cudaGraphInstantiate(&g32_exec, g32, split ? cudaGraphInstantiateFlagUseNodePriority : 0);
 }
 
 // g_out = A32 M g_in (the captured graph)

@@ -209,6 +209,11 @@ struct Fmm::Impl {
     // the FP32 preconditioned matvec v -> A32 M^-1 v captured as one CUDA
     // graph that reads g_in and writes g_out
     cudaStream_t cap_stream = nullptr;
+    // side stream and events of the captured graph's parallel branch (the
+    // list-4 P2L beside the M2M / M2L chain)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev[2] = {nullptr, nullptr};
+    bool graph_split = true;   // capture the branches in parallel
     cudaGraph_t g32 = nullptr;
     cudaGraphExec_t g32_exec = nullptr;
     int g32_kernels = 0;
@@ -230,6 +235,9 @@ struct Fmm::Impl {
         if (g32_exec) cudaGraphExecDestroy(g32_exec);
         if (g32) cudaGraphDestroy(g32);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (side) cudaStreamDestroy(side);
+        for (auto &ev : fork_ev)
+            if (ev) cudaEventDestroy(ev);
     }
 
     DevTree dt() const;
@@ -253,6 +261,11 @@ struct Fmm::Impl {
     // the FP32 operator at the nodes from segment values already in
     // sbar32 (single) or mbar32
     cudaError_t nodes32_from_segments(double *y, bool single, cudaStream_t st);
+    // the single layer of the inner operator with the list-4 P2L as a branch
+    // beside P2M -> M2M -> M2L; fork: the branch on side (while capturing
+    // the graph), else everything on st in the same order
+    bool split_ok() const;
+    cudaError_t nodes32_split(double *y, cudaStream_t st, bool fork);
     evalnodes::NodeArgs<float> node_args32(double *y, bool single) const;
     cudaError_t render_tiles32(int n_tiles, void *rgb, int rgb_dtype,
                                unsigned char *rgb8, const double *sb64, const double *mb64,

@@ -242,8 +242,9 @@ static __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(const int4 *_
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(32));
 }
 
-// Lout[cell][c] = sum over the cell's list-2 entries e, in list order, of
-// Y[e][c] + (coefficient 0) -log(w_cell) Re Mt_0 of the source.  One warp
+// Lout[cell][c] += sum over the cell's list-2 entries e, in list order, of
+// Y[e][c] + (coefficient 0) -log(w_cell) Re Mt_0 of the source (Lout holds
+// zero or the cell's list-4 P2L terms).  One warp
 // per cell, lane j holds real component j of the 2 P1.
 constexpr int kTcReduceWarps = 8;
 static __global__ void __launch_bounds__(32 * kTcReduceWarps) m2l_tc_reduce_kernel(TreeView<float> t,
@@ -285,9 +286,9 @@ static __global__ void __launch_bounds__(32 * kTcReduceWarps) m2l_tc_reduce_kern
         }
     if (lane < n2) {
         float *o = reinterpret_cast<float *>(Lout) + (size_t)cell * 3 * n2 + lane;
-        o[0] = acc[0];
-        o[n2] = acc[1];
-        o[2 * n2] = acc[2];
+        o[0] += acc[0];
+        o[n2] += acc[1];
+        o[2 * n2] += acc[2];
     }
 }
 
