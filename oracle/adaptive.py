@@ -58,13 +58,18 @@ def panel_lengths(disc: O.Discretisation) -> np.ndarray:
     return (chord * disc.seg_w).reshape(disc.n_panels, disc.nseg).sum(axis=1)
 
 
-def subdivide(drawing, disc: O.Discretisation, sigma: np.ndarray, eps_coef: float, eps_len: float):
+def subdivide(drawing, disc: O.Discretisation, sigma: np.ndarray, eps_coef: float, eps_len: float,
+              mask=None):
     """Alg. 5: returns (refined drawing, split flags per old panel, pmap)
-    with pmap[new panel] = (old panel, 0 kept / 1 left half / 2 right half)."""
+    with pmap[new panel] = (old panel, 0 kept / 1 left half / 2 right half).
+    mask: panels that may split (Sec. 6.4: those within the viewport); all
+    when None."""
     import copy
     top = top_coefficient(disc, sigma)
     length = panel_lengths(disc)
     split = (top > eps_coef) & (length >= eps_len)
+    if mask is not None:
+        split &= np.asarray(mask, bool)
     ptr, start = drawing.panel_ptr, drawing.panel_start
     new_ptr = [0]
     new_start, pmap = [], []
