@@ -16,7 +16,8 @@ then renders.  Readings taken here:
   * a panel meets the viewport when the bounding box of its solve polyline
     meets the viewport's closed rectangle;
   * only panels that meet the viewport may split; epsilon_1 = eps_len_px
-    times the pixel size, the larger side of a pixel;
+    times the pixel size, the larger side of a pixel; eps_coef = 0 turns the
+    subdivision off;
   * the length in the e rule is the panel's arc length in units of
     ``unit`` (default 1/512 of the unit canvas, the paper's 512-pixel
     images), rounded up: e_p = ceil(L_p / (10 unit)) + s;
@@ -75,7 +76,7 @@ def view_update(drawing, sigma, viewport, width: int, height: int, eps_coef: flo
     h = pixel_size(viewport, width, height)
     resolve = np.zeros(disc.n_panels, bool)
     rounds = n_split = 0
-    for _ in range(max_rounds):
+    for _ in range(max_rounds if eps_coef > 0 else 0):   # eps_coef = 0: no subdivision
         m = meets_viewport(disc, viewport)
         d2, split, pmap = A.subdivide(d, disc, sig, eps_coef, eps_len_px * h, mask=m)
         if not split.any():
