@@ -410,6 +410,60 @@ typedef struct {
  * dc_build_tree.  stats may be NULL. */
 dc_status dc_subdivide(dc_ctx *ctx, const dc_subdivide_options *opt, dc_subdivide_stats *stats);
 
+/* ------------------------------------------------------------------------
+ * Viewport update (Sec. 6.2, 6.4; Alg. 9)
+ * --------------------------------------------------------------------- */
+typedef struct {
+    double eps_coef;       /* epsilon_2 of Alg. 5 (0 = no subdivision)        */
+    double eps_len_px;     /* epsilon_1 of Alg. 5 in pixels of the viewport:
+                              panels shorter than this many pixel sizes (the
+                              larger side of a pixel) are not split          */
+    double len_unit;       /* unit of the curve length in the e rule,
+                              e = ceil(length / (10 len_unit)) + s per panel
+                              (0 = 1/512, a pixel of a 512-pixel image of the
+                              unit square)                                   */
+    int resolve;           /* dc_resolve_mode of each round                   */
+    int max_rounds;        /* rounds of subdivide + re-solve (0 = 4)          */
+    double label_ratio;    /* the 0.9 of Eq. 41 (0 = 0.9), in [0, 1)          */
+} dc_view_options;
+
+typedef struct {
+    int rounds;            /* rounds that split panels                        */
+    int n_split;           /* panels split over all rounds                    */
+    int n_resolve_panels;  /* panels re-solved in the last round              */
+    int n_fixed;           /* labels of Sec. 6.4 on the final panels: outside */
+    int n_interpolating;   /* ... meeting the viewport, density interpolated  */
+    int n_resolving;       /* ... re-solved in the last round                 */
+    int e;                 /* evaluation segments per panel                   */
+    long long n_eval_segments;
+    int converged;         /* 1 if every re-solve converged                   */
+    double ms_subdivide, ms_build, ms_total;   /* host wall time              */
+} dc_view_stats;
+
+/* Prepares the rendering of a viewport (Alg. 9 after the initial solve):
+ *  1. rounds of Alg. 5 restricted to the panels that meet the viewport
+ *     (the bounding box of a panel's solve polyline meets the viewport's
+ *     closed rectangle), with epsilon_1 = eps_len_px pixel sizes, each
+ *     followed by the re-solve of dc_subdivide (resolve mode), until a
+ *     round splits nothing or max_rounds;
+ *  2. labels (Sec. 6.4): fixed = panels outside the viewport, re-solving =
+ *     panels re-solved in the last round, interpolating = the others;
+ *  3. the evaluation polyline (Sec. 6.2): e = ceil(L / (10 len_unit)) + s
+ *     segments for every panel, the largest over the panels that meet the
+ *     viewport (s when none does), placed at equal arc length on each panel
+ *     like the solve's; the densities move to it by the interpolation
+ *     Lambda_e from the same nodes (no re-solve).
+ * dc_render_viewport then renders on that polyline (any viewport) until the
+ * panels or densities change (dc_build_tree, dc_solve_density,
+ * dc_solve_mixed, dc_set_density, dc_subdivide) or dc_view_reset;
+ * dc_eval_points stays on the solve polyline.  Needs a density
+ * (DC_ERR_STATE); DC_ERR_ARG for bad options or when e would exceed 4096;
+ * errors of dc_subdivide and dc_build_tree.  stats may be NULL. */
+dc_status dc_view_update(dc_ctx *ctx, const dc_viewport *vp, const dc_view_options *opt, dc_view_stats *stats);
+
+/* Renders on the solve polyline again (drops the view of dc_view_update). */
+dc_status dc_view_reset(dc_ctx *ctx);
+
 /* The current panels (after dc_subdivide, the refined ones), host outputs
  * in dc_build_tree's format: panel_ptr [n_curves + 1], panel_start
  * [panel_ptr[n_curves]] (either may be NULL; sizes from dc_get_sizes). */

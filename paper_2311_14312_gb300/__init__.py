@@ -82,6 +82,18 @@ class dc_subdivide_stats(ctypes.Structure):
                 ("ms_label", ctypes.c_double), ("ms_solve", ctypes.c_double)]
 
 
+class dc_view_options(ctypes.Structure):
+    _fields_ = [("eps_coef", ctypes.c_double), ("eps_len_px", ctypes.c_double), ("len_unit", ctypes.c_double),
+                ("resolve", ctypes.c_int), ("max_rounds", ctypes.c_int), ("label_ratio", ctypes.c_double)]
+
+
+class dc_view_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int), ("n_split", ctypes.c_int), ("n_resolve_panels", ctypes.c_int),
+                ("n_fixed", ctypes.c_int), ("n_interpolating", ctypes.c_int), ("n_resolving", ctypes.c_int),
+                ("e", ctypes.c_int), ("n_eval_segments", ctypes.c_longlong), ("converged", ctypes.c_int),
+                ("ms_subdivide", ctypes.c_double), ("ms_build", ctypes.c_double), ("ms_total", ctypes.c_double)]
+
+
 class dc_autotune_row(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int), ("p_inner", ctypes.c_int), ("eval_tile", ctypes.c_int),
                 ("ms", ctypes.c_double), ("max_err", ctypes.c_double), ("converged", ctypes.c_int)]
@@ -109,7 +121,7 @@ EXPORTS = ["dc_default_options", "dc_create", "dc_destroy", "dc_build_tree", "dc
            "dc_aux_panel_features", "dc_aux_set_warm_start_model", "dc_aux_apply_operator", "dc_aux_precond_info",
            "dc_aux_build_timings", "dc_aux_test_skip_mma_tile", "dc_aux_fp32_peak",
            "dc_aux_time_inner_m2l", "dc_subdivide", "dc_get_panels", "dc_aux_subdivision_info",
-           "dc_aux_adaptive_panels", "dc_autotune", "dc_solve_mixed"]
+           "dc_aux_adaptive_panels", "dc_autotune", "dc_solve_mixed", "dc_view_update", "dc_view_reset"]
 
 
 def _load():
@@ -160,6 +172,9 @@ def _load():
     lib.dc_aux_time_inner_m2l.argtypes = [P, I, P]
     lib.dc_subdivide.argtypes = [P, ctypes.POINTER(dc_subdivide_options), ctypes.POINTER(dc_subdivide_stats)]
     lib.dc_get_panels.argtypes = [P, P, P]
+    lib.dc_view_update.argtypes = [P, ctypes.POINTER(dc_viewport), ctypes.POINTER(dc_view_options),
+                                   ctypes.POINTER(dc_view_stats)]
+    lib.dc_view_reset.argtypes = [P]
     lib.dc_aux_subdivision_info.argtypes = [P, P, P, P]
     lib.dc_aux_adaptive_panels.argtypes = [I, P, D, I, I, D, I, P, P, P]
     lib.dc_autotune.argtypes = [P, I, ctypes.POINTER(dc_viewport), I, P, I, P, I, P, D, I,
@@ -365,6 +380,22 @@ class Context:
         st = dc_subdivide_stats()
         self._check(_get_lib().dc_subdivide(self._h, ctypes.byref(o), ctypes.byref(st)))
         return st
+
+    def view_update(self, viewport, eps_coef=0.0, eps_len_px=0.0, len_unit=0.0, resolve="local", max_rounds=0,
+                    label_ratio=0.0) -> dc_view_stats:
+        """dc_view_update: Alg. 9 for the viewport (x0, y0, x1, y1, width,
+        height): viewport-masked subdivision and re-solve, then the
+        evaluation polyline of e = length / 10 + s segments per panel that
+        the next renders use."""
+        v = dc_viewport(*[float(x) for x in viewport[:4]], int(viewport[4]), int(viewport[5]))
+        o = dc_view_options(float(eps_coef), float(eps_len_px), float(len_unit), RESOLVE.get(resolve, resolve),
+                            int(max_rounds), float(label_ratio))
+        st = dc_view_stats()
+        self._check(_get_lib().dc_view_update(self._h, ctypes.byref(v), ctypes.byref(o), ctypes.byref(st)))
+        return st
+
+    def view_reset(self):
+        self._check(_get_lib().dc_view_reset(self._h))
 
     def panels(self):
         """dc_get_panels: (panel_ptr, panel_start) of the current panels."""

@@ -60,10 +60,23 @@ struct dc_ctx {
     DevBuf<unsigned char> ad_mask;
     std::vector<double> last_top;
     std::vector<unsigned char> last_split, last_resolve;
-    ~dc_ctx() {
-        if (gw) dc::gmres_work_destroy(gw);
-    }
+    // the viewport's evaluation discretisation (Sec. 6.2, 6.4): a render-only
+    // context on the same panels with e segments each, used by
+    // dc_render_viewport while view_valid (cleared by every change of the
+    // panels or the densities)
+    dc_ctx *view = nullptr;
+    bool view_valid = false;
+    bool render_only = false;      // this context is a view: no solve structures
+    ~dc_ctx();
 };
+
+dc_ctx::~dc_ctx() {
+    if (view) {
+        cudaStreamSynchronize(view->stream);
+        delete view;
+    }
+    if (gw) dc::gmres_work_destroy(gw);
+}
 
 namespace {
 
@@ -382,6 +395,7 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
     if (!ctx) return DC_ERR_ARG;
     ctx->err.clear();
     ctx->state = 0;
+    ctx->view_valid = false;
     ctx->seg_density_valid = false;
     std::string msg;
     for (double &v : ctx->build_ms) v = 0.0;
@@ -460,13 +474,16 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
     ctx->AF.release();
     ctx->fmm.reset();
     if (ctx->opt.form == DC_FORM_DENSE64) {
-        size_t nn = size_t(D.N) * D.N;
-        DC_CK(ctx, ctx->AG.alloc(nn), "alloc dense A_G");
-        DC_CK(ctx, ctx->AF.alloc(nn), "alloc dense A_F");
-        DC_CK(ctx, dc::launch_dense_assemble(D, ctx->AG.ptr, ctx->AF.ptr, s), "dense assembly");
+        if (!ctx->render_only) {
+            size_t nn = size_t(D.N) * D.N;
+            DC_CK(ctx, ctx->AG.alloc(nn), "alloc dense A_G");
+            DC_CK(ctx, ctx->AF.alloc(nn), "alloc dense A_F");
+            DC_CK(ctx, dc::launch_dense_assemble(D, ctx->AG.ptr, ctx->AF.ptr, s), "dense assembly");
+        }
     } else {
         ctx->fmm.reset(new (std::nothrow) dc::Fmm());
         if (!ctx->fmm) return fail(ctx, DC_ERR_OOM, "build_tree: host allocation failed");
+        ctx->fmm->set_render_only(ctx->render_only);
         st = ctx->fmm->build(ctx->opt, G, D, s, msg);
         if (st != DC_OK) {
             ctx->fmm.reset();
@@ -475,6 +492,11 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
         ctx->fmm->build_timings(ctx->build_ms + 2);
     }
     t_prev = std::chrono::steady_clock::now();
+    if (ctx->render_only) {   // a view renders: no solve structures
+        DC_CK(ctx, cudaStreamSynchronize(s), "build_tree");
+        ctx->state = 1;
+        return DC_OK;
+    }
     DC_CK(ctx, ctx->pfeat.build(G, s), "panel features");
     lap(8);
     ctx->warm_a1_valid = false;
@@ -560,6 +582,8 @@ dc_status dc_solve_density(dc_ctx *ctx, const double *x0, dc_solve_stats *stats)
     if (!ctx) return DC_ERR_ARG;
     ctx->err.clear();
     if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "solve_density: call build_tree first");
+    if (ctx->render_only) return fail(ctx, DC_ERR_STATE, "solve_density: a view context renders only");
+    ctx->view_valid = false;
     if (ctx->opt.x0_mode == DC_X0_USER && !x0)
         return fail(ctx, DC_ERR_ARG, "solve_density: x0_mode is DC_X0_USER but x0 is NULL");
     if (ctx->opt.x0_mode == DC_X0_LEARNED && ctx->warm_hidden <= 0)
@@ -659,6 +683,7 @@ dc_status dc_set_density(dc_ctx *ctx, const double *sigma_in) {
     ctx->err.clear();
     if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "set_density: call build_tree first");
     if (!sigma_in) return fail(ctx, DC_ERR_ARG, "set_density: NULL input");
+    ctx->view_valid = false;
     size_t n3 = size_t(3) * ctx->dg.N;
     for (size_t i = 0; i < n3; ++i)
         if (!std::isfinite(sigma_in[i]))
@@ -754,6 +779,11 @@ dc_status dc_render_viewport(dc_ctx *ctx, int n_vp, const dc_viewport *vps, void
     }
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (total == 0) return DC_OK;
+    if (ctx->view && ctx->view_valid) {   // the viewport's evaluation polyline (Sec. 6.2)
+        dc_status vs = dc_render_viewport(ctx->view, n_vp, vps, rgb, rgb_dtype, rgb8, out_where, stats);
+        if (vs != DC_OK) return fail(ctx, vs, ctx->view->err);
+        return DC_OK;
+    }
     cudaStream_t s = ctx->stream;
     dc_status st = ensure_segment_density(ctx);
     if (st != DC_OK) return st;
@@ -1088,7 +1118,10 @@ dc_status dc_aux_subdivision_info(dc_ctx *ctx, double *top_old, unsigned char *s
     return DC_OK;
 }
 
-dc_status dc_subdivide(dc_ctx *ctx, const dc_subdivide_options *o, dc_subdivide_stats *stats) {
+// dc_subdivide with an optional mask: only panels p with mask[p] != 0 may
+// split (nullptr: all).
+dc_status subdivide_impl(dc_ctx *ctx, const dc_subdivide_options *o, const unsigned char *mask,
+                         dc_subdivide_stats *stats) {
     using clk = std::chrono::steady_clock;
     auto ms_since = [](clk::time_point a) { return std::chrono::duration<double, std::milli>(clk::now() - a).count(); };
     if (!ctx) return DC_ERR_ARG;
@@ -1125,7 +1158,7 @@ dc_status dc_subdivide(dc_ctx *ctx, const dc_subdivide_options *o, dc_subdivide_
             const double *e = &ctx->geo.seg_xy[4 * ((size_t)p * sp + k)];
             len += std::hypot(e[2] - e[0], e[3] - e[1]) * ctx->geo.seg_w[(size_t)p * sp + k];
         }
-        if (top[p] > o->eps_coef && len >= o->eps_len) {
+        if (top[p] > o->eps_coef && len >= o->eps_len && (!mask || mask[p])) {
             split[p] = 1;
             ++n_split;
         }
@@ -1307,6 +1340,148 @@ dc_status dc_subdivide(dc_ctx *ctx, const dc_subdivide_options *o, dc_subdivide_
     return DC_OK;
 }
 
+dc_status dc_subdivide(dc_ctx *ctx, const dc_subdivide_options *o, dc_subdivide_stats *stats) {
+    if (ctx && ctx->render_only) return fail(ctx, DC_ERR_STATE, "subdivide: a view context renders only");
+    return subdivide_impl(ctx, o, nullptr, stats);
+}
+
+// ------------------------------------------------ viewport update (6.4) --
+dc_status dc_view_update(dc_ctx *ctx, const dc_viewport *vp, const dc_view_options *o, dc_view_stats *stats) {
+    using clk = std::chrono::steady_clock;
+    auto ms_since = [](clk::time_point a) { return std::chrono::duration<double, std::milli>(clk::now() - a).count(); };
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (!vp || !o) return fail(ctx, DC_ERR_ARG, "view_update: NULL viewport or options");
+    if (ctx->render_only) return fail(ctx, DC_ERR_STATE, "view_update: a view context renders only");
+    if (ctx->state < 2) return fail(ctx, DC_ERR_STATE, "view_update: needs a density (solve_density or set_density)");
+    if (!(vp->width > 0 && vp->height > 0) || !std::isfinite(vp->x0) || !std::isfinite(vp->x1) ||
+        !std::isfinite(vp->y0) || !std::isfinite(vp->y1) || !(vp->x1 > vp->x0) || !(vp->y1 > vp->y0))
+        return fail(ctx, DC_ERR_ARG, "view_update: need a viewport with x1 > x0, y1 > y0 and pixels");
+    if (!(o->eps_coef >= 0.0) || !std::isfinite(o->eps_coef) || !(o->eps_len_px >= 0.0) ||
+        !std::isfinite(o->eps_len_px) || !(o->len_unit >= 0.0) || !std::isfinite(o->len_unit) || o->max_rounds < 0 ||
+        o->max_rounds > 64 || o->resolve < DC_RESOLVE_LOCAL || o->resolve > DC_RESOLVE_NONE ||
+        !(o->label_ratio >= 0.0) || !(o->label_ratio < 1.0))
+        return fail(ctx, DC_ERR_ARG, "view_update: need eps_coef, eps_len_px, len_unit >= 0, max_rounds in [0, 64], "
+                                     "a dc_resolve_mode and 0 <= label_ratio < 1");
+    const double unit = o->len_unit > 0.0 ? o->len_unit : 1.0 / 512.0;
+    const int max_rounds = o->max_rounds > 0 ? o->max_rounds : 4;
+    const double px = std::max((vp->x1 - vp->x0) / vp->width, (vp->y1 - vp->y0) / vp->height);
+    dc_view_stats S;
+    std::memset(&S, 0, sizeof(S));
+    S.converged = 1;
+    const auto t0 = clk::now();
+    ctx->view_valid = false;
+    // panels whose solve polyline's box meets the viewport's closed rectangle
+    auto meets = [&](std::vector<unsigned char> &m) {
+        const int P = ctx->dg.n_panels, sp = ctx->dg.s;
+        m.assign(P, 0);
+        for (int p = 0; p < P; ++p) {
+            double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
+            for (int k = 0; k < sp; ++k) {
+                const double *e = &ctx->geo.seg_xy[4 * ((size_t)p * sp + k)];
+                for (int q = 0; q < 2; ++q) {
+                    lo[0] = std::min(lo[0], e[2 * q]);
+                    hi[0] = std::max(hi[0], e[2 * q]);
+                    lo[1] = std::min(lo[1], e[2 * q + 1]);
+                    hi[1] = std::max(hi[1], e[2 * q + 1]);
+                }
+            }
+            m[p] = hi[0] >= vp->x0 && lo[0] <= vp->x1 && hi[1] >= vp->y0 && lo[1] <= vp->y1;
+        }
+    };
+    // Alg. 9: subdivide (Alg. 5, epsilon_1 in pixels, panels in the viewport
+    // only) and re-solve while panels split
+    std::vector<unsigned char> m, res_last;
+    if (o->eps_coef > 0.0) {
+        for (int r = 0; r < max_rounds; ++r) {
+            meets(m);
+            dc_subdivide_options so;
+            std::memset(&so, 0, sizeof(so));
+            so.eps_coef = o->eps_coef;
+            so.eps_len = o->eps_len_px * px;
+            so.resolve = o->resolve;
+            so.label_ratio = o->label_ratio;
+            dc_subdivide_stats ss;
+            dc_status st = subdivide_impl(ctx, &so, m.data(), &ss);
+            if (st != DC_OK) return st;
+            if (ss.n_split == 0) break;
+            ++S.rounds;
+            S.n_split += ss.n_split;
+            S.n_resolve_panels = ss.n_resolve_panels;
+            if (!ss.converged) S.converged = 0;
+            res_last = ctx->last_resolve;
+        }
+    }
+    S.ms_subdivide = ms_since(t0);
+    // labels of Sec. 6.4 and the e rule of Sec. 6.2 on the final panels
+    meets(m);
+    const int P = ctx->dg.n_panels, sp = ctx->dg.s;
+    long long e = sp;
+    for (int p = 0; p < P; ++p) {
+        const bool re = (int)res_last.size() == P && res_last[p];
+        if (re) ++S.n_resolving;
+        else if (m[p]) ++S.n_interpolating;
+        else ++S.n_fixed;
+        if (!m[p]) continue;
+        double len = 0.0;
+        for (int k = 0; k < sp; ++k) {
+            const double *q = &ctx->geo.seg_xy[4 * ((size_t)p * sp + k)];
+            len += std::hypot(q[2] - q[0], q[3] - q[1]) * ctx->geo.seg_w[(size_t)p * sp + k];
+        }
+        const double add = std::ceil(len / (10.0 * unit));
+        if (add > 4096.0) return fail(ctx, DC_ERR_ARG, "view_update: the e rule asks for more than 4096 segments per panel");
+        e = std::max(e, (long long)add + sp);
+    }
+    if (e > 4096) return fail(ctx, DC_ERR_ARG, "view_update: the e rule asks for more than 4096 segments per panel");
+    S.e = int(e);
+    S.n_eval_segments = (long long)P * e;
+    // the evaluation discretisation: a render-only context on the same
+    // panels with e segments each, the same nodes and densities
+    const auto t1 = clk::now();
+    if (ctx->view && ctx->view->opt.s_per_panel != int(e)) {
+        cudaStreamSynchronize(ctx->view->stream);
+        delete ctx->view;
+        ctx->view = nullptr;
+    }
+    if (!ctx->view) {
+        dc_options vo = ctx->opt;
+        vo.s_per_panel = int(e);
+        vo.stream = ctx->stream;
+        dc_ctx *v = nullptr;
+        dc_status st = dc_create(&v, &vo);
+        if (st != DC_OK) return fail(ctx, st, std::string("view_update: ") + dc_last_error(nullptr));
+        v->render_only = true;
+        ctx->view = v;
+    }
+    dc_ctx *v = ctx->view;
+    {
+        dc_status st = dc_build_tree(v, ctx->in_ncurves, ctx->in_ctrl.data(), ctx->in_ptr.data(),
+                                     ctx->in_start.data(), ctx->in_col.data());
+        if (st != DC_OK) return fail(ctx, st, std::string("view_update: ") + v->err);
+    }
+    const size_t n3 = size_t(3) * ctx->dg.N;
+    if (v->dg.N != ctx->dg.N) return fail(ctx, DC_ERR_STATE, "view_update: node counts differ");
+    DC_CK(ctx, cudaMemcpyAsync(v->sigma.ptr, ctx->sigma.ptr, n3 * sizeof(double), cudaMemcpyDeviceToDevice,
+                               ctx->stream), "view_update");
+    DC_CK(ctx, cudaMemcpyAsync(v->mu.ptr, ctx->mu.ptr, n3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream),
+          "view_update");
+    DC_CK(ctx, cudaStreamSynchronize(ctx->stream), "view_update");
+    v->seg_density_valid = false;
+    v->state = 2;
+    ctx->view_valid = true;
+    S.ms_build = ms_since(t1);
+    S.ms_total = ms_since(t0);
+    if (stats) *stats = S;
+    return DC_OK;
+}
+
+dc_status dc_view_reset(dc_ctx *ctx) {
+    if (!ctx) return DC_ERR_ARG;
+    ctx->err.clear();
+    ctx->view_valid = false;
+    return DC_OK;
+}
+
 dc_status dc_aux_adaptive_panels(int n_curves, const double *ctrl, double ratio, int max_level, int min_panels,
                                  double max_len, int capacity, int *panel_ptr, double *panel_start, int *n_panels) {
     if (n_curves < 1 || !ctrl || !panel_ptr || !n_panels || capacity < 0 || (capacity > 0 && !panel_start) ||
@@ -1451,6 +1626,8 @@ dc_status dc_solve_mixed(dc_ctx *ctx, const unsigned char *neumann, const double
     if (!ctx) return DC_ERR_ARG;
     ctx->err.clear();
     if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "solve_mixed: call build_tree first");
+    if (ctx->render_only) return fail(ctx, DC_ERR_STATE, "solve_mixed: a view context renders only");
+    ctx->view_valid = false;
     if (!neumann || !psi_star) return fail(ctx, DC_ERR_ARG, "solve_mixed: need the Neumann panels and psi");
     const int N = ctx->dg.N, g = ctx->dg.g, P = ctx->dg.n_panels;
     const size_t n3 = size_t(3) * N;

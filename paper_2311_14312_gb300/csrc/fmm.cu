@@ -1126,7 +1126,7 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     }
     // two-level preconditioner (panel blocks + coarse space of panel constants)
     phase(1);   // schedules, node items, uploads
-    if ((e = I.coarse.build(G, D, st, opt.coarse_max)) != cudaSuccess) {
+    if (!I.render_only && (e = I.coarse.build(G, D, st, opt.coarse_max)) != cudaSuccess) {
         err = std::string("fmm coarse preconditioner: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
     }
@@ -1148,7 +1148,7 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
     }
     phase(3);   // stored P2M / P2L rows
-    if ((e = I.build_near(st)) != cudaSuccess) {
+    if (!I.render_only && (e = I.build_near(st)) != cudaSuccess) {
         err = std::string("near-field coefficients: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
     }
@@ -1337,6 +1337,8 @@ cudaError_t Fmm::time_inner_m2l(int reps, cudaStream_t st, double out[6]) {
 }
 
 void Fmm::set_eval_tile(int t) { impl_->opt.eval_tile = t; }
+
+void Fmm::set_render_only(bool on) { impl_->render_only = on; }
 
 cudaError_t Fmm::set_mma_skip_tile(int tile, cudaStream_t st) {
     Impl &I = *impl_;

@@ -32,6 +32,10 @@ public:
     // MMA for it, so its bounded wait runs out (-1 = off).
     cudaError_t set_mma_skip_tile(int tile, cudaStream_t st);
     void set_eval_tile(int t);   // pixel tile shape of the FP32 render (options.eval_tile)
+    // A render-only build (a viewport's evaluation polyline) skips the
+    // solve's structures: the two-level preconditioner and the node
+    // near-field coefficients.  Set before build().
+    void set_render_only(bool on);
     // y = B x with B the panels' inverse self-interaction blocks of G_H (the
     // first level of the two-level preconditioner alone).
     cudaError_t apply_block_jacobi(const double *x, double *y, cudaStream_t st);

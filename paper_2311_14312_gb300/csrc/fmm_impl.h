@@ -214,6 +214,7 @@ struct Fmm::Impl {
     cudaStream_t side = nullptr;
     cudaEvent_t fork_ev[2] = {nullptr, nullptr};
     bool graph_split = true;   // capture the branches in parallel
+    bool render_only = false;  // no preconditioner, no node near-field coefficients
     cudaGraph_t g32 = nullptr;
     cudaGraphExec_t g32_exec = nullptr;
     int g32_kernels = 0;

@@ -56,6 +56,8 @@ int main(void){
         offsetof(dc_options, adapt_max_len), offsetof(dc_options, eval_tile));
  printf("%zu %zu %zu\n", offsetof(dc_options, aa_levels), offsetof(dc_render_stats, aa_pixels),
         offsetof(dc_render_stats, ms_aa));
+ printf("%zu %zu %zu %zu\n", sizeof(dc_view_options), sizeof(dc_view_stats), offsetof(dc_view_options, label_ratio),
+        offsetof(dc_view_stats, ms_total));
  return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
@@ -83,6 +85,9 @@ int main(void){
     aa = list(map(int, lines[3].split()))
     assert aa == [P.dc_options.aa_levels.offset, P.dc_render_stats.aa_pixels.offset,
                   P.dc_render_stats.ms_aa.offset]
+    vw = list(map(int, lines[4].split()))
+    assert vw == [ctypes.sizeof(P.dc_view_options), ctypes.sizeof(P.dc_view_stats),
+                  P.dc_view_options.label_ratio.offset, P.dc_view_stats.ms_total.offset]
 
 
 def test_defaults_and_status_strings(dcmod):
