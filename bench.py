@@ -277,6 +277,53 @@ def run_reference(args):
 
 
 # -------------------------------------------------------------- GPU leg --
+def next_rows(P, d, ctx, vp, npx):
+    """The beyond-the-step rows on the bench drawing, after the timed region
+    (host wall times from the library's stats, render times by CUDA events):
+    f3 anti-aliasing of the 2048^2 render (m = 2), f2 the viewport update of
+    a zoom-8 viewport (e rule, no subdivision) and its render, f1 one round
+    of adaptive subdivision with the local re-solve (epsilon_2 at the 99.5th
+    percentile of the test values)."""
+    import numpy as np
+    import torch
+
+    out = {}
+    sig = ctx.get_density()
+    rgb = torch.empty((npx, 3), dtype=torch.float32, device="cuda")
+    rgb8 = torch.empty((npx, 3), dtype=torch.uint8, device="cuda")
+    # f3
+    actx = P.Context(form="fmm32", g=d.g, s_per_panel=d.s_per_panel, aa_levels=2, **FORM_OPTS)
+    actx.build_drawing(d)
+    actx.set_density(sig)
+    actx.render_viewport(vp, rgb, rgb8)
+    rs = actx.render_viewport(vp, rgb, rgb8, stats=True)
+    out["f3_antialias"] = {"levels": 2, "ms": rs.ms, "ms_aa": rs.ms_aa, "refined_pixels": rs.aa_pixels,
+                           "samples": rs.aa_samples}
+    actx.close()
+    # f2
+    c = d.ctrl[0].mean(axis=0)
+    zv = (float(c[0] - 1 / 16), float(c[1] - 1 / 16), float(c[0] + 1 / 16), float(c[1] + 1 / 16), WIDTH, HEIGHT)
+    vs = ctx.view_update(zv, eps_coef=0.0)
+    ctx.render_viewport([zv], rgb, rgb8)
+    rv = ctx.render_viewport([zv], rgb, rgb8, stats=True)
+    ctx.view_reset()
+    rp = ctx.render_viewport([zv], rgb, rgb8, stats=True)
+    out["f2_view"] = {"zoom": 8, "e": vs.e, "s": d.s_per_panel, "labels_fixed_interp_resolve":
+                      [vs.n_fixed, vs.n_interpolating, vs.n_resolving], "ms_build": vs.ms_build,
+                      "render_ms": rv.ms, "render_ms_solve_polyline": rp.ms}
+    # f1
+    n0 = ctx.sizes().n_panels
+    ctx.subdivide(1e300)
+    top, _, _ = ctx.subdivision_info(n0)
+    eps = float(np.percentile(top, 99.5))
+    ss = ctx.subdivide(eps, 0.0, "local")
+    out["f1_subdivide"] = {"eps_coef": eps, "n_split": ss.n_split, "panels": [ss.n_panels_before, ss.n_panels_after],
+                           "resolved_panels": ss.n_resolve_panels, "iters": list(ss.iters),
+                           "ms_test": ss.ms_test, "ms_rebuild": ss.ms_rebuild, "ms_label": ss.ms_label,
+                           "ms_solve": ss.ms_solve}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -410,6 +457,8 @@ def run_ours(args):
                  "band_pixels": int(band.sum())}
         pctx.close()
 
+    nxt = next_rows(P, d, ctx, vp, npx) if rank == 0 else None
+
     cpu = None
     if rank == 0 and ws == 1:
         O, _, disc = _oracle_setup()
@@ -463,6 +512,7 @@ def run_ours(args):
                     "includes": "build_tree from host arrays + solve + render to pinned host"},
             "gpu_launches": launches,
             "clocks": clk,
+            "next_rows": nxt,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
