@@ -55,8 +55,12 @@ __device__ __forceinline__ float mono_lg2(float2 q, float2 c) {
 __device__ __forceinline__ float mono32(float2 q, float2 c) { return kMonoLog2 * mono_lg2(q, c); }
 
 // corr[e][m] = (G_H 1_j)(q_{i,m}) - l_j mono32(q_{i,m}, c_j) for the near pair
-// e = (i, j): the exact single layer of panel j with unit density (Lambda
-// reproduces constants) at the nodes of panel i, minus its monopole.
+// e = (i, j): the single layer of panel j with unit density (Lambda
+// reproduces constants) at the nodes of panel i, minus its monopole.  A
+// panel's own pairs (i = j, where the integrals are singular) run in FP64;
+// the others, whose terms are smooth, in FP32 on coordinates taken relative
+// to the node in FP64 (the same closed form, App. D): the FP64 logarithms
+// and arctangents cost 64 times as much here.
 __global__ void near_pairs_kernel(const int2 *__restrict__ pairs, const double *__restrict__ seg,
                                   const double *__restrict__ segw, const double *__restrict__ nxy,
                                   const int *__restrict__ nseg, const int *__restrict__ nseg2,
@@ -68,15 +72,34 @@ __global__ void near_pairs_kernel(const int2 *__restrict__ pairs, const double *
     const int a = pr.x * g + m, j = pr.y;
     const double qx = nxy[2 * a], qy = nxy[2 * a + 1];
     const int own1 = nseg[a], own2 = nseg2[a];
-    double acc = 0.0;
+    if (pr.x == pr.y) {
+        double acc64 = 0.0;
+        for (int kk = 0; kk < s; ++kk) {
+            const int k = j * s + kk;
+            const double *q = seg + 4 * (size_t)k;
+            double G, F;
+            seg_gf_f64(qx, qy, q[0], q[1], q[2], q[3], segw[k], k == own1 || k == own2, G, F);
+            acc64 += G;
+        }
+        corr[(size_t)e * g + m] = acc64 - plen[j] * (double)mono32(q32[a], c32[j]);
+        return;
+    }
+    float acc = 0.f;
     for (int kk = 0; kk < s; ++kk) {
         const int k = j * s + kk;
         const double *q = seg + 4 * (size_t)k;
-        double G, F;
-        seg_gf_f64(qx, qy, q[0], q[1], q[2], q[3], segw[k], k == own1 || k == own2, G, F);
-        acc += G;
+        const float ax = (float)(q[0] - qx), ay = (float)(q[1] - qy);
+        const float bx = (float)(q[2] - qx), by = (float)(q[3] - qy);
+        const float dx = (float)(q[2] - q[0]), dy = (float)(q[3] - q[1]);
+        const float c2 = dx * dx + dy * dy, ic = rsqrtf(c2), c = c2 * ic;
+        const float cr = ax * by - ay * bx;
+        const float phi = (k == own1 || k == own2) ? 0.f : atan2f(cr, ax * bx + ay * by);
+        const float ra2 = ax * ax + ay * ay, rb2 = bx * bx + by * by;
+        const float la = ra2 > 0.f ? (ax * dx + ay * dy) * ic * logf(ra2) : 0.f;
+        const float lb = rb2 > 0.f ? (bx * dx + by * dy) * ic * logf(rb2) : 0.f;
+        acc += -(float)segw[k] * (float)kInv2Pi * (0.5f * (lb - la) - c + cr * ic * phi);
     }
-    corr[(size_t)e * g + m] = acc - plen[j] * (double)mono32(q32[a], c32[j]);
+    corr[(size_t)e * g + m] = (double)acc - plen[j] * (double)mono32(q32[a], c32[j]);
 }
 
 // Ac[i][j] = sum_m (l_j mono32(q_{i,m}, c_j) + corr), padded with the identity
@@ -189,29 +212,27 @@ __global__ void spread_agg_kernel(const double *__restrict__ y, const int *__res
 //    the pivot column by shuffles, with the same operations per element as
 //    the textbook in-place elimination)
 __global__ void gj_diag_kernel(float *__restrict__ A, int n, int k) {
-    static_assert(kGJ == 32, "one lane per column of the diagonal block");
-    const int t = threadIdx.x;          // column
-    float *D = A + (size_t)k * kGJ * n + k * kGJ;
-    float a[kGJ];
-#pragma unroll
-    for (int r = 0; r < kGJ; ++r) a[r] = D[(size_t)r * n + t];
-#pragma unroll
+    static_assert(kGJ == 32, "a 32 x 32 thread block on the diagonal block");
+    // thread (tx, ty) holds element (row ty, column tx); one pivot per step,
+    // the block exchanged through shared memory (32 steps of two barriers)
+    __shared__ float D[kGJ][kGJ + 1];
+    __shared__ float rp;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    float *B = A + (size_t)k * kGJ * n + k * kGJ;
+    D[ty][tx] = B[(size_t)ty * n + tx];
+    __syncthreads();
     for (int c = 0; c < kGJ; ++c) {
-        const float piv = __shfl_sync(0xffffffffu, a[c], c);
-        float f[kGJ];
-#pragma unroll
-        for (int r = 0; r < kGJ; ++r) f[r] = __shfl_sync(0xffffffffu, a[r], c);   // column c before the step
-        // row c scaled; column c of the inverse replaces column c
-        const float rc = (t == c) ? 1.f / piv : a[c] / piv;
-        a[c] = rc;
-#pragma unroll
-        for (int r = 0; r < kGJ; ++r) {
-            if (r == c) continue;
-            a[r] = (t == c) ? -f[r] / piv : a[r] - f[r] * rc;
-        }
+        if (tx == 0 && ty == 0) rp = 1.f / D[c][c];
+        __syncthreads();
+        const float r = rp, dcol = D[ty][c], drow = D[c][tx];
+        float v;
+        if (ty == c) v = (tx == c) ? r : drow * r;
+        else v = (tx == c) ? -dcol * r : D[ty][tx] - dcol * drow * r;
+        __syncthreads();
+        D[ty][tx] = v;
+        __syncthreads();
     }
-#pragma unroll
-    for (int r = 0; r < kGJ; ++r) D[(size_t)r * n + t] = a[r];
+    B[(size_t)ty * n + tx] = D[ty][tx];
 }
 
 // 2. A_kj <- A_kk A_kj for the columns j outside block k (one thread per column)
@@ -648,7 +669,7 @@ cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st
     const int nb = n_pad_ / kGJ;
     dim3 ug((n_pad_ + 63) / 64, (n_pad_ + 63) / 64);
     for (int k = 0; k < nb; ++k) {
-        gj_diag_kernel<<<1, kGJ, 0, st>>>(Ainv_.ptr, n_pad_, k);
+        gj_diag_kernel<<<1, dim3(kGJ, kGJ), 0, st>>>(Ainv_.ptr, n_pad_, k);
         gj_row_kernel<<<(n_pad_ + 127) / 128, 128, 0, st>>>(Ainv_.ptr, n_pad_, k);
         gj_update_kernel<<<ug, 256, 0, st>>>(Ainv_.ptr, n_pad_, k);
         gj_col_kernel<<<(n_pad_ + 127) / 128, 128, 0, st>>>(Ainv_.ptr, n_pad_, k);

@@ -14,7 +14,9 @@ the chosen FP32 form with order 24 and leaf size 64, solves it, then:
           (profilers can filter on them), the FP64 double layer 4 times,
           and prints the mean device time of each;
   solve   solves again inside the NVTX range "solve" and prints the solve
-          statistics, the preconditioner state and the tree sizes.
+          statistics, the preconditioner state and the tree sizes;
+  build   builds the drawing again `reps` times (the last inside the NVTX
+          range "build") and prints the wall time of each build phase.
 """
 from __future__ import annotations
 
@@ -52,7 +54,7 @@ def _time(fn, n):
 def main(argv=None):
     import torch
     ap = argparse.ArgumentParser(description="fixed workloads for profiling")
-    ap.add_argument("what", choices=["render", "matvec", "solve"])
+    ap.add_argument("what", choices=["render", "matvec", "solve", "build"])
     ap.add_argument("--size", type=int, default=512)
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--p-inner", type=int, default=0, help="options.p_inner (0 = default)")
@@ -61,6 +63,23 @@ def main(argv=None):
     ap.add_argument("--m2l-engine", type=int, default=0, help="options.m2l_engine (0 tensor cores, 1 CUDA cores)")
     a = ap.parse_args(argv)
     ctx, st = _context(a.p_inner, a.inner_tol, a.leaf_size, a.m2l_engine)
+    if a.what == "build":
+        from dc_synth import drawing_by_name
+        d = drawing_by_name("mixed200")
+        rows = []
+        for r in range(max(1, a.reps)):
+            last = r == max(1, a.reps) - 1
+            if last:
+                torch.cuda.nvtx.range_push("build")
+            ctx.build_drawing(d)
+            torch.cuda.synchronize()
+            if last:
+                torch.cuda.nvtx.range_pop()
+            rows.append(ctx.build_timings())
+        for k in rows[0]:
+            vals = [row[k] for row in rows]
+            print(f"{k:>15s}: " + " ".join(f"{v:8.2f}" for v in vals) + " ms")
+        return
     if a.what == "solve":      # a second solve, inside the NVTX range "solve": steady state
         torch.cuda.nvtx.range_push("solve")
         st = ctx.solve_density()
