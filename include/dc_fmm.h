@@ -461,6 +461,15 @@ typedef struct {
  * errors of dc_subdivide and dc_build_tree.  stats may be NULL. */
 dc_status dc_view_update(dc_ctx *ctx, const dc_viewport *vp, const dc_view_options *opt, dc_view_stats *stats);
 
+/* Auxiliary: the quadtree of the context (its segments clipped into pieces
+ * on the device, level by level) against the host construction over the
+ * same segments.  out[0] = 1 when cells, piece counts and piece segments are
+ * identical, out[1] = the largest difference of piece endpoints, out[2] =
+ * cells, out[3] = pieces, out[4] and out[5] = wall ms of the last build's
+ * clipping (device) and lists (host).  FMM forms after dc_build_tree
+ * (DC_ERR_STATE). */
+dc_status dc_aux_tree_compare(dc_ctx *ctx, double *out);
+
 /* Renders on the solve polyline again (drops the view of dc_view_update). */
 dc_status dc_view_reset(dc_ctx *ctx);
 

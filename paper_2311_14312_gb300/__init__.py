@@ -121,7 +121,8 @@ EXPORTS = ["dc_default_options", "dc_create", "dc_destroy", "dc_build_tree", "dc
            "dc_aux_panel_features", "dc_aux_set_warm_start_model", "dc_aux_apply_operator", "dc_aux_precond_info",
            "dc_aux_build_timings", "dc_aux_test_skip_mma_tile", "dc_aux_fp32_peak",
            "dc_aux_time_inner_m2l", "dc_subdivide", "dc_get_panels", "dc_aux_subdivision_info",
-           "dc_aux_adaptive_panels", "dc_autotune", "dc_solve_mixed", "dc_view_update", "dc_view_reset"]
+           "dc_aux_adaptive_panels", "dc_autotune", "dc_solve_mixed", "dc_view_update", "dc_view_reset",
+           "dc_aux_tree_compare"]
 
 
 def _load():
@@ -175,6 +176,7 @@ def _load():
     lib.dc_view_update.argtypes = [P, ctypes.POINTER(dc_viewport), ctypes.POINTER(dc_view_options),
                                    ctypes.POINTER(dc_view_stats)]
     lib.dc_view_reset.argtypes = [P]
+    lib.dc_aux_tree_compare.argtypes = [P, P]
     lib.dc_aux_subdivision_info.argtypes = [P, P, P, P]
     lib.dc_aux_adaptive_panels.argtypes = [I, P, D, I, I, D, I, P, P, P]
     lib.dc_autotune.argtypes = [P, I, ctypes.POINTER(dc_viewport), I, P, I, P, I, P, D, I,
@@ -393,6 +395,13 @@ class Context:
         st = dc_view_stats()
         self._check(_get_lib().dc_view_update(self._h, ctypes.byref(v), ctypes.byref(o), ctypes.byref(st)))
         return st
+
+    def tree_compare(self) -> dict:
+        """dc_aux_tree_compare: the device-built quadtree against the host build."""
+        out = np.zeros(6)
+        self._check(_get_lib().dc_aux_tree_compare(self._h, _ptr(out)))
+        return dict(identical=bool(out[0]), max_xy_diff=float(out[1]), cells=int(out[2]), pieces=int(out[3]),
+                    ms_cut=float(out[4]), ms_lists=float(out[5]))
 
     def view_reset(self):
         self._check(_get_lib().dc_view_reset(self._h))

@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
           "-I", INCLUDE, "-I", CSRC]
 
-SOURCES = ["dc_api.cpp", "geometry.cpp", "tree.cpp", "dense.cu", "gmres.cu", "fmm.cu", "fmm32.cu", "noalloc.cu", "mlp.cu", "features.cu", "coarse.cu", "peaks.cu", "adaptive.cu", "panels.cpp", "aa.cu"]
+SOURCES = ["dc_api.cpp", "geometry.cpp", "tree.cpp", "dense.cu", "gmres.cu", "fmm.cu", "fmm32.cu", "noalloc.cu", "mlp.cu", "features.cu", "coarse.cu", "peaks.cu", "adaptive.cu", "panels.cpp", "aa.cu", "tree_gpu.cu"]
 
 
 def _nvcc() -> str:

@@ -1475,6 +1475,14 @@ dc_status dc_view_update(dc_ctx *ctx, const dc_viewport *vp, const dc_view_optio
     return DC_OK;
 }
 
+dc_status dc_aux_tree_compare(dc_ctx *ctx, double *out) {
+    if (!ctx || !out) return DC_ERR_ARG;
+    ctx->err.clear();
+    if (ctx->state < 1 || !ctx->fmm) return fail(ctx, DC_ERR_STATE, "tree_compare: needs an FMM form after build_tree");
+    ctx->fmm->compare_host_tree(ctx->geo, out);
+    return DC_OK;
+}
+
 dc_status dc_view_reset(dc_ctx *ctx) {
     if (!ctx) return DC_ERR_ARG;
     ctx->err.clear();

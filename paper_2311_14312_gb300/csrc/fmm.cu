@@ -636,7 +636,7 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         I.build_ms[i] = std::chrono::duration<double, std::milli>(t - t_prev).count();
         t_prev = t;
     };
-    if (!build_quadtree(G.seg_xy, opt.domain, opt.leaf_size, opt.max_depth, I.tree, err))
+    if (!build_quadtree_device(D.seg.ptr, G.seg_xy, opt.domain, opt.leaf_size, opt.max_depth, I.tree, st, err))
         return DC_ERR_GEOMETRY;
     if (I.P1 > 32) {
         err = "FMM forms support expansion orders p <= 31";
@@ -1339,6 +1339,27 @@ cudaError_t Fmm::time_inner_m2l(int reps, cudaStream_t st, double out[6]) {
 void Fmm::set_eval_tile(int t) { impl_->opt.eval_tile = t; }
 
 void Fmm::set_render_only(bool on) { impl_->render_only = on; }
+
+void Fmm::compare_host_tree(const Geometry &G, double out[6]) const {
+    const Tree &T = impl_->tree;
+    Tree H;
+    std::string err;
+    out[0] = out[1] = 0.0;
+    out[4] = T.ms_cut;
+    out[5] = T.ms_lists;
+    out[2] = T.n_cells();
+    out[3] = double(T.pc_seg.size());
+    if (!build_quadtree(G.seg_xy, impl_->opt.domain, impl_->opt.leaf_size, impl_->opt.max_depth, H, err)) return;
+    const bool same = H.x0 == T.x0 && H.y0 == T.y0 && H.w0 == T.w0 && H.depth == T.depth && H.level == T.level &&
+                      H.parent == T.parent && H.child0 == T.child0 && H.ix == T.ix && H.iy == T.iy &&
+                      H.level_start == T.level_start && H.piece_start == T.piece_start &&
+                      H.piece_count == T.piece_count && H.pc_seg == T.pc_seg && H.pc_xy.size() == T.pc_xy.size();
+    out[0] = same ? 1.0 : 0.0;
+    double d = 0.0;
+    if (same)
+        for (size_t i = 0; i < H.pc_xy.size(); ++i) d = std::max(d, std::fabs(H.pc_xy[i] - T.pc_xy[i]));
+    out[1] = d;
+}
 
 cudaError_t Fmm::set_mma_skip_tile(int tile, cudaStream_t st) {
     Impl &I = *impl_;

@@ -36,6 +36,12 @@ public:
     // solve's structures: the two-level preconditioner and the node
     // near-field coefficients.  Set before build().
     void set_render_only(bool on);
+    // The tree built on the device against build_quadtree on the host over
+    // the same segments: out[0] 1 when cells, piece counts and piece segments
+    // are identical, out[1] the largest piece-endpoint difference, out[2]
+    // cells, out[3] pieces, out[4] / out[5] wall ms of the device build's
+    // clipping and lists.
+    void compare_host_tree(const Geometry &G, double out[6]) const;
     // y = B x with B the panels' inverse self-interaction blocks of G_H (the
     // first level of the two-level preconditioner alone).
     cudaError_t apply_block_jacobi(const double *x, double *y, cudaStream_t st);

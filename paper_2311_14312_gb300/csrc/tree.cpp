@@ -69,9 +69,7 @@ void to_csr(const std::vector<std::vector<int>> &lists, std::vector<int> &ptr,
 
 }  // namespace
 
-bool build_quadtree(const std::vector<double> &seg_xy, const double domain[4], int leaf_size,
-                    int max_depth, Tree &t, std::string &err) {
-    t = Tree();
+bool quadtree_root(const std::vector<double> &seg_xy, const double domain[4], Tree &t, std::string &err) {
     const int S = int(seg_xy.size() / 4);
     double lo[2] = {domain[0], domain[1]}, hi[2] = {domain[2], domain[3]};
     for (int k = 0; k < S; ++k) {
@@ -95,6 +93,14 @@ bool build_quadtree(const std::vector<double> &seg_xy, const double domain[4], i
         err = "build_tree: internal error choosing the root box";
         return false;
     }
+    return true;
+}
+
+bool build_quadtree(const std::vector<double> &seg_xy, const double domain[4], int leaf_size,
+                    int max_depth, Tree &t, std::string &err) {
+    t = Tree();
+    const int S = int(seg_xy.size() / 4);
+    if (!quadtree_root(seg_xy, domain, t, err)) return false;
 
     // breadth-first construction
     std::vector<std::vector<Piece>> cur(1);
@@ -240,6 +246,12 @@ bool build_quadtree(const std::vector<double> &seg_xy, const double domain[4], i
         t.piece_count[c] = int(t.pc_seg.size()) - t.piece_start[c];
     }
 
+    quadtree_lists(t);
+    return true;
+}
+
+void quadtree_lists(Tree &t) {
+    const int nC = t.n_cells();
     // colleagues (same level, touching, not self), top-down
     std::vector<std::vector<int>> coll(nC);
     for (int c = 1; c < nC; ++c) {
@@ -303,7 +315,6 @@ bool build_quadtree(const std::vector<double> &seg_xy, const double domain[4], i
     to_csr(V, t.v_ptr, t.v_idx);
     to_csr(W, t.w_ptr, t.w_idx);
     to_csr(X, t.x_ptr, t.x_idx);
-    return true;
 }
 
 long long check_quadtree_routes(const Tree &t) {

@@ -29,6 +29,7 @@ struct Tree {
     std::vector<int> w_ptr, w_idx;      // list 3 (leaves): smaller separated list
     std::vector<int> x_ptr, x_idx;      // list 4 (all cells): bigger separated list
 
+    double ms_cut = 0.0, ms_lists = 0.0;   // wall time of the last build's clipping and lists
     int n_cells() const { return int(level.size()); }
     bool is_leaf(int c) const { return child0[c] < 0; }
     double width(int c) const;
@@ -44,6 +45,18 @@ struct Tree {
 // while it holds more than leaf_size pieces and is above max_depth.
 bool build_quadtree(const std::vector<double> &seg_xy, const double domain[4], int leaf_size,
                     int max_depth, Tree &t, std::string &err);
+
+// The root box alone (x0, y0, w0 of t), as build_quadtree chooses it.
+bool quadtree_root(const std::vector<double> &seg_xy, const double domain[4], Tree &t, std::string &err);
+
+// Lists 1-4 of a tree whose cells and pieces are set.
+void quadtree_lists(Tree &t);
+
+// build_quadtree with the clipping of segments into pieces on the device
+// (tree_gpu.cu): the same cells, pieces (in the same order, with the same
+// IEEE operations) and lists.  seg_dev: the segments [S][4] on the device.
+bool build_quadtree_device(const double *seg_dev, const std::vector<double> &seg_xy, const double domain[4],
+                           int leaf_size, int max_depth, Tree &t, void *stream, std::string &err);
 
 // Exhaustive check that every (target leaf, source leaf) pair is covered by
 // exactly one of the four routes of Alg. 8.  Returns the number of pairs
