@@ -57,10 +57,11 @@ __device__ __forceinline__ float mono32(float2 q, float2 c) { return kMonoLog2 *
 // corr[e][m] = (G_H 1_j)(q_{i,m}) - l_j mono32(q_{i,m}, c_j) for the near pair
 // e = (i, j): the single layer of panel j with unit density (Lambda
 // reproduces constants) at the nodes of panel i, minus its monopole.  A
-// panel's own pairs (i = j, where the integrals are singular) run in FP64;
-// the others, whose terms are smooth, in FP32 on coordinates taken relative
-// to the node in FP64 (the same closed form, App. D): the FP64 logarithms
-// and arctangents cost 64 times as much here.
+// panel's own pair (singular) and the pairs with the panels next to it in
+// the panel order (neighbours on a curve share an end point: nearly
+// singular) run in FP64; the others, whose terms are smooth, in FP32 on
+// coordinates taken relative to the node in FP64 (the same closed form,
+// App. D): the FP64 logarithms and arctangents cost 64 times as much here.
 __global__ void near_pairs_kernel(const int2 *__restrict__ pairs, const double *__restrict__ seg,
                                   const double *__restrict__ segw, const double *__restrict__ nxy,
                                   const int *__restrict__ nseg, const int *__restrict__ nseg2,
@@ -72,7 +73,7 @@ __global__ void near_pairs_kernel(const int2 *__restrict__ pairs, const double *
     const int a = pr.x * g + m, j = pr.y;
     const double qx = nxy[2 * a], qy = nxy[2 * a + 1];
     const int own1 = nseg[a], own2 = nseg2[a];
-    if (pr.x == pr.y) {
+    if (abs(pr.x - pr.y) <= 1) {
         double acc64 = 0.0;
         for (int kk = 0; kk < s; ++kk) {
             const int k = j * s + kk;

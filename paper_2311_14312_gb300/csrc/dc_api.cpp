@@ -49,6 +49,7 @@ struct dc_ctx {
     bool warm_a1_valid = false;
     double build_ms[11] = {};   // dc_aux_build_timings
     dc::PanelFeatures pfeat;
+    bool feat_built = false;       // pfeat for the current drawing (built on first use)
     // the drawing as given to dc_build_tree (host copies), for dc_subdivide
     int in_ncurves = 0;
     std::vector<double> in_ctrl, in_start, in_col;
@@ -497,7 +498,7 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
         ctx->state = 1;
         return DC_OK;
     }
-    DC_CK(ctx, ctx->pfeat.build(G, s), "panel features");
+    ctx->feat_built = false;   // the warm start's panel geometry: built on first use
     lap(8);
     ctx->warm_a1_valid = false;
     {   // G_H 1, once per drawing: the first residual of the paper's start
@@ -520,12 +521,21 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
     return DC_OK;
 }
 
+// The panel geometry of the warm-start features, once per drawing.
+dc_status ensure_features(dc_ctx *ctx) {
+    if (ctx->feat_built) return DC_OK;
+    DC_CK(ctx, ctx->pfeat.build(ctx->geo, ctx->stream), "panel features");
+    ctx->feat_built = true;
+    return DC_OK;
+}
+
 // Learned warm start: features -> network -> sigma_p, then per channel the
 // x0 = alpha sigma_p + beta 1 of least residual ||b - G_H x0|| (two FP64
 // operator applications, G_H 1 cached per drawing).  The span holds 0 and the
 // paper's start 1, so the start is never worse than either (cold fallback:
 // alpha = 0 when the prediction does not help).
 dc_status warm_start(dc_ctx *ctx, dc_solve_stats *stats) {
+    if (dc_status fs = ensure_features(ctx); fs != DC_OK) return fs;
     cudaStream_t s = ctx->stream;
     const int N = ctx->dg.N, g = ctx->dg.g;
     const int rows = ctx->pfeat.rows(), F = dc::PanelFeatures::n_features(g), H = ctx->warm_hidden;
@@ -1000,8 +1010,8 @@ dc_status dc_eval_points(dc_ctx *ctx, int n, const void *xy, int xy_where, void 
 dc_status dc_aux_feature_dims(dc_ctx *ctx, int *rows, int *n_features, int *n_out) {
     if (!ctx) return DC_ERR_ARG;
     ctx->err.clear();
-    if (ctx->state < 1 || !ctx->pfeat.ready())
-        return fail(ctx, DC_ERR_STATE, "feature_dims: call build_tree first");
+    if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "feature_dims: call build_tree first");
+    if (dc_status fs = ensure_features(ctx); fs != DC_OK) return fs;
     if (rows) *rows = ctx->pfeat.rows();
     if (n_features) *n_features = dc::PanelFeatures::n_features(ctx->dg.g);
     if (n_out) *n_out = ctx->dg.g;
@@ -1011,8 +1021,8 @@ dc_status dc_aux_feature_dims(dc_ctx *ctx, int *rows, int *n_features, int *n_ou
 dc_status dc_aux_panel_features(dc_ctx *ctx, float *feat_dev, float *target_dev) {
     if (!ctx) return DC_ERR_ARG;
     ctx->err.clear();
-    if (ctx->state < 1 || !ctx->pfeat.ready())
-        return fail(ctx, DC_ERR_STATE, "panel_features: call build_tree first");
+    if (ctx->state < 1) return fail(ctx, DC_ERR_STATE, "panel_features: call build_tree first");
+    if (dc_status fs = ensure_features(ctx); fs != DC_OK) return fs;
     if (target_dev && ctx->state < 2)
         return fail(ctx, DC_ERR_STATE, "panel_features: targets need a density");
     if (!feat_dev) return fail(ctx, DC_ERR_ARG, "panel_features: NULL feature buffer");

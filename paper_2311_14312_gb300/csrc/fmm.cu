@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -265,6 +266,25 @@ cudaError_t upload(DevBuf<T> &buf, const std::vector<T> &v, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     if (v.empty()) return cudaSuccess;
     return cudaMemcpyAsync(buf.ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+// Leaf c's list-1 pieces, flattened in list order (block per cell; other
+// cells have an empty range): idx = piece numbers, seg = their segments.
+__global__ void uf_fill_kernel(const int *__restrict__ u_ptr, const int *__restrict__ u_idx,
+                               const int *__restrict__ pstart, const int *__restrict__ pcount,
+                               const int *__restrict__ pseg, const int *__restrict__ ufp, int *__restrict__ idx,
+                               int *__restrict__ seg) {
+    const int c = blockIdx.x;
+    int o = ufp[c];
+    if (ufp[c + 1] == o) return;
+    for (int e = u_ptr[c]; e < u_ptr[c + 1]; ++e) {
+        const int src = u_idx[e], p0 = pstart[src], n = pcount[src];
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+            idx[o + q] = p0 + q;
+            seg[o + q] = pseg[p0 + q];
+        }
+        o += n;
+    }
 }
 
 cudaError_t upload_cd(DevBuf<double2> &buf, const std::vector<cd> &v, cudaStream_t st) {
@@ -699,13 +719,16 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
                 }
         return -1;
     };
+    int sym_tab[7][7];   // the codes of the offsets in [-3, 3]^2, looked up per entry
+    for (int dx = -3; dx <= 3; ++dx)
+        for (int dy = -3; dy <= 3; ++dy) sym_tab[dx + 3][dy + 3] = sym_code(dx, dy);
     std::vector<int> voff(T.v_idx.size()), vcode(T.v_idx.size());
     long long m2l_cnt = 0;
     for (int c = 0; c < nC; ++c)
         for (int e = T.v_ptr[c]; e < T.v_ptr[c + 1]; ++e) {
             int s = T.v_idx[e];
             int dx = int(T.ix[c] - T.ix[s]), dy = int(T.iy[c] - T.iy[s]);
-            int code = sym_code(dx, dy);
+            int code = (std::abs(dx) <= 3 && std::abs(dy) <= 3) ? sym_tab[dx + 3][dy + 3] : -1;
             if (std::abs(dx) > 3 || std::abs(dy) > 3 || code < 0) {
                 err = "internal error: interaction-list offset out of range";
                 return DC_ERR_GEOMETRY;
@@ -1010,23 +1033,31 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     UP(I.plen64, plen64);
     UP(I.v_code, vcode);
     UP(I.m2m_cells, m2m_cells);
-    {   // list-1 pieces of every leaf, flattened in list order
-        std::vector<int> ufp(nC + 1, 0), ufi, ufs;
+    {   // list-1 pieces of every leaf, flattened in list order: the offsets
+        // here, the piece and segment numbers by uf_fill_kernel
+        std::vector<int> ufp(nC + 1, 0);
+        long long tot = 0;
         for (int c = 0; c < nC; ++c) {
-            ufp[c] = int(ufi.size());
+            ufp[c] = int(tot);
             if (!T.is_leaf(c)) continue;
-            for (int e = T.u_ptr[c]; e < T.u_ptr[c + 1]; ++e) {
-                const int src = T.u_idx[e];
-                for (int q = 0; q < T.piece_count[src]; ++q) {
-                    ufi.push_back(T.piece_start[src] + q);
-                    ufs.push_back(T.pc_seg[T.piece_start[src] + q]);
-                }
-            }
+            for (int e = T.u_ptr[c]; e < T.u_ptr[c + 1]; ++e) tot += T.piece_count[T.u_idx[e]];
         }
-        ufp[nC] = int(ufi.size());
+        if (tot > INT_MAX) {
+            err = "build_tree: too many list-1 pieces";
+            return DC_ERR_UNSUPPORTED;
+        }
+        ufp[nC] = int(tot);
         UP(I.uf_ptr, ufp);
-        UP(I.uf_idx, ufi);
-        UP(I.uf_seg, ufs);
+        if ((e = I.uf_idx.alloc(std::max<size_t>(tot, 1))) != cudaSuccess ||
+            (e = I.uf_seg.alloc(std::max<size_t>(tot, 1))) != cudaSuccess) {
+            err = std::string("fmm allocation: ") + cudaGetErrorString(e);
+            return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
+        }
+        if (nC > 0) {
+            uf_fill_kernel<<<nC, 128, 0, st>>>(I.u_ptr.ptr, I.u_idx.ptr, I.pstart.ptr, I.pcount.ptr, I.pseg.ptr,
+                                               I.uf_ptr.ptr, I.uf_idx.ptr, I.uf_seg.ptr);
+            note_launch();
+        }
     }
     UP(I.mchunks, mchunks);
     UP(I.mred, mred);
