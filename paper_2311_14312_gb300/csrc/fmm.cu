@@ -1486,6 +1486,7 @@ dc_status Fmm::render_viewports(const VpDev *vpl, int n_vp, const double *sbar, 
         return DC_ERR_CUDA;
     }
     std::vector<Tile> tiles;
+    std::vector<double> cost;   // estimated flops per tile
     int TW = kEvalTile, TH = kEvalTile;
     if (I.fp32) tile_shape(I.opt.eval_tile, TW, TH);
     long long pairs = 0;
@@ -1510,9 +1511,20 @@ dc_status Fmm::render_viewports(const VpDev *vpl, int n_vp, const double *sbar, 
             I.render_m2p += wn * npx;
             I.render_flops += 45.0 * double(up * npx) + 24.0 * I.P1 * double((1 + wn) * npx);
             for (int r = r0; r < r1; r += TH)
-                for (int cc = c0; cc < c1; cc += TW)
+                for (int cc = c0; cc < c1; cc += TW) {
                     tiles.push_back({c, r, cc, std::min(TH, r1 - r), std::min(TW, c1 - cc), v});
+                    const double tp = double(std::min(TH, r1 - r)) * std::min(TW, c1 - cc);
+                    cost.push_back(tp * (45.0 * double(up) + 24.0 * I.P1 * double(1 + wn)));
+                }
         }
+    }
+    {   // the most expensive tiles first (the persistent launch takes them in order)
+        std::vector<int> ord(tiles.size());
+        for (size_t i = 0; i < ord.size(); ++i) ord[i] = int(i);
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+        std::vector<Tile> sorted(tiles.size());
+        for (size_t i = 0; i < ord.size(); ++i) sorted[i] = tiles[ord[i]];
+        tiles.swap(sorted);
     }
     I.render_pairs += pairs;
     std::vector<VpDev> vv(vpl, vpl + n_vp);

@@ -227,6 +227,9 @@ struct EvalArgs32 {
     const unsigned char *heavy, *hL, *hM;
     const double2 *M64, *L64;
 
+    // persistent launch: the item counter (zero at launch) and the item count
+    int *queue;
+    int n_items;
     // list mode
     const float2 *q32;
     const double *q64;
@@ -246,7 +249,7 @@ __device__ __forceinline__ void split2(double v, float &hi, float &lo) {
 }
 
 template <int MODE, int TW, int TH>
-__global__ void __launch_bounds__(TW * TH, kEvThreadsPerSM / (TW * TH)) eval32_kernel(EvalArgs32 a) {
+__device__ __forceinline__ void eval32_item(const EvalArgs32 &a, int item) {
     // staged pieces of one list-1 leaf, in the target leaf's frame, each
     // coordinate as a (hi, lo) float pair so differences keep full accuracy
     __shared__ float sx1h[kStage], sx1l[kStage], sy1h[kStage], sy1l[kStage];
@@ -256,7 +259,7 @@ __global__ void __launch_bounds__(TW * TH, kEvThreadsPerSM / (TW * TH)) eval32_k
     __shared__ int sseg[kStage], sidx[kStage];
     __shared__ unsigned char shv[kStage];
     const DevTree32 &t = a.t;
-    Tile tl = a.items[blockIdx.x];
+    Tile tl = a.items[item];
     const int leaf = tl.leaf;
     double h0 = 0.0, h1 = 0.0, h2 = 0.0;   // FP64 sums of heavy pieces
     const double cxB = a.t64.cc[2 * leaf], cyB = a.t64.cc[2 * leaf + 1];
@@ -521,6 +524,26 @@ __global__ void __launch_bounds__(TW * TH, kEvThreadsPerSM / (TW * TH)) eval32_k
         a.out[3 * (size_t)o + 0] = u0 + h0;
         a.out[3 * (size_t)o + 1] = u1 + h1;
         a.out[3 * (size_t)o + 2] = u2 + h2;
+    }
+}
+
+// One item per block, or, with a.queue, a persistent grid whose blocks take
+// items from the counter *a.queue in list order (the render's tiles are
+// listed by decreasing estimated cost, so the longest start first).
+template <int MODE, int TW, int TH>
+__global__ void __launch_bounds__(TW * TH, kEvThreadsPerSM / (TW * TH)) eval32_kernel(EvalArgs32 a) {
+    if (!a.queue) {
+        eval32_item<MODE, TW, TH>(a, blockIdx.x);
+        return;
+    }
+    __shared__ int next;
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) next = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int it = next;
+        if (it >= a.n_items) break;
+        eval32_item<MODE, TW, TH>(a, it);
     }
 }
 
@@ -1060,11 +1083,22 @@ cudaError_t Fmm::Impl::render_tiles32(int n_tiles, void *rgb, int rgb_dtype,
     a.rgb = rgb;
     a.rgb_dtype = rgb_dtype;
     a.rgb8 = rgb8;
+    // persistent: as many blocks as are resident (the same register budget
+    // for every tile shape), taking tiles from a counter
+    cudaError_t e;
+    if ((e = render_queue.ensure(1)) != cudaSuccess ||
+        (e = cudaMemsetAsync(render_queue.ptr, 0, sizeof(int), st)) != cudaSuccess)
+        return e;
+    a.queue = render_queue.ptr;
+    a.n_items = n_tiles;
+    int tw = 8, th = 8;
+    tile_shape(opt.eval_tile, tw, th);
+    const int grid = std::max(1, std::min(n_tiles, n_sms * (kEvThreadsPerSM / (tw * th))));
     switch (opt.eval_tile) {   // tile shapes of tile_shape()
-    case 1: eval32_kernel<0, 16, 8><<<n_tiles, 128, 0, st>>>(a); break;
-    case 2: eval32_kernel<0, 16, 16><<<n_tiles, 256, 0, st>>>(a); break;
-    case 3: eval32_kernel<0, 32, 8><<<n_tiles, 256, 0, st>>>(a); break;
-    default: eval32_kernel<0, 8, 8><<<n_tiles, 64, 0, st>>>(a); break;
+    case 1: eval32_kernel<0, 16, 8><<<grid, 128, 0, st>>>(a); break;
+    case 2: eval32_kernel<0, 16, 16><<<grid, 256, 0, st>>>(a); break;
+    case 3: eval32_kernel<0, 32, 8><<<grid, 256, 0, st>>>(a); break;
+    default: eval32_kernel<0, 8, 8><<<grid, 64, 0, st>>>(a); break;
     }
     note_launch();
     return cudaGetLastError();

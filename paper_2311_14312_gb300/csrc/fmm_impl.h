@@ -145,7 +145,8 @@ struct Fmm::Impl {
     // FP64 tables and expansions
     DevBuf<double2> m2m, l2l, m2l, M, L;
     DevBuf<double> sbar, mbar;
-    DevBuf<Tile> tiles;
+    DevBuf<Tile> tiles;               // the render's tiles, by decreasing estimated cost
+    DevBuf<int> render_queue;         // the persistent render's tile counter
     DevBuf<VpDev> vps;
     // FP32 form
     DevBuf<float> iw32, logw32, pw32, plen32;
