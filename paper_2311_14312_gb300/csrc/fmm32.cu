@@ -242,6 +242,18 @@ __device__ __forceinline__ unsigned char quant8(float v) {
     return (unsigned char)floorf(255.f * v + 0.5f);
 }
 
+// (hi, lo) of (ah + al) - (bh + bl) from float pairs on the FP32 pipe: the
+// difference of the hi parts exactly (two-sum, Knuth), the lo parts added
+// to its error; accurate to about 2^-48 of the operands, like split2 of the
+// FP64 difference, without FP64 instructions.
+__device__ __forceinline__ void diff2(float ah, float al, float bh, float bl, float &hi, float &lo) {
+    const float s = __fsub_rn(ah, bh);
+    const float bb = __fsub_rn(s, ah);
+    const float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(-bh, bb));
+    hi = s;
+    lo = __fadd_rn(e, __fsub_rn(al, bl));
+}
+
 // float pair (hi, lo) with hi + lo = v to about 2^-48 relative
 __device__ __forceinline__ void split2(double v, float &hi, float &lo) {
     hi = (float)v;
@@ -391,7 +403,10 @@ __device__ __forceinline__ void eval32_item(const EvalArgs32 &a, int item) {
         qyl *= iwq;
     }
     // P2P over list 1 (App. D): the leaf's list-1 pieces, flattened in list
-    // order, staged kStage at a time
+    // order, staged kStage at a time, relative to the leaf's centre
+    float cxh, cxl, cyh, cyl;
+    split2(cxB, cxh, cxl);
+    split2(cyB, cyh, cyl);
     const int f_end = t.uf_ptr[leaf + 1];
     for (int f0 = t.uf_ptr[leaf]; f0 < f_end; f0 += kStage) {
         {
@@ -399,19 +414,19 @@ __device__ __forceinline__ void eval32_item(const EvalArgs32 &a, int item) {
             __syncthreads();
             for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
                 int i = t.uf_idx[f0 + s];
-                const double *P = a.t64.pc + 4 * (size_t)i;
                 const float iwf = t.iw[leaf], rho = 1.f / iwf;   // exact powers of two
+                const float4 ph = t.pch[i], pl = t.pcl[i];
                 float h, l;
-                split2(P[0] - cxB, h, l);
+                diff2(ph.x, pl.x, cxh, cxl, h, l);
                 sx1h[s] = h * iwf;
                 sx1l[s] = l * iwf;
-                split2(P[1] - cyB, h, l);
+                diff2(ph.y, pl.y, cyh, cyl, h, l);
                 sy1h[s] = h * iwf;
                 sy1l[s] = l * iwf;
-                split2(P[2] - cxB, h, l);
+                diff2(ph.z, pl.z, cxh, cxl, h, l);
                 sx2h[s] = h * iwf;
                 sx2l[s] = l * iwf;
-                split2(P[3] - cyB, h, l);
+                diff2(ph.w, pl.w, cyh, cyl, h, l);
                 sy2h[s] = h * iwf;
                 sy2l[s] = l * iwf;
                 slen[s] = t.plen[i] * iwf;
@@ -596,6 +611,8 @@ DevTree32 Fmm::Impl::dt32() const {
     t.x_off = xoff32.ptr;
     t.uf_ptr = uf_ptr.ptr;
     t.uf_idx = uf_idx.ptr;
+    t.pch = pch32.ptr;
+    t.pcl = pcl32.ptr;
     return t;
 }
 
@@ -612,7 +629,7 @@ dc_status Fmm::Impl::build32(const Geometry &G, cudaStream_t st, std::string &er
         ccy[c] = T.cy(c);
     }
     const size_t np = T.pc_seg.size();
-    std::vector<float4> pcf(np);
+    std::vector<float4> pcf(np), pch(np), pcl(np);
     std::vector<float> pwf(np), plf(np);
     std::vector<int> owner(np, -1);
     for (int c = 0; c < nC; ++c)
@@ -622,6 +639,13 @@ dc_status Fmm::Impl::build32(const Geometry &G, cudaStream_t st, std::string &er
         int c = owner[i];
         pcf[i] = make_float4((float)(q[0] - ccx[c]), (float)(q[1] - ccy[c]), (float)(q[2] - ccx[c]),
                              (float)(q[3] - ccy[c]));
+        float h[4], l[4];
+        for (int k = 0; k < 4; ++k) {
+            h[k] = (float)q[k];
+            l[k] = (float)(q[k] - (double)h[k]);
+        }
+        pch[i] = make_float4(h[0], h[1], h[2], h[3]);
+        pcl[i] = make_float4(l[0], l[1], l[2], l[3]);
         pwf[i] = (float)G.seg_w[T.pc_seg[i]];
         plf[i] = (float)std::hypot(q[2] - q[0], q[3] - q[1]);
     }
@@ -656,7 +680,8 @@ dc_status Fmm::Impl::build32(const Geometry &G, cudaStream_t st, std::string &er
     }
     n_nt_items = int(items.size());
     if ((e = up(iw32, iw, st)) != cudaSuccess || (e = up(logw32, logw, st)) != cudaSuccess ||
-        (e = up(pc32, pcf, st)) != cudaSuccess || (e = up(pw32, pwf, st)) != cudaSuccess ||
+        (e = up(pc32, pcf, st)) != cudaSuccess || (e = up(pch32, pch, st)) != cudaSuccess ||
+        (e = up(pcl32, pcl, st)) != cudaSuccess || (e = up(pw32, pwf, st)) != cudaSuccess ||
         (e = up(plen32, plf, st)) != cudaSuccess || (e = up(uoff32, uo, st)) != cudaSuccess ||
         (e = up(woff32, wo, st)) != cudaSuccess || (e = up(xoff32, xo, st)) != cudaSuccess ||
         (e = up(nt_q32, q32, st)) != cudaSuccess || (e = up(nt_items, items, st)) != cudaSuccess ||

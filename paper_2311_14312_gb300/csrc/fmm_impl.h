@@ -43,6 +43,7 @@ struct DevTree32 {
     const float2 *w_off;    // per list-3 entry
     const float2 *x_off;    // per list-4 entry
     const int *uf_ptr, *uf_idx;   // list-1 pieces of each leaf, flattened (list order)
+    const float4 *pch, *pcl;      // [np] endpoints (x1, y1, x2, y2) as FP32 (hi, lo) pairs
 };
 
 // A unit of evaluation work inside one leaf: a pixel rectangle (r0, c0,
@@ -151,6 +152,7 @@ struct Fmm::Impl {
     // FP32 form
     DevBuf<float> iw32, logw32, pw32, plen32;
     DevBuf<float4> pc32;
+    DevBuf<float4> pch32, pcl32;  // piece endpoints as (hi, lo) float pairs
     DevBuf<float2> uoff32, woff32, xoff32;
     DevBuf<float2> m2m32, l2l32, m2l32, M32, L32;
     DevBuf<float> sbar32, mbar32;
