@@ -6,15 +6,17 @@
 //
 // Parameters are FP32 masters packed layer by layer (W_l [out][in], then
 // b_l [out]); the forward and backward passes read BF16-rounded weights and
-// accumulate in FP32.  All products go through one tiled SIMT GEMM with an
-// optional bias + GELU epilogue; reductions over the batch are done inside
-// the GEMM in a fixed order (deterministic).
+// accumulate in FP32.  All products go through one tcgen05 GEMM (mlp_tc.cuh:
+// TF32 terms, BF16 weights exact, FP32 operands split in two) with an
+// optional bias + GELU epilogue; reductions over the batch run inside the
+// GEMM in a fixed order (deterministic).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 
 #include "dc_internal.h"
+#include "mlp_tc.cuh"
 
 namespace dc {
 namespace mlp {
@@ -26,75 +28,6 @@ __device__ __forceinline__ float gelu_grad(float x) {
     // d/dx [x Phi(x)] = Phi(x) + x phi(x)
     const float phi = 0.39894228040143268f * __expf(-0.5f * x * x);
     return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * phi;
-}
-
-// C[M][N] = op(A) op(B) (+ bias[N]) (GELU if act), FP32 accumulate.
-//   opA = A [M][K] (lda) or, with ta, A^T of A [K][M]
-//   opB = B^T of B [N][K] (ldb) or, with tb, B [K][N]
-// B may be BF16 (weights) or FP32 (activations).
-constexpr int kTM = 64, kTN = 64, kTK = 16;
-
-template <typename TB>
-__device__ __forceinline__ float ldv(const TB *p, size_t i);
-template <> __device__ __forceinline__ float ldv<float>(const float *p, size_t i) { return p[i]; }
-template <> __device__ __forceinline__ float ldv<__nv_bfloat16>(const __nv_bfloat16 *p, size_t i) {
-    return __bfloat162float(p[i]);
-}
-
-template <typename TB>
-__global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const float *__restrict__ A,
-                                                   int lda, int ta, const TB *__restrict__ B, int ldb,
-                                                   int tb, float *__restrict__ C, int ldc,
-                                                   const float *__restrict__ bias, int act,
-                                                   float *__restrict__ Zpre) {
-    __shared__ float As[kTK][kTM + 1];
-    __shared__ float Bs[kTK][kTN + 1];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += kTK) {
-        for (int i = threadIdx.x; i < kTK * kTM; i += 256) {
-            int kk = i / kTM, mm = i % kTM;
-            int gm = m0 + mm, gk = k0 + kk;
-            float v = 0.f;
-            if (gm < M && gk < K) v = ta ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
-            As[kk][mm] = v;
-        }
-        for (int i = threadIdx.x; i < kTK * kTN; i += 256) {
-            int kk = i / kTN, nn = i % kTN;
-            int gn = n0 + nn, gk = k0 + kk;
-            float v = 0.f;
-            if (gn < N && gk < K) v = tb ? ldv(B, (size_t)gk * ldb + gn) : ldv(B, (size_t)gn * ldb + gk);
-            Bs[kk][nn] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kTK; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int gm = m0 + ty * 4 + i;
-        if (gm >= M) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int gn = n0 + tx * 4 + j;
-            if (gn >= N) continue;
-            float z = acc[i][j] + (bias ? bias[gn] : 0.f);
-            if (Zpre) Zpre[(size_t)gm * ldc + gn] = z;
-            C[(size_t)gm * ldc + gn] = act ? gelu(z) : z;
-        }
-    }
 }
 
 __global__ void to_bf16_kernel(const float *__restrict__ a, __nv_bfloat16 *__restrict__ b, size_t n) {
@@ -189,19 +122,31 @@ size_t workspace_floats(const Dims &D, int batch) {
     for (int l = 0; l <= kLayers; ++l) widest = widest > (size_t)D.d[l] ? widest : (size_t)D.d[l];
     w += 2 * (size_t)batch * widest;
     w += ((size_t)batch * D.d[kLayers] + 255) / 256 + 8;
+    w += 8;   // the GEMMs' wait-limit flag
     return w;
 }
 
+// C[M][N] = op(A) op(B) (+ bias[N]) (GELU if act), FP32 accumulate.
+//   opA = A [M][K] (lda) or, with ta, A^T of A [K][M]
+//   opB = B^T of B [N][K] (ldb) or, with tb, B [K][N]
+// B may be BF16 (weights) or FP32 (activations).
 void gemm(cudaStream_t st, int M, int N, int K, const float *A, int lda, int ta, const void *B, int ldb,
-          int tb, bool b_bf16, float *C, int ldc, const float *bias, int act, float *Zpre) {
-    dim3 grid((N + kTN - 1) / kTN, (M + kTM - 1) / kTM);
+          int tb, bool b_bf16, float *C, int ldc, const float *bias, int act, float *Zpre, int *err) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(gemm_tc_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kGtSmem);
+        cudaFuncSetAttribute(gemm_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGtSmem);
+        attr = true;
+    }
+    dim3 grid((M + kGtM - 1) / kGtM, (N + kGtN - 1) / kGtN);
     if (b_bf16)
-        gemm_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(M, N, K, A, lda, ta,
-                                                         static_cast<const __nv_bfloat16 *>(B), ldb, tb,
-                                                         C, ldc, bias, act, Zpre);
+        gemm_tc_kernel<__nv_bfloat16><<<grid, 128, kGtSmem, st>>>(M, N, K, A, lda, ta,
+                                                                 static_cast<const __nv_bfloat16 *>(B), ldb, tb,
+                                                                 C, ldc, bias, act, Zpre, err);
     else
-        gemm_kernel<float><<<grid, 256, 0, st>>>(M, N, K, A, lda, ta, static_cast<const float *>(B), ldb,
-                                                 tb, C, ldc, bias, act, Zpre);
+        gemm_tc_kernel<float><<<grid, 128, kGtSmem, st>>>(M, N, K, A, lda, ta, static_cast<const float *>(B), ldb,
+                                                         tb, C, ldc, bias, act, Zpre, err);
     note_launch();
 }
 
@@ -214,6 +159,7 @@ namespace {
 struct Layout {
     __nv_bfloat16 *wbf;
     float *Z[kLayers], *Y[kLayers], *g0, *g1, *partial;
+    int *err;   // set when a GEMM's wait on its MMAs ran out
 };
 Layout carve(const Dims &D, int batch, float *work) {
     Layout L;
@@ -232,20 +178,32 @@ Layout carve(const Dims &D, int batch, float *work) {
     L.g1 = p;
     p += (size_t)batch * widest;
     L.partial = p;
+    p += ((size_t)batch * D.d[kLayers] + 255) / 256 + 8;
+    L.err = reinterpret_cast<int *>(p);
     return L;
+}
+
+// DC_ERR_TIMEOUT when a GEMM's wait on its MMAs ran out (the stream drained)
+dc_status check_waits(const Layout &L, cudaStream_t st) {
+    int flag = 0;
+    if (cudaMemcpyAsync(&flag, L.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return DC_ERR_CUDA;
+    return flag ? DC_ERR_TIMEOUT : DC_OK;
 }
 
 // forward; the output of the last layer is L.Y[3] (linear)
 void forward(const Dims &D, const float *params, int batch, const float *x, const Layout &L,
              cudaStream_t st) {
     size_t n = D.total;
+    cudaMemsetAsync(L.err, 0, sizeof(int), st);
     to_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(params, L.wbf, n);
     dc::note_launch();
     const float *in = x;
     for (int l = 0; l < kLayers; ++l) {
         const int out = D.d[l + 1], inn = D.d[l];
         gemm(st, batch, out, inn, in, inn, 0, L.wbf + D.woff[l], inn, 0, true, L.Y[l], out,
-             params + D.boff[l], l + 1 < kLayers ? 1 : 0, L.Z[l]);
+             params + D.boff[l], l + 1 < kLayers ? 1 : 0, L.Z[l], L.err);
         in = L.Y[l];
     }
 }
@@ -271,7 +229,8 @@ dc_status dc_aux_mlp_forward(int n_in, int hidden, int n_out, const float *param
     cudaError_t e = cudaMemcpyAsync(y, L.Y[kLayers - 1], sizeof(float) * (size_t)batch * n_out,
                                     cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaGetLastError();
-    return e == cudaSuccess ? DC_OK : DC_ERR_CUDA;
+    if (e != cudaSuccess) return DC_ERR_CUDA;
+    return check_waits(L, st);
 }
 
 dc_status dc_aux_mlp_loss_grad(int n_in, int hidden, int n_out, const float *params, int batch,
@@ -304,19 +263,20 @@ dc_status dc_aux_mlp_loss_grad(int n_in, int hidden, int n_out, const float *par
         const float *xin = (l == 0) ? x : L.Y[l - 1];
         // dW [out][inn] = dZ^T [out][batch] x X [batch][inn]
         gemm(st, out, inn, batch, dcur, out, 1, xin, inn, 1, false, grad + D.woff[l], inn, nullptr, 0,
-             nullptr);
+             nullptr, L.err);
         colsum_kernel<<<(out + 127) / 128, 128, 0, st>>>(dcur, batch, out, grad + D.boff[l]);
         dc::note_launch();
         if (l > 0) {
             // dX [batch][inn] = dZ [batch][out] x W [out][inn]
             gemm(st, batch, inn, out, dcur, out, 0, L.wbf + D.woff[l], inn, 1, true, dnext, inn, nullptr,
-                 0, nullptr);
+                 0, nullptr, L.err);
             float *t = dcur;
             dcur = dnext;
             dnext = t;
         }
     }
-    return cudaGetLastError() == cudaSuccess ? DC_OK : DC_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return DC_ERR_CUDA;
+    return check_waits(L, st);
 }
 
 dc_status dc_aux_mlp_adam(size_t n, float *params, const float *grad, float *m, float *v, float lr,
