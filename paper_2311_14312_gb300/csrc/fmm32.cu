@@ -944,12 +944,14 @@ cudaError_t Fmm::Impl::nodes32_from_segments(double *y, bool single, cudaStream_
 }
 
 // The inner node operator with the list-4 P2L (it needs only the segment
-// densities) as a branch of its own on side beside P2M -> M2M ->
-// tensor-core M2L on st; the M2L reduction adds onto the P2L terms once the
-// branch is done, then the walk and the node evaluation.  (A third branch
-// for the near field measured slower: its blocks delay the chain's.)
+// densities) as a branch of its own on side beside P2M -> M2M (and the
+// tensor-core M2L's MMAs) on st; the M2L (its reduction, or the CUDA-core
+// kernel) adds onto the P2L terms once the branch is done, then the walk and
+// the node evaluation.  (A third branch for the near field measured slower:
+// its blocks delay the chain's.)
 bool Fmm::Impl::split_ok() const {
-    return graph_split && n_tc_tiles > 0 && sched_nodes.n_m2l > 0 && near_ready && n_nt_items4 > 0;
+    const bool m2l_ok = n_tc_tiles > 0 || P1i <= passes::kM2LSmallP1;   // both engines add onto the P2L terms
+    return graph_split && m2l_ok && sched_nodes.n_m2l > 0 && near_ready && n_nt_items4 > 0;
 }
 
 cudaError_t Fmm::Impl::nodes32_split(double *y, cudaStream_t st, bool fork) {
@@ -995,9 +997,12 @@ cudaError_t Fmm::Impl::nodes32_split(double *y, cudaStream_t st, bool fork) {
             note_launch();
         }
     }
-    if (sc.n_m2l > 0 && (e = launch_m2l32(sc, 0, st)) != cudaSuccess) return e;
+    // tensor cores: the MMAs beside the branch, their reduction after it;
+    // CUDA cores: the whole M2L after it (both add onto the P2L terms)
+    const bool tc = n_tc_tiles > 0;
+    if (tc && sc.n_m2l > 0 && (e = launch_m2l32(sc, 0, st)) != cudaSuccess) return e;
     if (fork && (e = cudaStreamWaitEvent(st, fork_ev[1], 0)) != cudaSuccess) return e;
-    if (sc.n_m2l > 0 && (e = launch_m2l32(sc, 1, st)) != cudaSuccess) return e;
+    if (sc.n_m2l > 0 && (e = launch_m2l32(sc, tc ? 1 : 0, st)) != cudaSuccess) return e;
     if (sc.n_walk > 0) {
         passes::walk_kernel<float><<<sc.n_walk, std::max(32, (std::max(P1, walk_nmax) + 31) / 32 * 32),
                                      passes::walk_smem<float>(P1, walk_nmax), st>>>(

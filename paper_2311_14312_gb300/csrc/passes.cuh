@@ -554,9 +554,13 @@ static __global__ void __launch_bounds__(32 * kM2LSmallWarps) m2l_small_kernel(T
                 acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, 16);
                 acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, 16);
             }
-        if (h == 0 && l < P1)
+        if (h == 0 && l < P1)   // onto zero, or the cell's list-4 P2L terms
 #pragma unroll
-            for (int c = 0; c < 3; ++c) Lout[((size_t)cell * 3 + c) * P1 + l] = acc[c];
+            for (int c = 0; c < 3; ++c) {
+                float2 &o = Lout[((size_t)cell * 3 + c) * P1 + l];
+                o.x += acc[c].x;
+                o.y += acc[c].y;
+            }
     }
     cp_async_wait<0>();
 }
