@@ -462,9 +462,9 @@ typedef struct {
 dc_status dc_view_update(dc_ctx *ctx, const dc_viewport *vp, const dc_view_options *opt, dc_view_stats *stats);
 
 /* Auxiliary: the quadtree of the context (its segments clipped into pieces
- * on the device, level by level) against the host construction over the
- * same segments.  out[0] = 1 when cells, piece counts and piece segments are
- * identical, out[1] = the largest difference of piece endpoints, out[2] =
+ * and its lists 1-4 built on the device) against the host construction over
+ * the same segments.  out[0] = 1 when cells, piece counts, piece segments
+ * and lists 1-4 (entry for entry, in order) are identical, out[1] = the largest difference of piece endpoints, out[2] =
  * cells, out[3] = pieces, out[4] and out[5] = wall ms of the last build's
  * clipping (device) and lists (host).  FMM forms after dc_build_tree
  * (DC_ERR_STATE). */

@@ -1381,10 +1381,33 @@ void Fmm::compare_host_tree(const Geometry &G, double out[6]) const {
     out[2] = T.n_cells();
     out[3] = double(T.pc_seg.size());
     if (!build_quadtree(G.seg_xy, impl_->opt.domain, impl_->opt.leaf_size, impl_->opt.max_depth, H, err)) return;
+    // the lists as the build keeps them: entries whose source holds no pieces dropped
+    std::vector<int> sub(H.n_cells(), 0);
+    for (int c = H.n_cells() - 1; c >= 0; --c) {
+        if (H.is_leaf(c)) sub[c] = H.piece_count[c];
+        else
+            for (int q = 0; q < 4; ++q) sub[c] += sub[H.child0[c] + q];
+    }
+    auto prune = [&](std::vector<int> &ptr, std::vector<int> &idx) {
+        std::vector<int> np(ptr.size(), 0), ni;
+        for (int c = 0; c + 1 < (int)ptr.size(); ++c) {
+            for (int e = ptr[c]; e < ptr[c + 1]; ++e)
+                if (sub[idx[e]] > 0) ni.push_back(idx[e]);
+            np[c + 1] = int(ni.size());
+        }
+        ptr.swap(np);
+        idx.swap(ni);
+    };
+    prune(H.u_ptr, H.u_idx);
+    prune(H.v_ptr, H.v_idx);
+    prune(H.w_ptr, H.w_idx);
+    prune(H.x_ptr, H.x_idx);
     const bool same = H.x0 == T.x0 && H.y0 == T.y0 && H.w0 == T.w0 && H.depth == T.depth && H.level == T.level &&
                       H.parent == T.parent && H.child0 == T.child0 && H.ix == T.ix && H.iy == T.iy &&
                       H.level_start == T.level_start && H.piece_start == T.piece_start &&
-                      H.piece_count == T.piece_count && H.pc_seg == T.pc_seg && H.pc_xy.size() == T.pc_xy.size();
+                      H.piece_count == T.piece_count && H.pc_seg == T.pc_seg && H.pc_xy.size() == T.pc_xy.size() &&
+                      H.u_ptr == T.u_ptr && H.u_idx == T.u_idx && H.v_ptr == T.v_ptr && H.v_idx == T.v_idx &&
+                      H.w_ptr == T.w_ptr && H.w_idx == T.w_idx && H.x_ptr == T.x_ptr && H.x_idx == T.x_idx;
     out[0] = same ? 1.0 : 0.0;
     double d = 0.0;
     if (same)

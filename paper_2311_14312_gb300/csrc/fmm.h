@@ -37,8 +37,8 @@ public:
     // near-field coefficients.  Set before build().
     void set_render_only(bool on);
     // The tree built on the device against build_quadtree on the host over
-    // the same segments: out[0] 1 when cells, piece counts and piece segments
-    // are identical, out[1] the largest piece-endpoint difference, out[2]
+    // the same segments: out[0] 1 when cells, piece counts, piece segments
+    // and lists 1-4 are identical, out[1] the largest piece-endpoint difference, out[2]
     // cells, out[3] pieces, out[4] / out[5] wall ms of the device build's
     // clipping and lists.
     void compare_host_tree(const Geometry &G, double out[6]) const;

@@ -163,7 +163,298 @@ __global__ void init_pieces_kernel(int S, int *__restrict__ ps, double *__restri
     pb[k] = 1.0;
 }
 
+// ------------------------------------------------------------ lists --
+// Lists 1-4 on the device, entry for entry the host construction's (same
+// order within each list: the colleagues, list 2 and list 3 in the order
+// their loops produce them, lists 1 and 4 sorted).
+constexpr int kMaxColl = 8, kMaxV = 27, kDfsStack = 64;
+
+struct CellsDev {
+    const int *level, *parent, *child0;
+    const long long *ix, *iy;
+};
+
+__device__ __forceinline__ bool touches_dev(const CellsDev &t, int a, int b) {
+    if (t.level[a] > t.level[b]) {
+        const int x = a;
+        a = b;
+        b = x;
+    }
+    const int d = t.level[b] - t.level[a];
+    const long long ax0 = t.ix[a] << d, ax1 = (t.ix[a] + 1) << d;
+    const long long ay0 = t.iy[a] << d, ay1 = (t.iy[a] + 1) << d;
+    const long long bx0 = t.ix[b], bx1 = t.ix[b] + 1, by0 = t.iy[b], by1 = t.iy[b] + 1;
+    return bx1 >= ax0 && bx0 <= ax1 && by1 >= ay0 && by0 <= ay1;
+}
+
+// colleagues of the cells [c0, c1) of one level (their parents' are known)
+__global__ void coll_kernel(CellsDev t, int c0, int c1, int *__restrict__ coll, int *__restrict__ ncoll) {
+    const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= c1) return;
+    const int P = t.parent[c];
+    int n = 0;
+    auto consider = [&](int Q) {
+        if (t.child0[Q] < 0) return;
+        for (int q = 0; q < 4; ++q) {
+            const int D = t.child0[Q] + q;
+            if (D != c && touches_dev(t, c, D) && n < kMaxColl) coll[kMaxColl * c + n++] = D;
+        }
+    };
+    consider(P);
+    for (int i = 0; i < ncoll[P]; ++i) consider(coll[kMaxColl * P + i]);
+    ncoll[c] = n;
+}
+
+// list 2 into fixed slots
+__global__ void v_kernel(CellsDev t, int nC, const int *__restrict__ coll, const int *__restrict__ ncoll,
+                         int *__restrict__ vtmp, int *__restrict__ vcnt) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nC) return;
+    int n = 0;
+    if (t.level[c] >= 2) {
+        const int P = t.parent[c];
+        for (int i = 0; i < ncoll[P]; ++i) {
+            const int Q = coll[kMaxColl * P + i];
+            if (t.child0[Q] < 0) continue;
+            for (int q = 0; q < 4; ++q) {
+                const int D = t.child0[Q] + q;
+                if (!touches_dev(t, c, D) && n < kMaxV) vtmp[kMaxV * c + n++] = D;
+            }
+        }
+    }
+    vcnt[c] = n;
+}
+
+__global__ void compact_kernel(const int *__restrict__ tmp, int slots, const int *__restrict__ cnt,
+                               const int *__restrict__ ptr, int nC, int *__restrict__ idx) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nC) return;
+    for (int i = 0; i < cnt[c]; ++i) idx[ptr[c] + i] = tmp[(size_t)slots * c + i];
+}
+
+// lists 1 (without the coarser neighbours) and 3 of each leaf by the host's
+// descent through the colleagues; PASS 0 counts, PASS 1 writes
+template <int PASS>
+__global__ void uw_kernel(CellsDev t, int nC, const int *__restrict__ coll, const int *__restrict__ ncoll,
+                          int *__restrict__ ucnt, int *__restrict__ wcnt, const int *__restrict__ uoff,
+                          const int *__restrict__ woff, int *__restrict__ uidx, int *__restrict__ widx,
+                          int *__restrict__ bad) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nC) return;
+    if (t.child0[b] >= 0) {
+        if (PASS == 0) ucnt[b] = wcnt[b] = 0;
+        return;
+    }
+    int nu = 0, nw = 0;
+    auto put_u = [&](int v) {
+        if (PASS == 1) uidx[uoff[b] + nu] = v;
+        ++nu;
+    };
+    auto put_w = [&](int v) {
+        if (PASS == 1) widx[woff[b] + nw] = v;
+        ++nw;
+    };
+    put_u(b);
+    int stack[kDfsStack];
+    int top = 0;
+    for (int i = 0; i < ncoll[b]; ++i) stack[top++] = coll[kMaxColl * b + i];
+    while (top > 0) {
+        const int C = stack[--top];
+        if (t.child0[C] < 0) {
+            put_u(C);
+            continue;
+        }
+        for (int q = 0; q < 4; ++q) {
+            const int D = t.child0[C] + q;
+            if (touches_dev(t, b, D)) {
+                if (top < kDfsStack) stack[top++] = D;
+                else atomicExch(bad, 1);
+            } else {
+                put_w(D);
+            }
+        }
+    }
+    if (PASS == 0) {
+        ucnt[b] = nu;
+        wcnt[b] = nw;
+    }
+}
+
+// the coarser adjacent leaves (U[d] gains b) and list 4 (X[d] gains b for d
+// in W[b]): PASS 0 counts per d, PASS 1 writes after d's own entries
+template <int PASS>
+__global__ void dual_kernel(CellsDev t, int nC, const int *__restrict__ uoff, const int *__restrict__ ucnt,
+                            const int *__restrict__ uidx, const int *__restrict__ woff, const int *__restrict__ wcnt,
+                            const int *__restrict__ widx, int *__restrict__ uadd, int *__restrict__ xcnt,
+                            const int *__restrict__ ufptr, int *__restrict__ uslot, int *__restrict__ ufidx,
+                            const int *__restrict__ xptr, int *__restrict__ xslot, int *__restrict__ xidx) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nC || t.child0[b] >= 0) return;
+    for (int i = 0; i < ucnt[b]; ++i) {
+        const int d = uidx[uoff[b] + i];
+        if (t.level[d] > t.level[b]) {
+            if (PASS == 0) atomicAdd(&uadd[d], 1);
+            else ufidx[ufptr[d] + ucnt[d] + atomicAdd(&uslot[d], 1)] = b;
+        }
+    }
+    for (int i = 0; i < wcnt[b]; ++i) {
+        const int d = widx[woff[b] + i];
+        if (PASS == 0) atomicAdd(&xcnt[d], 1);
+        else xidx[xptr[d] + atomicAdd(&xslot[d], 1)] = b;
+    }
+}
+
+__global__ void ucopy_kernel(int nC, const int *__restrict__ uoff, const int *__restrict__ ucnt,
+                             const int *__restrict__ uidx, const int *__restrict__ ufptr, int *__restrict__ ufidx) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nC) return;
+    for (int i = 0; i < ucnt[c]; ++i) ufidx[ufptr[c] + i] = uidx[uoff[c] + i];
+}
+
+// each list sorted (lists 1 and 4; a few dozen entries each)
+__global__ void sort_lists_kernel(int nC, const int *__restrict__ ptr, int *__restrict__ idx) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nC) return;
+    int *a = idx + ptr[c];
+    const int n = ptr[c + 1] - ptr[c];
+    for (int i = 1; i < n; ++i) {
+        const int v = a[i];
+        int k = i - 1;
+        while (k >= 0 && a[k] > v) {
+            a[k + 1] = a[k];
+            --k;
+        }
+        a[k + 1] = v;
+    }
+}
+
 }  // namespace
+
+// Lists 1-4 of t (cells set) on the device; false with err on a failure.
+static bool quadtree_lists_device(Tree &t, cudaStream_t st, std::string &err) {
+    const int nC = t.n_cells();
+    auto fail = [&](cudaError_t e) {
+        err = std::string("build_tree (device lists): ") + cudaGetErrorString(e);
+        return false;
+    };
+    DevBuf<int> level, parent, child0, coll, ncoll, vtmp, vcnt, vptr, ucnt, wcnt, uoff, woff, uidx, widx;
+    DevBuf<int> uadd, xcnt, ufcnt, ufptr, uslot, ufidx, xptr, xslot, xidx, bad, vidx;
+    DevBuf<long long> ix, iy;
+    ScanWork sw;
+    cudaError_t e;
+    auto up = [&](auto &buf, const auto &v) -> cudaError_t {
+        cudaError_t r = buf.alloc(std::max<size_t>(v.size(), 1));
+        if (r != cudaSuccess) return r;
+        return cudaMemcpyAsync(buf.ptr, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice, st);
+    };
+    const size_t n1 = size_t(nC) + 1;
+    if ((e = up(level, t.level)) != cudaSuccess || (e = up(parent, t.parent)) != cudaSuccess ||
+        (e = up(child0, t.child0)) != cudaSuccess || (e = up(ix, t.ix)) != cudaSuccess ||
+        (e = up(iy, t.iy)) != cudaSuccess || (e = coll.alloc(kMaxColl * (size_t)nC)) != cudaSuccess ||
+        (e = ncoll.alloc(nC)) != cudaSuccess || (e = vtmp.alloc(kMaxV * (size_t)nC)) != cudaSuccess ||
+        (e = vcnt.alloc(n1)) != cudaSuccess || (e = vptr.alloc(n1)) != cudaSuccess ||
+        (e = ucnt.alloc(n1)) != cudaSuccess || (e = wcnt.alloc(n1)) != cudaSuccess ||
+        (e = uoff.alloc(n1)) != cudaSuccess || (e = woff.alloc(n1)) != cudaSuccess ||
+        (e = uadd.alloc(n1)) != cudaSuccess || (e = xcnt.alloc(n1)) != cudaSuccess ||
+        (e = ufcnt.alloc(n1)) != cudaSuccess || (e = ufptr.alloc(n1)) != cudaSuccess ||
+        (e = uslot.alloc(n1)) != cudaSuccess || (e = xptr.alloc(n1)) != cudaSuccess ||
+        (e = xslot.alloc(n1)) != cudaSuccess || (e = bad.alloc(1)) != cudaSuccess)
+        return fail(e);
+    CellsDev cd{level.ptr, parent.ptr, child0.ptr, ix.ptr, iy.ptr};
+    const int th = 128, gC = (nC + th - 1) / th;
+    if ((e = cudaMemsetAsync(ncoll.ptr, 0, sizeof(int) * nC, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(bad.ptr, 0, sizeof(int), st)) != cudaSuccess)
+        return fail(e);
+    for (int l = 1; l <= t.depth; ++l) {   // colleagues, top down
+        const int c0 = t.level_start[l], c1 = t.level_start[l + 1];
+        if (c1 > c0) {
+            coll_kernel<<<(c1 - c0 + th - 1) / th, th, 0, st>>>(cd, c0, c1, coll.ptr, ncoll.ptr);
+            note_launch();
+        }
+    }
+    // sizes of every list, one scan each, then the entries
+    auto zero_tail = [&](DevBuf<int> &b) { return cudaMemsetAsync(b.ptr + nC, 0, sizeof(int), st); };
+    v_kernel<<<gC, th, 0, st>>>(cd, nC, coll.ptr, ncoll.ptr, vtmp.ptr, vcnt.ptr);
+    uw_kernel<0><<<gC, th, 0, st>>>(cd, nC, coll.ptr, ncoll.ptr, ucnt.ptr, wcnt.ptr, nullptr, nullptr, nullptr,
+                                    nullptr, bad.ptr);
+    note_launch(2);
+    if ((e = zero_tail(vcnt)) != cudaSuccess || (e = zero_tail(ucnt)) != cudaSuccess ||
+        (e = zero_tail(wcnt)) != cudaSuccess || (e = scan_exclusive(vcnt.ptr, vptr.ptr, nC + 1, sw, st)) != cudaSuccess ||
+        (e = scan_exclusive(ucnt.ptr, uoff.ptr, nC + 1, sw, st)) != cudaSuccess ||
+        (e = scan_exclusive(wcnt.ptr, woff.ptr, nC + 1, sw, st)) != cudaSuccess)
+        return fail(e);
+    std::vector<int> tot(3);
+    if ((e = cudaMemcpyAsync(&tot[0], vptr.ptr + nC, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&tot[1], uoff.ptr + nC, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&tot[2], woff.ptr + nC, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail(e);
+    if ((e = vidx.alloc(std::max(tot[0], 1))) != cudaSuccess || (e = uidx.alloc(std::max(tot[1], 1))) != cudaSuccess ||
+        (e = widx.alloc(std::max(tot[2], 1))) != cudaSuccess)
+        return fail(e);
+    compact_kernel<<<gC, th, 0, st>>>(vtmp.ptr, kMaxV, vcnt.ptr, vptr.ptr, nC, vidx.ptr);
+    uw_kernel<1><<<gC, th, 0, st>>>(cd, nC, coll.ptr, ncoll.ptr, ucnt.ptr, wcnt.ptr, uoff.ptr, woff.ptr, uidx.ptr,
+                                    widx.ptr, bad.ptr);
+    note_launch(2);
+    if ((e = cudaMemsetAsync(uadd.ptr, 0, sizeof(int) * n1, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(xcnt.ptr, 0, sizeof(int) * n1, st)) != cudaSuccess)
+        return fail(e);
+    dual_kernel<0><<<gC, th, 0, st>>>(cd, nC, uoff.ptr, ucnt.ptr, uidx.ptr, woff.ptr, wcnt.ptr, widx.ptr, uadd.ptr,
+                                      xcnt.ptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    note_launch();
+    // list 1 = own entries + coarser neighbours; list 4
+    std::vector<int> h_ucnt(n1), h_uadd(n1), h_xcnt(n1);
+    if ((e = cudaMemcpyAsync(h_ucnt.data(), ucnt.ptr, sizeof(int) * n1, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h_uadd.data(), uadd.ptr, sizeof(int) * n1, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h_xcnt.data(), xcnt.ptr, sizeof(int) * n1, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail(e);
+    t.u_ptr.assign(n1, 0);
+    t.x_ptr.assign(n1, 0);
+    for (int c = 0; c < nC; ++c) {
+        t.u_ptr[c + 1] = t.u_ptr[c] + h_ucnt[c] + h_uadd[c];
+        t.x_ptr[c + 1] = t.x_ptr[c] + h_xcnt[c];
+    }
+    if ((e = up(ufptr, t.u_ptr)) != cudaSuccess || (e = up(xptr, t.x_ptr)) != cudaSuccess ||
+        (e = ufidx.alloc(std::max(t.u_ptr[nC], 1))) != cudaSuccess ||
+        (e = xidx.alloc(std::max(t.x_ptr[nC], 1))) != cudaSuccess ||
+        (e = cudaMemsetAsync(uslot.ptr, 0, sizeof(int) * n1, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(xslot.ptr, 0, sizeof(int) * n1, st)) != cudaSuccess)
+        return fail(e);
+    ucopy_kernel<<<gC, th, 0, st>>>(nC, uoff.ptr, ucnt.ptr, uidx.ptr, ufptr.ptr, ufidx.ptr);
+    dual_kernel<1><<<gC, th, 0, st>>>(cd, nC, uoff.ptr, ucnt.ptr, uidx.ptr, woff.ptr, wcnt.ptr, widx.ptr, nullptr,
+                                      nullptr, ufptr.ptr, uslot.ptr, ufidx.ptr, xptr.ptr, xslot.ptr, xidx.ptr);
+    sort_lists_kernel<<<gC, th, 0, st>>>(nC, ufptr.ptr, ufidx.ptr);
+    sort_lists_kernel<<<gC, th, 0, st>>>(nC, xptr.ptr, xidx.ptr);
+    note_launch(4);
+    // back to the host tree
+    std::vector<int> hv(n1), hw(n1);
+    t.v_idx.resize(tot[0]);
+    t.w_idx.resize(tot[2]);
+    t.u_idx.resize(t.u_ptr[nC]);
+    t.x_idx.resize(t.x_ptr[nC]);
+    int hbad = 0;
+    if ((e = cudaMemcpyAsync(hv.data(), vptr.ptr, sizeof(int) * n1, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(hw.data(), woff.ptr, sizeof(int) * n1, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (tot[0] && (e = cudaMemcpyAsync(t.v_idx.data(), vidx.ptr, sizeof(int) * tot[0], cudaMemcpyDeviceToHost, st)) !=
+                       cudaSuccess) ||
+        (tot[2] && (e = cudaMemcpyAsync(t.w_idx.data(), widx.ptr, sizeof(int) * tot[2], cudaMemcpyDeviceToHost, st)) !=
+                       cudaSuccess) ||
+        (t.u_ptr[nC] && (e = cudaMemcpyAsync(t.u_idx.data(), ufidx.ptr, sizeof(int) * t.u_ptr[nC],
+                                             cudaMemcpyDeviceToHost, st)) != cudaSuccess) ||
+        (t.x_ptr[nC] && (e = cudaMemcpyAsync(t.x_idx.data(), xidx.ptr, sizeof(int) * t.x_ptr[nC],
+                                             cudaMemcpyDeviceToHost, st)) != cudaSuccess) ||
+        (e = cudaMemcpyAsync(&hbad, bad.ptr, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail(e);
+    if (hbad) {
+        err = "build_tree (device lists): descent stack exceeded";
+        return false;
+    }
+    t.v_ptr.swap(hv);
+    t.w_ptr.swap(hw);
+    return true;
+}
 
 bool build_quadtree_device(const double *seg_dev, const std::vector<double> &seg_xy, const double domain[4],
                            int leaf_size, int max_depth, Tree &t, void *stream, std::string &err) {
@@ -352,7 +643,7 @@ bool build_quadtree_device(const double *seg_dev, const std::vector<double> &seg
         return cuda_err(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_err(e);
     const auto t1 = std::chrono::steady_clock::now();
-    quadtree_lists(t);
+    if (!quadtree_lists_device(t, st, err)) return false;
     t.ms_cut = std::chrono::duration<double, std::milli>(t1 - t0).count();
     t.ms_lists = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
     return true;

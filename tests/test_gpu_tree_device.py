@@ -1,7 +1,8 @@
-"""The quadtree's clipping of segments into pieces on the device
-(tree_gpu.cu) against the host construction over the same segments
+"""The quadtree's clipping of segments into pieces and its lists 1-4 on the
+device (tree_gpu.cu) against the host construction over the same segments
 (dc_aux_tree_compare): identical cells (levels, parents, children, grid
-positions), identical pieces per leaf in the same order, and piece endpoints
+positions), identical pieces per leaf in the same order, identical lists
+entry for entry, and piece endpoints
 equal up to the last bit (the host compiler may contract a product and a sum
 into one FMA); on the bench drawing, a drawing with segments along the
 cells' midlines (ties at every level), and the 2000-curve drawing."""
@@ -38,7 +39,7 @@ def test_device_tree_equals_host_tree(dcmod, cuda_ok, name):
         ctx.build_drawing(d)
         r = ctx.tree_compare()
         bt = ctx.build_timings()
-        print(f"{name} leaf {leaf}: {r}; tree and lists {bt['tree_lists']:.1f} ms")
+        print(f"{name} leaf {leaf}: {r}; tree phase {bt['tree_lists']:.1f} ms")
         assert r["identical"] and r["max_xy_diff"] <= 1e-15
         assert r["pieces"] >= d.n_segments
         ctx.close()
