@@ -13,7 +13,8 @@
 //
 // The coarse matrix Ac = R A~ P (panels x panels, FP32) is inverted once per
 // drawing by blocked Gauss-Jordan elimination without pivoting (it is
-// strongly diagonal: a panel's self term dominates its row).
+// strongly diagonal: a panel's self term dominates its row), one launch per
+// 32-wide pivot block.
 //
 // Drawings with more panels than the dense coarse inverse can hold group
 // the panels into aggregates of K panels consecutive in the Morton order of
@@ -56,51 +57,51 @@ __device__ __forceinline__ float mono32(float2 q, float2 c) { return kMonoLog2 *
 
 // corr[e][m] = (G_H 1_j)(q_{i,m}) - l_j mono32(q_{i,m}, c_j) for the near pair
 // e = (i, j): the single layer of panel j with unit density (Lambda
-// reproduces constants) at the nodes of panel i, minus its monopole.  A
-// panel's own pair (singular) and the pairs with the panels next to it in
-// the panel order (neighbours on a curve share an end point: nearly
-// singular) run in FP64; the others, whose terms are smooth, in FP32 on
-// coordinates taken relative to the node in FP64 (the same closed form,
-// App. D): the FP64 logarithms and arctangents cost 64 times as much here.
-__global__ void near_pairs_kernel(const int2 *__restrict__ pairs, const double *__restrict__ seg,
-                                  const double *__restrict__ segw, const double *__restrict__ nxy,
-                                  const int *__restrict__ nseg, const int *__restrict__ nseg2,
-                                  const float2 *__restrict__ q32, const float2 *__restrict__ c32,
-                                  const double *__restrict__ plen, int s, int g, double *__restrict__ corr) {
-    const int e = blockIdx.x, m = threadIdx.x;
-    if (m >= g) return;
+// reproduces constants) at the nodes of panel i, minus its monopole.  One
+// warp per pair; with g <= 16 each node takes two lanes, which split the
+// segments between them.  A segment within kNearSeg chord lengths of the
+// node (and the node's own segment, singular) runs in FP64; the others,
+// whose terms are smooth, in FP32 on coordinates taken relative to the node
+// in FP64 (the same closed form, App. D): the FP64 logarithms and
+// arctangents cost 64 times as much here.
+constexpr double kNearSeg = 8.0;
+__global__ void __launch_bounds__(32) near_pairs_kernel(const int2 *__restrict__ pairs, const double *__restrict__ seg,
+                                                        const double *__restrict__ segw,
+                                                        const double *__restrict__ nxy, const int *__restrict__ nseg,
+                                                        const int *__restrict__ nseg2,
+                                                        const float2 *__restrict__ q32,
+                                                        const float2 *__restrict__ c32,
+                                                        const double *__restrict__ plen, int s, int g,
+                                                        double *__restrict__ corr) {
+    const int e = blockIdx.x, lane = threadIdx.x;
+    const int halves = g <= 16 ? 2 : 1;
+    const int m = halves == 2 ? (lane & 15) : lane, part = halves == 2 ? (lane >> 4) : 0;
+    const bool valid = m < g;
     const int2 pr = pairs[e];
-    const int a = pr.x * g + m, j = pr.y;
+    const int a = pr.x * g + (valid ? m : 0), j = pr.y;
     const double qx = nxy[2 * a], qy = nxy[2 * a + 1];
     const int own1 = nseg[a], own2 = nseg2[a];
-    if (abs(pr.x - pr.y) <= 1) {
-        double acc64 = 0.0;
-        for (int kk = 0; kk < s; ++kk) {
+    double acc64 = 0.0;
+    float acc = 0.f;
+    if (valid)
+        for (int kk = part; kk < s; kk += halves) {
             const int k = j * s + kk;
             const double *q = seg + 4 * (size_t)k;
-            double G, F;
-            seg_gf_f64(qx, qy, q[0], q[1], q[2], q[3], segw[k], k == own1 || k == own2, G, F);
-            acc64 += G;
+            const double ax = q[0] - qx, ay = q[1] - qy, bx = q[2] - qx, by = q[3] - qy;
+            const double dx = q[2] - q[0], dy = q[3] - q[1];
+            if (k == own1 || k == own2 || seg_is_near(ax, ay, bx, by, dx, dy, kNearSeg)) {
+                double G, F;
+                seg_gf_f64(qx, qy, q[0], q[1], q[2], q[3], segw[k], k == own1 || k == own2, G, F);
+                acc64 += G;
+            } else {
+                acc += (float)segw[k] * seg_g_far_f32(ax, ay, bx, by, dx, dy);
+            }
         }
-        corr[(size_t)e * g + m] = acc64 - plen[j] * (double)mono32(q32[a], c32[j]);
-        return;
+    if (halves == 2) {
+        acc64 += __shfl_down_sync(0xffffffffu, acc64, 16);
+        acc += __shfl_down_sync(0xffffffffu, acc, 16);
     }
-    float acc = 0.f;
-    for (int kk = 0; kk < s; ++kk) {
-        const int k = j * s + kk;
-        const double *q = seg + 4 * (size_t)k;
-        const float ax = (float)(q[0] - qx), ay = (float)(q[1] - qy);
-        const float bx = (float)(q[2] - qx), by = (float)(q[3] - qy);
-        const float dx = (float)(q[2] - q[0]), dy = (float)(q[3] - q[1]);
-        const float c2 = dx * dx + dy * dy, ic = rsqrtf(c2), c = c2 * ic;
-        const float cr = ax * by - ay * bx;
-        const float phi = (k == own1 || k == own2) ? 0.f : atan2f(cr, ax * bx + ay * by);
-        const float ra2 = ax * ax + ay * ay, rb2 = bx * bx + by * by;
-        const float la = ra2 > 0.f ? (ax * dx + ay * dy) * ic * logf(ra2) : 0.f;
-        const float lb = rb2 > 0.f ? (bx * dx + by * dy) * ic * logf(rb2) : 0.f;
-        acc += -(float)segw[k] * (float)kInv2Pi * (0.5f * (lb - la) - c + cr * ic * phi);
-    }
-    corr[(size_t)e * g + m] = (double)acc - plen[j] * (double)mono32(q32[a], c32[j]);
+    if (valid && part == 0) corr[(size_t)e * g + m] = acc64 + (double)acc - plen[j] * (double)mono32(q32[a], c32[j]);
 }
 
 // Ac[i][j] = sum_m (l_j mono32(q_{i,m}, c_j) + corr), padded with the identity
@@ -208,85 +209,95 @@ __global__ void spread_agg_kernel(const double *__restrict__ y, const int *__res
     py[t] = y[3 * agg_of[n / g] + c];
 }
 
-// Blocked Gauss-Jordan inversion in place (no pivoting), step k:
-// 1. A_kk <- A_kk^-1 (one warp; lane t holds column t in registers and reads
-//    the pivot column by shuffles, with the same operations per element as
-//    the textbook in-place elimination)
-__global__ void gj_diag_kernel(float *__restrict__ A, int n, int k) {
-    static_assert(kGJ == 32, "a 32 x 32 thread block on the diagonal block");
-    // thread (tx, ty) holds element (row ty, column tx); one pivot per step,
-    // the block exchanged through shared memory (32 steps of two barriers)
-    __shared__ float D[kGJ][kGJ + 1];
-    __shared__ float rp;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    float *B = A + (size_t)k * kGJ * n + k * kGJ;
-    D[ty][tx] = B[(size_t)ty * n + tx];
-    __syncthreads();
-    for (int c = 0; c < kGJ; ++c) {
-        if (tx == 0 && ty == 0) rp = 1.f / D[c][c];
-        __syncthreads();
-        const float r = rp, dcol = D[ty][c], drow = D[c][tx];
-        float v;
-        if (ty == c) v = (tx == c) ? r : drow * r;
-        else v = (tx == c) ? -dcol * r : D[ty][tx] - dcol * drow * r;
-        __syncthreads();
-        D[ty][tx] = v;
-        __syncthreads();
-    }
-    B[(size_t)ty * n + tx] = D[ty][tx];
-}
-
-// 2. A_kj <- A_kk A_kj for the columns j outside block k (one thread per column)
-__global__ void gj_row_kernel(float *__restrict__ A, int n, int k) {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= n || col / kGJ == k) return;
-    float x[kGJ];
-    for (int r = 0; r < kGJ; ++r) x[r] = A[(size_t)(k * kGJ + r) * n + col];
-    for (int r = 0; r < kGJ; ++r) {
-        const float *d = A + (size_t)(k * kGJ + r) * n + k * kGJ;
-        float s = 0.f;
-        for (int t = 0; t < kGJ; ++t) s += d[t] * x[t];
-        A[(size_t)(k * kGJ + r) * n + col] = s;
-    }
-}
-
-// 3. A_ij <- A_ij - A_ik A_kj for rows i and columns j outside block k
-// (64 x 64 output tiles, the 32-wide inner dimension staged in shared memory)
-__global__ void __launch_bounds__(256) gj_update_kernel(float *__restrict__ A, int n, int k) {
-    __shared__ float Aik[64][kGJ + 1];
-    __shared__ float Akj[kGJ][64 + 1];
-    const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    for (int u = threadIdx.x; u < 64 * kGJ; u += 256) {
-        const int r = u / kGJ, c = u % kGJ;
-        Aik[r][c] = (i0 + r < n) ? A[(size_t)(i0 + r) * n + k * kGJ + c] : 0.f;
-        const int r2 = u / 64, c2 = u % 64;
-        Akj[r2][c2] = (j0 + c2 < n) ? A[(size_t)(k * kGJ + r2) * n + j0 + c2] : 0.f;
-    }
-    __syncthreads();
-    for (int a = 0; a < 4; ++a) {
-        const int i = i0 + ty * 4 + a;
-        if (i >= n || i / kGJ == k) continue;
-        for (int b = 0; b < 4; ++b) {
-            const int j = j0 + tx * 4 + b;
-            if (j >= n || j / kGJ == k) continue;
-            float s = 0.f;
-            for (int t = 0; t < kGJ; ++t) s += Aik[ty * 4 + a][t] * Akj[t][tx * 4 + b];
-            A[(size_t)i * n + j] -= s;
+// One step k of the blocked Gauss-Jordan inversion (no pivoting), the whole
+// matrix read from A and written to B (every entry of the step's result reads
+// entries that other blocks rewrite, hence two buffers).  With D = A_kk the
+// pivot block and the rows / columns of block k called pivot rows / columns:
+//   B_kk = D^-1,  B_kj = D^-1 A_kj,  B_ik = -A_ik D^-1,  B_ij = A_ij - A_ik D^-1 A_kj.
+// A block of 256 threads writes a 64 x 64 tile.  Warp 0 inverts D in
+// registers (lane t holds column t; one pivot per step, the pivot column
+// passed by shuffles) while the others stage the tile's pivot-column rows
+// A_ik and pivot-row columns A_kj in shared memory.  Then Y = D^-1 A_kj
+// (D^-1 itself for pivot columns), and every entry is Y for pivot rows,
+// else (A_ij or 0 for pivot columns) - A_ik Y.
+constexpr int kGjTile = 64;
+__global__ void __launch_bounds__(256) gj_step_kernel(const float *__restrict__ A, float *__restrict__ B, int n,
+                                                      int k) {
+    static_assert(kGJ == 32, "one warp inverts the pivot block");
+    __shared__ float Di[kGJ][kGJ + 1];
+    __shared__ float Aik[kGjTile][kGJ + 1];
+    __shared__ float Akj[kGJ][kGjTile + 1];
+    __shared__ float Y[kGJ][kGjTile + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i0 = blockIdx.y * kGjTile, j0 = blockIdx.x * kGjTile, kc = k * kGJ;
+    if (warp == 0) {
+        float a[kGJ];   // a[r] = D[r][lane]
+#pragma unroll
+        for (int r = 0; r < kGJ; ++r) a[r] = A[(size_t)(kc + r) * n + kc + lane];
+#pragma unroll
+        for (int c = 0; c < kGJ; ++c) {
+            const float rp = 1.f / __shfl_sync(0xffffffffu, a[c], c);
+            const float rowc = (lane == c) ? rp : a[c] * rp;
+#pragma unroll
+            for (int r = 0; r < kGJ; ++r) {
+                if (r == c) continue;
+                const float f = __shfl_sync(0xffffffffu, a[r], c);   // D[r][c] before this pivot
+                a[r] = (lane == c) ? -f * rp : fmaf(-f, rowc, a[r]);
+            }
+            a[c] = rowc;
+        }
+#pragma unroll
+        for (int r = 0; r < kGJ; ++r) Di[r][lane] = a[r];
+    } else {
+        for (int u = tid - 32; u < kGjTile * kGJ; u += 224) {
+            const int r = u / kGJ, c = u % kGJ;
+            Aik[r][c] = (i0 + r < n) ? A[(size_t)(i0 + r) * n + kc + c] : 0.f;
+            const int r2 = u / kGjTile, c2 = u % kGjTile;
+            Akj[r2][c2] = (j0 + c2 < n) ? A[(size_t)(kc + r2) * n + j0 + c2] : 0.f;
         }
     }
-}
-
-// 4. A_ik <- -A_ik A_kk for the rows i outside block k (one thread per row)
-__global__ void gj_col_kernel(float *__restrict__ A, int n, int k) {
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= n || row / kGJ == k) return;
-    float x[kGJ];
-    for (int t = 0; t < kGJ; ++t) x[t] = A[(size_t)row * n + k * kGJ + t];
-    for (int c = 0; c < kGJ; ++c) {
-        float s = 0.f;
-        for (int t = 0; t < kGJ; ++t) s += x[t] * A[(size_t)(k * kGJ + t) * n + k * kGJ + c];
-        A[(size_t)row * n + k * kGJ + c] = -s;
+    __syncthreads();
+    for (int u = tid; u < kGJ * kGjTile; u += 256) {
+        const int t = u / kGjTile, jj = u % kGjTile, j = j0 + jj;
+        float v;
+        if (j >= kc && j < kc + kGJ) {
+            v = Di[t][j - kc];
+        } else {
+            v = 0.f;
+#pragma unroll 8
+            for (int q = 0; q < kGJ; ++q) v = fmaf(Di[t][q], Akj[q][jj], v);
+        }
+        Y[t][jj] = v;
+    }
+    __syncthreads();
+    // thread (ty, tx): rows ty + 16 a, columns tx + 16 b
+    const int tx = tid & 15, ty = tid >> 4;
+#pragma unroll
+    for (int aa = 0; aa < 4; ++aa) {
+        const int ii = ty + 16 * aa, i = i0 + ii;
+        if (i >= n) continue;
+        const bool prow = (i >= kc && i < kc + kGJ);
+        float acc[4];
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb) acc[bb] = 0.f;
+        if (!prow) {
+#pragma unroll 8
+            for (int q = 0; q < kGJ; ++q) {
+                const float w = Aik[ii][q];
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb) acc[bb] = fmaf(w, Y[q][tx + 16 * bb], acc[bb]);
+            }
+        }
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb) {
+            const int jj = tx + 16 * bb, j = j0 + jj;
+            if (j >= n) continue;
+            const bool pcol = (j >= kc && j < kc + kGJ);
+            float v;
+            if (prow) v = Y[i - kc][jj];
+            else v = (pcol ? 0.f : A[(size_t)i * n + j]) - acc[bb];
+            B[(size_t)i * n + j] = v;
+        }
     }
 }
 
@@ -530,17 +541,23 @@ __global__ void inverse_check_kernel(const float *__restrict__ Ai, const float *
 
 }  // namespace
 
-cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st, int max_coarse) {
+void TwoLevel::plan(const Geometry &G, int max_coarse) {
     ready_ = false;
+    planned_ = false;
     const int P = G.n_panels, g = G.g, s = G.s, N = G.n_nodes();
-    if (P < 2) return cudaSuccess;
+    if (P < 2) return;
     P_ = P;
     g_ = g;
+    s_seg_ = s;
+    N_ = N;
     const int maxc = max_coarse > 0 ? max_coarse : kMaxCoarse;
     // panel centroids (node average) and arc lengths
-    std::vector<double> cen(2 * P), pl(P);
-    std::vector<float2> c32(P), q32(N);
-    std::vector<float> pl32(P);
+    std::vector<double> cen(2 * P);
+    std::vector<double> &pl = h_pl_;
+    pl.assign(P, 0.0);
+    h_c32_.resize(P);
+    h_q32_.resize(N);
+    h_pl32_.resize(P);
     for (int j = 0; j < P; ++j) {
         double sx = 0, sy = 0;
         for (int m = 0; m < g; ++m) {
@@ -555,15 +572,18 @@ cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st
             L += G.seg_w[j * s + k] * std::hypot(q[2] - q[0], q[3] - q[1]);
         }
         pl[j] = L;
-        c32[j] = make_float2((float)cen[2 * j], (float)cen[2 * j + 1]);
-        pl32[j] = (float)L;
+        h_c32_[j] = make_float2((float)cen[2 * j], (float)cen[2 * j + 1]);
+        h_pl32_[j] = (float)L;
     }
-    for (int a = 0; a < N; ++a) q32[a] = make_float2((float)G.node_xy[2 * a], (float)G.node_xy[2 * a + 1]);
+    for (int a = 0; a < N; ++a) h_q32_[a] = make_float2((float)G.node_xy[2 * a], (float)G.node_xy[2 * a + 1]);
     // coarse unknowns: one per panel (K = 1) while the padded count fits the
     // dense inverse, else aggregates of K panels consecutive in the Morton
     // order of the centroids (16 bits per axis over the centroids' box, ties
     // by panel index), K = ceil(P / (limit - 32))
-    std::vector<int> pagg, perm(P), agg_of(P);
+    std::vector<int> &pagg = h_pagg_, &perm = h_perm_, &agg_of = h_agg_of_;
+    pagg.clear();
+    perm.resize(P);
+    agg_of.resize(P);
     if ((P + kGJ - 1) / kGJ * kGJ <= maxc) {
         K_ = 1;
         for (int j = 0; j < P; ++j) perm[j] = agg_of[j] = j;
@@ -599,8 +619,10 @@ cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st
     n_pad_ = (nA_ + kGJ - 1) / kGJ * kGJ;
     // near panel pairs (i, j), i's list in j order: |c_i - c_j| < 1.5 (l_i + l_j);
     // candidates from a sweep over the centroids sorted by x
-    std::vector<int> nptr(P + 1, 0);
-    std::vector<int2> pairs;
+    std::vector<int> &nptr = h_nptr_;
+    std::vector<int2> &pairs = h_pairs_;
+    nptr.assign(P + 1, 0);
+    pairs.clear();
     {
         std::vector<int> ord(P);
         for (int j = 0; j < P; ++j) ord[j] = j;
@@ -628,79 +650,110 @@ cudaError_t TwoLevel::build(const Geometry &G, const DevGeom &D, cudaStream_t st
         }
         nptr[P] = int(pairs.size());
     }
+    planned_ = true;
+}
 
+cudaError_t TwoLevel::launch(const DevGeom &D, cudaStream_t st) {
+    launched_ = false;
+    if (!planned_) return cudaSuccess;
+    const int P = P_, g = g_, s = s_seg_, N = N_;
     cudaError_t e;
+    // pageable sources: each copy has left the host vector when the call
+    // returns, so the vectors are released below.  A copy from pageable
+    // memory first waits for the stream's earlier work: all uploads come
+    // before the first kernel.
     auto up = [&](auto &buf, const auto &v) -> cudaError_t {
         cudaError_t r = buf.alloc(std::max<size_t>(v.size(), 1));
         if (r != cudaSuccess || v.empty()) return r;
         return cudaMemcpyAsync(buf.ptr, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice, st);
     };
-    if ((e = up(c32_, c32)) != cudaSuccess || (e = up(q32_, q32)) != cudaSuccess ||
-        (e = up(plen_, pl)) != cudaSuccess || (e = up(plen32_, pl32)) != cudaSuccess ||
-        (e = up(nptr_, nptr)) != cudaSuccess || (e = up(pairs_, pairs)) != cudaSuccess)
+    const size_t n_pairs = h_pairs_.size();
+    if ((e = up(c32_, h_c32_)) != cudaSuccess || (e = up(q32_, h_q32_)) != cudaSuccess ||
+        (e = up(plen_, h_pl_)) != cudaSuccess || (e = up(plen32_, h_pl32_)) != cudaSuccess ||
+        (e = up(nptr_, h_nptr_)) != cudaSuccess || (e = up(pairs_, h_pairs_)) != cudaSuccess)
         return e;
-    if ((e = corr_.alloc(pairs.size() * (size_t)g)) != cudaSuccess ||
+    if (K_ > 1 && ((e = up(pagg_, h_pagg_)) != cudaSuccess || (e = up(agg_of_, h_agg_of_)) != cudaSuccess ||
+                   (e = up(perm_, h_perm_)) != cudaSuccess))
+        return e;
+    if ((e = corr_.alloc(n_pairs * (size_t)g)) != cudaSuccess ||
         (e = Ainv_.alloc((size_t)n_pad_ * n_pad_)) != cudaSuccess || (e = s_.alloc(3 * (size_t)P)) != cudaSuccess ||
         (e = y_.alloc(3 * (size_t)P)) != cudaSuccess || (e = pan_.alloc((size_t)P)) != cudaSuccess || (e = pan2_.alloc((size_t)P)) != cudaSuccess ||
         (K_ == 1 && (e = part_.alloc((size_t)kSplit * 3 * N)) != cudaSuccess))
         return e;
-    near_pairs_kernel<<<(unsigned)pairs.size(), 32, 0, st>>>(pairs_.ptr, D.seg.ptr, D.segw.ptr, D.node_xy.ptr,
-                                                            D.node_seg.ptr, D.node_seg2.ptr, q32_.ptr, c32_.ptr,
-                                                            plen_.ptr, s, g, corr_.ptr);
+    const int ncol = (n_pad_ + 6) / 7;   // columns per checked row and block
+    if ((e = Ac_.alloc((size_t)n_pad_ * n_pad_)) != cudaSuccess ||
+        (e = gj_tmp_.alloc((size_t)n_pad_ * n_pad_)) != cudaSuccess || (e = errs_.alloc((size_t)5 * ncol)) != cudaSuccess ||
+        (e = bad_.alloc(1)) != cudaSuccess)
+        return e;
+    near_pairs_kernel<<<(unsigned)n_pairs, 32, 0, st>>>(pairs_.ptr, D.seg.ptr, D.segw.ptr, D.node_xy.ptr,
+                                                        D.node_seg.ptr, D.node_seg2.ptr, q32_.ptr, c32_.ptr,
+                                                        plen_.ptr, s, g, corr_.ptr);
     note_launch();
+    // the coarse matrix into Ac_ (kept for the check below)
     if (K_ == 1) {
         coarse_matrix_kernel<<<n_pad_, 256, 0, st>>>(q32_.ptr, c32_.ptr, plen32_.ptr, nptr_.ptr, pairs_.ptr,
-                                                    corr_.ptr, P, g, n_pad_, Ainv_.ptr);
+                                                    corr_.ptr, P, g, n_pad_, Ac_.ptr);
         note_launch();
     } else {
-        if ((e = up(pagg_, pagg)) != cudaSuccess || (e = up(agg_of_, agg_of)) != cudaSuccess ||
-            (e = up(perm_, perm)) != cudaSuccess)
-            return e;
         coarse_agg_matrix_kernel<<<n_pad_, 256, 0, st>>>(q32_.ptr, c32_.ptr, plen32_.ptr, pagg_.ptr, perm_.ptr, nA_,
-                                                        g, n_pad_, Ainv_.ptr);
+                                                        g, n_pad_, Ac_.ptr);
         coarse_agg_corr_kernel<<<(nA_ + 127) / 128, 128, 0, st>>>(pagg_.ptr, perm_.ptr, agg_of_.ptr, nA_, nptr_.ptr,
-                                                                 pairs_.ptr, corr_.ptr, g, n_pad_, Ainv_.ptr);
+                                                                 pairs_.ptr, corr_.ptr, g, n_pad_, Ac_.ptr);
         note_launch(2);
     }
-    // keep the coarse matrix for the check below
-    DevBuf<float> Ac;
-    if ((e = Ac.alloc((size_t)n_pad_ * n_pad_)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(Ac.ptr, Ainv_.ptr, Ac.bytes(), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-        return e;
+    // Gauss-Jordan steps between Ainv_ and gj_tmp_, the first reading Ac_
+    // and the last writing Ainv_
     const int nb = n_pad_ / kGJ;
-    dim3 ug((n_pad_ + 63) / 64, (n_pad_ + 63) / 64);
+    const dim3 ug((n_pad_ + kGjTile - 1) / kGjTile, (n_pad_ + kGjTile - 1) / kGjTile);
+    const float *src = Ac_.ptr;
     for (int k = 0; k < nb; ++k) {
-        gj_diag_kernel<<<1, dim3(kGJ, kGJ), 0, st>>>(Ainv_.ptr, n_pad_, k);
-        gj_row_kernel<<<(n_pad_ + 127) / 128, 128, 0, st>>>(Ainv_.ptr, n_pad_, k);
-        gj_update_kernel<<<ug, 256, 0, st>>>(Ainv_.ptr, n_pad_, k);
-        gj_col_kernel<<<(n_pad_ + 127) / 128, 128, 0, st>>>(Ainv_.ptr, n_pad_, k);
-        note_launch(4);
+        float *dst = ((nb - 1 - k) % 2 == 0) ? Ainv_.ptr : gj_tmp_.ptr;
+        gj_step_kernel<<<ug, 256, 0, st>>>(src, dst, n_pad_, k);
+        note_launch();
+        src = dst;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // check the inverse on a few rows, on the device (a vanished or tiny
-    // pivot shows up as non-finite entries or a large error): keep the
-    // one-level preconditioner unless it is accurate
-    const int ncol = (n_pad_ + 6) / 7;
-    DevBuf<double> errs;
-    DevBuf<int> bad;
-    if ((e = errs.alloc((size_t)5 * ncol)) != cudaSuccess || (e = bad.alloc(1)) != cudaSuccess ||
-        (e = cudaMemsetAsync(bad.ptr, 0, sizeof(int), st)) != cudaSuccess)
-        return e;
-    inverse_check_kernel<<<dim3(ncol, 5), 128, 0, st>>>(Ainv_.ptr, Ac.ptr, n_pad_,
+    // pivot shows up as non-finite entries or a large error)
+    if ((e = cudaMemsetAsync(bad_.ptr, 0, sizeof(int), st)) != cudaSuccess) return e;
+    inverse_check_kernel<<<dim3(ncol, 5), 128, 0, st>>>(Ainv_.ptr, Ac_.ptr, n_pad_,
                                                        make_int4(0, nA_ / 4, nA_ / 2, (3 * nA_) / 4), nA_ - 1,
-                                                       errs.ptr, bad.ptr);
+                                                       errs_.ptr, bad_.ptr);
     note_launch();
-    std::vector<double> errs_h((size_t)5 * ncol);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    n_pairs_ = int(n_pairs);
+    std::vector<double>().swap(h_pl_);
+    std::vector<float2>().swap(h_c32_);
+    std::vector<float2>().swap(h_q32_);
+    std::vector<float>().swap(h_pl32_);
+    std::vector<int2>().swap(h_pairs_);
+    std::vector<int>().swap(h_nptr_);
+    std::vector<int>().swap(h_pagg_);
+    std::vector<int>().swap(h_perm_);
+    std::vector<int>().swap(h_agg_of_);
+    launched_ = true;
+    return cudaSuccess;
+}
+
+cudaError_t TwoLevel::finish(cudaStream_t st) {
+    if (!launched_) return cudaSuccess;
+    launched_ = false;
+    cudaError_t e;
+    std::vector<double> errs_h(errs_.n);
     int bad_h = 0;
-    if ((e = cudaMemcpyAsync(errs_h.data(), errs.ptr, errs.bytes(), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(&bad_h, bad.ptr, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess ||
+        (e = cudaMemcpy(errs_h.data(), errs_.ptr, errs_.bytes(), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(&bad_h, bad_.ptr, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
         return e;
+    Ac_.release();
+    gj_tmp_.release();
+    errs_.release();
+    bad_.release();
+    // keep the one-level preconditioner unless the inverse is accurate
     if (bad_h) return cudaSuccess;
     double worst = 0.0;
     for (double v : errs_h) worst = std::max(worst, v);
     check_ = worst;
-    n_pairs_ = int(pairs.size());
     if (!(worst < 1e-2)) return cudaSuccess;
     ready_ = true;
     return cudaSuccess;

@@ -21,6 +21,30 @@ using dc::DevBuf;
 namespace dc {
 static std::atomic<long long> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+thread_local FreeDefer *t_defer = nullptr;
+}
+FreeDefer::FreeDefer() : prev(t_defer) { t_defer = this; }
+FreeDefer::~FreeDefer() {
+    flush();
+    t_defer = prev;
+}
+void FreeDefer::flush() {
+    for (void *p : ptrs) cudaFree(p);
+    ptrs.clear();
+}
+void dev_free(void *p) {
+    if (!p) return;
+    if (t_defer) {
+        try {
+            t_defer->ptrs.push_back(p);
+            return;
+        } catch (...) {   // no room to hold it back: free now
+        }
+    }
+    cudaFree(p);
+}
 long long kernel_launches() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace dc
 

@@ -70,6 +70,21 @@ cudaError_t launch_blend(double *out, const double *a, double alpha, const doubl
 cudaError_t launch_max_diff(const float *a, const double *b, long long n, unsigned *out, cudaStream_t st);
 
 // ---------------------------------------------------------- device util --
+// While a FreeDefer lives on a thread, the frees of device buffers released
+// on that thread are held back until flush() or its end: cudaFree waits for
+// all of the device's work, including other streams' work that the thread
+// means to overlap.
+struct FreeDefer {
+    std::vector<void *> ptrs;
+    FreeDefer *prev;
+    FreeDefer();
+    ~FreeDefer();
+    void flush();
+    FreeDefer(const FreeDefer &) = delete;
+    FreeDefer &operator=(const FreeDefer &) = delete;
+};
+void dev_free(void *p);   // cudaFree, or held back by the thread's FreeDefer
+
 template <typename T>
 struct DevBuf {
     T *ptr = nullptr;
@@ -90,7 +105,7 @@ struct DevBuf {
         return alloc(count);
     }
     void release() {
-        if (ptr) cudaFree(ptr);
+        if (ptr) dev_free(ptr);
         ptr = nullptr;
         n = 0;
     }
@@ -205,8 +220,15 @@ private:
 // the coarse matrix; ready() is false when that failed (one level then).
 class TwoLevel {
 public:
-    // max_coarse: most coarse unknowns (0 = the built-in 12288)
-    cudaError_t build(const Geometry &G, const DevGeom &D, cudaStream_t st, int max_coarse);
+    // Built in three steps, so that the caller can overlap them with other
+    // work: plan() is host work only (centroids, aggregates, near panel
+    // pairs; max_coarse: most coarse unknowns, 0 = the built-in 12288);
+    // launch() enqueues the uploads, the coarse matrix, its inversion and the
+    // check of the inverse on st and waits for none of them; finish() waits
+    // for st and decides from the check whether the coarse level is used.
+    void plan(const Geometry &G, int max_coarse);
+    cudaError_t launch(const DevGeom &D, cudaStream_t st);
+    cudaError_t finish(cudaStream_t st);
     bool ready() const { return ready_; }
     // coarse unknowns (panels, or aggregates of K panels), near panel pairs,
     // max |(Ac^-1 Ac - I)_ij| over 5 sampled rows, K
@@ -232,8 +254,19 @@ public:
                              const float2 *lam = nullptr, int s = 0, float *sv = nullptr);
 
 private:
-    bool ready_ = false;
-    int P_ = 0, g_ = 0, n_pad_ = 0, n_pairs_ = 0, nA_ = 0, K_ = 1;
+    bool ready_ = false, planned_ = false, launched_ = false;
+    int P_ = 0, g_ = 0, s_seg_ = 0, N_ = 0, n_pad_ = 0, n_pairs_ = 0, nA_ = 0, K_ = 1;
+    // plan() output, uploaded by launch()
+    std::vector<float2> h_c32_, h_q32_;
+    std::vector<double> h_pl_;
+    std::vector<float> h_pl32_;
+    std::vector<int> h_pagg_, h_perm_, h_agg_of_, h_nptr_;
+    std::vector<int2> h_pairs_;
+    // launch() to finish(): the coarse matrix before inversion, the check's
+    // row errors and its bad-pivot flag
+    DevBuf<float> Ac_, gj_tmp_;
+    DevBuf<double> errs_;
+    DevBuf<int> bad_;
     DevBuf<int> pagg_, agg_of_, perm_;   // aggregates: start of each in perm_ (+ end), aggregate of each
                                          // panel, panels in Morton order
     double check_ = -1.0;

@@ -193,30 +193,52 @@ dense_eval_points_kernel(const double *__restrict__ seg, const double *__restric
 
 // ------------------------------------------ panel block preconditioner --
 // Diagonal blocks of G_H: B_j[m][n] = sum_{k in panel j} w_k int_{S_k} G(p, q_jm) dS
-// Lambda[k][n] (the self-interaction of panel j, Eq. 19), one thread per row.
+// Lambda[k][n] (the self-interaction of panel j, Eq. 19), one warp per panel:
+// one lane per row, or with g <= 16 two lanes per row splitting the
+// segments.  Segments within kBlockNearSeg chord lengths of the node (and
+// its own, singular) take the FP64 closed form, the others the FP32 one on
+// FP64 relative coordinates (smooth terms; the blocks only precondition).
+constexpr double kBlockNearSeg = 8.0;
 template <int MAXG>
-__global__ void panel_blocks_kernel(const double *__restrict__ seg, const double *__restrict__ segw,
-                                    const double *__restrict__ nxy, const int *__restrict__ nseg,
-                                    const int *__restrict__ nseg2, const double *__restrict__ lam,
-                                    double *__restrict__ blocks, int s, int g) {
-    int j = blockIdx.x, m = threadIdx.x;
-    if (m >= g) return;
-    int i = j * g + m;
-    double qx = nxy[2 * i], qy = nxy[2 * i + 1];
-    int own1 = nseg[i], own2 = nseg2[i];
+__global__ void __launch_bounds__(32) panel_blocks_kernel(const double *__restrict__ seg,
+                                                          const double *__restrict__ segw,
+                                                          const double *__restrict__ nxy, const int *__restrict__ nseg,
+                                                          const int *__restrict__ nseg2,
+                                                          const double *__restrict__ lam,
+                                                          double *__restrict__ blocks, int s, int g) {
+    const int j = blockIdx.x, lane = threadIdx.x;
+    const int halves = g <= 16 ? 2 : 1;
+    const int m = halves == 2 ? (lane & 15) : lane, part = halves == 2 ? (lane >> 4) : 0;
+    const bool valid = m < g;
+    const int i = j * g + (valid ? m : 0);
+    const double qx = nxy[2 * i], qy = nxy[2 * i + 1];
+    const int own1 = nseg[i], own2 = nseg2[i];
     double acc[MAXG];
 #pragma unroll
     for (int n = 0; n < MAXG; ++n) acc[n] = 0.0;
-    for (int kk = 0; kk < s; ++kk) {
-        int k = j * s + kk;
-        const double *q = seg + 4 * (size_t)k;
-        double G, F;
-        seg_gf_f64(qx, qy, q[0], q[1], q[2], q[3], segw[k], k == own1 || k == own2, G, F);
-        const double *lr = lam + (size_t)kk * g;
+    if (valid)
+        for (int kk = part; kk < s; kk += halves) {
+            const int k = j * s + kk;
+            const double *q = seg + 4 * (size_t)k;
+            const double ax = q[0] - qx, ay = q[1] - qy, bx = q[2] - qx, by = q[3] - qy;
+            const double dx = q[2] - q[0], dy = q[3] - q[1];
+            double G;
+            if (k == own1 || k == own2 || seg_is_near(ax, ay, bx, by, dx, dy, kBlockNearSeg)) {
+                double F;
+                seg_gf_f64(qx, qy, q[0], q[1], q[2], q[3], segw[k], k == own1 || k == own2, G, F);
+            } else {
+                G = segw[k] * (double)seg_g_far_f32(ax, ay, bx, by, dx, dy);
+            }
+            const double *lr = lam + (size_t)kk * g;
 #pragma unroll
-        for (int n = 0; n < MAXG; ++n)
-            if (n < g) acc[n] += G * lr[n];
+            for (int n = 0; n < MAXG; ++n)
+                if (n < g) acc[n] += G * lr[n];
+        }
+    if (halves == 2) {
+#pragma unroll
+        for (int n = 0; n < MAXG; ++n) acc[n] += __shfl_down_sync(0xffffffffu, acc[n], 16);
     }
+    if (!valid || part != 0) return;
     double *row = blocks + ((size_t)j * g + m) * g;
 #pragma unroll
     for (int n = 0; n < MAXG; ++n)

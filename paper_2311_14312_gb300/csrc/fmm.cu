@@ -25,6 +25,10 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "evalnodes.cuh"
@@ -258,6 +262,25 @@ void build_base_tables(int p, std::vector<cd> &base) {
                 base[(size_t)b * P1 * P1 + k * P1 + l] = v;
             }
     }
+}
+
+// The tables of an expansion order, built once per process and kept (they
+// depend on p alone; entries are never removed, so references stay valid).
+struct OrderTables {
+    std::vector<cd> m2m, l2l, m2l, base;
+};
+const OrderTables &order_tables(int p) {
+    static std::mutex mu;
+    static std::map<int, std::unique_ptr<OrderTables>> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    std::unique_ptr<OrderTables> &t = cache[p];
+    if (!t) {
+        std::unique_ptr<OrderTables> n(new OrderTables());
+        build_tables(p, n->m2m, n->l2l, n->m2l);
+        build_base_tables(p, n->base);
+        t = std::move(n);
+    }
+    return *t;
 }
 
 template <typename T>
@@ -656,8 +679,88 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         I.build_ms[i] = std::chrono::duration<double, std::milli>(t - t_prev).count();
         t_prev = t;
     };
-    if (!build_quadtree_device(D.seg.ptr, G.seg_xy, opt.domain, opt.leaf_size, opt.max_depth, I.tree, st, err))
+    // Both preconditioner levels depend on the discretisation alone: a host
+    // thread plans the coarse level and enqueues the device work of both
+    // levels on a stream of their own, which runs beside the tree build and
+    // the schedules here; the build waits for it before the stored
+    // coefficients.  Meanwhile frees of device memory on this thread are
+    // deferred (cudaFree would wait for that stream too).  On an early
+    // return the guard joins the thread and drains the stream.
+    FreeDefer defer;
+    struct Overlap {
+        std::thread th;
+        cudaStream_t drain = nullptr;
+        ~Overlap() {
+            if (th.joinable()) th.join();
+            if (drain) cudaStreamSynchronize(drain);
+        }
+    } ov;
+    cudaError_t pre_err = cudaSuccess;
+    bool pre_oom = false;
+    {
+        // the preconditioner's stream at the lowest priority and the tree's
+        // at the highest: the tree build's short kernels, each waited for by
+        // the host, are not queued behind the preconditioner's blocks
+        cudaError_t e;
+        int prio_lo = 0, prio_hi = 0;
+        cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+        if (!I.pre_stream &&
+            (e = cudaStreamCreateWithPriority(&I.pre_stream, cudaStreamNonBlocking, prio_lo)) != cudaSuccess) {
+            err = std::string("fmm stream: ") + cudaGetErrorString(e);
+            return DC_ERR_CUDA;
+        }
+        if (!I.tree_stream &&
+            (e = cudaStreamCreateWithPriority(&I.tree_stream, cudaStreamNonBlocking, prio_hi)) != cudaSuccess) {
+            err = std::string("fmm stream: ") + cudaGetErrorString(e);
+            return DC_ERR_CUDA;
+        }
+        if (!I.pre_ev && (e = cudaEventCreateWithFlags(&I.pre_ev, cudaEventDisableTiming)) != cudaSuccess) {
+            err = std::string("fmm event: ") + cudaGetErrorString(e);
+            return DC_ERR_CUDA;
+        }
+        // the discretisation's device copy is complete on st before the
+        // preconditioner's stream reads it
+        if ((e = cudaEventRecord(I.pre_ev, st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(I.pre_stream, I.pre_ev, 0)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(I.tree_stream, I.pre_ev, 0)) != cudaSuccess) {
+            err = std::string("fmm event: ") + cudaGetErrorString(e);
+            return DC_ERR_CUDA;
+        }
+        int dev = 0;
+        cudaGetDevice(&dev);
+        auto pre = [&I, &G, &D, &opt, &pre_err, &pre_oom, dev] {
+            try {
+                cudaError_t r = cudaSetDevice(dev);
+                if (r == cudaSuccess && !I.render_only) {
+                    I.coarse.plan(G, opt.coarse_max);
+                    r = I.coarse.launch(D, I.pre_stream);
+                }
+                if (r == cudaSuccess) r = I.pinv.alloc((size_t)D.n_panels * D.g * D.g);
+                if (r == cudaSuccess) r = I.pinfo.alloc((size_t)D.n_panels);
+                if (r == cudaSuccess) r = launch_panel_block_inverse(D, I.pinv.ptr, I.pinfo.ptr, I.pre_stream);
+                pre_err = r;
+            } catch (...) {
+                pre_oom = true;
+            }
+        };
+        ov.drain = I.pre_stream;
+        try {
+            ov.th = std::thread(pre);
+        } catch (...) {
+            pre();   // no thread: enqueue from here
+        }
+    }
+    if (!build_quadtree_device(D.seg.ptr, G.seg_xy, opt.domain, opt.leaf_size, opt.max_depth, I.tree,
+                               I.tree_stream, err))
         return DC_ERR_GEOMETRY;
+    {   // later work on st follows the tree's
+        cudaError_t e;
+        if ((e = cudaEventRecord(I.pre_ev, I.tree_stream)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(st, I.pre_ev, 0)) != cudaSuccess) {
+            err = std::string("fmm event: ") + cudaGetErrorString(e);
+            return DC_ERR_CUDA;
+        }
+    }
     if (I.P1 > 32) {
         err = "FMM forms support expansion orders p <= 31";
         return DC_ERR_UNSUPPORTED;
@@ -745,8 +848,15 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     // node targets sorted by leaf
     const int N = G.n_nodes();
     std::vector<int> leaf_of(N), cnt(nC, 0);
+    // Tree::locate with the cell centres read from cc (the same values)
+    auto locate = [&](double x, double y) {
+        if (!(x >= T.x0 && x < T.x0 + T.w0 && y >= T.y0 && y < T.y0 + T.w0)) return -1;
+        int c = 0;
+        while (T.child0[c] >= 0) c = T.child0[c] + (x >= cc[2 * c] ? 1 : 0) + (y >= cc[2 * c + 1] ? 2 : 0);
+        return c;
+    };
     for (int i = 0; i < N; ++i) {
-        int lf = T.locate(G.node_xy[2 * i], G.node_xy[2 * i + 1]);
+        int lf = locate(G.node_xy[2 * i], G.node_xy[2 * i + 1]);
         if (lf < 0) {
             err = "internal error: node outside the quadtree root";
             return DC_ERR_GEOMETRY;
@@ -900,14 +1010,12 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     I.n_nt_items4 = int(items4.size());
     I.near_total = near_total;
     I.far_blocks = far_blocks;
-    std::vector<cd> m2m, l2l, m2l, base;
-    build_tables(I.p, m2m, l2l, m2l);
-    build_base_tables(I.p, base);
+    const OrderTables &tab = order_tables(I.p);
+    const std::vector<cd> &m2m = tab.m2m, &l2l = tab.l2l, &m2l = tab.m2l, &base = tab.base;
     const int p_inner = opt.p_inner > 0 ? std::min(opt.p_inner, I.p) : std::min(I.p, 12);
     I.P1i = p_inner + 1;
-    std::vector<cd> m2mi, l2li, m2li, basei;
-    build_tables(p_inner, m2mi, l2li, m2li);
-    build_base_tables(p_inner, basei);
+    const OrderTables &tabi = order_tables(p_inner);
+    const std::vector<cd> &m2mi = tabi.m2m, &l2li = tabi.l2l, &basei = tabi.base;
     // the 56 (base, rotation, conjugation) variants in full for the
     // low-order M2L: F[b + 7 r + 28 cj][l][k] = conj^cj(B_b[k][l]) i^(-r (k + l))
     std::vector<cd> fulli(56 * (size_t)I.P1i * I.P1i);
@@ -1130,21 +1238,30 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     // the other channel of interp output must be defined (zero) for passes
     cudaMemsetAsync(I.sbar.ptr, 0, I.sbar.bytes(), st);
     cudaMemsetAsync(I.mbar.ptr, 0, I.mbar.bytes(), st);
-    // block-Jacobi preconditioner over panels and refinement buffers
-    if ((e = I.pinv.alloc((size_t)D.n_panels * D.g * D.g)) != cudaSuccess ||
-        (e = I.pinfo.alloc((size_t)D.n_panels)) != cudaSuccess ||
-        (e = I.ir_r.alloc((size_t)3 * D.N)) != cudaSuccess ||
-        (e = I.ir_d.alloc((size_t)3 * D.N)) != cudaSuccess ||
-        (e = I.ir_t.alloc((size_t)3 * D.N)) != cudaSuccess ||
-        (e = launch_panel_block_inverse(D, I.pinv.ptr, I.pinfo.ptr, st)) != cudaSuccess) {
+    // refinement buffers
+    if ((e = I.ir_r.alloc((size_t)3 * D.N)) != cudaSuccess || (e = I.ir_d.alloc((size_t)3 * D.N)) != cudaSuccess ||
+        (e = I.ir_t.alloc((size_t)3 * D.N)) != cudaSuccess) {
+        err = std::string("fmm allocation: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
+    }
+    phase(1);   // schedules, node items, uploads
+    // the two-level preconditioner (panel blocks + coarse space of panel
+    // constants): wait for its thread and stream, then check both levels
+    if (ov.th.joinable()) ov.th.join();
+    if (pre_oom || pre_err != cudaSuccess) {
+        err = pre_oom ? std::string("fmm preconditioner: host allocation failed")
+                      : std::string("fmm preconditioner: ") + cudaGetErrorString(pre_err);
+        return (pre_oom || pre_err == cudaErrorMemoryAllocation) ? DC_ERR_OOM : DC_ERR_CUDA;
+    }
+    if ((e = I.render_only ? cudaStreamSynchronize(I.pre_stream) : I.coarse.finish(I.pre_stream)) != cudaSuccess) {
         err = std::string("fmm preconditioner: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
     }
+    ov.drain = nullptr;
+    defer.flush();
     {
         std::vector<int> info(D.n_panels);
-        e = cudaMemcpyAsync(info.data(), I.pinfo.ptr, info.size() * sizeof(int),
-                            cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        e = cudaMemcpy(info.data(), I.pinfo.ptr, info.size() * sizeof(int), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) {
             err = cudaGetErrorString(e);
             return DC_ERR_CUDA;
@@ -1154,12 +1271,6 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
                 err = "build_tree: singular self-interaction block on panel " + std::to_string(j);
                 return DC_ERR_GEOMETRY;
             }
-    }
-    // two-level preconditioner (panel blocks + coarse space of panel constants)
-    phase(1);   // schedules, node items, uploads
-    if (!I.render_only && (e = I.coarse.build(G, D, st, opt.coarse_max)) != cudaSuccess) {
-        err = std::string("fmm coarse preconditioner: ") + cudaGetErrorString(e);
-        return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
     }
     cudaFuncSetAttribute(passes::m2l_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)passes::m2l_ff_smem(I.P1));

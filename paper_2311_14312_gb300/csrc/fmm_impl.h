@@ -216,6 +216,12 @@ struct Fmm::Impl {
     // list-4 P2L beside the M2M / M2L chain)
     cudaStream_t side = nullptr;
     cudaEvent_t fork_ev[2] = {nullptr, nullptr};
+    // stream of the preconditioner's build, beside the schedules, and the
+    // event it starts from
+    cudaStream_t pre_stream = nullptr;
+    cudaEvent_t pre_ev = nullptr;
+    // stream of the tree build (highest priority)
+    cudaStream_t tree_stream = nullptr;
     bool graph_split = true;   // capture the branches in parallel
     bool render_only = false;  // no preconditioner, no node near-field coefficients
     cudaGraph_t g32 = nullptr;
@@ -240,6 +246,9 @@ struct Fmm::Impl {
         if (g32) cudaGraphDestroy(g32);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         if (side) cudaStreamDestroy(side);
+        if (pre_stream) cudaStreamDestroy(pre_stream);
+        if (tree_stream) cudaStreamDestroy(tree_stream);
+        if (pre_ev) cudaEventDestroy(pre_ev);
         for (auto &ev : fork_ev)
             if (ev) cudaEventDestroy(ev);
     }

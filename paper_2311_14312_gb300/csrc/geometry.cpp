@@ -12,6 +12,8 @@
 // holds it is integrated with the singular rules Eq. 52 / Eq. 53 (App. C.1),
 // both segments when the node sits on a vertex.
 #include <algorithm>
+#include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -48,7 +50,7 @@ struct Cubic {
         double d2x = c[6] - c[4], d2y = c[7] - c[5];
         double x = 3.0 * (s * s * d0x + 2.0 * s * t * d1x + t * t * d2x);
         double y = 3.0 * (s * s * d0y + 2.0 * s * t * d1y + t * t * d2y);
-        return std::hypot(x, y);
+        return std::sqrt(x * x + y * y);   // |B'| of a drawing's curves: far from overflow
     }
 };
 
@@ -223,30 +225,41 @@ dc_status discretise(int n_curves, const double *ctrl, const int *panel_ptr,
         for (int m = 0; m < g; ++m) out.lambda[size_t(k) * g + m] = (bw[m] / (xb - gx[m])) / den;
     }
 
-    // curves are independent: host threads take contiguous ranges of them
-    // (each writes only its curves' nodes and segments), then the bounding
-    // boxes and the first error in curve order are merged
+    // curves are independent: host threads take them one at a time from a
+    // shared counter (each writes only its curves' nodes and segments), then
+    // the bounding boxes and the error of the first failing curve are merged
     struct Part {
         double bb[4] = {1e300, 1e300, -1e300, -1e300};
         dc_status st = DC_OK;
+        int err_curve = INT_MAX;
         std::string err;
     };
-    auto work = [&](int c0, int c1, Part &pt) {
+    std::atomic<int> next_curve(0);
+    auto work = [&](Part &pt) {
         std::vector<double> vx(s + 1), vy(s + 1);
         double *bb = pt.bb;
-        for (int ci = c0; ci < c1; ++ci) {
+        for (int ci = next_curve.fetch_add(1); ci < n_curves; ci = next_curve.fetch_add(1)) {
+            // a failing curve records its error and skips its other panels;
+            // the smallest failing curve over all threads is reported
+            auto fail = [&](const std::string &msg) {
+                if (ci < pt.err_curve) {
+                    pt.err_curve = ci;
+                    pt.err = msg;
+                    pt.st = DC_ERR_GEOMETRY;
+                }
+            };
             Cubic cu;
             std::memcpy(cu.c, ctrl + 8 * size_t(ci), sizeof(cu.c));
             ArcLength al(&cu);
             double L = al.total();
             out.curve_len[ci] = L;
             if (!(L > 0.0)) {
-                pt.err = "build_tree: curve " + std::to_string(ci) + " has zero length";
-                pt.st = DC_ERR_GEOMETRY;
-                return;
+                fail("build_tree: curve " + std::to_string(ci) + " has zero length");
+                continue;
             }
+            bool bad = false;
             const double *col = colours + 12 * size_t(ci);
-            for (int pj = panel_ptr[ci]; pj < panel_ptr[ci + 1]; ++pj) {
+            for (int pj = panel_ptr[ci]; pj < panel_ptr[ci + 1] && !bad; ++pj) {
                 double fa = panel_start[pj];
                 double fb = (pj + 1 < panel_ptr[ci + 1]) ? panel_start[pj + 1] : 1.0;
                 double sa = fa * L, sb = fb * L, h = (sb - sa) / s;
@@ -266,9 +279,9 @@ dc_status discretise(int n_curves, const double *ctrl, const int *panel_ptr,
                     q[3] = vy[k + 1];
                     double chord = std::hypot(vx[k + 1] - vx[k], vy[k + 1] - vy[k]);
                     if (!(chord > 0.0)) {
-                        pt.err = "build_tree: zero-length segment on curve " + std::to_string(ci);
-                        pt.st = DC_ERR_GEOMETRY;
-                        return;
+                        fail("build_tree: zero-length segment on curve " + std::to_string(ci));
+                        bad = true;
+                        break;
                     }
                     out.seg_w[sid] = h / chord;
                     bb[0] = std::min(bb[0], std::min(q[0], q[2]));
@@ -276,7 +289,7 @@ dc_status discretise(int n_curves, const double *ctrl, const int *panel_ptr,
                     bb[2] = std::max(bb[2], std::max(q[0], q[2]));
                     bb[3] = std::max(bb[3], std::max(q[1], q[3]));
                 }
-                for (int m = 0; m < g; ++m) {
+                for (int m = 0; m < g && !bad; ++m) {
                     size_t nid = size_t(pj) * g + m;
                     double pos = 0.5 * (gx[m] + 1.0) * s;   // in segment units
                     int k = std::min(s - 1, int(std::floor(pos)));
@@ -307,18 +320,19 @@ dc_status discretise(int n_curves, const double *ctrl, const int *panel_ptr,
     std::vector<Part> parts(nt);
     {
         std::vector<std::thread> pool;
-        for (int t = 1; t < nt; ++t)
-            pool.emplace_back(work, int((long long)n_curves * t / nt), int((long long)n_curves * (t + 1) / nt),
-                              std::ref(parts[t]));
-        work(0, int((long long)n_curves / nt), parts[0]);
+        for (int t = 1; t < nt; ++t) pool.emplace_back(work, std::ref(parts[t]));
+        work(parts[0]);
         for (auto &th : pool) th.join();
+    }
+    const Part *first_bad = nullptr;
+    for (const Part &pt : parts)
+        if (pt.st != DC_OK && (!first_bad || pt.err_curve < first_bad->err_curve)) first_bad = &pt;
+    if (first_bad) {
+        err = first_bad->err;
+        return first_bad->st;
     }
     double bb[4] = {1e300, 1e300, -1e300, -1e300};
     for (const Part &pt : parts) {
-        if (pt.st != DC_OK) {
-            err = pt.err;
-            return pt.st;
-        }
         bb[0] = std::min(bb[0], pt.bb[0]);
         bb[1] = std::min(bb[1], pt.bb[1]);
         bb[2] = std::max(bb[2], pt.bb[2]);

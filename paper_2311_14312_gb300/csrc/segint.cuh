@@ -41,6 +41,27 @@ __device__ __forceinline__ void seg_gf_f64(double qx, double qy, double x1, doub
     F = -w * kInv2Pi * phi;
 }
 
+// int G dS / w of a segment far from q (at least a few chord lengths), in
+// FP32 from a = p1 - q, b = p2 - q and d = p2 - p1 taken in FP64 and then
+// rounded: the terms are smooth there.
+__device__ __forceinline__ float seg_g_far_f32(double ax, double ay, double bx, double by, double dx, double dy) {
+    const float fax = (float)ax, fay = (float)ay, fbx = (float)bx, fby = (float)by;
+    const float fdx = (float)dx, fdy = (float)dy;
+    const float c2 = fdx * fdx + fdy * fdy, ic = rsqrtf(c2), c = c2 * ic;
+    const float cr = fax * fby - fay * fbx;
+    const float phi = atan2f(cr, fax * fbx + fay * fby);
+    const float la = (fax * fdx + fay * fdy) * ic * logf(fax * fax + fay * fay);
+    const float lb = (fbx * fdx + fby * fdy) * ic * logf(fbx * fbx + fby * fby);
+    return -(float)kInv2Pi * (0.5f * (lb - la) - c + cr * ic * phi);
+}
+
+// Whether segment (a, b, d as above) is within r chord lengths of q.
+__device__ __forceinline__ bool seg_is_near(double ax, double ay, double bx, double by, double dx, double dy,
+                                            double r) {
+    const double h2 = r * r * (dx * dx + dy * dy);
+    return ax * ax + ay * ay < h2 || bx * bx + by * by < h2;
+}
+
 // Unweighted parts of the same rule: ilog = int log|p - q| dS over the chord
 // and phi = subtended angle (0 on the own segment).
 __device__ __forceinline__ void seg_ilog_phi_f64(double qx, double qy, double x1, double y1,
