@@ -327,36 +327,45 @@ __device__ __forceinline__ void dot2_step(float &hi, float &lo, float w, float2 
 }
 
 // y = Ac^-1 s (fixed-order reduction); pan[j] = (c_j, k l_j y_j for
-// channels 0, 1), pan2[j] = k l_j y_j for channel 2, k = kMonoLog2 (FP32)
-__global__ void __launch_bounds__(128) coarse_solve_kernel(const float *__restrict__ Ainv, int n_pad, int P,
-                                                           const float2 *__restrict__ s,
-                                                           const float *__restrict__ plen32,
-                                                           const float2 *__restrict__ c32,
-                                                           double *__restrict__ y, float4 *__restrict__ pan,
-                                                           float *__restrict__ pan2) {
-    // one block of 128 threads per row; compensated (float-float) sums: M
-    // amplifies by ~1e4-1e5, and its rounding must stay well below the FP32
-    // operator's own error
-    __shared__ double red[4][3];
-    const int i = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const float *row = Ainv + (size_t)i * n_pad;
+// channels 0, 1), pan2[j] = k l_j y_j for channel 2, k = kMonoLog2 (FP32).
+// One warp per row, kSolveRows rows per block: the vector s is staged in
+// shared memory kSolveCols columns at a time and serves all of the block's
+// rows.  Compensated (float-float) sums: M amplifies by ~1e4-1e5, and its
+// rounding must stay well below the FP32 operator's own error.
+constexpr int kSolveRows = 8, kSolveCols = 2048;
+__global__ void __launch_bounds__(32 * kSolveRows) coarse_solve_kernel(const float *__restrict__ Ainv, int n_pad, int P,
+                                                                       const float2 *__restrict__ s,
+                                                                       const float *__restrict__ plen32,
+                                                                       const float2 *__restrict__ c32,
+                                                                       double *__restrict__ y,
+                                                                       float4 *__restrict__ pan,
+                                                                       float *__restrict__ pan2) {
+    __shared__ float2 ss[3 * kSolveCols];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * kSolveRows + w;
+    const float *row = Ainv + (size_t)min(i, P - 1) * n_pad;
     float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
-    for (int j0 = t; j0 < P; j0 += 4 * 128) {
-        // four columns' loads in flight per thread (a missing column adds exact zeros)
-        float wv[4];
-        float2 xv[4][3];
+    for (int c0 = 0; c0 < P; c0 += kSolveCols) {
+        const int cn = min(kSolveCols, P - c0);
+        __syncthreads();
+        for (int u = threadIdx.x; u < 3 * cn; u += 32 * kSolveRows) ss[u] = s[3 * (size_t)c0 + u];
+        __syncthreads();
+        for (int jj = lane; jj < cn; jj += 4 * 32) {
+            // four columns' loads in flight per lane (a missing column adds exact zeros)
+            float wv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int j = j0 + 128 * u;
-            const bool ok = j < P;
-            wv[u] = ok ? row[j] : 0.f;
-            for (int c = 0; c < 3; ++c) xv[u][c] = ok ? s[3 * j + c] : make_float2(0.f, 0.f);
-        }
+            for (int u = 0; u < 4; ++u) {
+                const int j = jj + 32 * u;
+                wv[u] = j < cn ? row[c0 + j] : 0.f;
+            }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            dot2_step(h0, l0, wv[u], xv[u][0]);
-            dot2_step(h1, l1, wv[u], xv[u][1]);
-            dot2_step(h2, l2, wv[u], xv[u][2]);
+            for (int u = 0; u < 4; ++u) {
+                const int j = jj + 32 * u;
+                if (j >= cn) break;
+                dot2_step(h0, l0, wv[u], ss[3 * j]);
+                dot2_step(h1, l1, wv[u], ss[3 * j + 1]);
+                dot2_step(h2, l2, wv[u], ss[3 * j + 2]);
+            }
         }
     }
     double a0 = (double)h0 + (double)l0, a1 = (double)h1 + (double)l1, a2 = (double)h2 + (double)l2;
@@ -365,22 +374,14 @@ __global__ void __launch_bounds__(128) coarse_solve_kernel(const float *__restri
         a1 += __shfl_xor_sync(0xffffffffu, a1, off);
         a2 += __shfl_xor_sync(0xffffffffu, a2, off);
     }
-    if (lane == 0) {
-        red[w][0] = a0;
-        red[w][1] = a1;
-        red[w][2] = a2;
-    }
-    __syncthreads();
-    if (t == 0) {
-        double v[3];
-        for (int c = 0; c < 3; ++c) {
-            v[c] = red[0][c] + red[1][c] + red[2][c] + red[3][c];
-            y[3 * i + c] = v[c];
-        }
+    if (lane == 0 && i < P) {
+        y[3 * i + 0] = a0;
+        y[3 * i + 1] = a1;
+        y[3 * i + 2] = a2;
         const float k = kMonoLog2 * plen32[i];
         const float2 c = c32[i];
-        pan[i] = make_float4(c.x, c.y, k * (float)v[0], k * (float)v[1]);
-        pan2[i] = k * (float)v[2];
+        pan[i] = make_float4(c.x, c.y, k * (float)a0, k * (float)a1);
+        pan2[i] = k * (float)a2;
     }
 }
 
@@ -764,8 +765,8 @@ cudaError_t TwoLevel::apply(const double *inv, const double *v, double *w, cudaS
     const int P = P_, g = g_, N = P * g;
     if (K_ > 1) return cudaErrorNotSupported;   // aggregated: apply_stage1 / apply_stage2
     restrict_kernel<<<(3 * P + 255) / 256, 256, 0, st>>>(v, P, g, s_.ptr);
-    coarse_solve_kernel<<<P, 128, 0, st>>>(Ainv_.ptr, n_pad_, P, s_.ptr, plen32_.ptr, c32_.ptr, y_.ptr, pan_.ptr,
-                                          pan2_.ptr);
+    coarse_solve_kernel<<<(P + kSolveRows - 1) / kSolveRows, 32 * kSolveRows, 0, st>>>(
+        Ainv_.ptr, n_pad_, P, s_.ptr, plen32_.ptr, c32_.ptr, y_.ptr, pan_.ptr, pan2_.ptr);
     const int per_block = kMonoThreads * kMonoNodes;
     monopole_kernel<<<dim3((N + per_block - 1) / per_block, kSplit), kMonoThreads, 0, st>>>(q32_.ptr, pan_.ptr,
                                                                                          pan2_.ptr, P, N, part_.ptr);
@@ -778,8 +779,8 @@ cudaError_t TwoLevel::apply(const double *inv, const double *v, double *w, cudaS
 cudaError_t TwoLevel::apply_stage1(const double *v, double *py, cudaStream_t st) {
     const int N = P_ * g_;
     restrict_agg_kernel<<<(3 * nA_ + 255) / 256, 256, 0, st>>>(v, pagg_.ptr, perm_.ptr, nA_, g_, s_.ptr);
-    coarse_solve_kernel<<<nA_, 128, 0, st>>>(Ainv_.ptr, n_pad_, nA_, s_.ptr, plen32_.ptr, c32_.ptr, y_.ptr, pan_.ptr,
-                                            pan2_.ptr);
+    coarse_solve_kernel<<<(nA_ + kSolveRows - 1) / kSolveRows, 32 * kSolveRows, 0, st>>>(
+        Ainv_.ptr, n_pad_, nA_, s_.ptr, plen32_.ptr, c32_.ptr, y_.ptr, pan_.ptr, pan2_.ptr);
     spread_agg_kernel<<<(3 * N + 255) / 256, 256, 0, st>>>(y_.ptr, agg_of_.ptr, N, g_, py);
     note_launch(3);
     return cudaGetLastError();

@@ -688,10 +688,11 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     // return the guard joins the thread and drains the stream.
     FreeDefer defer;
     struct Overlap {
-        std::thread th;
+        std::thread th, th32;   // the preconditioner's, the FP32 form's host arrays'
         cudaStream_t drain = nullptr;
         ~Overlap() {
             if (th.joinable()) th.join();
+            if (th32.joinable()) th32.join();
             if (drain) cudaStreamSynchronize(drain);
         }
     } ov;
@@ -945,6 +946,24 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     };
     std::vector<int> am2l, ap2l, al2l, aw, nm2l, np2l, nl2l, nw;
     phase(0);   // quadtree, lists, tables, multi-level M2M chunks
+    // the FP32 form's host arrays (tree and discretisation only) on a helper
+    // thread while the schedules, preconditioner and coefficients are built
+    Impl::Prep32 prep;
+    bool prep_failed = false;
+    if (I.fp32) {
+        auto run = [&T, &G, &prep, &prep_failed] {
+            try {
+                Impl::prep32(T, G, prep);
+            } catch (...) {
+                prep_failed = true;
+            }
+        };
+        try {
+            ov.th32 = std::thread(run);
+        } catch (...) {
+            run();
+        }
+    }
     make_sched(I.sched_all, false, am2l, ap2l, al2l, aw);
     make_sched(I.sched_nodes, true, nm2l, np2l, nl2l, nw);
     // rows of the stored P2L coefficients: the pieces of each list-4 cell of
@@ -1295,7 +1314,12 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
     }
     phase(4);   // near / far coefficients
-    dc_status r = I.fp32 ? I.build32(G, st, err) : DC_OK;
+    if (ov.th32.joinable()) ov.th32.join();
+    if (prep_failed) {
+        err = "fmm32 build: host allocation failed";
+        return DC_ERR_OOM;
+    }
+    dc_status r = I.fp32 ? I.build32(G, prep, txy, start, cnt, st, err) : DC_OK;
     phase(5);   // FP32 form
     return r;
 }
@@ -1613,12 +1637,9 @@ dc_status Fmm::render_viewports(const VpDev *vpl, int n_vp, const double *sbar, 
         I.render_flops += I.plan_flops;
         return launch_render(I, I.plan_tiles, rgb, rgb_dtype, rgb8, sbar, mbar, st, err);
     }
+    // the plan is built here while the stream runs the passes before the
+    // render; its upload is ordered after them on the stream
     I.plan_valid = false;
-    e = cudaStreamSynchronize(st);   // tile and viewport buffers are reused
-    if (e != cudaSuccess) {
-        err = cudaGetErrorString(e);
-        return DC_ERR_CUDA;
-    }
     std::vector<Tile> tiles;
     std::vector<double> cost;   // estimated flops per tile
     int TW = kEvalTile, TH = kEvalTile;
@@ -1652,18 +1673,31 @@ dc_status Fmm::render_viewports(const VpDev *vpl, int n_vp, const double *sbar, 
                 }
         }
     }
-    {   // the most expensive tiles first (the persistent launch takes them in order)
-        std::vector<int> ord(tiles.size());
-        for (size_t i = 0; i < ord.size(); ++i) ord[i] = int(i);
-        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    {   // the most expensive tiles first (the persistent launch takes them in
+        // order): a counting sort on the cost's binary logarithm in steps of
+        // 1/16 octave, stable within a step (ties keep the generation order)
+        constexpr int kSub = 16, kBins = 64 * kSub;
+        std::vector<int> bin(tiles.size()), cnt(kBins + 1, 0);
+        for (size_t i = 0; i < tiles.size(); ++i) {
+            int e2 = 0;
+            const double f = std::frexp(std::max(cost[i], 1.0), &e2);   // cost = f 2^e2, f in [0.5, 1)
+            const int b = std::min(kBins - 1, std::max(0, e2 * kSub + int((2.0 * f - 1.0) * kSub)));
+            bin[i] = kBins - 1 - b;   // descending cost
+            cnt[bin[i] + 1]++;
+        }
+        for (int b = 0; b < kBins; ++b) cnt[b + 1] += cnt[b];
         std::vector<Tile> sorted(tiles.size());
-        for (size_t i = 0; i < ord.size(); ++i) sorted[i] = tiles[ord[i]];
+        for (size_t i = 0; i < tiles.size(); ++i) sorted[cnt[bin[i]]++] = tiles[i];
         tiles.swap(sorted);
     }
     I.render_pairs += pairs;
     std::vector<VpDev> vv(vpl, vpl + n_vp);
-    if (!tiles.empty() &&
-        ((e = upload(I.tiles, tiles, st)) != cudaSuccess || (e = upload(I.vps, vv, st)) != cudaSuccess)) {
+    auto put = [&](auto &buf, const auto &v) -> cudaError_t {   // reuses the buffer when it is large enough
+        cudaError_t r = buf.ensure(std::max<size_t>(v.size(), 1));
+        if (r != cudaSuccess || v.empty()) return r;
+        return cudaMemcpyAsync(buf.ptr, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice, st);
+    };
+    if (!tiles.empty() && ((e = put(I.tiles, tiles)) != cudaSuccess || (e = put(I.vps, vv)) != cudaSuccess)) {
         err = cudaGetErrorString(e);
         return DC_ERR_CUDA;
     }

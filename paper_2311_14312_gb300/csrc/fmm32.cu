@@ -616,61 +616,64 @@ DevTree32 Fmm::Impl::dt32() const {
     return t;
 }
 
-dc_status Fmm::Impl::build32(const Geometry &G, cudaStream_t st, std::string &err) {
-    const Tree &T = tree;
+void Fmm::Impl::prep32(const Tree &T, const Geometry &G, Prep32 &o) {
     const int nC = T.n_cells();
-    std::vector<float> iw(nC), logw(nC);
-    std::vector<double> ccx(nC), ccy(nC);
+    o.iw.resize(nC);
+    o.logw.resize(nC);
+    o.ccx.resize(nC);
+    o.ccy.resize(nC);
     for (int c = 0; c < nC; ++c) {
         double w = T.width(c);
-        iw[c] = (float)(1.0 / w);
-        logw[c] = (float)std::log(w);
-        ccx[c] = T.cx(c);
-        ccy[c] = T.cy(c);
+        o.iw[c] = (float)(1.0 / w);
+        o.logw[c] = (float)std::log(w);
+        o.ccx[c] = T.cx(c);
+        o.ccy[c] = T.cy(c);
     }
     const size_t np = T.pc_seg.size();
-    std::vector<float4> pcf(np), pch(np), pcl(np);
-    std::vector<float> pwf(np), plf(np);
+    o.pcf.resize(np);
+    o.pch.resize(np);
+    o.pcl.resize(np);
+    o.pwf.resize(np);
+    o.plf.resize(np);
     std::vector<int> owner(np, -1);
     for (int c = 0; c < nC; ++c)
         for (int i = T.piece_start[c]; i < T.piece_start[c] + T.piece_count[c]; ++i) owner[i] = c;
     for (size_t i = 0; i < np; ++i) {
         const double *q = &T.pc_xy[4 * i];
         int c = owner[i];
-        pcf[i] = make_float4((float)(q[0] - ccx[c]), (float)(q[1] - ccy[c]), (float)(q[2] - ccx[c]),
-                             (float)(q[3] - ccy[c]));
+        o.pcf[i] = make_float4((float)(q[0] - o.ccx[c]), (float)(q[1] - o.ccy[c]), (float)(q[2] - o.ccx[c]),
+                               (float)(q[3] - o.ccy[c]));
         float h[4], l[4];
         for (int k = 0; k < 4; ++k) {
             h[k] = (float)q[k];
             l[k] = (float)(q[k] - (double)h[k]);
         }
-        pch[i] = make_float4(h[0], h[1], h[2], h[3]);
-        pcl[i] = make_float4(l[0], l[1], l[2], l[3]);
-        pwf[i] = (float)G.seg_w[T.pc_seg[i]];
-        plf[i] = (float)std::hypot(q[2] - q[0], q[3] - q[1]);
+        o.pch[i] = make_float4(h[0], h[1], h[2], h[3]);
+        o.pcl[i] = make_float4(l[0], l[1], l[2], l[3]);
+        o.pwf[i] = (float)G.seg_w[T.pc_seg[i]];
+        o.plf[i] = (float)std::hypot(q[2] - q[0], q[3] - q[1]);
     }
     auto offsets = [&](const std::vector<int> &ptr, const std::vector<int> &idx) {
-        std::vector<float2> o(idx.size());
+        std::vector<float2> v(idx.size());
         for (int c = 0; c + 1 < (int)ptr.size(); ++c)
             for (int e = ptr[c]; e < ptr[c + 1]; ++e)
-                o[e] = make_float2((float)(ccx[idx[e]] - ccx[c]), (float)(ccy[idx[e]] - ccy[c]));
-        return o;
+                v[e] = make_float2((float)(o.ccx[idx[e]] - o.ccx[c]), (float)(o.ccy[idx[e]] - o.ccy[c]));
+        return v;
     };
-    std::vector<float2> uo = offsets(T.u_ptr, T.u_idx), wo = offsets(T.w_ptr, T.w_idx),
-                        xo = offsets(T.x_ptr, T.x_idx);
+    o.uo = offsets(T.u_ptr, T.u_idx);
+    o.wo = offsets(T.w_ptr, T.w_idx);
+    o.xo = offsets(T.x_ptr, T.x_idx);
+}
+
+dc_status Fmm::Impl::build32(const Geometry &G, const Prep32 &pr, const std::vector<double> &nxy,
+                             const std::vector<int> &start, const std::vector<int> &cnt, cudaStream_t st,
+                             std::string &err) {
+    const Tree &T = tree;
+    const int nC = T.n_cells();
+    const size_t np = T.pc_seg.size();
+    const std::vector<double> &ccx = pr.ccx, &ccy = pr.ccy;
     // node targets relative to their leaf; work items of <= 64 targets
     const int N = G.n_nodes();
-    std::vector<double> nxy(2 * size_t(N));
-    std::vector<int> start(nC), cnt(nC);
-    cudaError_t e = cudaMemcpyAsync(nxy.data(), nt_xy.ptr, nxy.size() * sizeof(double),
-                                    cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(start.data(), nt_start.ptr, nC * sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), nt_count.ptr, nC * sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) {
-        err = std::string("fmm32 build: ") + cudaGetErrorString(e);
-        return DC_ERR_CUDA;
-    }
     std::vector<float2> q32(N);
     std::vector<Tile> items;
     for (int c = 0; c < nC; ++c) {
@@ -678,12 +681,13 @@ dc_status Fmm::Impl::build32(const Geometry &G, cudaStream_t st, std::string &er
             q32[j] = make_float2((float)(nxy[2 * j] - ccx[c]), (float)(nxy[2 * j + 1] - ccy[c]));
         for (int j = 0; j < cnt[c]; j += 64) items.push_back({c, start[c] + j, 0, std::min(64, cnt[c] - j), 0});
     }
+    cudaError_t e;
     n_nt_items = int(items.size());
-    if ((e = up(iw32, iw, st)) != cudaSuccess || (e = up(logw32, logw, st)) != cudaSuccess ||
-        (e = up(pc32, pcf, st)) != cudaSuccess || (e = up(pch32, pch, st)) != cudaSuccess ||
-        (e = up(pcl32, pcl, st)) != cudaSuccess || (e = up(pw32, pwf, st)) != cudaSuccess ||
-        (e = up(plen32, plf, st)) != cudaSuccess || (e = up(uoff32, uo, st)) != cudaSuccess ||
-        (e = up(woff32, wo, st)) != cudaSuccess || (e = up(xoff32, xo, st)) != cudaSuccess ||
+    if ((e = up(iw32, pr.iw, st)) != cudaSuccess || (e = up(logw32, pr.logw, st)) != cudaSuccess ||
+        (e = up(pc32, pr.pcf, st)) != cudaSuccess || (e = up(pch32, pr.pch, st)) != cudaSuccess ||
+        (e = up(pcl32, pr.pcl, st)) != cudaSuccess || (e = up(pw32, pr.pwf, st)) != cudaSuccess ||
+        (e = up(plen32, pr.plf, st)) != cudaSuccess || (e = up(uoff32, pr.uo, st)) != cudaSuccess ||
+        (e = up(woff32, pr.wo, st)) != cudaSuccess || (e = up(xoff32, pr.xo, st)) != cudaSuccess ||
         (e = up(nt_q32, q32, st)) != cudaSuccess || (e = up(nt_items, items, st)) != cudaSuccess ||
         (e = to_f32(m2m32, m2m, st)) != cudaSuccess || (e = to_f32(l2l32, l2l, st)) != cudaSuccess ||
         (e = to_f32(m2l32, m2l, st)) != cudaSuccess || (e = to_f32(base32, base64, st)) != cudaSuccess ||

@@ -260,7 +260,20 @@ struct Fmm::Impl {
                        const Schedule &sc);
     cudaError_t apply_nodes(const double *x, double *y, bool single, cudaStream_t st);
     // FP32 (fmm32.cu)
-    dc_status build32(const Geometry &G, cudaStream_t st, std::string &err);
+    // host arrays of the FP32 form that depend on the (pruned) tree and the
+    // discretisation alone: built on a helper thread during the schedules
+    struct Prep32 {
+        std::vector<float> iw, logw;
+        std::vector<double> ccx, ccy;
+        std::vector<float4> pcf, pch, pcl;
+        std::vector<float> pwf, plf;
+        std::vector<float2> uo, wo, xo;
+    };
+    static void prep32(const Tree &T, const Geometry &G, Prep32 &out);
+    // txy, start, cnt: the node targets sorted by leaf and each leaf's range
+    dc_status build32(const Geometry &G, const Prep32 &pr, const std::vector<double> &txy,
+                      const std::vector<int> &start, const std::vector<int> &cnt, cudaStream_t st,
+                      std::string &err);
     cudaError_t passes32(const float *sb, const float *mb, int use_s, int use_m, cudaStream_t st,
                          const Schedule &sc);
     // render preparation of the FP32 form: FP64 passes, FP32 copies of the
