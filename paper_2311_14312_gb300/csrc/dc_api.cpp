@@ -470,8 +470,9 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
     D.s = G.s;
     D.n_panels = G.n_panels;
     cudaStream_t s = ctx->stream;
+    // buffers of the previous drawing are reused when large enough
     auto up = [&](auto &buf, const auto &vec, const char *what) -> dc_status {
-        DC_CK(ctx, buf.alloc(vec.size()), what);
+        DC_CK(ctx, buf.ensure(vec.size()), what);
         DC_CK(ctx,
               cudaMemcpyAsync(buf.ptr, vec.data(), vec.size() * sizeof(vec[0]),
                               cudaMemcpyHostToDevice, s),
@@ -487,12 +488,12 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
     if ((st = up(D.u_plus, G.u_plus, "upload colours")) != DC_OK) return st;
     if ((st = up(D.u_minus, G.u_minus, "upload colours")) != DC_OK) return st;
     size_t n3 = size_t(3) * D.N, s3 = size_t(3) * D.S;
-    DC_CK(ctx, ctx->mu.alloc(n3), "alloc");
-    DC_CK(ctx, ctx->sigma.alloc(n3), "alloc");
-    DC_CK(ctx, ctx->b.alloc(n3), "alloc");
-    DC_CK(ctx, ctx->fmu.alloc(n3), "alloc");
-    DC_CK(ctx, ctx->sbar.alloc(s3), "alloc");
-    DC_CK(ctx, ctx->mbar.alloc(s3), "alloc");
+    DC_CK(ctx, ctx->mu.ensure(n3), "alloc");
+    DC_CK(ctx, ctx->sigma.ensure(n3), "alloc");
+    DC_CK(ctx, ctx->b.ensure(n3), "alloc");
+    DC_CK(ctx, ctx->fmu.ensure(n3), "alloc");
+    DC_CK(ctx, ctx->sbar.ensure(s3), "alloc");
+    DC_CK(ctx, ctx->mbar.ensure(s3), "alloc");
     DC_CK(ctx, dc::launch_mu(D, ctx->mu.ptr, s), "mu");
     lap(1);
     ctx->AG.release();

@@ -680,17 +680,21 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         t_prev = t;
     };
     // Both preconditioner levels depend on the discretisation alone: a host
-    // thread plans the coarse level and enqueues the device work of both
-    // levels on a stream of their own, which runs beside the tree build and
-    // the schedules here; the build waits for it before the stored
+    // thread plans the coarse level during the tree build; once the tree is
+    // built a second one enqueues the device work of both levels on a stream
+    // of their own, which runs beside the rest of the tree phase and the
+    // schedules here (not beside the tree build, whose short kernels the
+    // host waits for one by one); the build waits for it before the stored
     // coefficients.  Meanwhile frees of device memory on this thread are
     // deferred (cudaFree would wait for that stream too).  On an early
-    // return the guard joins the thread and drains the stream.
+    // return the guard joins the threads and drains the stream.
     FreeDefer defer;
     struct Overlap {
-        std::thread th, th32;   // the preconditioner's, the FP32 form's host arrays'
+        // the coarse plan, the preconditioner's launches, the FP32 form's host arrays
+        std::thread th_plan, th, th32;
         cudaStream_t drain = nullptr;
         ~Overlap() {
+            if (th_plan.joinable()) th_plan.join();
             if (th.joinable()) th.join();
             if (th32.joinable()) th32.join();
             if (drain) cudaStreamSynchronize(drain);
@@ -727,15 +731,36 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
             err = std::string("fmm event: ") + cudaGetErrorString(e);
             return DC_ERR_CUDA;
         }
+        auto plan = [&I, &G, &opt, &pre_oom] {   // host work only
+            try {
+                if (!I.render_only) I.coarse.plan(G, opt.coarse_max);
+            } catch (...) {
+                pre_oom = true;
+            }
+        };
+        try {
+            ov.th_plan = std::thread(plan);
+        } catch (...) {
+            plan();
+        }
+    }
+    if (!build_quadtree_device(D.seg.ptr, G.seg_xy, opt.domain, opt.leaf_size, opt.max_depth, I.tree,
+                               I.tree_stream, err))
+        return DC_ERR_GEOMETRY;
+    {   // later work on st follows the tree's; the preconditioner's device work starts
+        cudaError_t e;
+        if ((e = cudaEventRecord(I.pre_ev, I.tree_stream)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(st, I.pre_ev, 0)) != cudaSuccess) {
+            err = std::string("fmm event: ") + cudaGetErrorString(e);
+            return DC_ERR_CUDA;
+        }
+        if (ov.th_plan.joinable()) ov.th_plan.join();
         int dev = 0;
         cudaGetDevice(&dev);
-        auto pre = [&I, &G, &D, &opt, &pre_err, &pre_oom, dev] {
+        auto pre = [&I, &D, &pre_err, &pre_oom, dev] {
             try {
                 cudaError_t r = cudaSetDevice(dev);
-                if (r == cudaSuccess && !I.render_only) {
-                    I.coarse.plan(G, opt.coarse_max);
-                    r = I.coarse.launch(D, I.pre_stream);
-                }
+                if (r == cudaSuccess && !I.render_only && !pre_oom) r = I.coarse.launch(D, I.pre_stream);
                 if (r == cudaSuccess) r = I.pinv.alloc((size_t)D.n_panels * D.g * D.g);
                 if (r == cudaSuccess) r = I.pinfo.alloc((size_t)D.n_panels);
                 if (r == cudaSuccess) r = launch_panel_block_inverse(D, I.pinv.ptr, I.pinfo.ptr, I.pre_stream);
@@ -749,17 +774,6 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
             ov.th = std::thread(pre);
         } catch (...) {
             pre();   // no thread: enqueue from here
-        }
-    }
-    if (!build_quadtree_device(D.seg.ptr, G.seg_xy, opt.domain, opt.leaf_size, opt.max_depth, I.tree,
-                               I.tree_stream, err))
-        return DC_ERR_GEOMETRY;
-    {   // later work on st follows the tree's
-        cudaError_t e;
-        if ((e = cudaEventRecord(I.pre_ev, I.tree_stream)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(st, I.pre_ev, 0)) != cudaSuccess) {
-            err = std::string("fmm event: ") + cudaGetErrorString(e);
-            return DC_ERR_CUDA;
         }
     }
     if (I.P1 > 32) {

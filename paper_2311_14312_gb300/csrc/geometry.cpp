@@ -60,10 +60,11 @@ constexpr int kRule = 16;  // quadrature points per (partial) interval
 struct ArcLength {
     const Cubic *cu;
     double cum[kTab + 1];
-    double rx[kRule], rw[kRule];
+    double rx[kRule], rw[kRule], r8x[8], r8w[8];
 
     explicit ArcLength(const Cubic *c) : cu(c) {
         gauss_legendre_rule(kRule, rx, rw);
+        gauss_legendre_rule(8, r8x, r8w);
         cum[0] = 0.0;
         for (int j = 0; j < kTab; ++j)
             cum[j + 1] = cum[j] + piece(double(j) / kTab, double(j + 1) / kTab);
@@ -79,6 +80,33 @@ struct ArcLength {
         if (t >= 1.0) return cum[kTab];
         int j = std::min(kTab - 1, int(t * kTab));
         return cum[j] + piece(double(j) / kTab, t);
+    }
+    // int_a^b |B'| by an 8-point Gauss-Legendre rule (for short intervals:
+    // between neighbouring points of a panel)
+    double short_piece(double a, double b) const {
+        double h = 0.5 * (b - a), m = 0.5 * (a + b), acc = 0.0;
+        for (int i = 0; i < 8; ++i) acc += r8w[i] * cu->speed(m + h * r8x[i]);
+        return acc * h;
+    }
+    // t with L(t) = T from a nearby point t0 with L(t0) = T0 <= T (T - T0 a
+    // small part of the curve): Newton on T0 + int_t0^t |B'| - T, started one
+    // Newton step from t0, inside the bracket [t0, 1].
+    double invert_from(double t0, double T0, double T) const {
+        const double L = cum[kTab];
+        if (T >= L) return 1.0;
+        if (T <= T0) return t0;   // a node on its segment's start (T0 - T a rounding)
+        double lo = t0, hi = 1.0;
+        double t = std::min(1.0, t0 + (T - T0) / cu->speed(t0));
+        for (int it = 0; it < 60; ++it) {
+            const double f = T0 + short_piece(t0, t) - T;
+            if (std::fabs(f) <= 4e-16 * L) break;
+            if (f > 0) hi = t; else lo = t;
+            double tn = t - f / cu->speed(t);
+            if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+            if (tn == t) break;
+            t = tn;
+        }
+        return t;
     }
     // t with L(t) = T: Newton t <- t - (L(t) - T) / |B'(t)| inside a bracket.
     double invert(double T) const {
@@ -182,7 +210,8 @@ dc_status discretise(int n_curves, const double *ctrl, const int *panel_ptr,
         }
     }
 
-    out = Geometry();
+    // the vectors keep their storage from the previous drawing (every entry
+    // is written below): no fresh pages to fault in on a rebuild
     out.n_curves = n_curves;
     out.n_panels = P;
     out.g = g;
@@ -236,7 +265,7 @@ dc_status discretise(int n_curves, const double *ctrl, const int *panel_ptr,
     };
     std::atomic<int> next_curve(0);
     auto work = [&](Part &pt) {
-        std::vector<double> vx(s + 1), vy(s + 1);
+        std::vector<double> vx(s + 1), vy(s + 1), vt(s + 1);
         double *bb = pt.bb;
         for (int ci = next_curve.fetch_add(1); ci < n_curves; ci = next_curve.fetch_add(1)) {
             // a failing curve records its error and skips its other panels;
@@ -263,11 +292,14 @@ dc_status discretise(int n_curves, const double *ctrl, const int *panel_ptr,
                 double fa = panel_start[pj];
                 double fb = (pj + 1 < panel_ptr[ci + 1]) ? panel_start[pj + 1] : 1.0;
                 double sa = fa * L, sb = fb * L, h = (sb - sa) / s;
+                // panel ends from the table (neighbouring panels share them
+                // bit for bit), interior points each from the one before
                 for (int k = 0; k <= s; ++k) {
                     double t;
                     if (k == 0) t = (fa == 0.0) ? 0.0 : al.invert(sa);
                     else if (k == s) t = (fb == 1.0) ? 1.0 : al.invert(sb);
-                    else t = al.invert(sa + k * h);
+                    else t = al.invert_from(vt[k - 1], sa + (k - 1) * h, sa + k * h);
+                    vt[k] = t;
                     cu.point(t, vx[k], vy[k]);
                 }
                 for (int k = 0; k < s; ++k) {
