@@ -20,11 +20,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <climits>
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -801,10 +803,95 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         ptr.swap(np);
         idx.swap(ni);
     };
-    prune(T.u_ptr, T.u_idx);
-    prune(T.v_ptr, T.v_idx);
-    prune(T.w_ptr, T.w_idx);
-    prune(T.x_ptr, T.x_idx);
+    // Host work of the tree phase on three threads: the lists are pruned on
+    // one, the multi-level M2M chunks (which read no list) are built on
+    // another, while the cell and piece tables and the node order are
+    // built here.  Each guard joins its thread before the variables it
+    // uses go out of scope (on an early return too).
+    struct Joiner {
+        std::thread th;
+        ~Joiner() {
+            if (th.joinable()) th.join();
+        }
+        void run(std::function<void()> f) {
+            try {
+                th = std::thread(f);
+            } catch (...) {
+                f();   // no thread: run here
+            }
+        }
+        void join() {
+            if (th.joinable()) th.join();
+        }
+    };
+    std::atomic<bool> helper_oom(false);
+    auto guarded = [&helper_oom](auto f) {
+        return [f, &helper_oom] {
+            try {
+                f();
+            } catch (...) {
+                helper_oom = true;
+            }
+        };
+    };
+    Joiner j_prune;
+    j_prune.run(guarded([&] {
+        prune(T.u_ptr, T.u_idx);
+        prune(T.v_ptr, T.v_idx);
+        prune(T.w_ptr, T.w_idx);
+        prune(T.x_ptr, T.x_idx);
+    }));
+    // pass schedules: inner cells of level >= 2 with pieces, by level; the
+    // leaf -> ancestor M2M pairs of every inner cell, chunked for the
+    // one-launch upward pass (cells with several chunks get partial slots)
+    std::vector<int> m2m_cells;
+    std::vector<int4> mchunks, mred;
+    std::vector<int> pair_leaf;
+    std::vector<float4> pair_geo;
+    int n_slots = 0;
+    Joiner j_mchunks;
+    j_mchunks.run(guarded([&] {
+        I.m2m_ptr.assign(T.depth + 2, 0);
+        for (int l = 0; l <= T.depth; ++l) {
+            I.m2m_ptr[l] = int(m2m_cells.size());
+            if (l >= 2)
+                for (int c = T.level_start[l]; c < T.level_start[l + 1]; ++c)
+                    if (!T.is_leaf(c) && sub_pieces[c] > 0) m2m_cells.push_back(c);
+        }
+        I.m2m_ptr[T.depth + 1] = int(m2m_cells.size());
+        std::vector<int> stack, lv;
+        for (int a : m2m_cells) {
+            lv.clear();
+            stack.assign(1, a);
+            while (!stack.empty()) {
+                const int c = stack.back();
+                stack.pop_back();
+                if (T.is_leaf(c)) {
+                    if (T.piece_count[c] > 0) lv.push_back(c);
+                } else {
+                    for (int q = 3; q >= 0; --q)
+                        if (sub_pieces[T.child0[c] + q] > 0) stack.push_back(T.child0[c] + q);
+                }
+            }
+            const int beg = int(pair_leaf.size());
+            pair_leaf.insert(pair_leaf.end(), lv.begin(), lv.end());
+            const double wa = T.width(a), ax = T.cx(a), ay = T.cy(a);
+            for (int lf : lv)
+                pair_geo.push_back(make_float4((float)((T.cx(lf) - ax) / wa), (float)((T.cy(lf) - ay) / wa),
+                                               (float)(T.width(lf) / wa), 0.f));
+            const int nch = (int(lv.size()) + passes::kMultiLeaves - 1) / passes::kMultiLeaves;
+            if (nch == 1) {
+                mchunks.push_back(make_int4(a, beg, int(lv.size()), -1));
+            } else if (nch > 1) {
+                mred.push_back(make_int4(a, n_slots, nch, 0));
+                for (int q = 0; q < nch; ++q) {
+                    const int b = beg + q * passes::kMultiLeaves;
+                    const int cnt = std::min(passes::kMultiLeaves, beg + int(lv.size()) - b);
+                    mchunks.push_back(make_int4(a, b, cnt, n_slots++));
+                }
+            }
+        }
+    }));
     std::vector<double> cc(2 * nC), cw(nC), iw64(nC), logw64(nC);
     std::vector<int> quad(nC, 0);
     for (int c = 0; c < nC; ++c) {
@@ -840,22 +927,6 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     int sym_tab[7][7];   // the codes of the offsets in [-3, 3]^2, looked up per entry
     for (int dx = -3; dx <= 3; ++dx)
         for (int dy = -3; dy <= 3; ++dy) sym_tab[dx + 3][dy + 3] = sym_code(dx, dy);
-    std::vector<int> voff(T.v_idx.size()), vcode(T.v_idx.size());
-    long long m2l_cnt = 0;
-    for (int c = 0; c < nC; ++c)
-        for (int e = T.v_ptr[c]; e < T.v_ptr[c + 1]; ++e) {
-            int s = T.v_idx[e];
-            int dx = int(T.ix[c] - T.ix[s]), dy = int(T.iy[c] - T.iy[s]);
-            int code = (std::abs(dx) <= 3 && std::abs(dy) <= 3) ? sym_tab[dx + 3][dy + 3] : -1;
-            if (std::abs(dx) > 3 || std::abs(dy) > 3 || code < 0) {
-                err = "internal error: interaction-list offset out of range";
-                return DC_ERR_GEOMETRY;
-            }
-            voff[e] = offset_code(dx, dy);
-            vcode[e] = code;
-            ++m2l_cnt;
-        }
-    I.m2l_cnt = m2l_cnt;
     std::vector<int> p2m;
     for (int c = 0; c < nC; ++c)
         if (T.is_leaf(c) && T.piece_count[c] > 0) p2m.push_back(c);
@@ -879,59 +950,35 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         leaf_of[i] = lf;
         cnt[lf]++;
     }
+    j_prune.join();
+    if (helper_oom) {
+        err = "fmm build: host allocation failed";
+        return DC_ERR_OOM;
+    }
+    std::vector<int> voff(T.v_idx.size()), vcode(T.v_idx.size());
+    long long m2l_cnt = 0;
+    for (int c = 0; c < nC; ++c)
+        for (int e = T.v_ptr[c]; e < T.v_ptr[c + 1]; ++e) {
+            int s = T.v_idx[e];
+            int dx = int(T.ix[c] - T.ix[s]), dy = int(T.iy[c] - T.iy[s]);
+            int code = (std::abs(dx) <= 3 && std::abs(dy) <= 3) ? sym_tab[dx + 3][dy + 3] : -1;
+            if (std::abs(dx) > 3 || std::abs(dy) > 3 || code < 0) {
+                err = "internal error: interaction-list offset out of range";
+                return DC_ERR_GEOMETRY;
+            }
+            voff[e] = offset_code(dx, dy);
+            vcode[e] = code;
+            ++m2l_cnt;
+        }
+    I.m2l_cnt = m2l_cnt;
     std::vector<int> sub_nodes(cnt);
     for (int c = nC - 1; c >= 0; --c)
         if (!T.is_leaf(c))
             for (int q = 0; q < 4; ++q) sub_nodes[c] += sub_nodes[T.child0[c] + q];
-    // pass schedules
-    std::vector<int> m2m_cells;        // inner cells of level >= 2 with pieces, by level
-    I.m2m_ptr.assign(T.depth + 2, 0);
-    for (int l = 0; l <= T.depth; ++l) {
-        I.m2m_ptr[l] = int(m2m_cells.size());
-        if (l >= 2)
-            for (int c = T.level_start[l]; c < T.level_start[l + 1]; ++c)
-                if (!T.is_leaf(c) && sub_pieces[c] > 0) m2m_cells.push_back(c);
-    }
-    I.m2m_ptr[T.depth + 1] = int(m2m_cells.size());
-    // leaf -> ancestor M2M pairs of every inner cell, chunked for the
-    // one-launch upward pass (cells with several chunks get partial slots)
-    std::vector<int4> mchunks, mred;
-    std::vector<int> pair_leaf;
-    std::vector<float4> pair_geo;
-    int n_slots = 0;
-    {
-        std::vector<int> stack, lv;
-        for (int a : m2m_cells) {
-            lv.clear();
-            stack.assign(1, a);
-            while (!stack.empty()) {
-                const int c = stack.back();
-                stack.pop_back();
-                if (T.is_leaf(c)) {
-                    if (T.piece_count[c] > 0) lv.push_back(c);
-                } else {
-                    for (int q = 3; q >= 0; --q)
-                        if (sub_pieces[T.child0[c] + q] > 0) stack.push_back(T.child0[c] + q);
-                }
-            }
-            const int beg = int(pair_leaf.size());
-            pair_leaf.insert(pair_leaf.end(), lv.begin(), lv.end());
-            const double wa = T.width(a), ax = T.cx(a), ay = T.cy(a);
-            for (int lf : lv)
-                pair_geo.push_back(make_float4((float)((T.cx(lf) - ax) / wa), (float)((T.cy(lf) - ay) / wa),
-                                               (float)(T.width(lf) / wa), 0.f));
-            const int nch = (int(lv.size()) + passes::kMultiLeaves - 1) / passes::kMultiLeaves;
-            if (nch == 1) {
-                mchunks.push_back(make_int4(a, beg, int(lv.size()), -1));
-            } else if (nch > 1) {
-                mred.push_back(make_int4(a, n_slots, nch, 0));
-                for (int q = 0; q < nch; ++q) {
-                    const int b = beg + q * passes::kMultiLeaves;
-                    const int cnt = std::min(passes::kMultiLeaves, beg + int(lv.size()) - b);
-                    mchunks.push_back(make_int4(a, b, cnt, n_slots++));
-                }
-            }
-        }
+    j_mchunks.join();
+    if (helper_oom) {
+        err = "fmm build: host allocation failed";
+        return DC_ERR_OOM;
     }
     I.n_mchunks = int(mchunks.size());
     I.n_mred = int(mred.size());
@@ -986,16 +1033,19 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     std::vector<int> p2l_cnt(nC, 0);
     std::vector<int2> p2l_item;   // (piece, list-4 entry) per row
     long long p2l_rows = 0;
-    for (int c : ap2l) {
-        p2l_off[c] = p2l_rows;
-        for (int e = T.x_ptr[c]; e < T.x_ptr[c + 1]; ++e) {
-            const int src = T.x_idx[e];
-            for (int k = 0; k < T.piece_count[src]; ++k) p2l_item.push_back(make_int2(T.piece_start[src] + k, e));
-            p2l_rows += T.piece_count[src];
+    Joiner j_p2l;   // on a helper thread while the node items and tables are built
+    j_p2l.run(guarded([&] {
+        for (int c : ap2l) {
+            p2l_off[c] = p2l_rows;
+            for (int e = T.x_ptr[c]; e < T.x_ptr[c + 1]; ++e) {
+                const int src = T.x_idx[e];
+                for (int k = 0; k < T.piece_count[src]; ++k)
+                    p2l_item.push_back(make_int2(T.piece_start[src] + k, e));
+                p2l_rows += T.piece_count[src];
+            }
+            p2l_cnt[c] = int(p2l_rows - p2l_off[c]);
         }
-        p2l_cnt[c] = int(p2l_rows - p2l_off[c]);
-    }
-    I.p2l_rows = p2l_rows;
+    }));
     {
         cudaDeviceProp prop;
         int dev = 0;
@@ -1130,6 +1180,12 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         for (size_t i = 0; i < v.size(); ++i) f[i] = make_float2((float)v[i].real(), (float)v[i].imag());
         return f;
     };
+    j_p2l.join();
+    if (helper_oom) {
+        err = "fmm build: host allocation failed";
+        return DC_ERR_OOM;
+    }
+    I.p2l_rows = p2l_rows;
     cudaError_t e;
 #define UP(buf, vec)                                                   \
     if ((e = upload(buf, vec, st)) != cudaSuccess) {                   \
