@@ -24,27 +24,99 @@ void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 namespace {
 thread_local FreeDefer *t_defer = nullptr;
+thread_local DevPool *t_pool = nullptr;
+void free_now(void *p, size_t bytes) {   // to the thread's pool, else cudaFree
+    if (t_pool) {
+        try {
+            t_pool->put(p, bytes);
+            return;
+        } catch (...) {   // no room to record it: free now
+        }
+    }
+    cudaFree(p);
 }
+}  // namespace
 FreeDefer::FreeDefer() : prev(t_defer) { t_defer = this; }
 FreeDefer::~FreeDefer() {
     flush();
     t_defer = prev;
 }
 void FreeDefer::flush() {
-    for (void *p : ptrs) cudaFree(p);
+    for (auto &b : ptrs) free_now(b.first, b.second);
     ptrs.clear();
 }
-void dev_free(void *p) {
+void FreeDefer::take(std::vector<std::pair<void *, size_t>> &out) {
+    out.insert(out.end(), ptrs.begin(), ptrs.end());
+    ptrs.clear();
+}
+void FreeDefer::adopt(std::vector<std::pair<void *, size_t>> &in) {
+    ptrs.insert(ptrs.end(), in.begin(), in.end());
+    in.clear();
+}
+void dev_free(void *p, size_t bytes) {
     if (!p) return;
     if (t_defer) {
         try {
-            t_defer->ptrs.push_back(p);
+            t_defer->ptrs.emplace_back(p, bytes);
             return;
         } catch (...) {   // no room to hold it back: free now
         }
     }
-    cudaFree(p);
+    free_now(p, bytes);
 }
+cudaError_t dev_alloc(void **p, size_t bytes) {
+    *p = nullptr;
+    if (t_pool) {
+        try {
+            if ((*p = t_pool->get(bytes)) != nullptr) return cudaSuccess;
+        } catch (...) {
+        }
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) *p = nullptr;
+    return e;
+}
+void *DevPool::get(size_t bytes) {
+    std::lock_guard<std::mutex> lock(mu_);
+    // the smallest cached block that holds the request without wasting more
+    // than about as much again
+    auto it = free_.lower_bound(bytes);
+    if (it == free_.end() || it->first > 2 * bytes + 4096) return nullptr;
+    Block b = it->second;
+    free_.erase(it);
+    cap_[b.p] = b.cap;
+    return b.p;
+}
+void DevPool::put(void *p, size_t bytes) {
+    std::lock_guard<std::mutex> lock(mu_);
+    size_t cap = bytes;
+    auto it = cap_.find(p);
+    if (it != cap_.end()) {
+        cap = std::max(cap, it->second);
+        cap_.erase(it);
+    }
+    free_.emplace(cap, Block{p, cap, gen_});
+}
+void DevPool::next_generation() {
+    std::lock_guard<std::mutex> lock(mu_);
+    for (auto it = free_.begin(); it != free_.end();) {
+        if (it->second.gen < gen_) {
+            cudaFree(it->second.p);
+            it = free_.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    ++gen_;
+}
+void DevPool::trim() {
+    std::lock_guard<std::mutex> lock(mu_);
+    for (auto &kv : free_) cudaFree(kv.second.p);
+    free_.clear();
+}
+PoolScope::PoolScope(DevPool *p) : prev(t_pool) { t_pool = p; }
+PoolScope::~PoolScope() { t_pool = prev; }
+DevPool *current_pool() { return t_pool; }
 long long kernel_launches() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace dc
 
@@ -54,6 +126,7 @@ struct dc_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     int state = 0;                 // 0 empty, 1 built, 2 density available
+    dc::DevPool pool;              // idle device blocks recycled between rebuilds
     dc::Geometry geo;
     dc::DevGeom dg;
     DevBuf<double> mu, sigma, b, fmu, sbar, mbar, u64, xy;
@@ -425,6 +498,11 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
     std::string msg;
     for (double &v : ctx->build_ms) v = 0.0;
     const auto t_start = std::chrono::steady_clock::now();
+    // The previous drawing's buffers are recycled through the context's
+    // block cache (no cudaFree / cudaMalloc per buffer): nothing of its may
+    // still run, so the device is drained first (as cudaFree would).
+    DC_CK(ctx, cudaDeviceSynchronize(), "build_tree");
+    dc::PoolScope pool_scope(&ctx->pool);
     auto t_prev = t_start;
     auto lap = [&](int i) {   // the stream drained first
         cudaStreamSynchronize(ctx->stream);
@@ -520,6 +598,7 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
     t_prev = std::chrono::steady_clock::now();
     if (ctx->render_only) {   // a view renders: no solve structures
         DC_CK(ctx, cudaStreamSynchronize(s), "build_tree");
+        ctx->pool.next_generation();
         ctx->state = 1;
         return DC_OK;
     }
@@ -542,6 +621,7 @@ dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl, const int
     lap(9);
     DC_CK(ctx, cudaStreamSynchronize(s), "build_tree");
     ctx->build_ms[10] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    ctx->pool.next_generation();   // blocks no longer taken are freed
     ctx->state = 1;
     return DC_OK;
 }

@@ -7,6 +7,10 @@
 #include <cstdint>
 #include <string>
 #include <vector>
+#include <utility>
+#include <unordered_map>
+#include <mutex>
+#include <map>
 
 #include "dc_fmm.h"
 
@@ -75,15 +79,53 @@ cudaError_t launch_max_diff(const float *a, const double *b, long long n, unsign
 // all of the device's work, including other streams' work that the thread
 // means to overlap.
 struct FreeDefer {
-    std::vector<void *> ptrs;
+    std::vector<std::pair<void *, size_t>> ptrs;   // block, bytes
     FreeDefer *prev;
     FreeDefer();
     ~FreeDefer();
     void flush();
+    void take(std::vector<std::pair<void *, size_t>> &out);    // hands the held frees to the caller
+    void adopt(std::vector<std::pair<void *, size_t>> &in);    // holds another thread's frees too
     FreeDefer(const FreeDefer &) = delete;
     FreeDefer &operator=(const FreeDefer &) = delete;
 };
-void dev_free(void *p);   // cudaFree, or held back by the thread's FreeDefer
+
+// A cache of idle device blocks, one per context.  While a DevPool is
+// installed on a thread (PoolScope), buffers allocated there take a cached
+// block that fits before calling cudaMalloc, and buffers freed there (after
+// a FreeDefer, if one holds them back) return their block to the cache
+// instead of calling cudaFree.  Whoever installs it guarantees that no
+// pending device work reads or writes a block that is freed meanwhile.
+// Blocks not taken during one rebuild are freed at the end of the next.
+class DevPool {
+public:
+    void *get(size_t bytes);          // nullptr when no cached block fits
+    void put(void *p, size_t bytes);
+    void next_generation();           // cudaFree blocks cached before the last call and not taken since
+    void trim();                      // cudaFree every cached block
+    ~DevPool() { trim(); }
+
+private:
+    struct Block {
+        void *p;
+        size_t cap;
+        int gen;
+    };
+    std::mutex mu_;
+    std::multimap<size_t, Block> free_;   // by capacity
+    std::unordered_map<void *, size_t> cap_;   // capacities of the blocks handed out
+    int gen_ = 0;
+};
+struct PoolScope {
+    explicit PoolScope(DevPool *p);
+    ~PoolScope();
+    DevPool *prev;
+    PoolScope(const PoolScope &) = delete;
+    PoolScope &operator=(const PoolScope &) = delete;
+};
+DevPool *current_pool();                        // the pool installed on this thread, or null
+cudaError_t dev_alloc(void **p, size_t bytes);  // the thread's pool, else cudaMalloc
+void dev_free(void *p, size_t bytes);           // held back, cached, or cudaFree
 
 template <typename T>
 struct DevBuf {
@@ -96,7 +138,7 @@ struct DevBuf {
     cudaError_t alloc(size_t count) {
         release();
         if (count == 0) return cudaSuccess;
-        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&ptr), count * sizeof(T));
+        cudaError_t e = dev_alloc(reinterpret_cast<void **>(&ptr), count * sizeof(T));
         if (e == cudaSuccess) n = count; else ptr = nullptr;
         return e;
     }
@@ -105,7 +147,7 @@ struct DevBuf {
         return alloc(count);
     }
     void release() {
-        if (ptr) dev_free(ptr);
+        if (ptr) dev_free(ptr, n * sizeof(T));
         ptr = nullptr;
         n = 0;
     }

@@ -648,9 +648,8 @@ cudaError_t Fmm::Impl::build_rows(cudaStream_t st) {
         if (r != cudaSuccess || src.n == 0) return r;
         passes::rows_to_ff_kernel<<<4 * n_sms, 256, 0, st>>>(src.ptr, dst.ptr, src.n);
         note_launch();
-        r = cudaStreamSynchronize(st);
-        src.release();
-        return r;
+        src.release();   // a device-wide wait in cudaFree, or held back
+        return cudaGetLastError();
     };
     if ((e = to_ff(p2m_g64, p2m_gff)) != cudaSuccess || (e = to_ff(p2m_f64, p2m_fff)) != cudaSuccess ||
         (e = to_ff(p2l_g64, p2l_gff)) != cudaSuccess || (e = to_ff(p2l_f64, p2l_fff)) != cudaSuccess)
@@ -691,6 +690,12 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     // deferred (cudaFree would wait for that stream too).  On an early
     // return the guard joins the threads and drains the stream.
     FreeDefer defer;
+    // written by the helper threads: declared before their guard, which
+    // joins them before these go out of scope
+    cudaError_t pre_err = cudaSuccess;
+    bool pre_oom = false;
+    Impl::Prep32 prep;
+    bool prep_failed = false;
     struct Overlap {
         // the coarse plan, the preconditioner's launches, the FP32 form's host arrays
         std::thread th_plan, th, th32;
@@ -702,8 +707,6 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
             if (drain) cudaStreamSynchronize(drain);
         }
     } ov;
-    cudaError_t pre_err = cudaSuccess;
-    bool pre_oom = false;
     {
         // the preconditioner's stream at the lowest priority and the tree's
         // at the highest: the tree build's short kernels, each waited for by
@@ -759,8 +762,10 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         if (ov.th_plan.joinable()) ov.th_plan.join();
         int dev = 0;
         cudaGetDevice(&dev);
-        auto pre = [&I, &D, &pre_err, &pre_oom, dev] {
+        DevPool *pool = current_pool();
+        auto pre = [&I, &D, &pre_err, &pre_oom, dev, pool] {
             try {
+                PoolScope ps(pool);
                 cudaError_t r = cudaSetDevice(dev);
                 if (r == cudaSuccess && !I.render_only && !pre_oom) r = I.coarse.launch(D, I.pre_stream);
                 if (r == cudaSuccess) r = I.pinv.alloc((size_t)D.n_panels * D.g * D.g);
@@ -1009,8 +1014,6 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     phase(0);   // quadtree, lists, tables, multi-level M2M chunks
     // the FP32 form's host arrays (tree and discretisation only) on a helper
     // thread while the schedules, preconditioner and coefficients are built
-    Impl::Prep32 prep;
-    bool prep_failed = false;
     if (I.fp32) {
         auto run = [&T, &G, &prep, &prep_failed] {
             try {
@@ -1347,7 +1350,6 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
         return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
     }
     ov.drain = nullptr;
-    defer.flush();
     {
         std::vector<int> info(D.n_panels);
         e = cudaMemcpy(info.data(), I.pinfo.ptr, info.size() * sizeof(int), cudaMemcpyDeviceToHost);
@@ -1374,16 +1376,50 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     cudaFuncSetAttribute(passes::m2m_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)passes::mlff_smem(I.P1));
     phase(2);   // two-level preconditioner
+    // The node near / far coefficients on a helper thread and the tree's
+    // stream (free again) while the stored rows and the FP32 form are built
+    // here; the helper's frees are held back and done with this thread's at
+    // the end, so that no cudaFree waits for the other's kernels.
+    cudaError_t near_err = cudaSuccess;
+    bool near_oom = false;
+    std::vector<std::pair<void *, size_t>> near_frees;
+    struct Adopt {   // the helper's held frees join this thread's, on every return
+        FreeDefer &d;
+        std::vector<std::pair<void *, size_t>> &v;
+        ~Adopt() { d.adopt(v); }
+    } adopt_near{defer, near_frees};
+    Joiner j_near;   // joined before the variables above go out of scope
+    if (!I.render_only) {
+        if ((e = cudaEventRecord(I.pre_ev, st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(I.tree_stream, I.pre_ev, 0)) != cudaSuccess) {
+            err = std::string("fmm event: ") + cudaGetErrorString(e);
+            return DC_ERR_CUDA;
+        }
+        int dev = 0;
+        cudaGetDevice(&dev);
+        DevPool *pool = current_pool();
+        j_near.run([&I, &near_err, &near_oom, &near_frees, dev, pool] {
+            PoolScope ps(pool);
+            FreeDefer held;
+            try {
+                near_err = cudaSetDevice(dev);
+                if (near_err == cudaSuccess) near_err = I.build_near(I.tree_stream);
+            } catch (...) {
+                near_oom = true;
+            }
+            // its kernels are done before any block it released is recycled
+            cudaStreamSynchronize(I.tree_stream);
+            try {
+                held.take(near_frees);
+            } catch (...) {   // no room to hand them over: the guard frees them here
+            }
+        });
+    }
     if ((e = I.build_rows(st)) != cudaSuccess) {
         err = std::string("stored P2M / P2L coefficients: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
     }
     phase(3);   // stored P2M / P2L rows
-    if (!I.render_only && (e = I.build_near(st)) != cudaSuccess) {
-        err = std::string("near-field coefficients: ") + cudaGetErrorString(e);
-        return e == cudaErrorMemoryAllocation ? DC_ERR_OOM : DC_ERR_CUDA;
-    }
-    phase(4);   // near / far coefficients
     if (ov.th32.joinable()) ov.th32.join();
     if (prep_failed) {
         err = "fmm32 build: host allocation failed";
@@ -1391,6 +1427,18 @@ dc_status Fmm::build(const dc_options &opt, const Geometry &G, const DevGeom &D,
     }
     dc_status r = I.fp32 ? I.build32(G, prep, txy, start, cnt, st, err) : DC_OK;
     phase(5);   // FP32 form
+    j_near.join();
+    if (near_oom || near_err != cudaSuccess) {
+        err = near_oom ? std::string("near-field coefficients: host allocation failed")
+                       : std::string("near-field coefficients: ") + cudaGetErrorString(near_err);
+        return (near_oom || near_err == cudaErrorMemoryAllocation) ? DC_ERR_OOM : DC_ERR_CUDA;
+    }
+    if (!I.render_only && ((e = cudaEventRecord(I.pre_ev, I.tree_stream)) != cudaSuccess ||
+                           (e = cudaStreamWaitEvent(st, I.pre_ev, 0)) != cudaSuccess)) {
+        err = std::string("fmm event: ") + cudaGetErrorString(e);
+        return DC_ERR_CUDA;
+    }
+    phase(4);   // near / far coefficients (the wait for them)
     return r;
 }
 
