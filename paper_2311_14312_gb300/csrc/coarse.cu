@@ -60,11 +60,17 @@ __device__ __forceinline__ float mono32(float2 q, float2 c) { return kMonoLog2 *
 // reproduces constants) at the nodes of panel i, minus its monopole.  One
 // warp per pair; with g <= 16 each node takes two lanes, which split the
 // segments between them.  A segment within kNearSeg chord lengths of the
-// node (and the node's own segment, singular) runs in FP64; the others,
-// whose terms are smooth, in FP32 on coordinates taken relative to the node
-// in FP64 (the same closed form, App. D): the FP64 logarithms and
-// arctangents cost 64 times as much here.
+// node (and the node's own segment, singular) needs the FP64 closed form;
+// the others, whose terms are smooth, take the FP32 one on coordinates
+// taken relative to the node in FP64 (the same closed form, App. D).  The
+// FP64 logarithms and arctangents are this GPU's slowest path, and a warp
+// pays for an FP64 instruction whatever lanes it runs for: the first sweep
+// does the FP32 terms and lists the near (node, segment) entries in shared
+// memory (in sweep order), the warp then computes the listed entries with
+// all lanes busy, and each node adds its entries in list order (entries
+// beyond the list's room are computed in place).
 constexpr double kNearSeg = 8.0;
+constexpr int kNearCap = 512;
 __global__ void __launch_bounds__(32) near_pairs_kernel(const int2 *__restrict__ pairs, const double *__restrict__ seg,
                                                         const double *__restrict__ segw,
                                                         const double *__restrict__ nxy, const int *__restrict__ nseg,
@@ -73,6 +79,8 @@ __global__ void __launch_bounds__(32) near_pairs_kernel(const int2 *__restrict__
                                                         const float2 *__restrict__ c32,
                                                         const double *__restrict__ plen, int s, int g,
                                                         double *__restrict__ corr) {
+    __shared__ int nl_tag[kNearCap];      // node m << 16 | segment kk
+    __shared__ double nl_g[kNearCap];
     const int e = blockIdx.x, lane = threadIdx.x;
     const int halves = g <= 16 ? 2 : 1;
     const int m = halves == 2 ? (lane & 15) : lane, part = halves == 2 ? (lane >> 4) : 0;
@@ -81,27 +89,56 @@ __global__ void __launch_bounds__(32) near_pairs_kernel(const int2 *__restrict__
     const int a = pr.x * g + (valid ? m : 0), j = pr.y;
     const double qx = nxy[2 * a], qy = nxy[2 * a + 1];
     const int own1 = nseg[a], own2 = nseg2[a];
-    double acc64 = 0.0;
+    double acc64 = 0.0;   // entries beyond the list's room
     float acc = 0.f;
-    if (valid)
-        for (int kk = part; kk < s; kk += halves) {
-            const int k = j * s + kk;
-            const double *q = seg + 4 * (size_t)k;
-            const double ax = q[0] - qx, ay = q[1] - qy, bx = q[2] - qx, by = q[3] - qy;
-            const double dx = q[2] - q[0], dy = q[3] - q[1];
-            if (k == own1 || k == own2 || seg_is_near(ax, ay, bx, by, dx, dy, kNearSeg)) {
-                double G, F;
-                seg_gf_f64(qx, qy, q[0], q[1], q[2], q[3], segw[k], k == own1 || k == own2, G, F);
-                acc64 += G;
+    int listed = 0;       // entries listed so far (the same in every lane)
+    const int sweeps = (s + halves - 1) / halves;
+    for (int it = 0; it < sweeps; ++it) {
+        const int kk = part + it * halves;
+        const bool act = valid && kk < s;
+        const int k = j * s + (act ? kk : 0);
+        const double *q = seg + 4 * (size_t)k;
+        const double ax = q[0] - qx, ay = q[1] - qy, bx = q[2] - qx, by = q[3] - qy;
+        const double dx = q[2] - q[0], dy = q[3] - q[1];
+        const bool own = k == own1 || k == own2;
+        const bool near = act && (own || seg_is_near(ax, ay, bx, by, dx, dy, kNearSeg));
+        const unsigned bal = __ballot_sync(0xffffffffu, near);
+        if (near) {
+            const int pos = listed + __popc(bal & ((1u << lane) - 1u));
+            if (pos < kNearCap) {
+                nl_tag[pos] = (m << 16) | kk;
             } else {
-                acc += (float)segw[k] * seg_g_far_f32(ax, ay, bx, by, dx, dy);
+                double G, F;
+                seg_gf_f64(qx, qy, q[0], q[1], q[2], q[3], segw[k], own, G, F);
+                acc64 += G;
             }
+        } else if (act) {
+            acc += (float)segw[k] * seg_g_far_f32(ax, ay, bx, by, dx, dy);
         }
+        listed += __popc(bal);
+    }
+    __syncwarp();
+    const int n_list = min(listed, kNearCap);
+    for (int i = lane; i < n_list; i += 32) {
+        const int mi = nl_tag[i] >> 16, k = j * s + (nl_tag[i] & 0xffff);
+        const int ai = pr.x * g + mi;
+        const double *q = seg + 4 * (size_t)k;
+        double G, F;
+        seg_gf_f64(nxy[2 * ai], nxy[2 * ai + 1], q[0], q[1], q[2], q[3], segw[k], k == nseg[ai] || k == nseg2[ai],
+                   G, F);
+        nl_g[i] = G;
+    }
+    __syncwarp();
     if (halves == 2) {
         acc64 += __shfl_down_sync(0xffffffffu, acc64, 16);
         acc += __shfl_down_sync(0xffffffffu, acc, 16);
     }
-    if (valid && part == 0) corr[(size_t)e * g + m] = acc64 + (double)acc - plen[j] * (double)mono32(q32[a], c32[j]);
+    if (valid && part == 0) {
+        double near_sum = 0.0;
+        for (int i = 0; i < n_list; ++i)
+            if ((nl_tag[i] >> 16) == m) near_sum += nl_g[i];
+        corr[(size_t)e * g + m] = near_sum + acc64 + (double)acc - plen[j] * (double)mono32(q32[a], c32[j]);
+    }
 }
 
 // Ac[i][j] = sum_m (l_j mono32(q_{i,m}, c_j) + corr), padded with the identity

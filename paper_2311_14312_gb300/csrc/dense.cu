@@ -198,7 +198,12 @@ dense_eval_points_kernel(const double *__restrict__ seg, const double *__restric
 // segments.  Segments within kBlockNearSeg chord lengths of the node (and
 // its own, singular) take the FP64 closed form, the others the FP32 one on
 // FP64 relative coordinates (smooth terms; the blocks only precondition).
+// As in the coarse level's near pairs, the first sweep does the FP32 terms
+// and lists the near (row, segment) entries, whose FP64 closed forms the
+// warp then computes with all lanes busy; each row adds its entries in
+// list order (entries beyond the list's room are computed in place).
 constexpr double kBlockNearSeg = 8.0;
+constexpr int kBlockNearCap = 512;
 template <int MAXG>
 __global__ void __launch_bounds__(32) panel_blocks_kernel(const double *__restrict__ seg,
                                                           const double *__restrict__ segw,
@@ -206,6 +211,8 @@ __global__ void __launch_bounds__(32) panel_blocks_kernel(const double *__restri
                                                           const int *__restrict__ nseg2,
                                                           const double *__restrict__ lam,
                                                           double *__restrict__ blocks, int s, int g) {
+    __shared__ int nl_tag[kBlockNearCap];   // row m << 16 | segment kk
+    __shared__ double nl_g[kBlockNearCap];
     const int j = blockIdx.x, lane = threadIdx.x;
     const int halves = g <= 16 ? 2 : 1;
     const int m = halves == 2 ? (lane & 15) : lane, part = halves == 2 ? (lane >> 4) : 0;
@@ -216,29 +223,66 @@ __global__ void __launch_bounds__(32) panel_blocks_kernel(const double *__restri
     double acc[MAXG];
 #pragma unroll
     for (int n = 0; n < MAXG; ++n) acc[n] = 0.0;
-    if (valid)
-        for (int kk = part; kk < s; kk += halves) {
-            const int k = j * s + kk;
-            const double *q = seg + 4 * (size_t)k;
-            const double ax = q[0] - qx, ay = q[1] - qy, bx = q[2] - qx, by = q[3] - qy;
-            const double dx = q[2] - q[0], dy = q[3] - q[1];
-            double G;
-            if (k == own1 || k == own2 || seg_is_near(ax, ay, bx, by, dx, dy, kBlockNearSeg)) {
-                double F;
-                seg_gf_f64(qx, qy, q[0], q[1], q[2], q[3], segw[k], k == own1 || k == own2, G, F);
+    int listed = 0;   // the same in every lane
+    const int sweeps = (s + halves - 1) / halves;
+    for (int it = 0; it < sweeps; ++it) {
+        const int kk = part + it * halves;
+        const bool act = valid && kk < s;
+        const int k = j * s + (act ? kk : 0);
+        const double *q = seg + 4 * (size_t)k;
+        const double ax = q[0] - qx, ay = q[1] - qy, bx = q[2] - qx, by = q[3] - qy;
+        const double dx = q[2] - q[0], dy = q[3] - q[1];
+        const bool own = k == own1 || k == own2;
+        const bool near = act && (own || seg_is_near(ax, ay, bx, by, dx, dy, kBlockNearSeg));
+        const unsigned bal = __ballot_sync(0xffffffffu, near);
+        double G = 0.0;
+        bool add = false;
+        if (near) {
+            const int pos = listed + __popc(bal & ((1u << lane) - 1u));
+            if (pos < kBlockNearCap) {
+                nl_tag[pos] = (m << 16) | kk;
             } else {
-                G = segw[k] * (double)seg_g_far_f32(ax, ay, bx, by, dx, dy);
+                double F;
+                seg_gf_f64(qx, qy, q[0], q[1], q[2], q[3], segw[k], own, G, F);
+                add = true;
             }
+        } else if (act) {
+            G = segw[k] * (double)seg_g_far_f32(ax, ay, bx, by, dx, dy);
+            add = true;
+        }
+        if (add) {
             const double *lr = lam + (size_t)kk * g;
 #pragma unroll
             for (int n = 0; n < MAXG; ++n)
                 if (n < g) acc[n] += G * lr[n];
         }
+        listed += __popc(bal);
+    }
+    __syncwarp();
+    const int n_list = min(listed, kBlockNearCap);
+    for (int u = lane; u < n_list; u += 32) {
+        const int mi = nl_tag[u] >> 16, k = j * s + (nl_tag[u] & 0xffff);
+        const int ii = j * g + mi;
+        const double *q = seg + 4 * (size_t)k;
+        double G, F;
+        seg_gf_f64(nxy[2 * ii], nxy[2 * ii + 1], q[0], q[1], q[2], q[3], segw[k], k == nseg[ii] || k == nseg2[ii],
+                   G, F);
+        nl_g[u] = G;
+    }
+    __syncwarp();
     if (halves == 2) {
 #pragma unroll
         for (int n = 0; n < MAXG; ++n) acc[n] += __shfl_down_sync(0xffffffffu, acc[n], 16);
     }
     if (!valid || part != 0) return;
+    for (int u = 0; u < n_list; ++u) {
+        if ((nl_tag[u] >> 16) != m) continue;
+        const double G = nl_g[u];
+        const double *lr = lam + (size_t)(nl_tag[u] & 0xffff) * g;
+#pragma unroll
+        for (int n = 0; n < MAXG; ++n)
+            if (n < g) acc[n] += G * lr[n];
+    }
     double *row = blocks + ((size_t)j * g + m) * g;
 #pragma unroll
     for (int n = 0; n < MAXG; ++n)
