@@ -228,7 +228,10 @@ void dc_destroy(dc_ctx *ctx);
  *                are linear in the Bezier parameter t between the ends
  * Errors: DC_ERR_ARG for bad sizes/ordering/non-finite values,
  * DC_ERR_GEOMETRY for a zero-length curve or panel, DC_ERR_OOM/CUDA.
- * Replaces any previous drawing of the context. */
+ * Replaces any previous drawing of the context.  It first waits for the
+ * device's queued work (as a cudaFree would: the previous drawing's device
+ * buffers are recycled for the new one); it runs helper host threads and
+ * streams of its own and returns with the build complete. */
 dc_status dc_build_tree(dc_ctx *ctx, int n_curves, const double *ctrl,
                         const int *panel_ptr, const double *panel_start,
                         const double *colours);
