@@ -528,6 +528,18 @@ dc_status dc_aux_adaptive_panels(int n_curves, const double *ctrl, double ratio,
                                  int min_panels, double max_len, int capacity, int *panel_ptr,
                                  double *panel_start, int *n_panels);
 
+/* Auxiliary, host only (no GPU): the discretisation dc_build_tree starts
+ * from (Sec. 4.2, App. A-B), with the inputs of dc_build_tree (explicit
+ * panels) and g, s as in dc_options.  With P = panel_ptr[n_curves],
+ * N = P g nodes and S = P s segments it writes, each when not NULL:
+ * node_xy host [N][2] collocation points, node_t [N] their Bezier
+ * parameters, seg_xy [S][4] segment end points (x1 y1 x2 y2), seg_w [S]
+ * arc length / chord length, u_plus and u_minus [N][3] boundary colours.
+ * Errors as dc_build_tree's: DC_ERR_ARG, DC_ERR_GEOMETRY. */
+dc_status dc_aux_discretise(int n_curves, const double *ctrl, const int *panel_ptr, const double *panel_start,
+                            const double *colours, int g, int s, double *node_xy, double *node_t,
+                            double *seg_xy, double *seg_w, double *u_plus, double *u_minus);
+
 /* ---------------------------------------------------------------------
  * Learned warm start (no counterpart in the paper: its warm start, Sec. 6.1,
  * re-uses an earlier solution).  A 4-layer perceptron

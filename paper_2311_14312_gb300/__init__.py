@@ -122,7 +122,7 @@ EXPORTS = ["dc_default_options", "dc_create", "dc_destroy", "dc_build_tree", "dc
            "dc_aux_build_timings", "dc_aux_test_skip_mma_tile", "dc_aux_fp32_peak",
            "dc_aux_time_inner_m2l", "dc_subdivide", "dc_get_panels", "dc_aux_subdivision_info",
            "dc_aux_adaptive_panels", "dc_autotune", "dc_solve_mixed", "dc_view_update", "dc_view_reset",
-           "dc_aux_tree_compare"]
+           "dc_aux_tree_compare", "dc_aux_discretise"]
 
 
 def _load():
@@ -179,6 +179,7 @@ def _load():
     lib.dc_aux_tree_compare.argtypes = [P, P]
     lib.dc_aux_subdivision_info.argtypes = [P, P, P, P]
     lib.dc_aux_adaptive_panels.argtypes = [I, P, D, I, I, D, I, P, P, P]
+    lib.dc_aux_discretise.argtypes = [I, P, P, P, P, I, I, P, P, P, P, P, P]
     lib.dc_autotune.argtypes = [P, I, ctypes.POINTER(dc_viewport), I, P, I, P, I, P, D, I,
                                 ctypes.POINTER(dc_autotune_row), P]
     for name in EXPORTS:
@@ -536,6 +537,26 @@ def aux_adaptive_panels(ctrl, ratio=0.2, max_level=8, min_panels=2, max_len=0.5)
     if st != DC_OK:
         raise DcError(st, "dc_aux_adaptive_panels failed")
     return ptr, start[:cnt.value]
+
+
+def aux_discretise(ctrl, panel_ptr, panel_start, colours, g=16, s_per_panel=80):
+    """Host-only discretisation (dc_aux_discretise): dict of node_xy [N, 2],
+    node_t [N], seg_xy [S, 4], seg_w [S], u_plus / u_minus [N, 3]."""
+    ctrl = np.ascontiguousarray(ctrl, dtype=np.float64)
+    ptr = np.ascontiguousarray(panel_ptr, dtype=np.int32)
+    start = np.ascontiguousarray(panel_start, dtype=np.float64)
+    col = np.ascontiguousarray(colours, dtype=np.float64)
+    n = int(ctrl.shape[0])
+    P = int(ptr[n])
+    N, S = P * int(g), P * int(s_per_panel)
+    out = dict(node_xy=np.zeros((N, 2)), node_t=np.zeros(N), seg_xy=np.zeros((S, 4)), seg_w=np.zeros(S),
+               u_plus=np.zeros((N, 3)), u_minus=np.zeros((N, 3)))
+    st = _get_lib().dc_aux_discretise(n, _ptr(ctrl), _ptr(ptr), _ptr(start), _ptr(col), int(g), int(s_per_panel),
+                                      _ptr(out["node_xy"]), _ptr(out["node_t"]), _ptr(out["seg_xy"]),
+                                      _ptr(out["seg_w"]), _ptr(out["u_plus"]), _ptr(out["u_minus"]))
+    if st != DC_OK:
+        raise DcError(st, "dc_aux_discretise failed")
+    return out
 
 
 def kernel_launches() -> int:

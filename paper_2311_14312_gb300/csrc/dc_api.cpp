@@ -1624,6 +1624,25 @@ dc_status dc_aux_adaptive_panels(int n_curves, const double *ctrl, double ratio,
     return DC_OK;
 }
 
+dc_status dc_aux_discretise(int n_curves, const double *ctrl, const int *panel_ptr, const double *panel_start,
+                            const double *colours, int g, int s, double *node_xy, double *node_t, double *seg_xy,
+                            double *seg_w, double *u_plus, double *u_minus) {
+    dc::Geometry G;
+    std::string msg;
+    dc_status st = dc::discretise(n_curves, ctrl, panel_ptr, panel_start, colours, g, s, G, msg);
+    if (st != DC_OK) return st;
+    auto put = [](double *dst, const std::vector<double> &v) {
+        if (dst && !v.empty()) std::memcpy(dst, v.data(), sizeof(double) * v.size());
+    };
+    put(node_xy, G.node_xy);
+    put(node_t, G.node_t);
+    put(seg_xy, G.seg_xy);
+    put(seg_w, G.seg_w);
+    put(u_plus, G.u_plus);
+    put(u_minus, G.u_minus);
+    return DC_OK;
+}
+
 // ------------------------------------------------------------- autotune --
 dc_status dc_autotune(dc_ctx *ctx, int n_vp, const dc_viewport *vps, int n_leaf, const int *leaf_sizes,
                       int n_pinner, const int *p_inners, int n_tile, const int *eval_tiles, double tol,
