@@ -369,7 +369,7 @@ __device__ __forceinline__ void dot2_step(float &hi, float &lo, float w, float2 
 // shared memory kSolveCols columns at a time and serves all of the block's
 // rows.  Compensated (float-float) sums: M amplifies by ~1e4-1e5, and its
 // rounding must stay well below the FP32 operator's own error.
-constexpr int kSolveRows = 8, kSolveCols = 2048;
+constexpr int kSolveRows = 8, kSolveCols = 2048, kSolveLoads = 8;
 __global__ void __launch_bounds__(32 * kSolveRows) coarse_solve_kernel(const float *__restrict__ Ainv, int n_pad, int P,
                                                                        const float2 *__restrict__ s,
                                                                        const float *__restrict__ plen32,
@@ -387,16 +387,17 @@ __global__ void __launch_bounds__(32 * kSolveRows) coarse_solve_kernel(const flo
         __syncthreads();
         for (int u = threadIdx.x; u < 3 * cn; u += 32 * kSolveRows) ss[u] = s[3 * (size_t)c0 + u];
         __syncthreads();
-        for (int jj = lane; jj < cn; jj += 4 * 32) {
-            // four columns' loads in flight per lane (a missing column adds exact zeros)
-            float wv[4];
+        for (int jj = lane; jj < cn; jj += kSolveLoads * 32) {
+            // kSolveLoads columns' loads in flight per lane (the warp waits on
+            // load latency: one warp per row leaves most warp slots empty)
+            float wv[kSolveLoads];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kSolveLoads; ++u) {
                 const int j = jj + 32 * u;
                 wv[u] = j < cn ? row[c0 + j] : 0.f;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kSolveLoads; ++u) {
                 const int j = jj + 32 * u;
                 if (j >= cn) break;
                 dot2_step(h0, l0, wv[u], ss[3 * j]);
