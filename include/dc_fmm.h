@@ -623,9 +623,11 @@ dc_status dc_aux_apply_operator(dc_ctx *ctx, int op, int inner, const double *x,
 dc_status dc_aux_precond_info(dc_ctx *ctx, double *out);
 
 /* Auxiliary: wall-clock ms of the last dc_build_tree, by phase (each phase
- * drains the stream before it is timed): out[0] discretisation (host),
- * out[1] uploads, out[2..7] the FMM build (quadtree and lists; schedules and
- * uploads; two-level preconditioner; stored P2M / P2L rows; near / far
+ * drains the context's stream before it is timed): out[0] discretisation
+ * (host), out[1] uploads, out[2..7] the FMM build (quadtree and lists;
+ * schedules and uploads; the wait for the two-level preconditioner, whose
+ * work runs beside the two phases before it; stored P2M / P2L rows, with
+ * the node near / far coefficients built beside them; the wait for those
  * coefficients; FP32 form), out[8] panel features, out[9] G_H 1, out[10]
  * total.  out: host array of 11 doubles (zero where a phase does not
  * apply).  Errors: DC_ERR_STATE before dc_build_tree. */
